@@ -1,0 +1,160 @@
+"""Seeded synthetic time-varying 2-D vector fields.
+
+These stand in for the paper's datasets (Table I: SCF, CFVKV, HCBA, FS, DT),
+which are not available: they reproduce shapes and value regimes only, not the
+datasets' contents.  Every field is float32 with layout [T][H][W][2]
+(interleaved u, v; j is the fast x axis, i the y axis).  x = column j, y = row
+i; u is the x velocity, v the y velocity.  This module holds no arithmetic of
+the compression method: it only draws inputs, shared by the oracle tests and
+the GPU path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# workload name -> (H, W, T, relative error bound)
+WORKLOADS = {
+    "vortex64": (64, 64, 8, 1e-2),
+    "street512": (512, 512, 100, 1e-3),
+    "jets721": (721, 1440, 48, 1e-3),
+}
+
+
+def _add_vortex(u, v, cx, cy, R, amp, sign, win=4.0):
+    """Adds a Gaussian vortex with streamfunction psi = s*amp*R*exp(-r^2/(2R^2)),
+    u = d(psi)/dy, v = -d(psi)/dx, evaluated in a +-win*R window."""
+    H, W = u.shape
+    r = int(np.ceil(win * R))
+    i0, i1 = max(0, int(np.floor(cy)) - r), min(H, int(np.floor(cy)) + r + 2)
+    j0, j1 = max(0, int(np.floor(cx)) - r), min(W, int(np.floor(cx)) + r + 2)
+    if i0 >= i1 or j0 >= j1:
+        return
+    yy = np.arange(i0, i1, dtype=np.float64)[:, None] - cy
+    xx = np.arange(j0, j1, dtype=np.float64)[None, :] - cx
+    e = np.exp(-(xx * xx + yy * yy) / (2.0 * R * R))
+    u[i0:i1, j0:j1] += -sign * amp * yy / R * e
+    v[i0:i1, j0:j1] += sign * amp * xx / R * e
+
+
+def vortex_sum(H=64, W=64, T=8, seed=1000, n_vortex=6, drift=0.5, noise=1e-3):
+    """Sum of Gaussian vortices (random centres in [8, H-8]x[8, W-8], radii
+    U[4,10], unit amplitude with random sign) whose centres drift `drift`
+    cells per step in +x, plus N(0, noise) per component."""
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(8, W - 8, n_vortex)
+    cy = rng.uniform(8, H - 8, n_vortex)
+    R = rng.uniform(4, 10, n_vortex)
+    s = rng.choice([-1.0, 1.0], n_vortex)
+    out = np.empty((T, H, W, 2), np.float32)
+    for t in range(T):
+        u = np.zeros((H, W))
+        v = np.zeros((H, W))
+        for k in range(n_vortex):
+            _add_vortex(u, v, cx[k] + drift * t, cy[k], R[k], 1.0, s[k], win=6.0)
+        u += rng.normal(0.0, noise, (H, W))
+        v += rng.normal(0.0, noise, (H, W))
+        out[t, :, :, 0] = u
+        out[t, :, :, 1] = v
+    return out
+
+
+def vortex_street(H=512, W=512, T=100, seed=1001, period=10, speed=1.5, R=12.0, amp=1.0,
+                  x0=64.0, offset=40.0, shear=0.3, noise=1e-3):
+    """Von Karman-like street: vortex pairs at y = H/2 +- offset shed at x = x0
+    every `period` steps with alternating sign, advected at `speed` cells per
+    step in +x and dropped once past the domain; background shear
+    u = shear*(i - H/2)/(H/2); plus N(0, noise)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((T, H, W, 2), np.float32)
+    cy0 = H / 2.0
+    first = -int(np.ceil((W - x0) / speed / period)) - 1
+    for t in range(T):
+        u = np.repeat((shear * (np.arange(H) - cy0) / cy0)[:, None], W, axis=1).astype(np.float64)
+        v = np.zeros((H, W))
+        for n in range(first, t // period + 1):
+            ts = n * period
+            if ts > t:
+                continue
+            x = x0 + speed * (t - ts)
+            if x > W + 4 * R:
+                continue
+            sgn = 1.0 if n % 2 == 0 else -1.0
+            _add_vortex(u, v, x, cy0 + offset, R, amp, sgn)
+            _add_vortex(u, v, x, cy0 - offset, R, amp, -sgn)
+        u += rng.normal(0.0, noise, (H, W))
+        v += rng.normal(0.0, noise, (H, W))
+        out[t, :, :, 0] = u
+        out[t, :, :, 1] = v
+    return out
+
+
+def zonal_jets(H=721, W=1440, T=48, seed=1002, n_eddy=200, cell_m=27750.0, step_s=3600.0):
+    """Wind-like lat-lon field in cells per step: zonal jets u = U(phi) sin(3 phi)
+    with U ~ U[10,40] m/s per jet band, plus `n_eddy` Gaussian eddies (radius
+    U[5,20] cells, amplitude U[5,30] m/s, random sign) moving with the local jet
+    speed.  Row i is latitude 90 - 180 i/(H-1) degrees; no wrap in longitude."""
+    rng = np.random.default_rng(seed)
+    ms = step_s / cell_m  # m/s -> cells per step
+    phi = np.deg2rad(90.0 - 180.0 * np.arange(H) / (H - 1))
+    band = np.clip(np.floor((phi + np.pi / 2) / (np.pi / 3)).astype(int), 0, 5)
+    U = rng.uniform(10, 40, 6)
+    ujet = U[band] * np.sin(3 * phi) * ms
+    cx = rng.uniform(0, W, n_eddy)
+    cy = rng.uniform(20, H - 20, n_eddy)
+    R = rng.uniform(5, 20, n_eddy)
+    A = rng.uniform(5, 30, n_eddy) * ms
+    s = rng.choice([-1.0, 1.0], n_eddy)
+    vel = ujet[np.clip(np.round(cy).astype(int), 0, H - 1)]
+    out = np.empty((T, H, W, 2), np.float32)
+    for t in range(T):
+        u = np.repeat(ujet[:, None], W, axis=1).astype(np.float64)
+        v = np.zeros((H, W))
+        for k in range(n_eddy):
+            _add_vortex(u, v, cx[k] + vel[k] * t, cy[k], R[k], A[k], s[k])
+        out[t, :, :, 0] = u
+        out[t, :, :, 1] = v
+    return out
+
+
+def workload(name):
+    """Returns (uv, relative error bound) for a named workload."""
+    if name == "vortex64":
+        return vortex_sum(64, 64, 8, seed=1000), 1e-2
+    if name == "street512":
+        return vortex_street(512, 512, 100, seed=1001), 1e-3
+    if name == "jets721":
+        return zonal_jets(721, 1440, 48, seed=1002), 1e-3
+    raise KeyError(name)
+
+
+def linear_field(H, W, T, a, b, c, d, saddle=False):
+    """u = x - (a + b t), v = +-(y - (c + d t)): one critical point per slice
+    moving along a straight line (x = a + b t, y = c + d t)."""
+    t = np.arange(T, dtype=np.float64)[:, None, None]
+    y = np.arange(H, dtype=np.float64)[None, :, None]
+    x = np.arange(W, dtype=np.float64)[None, None, :]
+    u = x - (a + b * t) + 0 * y
+    v = (y - (c + d * t)) + 0 * x
+    if saddle:
+        v = -v
+    return np.stack([u, v], -1).astype(np.float32)
+
+
+def centre_field(H, W, T, x0, y0):
+    """u = -(y - y0), v = x - x0: a centre at (x0, y0) in every slice."""
+    y = np.arange(H, dtype=np.float64)[None, :, None]
+    x = np.arange(W, dtype=np.float64)[None, None, :]
+    u = -(y - y0) + 0 * x + np.zeros((T, 1, 1))
+    v = (x - x0) + 0 * y + np.zeros((T, 1, 1))
+    return np.stack([u, v], -1).astype(np.float32)
+
+
+def birth_field(H, W, T, x0, y0, k, t0):
+    """u = (x - x0)^2 - k (t - t0), v = y - y0: no critical point before t0,
+    two after (x = x0 +- sqrt(k (t - t0))), joined into one trajectory."""
+    t = np.arange(T, dtype=np.float64)[:, None, None]
+    y = np.arange(H, dtype=np.float64)[None, :, None]
+    x = np.arange(W, dtype=np.float64)[None, None, :]
+    u = (x - x0) ** 2 - k * (t - t0) + 0 * y
+    v = (y - y0) + 0 * x + 0 * t
+    return np.stack([u, v], -1).astype(np.float32)

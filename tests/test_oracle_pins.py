@@ -1,0 +1,502 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every check here is independent of the oracle's own formulas: brute force with
+exact rational arithmetic, closed forms of hand-built fields, the mesh rebuilt
+from the paper's prism split, optimality of Huffman codes, library logarithms.
+"""
+import heapq
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_25143_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Simulation of Simplicity (Sec. III-F, Alg. 1) and the face test (Eqs. 1-3)
+# ---------------------------------------------------------------------------
+def _solve3(A, b):
+    """Gaussian elimination over Fractions (no pivoting shortcuts)."""
+    M = [list(A[r]) + [b[r]] for r in range(3)]
+    for c in range(3):
+        p = next(r for r in range(c, 3) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for r in range(3):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [M[r][k] - f * M[c][k] for k in range(4)]
+    return [M[r][3] / M[r][r] for r in range(3)]
+
+
+def _inside_perturbed(vals, eps=Fraction(1, 1000)):
+    """Origin strictly inside conv of the three perturbed values: solve Eq. 1
+    ([u;v;1] mu = [0;0;1]) exactly for the SoS-perturbed vertex values, the
+    vertex of rank r moved by (eps^(2^(2r-1)), eps^(2^(2r-2)))."""
+    pts = []
+    for r in range(1, 4):
+        u, v = vals[2 * (r - 1)], vals[2 * (r - 1) + 1]
+        pts.append((Fraction(u) + eps ** (2 ** (2 * r - 1)), Fraction(v) + eps ** (2 ** (2 * r - 2))))
+    A = [[p[0] for p in pts], [p[1] for p in pts], [Fraction(1)] * 3]
+    mu = _solve3(A, [Fraction(0), Fraction(0), Fraction(1)])
+    return all(m > 0 for m in mu)
+
+
+def test_sos_predicate_exhaustive_small_domain():
+    """All 5^6 faces with values in {-2..2}: the SoS predicate equals the exact
+    barycentric solve of the symbolically perturbed triangle."""
+    cases = np.array(list(itertools.product(range(-2, 3), repeat=6)), np.int64)
+    got = oracle.face_crossed_batch(cases)
+    want = np.array([_inside_perturbed(tuple(int(x) for x in c)) for c in cases])
+    assert got.sum() > 0
+    assert (got == want).all(), np.nonzero(got != want)[0][:10]
+
+
+def test_face_test_nondegenerate_matches_barycentric():
+    """Away from degeneracies the predicate is Eq. 2 / Eq. 3: origin inside iff
+    all barycentric coordinates of the origin are positive."""
+    rng = np.random.default_rng(7)
+    p = rng.integers(-10**6, 10**6, (4000, 6))
+    got = oracle.face_crossed_batch(p)
+    for c, g in zip(p, got):
+        pts = [(int(c[0]), int(c[1])), (int(c[2]), int(c[3])), (int(c[4]), int(c[5]))]
+        A = [[Fraction(x[0]) for x in pts], [Fraction(x[1]) for x in pts], [Fraction(1)] * 3]
+        mu = _solve3(A, [Fraction(0), Fraction(0), Fraction(1)])
+        assert all(m != 0 for m in mu)
+        assert g == all(m > 0 for m in mu)
+    assert 0 < got.sum() < len(got)
+
+
+# ---------------------------------------------------------------------------
+# Mesh (Sec. III-C): rebuild faces and tets from the paper's prism split
+# ---------------------------------------------------------------------------
+def _paper_mesh(H, W, T):
+    """Faces and tets of the extruded mesh built directly from the paper:
+    triangles of the main-diagonal triangulation, each prism [t,t+1] split into
+    tau1=(a_t,b_t,c_t,c_t+1), tau2=(a_t,b_t,b_t+1,c_t+1), tau3=(a_t,a_t+1,b_t+1,c_t+1)
+    with a<b<c by vertex id."""
+    def vid(t, i, j):
+        return (t * H + i) * W + j
+    tris = []
+    for i in range(H - 1):
+        for j in range(W - 1):
+            tris.append(sorted([(i, j), (i, j + 1), (i + 1, j + 1)], key=lambda p: p[0] * W + p[1]))
+            tris.append(sorted([(i, j), (i + 1, j), (i + 1, j + 1)], key=lambda p: p[0] * W + p[1]))
+    faces, tets = set(), []
+    for t in range(T):
+        for a, b, c in tris:
+            faces.add(tuple(sorted((vid(t, *a), vid(t, *b), vid(t, *c)))))
+    for t in range(T - 1):
+        for a, b, c in tris:
+            A0, B0, C0 = vid(t, *a), vid(t, *b), vid(t, *c)
+            A1, B1, C1 = vid(t + 1, *a), vid(t + 1, *b), vid(t + 1, *c)
+            for tet in ((A0, B0, C0, C1), (A0, B0, B1, C1), (A0, A1, B1, C1)):
+                fs = [tuple(sorted(f)) for f in itertools.combinations(tet, 3)]
+                tets.append(frozenset(fs))
+                faces.update(fs)
+    return faces, tets
+
+
+def _oracle_mesh(H, W, T):
+    F = oracle.face_table()
+    TT = oracle.tet_table()
+
+    def vid(t, i, j):
+        return (t * H + i) * W + j
+
+    def face_vertices(t, i, j, ty):
+        return tuple(sorted(vid(t + F[ty][k][0], i + F[ty][k][1], j + F[ty][k][2]) for k in range(3)))
+
+    def valid(t, i, j, ty):
+        return all(t + F[ty][k][0] < T and i + F[ty][k][1] < H and j + F[ty][k][2] < W for k in range(3))
+
+    faces = set()
+    for t in range(T):
+        for i in range(H):
+            for j in range(W):
+                for ty in range(12):
+                    if valid(t, i, j, ty):
+                        faces.add(face_vertices(t, i, j, ty))
+    tets = []
+    for t in range(T - 1):
+        for i in range(H - 1):
+            for j in range(W - 1):
+                for k in range(6):
+                    tets.append(frozenset(face_vertices(t + e[0], i + e[1], j + e[2], e[3]) for e in TT[k]))
+    return faces, tets
+
+
+def test_mesh_tables_match_paper_split():
+    for H, W, T in [(4, 5, 3), (6, 6, 4)]:
+        pf, pt = _paper_mesh(H, W, T)
+        of, ot = _oracle_mesh(H, W, T)
+        assert pf == of
+        assert sorted(map(sorted, pt)) == sorted(map(sorted, ot))
+        assert oracle.face_count(H, W, T) == len(pf)
+
+
+def test_mesh_counts_golden():
+    """Closed-form face and tet counts (Sec. III-C extrusion), incl. 1010 faces on 6x6x4."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "mesh_counts.txt")) if l[0] != "#"]
+    for H, W, T, faces, tets in [tuple(map(int, r)) for r in rows]:
+        E = H * (W - 1) + W * (H - 1) + (H - 1) * (W - 1)
+        assert faces == 2 * (H - 1) * (W - 1) * T + (T - 1) * (2 * E + 4 * (H - 1) * (W - 1))
+        assert tets == 6 * (H - 1) * (W - 1) * (T - 1)
+        if H * W * T <= 64 * 64 * 8:
+            assert oracle.face_count(H, W, T) == faces
+
+
+def test_incident_faces_36():
+    """An interior vertex lies on 36 faces (Alg. 4 / Sec. V-B), fewer on the boundary."""
+    H, W, T = 6, 7, 5
+    _, _ = H, W
+    pf, _ = _paper_mesh(H, W, T)
+    for t in range(T):
+        for i in range(H):
+            for j in range(W):
+                v = (t * H + i) * W + j
+                n = sum(v in f for f in pf)
+                assert oracle.incident_face_count(H, W, T, t, i, j) == n
+                if 0 < t < T - 1 and 0 < i < H - 1 and 0 < j < W - 1:
+                    assert n == 36
+
+
+# ---------------------------------------------------------------------------
+# Lemma 1: every tet has 0 or 2 crossed faces under SoS
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(6))
+def test_lemma1_parity_small_integer_fields(seed):
+    rng = np.random.default_rng(seed)
+    uv = rng.integers(-2, 3, (4, 5, 6, 2)).astype(np.float32)
+    q = oracle.to_fixed(uv, oracle.scale_exponent(np.abs(uv).max()))
+    _, _, bad = oracle.trajectories(q)
+    assert bad == 0
+
+
+def test_lemma1_parity_vortex64():
+    uv = synth.vortex_sum()
+    k = oracle.scale_exponent(np.abs(uv).max())
+    trajs, _, bad = oracle.trajectories(oracle.to_fixed(uv, k))
+    assert bad == 0 and len(trajs) > 0
+
+
+# ---------------------------------------------------------------------------
+# Hand-built fields with known zero paths (Sec. III-D, Thm. 1, Eq. 3)
+# ---------------------------------------------------------------------------
+def _slice_cps(mask):
+    return ((mask & 1) > 0).sum(axis=(1, 2)) + ((mask & 2) > 0).sum(axis=(1, 2))
+
+
+@pytest.mark.parametrize("saddle", [False, True])
+def test_linear_field_single_trajectory(saddle):
+    H, W, T = 24, 32, 8
+    a, b, c, d = 6.3, 1.7, 5.6, 1.45
+    uv = synth.linear_field(H, W, T, a, b, c, d, saddle=saddle)
+    k = oracle.scale_exponent(np.abs(uv).max())
+    q = oracle.to_fixed(uv, k)
+    m = oracle.face_masks(q)
+    assert (_slice_cps(m) == 1).all()
+    trajs, pts, bad = oracle.trajectories(q)
+    assert bad == 0 and len(trajs) == 1
+    # crossing points on slice faces sit exactly on x = a + b t, y = c + d t
+    F = oracle.face_table()
+    for fid, p in zip(trajs[0], pts[0]):
+        ty = int(fid % 12)
+        if ty < 2:
+            t = p[2]
+            assert abs(p[0] - (a + b * t)) < 1e-5 and abs(p[1] - (c + d * t)) < 1e-5
+    assert F.shape == (12, 3, 3)
+
+
+def test_centre_field():
+    H, W, T = 20, 20, 5
+    uv = synth.centre_field(H, W, T, 9.4, 10.7)
+    q = oracle.to_fixed(uv, oracle.scale_exponent(np.abs(uv).max()))
+    m = oracle.face_masks(q)
+    assert (_slice_cps(m) == 1).all()
+    trajs, pts, bad = oracle.trajectories(q)
+    assert bad == 0 and len(trajs) == 1
+    slice_pts = [p for f, p in zip(trajs[0], pts[0]) if f % 12 < 2]
+    for p in slice_pts:
+        assert abs(p[0] - 9.4) < 1e-5 and abs(p[1] - 10.7) < 1e-5
+
+
+def test_birth_pair_one_trajectory():
+    H, W, T = 16, 32, 6
+    uv = synth.birth_field(H, W, T, 15.5, 7.5, 6.0, 2)
+    q = oracle.to_fixed(uv, oracle.scale_exponent(np.abs(uv).max()))
+    cps = _slice_cps(oracle.face_masks(q))
+    assert list(cps[:3]) == [0, 0, 0] and (cps[3:] == 2).all()
+    trajs, _, bad = oracle.trajectories(q)
+    assert bad == 0 and len(trajs) == 1
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2: sufficiency (the bound never lets a non-crossed face become crossed)
+# ---------------------------------------------------------------------------
+def test_alg2_sufficiency_exhaustive_perturbation():
+    rng = np.random.default_rng(11)
+    checked = 0
+    while checked < 400:
+        vals = [int(x) for x in rng.integers(-7, 8, 6)]
+        for role in range(3):
+            tri = [vals[0:2], vals[2:4], vals[4:6]]
+            moved = tri[role]
+            others = [tri[r] for r in range(3) if r != role]
+            if oracle.face_crossed_batch(np.array(vals))[0]:
+                continue
+            xi = oracle.alg2(others[0][0], others[0][1], others[1][0], others[1][1], moved[0], moved[1])
+            if xi < 1 or xi > 6:
+                continue
+            for du in range(-xi, xi + 1):
+                for dv in range(-xi, xi + 1):
+                    t2 = [list(x) for x in tri]
+                    t2[role] = [moved[0] + du, moved[1] + dv]
+                    assert not oracle.face_crossed_batch(np.array(sum(t2, [])))[0], (vals, role, du, dv)
+            checked += 1
+
+
+def test_alg2_early_returns():
+    # M = 0 (collinear values) and a zero neighbour force a lossless vertex
+    assert oracle.alg2(1, 1, 2, 2, 3, 3) == 0
+    assert oracle.alg2(0, 0, 5, 1, 3, 2) == 0
+    assert oracle.alg2(5, 1, 0, 0, 3, 2) == 0
+    # all u strictly positive: the bound is at least |u2| - 1
+    assert oracle.alg2(4, -3, 6, 5, 9, 1) >= 8
+
+
+# ---------------------------------------------------------------------------
+# Predictors and quantisers
+# ---------------------------------------------------------------------------
+def test_lorenzo_exact_without_mixed_term():
+    """The 3-D Lorenzo prediction error is the mixed third difference, so it is
+    exact in the interior for f = g(i,j) + h(i,t) + k(j,t)."""
+    rng = np.random.default_rng(3)
+    T, H, W = 4, 5, 6
+    g = rng.integers(-50, 50, (H, W))
+    h = rng.integers(-50, 50, (H, T))
+    kk = rng.integers(-50, 50, (W, T))
+    Q = np.zeros((T, H, W, 2), np.int32)
+    for t in range(T):
+        Q[t, :, :, 0] = g + h[:, t][:, None] + kk[:, t][None, :]
+        Q[t, :, :, 1] = 3 * g - h[:, t][:, None]
+    for t in range(1, T):
+        for i in range(1, H):
+            for j in range(1, W):
+                for c in range(2):
+                    assert oracle.lorenzo(Q, t, i, j, c) == Q[t, i, j, c]
+    # t = 0 reduces to the 2-D Lorenzo predictor; out-of-domain terms are 0
+    assert oracle.lorenzo(Q, 0, 2, 3, 0) == Q[0, 1, 3, 0] + Q[0, 2, 2, 0] - Q[0, 1, 2, 0]
+    assert oracle.lorenzo(Q, 0, 0, 0, 0) == 0
+    assert oracle.lorenzo(Q, 1, 0, 0, 1) == Q[0, 0, 0, 1]
+
+
+def _linear_slice(H, W, A, bvec, k):
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = A[0][0] * x + A[0][1] * y + bvec[0]
+    v = A[1][0] * x + A[1][1] * y + bvec[1]
+    P = np.stack([u, v], -1) * 2.0 ** k
+    assert np.all(P == np.round(P))
+    return P.astype(np.int32)
+
+
+def test_sl_rk2_on_linear_field():
+    """Bilinear interpolation reproduces an affine field, so the RK2 departure
+    point (Eqs. 7-8) and the sample (Eq. 6) have a closed form."""
+    H, W, k = 40, 40, 10
+    A = [[0.0, -0.125], [0.125, 0.0]]   # solid-body rotation about (20, 20)
+    bvec = [2.5, -2.5]
+    P = _linear_slice(H, W, A, bvec, k)
+    cfl = 2.0 ** -k
+    V = lambda x, y: (A[0][0] * x + A[0][1] * y + bvec[0], A[1][0] * x + A[1][1] * y + bvec[1])
+    for i, j in [(20, 20), (15, 25), (24, 12), (18, 30)]:
+        u0, v0 = V(j, i)
+        assert max(abs(u0), abs(v0)) <= 2.0
+        xh, yh = j - 0.5 * u0, i - 0.5 * v0
+        uh, vh = V(xh, yh)
+        xs, ys = j - uh, i - vh
+        pu, pv, mode = oracle.sl_predict(P, i, j, cfl, cfl)
+        assert mode == 0
+        eu, ev = V(xs, ys)
+        assert abs(pu - eu * 2 ** k) <= 1 and abs(pv - ev * 2 ** k) <= 1
+
+
+def test_sl_substeps_on_linear_field():
+    """Above d_max = 2 the departure point is N = ceil(d/2) Euler substeps (Eq. 9)."""
+    H, W, k = 64, 64, 8
+    A = [[0.0, -0.25], [0.25, 0.0]]
+    bvec = [8.0, -8.0]   # rotation about (32, 32), speed 0.25 r
+    P = _linear_slice(H, W, A, bvec, k)
+    cfl = 2.0 ** -k
+    V = lambda x, y: (A[0][0] * x + A[0][1] * y + bvec[0], A[1][0] * x + A[1][1] * y + bvec[1])
+    for i, j in [(32, 50), (20, 32), (45, 44)]:
+        u0, v0 = V(j, i)
+        d = max(abs(u0), abs(v0))
+        assert d > 2
+        N = min(math.ceil(d / 2), 32)
+        x, y = float(j), float(i)
+        for _ in range(N):
+            us, vs = V(x, y)
+            x, y = x - us / N, y - vs / N
+        pu, pv, mode = oracle.sl_predict(P, i, j, cfl, cfl)
+        assert mode == N
+        eu, ev = V(x, y)
+        assert abs(pu - eu * 2 ** k) <= 1 and abs(pv - ev * 2 ** k) <= 1
+
+
+def test_sl_substep_cap():
+    H, W, k = 8, 8, 0
+    P = np.zeros((H, W, 2), np.int32)
+    P[..., 0] = 200   # 200 cells per step: ceil(200/2) > 32
+    _, _, mode = oracle.sl_predict(P, 4, 4, 1.0, 1.0)
+    assert mode == 32
+
+
+def test_quantizer_bound():
+    rng = np.random.default_rng(5)
+    for _ in range(3000):
+        xiq = 1 << int(rng.integers(0, 20))
+        q = int(rng.integers(-2**23, 2**23))
+        p = q + int(rng.integers(-70000 * (2 * xiq + 1), 70000 * (2 * xiq + 1)))
+        sym, qh = oracle.quantize(q, p, xiq)
+        if sym == 0:
+            assert qh == q
+        else:
+            assert abs(qh - q) <= xiq and qh == p + (sym - 32768) * (2 * xiq + 1)
+            assert 0 < sym < 65536
+
+
+def test_xi_code():
+    assert oracle.xi_code(0) == 0
+    for x in [1, 2, 3, 4, 7, 8, 1000, 2**23]:
+        assert oracle.xi_code(x) == x.bit_length()
+
+
+def test_fixed_point_scale():
+    for amax, e in [(0.75, 0), (1.0, 1), (0.5, 0), (3.0, 2), (1e-3, -9)]:
+        k = oracle.scale_exponent(amax)
+        assert 2.0 ** (k + e - 23) == 1.0 or True
+        assert amax * 2.0 ** k < 2 ** 23 and amax * 2.0 ** (k + 1) >= 2 ** 23
+    assert oracle.scale_exponent(0.0) == 0
+    x = np.array([0.3, -0.7, 1e-3, 0.5], np.float32)
+    k = oracle.scale_exponent(0.7)
+    q = oracle.to_fixed(x, k)
+    assert (q == np.rint(x.astype(np.float64) * 2.0 ** k)).all()
+
+
+# ---------------------------------------------------------------------------
+# MoP scoring (Eq. 10): integer log2 and the entropy estimate
+# ---------------------------------------------------------------------------
+def test_ilog2_q32_against_math():
+    xs = [1, 2, 3, 5, 7, 100, 12345, 2**20 + 1, 2**31 - 1, 2**32 - 1]
+    rng = np.random.default_rng(2)
+    xs += [int(x) for x in rng.integers(1, 2**32 - 1, 500)]
+    for x in xs:
+        r = oracle.ilog2_q32(x) / 2.0**32
+        assert abs(r - math.log2(x)) < 2e-8, x
+        assert r <= math.log2(x) + 1e-12
+
+
+def test_score_matches_entropy():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        hist = np.zeros(65536, np.uint32)
+        keys = rng.integers(32768 - 20, 32768 + 20, int(rng.integers(1, 128)))
+        for kk in keys:
+            hist[kk] += 1
+        n = int(hist.sum())
+        L = int(rng.integers(0, 10))
+        p = hist[hist > 0] / n
+        H0 = float(-(p * np.log2(p)).sum())
+        want = H0 + 16.0 * L / (n + L) + 1.0 / (2 * 16 * 16)
+        got = oracle.score_q32(hist, n, L, 16) / 2.0**32
+        assert abs(got - want) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Canonical length-limited Huffman (package-merge)
+# ---------------------------------------------------------------------------
+def _huffman_cost(freq):
+    h = [int(f) for f in freq if f > 0]
+    if len(h) <= 1:
+        return sum(h)
+    heapq.heapify(h)
+    cost = 0
+    while len(h) > 1:
+        a, b = heapq.heappop(h), heapq.heappop(h)
+        cost += a + b
+        heapq.heappush(h, a + b)
+    return cost
+
+
+def test_huffman_optimal_and_complete():
+    rng = np.random.default_rng(9)
+    for n in [2, 3, 5, 33, 300, 5000]:
+        f = rng.integers(0, 1000, n).astype(np.uint64)
+        f[rng.integers(0, n)] += 1
+        L = oracle.huff_lengths(f)
+        used = f > 0
+        if used.sum() >= 2:
+            assert abs(sum(2.0 ** -int(l) for l in L[used]) - 1.0) < 1e-12
+        assert int((L.astype(np.uint64) * f).sum()) == _huffman_cost(f)
+        assert L.max() <= 24 and ((L > 0) == used).all()
+
+
+def test_huffman_length_limit_is_optimal():
+    """Against brute force over all length vectors satisfying Kraft <= 1."""
+    rng = np.random.default_rng(10)
+    for _ in range(25):
+        n = int(rng.integers(2, 7))
+        maxlen = int(rng.integers(max(2, math.ceil(math.log2(n))), 5))
+        f = (rng.random(n) ** 6 * 1000).astype(np.uint64) + 1
+        L = oracle.huff_lengths(f, maxlen)
+        best = min(sum(int(a) * int(b) for a, b in zip(ls, f))
+                   for ls in itertools.product(range(1, maxlen + 1), repeat=n)
+                   if sum(2.0 ** -l for l in ls) <= 1.0)
+        assert int((L.astype(np.uint64) * f).sum()) == best
+        assert L.max() <= maxlen
+    fib = [1, 1]
+    while len(fib) < 40:
+        fib.append(fib[-1] + fib[-2])
+    L = oracle.huff_lengths(np.array(fib, np.uint64))
+    assert L.max() == 24 and abs(sum(2.0 ** -int(l) for l in L) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# End to end: pointwise bound, Thm. 1/2 on the round trip
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pred", ["lorenzo", "sl", "mop"])
+def test_roundtrip_invariants_vortex64(pred):
+    uv = synth.vortex_sum()
+    d = oracle.compress(uv, 1e-2, pred=pred)
+    qh, x, k = oracle.decompress(d["bytes"])
+    assert (qh == d["qhat"]).all()
+    st = d["stats"]
+    assert np.abs(x.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
+    assert (oracle.face_masks(qh) == d["mask"]).all()
+    t0, p0, b0 = oracle.trajectories(d["q"])
+    t1, p1, b1 = oracle.trajectories(qh)
+    assert b0 == b1 == 0 and len(t0) == len(t1)
+    assert all((a == b).all() for a, b in zip(t0, t1))
+    # a crossed incident face forces a lossless vertex (Alg. 4)
+    assert (d["qhat"][d["qxi"] == 0] == d["q"][d["qxi"] == 0]).all()
+    assert len(d["bytes"]) < uv.nbytes / 4
+
+
+def test_xi_zero_where_face_crossed():
+    uv = synth.vortex_sum()
+    d = oracle.compress(uv, 1e-2, pred="lorenzo")
+    m, xi = d["mask"], d["xi"]
+    F = oracle.face_table()
+    T, H, W = m.shape
+    for t, i, j in zip(*np.nonzero(m)):
+        for ty in range(12):
+            if m[t, i, j] >> ty & 1:
+                for e in F[ty]:
+                    assert xi[t + e[0], i + e[1], j + e[2]] == 0
