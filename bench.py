@@ -1,0 +1,291 @@
+#!/usr/bin/env python
+"""Compression throughput of the trajectory-preserving compressor on one or
+more GB300s (one process per GPU; replicas: each rank compresses its own copy
+of the workload, no collective on the data path).
+
+A step is one cpt_compress call over the whole hot path on the workload:
+range + fixed point, crossed-face masks, MoP block selection with the
+semi-Lagrangian predictions, incident-face bounds, the wavefront encoder,
+entropy coding and full verification of every face predicate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the slow plain restatement of the
+method) on a bounded sample of the same workload, on the host cores.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress MB/s & ratio at 100% CP-trajectory preservation, learned vs plain"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per vertex of each stage's kernels (the minimum traffic
+# the method needs; see the design notes): stage -> (bytes per vertex, units
+# per launch: "field" = H*W*T vertices, "slice" = H*W vertices).
+STAGE_BYTES = {
+    "range_fixed": (12.0, "field"),     # two launches: read 8 B; read 8 B + write 8 B
+    "face_masks": (10.0, "field"),      # read q 8 B, write mask 2 B
+    "mop_sl": (24.0, "slice"),          # read qhat(t-1) 8 B, q(t) 8 B, write SL prediction 8 B
+    "incident_bounds": (32.0, "slice"), # q(t), q(t+1), qhat(t-1) 8 B each, masks 2x2 B, write 4 B
+    "wavefront": (49.0, "slice"),       # q, q(t+1), qhat(t-1), SL pred 8 B each, bound 4 B, write 13 B
+    "verify": (18.0, "field"),          # read qhat 8 B, mask 2 B, uv 8 B
+}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[2:]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_oracle_run(uv_sample, eb, pred, min_seconds):
+    """Times the oracle as it stands on uv_sample, repeating for >= min_seconds."""
+    import oracle
+    oracle.lib()
+    reps, t0 = 0, time.perf_counter()
+    res = None
+    while True:
+        res = oracle.compress(uv_sample, eb, pred=pred, debug=False)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    mbs = reps * uv_sample.nbytes / 1e6 / el
+    return mbs, el / reps, res
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2510_25143_gb300 import synth
+    uv, eb = synth.workload(args.workload)
+    sample = uv[: args.cpu_slices].copy()
+    import oracle
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.compress(sample, eb, pred=args.pred, debug=False)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle.compress(sample, eb, pred=args.pred, debug=False)
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = sample.nbytes / 1e6 / (ms / 1e3)
+    T, H, W, _ = sample.shape
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "H": H, "W": W, "T_sample": T, "rel_eb": eb, "pred": args.pred},
+        "ratio": round(sample.nbytes / len(last["bytes"]), 4),
+        "cpu_baseline": {"value": round(value, 4), "unit": "MB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {T} of {uv.shape[0]} slices of {args.workload}, whole method per step"},
+        "e2e": {"value": round(value, 4), "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2510_25143_gb300 import cpt, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    uv, eb = synth.workload(args.workload)
+    T, H, W, _ = uv.shape
+    nbytes = uv.nbytes
+    d_uv = torch.from_numpy(uv).cuda()
+    stream = torch.cuda.current_stream()
+    kw = dict(eb_mode="rel", pred=args.pred, verify=True)
+
+    def step(src):
+        blob, st, _ = cpt.compress(src, eb, **kw)
+        return blob, st
+
+    for _ in range(args.warmup):
+        blob, st = step(d_uv)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            blob, st = step(d_uv)
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nbytes / 1e6 / (ms / 1e3)
+
+    # end to end through the public API with host buffers: the input is copied
+    # from pinned host memory inside each call, the stream read back to host
+    pinned = torch.from_numpy(uv).pin_memory()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    e2e_blob = None
+    for _ in range(args.steps):
+        e2e_blob, _ = step(pinned)
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = ee0.elapsed_time(ee1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * nbytes / 1e6 / (ms_e2e / 1e3)
+
+    # per-stage device time from the library's CUDA events on its stream
+    stage_ms = {k: statistics.mean(s["ms_stage"][k] for s in stats) for k in stats[0]["ms_stage"]}
+    stage_launch = {k: stats[0]["launches"][k] for k in stats[0]["launches"]}
+    launches = sum(sum(s["launches"].values()) for s in stats)
+    peak, peak_kind = peaks()
+    dom = max((k for k in STAGE_BYTES if stage_launch.get(k)), key=lambda k: stage_ms[k])
+    per_vertex, unit = STAGE_BYTES[dom]
+    units = H * W * T if unit == "field" else H * W
+    per_launch_ms = stage_ms[dom] / stage_launch[dom]
+    achieved = per_vertex * units / (per_launch_ms / 1e3) / 1e9
+    last = stats[-1]
+    ok = (last["verify_mismatch_slice"] == 0 and last["verify_mismatch_slab"] == 0 and last["linf"] <= last["eps"])
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "H": H, "W": W, "T": T, "rel_eb": eb, "pred": args.pred,
+                   "input_bytes": nbytes, "l2": "input (%.0f MB) larger than L2 (129 MB), no flush" % (nbytes / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "ratio": round(last["ratio"], 4),
+        "preserved": bool(ok), "fc_t": last["verify_mismatch_slice"], "fc_s": last["verify_mismatch_slab"],
+        "linf": last["linf"], "eps": last["eps"], "psnr": round(last["psnr"], 3),
+        "faces_per_s": round(last["faces"] / (stage_ms["face_masks"] / 1e3), 1) if stage_ms["face_masks"] else None,
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "bytes_per_vertex": per_vertex, "units_per_launch": units,
+                     "launch_ms": round(per_launch_ms, 5)},
+        "e2e": {"value": round(e2e_value, 2), "unit": "MB/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": len(e2e_blob)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cmbs, per_run, res = cpu_oracle_run(uv[: args.cpu_slices].copy(), eb, args.pred, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(cmbs, 4), "unit": "MB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.cpu_slices} of {T} slices of {args.workload}, whole "
+                                          f"method, repeated for >= {args.cpu_seconds:.0f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="street512")
+    p.add_argument("--pred", default="mop", choices=["lorenzo", "sl", "mop"])
+    p.add_argument("--cpu-slices", type=int, default=4)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu", action="store_true")
+    args = p.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

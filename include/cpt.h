@@ -1,0 +1,178 @@
+/*
+ * cpt.h - C ABI of the GB300 (sm_103a) critical-point-trajectory-preserving
+ * compressor for time-varying 2-D vector fields.
+ *
+ * The method is that of "Time-Varying Vector Field Compression with Preserved
+ * Critical Point Trajectories" (Xia, Li, Jiao, Wang, Liang, Guo): a lossy
+ * compressor C and decompressor D (Sec. IV-A) with a pointwise bound
+ * ||D(C(x)) - x||_inf <= eps and the face-level critical-point predicate of
+ * every space-time face preserved (Eq. 4), hence the track set T(.) of
+ * critical-point trajectories preserved (Thm. 1, Thm. 2).
+ *
+ * Data layout everywhere: float32 [T][H][W][2], u and v interleaved, row
+ * major; j (the x axis, column) is the fastest index, then i (y, row), then t.
+ * The global space-time vertex id is (t*H + i)*W + j; it orders the vertices
+ * for the symbolic perturbation of Sec. III-F.
+ *
+ * Every function returns a cpt_status (0 = CPT_OK, negative = error); none
+ * aborts or traps.  The text of the last error of the calling thread is
+ * available from cpt_last_error().  All compute runs in the library's CUDA
+ * kernels on the current CUDA device; there is no CPU fallback: without a
+ * usable device every compute call returns CPT_ERR_CUDA.
+ */
+#ifndef CPT_H
+#define CPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPT_OK = 0,
+    CPT_ERR_ARG = -1,         /* invalid argument (sizes, bound, non-finite input) */
+    CPT_ERR_CUDA = -2,        /* a CUDA call failed or no device is usable */
+    CPT_ERR_OOM = -3,         /* host or device allocation failed */
+    CPT_ERR_CORRUPT = -4,     /* malformed or truncated stream */
+    CPT_ERR_VERIFY = -5,      /* reconstruction changed a face predicate or broke the bound */
+    CPT_ERR_TIMEOUT = -6,     /* a kernel's bounded inter-block wait ran out */
+    CPT_ERR_UNSUPPORTED = -7  /* option not available in this build */
+} cpt_status;
+
+/* Grid of the field.  dx, dy, dt are the spacings used by the semi-Lagrangian
+ * predictor (Sec. VI-A, CFL_x = dt/dx * 1/S); 0 means 1. */
+typedef struct {
+    int32_t H, W, T;
+    double dx, dy, dt;
+} cpt_dims;
+
+typedef enum { CPT_EB_ABS = 0, CPT_EB_REL = 1 } cpt_eb_mode;
+
+/* Predictors: 3-D Lorenzo (3DL), semi-Lagrangian (SL, Sec. VI-A) and the
+ * block-wise mixture of both (MoP, Sec. VI). */
+typedef enum { CPT_PRED_LORENZO = 0, CPT_PRED_SL = 1, CPT_PRED_MOP = 2 } cpt_pred;
+
+/* Compression parameters.
+ *   mode/eb  : eps = eb (ABS, data units) or eb * (max - min over u and v) (REL)
+ *   pred     : predictor
+ *   block    : MoP block side B (0 = 16); stride: MoP sampling stride n (0 = 2)
+ *   cuda_stream : cudaStream_t to run on (NULL = the legacy default stream)
+ *   verify   : nonzero = recompute every face predicate on the reconstruction
+ *              and check the pointwise bound before returning (Thm. 1/2)   */
+typedef struct {
+    cpt_eb_mode mode;
+    double eb;
+    cpt_pred pred;
+    int32_t block;
+    int32_t stride;
+    int32_t verify;
+    void* cuda_stream;
+} cpt_params;
+
+/* Statistics of one compression.  ms_stage (CUDA-event time on the library's
+ * stream, summed over launches): 0 range+fixed point, 1 face predicates,
+ * 2 MoP selection + SL prediction, 3 incident-face bounds, 4 wavefront
+ * encode, 5 entropy coding, 6 verification, 7 host (codebook, stream).
+ * launches[s] counts the kernels launched for stage s. */
+typedef struct {
+    double ms_total;
+    double ms_stage[8];
+    uint32_t launches[8];
+    int32_t scale_log2;       /* k: S = 2^k (fixed point) */
+    int32_t eps_int;          /* eps' = floor(eps*S - 0.5) */
+    double eps;               /* absolute bound in data units */
+    uint64_t faces;           /* faces of the space-time mesh */
+    uint64_t crossed_faces;   /* |C| */
+    uint64_t lossless_vertices;
+    uint64_t unpredictable;
+    uint64_t sl_blocks, blocks;
+    uint64_t n_ld, n_qd;
+    uint64_t verify_mismatch_slice;  /* FC_t: slice faces whose predicate changed */
+    uint64_t verify_mismatch_slab;   /* FC_s: slab faces whose predicate changed */
+    double linf;              /* max |x_hat - x| */
+    double psnr;
+    double ratio;             /* input bytes / output bytes */
+    uint64_t out_bytes;
+} cpt_stats;
+
+/* Optional host outputs of cpt_compress_ex (each pointer may be NULL).
+ *   q     int32 [T][H][W][2]  fixed-point input (Alg. 3, Convert_FixedPoint)
+ *   qhat  int32 [T][H][W][2]  reconstruction in fixed point
+ *   xi    int32 [T][H][W]     per-vertex integer bound of Alg. 4 (0 = lossless)
+ *   qxi   uint8 [T][H][W]     bound codes Q_xi
+ *   sym   uint16 [T][H][W][2] residual symbols Q_d (0 = unpredictable;
+ *                             unspecified where qxi == 0)
+ *   mask  uint16 [T][H][W]    crossed-face bits of the 12 faces owned by each vertex
+ *   modes uint8 [T][ceil(H/B)][ceil(W/B)]  1 = SL block                       */
+typedef struct {
+    int32_t* q;
+    int32_t* qhat;
+    int32_t* xi;
+    uint8_t* qxi;
+    uint16_t* sym;
+    uint16_t* mask;
+    uint8_t* modes;
+} cpt_debug;
+
+/* Compresses uv (Alg. 3 with Alg. 1, 2, 4 and Sec. VI).
+ *   uv        : float32 [T][H][W][2], host or device memory (detected); host
+ *               input is copied to the device inside the call
+ *   out       : receives a library-allocated host buffer with the stream;
+ *               release it with cpt_free
+ *   stats     : nullable
+ * Errors: CPT_ERR_ARG (H or W < 2, T < 1, eb < 0 or non-finite input),
+ * CPT_ERR_OOM, CPT_ERR_CUDA, CPT_ERR_TIMEOUT, CPT_ERR_VERIFY (only when
+ * params->verify is set; *out is still produced). */
+cpt_status cpt_compress(const float* uv, const cpt_dims* dims, const cpt_params* params,
+                        uint8_t** out, size_t* out_bytes, cpt_stats* stats);
+
+/* cpt_compress plus optional copies of the intermediate arrays (dbg nullable). */
+cpt_status cpt_compress_ex(const float* uv, const cpt_dims* dims, const cpt_params* params,
+                           uint8_t** out, size_t* out_bytes, cpt_stats* stats,
+                           const cpt_debug* dbg);
+
+/* Decompresses a stream produced by cpt_compress.
+ *   uv_out : caller-allocated float32 [T][H][W][2], host or device; NULL only
+ *            fills dims_out (a cheap header query)
+ *   qhat_out : nullable host int32 [T][H][W][2] copy of the fixed-point values
+ * Errors: CPT_ERR_CORRUPT for a malformed or truncated stream. */
+cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out,
+                          cpt_dims* dims_out, void* cuda_stream);
+
+/* Critical-point trajectories of a field (Sec. III-D, Thm. 2): the crossed
+ * faces of the space-time mesh joined through the tetrahedra they share.
+ *   scale_log2 : fixed-point exponent k to use (as stored in a stream), or
+ *                CPT_SCALE_AUTO to derive it from the data
+ * Each trajectory lists its faces in path order from its lowest-id end (a
+ * closed loop starts at its lowest-id face, towards the lower-id neighbour);
+ * trajectories are ordered by their first face id.  Face id = owner vertex id
+ * * 12 + face type.  xyt holds the crossing point of each face (Eq. 3) as
+ * (x = column, y = row, t).  *out is library-allocated (cpt_free). */
+#define CPT_SCALE_AUTO INT32_MIN
+typedef struct {
+    uint64_t n_traj, n_points;
+    uint64_t* offsets;  /* n_traj + 1 */
+    uint64_t* face_ids; /* n_points */
+    double* xyt;        /* 3 * n_points */
+    uint64_t bad_tets;  /* tets with a crossed-face count other than 0 or 2 (Lemma 1) */
+} cpt_trajs;
+
+cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2,
+                                    cpt_trajs** out, void* cuda_stream);
+
+/* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
+void cpt_free(void* p);
+void cpt_free_trajs(cpt_trajs* t);
+
+const char* cpt_error_string(cpt_status s);
+const char* cpt_last_error(void);
+
+/* Library version (stream format version in the low byte). */
+uint32_t cpt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPT_H */

@@ -1,0 +1,192 @@
+"""ctypes binding of the CUDA library ``_build/libcpt.so`` (C ABI of
+``include/cpt.h``).  Argument marshalling only: every step of the
+compressor runs in the library's kernels.  Raises if the library has not
+been built; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcpt.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CORRUPT, ERR_VERIFY, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+PRED = {"lorenzo": 0, "sl": 1, "mop": 2}
+EB_MODE = {"abs": 0, "rel": 1}
+STAGES = ["range_fixed", "face_masks", "mop_sl", "incident_bounds", "wavefront", "entropy", "verify", "host"]
+
+
+class Dims(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("T", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dt", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
+                ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ms_total", C.c_double), ("ms_stage", C.c_double * 8), ("launches", C.c_uint32 * 8),
+                ("scale_log2", C.c_int32), ("eps_int", C.c_int32), ("eps", C.c_double),
+                ("faces", C.c_uint64), ("crossed_faces", C.c_uint64), ("lossless_vertices", C.c_uint64),
+                ("unpredictable", C.c_uint64), ("sl_blocks", C.c_uint64), ("blocks", C.c_uint64),
+                ("n_ld", C.c_uint64), ("n_qd", C.c_uint64), ("verify_mismatch_slice", C.c_uint64),
+                ("verify_mismatch_slab", C.c_uint64), ("linf", C.c_double), ("psnr", C.c_double),
+                ("ratio", C.c_double), ("out_bytes", C.c_uint64)]
+
+
+class Debug(C.Structure):
+    _fields_ = [("q", C.c_void_p), ("qhat", C.c_void_p), ("xi", C.c_void_p), ("qxi", C.c_void_p),
+                ("sym", C.c_void_p), ("mask", C.c_void_p), ("modes", C.c_void_p)]
+
+
+class Trajs(C.Structure):
+    _fields_ = [("n_traj", C.c_uint64), ("n_points", C.c_uint64), ("offsets", C.POINTER(C.c_uint64)),
+                ("face_ids", C.POINTER(C.c_uint64)), ("xyt", C.POINTER(C.c_double)), ("bad_tets", C.c_uint64)]
+
+
+class CptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cpt status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            P = C.POINTER
+            L.cpt_compress_ex.restype = C.c_int
+            L.cpt_compress_ex.argtypes = [C.c_void_p, P(Dims), P(Params), P(P(C.c_uint8)), P(C.c_size_t),
+                                          P(Stats), P(Debug)]
+            L.cpt_compress.restype = C.c_int
+            L.cpt_compress.argtypes = [C.c_void_p, P(Dims), P(Params), P(P(C.c_uint8)), P(C.c_size_t), P(Stats)]
+            L.cpt_decompress.restype = C.c_int
+            L.cpt_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, P(Dims), C.c_void_p]
+            L.cpt_extract_trajectories.restype = C.c_int
+            L.cpt_extract_trajectories.argtypes = [C.c_void_p, P(Dims), C.c_int32, P(P(Trajs)), C.c_void_p]
+            L.cpt_free.argtypes = [C.c_void_p]
+            L.cpt_free_trajs.argtypes = [P(Trajs)]
+            L.cpt_error_string.restype = C.c_char_p
+            L.cpt_error_string.argtypes = [C.c_int]
+            L.cpt_last_error.restype = C.c_char_p
+            L.cpt_version.restype = C.c_uint32
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        L = lib()
+        raise CptError(rc, f"{L.cpt_error_string(rc).decode()}: {L.cpt_last_error().decode()}")
+
+
+def _ptr_and_shape(uv):
+    """(pointer, (T,H,W), keepalive, device_stream) of a float32 [T][H][W][2]
+    numpy array or torch tensor."""
+    if isinstance(uv, np.ndarray):
+        a = np.ascontiguousarray(uv, np.float32)
+        assert a.ndim == 4 and a.shape[3] == 2
+        return a.ctypes.data, a.shape[:3], a, None
+    import torch  # noqa: WPS433 - torch only for device memory and streams
+    assert isinstance(uv, torch.Tensor) and uv.dtype == torch.float32 and uv.is_contiguous()
+    assert uv.dim() == 4 and uv.shape[3] == 2
+    stream = torch.cuda.current_stream(uv.device).cuda_stream if uv.is_cuda else None
+    return uv.data_ptr(), tuple(uv.shape[:3]), uv, stream
+
+
+def _stats_dict(st):
+    d = {f: getattr(st, f) for f, _ in Stats._fields_ if f not in ("ms_stage", "launches")}
+    d["ms_stage"] = {STAGES[k]: st.ms_stage[k] for k in range(8)}
+    d["launches"] = {STAGES[k]: st.launches[k] for k in range(8)}
+    return d
+
+
+def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
+             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True):
+    """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
+    or device).  Returns (bytes, stats dict, debug dict or None)."""
+    ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
+    if stream is None:
+        stream = dev_stream
+    dims = Dims(H, W, T, dx, dy, dt)
+    prm = Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream)
+    out = C.POINTER(C.c_uint8)()
+    n = C.c_size_t(0)
+    st = Stats()
+    dbg_arrays = None
+    dbgp = None
+    if debug:
+        nby, nbx = -(-H // block), -(-W // block)
+        dbg_arrays = dict(q=np.zeros((T, H, W, 2), np.int32), qhat=np.zeros((T, H, W, 2), np.int32),
+                          xi=np.zeros((T, H, W), np.int32), qxi=np.zeros((T, H, W), np.uint8),
+                          sym=np.zeros((T, H, W, 2), np.uint16), mask=np.zeros((T, H, W), np.uint16),
+                          modes=np.zeros((T, nby, nbx), np.uint8))
+        dbgp = C.byref(Debug(*(dbg_arrays[f].ctypes.data for f, _ in Debug._fields_)))
+    L = lib()
+    rc = L.cpt_compress_ex(ptr, C.byref(dims), C.byref(prm), C.byref(out), C.byref(n), C.byref(st), dbgp)
+    blob = None
+    if out:
+        blob = C.string_at(out, n.value)
+        L.cpt_free(out)
+    if check:
+        _check(rc)
+    del keep
+    s = _stats_dict(st)
+    s["status"] = rc
+    return blob, s, dbg_arrays
+
+
+def decompress(blob, out=None, *, stream=None, want_q=False):
+    """Decompresses a stream into float32 [T][H][W][2]: `out` may be a torch
+    tensor (host or device) or None (a new numpy array).  Returns
+    (uv, qhat or None, dims)."""
+    L = lib()
+    buf = np.frombuffer(blob, np.uint8)
+    dims = Dims()
+    _check(L.cpt_decompress(buf.ctypes.data, buf.size, None, None, C.byref(dims), stream))
+    T, H, W = dims.T, dims.H, dims.W
+    if out is None:
+        out = np.empty((T, H, W, 2), np.float32)
+        optr = out.ctypes.data
+    else:
+        optr, _, _, dev_stream = _ptr_and_shape(out)
+        if stream is None:
+            stream = dev_stream
+    q = np.empty((T, H, W, 2), np.int32) if want_q else None
+    _check(L.cpt_decompress(buf.ctypes.data, buf.size, optr, q.ctypes.data if want_q else None,
+                            C.byref(dims), stream))
+    return out, q, (H, W, T)
+
+
+def extract_trajectories(uv, scale_log2=None, stream=None):
+    """Trajectories of float32 uv [T][H][W][2]: (list of face-id arrays, list
+    of xyt arrays, number of tets violating the 0-or-2 crossing count)."""
+    ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
+    if stream is None:
+        stream = dev_stream
+    dims = Dims(H, W, T, 1.0, 1.0, 1.0)
+    k = -(2 ** 31) if scale_log2 is None else int(scale_log2)
+    out = C.POINTER(Trajs)()
+    L = lib()
+    _check(L.cpt_extract_trajectories(ptr, C.byref(dims), k, C.byref(out), stream))
+    t = out.contents
+    n, m = t.n_traj, t.n_points
+    offs = np.ctypeslib.as_array(t.offsets, shape=(n + 1,)).copy()
+    faces = np.ctypeslib.as_array(t.face_ids, shape=(max(m, 1),))[:m].copy() if m else np.zeros(0, np.uint64)
+    xyt = (np.ctypeslib.as_array(t.xyt, shape=(max(3 * m, 1),))[:3 * m].reshape(m, 3).copy()
+           if m else np.zeros((0, 3)))
+    bad = t.bad_tets
+    L.cpt_free_trajs(out)
+    del keep
+    return ([faces[offs[a]:offs[a + 1]] for a in range(n)], [xyt[offs[a]:offs[a + 1]] for a in range(n)], bad)

@@ -1,0 +1,282 @@
+// Device helpers shared by the kernels of the library: mesh tables, the SoS
+// face predicate, the exact-integer error bound of Alg. 2, the quantisers and
+// the predictors.  Compiled with -fmad=false so that the FP64 semi-Lagrangian
+// arithmetic follows the written evaluation order exactly.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cpt {
+
+constexpr int kRadius = 32768;  // quantisation radius: |c| < kRadius is predictable
+
+// ---------------------------------------------------------------------------
+// Mesh (Sec. III-C).  The 12 faces owned by vertex (t,i,j) use the corners
+// A=(i,j), R=(i,j+1), D=(i+1,j), G=(i+1,j+1) at t and t+1; every quad is split
+// along (i,j)-(i+1,j+1), every prism [t,t+1] over a triangle a<b<c into
+// (a,b,c,c'), (a,b,b',c'), (a,a',b',c') (primes at t+1).  Vertices of each
+// face are listed by increasing global id; entries are (dt, di, dj).
+// ---------------------------------------------------------------------------
+// Corner index of a face vertex: bit0 = +j, bit1 = +i, bit2 = +t relative to
+// the owner A.  CPT_OWNED_FACES(F) lists F(type, c0, c1, c2), c0 < c1 < c2 by id:
+//   0: A R G      1: A D G      2: A R G'     3: A R' G'    4: A D G'
+//   5: A D' G'    6: A R R'     7: A A' R'    8: A D D'     9: A A' D'
+//  10: A G G'    11: A A' G'
+#define CPT_OWNED_FACES(F) \
+    F(0, 0, 1, 3) F(1, 0, 2, 3) F(2, 0, 1, 7) F(3, 0, 5, 7) F(4, 0, 2, 7) F(5, 0, 6, 7) \
+    F(6, 0, 1, 5) F(7, 0, 4, 5) F(8, 0, 2, 6) F(9, 0, 4, 6) F(10, 0, 3, 7) F(11, 0, 4, 7)
+
+// Neighbourhood of a vertex v=(t,i,j): the 14 vertices that share a face with
+// it.  Indices:  0..3 at t-1: (i-1,j-1) (i-1,j) (i,j-1) (i,j)
+//                4..6 at t  : (i-1,j-1) (i-1,j) (i,j-1)   (raster predecessors)
+//                7..9 at t  : (i,j+1) (i+1,j) (i+1,j+1)   (raster successors)
+//               10..13 at t+1: (i,j) (i,j+1) (i+1,j) (i+1,j+1)
+// Each of the (at most) 36 faces containing v is named by the pair of its two
+// other vertices: CPT_FREE_FACES lists the 22 faces without a raster
+// predecessor, CPT_PRED_FACES the 14 that use at least one (those depend on
+// reconstructions of the same slice and sit on the wavefront's chain).
+#define CPT_FREE_FACES(F)                                                                           \
+    F(7, 9) F(8, 9) F(7, 13) F(0, 1) F(11, 13) F(2, 8) F(8, 13) F(0, 2) F(12, 13) F(1, 7) F(7, 11) \
+    F(2, 3) F(10, 11) F(3, 7) F(8, 12) F(1, 3) F(10, 12) F(3, 8) F(9, 13) F(0, 3) F(10, 13) F(3, 9)
+#define CPT_PRED_FACES(F)                                                                          \
+    F(6, 8) F(4, 5) F(5, 7) F(4, 6) F(6, 12) F(0, 5) F(5, 11) F(0, 6) F(6, 10) F(2, 6) F(5, 10)  \
+    F(1, 5) F(4, 10) F(0, 4)
+
+__host__ __device__ constexpr int nb_dt(int n) { return n < 4 ? -1 : (n < 10 ? 0 : 1); }
+__host__ __device__ constexpr int nb_di(int n) {
+    return (n == 0 || n == 1 || n == 4 || n == 5) ? -1 : ((n == 8 || n == 9 || n == 12 || n == 13) ? 1 : 0);
+}
+__host__ __device__ constexpr int nb_dj(int n) {
+    return (n == 0 || n == 2 || n == 4 || n == 6) ? -1 : ((n == 7 || n == 9 || n == 11 || n == 13) ? 1 : 0);
+}
+
+// Owners whose faces contain v, as (dt, di, dj, type bit set): the crossed
+// bits of these eight masks decide whether an incident face is in C (Alg. 4).
+struct OwnerSel { int8_t dt, di, dj; uint16_t types; };
+__device__ __constant__ const OwnerSel kOwners[8] = {
+    {0, 0, 0, 0xFFF},
+    {0, 0, -1, (1 << 0) | (1 << 2) | (1 << 6)},
+    {0, -1, -1, (1 << 0) | (1 << 1) | (1 << 10)},
+    {0, -1, 0, (1 << 1) | (1 << 4) | (1 << 8)},
+    {-1, -1, -1, (1 << 2) | (1 << 3) | (1 << 4) | (1 << 5) | (1 << 10) | (1 << 11)},
+    {-1, 0, -1, (1 << 3) | (1 << 6) | (1 << 7)},
+    {-1, -1, 0, (1 << 5) | (1 << 8) | (1 << 9)},
+    {-1, 0, 0, (1 << 7) | (1 << 9) | (1 << 11)},
+};
+
+// ---------------------------------------------------------------------------
+// Simulation of Simplicity (Sec. III-F).  Vertex values carry symbolic
+// perturbations ordered by global id, the origin is exact.  For det(a,b) with
+// id(a) < id(b) the sign is that of the first nonzero of
+// (a.u b.v - a.v b.u, -b.u, b.v, a.u, 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sos_det2(int au, int av, int bu, int bv) {
+    long long d = (long long)au * bv - (long long)av * bu;
+    if (d != 0) return d > 0 ? 1 : -1;
+    if (bu != 0) return bu > 0 ? -1 : 1;
+    if (bv != 0) return bv > 0 ? 1 : -1;
+    if (au != 0) return au > 0 ? 1 : -1;
+    return 1;
+}
+
+// Sign class of a value pair: bit0 u>0, bit1 u<0, bit2 v>0, bit3 v<0.  Three
+// vertices sharing a bit cannot enclose the origin (one component keeps a
+// strict sign over the whole triangle, also after perturbation).
+__device__ __forceinline__ unsigned sign_class(int u, int v) {
+    return (unsigned)(u > 0) | ((unsigned)(u < 0) << 1) | ((unsigned)(v > 0) << 2) | ((unsigned)(v < 0) << 3);
+}
+
+// Face predicate (Eq. 2 under SoS) for vertices p0 < p1 < p2 by id: the
+// origin is inside iff det(p1,p2), det(p2,p0), det(p0,p1) share one sign.
+__device__ __forceinline__ bool face_crossed(int2 p0, int2 p1, int2 p2) {
+    if (sign_class(p0.x, p0.y) & sign_class(p1.x, p1.y) & sign_class(p2.x, p2.y)) return false;
+    int s12 = sos_det2(p1.x, p1.y, p2.x, p2.y);
+    int s20 = -sos_det2(p0.x, p0.y, p2.x, p2.y);
+    if (s12 != s20) return false;
+    int s01 = sos_det2(p0.x, p0.y, p1.x, p1.y);
+    return s01 == s12;
+}
+
+// The 12 owned-face bits of vertex A from its eight corner values
+// (index bit0 = +j, bit1 = +i, bit2 = +t).  valid: bit set per usable type.
+__device__ __forceinline__ uint16_t owned_face_mask(const int2 c[8], unsigned valid) {
+    uint16_t m = 0;
+#define CPT_F(ty, a, b, cc) \
+    if (((valid >> ty) & 1u) && face_crossed(c[a], c[b], c[cc])) m |= (uint16_t)(1u << ty);
+    CPT_OWNED_FACES(CPT_F)
+#undef CPT_F
+    return m;
+}
+
+// Which of the 12 owned faces exist for owner (t,i,j).
+__host__ __device__ __forceinline__ unsigned owned_valid(int H, int W, int T, int t, int i, int j) {
+    bool r = j + 1 < W, d = i + 1 < H, n = t + 1 < T;
+    unsigned m = 0;
+    if (r && d) m |= 0x3u;                                   // 0,1
+    if (r && d && n) m |= 0x3Cu | (1u << 10) | (1u << 11);    // 2..5, 10, 11
+    if (r && n) m |= (1u << 6) | (1u << 7);
+    if (d && n) m |= (1u << 8) | (1u << 9);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 2 in exact integers with strict bounds: a ratio num/den becomes the
+// largest integer e with e < num/den.  min_alg2 returns min(cur, Alg2(...))
+// for vertex 2 = the vertex being bounded; it skips the divisions whenever
+// the same-sign clauses already keep the face's bound at or above cur.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ratio_min(int cur, long long num, long long den) {
+    if (num == 0) return 0;
+    long long n1 = num - 1;
+    if (n1 >= den * (long long)(cur + 1)) return cur;  // floor(n1/den) > cur
+    int q = (int)((float)n1 / (float)den);               // within a few units
+    while ((long long)q * den > n1) --q;
+    while ((long long)(q + 1) * den <= n1) ++q;
+    return q;
+}
+
+__device__ __forceinline__ int min_alg2(int cur, int u0, int v0, int u1, int v1, int u2, int v2) {
+    long long M = (long long)(u1 - u0) * (v2 - v0) - (long long)(v1 - v0) * (u2 - u0);
+    if (M == 0) return 0;
+    bool su = (u0 > 0 && u1 > 0 && u2 > 0) || (u0 < 0 && u1 < 0 && u2 < 0);
+    bool sv = (v0 > 0 && v1 > 0 && v2 > 0) || (v0 < 0 && v1 < 0 && v2 < 0);
+    int fl = -1;
+    if (su) fl = abs(u2) - 1;
+    if (sv) fl = max(fl, abs(v2) - 1);
+    if (fl >= cur) return cur;
+    if ((u1 == 0 && v1 == 0) || (u0 == 0 && v0 == 0)) return 0;
+    long long M1 = (long long)u1 * v2 - (long long)u2 * v1;
+    long long M0 = (long long)u2 * v0 - (long long)u0 * v2;
+    int m = ratio_min(cur, M < 0 ? -M : M, (long long)abs(u1 - u0) + abs(v0 - v1));
+    m = ratio_min(m, M1 < 0 ? -M1 : M1, (long long)abs(u1) + abs(v1));
+    m = ratio_min(m, M0 < 0 ? -M0 : M0, (long long)abs(u0) + abs(v0));
+    return max(m, fl);
+}
+
+// ---------------------------------------------------------------------------
+// Quantisers.  The bound xi becomes xi_q = 2^floor(log2 xi) with code
+// floor(log2 xi)+1 (0 = lossless); the residual r = q - p becomes
+// c = floor((r + xi_q)/(2 xi_q + 1)), predictable when |c| < kRadius.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int xi_code(int xi) { return xi >= 1 ? 32 - __clz(xi) : 0; }
+
+__device__ __forceinline__ int floor_div(int n, int w) {  // w > 0
+    int q = n / w;
+    return (n % w != 0 && n < 0) ? q - 1 : q;
+}
+
+// returns the symbol (0 = unpredictable) and the reconstruction
+__device__ __forceinline__ unsigned quantize(int q, int p, int xiq, int& qhat) {
+    int w = 2 * xiq + 1;
+    int c = floor_div(q - p + xiq, w);
+    if (c > -kRadius && c < kRadius) {
+        qhat = p + c * w;
+        return (unsigned)(c + kRadius);
+    }
+    qhat = q;
+    return 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Semi-Lagrangian predictor (Sec. VI-A, Eqs. 5-9) in FP64 with a fixed
+// evaluation order (no contraction): x = column moves by u*CFL_x, y = row by
+// v*CFL_y; RK2 midpoint when d_inf <= 2, otherwise N = min(ceil(d_inf/2), 32)
+// Euler substeps; every position is clamped to the domain before sampling;
+// the prediction is floor(p + 0.5).  P = reconstructed slice t-1 [H][W].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double clamp_pos(double x, double hi) {
+    if (x < 0.0) return 0.0;
+    if (x > hi) return hi;
+    return x;
+}
+
+struct Bil {
+    int x0, x1, y0, y1;
+    double w00, w10, w01, w11;
+};
+
+__device__ __forceinline__ Bil bil_weights(double x, double y, int H, int W) {
+    Bil b;
+    double xf = floor(x), yf = floor(y);
+    b.x0 = (int)xf;
+    b.y0 = (int)yf;
+    b.x1 = b.x0 + 1 < W ? b.x0 + 1 : W - 1;
+    b.y1 = b.y0 + 1 < H ? b.y0 + 1 : H - 1;
+    double fx = x - xf, fy = y - yf;
+    double gx = 1.0 - fx, gy = 1.0 - fy;
+    b.w00 = __dmul_rn(gx, gy);
+    b.w10 = __dmul_rn(fx, gy);
+    b.w01 = __dmul_rn(gx, fy);
+    b.w11 = __dmul_rn(fx, fy);
+    return b;
+}
+
+__device__ __forceinline__ double bil_sample(const Bil& b, const int2* P, int W, int c) {
+    const int2 a00 = P[(size_t)b.y0 * W + b.x0], a10 = P[(size_t)b.y0 * W + b.x1];
+    const int2 a01 = P[(size_t)b.y1 * W + b.x0], a11 = P[(size_t)b.y1 * W + b.x1];
+    double f00 = (double)(c ? a00.y : a00.x), f10 = (double)(c ? a10.y : a10.x);
+    double f01 = (double)(c ? a01.y : a01.x), f11 = (double)(c ? a11.y : a11.x);
+    double p = __dadd_rn(__dmul_rn(b.w00, f00), __dmul_rn(b.w10, f10));
+    p = __dadd_rn(p, __dmul_rn(b.w01, f01));
+    p = __dadd_rn(p, __dmul_rn(b.w11, f11));
+    return p;
+}
+
+// returns 0 for RK2, N for N substeps
+__device__ __forceinline__ int sl_predict(const int2* P, int H, int W, int i, int j, double cfl_x,
+                                          double cfl_y, int& pu, int& pv) {
+    const int2 g = P[(size_t)i * W + j];
+    double du = __dmul_rn((double)g.x, cfl_x);
+    double dv = __dmul_rn((double)g.y, cfl_y);
+    double dinf = fabs(du) > fabs(dv) ? fabs(du) : fabs(dv);
+    double xs, ys;
+    int mode;
+    const double xmax = (double)(W - 1), ymax = (double)(H - 1);
+    if (dinf <= 2.0) {
+        double xh = clamp_pos(__dsub_rn((double)j, __dmul_rn(0.5, du)), xmax);
+        double yh = clamp_pos(__dsub_rn((double)i, __dmul_rn(0.5, dv)), ymax);
+        Bil b = bil_weights(xh, yh, H, W);
+        double uh = bil_sample(b, P, W, 0);
+        double vh = bil_sample(b, P, W, 1);
+        xs = clamp_pos(__dsub_rn((double)j, __dmul_rn(uh, cfl_x)), xmax);
+        ys = clamp_pos(__dsub_rn((double)i, __dmul_rn(vh, cfl_y)), ymax);
+        mode = 0;
+    } else {
+        double nd = ceil(__ddiv_rn(dinf, 2.0));
+        int N = nd > 32.0 ? 32 : (int)nd;
+        double sx = __ddiv_rn(cfl_x, (double)N), sy = __ddiv_rn(cfl_y, (double)N);
+        xs = (double)j;
+        ys = (double)i;
+        for (int s = 0; s < N; ++s) {
+            Bil b = bil_weights(xs, ys, H, W);
+            double us = bil_sample(b, P, W, 0);
+            double vs = bil_sample(b, P, W, 1);
+            xs = clamp_pos(__dsub_rn(xs, __dmul_rn(us, sx)), xmax);
+            ys = clamp_pos(__dsub_rn(ys, __dmul_rn(vs, sy)), ymax);
+        }
+        mode = N;
+    }
+    Bil b = bil_weights(xs, ys, H, W);
+    pu = (int)floor(__dadd_rn(bil_sample(b, P, W, 0), 0.5));
+    pv = (int)floor(__dadd_rn(bil_sample(b, P, W, 1), 0.5));
+    return mode;
+}
+
+// %globaltimer in nanoseconds (for bounded waits)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace cpt

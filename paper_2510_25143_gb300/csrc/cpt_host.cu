@@ -1,0 +1,616 @@
+// Host side of the library: the C ABI (include/cpt.h), argument checks, device
+// buffers, the launch schedule of the compressor (Alg. 3), the canonical
+// Huffman codebooks and the byte stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/cpt.h"
+#include "cpt_internal.h"
+
+namespace cpt {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static cpt_status fail(cpt_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define CPT_CUDA(call)                                                                                  \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? CPT_ERR_OOM : CPT_ERR_CUDA,                   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+        }                                                                                               \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// stream-ordered device buffers
+// ---------------------------------------------------------------------------
+struct DevArena {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit DevArena(cudaStream_t st) : s(st) {}
+    ~DevArena() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t n) {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(n * sizeof(T), 16), s);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = static_cast<T*>(q);
+        return e;
+    }
+};
+
+static void retain_pool_memory() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// stage timing with CUDA events on the library stream
+// ---------------------------------------------------------------------------
+struct StageTimer {
+    cudaStream_t s;
+    bool on;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int open_stage = -1;
+    cudaEvent_t open_ev = nullptr;
+    StageTimer(cudaStream_t st, bool enable) : s(st), on(enable) {}
+    ~StageTimer() {
+        for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        if (open_ev) cudaEventDestroy(open_ev);
+    }
+    void begin(int stage) {
+        if (!on) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        cudaEventRecord(e, s);
+        open_stage = stage;
+        open_ev = e;
+    }
+    void end() {
+        if (!on || open_stage < 0) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        cudaEventRecord(e, s);
+        recs.push_back({open_stage, open_ev, e});
+        open_stage = -1;
+        open_ev = nullptr;
+    }
+    void collect(cpt_stats* st) {
+        if (!on || !st) return;
+        for (auto& r : recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) st->ms_stage[r.stage] += ms;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// canonical length-limited Huffman codebook (package-merge)
+// ---------------------------------------------------------------------------
+// Leaves are ordered by (weight, symbol).  Level 0 holds the leaves; level l
+// merges the leaves with the pairwise sums of level l-1 (a leaf before a
+// package of equal weight).  Selecting the 2n-2 cheapest items of the last
+// level, a leaf's code length is the number of levels whose selection reaches
+// it; the selection of level l-1 is twice the packages selected at level l.
+static bool huffman_lengths(const std::vector<uint64_t>& freq, int maxlen, std::vector<uint8_t>& len) {
+    const size_t A = freq.size();
+    len.assign(A, 0);
+    std::vector<uint32_t> order;
+    for (uint32_t s = 0; s < A; ++s)
+        if (freq[s]) order.push_back(s);
+    const size_t n = order.size();
+    if (n == 0) return true;
+    if (n == 1) { len[order[0]] = 1; return true; }
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        return freq[a] != freq[b] ? freq[a] < freq[b] : a < b;
+    });
+    if ((size_t)1 << maxlen < n) return false;
+    std::vector<std::vector<uint8_t>> is_leaf(maxlen);
+    std::vector<uint64_t> lvl_w, next_w;
+    lvl_w.reserve(2 * n);
+    next_w.reserve(2 * n);
+    for (size_t a = 0; a < n; ++a) lvl_w.push_back(freq[order[a]]);
+    is_leaf[0].assign(n, 1);
+    for (int l = 1; l < maxlen; ++l) {
+        const size_t npk = lvl_w.size() / 2;
+        next_w.clear();
+        std::vector<uint8_t>& fl = is_leaf[l];
+        fl.clear();
+        size_t a = 0, b = 0;
+        while (a < n || b < npk) {
+            const bool take_leaf = a < n && (b == npk || freq[order[a]] <= lvl_w[2 * b] + lvl_w[2 * b + 1]);
+            if (take_leaf) { next_w.push_back(freq[order[a]]); fl.push_back(1); ++a; }
+            else { next_w.push_back(lvl_w[2 * b] + lvl_w[2 * b + 1]); fl.push_back(0); ++b; }
+        }
+        lvl_w.swap(next_w);
+    }
+    size_t sel = 2 * n - 2;
+    for (int l = maxlen - 1; l >= 0 && sel > 0; --l) {
+        size_t leaves = 0;
+        for (size_t x = 0; x < sel; ++x) leaves += is_leaf[l][x];
+        for (size_t x = 0; x < leaves; ++x) len[order[x]]++;
+        sel = 2 * (sel - leaves);
+    }
+    return true;
+}
+
+// table entry (code << 5) | len; symbols of one length get consecutive codes
+// in symbol order, shorter lengths first
+static void canonical_table(const std::vector<uint8_t>& len, std::vector<uint32_t>& table) {
+    table.assign(len.size(), 0);
+    uint32_t count[33] = {0};
+    for (uint8_t l : len) count[l]++;
+    count[0] = 0;
+    uint32_t next[33] = {0};
+    uint32_t code = 0;
+    for (int l = 1; l <= 32; ++l) {
+        code = (code + count[l - 1]) << 1;
+        next[l] = code;
+    }
+    for (size_t s = 0; s < len.size(); ++s)
+        if (len[s]) table[s] = (next[len[s]]++ << 5) | len[s];
+}
+
+// ---------------------------------------------------------------------------
+// byte stream (little endian)
+// ---------------------------------------------------------------------------
+struct Bytes {
+    std::vector<uint8_t> b;
+    void u32(uint32_t x) { for (int k = 0; k < 4; ++k) b.push_back((uint8_t)(x >> (8 * k))); }
+    void u64(uint64_t x) { u32((uint32_t)x); u32((uint32_t)(x >> 32)); }
+    void f64(double d) { uint64_t x; std::memcpy(&x, &d, 8); u64(x); }
+    void raw(const void* p, size_t n) {
+        const uint8_t* c = static_cast<const uint8_t*>(p);
+        b.insert(b.end(), c, c + n);
+    }
+};
+
+static constexpr uint32_t kMaxCodeLen = 24;
+static constexpr int kRadius = 32768;  // quantisation radius (symbol = c + kRadius)
+static constexpr uint32_t kFormat = 1;
+
+// One Huffman-coded stream: histogram -> codebook -> tile offsets -> words.
+template <typename Sym>
+static cpt_status encode_stream(const Sym* d_sym, size_t nsym, uint32_t alphabet, DevArena& ar, cudaStream_t s,
+                                Bytes& out) {
+    unsigned* d_hist;
+    CPT_CUDA(ar.alloc(&d_hist, alphabet));
+    CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * alphabet, s));
+    if constexpr (sizeof(Sym) == 1) launch_hist_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_hist, s);
+    else launch_hist_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_hist, s);
+    std::vector<unsigned> h(alphabet);
+    CPT_CUDA(cudaMemcpyAsync(h.data(), d_hist, sizeof(unsigned) * alphabet, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint64_t> freq(h.begin(), h.end());
+    std::vector<uint8_t> len;
+    if (!huffman_lengths(freq, kMaxCodeLen, len)) return fail(CPT_ERR_ARG, "alphabet too large for code length limit");
+    std::vector<uint32_t> table;
+    canonical_table(len, table);
+    uint32_t nused = 0;
+    for (uint8_t l : len) nused += l > 0;
+    out.u64(nsym);
+    out.u32(nused);
+    out.u32((uint32_t)kChunkSyms);
+    for (uint32_t sy = 0; sy < alphabet; ++sy)
+        if (len[sy]) out.u32((sy << 8) | len[sy]);
+    const size_t nt = (nsym + kTileSyms - 1) / kTileSyms;
+    uint32_t* d_table;
+    unsigned long long *d_tiles, *d_tmp;
+    CPT_CUDA(ar.alloc(&d_table, alphabet));
+    CPT_CUDA(ar.alloc(&d_tiles, nt + 1));
+    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(nt + 1)));
+    CPT_CUDA(cudaMemcpyAsync(d_table, table.data(), sizeof(uint32_t) * alphabet, cudaMemcpyHostToDevice, s));
+    CPT_CUDA(cudaMemsetAsync(d_tiles, 0, sizeof(unsigned long long) * (nt + 1), s));
+    if constexpr (sizeof(Sym) == 1) launch_tile_bits_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_table, d_tiles, s);
+    else launch_tile_bits_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_table, d_tiles, s);
+    launch_exclusive_scan_u64(d_tiles, nt + 1, d_tmp, s);
+    std::vector<unsigned long long> toff(nt + 1);
+    CPT_CUDA(cudaMemcpyAsync(toff.data(), d_tiles, sizeof(unsigned long long) * (nt + 1), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    const uint64_t nbits = toff[nt];
+    const uint64_t nwords = (nbits + 31) / 32;
+    const size_t per_chunk = kChunkSyms / kTileSyms;
+    for (size_t c = 0; c * kChunkSyms < nsym; ++c) out.u64(toff[c * per_chunk]);
+    out.u64(nwords);
+    uint32_t* d_words;
+    CPT_CUDA(ar.alloc(&d_words, nwords + 1));
+    CPT_CUDA(cudaMemsetAsync(d_words, 0, sizeof(uint32_t) * (nwords + 1), s));
+    if constexpr (sizeof(Sym) == 1)
+        launch_encode_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_table, d_tiles, d_words, s);
+    else
+        launch_encode_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_table, d_tiles, d_words, s);
+    const size_t at = out.b.size();
+    out.b.resize(at + 4 * nwords);
+    if (nwords) CPT_CUDA(cudaMemcpyAsync(out.b.data() + at, d_words, 4 * nwords, cudaMemcpyDeviceToHost, s));
+    return CPT_OK;
+}
+
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------------------
+// compression (Alg. 3)
+// ---------------------------------------------------------------------------
+static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
+                                size_t* out_bytes, cpt_stats* stats, const cpt_debug* dbg) {
+    if (!uv || !dims || !prm || !out || !out_bytes) return fail(CPT_ERR_ARG, "null argument");
+    const int H = dims->H, W = dims->W, T = dims->T;
+    if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
+    if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
+    if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
+    if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+    const int B = prm->block > 0 ? prm->block : 16;
+    const int nstride = prm->stride > 0 ? prm->stride : 2;
+    if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
+    const double dx = dims->dx > 0 ? dims->dx : 1.0, dy = dims->dy > 0 ? dims->dy : 1.0;
+    const double dt = dims->dt > 0 ? dims->dt : 1.0;
+    const size_t N = (size_t)H * W * T, NV = 2 * N, SL = (size_t)H * W;
+    cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(CPT_ERR_CUDA, "no CUDA device available");
+    }
+    retain_pool_memory();
+    cpt_stats st;
+    std::memset(&st, 0, sizeof(st));
+    StageTimer tm(s, true);
+    cudaEvent_t ev0, ev1;
+    CPT_CUDA(cudaEventCreate(&ev0));
+    CPT_CUDA(cudaEventCreate(&ev1));
+    struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
+    DevArena ar(s);
+    CPT_CUDA(cudaEventRecord(ev0, s));
+
+    // input on the device, 16-byte aligned
+    const float* d_uv = uv;
+    if (!is_device_pointer(uv) || (reinterpret_cast<uintptr_t>(uv) & 15u)) {
+        float* tmp;
+        CPT_CUDA(ar.alloc(&tmp, NV));
+        CPT_CUDA(cudaMemcpyAsync(tmp, uv, NV * sizeof(float), cudaMemcpyDefault, s));
+        d_uv = tmp;
+    }
+    const int nsm = sm_count();
+
+    // ---- stage 0: range, scale, fixed point
+    tm.begin(0);
+    const int rblocks = nsm * 4;
+    RangePartial* d_part;
+    CPT_CUDA(ar.alloc(&d_part, rblocks));
+    launch_range(d_uv, NV, d_part, rblocks, s);
+    st.launches[0]++;
+    std::vector<RangePartial> part(rblocks);
+    CPT_CUDA(cudaMemcpyAsync(part.data(), d_part, sizeof(RangePartial) * rblocks, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    float mn = INFINITY, mx = -INFINITY, am = 0.f;
+    unsigned bad = 0;
+    for (auto& p : part) { mn = std::min(mn, p.mn); mx = std::max(mx, p.mx); am = std::max(am, p.amax); bad |= p.bad; }
+    if (bad) return fail(CPT_ERR_ARG, "input holds a non-finite value");
+    int k = 0;
+    if (am > 0.f) { int e; std::frexp((double)am, &e); k = 23 - e; }
+    const double eps = prm->mode == CPT_EB_REL ? prm->eb * ((double)mx - (double)mn) : prm->eb;
+    double ef = std::floor(std::ldexp(eps, k) - 0.5);
+    int eps_int = !(ef > 0) ? 0 : (ef > 8388608.0 ? 8388608 : (int)ef);
+    st.scale_log2 = k;
+    st.eps_int = eps_int;
+    st.eps = eps;
+    int32_t *d_q, *d_qhat;
+    CPT_CUDA(ar.alloc(&d_q, NV));
+    CPT_CUDA(ar.alloc(&d_qhat, NV));
+    launch_to_fixed(d_uv, NV, std::ldexp(1.0, k), d_q, nsm * 8, s);
+    st.launches[0]++;
+    tm.end();
+
+    // ---- stage 1: crossed-face masks (C)
+    tm.begin(1);
+    uint16_t* d_mask;
+    unsigned long long* d_cnt64;  // [0] crossed faces, [1..4] encoder counters
+    CPT_CUDA(ar.alloc(&d_mask, N));
+    CPT_CUDA(ar.alloc(&d_cnt64, 8));
+    CPT_CUDA(cudaMemsetAsync(d_cnt64, 0, 8 * sizeof(unsigned long long), s));
+    launch_face_masks(d_q, H, W, T, d_mask, d_cnt64, s);
+    st.launches[1]++;
+    tm.end();
+
+    // ---- stages 2-4: per slice MoP / SL, incident-face bounds, wavefront
+    const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
+    const int nstrips = wave_strips(H);
+    uint8_t *d_qxi, *d_modes;
+    uint32_t* d_sym;
+    int *d_xipart, *d_status, *d_xiout = nullptr;
+    int2* d_psl;
+    unsigned *d_prog, *d_ticket;
+    CPT_CUDA(ar.alloc(&d_qxi, N));
+    CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
+    CPT_CUDA(ar.alloc(&d_sym, N));
+    CPT_CUDA(ar.alloc(&d_xipart, SL));
+    CPT_CUDA(ar.alloc(&d_psl, SL));
+    CPT_CUDA(ar.alloc(&d_status, 1));
+    CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
+    CPT_CUDA(ar.alloc(&d_ticket, T));
+    if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
+    CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
+    CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    CPT_CUDA(cudaMemsetAsync(d_prog, 0, sizeof(unsigned) * T * nstrips, s));
+    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned) * T, s));
+    SliceArgs a;
+    a.q = reinterpret_cast<const int2*>(d_q);
+    a.qhat = reinterpret_cast<int2*>(d_qhat);
+    a.mask = d_mask;
+    a.xi_part = d_xipart;
+    a.psl = d_psl;
+    a.modes = d_modes;
+    a.qxi = d_qxi;
+    a.sym = d_sym;
+    a.xi_out = d_xiout;
+    a.progress = d_prog;
+    a.ticket = d_ticket;
+    a.status = d_status;
+    a.counters = d_cnt64 + 1;
+    a.H = H; a.W = W; a.T = T;
+    a.eps_int = eps_int;
+    a.pred = (int)prm->pred;
+    a.B = B; a.n = nstride; a.nby = nby; a.nbx = nbx;
+    a.cfl_x = std::ldexp(dt / dx, -k);
+    a.cfl_y = std::ldexp(dt / dy, -k);
+    a.timeout_ns = 2000000000ll;
+    for (int t = 0; t < T; ++t) {
+        a.t = t;
+        if (t >= 1 && eps_int >= 1 && prm->pred != CPT_PRED_LORENZO) {
+            tm.begin(2);
+            if (prm->pred == CPT_PRED_MOP) launch_mop(a, s);
+            else launch_sl(a, s);
+            st.launches[2]++;
+            tm.end();
+        }
+        tm.begin(3);
+        launch_pre(a, s);
+        st.launches[3]++;
+        tm.end();
+        tm.begin(4);
+        launch_wave(a, s);
+        st.launches[4]++;
+        tm.end();
+    }
+    CPT_CUDA(cudaGetLastError());
+
+    // ---- stage 5: compaction + entropy coding
+    tm.begin(5);
+    unsigned long long *d_off, *d_stmp;
+    CPT_CUDA(ar.alloc(&d_off, N));
+    CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(N)));
+    launch_count_pack(d_qxi, d_sym, N, d_off, s);
+    unsigned long long last_cnt = 0, last_off = 0;
+    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    launch_exclusive_scan_u64(d_off, N, d_stmp, s);
+    CPT_CUDA(cudaMemcpyAsync(&last_off, d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    int status = 0;
+    unsigned long long cnt_h[8];
+    CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaMemcpyAsync(cnt_h, d_cnt64, sizeof(cnt_h), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (status != 0) return fail((cpt_status)status, "wavefront wait timed out");
+    const unsigned long long tot = last_off + last_cnt;
+    const size_t n_qd = (size_t)(tot >> 32), n_ld = (size_t)(tot & 0xFFFFFFFFull);
+    uint16_t* d_qd;
+    int32_t* d_ld;
+    CPT_CUDA(ar.alloc(&d_qd, n_qd));
+    CPT_CUDA(ar.alloc(&d_ld, n_ld));
+    launch_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
+    Bytes bs;
+    bs.raw("CPT1", 4);
+    bs.u32(kFormat);
+    bs.u32((uint32_t)H);
+    bs.u32((uint32_t)W);
+    bs.u32((uint32_t)T);
+    bs.u32((uint32_t)k);
+    bs.u32((uint32_t)eps_int);
+    bs.u32((uint32_t)prm->pred);
+    bs.u32((uint32_t)B);
+    bs.u32((uint32_t)nstride);
+    bs.u32((uint32_t)kRadius);
+    bs.u32(0);
+    bs.f64(dx);
+    bs.f64(dy);
+    bs.f64(dt);
+    bs.f64(eps);
+    bs.u64(n_ld);
+    const size_t nblk = prm->pred == CPT_PRED_MOP ? (size_t)T * nby * nbx : 0;
+    const size_t mode_bytes = (nblk + 7) / 8;
+    bs.u64(mode_bytes);
+    std::vector<uint8_t> modes_h((size_t)T * nby * nbx);
+    if (nblk) {
+        CPT_CUDA(cudaMemcpyAsync(modes_h.data(), d_modes, nblk, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        std::vector<uint8_t> packed(mode_bytes, 0);
+        for (size_t x = 0; x < nblk; ++x)
+            if (modes_h[x]) packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+        bs.raw(packed.data(), packed.size());
+    }
+    cpt_status rc = encode_stream<uint8_t>(d_qxi, N, 33, ar, s, bs);
+    if (rc != CPT_OK) return rc;
+    rc = encode_stream<uint16_t>(d_qd, n_qd, 2 * kRadius, ar, s, bs);
+    if (rc != CPT_OK) return rc;
+    const size_t at = bs.b.size();
+    bs.b.resize(at + 4 * n_ld);
+    if (n_ld) CPT_CUDA(cudaMemcpyAsync(bs.b.data() + at, d_ld, 4 * n_ld, cudaMemcpyDeviceToHost, s));
+    st.launches[5] += 9;
+    tm.end();
+
+    // ---- stage 6: verification (Eq. 4 on every face, pointwise bound)
+    VerifyOut vo;
+    std::memset(&vo, 0, sizeof(vo));
+    if (prm->verify) {
+        tm.begin(6);
+        VerifyOut* d_vo;
+        CPT_CUDA(ar.alloc(&d_vo, 1));
+        CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
+        launch_verify(d_qhat, d_mask, d_uv, H, W, T, std::ldexp(1.0, -k), d_vo, s);
+        st.launches[6]++;
+        CPT_CUDA(cudaMemcpyAsync(&vo, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
+        tm.end();
+    }
+    // ---- debug copies
+    if (dbg) {
+        if (dbg->q) CPT_CUDA(cudaMemcpyAsync(dbg->q, d_q, NV * 4, cudaMemcpyDeviceToHost, s));
+        if (dbg->qhat) CPT_CUDA(cudaMemcpyAsync(dbg->qhat, d_qhat, NV * 4, cudaMemcpyDeviceToHost, s));
+        if (dbg->xi) CPT_CUDA(cudaMemcpyAsync(dbg->xi, d_xiout, N * 4, cudaMemcpyDeviceToHost, s));
+        if (dbg->qxi) CPT_CUDA(cudaMemcpyAsync(dbg->qxi, d_qxi, N, cudaMemcpyDeviceToHost, s));
+        if (dbg->mask) CPT_CUDA(cudaMemcpyAsync(dbg->mask, d_mask, N * 2, cudaMemcpyDeviceToHost, s));
+        if (dbg->modes) CPT_CUDA(cudaMemcpyAsync(dbg->modes, d_modes, (size_t)T * nby * nbx, cudaMemcpyDeviceToHost, s));
+        if (dbg->sym) {
+            std::vector<uint32_t> tmp(N);
+            CPT_CUDA(cudaMemcpyAsync(tmp.data(), d_sym, N * 4, cudaMemcpyDeviceToHost, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+            for (size_t v = 0; v < N; ++v) {
+                dbg->sym[2 * v] = (uint16_t)(tmp[v] & 0xFFFFu);
+                dbg->sym[2 * v + 1] = (uint16_t)(tmp[v] >> 16);
+            }
+        }
+    }
+    CPT_CUDA(cudaEventRecord(ev1, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    CPT_CUDA(cudaGetLastError());
+
+    uint8_t* buf = static_cast<uint8_t*>(std::malloc(bs.b.size()));
+    if (!buf) return fail(CPT_ERR_OOM, "host allocation failed");
+    std::memcpy(buf, bs.b.data(), bs.b.size());
+    *out = buf;
+    *out_bytes = bs.b.size();
+
+    float ms_total = 0.f;
+    cudaEventElapsedTime(&ms_total, ev0, ev1);
+    tm.collect(&st);
+    st.ms_total = ms_total;
+    st.faces = 0;
+    {
+        const unsigned long long Hl = H, Wl = W, Tl = T;
+        const unsigned long long E = Hl * (Wl - 1) + Wl * (Hl - 1) + (Hl - 1) * (Wl - 1);
+        st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
+    }
+    st.crossed_faces = cnt_h[0];
+    st.sl_blocks = cnt_h[3];
+    st.blocks = prm->pred == CPT_PRED_MOP ? (uint64_t)T * nby * nbx : 0;
+    st.n_ld = n_ld;
+    st.n_qd = n_qd;
+    st.out_bytes = bs.b.size();
+    st.ratio = (double)(NV * 4) / (double)bs.b.size();
+    // lossless and unpredictable counts from the compaction totals
+    {
+        std::vector<unsigned> hx(33, 0);
+        (void)hx;
+    }
+    st.verify_mismatch_slice = vo.mismatch_slice;
+    st.verify_mismatch_slab = vo.mismatch_slab;
+    double linf;
+    std::memcpy(&linf, &vo.linf_bits, 8);
+    st.linf = linf;
+    if (prm->verify) {
+        double mse = vo.sq_err / (double)NV;
+        double range = (double)mx - (double)mn;
+        st.psnr = mse > 0 ? 20.0 * std::log10(range) - 10.0 * std::log10(mse) : INFINITY;
+    }
+    // lossless vertices: n_ld minus the unpredictable components; n_qd = 2 * (N - lossless)
+    st.lossless_vertices = N - n_qd / 2;
+    st.unpredictable = n_ld - 2 * st.lossless_vertices;
+    if (stats) *stats = st;
+    if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= eps)))
+        return fail(CPT_ERR_VERIFY, "reconstruction changed a face predicate or exceeded the bound");
+    return CPT_OK;
+}
+
+}  // namespace cpt
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+cpt_status cpt_compress_ex(const float* uv, const cpt_dims* dims, const cpt_params* params, uint8_t** out,
+                           size_t* out_bytes, cpt_stats* stats, const cpt_debug* dbg) {
+    return cpt::compress_impl(uv, dims, params, out, out_bytes, stats, dbg);
+}
+
+cpt_status cpt_compress(const float* uv, const cpt_dims* dims, const cpt_params* params, uint8_t** out,
+                        size_t* out_bytes, cpt_stats* stats) {
+    return cpt::compress_impl(uv, dims, params, out, out_bytes, stats, nullptr);
+}
+
+cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out, cpt_dims* dims_out,
+                          void* cuda_stream) {
+    (void)in; (void)in_bytes; (void)uv_out; (void)qhat_out; (void)dims_out; (void)cuda_stream;
+    return cpt::fail(CPT_ERR_UNSUPPORTED, "decompression not built yet");
+}
+
+cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
+                                    void* cuda_stream) {
+    (void)uv; (void)dims; (void)scale_log2; (void)out; (void)cuda_stream;
+    return cpt::fail(CPT_ERR_UNSUPPORTED, "trajectory extraction not built yet");
+}
+
+void cpt_free(void* p) { std::free(p); }
+
+void cpt_free_trajs(cpt_trajs* t) {
+    if (!t) return;
+    std::free(t->offsets);
+    std::free(t->face_ids);
+    std::free(t->xyt);
+    std::free(t);
+}
+
+const char* cpt_error_string(cpt_status s) {
+    switch (s) {
+        case CPT_OK: return "ok";
+        case CPT_ERR_ARG: return "invalid argument";
+        case CPT_ERR_CUDA: return "CUDA error";
+        case CPT_ERR_OOM: return "out of memory";
+        case CPT_ERR_CORRUPT: return "corrupt stream";
+        case CPT_ERR_VERIFY: return "verification failed";
+        case CPT_ERR_TIMEOUT: return "kernel wait timed out";
+        case CPT_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* cpt_last_error(void) { return cpt::g_last_error.c_str(); }
+
+uint32_t cpt_version(void) { return (1u << 8) | cpt::kFormat; }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations of the library: small device structs and the host-side
+// launchers of every kernel (one translation unit per kernel family).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cpt {
+
+struct RangePartial {
+    float mn, mx, amax;
+    unsigned bad;
+};
+
+struct VerifyOut {
+    unsigned long long mismatch_slice;
+    unsigned long long mismatch_slab;
+    unsigned long long linf_bits;  // double bits of max |x_hat - x|
+    double sq_err;
+};
+
+// Per-slice arguments of the encoder kernels.
+struct SliceArgs {
+    const int2* q;          // original fixed point [T][H][W]
+    int2* qhat;             // reconstruction [T][H][W] (slices < t final)
+    const uint16_t* mask;   // crossed-face masks [T][H][W]
+    int* xi_part;           // [H][W] bound over the faces without raster predecessors
+    int2* psl;              // [H][W] semi-Lagrangian predictions of slice t
+    uint8_t* modes;         // [T][nby][nbx] block modes (1 = SL)
+    uint8_t* qxi;           // [T][H][W] bound codes
+    uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
+    int* xi_out;            // optional [T][H][W] integer bounds
+    unsigned* progress;     // [T][nstrips] wavefront progress (columns published)
+    unsigned* ticket;       // [T] strip tickets
+    int* status;            // device status word (0 = ok)
+    unsigned long long* counters;  // [4]: substep vertices, substeps, sl blocks, spare
+    int H, W, T, t;
+    int eps_int;
+    int pred;               // 0 3DL, 1 SL, 2 MoP
+    int B, n;               // MoP block side and sampling stride
+    int nby, nbx;
+    double cfl_x, cfl_y;
+    long long timeout_ns;
+};
+
+// k_field.cu
+void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s);
+void launch_to_fixed(const float* uv, size_t n, double scale, int32_t* q, int nblocks, cudaStream_t s);
+void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, unsigned long long* ncrossed,
+                       cudaStream_t s);
+void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T,
+                   double inv_scale, VerifyOut* out, cudaStream_t s);
+
+// k_encode.cu
+void launch_sl(const SliceArgs& a, cudaStream_t s);
+void launch_mop(const SliceArgs& a, cudaStream_t s);
+void launch_pre(const SliceArgs& a, cudaStream_t s);
+void launch_wave(const SliceArgs& a, cudaStream_t s);
+int wave_strips(int H);
+
+// k_entropy.cu
+struct EntropyBufs;
+size_t scan_temp_elems(size_t n);
+void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s);
+void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long long* tmp, cudaStream_t s);
+void launch_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q, const unsigned long long* off,
+                    size_t N, uint16_t* qd_out, int32_t* ld_out, cudaStream_t s);
+void launch_hist_u8(const uint8_t* x, size_t n, unsigned* hist /*33*/, cudaStream_t s);
+void launch_hist_u16(const uint16_t* x, size_t n, unsigned* hist /*65536*/, cudaStream_t s);
+// code table entries: (code << 5) | len, len <= 24
+void launch_tile_bits_u8(const uint8_t* x, size_t n, const uint32_t* table, unsigned long long* tile_bits,
+                         cudaStream_t s);
+void launch_tile_bits_u16(const uint16_t* x, size_t n, const uint32_t* table, unsigned long long* tile_bits,
+                          cudaStream_t s);
+void launch_encode_u8(const uint8_t* x, size_t n, const uint32_t* table, const unsigned long long* tile_off,
+                      uint32_t* words, cudaStream_t s);
+void launch_encode_u16(const uint16_t* x, size_t n, const uint32_t* table, const unsigned long long* tile_off,
+                       uint32_t* words, cudaStream_t s);
+constexpr int kTileSyms = 4096;     // symbols per encode tile
+constexpr int kChunkSyms = 16384;   // symbols per decode chunk (stream sync points)
+
+}  // namespace cpt

@@ -1,0 +1,107 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element on the same seeded inputs.  Integer work (fixed point,
+face predicates, bounds, codes, reconstruction, bytes) must be bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_25143_gb300 import cpt, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(uv):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(uv)).to("cuda:0")
+
+
+def compare(uv, eb, pred="lorenzo", eb_mode="rel", block=16, stride=2, dx=1.0, dy=1.0, dt=1.0,
+            host_input=False):
+    src = uv if host_input else _dev(uv)
+    blob, st, g = cpt.compress(src, eb, eb_mode=eb_mode, pred=pred, block=block, stride=stride,
+                               dx=dx, dy=dy, dt=dt, debug=True)
+    r = oracle.compress(uv, eb, eb_mode=eb_mode, pred=pred, block=block, stride=stride, dx=dx, dy=dy, dt=dt)
+    assert st["scale_log2"] == r["stats"]["k"] and st["eps_int"] == r["stats"]["eps_int"]
+    assert (g["q"] == r["q"]).all()
+    assert (g["mask"] == r["mask"]).all()
+    assert (g["xi"] == r["xi"]).all()
+    assert (g["qxi"] == r["qxi"]).all()
+    nz = r["qxi"] > 0
+    assert (g["sym"][nz] == r["qd"][nz]).all()
+    if pred == "mop":
+        assert (g["modes"] == r["modes"]).all()
+    assert (g["qhat"] == r["qhat"]).all()
+    assert blob == r["bytes"]
+    assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
+    assert st["linf"] <= st["eps"] or st["eps_int"] == 0
+    assert st["crossed_faces"] == r["stats"]["crossed_faces"]
+    assert st["n_ld"] == r["stats"]["n_ld"] and st["n_qd"] == r["stats"]["n_qd"]
+    return blob, st, g, r
+
+
+@pytest.mark.parametrize("pred", ["lorenzo", "sl", "mop"])
+def test_vortex64(pred):
+    uv, eb = synth.workload("vortex64")
+    compare(uv, eb, pred)
+
+
+@pytest.mark.parametrize("shape", [(37, 45, 5), (33, 70, 3), (100, 40, 4), (2, 2, 3), (5, 3, 1)])
+@pytest.mark.parametrize("pred", ["lorenzo", "mop"])
+def test_ragged_shapes(shape, pred):
+    H, W, T = shape
+    uv = synth.vortex_sum(H, W, T, seed=7 + H, n_vortex=3)
+    compare(uv, 5e-3, pred)
+
+
+def test_sl_nonunit_spacing_and_host_input():
+    uv = synth.vortex_sum(48, 40, 6, seed=3, drift=2.5)
+    compare(uv, 2e-2, "sl", dx=0.5, dy=2.0, dt=3.0, host_input=True)
+
+
+def test_mop_block8_stride3():
+    uv = synth.vortex_sum(50, 61, 5, seed=4)
+    compare(uv, 1e-2, "mop", block=8, stride=3)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_small_integer_fields_degenerate_sos(seed):
+    rng = np.random.default_rng(100 + seed)
+    uv = rng.integers(-2, 3, (4, 9, 11, 2)).astype(np.float32)
+    compare(uv, 0.4, "lorenzo", eb_mode="abs")
+    compare(uv, 0.4, "mop", eb_mode="abs", block=4)
+
+
+def test_zero_and_constant_fields():
+    compare(np.zeros((3, 6, 7, 2), np.float32), 1e-2, "mop")
+    c = np.ones((3, 6, 7, 2), np.float32) * 0.25
+    compare(c, 0.01, "sl", eb_mode="abs")
+
+
+def test_zero_error_bound_is_lossless():
+    uv = synth.vortex_sum(20, 24, 3, seed=5)
+    blob, st, g, r = compare(uv, 0.0, "lorenzo", eb_mode="abs")
+    assert (g["qhat"] == g["q"]).all() and st["lossless_vertices"] == 20 * 24 * 3
+
+
+def test_large_bound():
+    uv = synth.vortex_sum(30, 30, 4, seed=6)
+    compare(uv, 10.0, "lorenzo", eb_mode="abs")
+
+
+def test_street512_full_size():
+    """Full 512x512x100 workload in the benchmark's configuration: codes of the
+    first slices against the oracle (which stops after them), crossed-face
+    masks everywhere, the oracle decoder on the GPU stream, and the invariants."""
+    uv, eb = synth.workload("street512")
+    blob, st, g = cpt.compress(_dev(uv), eb, pred="lorenzo", debug=True)
+    r = oracle.compress(uv, eb, pred="lorenzo", t_end=3)
+    assert (g["q"] == r["q"]).all()
+    assert (g["mask"] == r["mask"]).all()
+    for f in ("xi", "qxi"):
+        assert (g[f][:3] == r[f][:3]).all()
+    assert (g["qhat"][:3] == r["qhat"][:3]).all()
+    qh, x, k = oracle.decompress(blob)
+    assert (qh == g["qhat"]).all()
+    assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
+    assert st["linf"] <= st["eps"]
+    assert np.abs(x.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
