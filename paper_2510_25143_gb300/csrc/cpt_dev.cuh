@@ -153,12 +153,68 @@ __device__ __forceinline__ int min_alg2(int cur, int u0, int v0, int u1, int v1,
     return max(m, fl);
 }
 
+// A face through raster predecessors, evaluated before those predecessors are
+// reconstructed: vertex 2 = the bounded vertex (its own value is final at
+// that time), neighbours 0 and 1 hold their current values, a predecessor's
+// original value standing in for a reconstruction within +-E of it (E bounds
+// every |qhat - q|).  Returns true when, for any such reconstructions, the
+// face keeps M != 0 and a same-sign clause holding with bound >= xi, so its
+// Alg. 2 value cannot lower a bound that starts at xi.
+__device__ __forceinline__ bool pred_face_inert(int2 a0, int2 a1, int2 c, bool p0, bool p1, int E, int xi) {
+    const int m0 = p0 ? E : 0, m1 = p1 ? E : 0;
+    const bool su = (c.x > 0 && a0.x > m0 && a1.x > m1) || (c.x < 0 && a0.x < -m0 && a1.x < -m1);
+    const bool sv = (c.y > 0 && a0.y > m0 && a1.y > m1) || (c.y < 0 && a0.y < -m0 && a1.y < -m1);
+    int fl = -1;
+    if (su) fl = abs(c.x) - 1;
+    if (sv) fl = max(fl, abs(c.y) - 1);
+    if (fl < xi) return false;
+    const long long A = (long long)a1.x - a0.x, Bv = (long long)c.y - a0.y;
+    const long long Cv = (long long)a1.y - a0.y, Du = (long long)c.x - a0.x;
+    long long M = A * Bv - Cv * Du;
+    M = M < 0 ? -M : M;
+    const long long e = E, k0 = p0 ? 1 : 0, k01 = (p0 ? 1 : 0) + (p1 ? 1 : 0);
+    const long long D = e * (k0 * (llabs(A) + llabs(Cv)) + k01 * (llabs(Bv) + llabs(Du))) + 2 * k0 * k01 * e * e;
+    return M > D;
+}
+
 // ---------------------------------------------------------------------------
 // Quantisers.  The bound xi becomes xi_q = 2^floor(log2 xi) with code
 // floor(log2 xi)+1 (0 = lossless); the residual r = q - p becomes
 // c = floor((r + xi_q)/(2 xi_q + 1)), predictable when |c| < kRadius.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int xi_code(int xi) { return xi >= 1 ? 32 - __clz(xi) : 0; }
+
+// floor(2^32 / (2^c + 1)): reciprocal of the quantiser width w = 2 xi_q + 1
+// for bound code c (xi_q = 2^(c-1)), c = 1..24
+#define CPT_INVW(c) (unsigned)(4294967296ull / ((1ull << (c)) + 1ull))
+__device__ __constant__ const unsigned kInvW[25] = {
+    0u,          CPT_INVW(1),  CPT_INVW(2),  CPT_INVW(3),  CPT_INVW(4),  CPT_INVW(5),  CPT_INVW(6),
+    CPT_INVW(7), CPT_INVW(8),  CPT_INVW(9),  CPT_INVW(10), CPT_INVW(11), CPT_INVW(12), CPT_INVW(13),
+    CPT_INVW(14), CPT_INVW(15), CPT_INVW(16), CPT_INVW(17), CPT_INVW(18), CPT_INVW(19), CPT_INVW(20),
+    CPT_INVW(21), CPT_INVW(22), CPT_INVW(23), CPT_INVW(24)};
+#undef CPT_INVW
+
+// floor(n / w) for |n| < 2^31, w > 1, m = floor(2^32 / w): the multiply-high
+// estimate is at most one below the quotient of the non-negative operand.
+__device__ __forceinline__ int floor_div_inv(int n, int w, unsigned m) {
+    unsigned x = n >= 0 ? (unsigned)n : (unsigned)(-(n + 1));
+    unsigned q = __umulhi(x, m);
+    if (x - q * (unsigned)w >= (unsigned)w) ++q;
+    return n >= 0 ? (int)q : -(int)q - 1;
+}
+
+// returns the symbol (0 = unpredictable) and the reconstruction; code >= 1
+__device__ __forceinline__ unsigned quantize_code(int q, int p, int code, int& qhat) {
+    const int xiq = 1 << (code - 1);
+    const int w = 2 * xiq + 1;
+    const int c = floor_div_inv(q - p + xiq, w, kInvW[code]);
+    if (c > -kRadius && c < kRadius) {
+        qhat = p + c * w;
+        return (unsigned)(c + kRadius);
+    }
+    qhat = q;
+    return 0u;
+}
 
 __device__ __forceinline__ int floor_div(int n, int w) {  // w > 0
     int q = n / w;

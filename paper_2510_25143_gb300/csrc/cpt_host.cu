@@ -356,12 +356,14 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     uint32_t* d_sym;
     int *d_xipart, *d_status, *d_xiout = nullptr;
     int2* d_psl;
+    uint16_t* d_pmask;
     unsigned *d_prog, *d_ticket;
     CPT_CUDA(ar.alloc(&d_qxi, N));
     CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
     CPT_CUDA(ar.alloc(&d_sym, N));
     CPT_CUDA(ar.alloc(&d_xipart, SL));
     CPT_CUDA(ar.alloc(&d_psl, SL));
+    CPT_CUDA(ar.alloc(&d_pmask, SL));
     CPT_CUDA(ar.alloc(&d_status, 1));
     CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
     CPT_CUDA(ar.alloc(&d_ticket, T));
@@ -375,6 +377,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     a.qhat = reinterpret_cast<int2*>(d_qhat);
     a.mask = d_mask;
     a.xi_part = d_xipart;
+    a.pmask = d_pmask;
     a.psl = d_psl;
     a.modes = d_modes;
     a.qxi = d_qxi;

@@ -25,6 +25,7 @@ struct SliceArgs {
     int2* qhat;             // reconstruction [T][H][W] (slices < t final)
     const uint16_t* mask;   // crossed-face masks [T][H][W]
     int* xi_part;           // [H][W] bound over the faces without raster predecessors
+    uint16_t* pmask;        // [H][W] predecessor faces that may still lower the bound
     int2* psl;              // [H][W] semi-Lagrangian predictions of slice t
     uint8_t* modes;         // [T][nby][nbx] block modes (1 = SL)
     uint8_t* qxi;           // [T][H][W] bound codes

@@ -51,9 +51,18 @@ __device__ __forceinline__ void load_far_neighbours(const int2* __restrict__ q, 
         xi = min_alg2(xi, nb[a].x, nb[a].y, nb[b].x, nb[b].y, qv.x, qv.y);
 
 // ---------------------------------------------------------------------------
-// pre_kernel: C membership of the 36 incident faces and the bound over the
-// 22 predecessor-free faces.
+// pre_kernel: C membership of the 36 incident faces, the bound over the 22
+// predecessor-free faces, and the set of the 14 predecessor faces that may
+// still lower that bound once the predecessors are reconstructed.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr bool is_pred(int n) { return n >= 4 && n <= 6; }
+
+#define CPT_PRED_MARK(a, b)                                                                       \
+    if (((valid >> (a)) & (valid >> (b)) & 1u) &&                                                 \
+        !pred_face_inert(nb[a], nb[b], qv, is_pred(a), is_pred(b), E, xi))                        \
+        pm |= 1u << bit;                                                                          \
+    ++bit;
+
 __global__ void __launch_bounds__(256) pre_kernel(SliceArgs a) {
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
     const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -67,16 +76,29 @@ __global__ void __launch_bounds__(256) pre_kernel(SliceArgs a) {
             crossed |= (__ldg(a.mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
     }
     int xi = 0;
+    unsigned pm = 0;
     if (!crossed && a.eps_int > 0) {
         xi = a.eps_int;
         const unsigned valid = nb_valid(H, W, T, t, i, j);
         int2 nb[14];
         load_far_neighbours(a.q, a.qhat, H, W, t, i, j, valid, nb);
-        const int2 qv = __ldg(a.q + ((size_t)t * H + i) * W + j);
+        const size_t v = ((size_t)t * H + i) * W + j;
+        const int2 qv = __ldg(a.q + v);
         CPT_FREE_FACES(CPT_FACE)
+        if (xi > 0) {
+            const int2 z = make_int2(0, 0);
+            nb[4] = (valid & (1u << 4)) ? __ldg(a.q + v - W - 1) : z;
+            nb[5] = (valid & (1u << 5)) ? __ldg(a.q + v - W) : z;
+            nb[6] = (valid & (1u << 6)) ? __ldg(a.q + v - 1) : z;
+            const int E = 1 << (31 - __clz(a.eps_int));
+            int bit = 0;
+            CPT_PRED_FACES(CPT_PRED_MARK)
+        }
     }
     a.xi_part[(size_t)i * W + j] = xi;
+    a.pmask[(size_t)i * W + j] = (uint16_t)pm;
 }
+#undef CPT_PRED_MARK
 
 // ---------------------------------------------------------------------------
 // sl_kernel: semi-Lagrangian predictions of every vertex of slice t >= 1.
@@ -251,6 +273,7 @@ __global__ void __launch_bounds__(1024) mop_kernel(SliceArgs a) {
 struct StepIn {
     int2 qv;
     int xi;
+    unsigned pm;
     int2 psl;
     unsigned use_sl;
     int2 nb[14];
@@ -259,20 +282,37 @@ struct StepIn {
 __device__ __forceinline__ void load_step(const SliceArgs& a, int i, int j, StepIn& in) {
     const int H = a.H, W = a.W, t = a.t;
     in.xi = 0;
+    in.pm = 0;
     in.use_sl = 0;
     if (i >= H || j < 0 || j >= W) return;
     const size_t v = ((size_t)t * H + i) * W + j;
     in.qv = __ldg(a.q + v);
     in.xi = __ldg(a.xi_part + (size_t)i * W + j);
     if (in.xi > 0) {
+        in.pm = __ldg(a.pmask + (size_t)i * W + j);
         const unsigned valid = nb_valid(H, W, a.T, t, i, j);
-        load_far_neighbours(a.q, a.qhat, H, W, t, i, j, valid, in.nb);
         if (t >= 1 && (a.pred == 1 || (a.pred == 2 && a.modes[((size_t)t * a.nby + i / a.B) * a.nbx + j / a.B]))) {
             in.use_sl = 1;
             in.psl = __ldg(a.psl + (size_t)i * W + j);
         }
+        if (in.pm) {
+            load_far_neighbours(a.q, a.qhat, H, W, t, i, j, valid, in.nb);
+        } else if (!in.use_sl) {
+            const size_t sl = (size_t)H * W;
+            const int2 z = make_int2(0, 0);
+            in.nb[0] = (valid & 1u) ? __ldg(a.qhat + v - sl - W - 1) : z;
+            in.nb[1] = (valid & 2u) ? __ldg(a.qhat + v - sl - W) : z;
+            in.nb[2] = (valid & 4u) ? __ldg(a.qhat + v - sl - 1) : z;
+            in.nb[3] = (valid & 8u) ? __ldg(a.qhat + v - sl) : z;
+        }
     }
 }
+
+#define CPT_PRED_EVAL(a, b)                                                                       \
+    if ((pm >> bit) & 1u) r = min(r, min_alg2(xi, nb[a].x, nb[a].y, nb[b].x, nb[b].y, qv.x, qv.y)); \
+    ++bit;
+
+constexpr int kPublishEvery = 16;  // columns between progress publications
 
 __global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
     const unsigned FULL = 0xffffffffu;
@@ -329,19 +369,20 @@ __global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
         if (active) {
             int xi = cur.xi;
             const int2 qv = cur.qv;
-            if (xi > 0) {
+            if (xi > 0 && cur.pm) {
                 cur.nb[4] = upleft;
                 cur.nb[5] = up;
                 cur.nb[6] = left;
                 const int2* nb = cur.nb;
-                const unsigned valid = nb_valid(H, W, T, t, i, j);
-                CPT_PRED_FACES(CPT_FACE)
+                const unsigned pm = cur.pm;
+                int r = xi, bit = 0;
+                CPT_PRED_FACES(CPT_PRED_EVAL)
+                xi = r;
             }
             const int code = xi_code(xi);
-            int2 r = qv;
+            int2 rec = qv;
             unsigned sym = 0;
             if (code > 0) {
-                const int xiq = 1 << (code - 1);
                 int pu, pv;
                 if (cur.use_sl) {
                     pu = cur.psl.x;
@@ -350,17 +391,18 @@ __global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
                     pu = up.x + left.x + cur.nb[3].x - upleft.x - cur.nb[1].x - cur.nb[2].x + cur.nb[0].x;
                     pv = up.y + left.y + cur.nb[3].y - upleft.y - cur.nb[1].y - cur.nb[2].y + cur.nb[0].y;
                 }
-                unsigned su = quantize(qv.x, pu, xiq, r.x);
-                unsigned sv = quantize(qv.y, pv, xiq, r.y);
+                unsigned su = quantize_code(qv.x, pu, code, rec.x);
+                unsigned sv = quantize_code(qv.y, pv, code, rec.y);
                 sym = su | (sv << 16);
             }
             const size_t v = base + (size_t)i * W + j;
-            a.qhat[v] = r;
+            a.qhat[v] = rec;
             a.qxi[v] = (uint8_t)code;
             a.sym[v] = sym;
             if (a.xi_out) a.xi_out[v] = xi;
-            res = r;
-            if (lane == 31 && ((j & 7) == 7 || j == W - 1)) st_release(prog_me, (unsigned)(j + 1));
+            res = rec;
+            if (lane == 31 && ((j % kPublishEvery) == kPublishEvery - 1 || j == W - 1))
+                st_release(prog_me, (unsigned)(j + 1));
         } else {
             res = make_int2(0, 0);
         }
@@ -368,6 +410,7 @@ __global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
         cur = nxt;
     }
 }
+#undef CPT_PRED_EVAL
 
 #undef CPT_FACE
 

@@ -37,12 +37,14 @@ def _add_vortex(u, v, cx, cy, R, amp, sign, win=4.0):
 
 
 def vortex_sum(H=64, W=64, T=8, seed=1000, n_vortex=6, drift=0.5, noise=1e-3):
-    """Sum of Gaussian vortices (random centres in [8, H-8]x[8, W-8], radii
-    U[4,10], unit amplitude with random sign) whose centres drift `drift`
-    cells per step in +x, plus N(0, noise) per component."""
+    """Sum of Gaussian vortices (random centres in [8, H-8]x[8, W-8], or the
+    middle half of a smaller side, radii U[4,10], unit amplitude with random
+    sign) whose centres drift `drift` cells per step in +x, plus N(0, noise)
+    per component."""
     rng = np.random.default_rng(seed)
-    cx = rng.uniform(8, W - 8, n_vortex)
-    cy = rng.uniform(8, H - 8, n_vortex)
+    mx, my = min(8.0, W / 4.0), min(8.0, H / 4.0)
+    cx = rng.uniform(mx, W - mx, n_vortex)
+    cy = rng.uniform(my, H - my, n_vortex)
     R = rng.uniform(4, 10, n_vortex)
     s = rng.choice([-1.0, 1.0], n_vortex)
     out = np.empty((T, H, W, 2), np.float32)
