@@ -554,7 +554,10 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     st.lossless_vertices = N - n_qd / 2;
     st.unpredictable = n_ld - 2 * st.lossless_vertices;
     if (stats) *stats = st;
-    if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= eps)))
+    // The pointwise bound holds for eps >= half a fixed-point unit; below that
+    // every value is stored losslessly and the error is the rounding to 2^-k.
+    const double bound = std::max(eps, std::ldexp(0.5, -k));
+    if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= bound)))
         return fail(CPT_ERR_VERIFY, "reconstruction changed a face predicate or exceeded the bound");
     return CPT_OK;
 }
