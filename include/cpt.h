@@ -162,6 +162,29 @@ typedef struct {
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2,
                                     cpt_trajs** out, void* cuda_stream);
 
+/* Range reduction and fixed-point conversion (the first step of
+ * cpt_compress) without any device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory when
+ * they call it (a pre-reserved memory pool, an allocator that forbids foreign
+ * allocations, a context where cudaMalloc would synchronise the device).
+ *   uv         : device float32 [T][H][W][2], 16-byte aligned (read)
+ *   q          : device int32 [T][H][W][2], 16-byte aligned (written):
+ *                q = rint(x * 2^k)
+ *   scale_log2 : device int32 (written): k = 23 - e with max|x| < 2^e, 0 for
+ *                an all-zero field, INT32_MIN when a value is not finite (q is
+ *                then left untouched)
+ * Runs asynchronously on cuda_stream.  Its scratch is a 256 KiB array in
+ * device memory that every GPU loading the library holds until the process
+ * exits; inputs of more than 16384 * 16384 float values (2*H*W*T) are
+ * rejected with CPT_ERR_ARG.  Calls share that array: calls whose kernels
+ * overlap on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up the array's address; make it before capturing a
+ * stream into a CUDA graph.
+ * Errors: CPT_ERR_ARG (null or misaligned pointer, empty or oversized field),
+ * CPT_ERR_CUDA. */
+cpt_status cpt_fixed_point_noalloc(const float* uv, const cpt_dims* dims, int32_t* q, int32_t* scale_log2,
+                                   void* cuda_stream);
+
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);

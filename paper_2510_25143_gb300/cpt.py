@@ -81,6 +81,8 @@ def lib():
             L.cpt_error_string.argtypes = [C.c_int]
             L.cpt_last_error.restype = C.c_char_p
             L.cpt_version.restype = C.c_uint32
+            L.cpt_fixed_point_noalloc.restype = C.c_int
+            L.cpt_fixed_point_noalloc.argtypes = [C.c_void_p, P(Dims), C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -190,3 +192,17 @@ def extract_trajectories(uv, scale_log2=None, stream=None):
     L.cpt_free_trajs(out)
     del keep
     return ([faces[offs[a]:offs[a + 1]] for a in range(n)], [xyt[offs[a]:offs[a + 1]] for a in range(n)], bad)
+
+
+def fixed_point_noalloc(uv, q, k, stream=None):
+    """Allocation-free range reduction + fixed-point conversion on the device:
+    uv float32 [T][H][W][2], q int32 of the same shape and k an int32 tensor of
+    one element, all CUDA tensors supplied by the caller.  Returns the status
+    (asynchronous on `stream`, default the current torch stream)."""
+    import torch
+    assert uv.is_cuda and q.is_cuda and k.is_cuda and uv.dtype == torch.float32 and q.dtype == torch.int32
+    T, H, W, _ = uv.shape
+    if stream is None:
+        stream = torch.cuda.current_stream(uv.device).cuda_stream
+    dims = Dims(H, W, T, 1.0, 1.0, 1.0)
+    return lib().cpt_fixed_point_noalloc(uv.data_ptr(), C.byref(dims), q.data_ptr(), k.data_ptr(), stream)
