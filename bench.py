@@ -39,8 +39,13 @@ STAGE_BYTES = {
     "range_fixed": (12.0, "field"),     # two launches: read 8 B; read 8 B + write 8 B
     "face_masks": (10.0, "field"),      # read q 8 B, write mask 2 B
     "mop_sl": (24.0, "slice"),          # read qhat(t-1) 8 B, q(t) 8 B, write SL prediction 8 B
-    "incident_bounds": (32.0, "slice"), # q(t), q(t+1), qhat(t-1) 8 B each, masks 2x2 B, write 4 B
-    "wavefront": (49.0, "slice"),       # q, q(t+1), qhat(t-1), SL pred 8 B each, bound 4 B, write 13 B
+    # classification of the incident faces: read q(t-1), q(t), q(t+1) 8 B each and
+    # the masks of t and t-1 2 B each, write 8 B
+    "incident_bounds": (36.0, "field"),
+    # the encoder pipeline (MoP/SL tiles and the wavefront) over the whole
+    # field: read the classification 8 B, q(t) 8 B and qhat(t-1) 8 B, write
+    # qhat 8 B, bound code 1 B, symbols 4 B
+    "wavefront": (37.0, "field"),
     "verify": (18.0, "field"),          # read qhat 8 B, mask 2 B, uv 8 B
 }
 

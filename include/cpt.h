@@ -57,7 +57,8 @@ typedef enum { CPT_PRED_LORENZO = 0, CPT_PRED_SL = 1, CPT_PRED_MOP = 2 } cpt_pre
 /* Compression parameters.
  *   mode/eb  : eps = eb (ABS, data units) or eb * (max - min over u and v) (REL)
  *   pred     : predictor
- *   block    : MoP block side B (0 = 16); stride: MoP sampling stride n (0 = 2)
+ *   block    : MoP block side B (0 = 16; 4, 8, 16 or 32); stride: MoP sampling
+ *              stride n (0 = 2)
  *   cuda_stream : cudaStream_t to run on (NULL = the legacy default stream)
  *   verify   : nonzero = recompute every face predicate on the reconstruction
  *              and check the pointwise bound before returning (Thm. 1/2)   */

@@ -32,14 +32,19 @@ constexpr int kRadius = 32768;  // quantisation radius: |c| < kRadius is predict
 //                7..9 at t  : (i,j+1) (i+1,j) (i+1,j+1)   (raster successors)
 //               10..13 at t+1: (i,j) (i,j+1) (i+1,j) (i+1,j+1)
 // Each of the (at most) 36 faces containing v is named by the pair of its two
-// other vertices: CPT_FREE_FACES lists the 22 faces without a raster
-// predecessor, CPT_PRED_FACES the 14 that use at least one (those depend on
-// reconstructions of the same slice and sit on the wavefront's chain).
-#define CPT_FREE_FACES(F)                                                                           \
-    F(7, 9) F(8, 9) F(7, 13) F(0, 1) F(11, 13) F(2, 8) F(8, 13) F(0, 2) F(12, 13) F(1, 7) F(7, 11) \
-    F(2, 3) F(10, 11) F(3, 7) F(8, 12) F(1, 3) F(10, 12) F(3, 8) F(9, 13) F(0, 3) F(10, 13) F(3, 9)
-#define CPT_PRED_FACES(F)                                                                          \
-    F(6, 8) F(4, 5) F(5, 7) F(4, 6) F(6, 12) F(0, 5) F(5, 11) F(0, 6) F(6, 10) F(2, 6) F(5, 10)  \
+// other vertices.  When v is processed, neighbours 7..13 still hold their
+// original values, 0..3 (slice t-1) and 4..6 (raster predecessors) hold
+// reconstructions that differ from the originals by at most the quantiser
+// half width.  CPT_CERT_FACES lists the 12 faces through original values
+// only; CPT_UNC_FACES the 24 others: 10 through slice t-1 without a
+// predecessor, then 14 through a predecessor (those sit on the wavefront's
+// dependency chain).
+#define CPT_CERT_FACES(F)                                                                          \
+    F(7, 9) F(8, 9) F(7, 13) F(11, 13) F(8, 13) F(12, 13) F(7, 11) F(10, 11) F(8, 12) F(10, 12)   \
+    F(9, 13) F(10, 13)
+#define CPT_UNC_FACES(F)                                                                           \
+    F(0, 1) F(2, 8) F(0, 2) F(1, 7) F(2, 3) F(3, 7) F(1, 3) F(3, 8) F(0, 3) F(3, 9)                \
+    F(6, 8) F(4, 5) F(5, 7) F(4, 6) F(6, 12) F(0, 5) F(5, 11) F(0, 6) F(6, 10) F(2, 6) F(5, 10)   \
     F(1, 5) F(4, 10) F(0, 4)
 
 __host__ __device__ constexpr int nb_dt(int n) { return n < 4 ? -1 : (n < 10 ? 0 : 1); }
@@ -153,28 +158,39 @@ __device__ __forceinline__ int min_alg2(int cur, int u0, int v0, int u1, int v1,
     return max(m, fl);
 }
 
-// A face through raster predecessors, evaluated before those predecessors are
-// reconstructed: vertex 2 = the bounded vertex (its own value is final at
-// that time), neighbours 0 and 1 hold their current values, a predecessor's
-// original value standing in for a reconstruction within +-E of it (E bounds
-// every |qhat - q|).  Returns true when, for any such reconstructions, the
-// face keeps M != 0 and a same-sign clause holding with bound >= xi, so its
-// Alg. 2 value cannot lower a bound that starts at xi.
-__device__ __forceinline__ bool pred_face_inert(int2 a0, int2 a1, int2 c, bool p0, bool p1, int E, int xi) {
+// A face through vertices whose reconstructions are not known yet (slice t-1
+// and raster predecessors), classified from original values: vertex 2 = the
+// bounded vertex (its value is final when it is processed), neighbours 0 and 1
+// hold their current values, an uncertain neighbour's original value standing
+// in for a reconstruction within +-E of it (E bounds every |qhat - q|).
+// Returns 0 when, for any such reconstructions, M != 0 and a same-sign clause
+// holds with bound >= xi (the face cannot lower a bound that starts at xi);
+// 1 when the same-sign clause is guaranteed but M = 0 cannot be excluded (only
+// M needs evaluating once the reconstructions are known: M = 0 makes Alg. 2
+// return 0); 2 otherwise (the full Alg. 2 is needed).
+__device__ __forceinline__ int unc_face_class(int2 a0, int2 a1, int2 c, bool p0, bool p1, int E, int xi) {
     const int m0 = p0 ? E : 0, m1 = p1 ? E : 0;
     const bool su = (c.x > 0 && a0.x > m0 && a1.x > m1) || (c.x < 0 && a0.x < -m0 && a1.x < -m1);
     const bool sv = (c.y > 0 && a0.y > m0 && a1.y > m1) || (c.y < 0 && a0.y < -m0 && a1.y < -m1);
     int fl = -1;
     if (su) fl = abs(c.x) - 1;
     if (sv) fl = max(fl, abs(c.y) - 1);
-    if (fl < xi) return false;
-    const long long A = (long long)a1.x - a0.x, Bv = (long long)c.y - a0.y;
-    const long long Cv = (long long)a1.y - a0.y, Du = (long long)c.x - a0.x;
-    long long M = A * Bv - Cv * Du;
+    if (fl < xi) return 2;
+    // With a0' = a0 + d0, a1' = a1 + d1 (|d|_inf <= E, zero for exact values):
+    // M' = M + det(d0, a1 - c) + det(d1, c - a0) + det(d0, d1).
+    long long M = (long long)(a1.x - a0.x) * (c.y - a0.y) - (long long)(a1.y - a0.y) * (c.x - a0.x);
     M = M < 0 ? -M : M;
-    const long long e = E, k0 = p0 ? 1 : 0, k01 = (p0 ? 1 : 0) + (p1 ? 1 : 0);
-    const long long D = e * (k0 * (llabs(A) + llabs(Cv)) + k01 * (llabs(Bv) + llabs(Du))) + 2 * k0 * k01 * e * e;
-    return M > D;
+    const long long e = E;
+    long long D = 0;
+    if (p0) D += e * ((long long)abs(a1.x - c.x) + abs(a1.y - c.y));
+    if (p1) D += e * ((long long)abs(c.x - a0.x) + abs(c.y - a0.y));
+    if (p0 && p1) D += 2 * e * e;
+    return M > D ? 0 : 1;
+}
+
+// M of Alg. 2 (twice the signed area of the triangle of values) is zero.
+__device__ __forceinline__ bool m_zero(int2 a0, int2 a1, int2 c) {
+    return (long long)(a1.x - a0.x) * (c.y - a0.y) == (long long)(a1.y - a0.y) * (c.x - a0.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,9 +283,24 @@ __device__ __forceinline__ Bil bil_weights(double x, double y, int H, int W) {
     return b;
 }
 
-__device__ __forceinline__ double bil_sample(const Bil& b, const int2* P, int W, int c) {
-    const int2 a00 = P[(size_t)b.y0 * W + b.x0], a10 = P[(size_t)b.y0 * W + b.x1];
-    const int2 a01 = P[(size_t)b.y1 * W + b.x0], a11 = P[(size_t)b.y1 * W + b.x1];
+// Samplers of the reconstructed slice t-1: GlobalSlice reads through L2 (the
+// slice is written by other thread blocks of a running kernel), SmemSlice a
+// staged window of it.  at(i, j) takes global row/column indices.
+struct GlobalSlice {
+    const int2* P;
+    int W;
+    __device__ __forceinline__ int2 at(int i, int j) const { return __ldcg(P + (size_t)i * W + j); }
+};
+struct SmemSlice {
+    const int2* S;  // window origin (row i_org, column j_org), pitch columns
+    int i_org, j_org, pitch;
+    __device__ __forceinline__ int2 at(int i, int j) const { return S[(i - i_org) * pitch + (j - j_org)]; }
+};
+
+template <class Slice>
+__device__ __forceinline__ double bil_sample(const Bil& b, const Slice& P, int c) {
+    const int2 a00 = P.at(b.y0, b.x0), a10 = P.at(b.y0, b.x1);
+    const int2 a01 = P.at(b.y1, b.x0), a11 = P.at(b.y1, b.x1);
     double f00 = (double)(c ? a00.y : a00.x), f10 = (double)(c ? a10.y : a10.x);
     double f01 = (double)(c ? a01.y : a01.x), f11 = (double)(c ? a11.y : a11.x);
     double p = __dadd_rn(__dmul_rn(b.w00, f00), __dmul_rn(b.w10, f10));
@@ -279,9 +310,10 @@ __device__ __forceinline__ double bil_sample(const Bil& b, const int2* P, int W,
 }
 
 // returns 0 for RK2, N for N substeps
-__device__ __forceinline__ int sl_predict(const int2* P, int H, int W, int i, int j, double cfl_x,
+template <class Slice>
+__device__ __forceinline__ int sl_predict(const Slice& P, int H, int W, int i, int j, double cfl_x,
                                           double cfl_y, int& pu, int& pv) {
-    const int2 g = P[(size_t)i * W + j];
+    const int2 g = P.at(i, j);
     double du = __dmul_rn((double)g.x, cfl_x);
     double dv = __dmul_rn((double)g.y, cfl_y);
     double dinf = fabs(du) > fabs(dv) ? fabs(du) : fabs(dv);
@@ -292,8 +324,8 @@ __device__ __forceinline__ int sl_predict(const int2* P, int H, int W, int i, in
         double xh = clamp_pos(__dsub_rn((double)j, __dmul_rn(0.5, du)), xmax);
         double yh = clamp_pos(__dsub_rn((double)i, __dmul_rn(0.5, dv)), ymax);
         Bil b = bil_weights(xh, yh, H, W);
-        double uh = bil_sample(b, P, W, 0);
-        double vh = bil_sample(b, P, W, 1);
+        double uh = bil_sample(b, P, 0);
+        double vh = bil_sample(b, P, 1);
         xs = clamp_pos(__dsub_rn((double)j, __dmul_rn(uh, cfl_x)), xmax);
         ys = clamp_pos(__dsub_rn((double)i, __dmul_rn(vh, cfl_y)), ymax);
         mode = 0;
@@ -305,18 +337,31 @@ __device__ __forceinline__ int sl_predict(const int2* P, int H, int W, int i, in
         ys = (double)i;
         for (int s = 0; s < N; ++s) {
             Bil b = bil_weights(xs, ys, H, W);
-            double us = bil_sample(b, P, W, 0);
-            double vs = bil_sample(b, P, W, 1);
+            double us = bil_sample(b, P, 0);
+            double vs = bil_sample(b, P, 1);
             xs = clamp_pos(__dsub_rn(xs, __dmul_rn(us, sx)), xmax);
             ys = clamp_pos(__dsub_rn(ys, __dmul_rn(vs, sy)), ymax);
         }
         mode = N;
     }
     Bil b = bil_weights(xs, ys, H, W);
-    pu = (int)floor(__dadd_rn(bil_sample(b, P, W, 0), 0.5));
-    pv = (int)floor(__dadd_rn(bil_sample(b, P, W, 1), 0.5));
+    pu = (int)floor(__dadd_rn(bil_sample(b, P, 0), 0.5));
+    pv = (int)floor(__dadd_rn(bil_sample(b, P, 1), 0.5));
     return mode;
 }
+
+// Asynchronous global -> shared copies (zero-filled when !valid; the source is
+// then not read).  Only for data that no running kernel writes: they may be
+// served from L1.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // %globaltimer in nanoseconds (for bounded waits)
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/cpt.h"
+#include "cpt.h"
 #include "cpt_internal.h"
 
 namespace cpt {
@@ -281,7 +281,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
     const double dx = dims->dx > 0 ? dims->dx : 1.0, dy = dims->dy > 0 ? dims->dy : 1.0;
     const double dt = dims->dt > 0 ? dims->dt : 1.0;
-    const size_t N = (size_t)H * W * T, NV = 2 * N, SL = (size_t)H * W;
+    const size_t N = (size_t)H * W * T, NV = 2 * N;
     cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -349,41 +349,47 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     st.launches[1]++;
     tm.end();
 
-    // ---- stages 2-4: per slice MoP / SL, incident-face bounds, wavefront
+    // ---- stage 4: the encoder pipeline (MoP / SL, incident-face bounds, wavefront)
     const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
-    const int nstrips = wave_strips(H);
+    const int nstrips = (H + 31) / 32, nchunks = (W + 31) / 32;
+    if (prm->pred == CPT_PRED_MOP && (32 % B != 0 || B < 4))
+        return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
+    const bool want_sl = prm->pred != CPT_PRED_LORENZO && T > 1 && eps_int > 0;
     uint8_t *d_qxi, *d_modes;
     uint32_t* d_sym;
-    int *d_xipart, *d_status, *d_xiout = nullptr;
-    int2* d_psl;
-    uint16_t* d_pmask;
-    unsigned *d_prog, *d_ticket;
+    int *d_status, *d_xiout = nullptr;
+    int2 *d_psl, *d_cls;
+    unsigned* d_clsm;
+    unsigned *d_prog, *d_prep, *d_ticket;
     CPT_CUDA(ar.alloc(&d_qxi, N));
     CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
     CPT_CUDA(ar.alloc(&d_sym, N));
-    CPT_CUDA(ar.alloc(&d_xipart, SL));
-    CPT_CUDA(ar.alloc(&d_psl, SL));
-    CPT_CUDA(ar.alloc(&d_pmask, SL));
+    CPT_CUDA(ar.alloc(&d_cls, N));
+    CPT_CUDA(ar.alloc(&d_clsm, N));
+    CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
     CPT_CUDA(ar.alloc(&d_status, 1));
     CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
-    CPT_CUDA(ar.alloc(&d_ticket, T));
+    CPT_CUDA(ar.alloc(&d_prep, (size_t)T * nstrips * nchunks));
+    CPT_CUDA(ar.alloc(&d_ticket, 1));
     if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
     CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
     CPT_CUDA(cudaMemsetAsync(d_prog, 0, sizeof(unsigned) * T * nstrips, s));
-    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned) * T, s));
+    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * T * nstrips * nchunks, s));
+    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
     SliceArgs a;
     a.q = reinterpret_cast<const int2*>(d_q);
     a.qhat = reinterpret_cast<int2*>(d_qhat);
     a.mask = d_mask;
-    a.xi_part = d_xipart;
-    a.pmask = d_pmask;
+    a.cls = d_cls;
+    a.cls_m = d_clsm;
     a.psl = d_psl;
     a.modes = d_modes;
     a.qxi = d_qxi;
     a.sym = d_sym;
     a.xi_out = d_xiout;
     a.progress = d_prog;
+    a.prep_done = d_prep;
     a.ticket = d_ticket;
     a.status = d_status;
     a.counters = d_cnt64 + 1;
@@ -391,28 +397,28 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     a.eps_int = eps_int;
     a.pred = (int)prm->pred;
     a.B = B; a.n = nstride; a.nby = nby; a.nbx = nbx;
+    a.nchunks = nchunks;
     a.cfl_x = std::ldexp(dt / dx, -k);
     a.cfl_y = std::ldexp(dt / dy, -k);
-    a.timeout_ns = 2000000000ll;
-    for (int t = 0; t < T; ++t) {
-        a.t = t;
-        if (t >= 1 && eps_int >= 1 && prm->pred != CPT_PRED_LORENZO) {
-            tm.begin(2);
-            if (prm->pred == CPT_PRED_MOP) launch_mop(a, s);
-            else launch_sl(a, s);
-            st.launches[2]++;
-            tm.end();
-        }
-        tm.begin(3);
-        launch_pre(a, s);
-        st.launches[3]++;
-        tm.end();
-        tm.begin(4);
-        launch_wave(a, s);
-        st.launches[4]++;
-        tm.end();
+    // Reach of the semi-Lagrangian back-trace into slice t-1: no
+    // reconstruction exceeds max|q| + E in magnitude, every displacement is
+    // at most that times CFL, the bilinear stencil adds one cell, and one
+    // more cell covers rounding of the positions.
+    a.R = 0;
+    if (want_sl) {
+        const double qmax = std::ceil((double)am * std::ldexp(1.0, k)) + (eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)eps_int))) : 0.0);
+        const double reach = std::ceil(qmax * std::max(a.cfl_x, a.cfl_y)) + 2.0;
+        a.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
     }
-    CPT_CUDA(cudaGetLastError());
+    a.timeout_ns = 2000000000ll;
+    tm.begin(3);
+    launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, s);
+    st.launches[3]++;
+    tm.end();
+    tm.begin(4);
+    CPT_CUDA(launch_encode_pipeline(a, nsm, s));
+    st.launches[4]++;
+    tm.end();
 
     // ---- stage 5: compaction + entropy coding
     tm.begin(5);
@@ -464,7 +470,10 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         CPT_CUDA(cudaStreamSynchronize(s));
         std::vector<uint8_t> packed(mode_bytes, 0);
         for (size_t x = 0; x < nblk; ++x)
-            if (modes_h[x]) packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+            if (modes_h[x]) {
+                packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+                ++st.sl_blocks;
+            }
         bs.raw(packed.data(), packed.size());
     }
     cpt_status rc = encode_stream<uint8_t>(d_qxi, N, 33, ar, s, bs);
@@ -529,7 +538,6 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
     }
     st.crossed_faces = cnt_h[0];
-    st.sl_blocks = cnt_h[3];
     st.blocks = prm->pred == CPT_PRED_MOP ? (uint64_t)T * nby * nbx : 0;
     st.n_ld = n_ld;
     st.n_qd = n_qd;

@@ -19,27 +19,31 @@ struct VerifyOut {
     double sq_err;
 };
 
-// Per-slice arguments of the encoder kernels.
+// Arguments of the encoder pipeline (one persistent launch over all slices).
 struct SliceArgs {
     const int2* q;          // original fixed point [T][H][W]
-    int2* qhat;             // reconstruction [T][H][W] (slices < t final)
+    int2* qhat;             // reconstruction [T][H][W]
     const uint16_t* mask;   // crossed-face masks [T][H][W]
-    int* xi_part;           // [H][W] bound over the faces without raster predecessors
-    uint16_t* pmask;        // [H][W] predecessor faces that may still lower the bound
-    int2* psl;              // [H][W] semi-Lagrangian predictions of slice t
+    const int2* cls;        // [T][H][W] (bound over certain faces, faces needing the full Alg. 2)
+    const unsigned* cls_m;  // [T][H][W] faces needing only the M = 0 check
+    int2* psl;              // [T][H][W] semi-Lagrangian predictions (where needed)
     uint8_t* modes;         // [T][nby][nbx] block modes (1 = SL)
     uint8_t* qxi;           // [T][H][W] bound codes
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
-    unsigned* progress;     // [T][nstrips] wavefront progress (columns published)
-    unsigned* ticket;       // [T] strip tickets
+    unsigned* progress;     // [T][nstrips] wavefront columns published per strip
+    unsigned* prep_done;    // [T][nstrips][nchunks] prep tiles finished
+    unsigned* ticket;       // work-item counter
     int* status;            // device status word (0 = ok)
-    unsigned long long* counters;  // [4]: substep vertices, substeps, sl blocks, spare
-    int H, W, T, t;
+    unsigned long long* counters;  // [4]: substep vertices, substeps, SL blocks, spare
+    int H, W, T;
     int eps_int;
     int pred;               // 0 3DL, 1 SL, 2 MoP
-    int B, n;               // MoP block side and sampling stride
+    int B, n;               // MoP block side (divides 32) and sampling stride
     int nby, nbx;
+    int nchunks;            // ceil(W / 32)
+    int prep_groups;        // prep items per strip (round-robin groups of its tiles)
+    int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
     long long timeout_ns;
 };
@@ -53,11 +57,10 @@ void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, i
                    double inv_scale, VerifyOut* out, cudaStream_t s);
 
 // k_encode.cu
-void launch_sl(const SliceArgs& a, cudaStream_t s);
-void launch_mop(const SliceArgs& a, cudaStream_t s);
-void launch_pre(const SliceArgs& a, cudaStream_t s);
-void launch_wave(const SliceArgs& a, cudaStream_t s);
-int wave_strips(int H);
+void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
+                     unsigned* out_m, cudaStream_t s);
+cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s);
+size_t encode_smem_bytes();
 
 // k_entropy.cu
 struct EntropyBufs;

@@ -1,21 +1,40 @@
-// Encoder kernels, launched once per slice t in raster order of slices
-// (Alg. 3, loop over t):
-//   sl_kernel    semi-Lagrangian predictions of slice t (Sec. VI-A)
-//   mop_kernel   block-wise predictor choice of slice t (Sec. VI-B), which
-//                also writes the SL predictions
-//   pre_kernel   per vertex: membership of an incident face in C and the
-//                Alg. 2 bound over the 22 incident faces that contain no
-//                raster predecessor of the same slice (Alg. 4, first part)
-//   wave_kernel  the dependency-carrying part: the 14 faces through raster
-//                predecessors, xi quantisation, prediction and residual
-//                quantisation with immediate write-back (Sec. V-A), run as a
-//                warp-systolic anti-diagonal sweep that reproduces raster order.
+// Encoder kernels for the raster loop of Alg. 3.
+//
+// classify_kernel (fully parallel over every vertex of every slice) settles
+// all of Alg. 4 that does not depend on reconstructions: whether an incident
+// face is in C (the vertex is then lossless), the Alg. 2 bound over the 12
+// faces whose other vertices still hold original values when the vertex is
+// processed, and which of the 24 other faces (through slice t-1 or through a
+// raster predecessor, whose reconstructions lie within +-E of the originals)
+// could still lower that bound.
+//
+// encode_pipeline_kernel (one persistent launch over all slices) does the
+// rest, pipelining consecutive slices.  Work items, taken by warps from one
+// ticket counter in this order:
+//   for t in 0..T-1, for strip s (32 rows) in 0..nstrips-1:
+//       prep(t, s, g) for g in 0..PG-1 (SL and MoP only), then wave(t, s)
+// prep(t, s, g)  the 32 x 32 tiles c = g, g+PG, ... of strip s of slice t, in
+//                column order: semi-Lagrangian predictions (Sec. VI-A) and
+//                MoP block modes (Sec. VI-B); each needs slice t-1
+//                reconstructed around the tile (waits on wave(t-1, .)).
+// wave(t, s)     rows 32s..32s+31 of slice t: the flagged faces with the actual
+//                reconstructions, xi quantisation, prediction and residual
+//                quantisation with immediate write-back (Sec. V-A).  Lane l
+//                handles row 32s+l and, at step k, column k-l; the
+//                reconstruction of (i-1, j) arrives from lane l-1 by shuffle,
+//                the row above the strip from wave(t, s-1) through global memory
+//                (release/acquire progress words).
+// Every item waits only for items with smaller tickets, which were taken by
+// running warps, so the pipeline cannot deadlock; each wait is bounded in
+// time and sets the status word when it expires.
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
 
 namespace cpt {
 
 constexpr int kStatusTimeout = -6;
+constexpr int kPublishEvery = 16;  // columns between progress publications of a strip
+constexpr int kHalo = 34;          // row stride of the staged slice t-1 halo tile
 
 __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, int j) {
     unsigned tm = t > 0, tp = t + 1 < T, im = i > 0, ip = i + 1 < H, jm = j > 0, jp = j + 1 < W;
@@ -24,111 +43,153 @@ __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, 
            ((tp & ip) << 12) | ((tp & ip & jp) << 13);
 }
 
-// Loads the neighbours that do not belong to the current slice's raster
-// predecessors: 0..3 from the reconstruction of slice t-1, 7..13 from the
-// original field (slice t successors and slice t+1).  Invalid ones read 0.
-__device__ __forceinline__ void load_far_neighbours(const int2* __restrict__ q, const int2* __restrict__ qhat,
-                                                    int H, int W, int t, int i, int j, unsigned valid,
-                                                    int2 nb[14]) {
-    const size_t sl = (size_t)H * W;
-    const size_t v = ((size_t)t * H + i) * W + j;
-    const int2 z = make_int2(0, 0);
-    nb[0] = (valid & (1u << 0)) ? __ldg(qhat + v - sl - W - 1) : z;
-    nb[1] = (valid & (1u << 1)) ? __ldg(qhat + v - sl - W) : z;
-    nb[2] = (valid & (1u << 2)) ? __ldg(qhat + v - sl - 1) : z;
-    nb[3] = (valid & (1u << 3)) ? __ldg(qhat + v - sl) : z;
-    nb[7] = (valid & (1u << 7)) ? __ldg(q + v + 1) : z;
-    nb[8] = (valid & (1u << 8)) ? __ldg(q + v + W) : z;
-    nb[9] = (valid & (1u << 9)) ? __ldg(q + v + W + 1) : z;
-    nb[10] = (valid & (1u << 10)) ? __ldg(q + v + sl) : z;
-    nb[11] = (valid & (1u << 11)) ? __ldg(q + v + sl + 1) : z;
-    nb[12] = (valid & (1u << 12)) ? __ldg(q + v + sl + W) : z;
-    nb[13] = (valid & (1u << 13)) ? __ldg(q + v + sl + W + 1) : z;
+__host__ __device__ constexpr bool is_uncertain(int n) { return n <= 6; }
+
+// The CPT_UNC_FACES pairs as bytes (first | second << 4), face f in byte f % 8
+// of word f / 8, for loops over a face mask.
+constexpr unsigned long long kUncPairs0 = 0x8331733271208210ull;
+constexpr unsigned long long kUncPairs1 = 0x50C6647554869330ull;
+constexpr unsigned long long kUncPairs2 = 0x40A451A562A660B5ull;
+__device__ __forceinline__ unsigned unc_pair(int f) {
+    const unsigned long long w = f < 8 ? kUncPairs0 : (f < 16 ? kUncPairs1 : kUncPairs2);
+    return (unsigned)(w >> (8 * (f & 7))) & 0xFFu;
 }
 
 #define CPT_FACE(a, b)                                                                  \
     if (xi > 0 && ((valid >> (a)) & (valid >> (b)) & 1u))                               \
         xi = min_alg2(xi, nb[a].x, nb[a].y, nb[b].x, nb[b].y, qv.x, qv.y);
 
-// ---------------------------------------------------------------------------
-// pre_kernel: C membership of the 36 incident faces, the bound over the 22
-// predecessor-free faces, and the set of the 14 predecessor faces that may
-// still lower that bound once the predecessors are reconstructed.
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr bool is_pred(int n) { return n >= 4 && n <= 6; }
-
-#define CPT_PRED_MARK(a, b)                                                                       \
-    if (((valid >> (a)) & (valid >> (b)) & 1u) &&                                                 \
-        !pred_face_inert(nb[a], nb[b], qv, is_pred(a), is_pred(b), E, xi))                        \
-        pm |= 1u << bit;                                                                          \
+#define CPT_UNC_MARK(a, b)                                                                   \
+    if ((valid >> (a)) & (valid >> (b)) & 1u) {                                              \
+        const int cls_ = unc_face_class(nb[a], nb[b], qv, is_uncertain(a), is_uncertain(b), E, xi); \
+        if (cls_ == 2) um_full |= 1u << bit;                                                 \
+        else if (cls_ == 1) um_m |= 1u << bit;                                               \
+    }                                                                                        \
     ++bit;
 
-__global__ void __launch_bounds__(256) pre_kernel(SliceArgs a) {
+
+
+// ---------------------------------------------------------------------------
+// classify_kernel: one thread per vertex; out[v] = (bound over the certain
+// faces, 0 = lossless; uncertain faces that need the full Alg. 2), out_m[v] =
+// uncertain faces of which only M = 0 must be checked
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
+                                                       int H, int W, int T, int eps_int, int2* __restrict__ out,
+                                                       unsigned* __restrict__ out_m) {
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
     const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int H = a.H, W = a.W, T = a.T, t = a.t;
+    const int t = blockIdx.z;
     if (i >= H || j >= W) return;
+    const size_t sl = (size_t)H * W;
+    const size_t v = ((size_t)t * H + i) * W + j;
     bool crossed = false;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-        int ot = t + kOwners[o].dt, oi = i + kOwners[o].di, oj = j + kOwners[o].dj;
+        const int ot = t + kOwners[o].dt, oi = i + kOwners[o].di, oj = j + kOwners[o].dj;
         if (ot >= 0 && oi >= 0 && oj >= 0)
-            crossed |= (__ldg(a.mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
+            crossed |= (__ldg(mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
     }
     int xi = 0;
-    unsigned pm = 0;
-    if (!crossed && a.eps_int > 0) {
-        xi = a.eps_int;
+    unsigned um_full = 0, um_m = 0;
+    if (!crossed && eps_int > 0) {
+        xi = eps_int;
         const unsigned valid = nb_valid(H, W, T, t, i, j);
+        const int2 z = make_int2(0, 0);
         int2 nb[14];
-        load_far_neighbours(a.q, a.qhat, H, W, t, i, j, valid, nb);
-        const size_t v = ((size_t)t * H + i) * W + j;
-        const int2 qv = __ldg(a.q + v);
-        CPT_FREE_FACES(CPT_FACE)
+        nb[0] = (valid & (1u << 0)) ? __ldg(q + v - sl - W - 1) : z;
+        nb[1] = (valid & (1u << 1)) ? __ldg(q + v - sl - W) : z;
+        nb[2] = (valid & (1u << 2)) ? __ldg(q + v - sl - 1) : z;
+        nb[3] = (valid & (1u << 3)) ? __ldg(q + v - sl) : z;
+        nb[4] = (valid & (1u << 4)) ? __ldg(q + v - W - 1) : z;
+        nb[5] = (valid & (1u << 5)) ? __ldg(q + v - W) : z;
+        nb[6] = (valid & (1u << 6)) ? __ldg(q + v - 1) : z;
+        nb[7] = (valid & (1u << 7)) ? __ldg(q + v + 1) : z;
+        nb[8] = (valid & (1u << 8)) ? __ldg(q + v + W) : z;
+        nb[9] = (valid & (1u << 9)) ? __ldg(q + v + W + 1) : z;
+        nb[10] = (valid & (1u << 10)) ? __ldg(q + v + sl) : z;
+        nb[11] = (valid & (1u << 11)) ? __ldg(q + v + sl + 1) : z;
+        nb[12] = (valid & (1u << 12)) ? __ldg(q + v + sl + W) : z;
+        nb[13] = (valid & (1u << 13)) ? __ldg(q + v + sl + W + 1) : z;
+        const int2 qv = __ldg(q + v);
+        CPT_CERT_FACES(CPT_FACE)
         if (xi > 0) {
-            const int2 z = make_int2(0, 0);
-            nb[4] = (valid & (1u << 4)) ? __ldg(a.q + v - W - 1) : z;
-            nb[5] = (valid & (1u << 5)) ? __ldg(a.q + v - W) : z;
-            nb[6] = (valid & (1u << 6)) ? __ldg(a.q + v - 1) : z;
-            const int E = 1 << (31 - __clz(a.eps_int));
+            const int E = 1 << (31 - __clz(eps_int));
             int bit = 0;
-            CPT_PRED_FACES(CPT_PRED_MARK)
+            CPT_UNC_FACES(CPT_UNC_MARK)
         }
     }
-    a.xi_part[(size_t)i * W + j] = xi;
-    a.pmask[(size_t)i * W + j] = (uint16_t)pm;
-}
-#undef CPT_PRED_MARK
-
-// ---------------------------------------------------------------------------
-// sl_kernel: semi-Lagrangian predictions of every vertex of slice t >= 1.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) sl_kernel(SliceArgs a) {
-    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int H = a.H, W = a.W;
-    unsigned sub = 0, steps = 0;
-    if (i < H && j < W) {
-        const int2* P = a.qhat + (size_t)(a.t - 1) * H * W;
-        int pu, pv;
-        int md = sl_predict(P, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-        a.psl[(size_t)i * W + j] = make_int2(pu, pv);
-        sub = md > 0;
-        steps = md;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sub += __shfl_xor_sync(0xffffffffu, sub, o);
-        steps += __shfl_xor_sync(0xffffffffu, steps, o);
-    }
-    if ((threadIdx.x & 31) == 0 && sub) {
-        atomicAdd(a.counters + 0, (unsigned long long)sub);
-        atomicAdd(a.counters + 1, (unsigned long long)steps);
-    }
+    out[v] = make_int2(xi, (int)um_full);
+    out_m[v] = um_m;
 }
 
 // ---------------------------------------------------------------------------
-// mop_kernel: one CTA per B x B block of slice t >= 1 (Sec. VI-B).
+// waits (lane 0 polls; the result is broadcast to the warp)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned warp_wait_geq(const SliceArgs& a, const unsigned* flag, unsigned target) {
+    unsigned seen = 0;
+    if (threadIdx.x == 0) {
+        seen = ld_acquire(flag);
+        if (seen < target) {
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                __nanosleep(64);
+                seen = ld_acquire(flag);
+                if (seen >= target) break;
+                if (*(volatile int*)a.status != 0) { seen = 0; break; }
+                if ((long long)(global_ns() - t0) > a.timeout_ns) {
+                    atomicCAS(a.status, 0, kStatusTimeout);
+                    seen = 0;
+                    break;
+                }
+            }
+        }
+    }
+    seen = __shfl_sync(0xffffffffu, seen, 0);
+    __syncwarp();
+    return seen;  // 0 = gave up (target is always >= 1)
+}
+
+// Publishes that everything this warp wrote so far is visible.
+__device__ __forceinline__ void warp_publish(unsigned* flag, unsigned value) {
+    __threadfence();
+    __syncwarp();
+    if (threadIdx.x == 0) st_release(flag, value);
+}
+
+// ---------------------------------------------------------------------------
+// shared memory of one worker warp (one warp per CTA)
+// ---------------------------------------------------------------------------
+struct ChunkBuf {
+    int2 cls[32][32];       // (bound over certain faces, faces needing the full Alg. 2)
+    unsigned cm[32][32];    // faces needing only the M = 0 check
+    int2 qv[33][kHalo];     // q(t): rows/cols 0..32 of the chunk
+    int2 qn[33][kHalo];     // q(t+1): rows/cols 0..32 of the chunk
+    int2 psl[32][32];
+    int2 qp[33][kHalo];     // reconstruction of slice t-1, rows/cols -1..31 of the chunk
+    uint8_t modes[64];      // MoP modes of the blocks covering the chunk
+};
+constexpr int kStageR = 8;                 // largest SL reach served from the staged window
+constexpr int kPP = 34 + 2 * kStageR;      // pitch of the staged slice t-1 window
+struct PrepSmem {
+    int2 qc[34][34];                       // q(t): rows i0-1..i0+32, columns j0-1..j0+32
+    int2 pp[kPP * kPP];                    // qhat(t-1): rows/cols -1-R..32+R around the tile
+    int2 psl[32][32];                      // SL predictions of the tile
+    unsigned smp[2][2048];                 // sampled symbols per mode (0xFFFFFFFF = none)
+    unsigned hist[256];
+    unsigned char modes[64];               // decisions of the tile's blocks
+};
+struct WarpSmem {
+    union {
+        ChunkBuf buf[2];
+        PrepSmem prep;
+    };
+    int2 border[64];          // ring of the row above the strip
+    int2 nbs[32][15];         // per-lane neighbour values for the face loops
+};
+
+// ---------------------------------------------------------------------------
+// prep(t, s, g): semi-Lagrangian predictions and MoP modes
 // ---------------------------------------------------------------------------
 // log2(x) in Q32 for x >= 1: integer part from the bit length, then one
 // fraction bit per squaring of the Q31 mantissa (binary logarithm by
@@ -147,252 +208,445 @@ __device__ __forceinline__ unsigned long long log2_q32(unsigned x) {
     return r;
 }
 
-// Score in Q32 bits per sample: H0 + 16 L/(n+L) + 1/(2 B^2), over the
-// symbols of the sampled sites (0 marks an overflow).
-__device__ long long block_score(const unsigned* smp, int nslots, int B, long long* red, int* cnt) {
-    const int tid = threadIdx.x;
-    if (tid == 0) { red[0] = 0; cnt[0] = 0; cnt[1] = 0; }
-    __syncthreads();
-    for (int k = tid; k < nslots; k += blockDim.x) {
+// Score of one block and mode in Q32 bits per sample (Eq. 10 plus the
+// overflow penalty and the metadata term): H0 + 16 L/(n+L) + 1/(2 B^2).
+// smp holds nslots entries: a symbol, 0 for an overflow, 0xFFFFFFFF unused.
+__device__ long long warp_block_score(const unsigned* smp, int nslots, int B, unsigned* hist) {
+    const int lane = threadIdx.x;
+    const unsigned lo = (unsigned)kRadius - 128u;
+    for (int k = lane; k < 256; k += 32) hist[k] = 0;
+    __syncwarp();
+    unsigned nv = 0, nf = 0;
+    unsigned long long acc = 0;
+    for (int k = lane; k < nslots; k += 32) {
         unsigned x = smp[k];
-        if (x == 0) { atomicAdd(cnt + 1, 1); continue; }
-        atomicAdd(cnt, 1);
-        int c = 0;
-        bool first = true;
-        for (int m = 0; m < nslots; ++m) {
-            if (smp[m] == x) {
-                ++c;
-                if (m < k) first = false;
+        if (x == 0xFFFFFFFFu) continue;
+        if (x == 0) { ++nf; continue; }
+        ++nv;
+        if (x - lo < 256u) {
+            atomicAdd(&hist[x - lo], 1u);
+        } else {
+            // symbol outside the window: count its multiplicity directly
+            unsigned c = 0;
+            bool first = true;
+            for (int m = 0; m < nslots; ++m) {
+                if (smp[m] == x) {
+                    ++c;
+                    if (m < k) first = false;
+                }
             }
+            if (first) acc += (unsigned long long)c * log2_q32(c);
         }
-        if (first) atomicAdd((unsigned long long*)red, (unsigned long long)((long long)c * (long long)log2_q32(c)));
     }
-    __syncthreads();
-    long long nv = cnt[0], nf = cnt[1];
+    __syncwarp();
+    for (int k = lane; k < 256; k += 32) {
+        unsigned h = hist[k];
+        if (h) acc += (unsigned long long)h * log2_q32(h);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
     long long h0 = 0;
-    if (nv > 0) h0 = ((long long)nv * (long long)log2_q32((unsigned)nv) - red[0]) / nv;
+    if (nv > 0) h0 = ((long long)nv * (long long)log2_q32(nv) - (long long)acc) / (long long)nv;
     long long pen = 0;
-    if (nv + nf > 0) pen = (long long)(((unsigned long long)(16 * nf) << 32) / (unsigned long long)(nv + nf));
+    if (nv + nf > 0) pen = (long long)(((unsigned long long)(16u * nf) << 32) / (unsigned long long)(nv + nf));
     long long meta = (long long)((1ull << 32) / (unsigned long long)(2 * B * B));
-    __syncthreads();
+    __syncwarp();
     return h0 + pen + meta;
 }
 
-__global__ void __launch_bounds__(1024) mop_kernel(SliceArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    const int B = a.B, n = a.n, H = a.H, W = a.W, t = a.t;
-    int2* cand = reinterpret_cast<int2*>(smem_raw);                       // (B+1)^2
-    unsigned* s3 = reinterpret_cast<unsigned*>(cand + (B + 1) * (B + 1));  // 2 B^2
-    unsigned* ss = s3 + 2 * B * B;                                         // 2 B^2
-    __shared__ long long red[1];
-    __shared__ int cnt[3];
-    const int tid = threadIdx.x, bi = tid / B, bj = tid % B;
-    const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
-    const int i = i0 + bi, j = j0 + bj;
-    const bool inb = i < H && j < W;
-    const size_t sl = (size_t)H * W;
-    const int2* P = a.qhat + (size_t)(t - 1) * sl;
-    const int2* Qt = a.q + (size_t)t * sl;
-    const int xiq = 1 << (31 - __clz(a.eps_int));
-    if (tid == 0) cnt[2] = 0;
-    for (int k = tid; k < (B + 1) * (B + 1); k += blockDim.x) {
-        int ii = i0 - 1 + k / (B + 1), jj = j0 - 1 + k % (B + 1);
-        cand[k] = (ii >= 0 && jj >= 0 && ii < H && jj < W) ? Qt[(size_t)ii * W + jj] : make_int2(0, 0);
-    }
-    int2 qv = make_int2(0, 0), p0 = qv, p1 = qv, p2 = qv, p3 = qv;
-    unsigned ssu = 0, ssv = 0, sub = 0, steps = 0;
-    if (inb) {
-        qv = Qt[(size_t)i * W + j];
-        int pu, pv;
-        int md = sl_predict(P, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-        a.psl[(size_t)i * W + j] = make_int2(pu, pv);
-        sub = md > 0;
-        steps = md;
-        int dummy;
-        ssu = quantize(qv.x, pu, xiq, dummy);
-        ssv = quantize(qv.y, pv, xiq, dummy);
-        if (i > 0 && j > 0) p0 = P[(size_t)(i - 1) * W + j - 1];
-        if (i > 0) p1 = P[(size_t)(i - 1) * W + j];
-        if (j > 0) p2 = P[(size_t)i * W + j - 1];
-        p3 = P[(size_t)i * W + j];
-    }
-    __syncthreads();
-    unsigned s3u = 0, s3v = 0;
-    for (int s = 0; s <= 2 * (B - 1); ++s) {
-        if (inb && bi + bj == s) {
-            const int2 up = cand[bi * (B + 1) + bj + 1], left = cand[(bi + 1) * (B + 1) + bj],
-                       ul = cand[bi * (B + 1) + bj];
-            int pu = up.x + left.x + p3.x - ul.x - p1.x - p2.x + p0.x;
-            int pv = up.y + left.y + p3.y - ul.y - p1.y - p2.y + p0.y;
-            int2 r;
-            s3u = quantize(qv.x, pu, xiq, r.x);
-            s3v = quantize(qv.y, pv, xiq, r.y);
-            cand[(bi + 1) * (B + 1) + bj + 1] = r;
+// MoP decisions of the blocks inside the tile (B divides 32), from the staged
+// window.  Lanes are grouped by block: lane l handles row l % B of block l / B
+// of a row of blocks; the 3DL micro-encoding runs as an anti-diagonal sweep
+// inside each block with the original slice t outside the block
+// (context-preserving candidate buffer).  The SL symbols come from psl.
+__device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps, int Rw) {
+    const int lane = threadIdx.x, B = a.B, n = a.n, H = a.H, W = a.W;
+    const int nb = 32 / B;  // blocks per tile row
+    const int code = xi_code(a.eps_int);
+    const int r = lane % B, bc = lane / B;
+    const int nslots = 2 * B * B;
+    const int2* pp = ps.pp + (Rw + 1) * kPP + (Rw + 1);  // (0,0) = vertex (i0, j0) of slice t-1
+    for (int br = 0; br < nb; ++br) {
+        const int ib = i0 + br * B;
+        if (ib >= H) break;
+        const int i = ib + r, li = i - i0;
+        const int jb = j0 + bc * B;
+        for (int k = lane; k < nb * nslots; k += 32) {
+            ps.smp[0][k] = 0xFFFFFFFFu;
+            ps.smp[1][k] = 0xFFFFFFFFu;
         }
-        __syncthreads();
+        __syncwarp();
+        for (int jj = 0; jj < B; ++jj) {
+            const int j = jb + jj;
+            if (i < H && j < W && (i % n) == 0 && (j % n) == 0) {
+                const int2 qv = ps.qc[li + 1][j - j0 + 1];
+                const int2 p = ps.psl[li][j - j0];
+                int d;
+                unsigned* dst = &ps.smp[1][bc * nslots + 2 * (r * B + jj)];
+                dst[0] = quantize_code(qv.x, p.x, code, d);
+                dst[1] = quantize_code(qv.y, p.y, code, d);
+            }
+        }
+        int2 res = make_int2(0, 0), up = res, left = res;
+        for (int k = 0; k < 2 * B - 1; ++k) {
+            const int jj = k - r;
+            const int j = jb + jj, lj = j - j0;
+            int2 fromprev;
+            fromprev.x = __shfl_up_sync(0xffffffffu, res.x, 1);
+            fromprev.y = __shfl_up_sync(0xffffffffu, res.y, 1);
+            const int2 upleft_in = up;
+            if (jj >= 0 && jj < B && i < H && j < W) {
+                const int2 u = r > 0 ? fromprev : ps.qc[li][lj + 1];
+                const int2 lft = jj > 0 ? left : ps.qc[li + 1][lj];
+                const int2 ul = (r > 0 && jj > 0) ? upleft_in : ps.qc[li][lj];
+                const int2 p0 = pp[(li - 1) * kPP + lj - 1], p1 = pp[(li - 1) * kPP + lj];
+                const int2 p2 = pp[li * kPP + lj - 1], p3 = pp[li * kPP + lj];
+                const int pu = u.x + lft.x + p3.x - ul.x - p1.x - p2.x + p0.x;
+                const int pv = u.y + lft.y + p3.y - ul.y - p1.y - p2.y + p0.y;
+                const int2 qv = ps.qc[li + 1][lj + 1];
+                int2 rec;
+                const unsigned su = quantize_code(qv.x, pu, code, rec.x);
+                const unsigned sv = quantize_code(qv.y, pv, code, rec.y);
+                if ((i % n) == 0 && (j % n) == 0) {
+                    unsigned* dst = &ps.smp[0][bc * nslots + 2 * (r * B + jj)];
+                    dst[0] = su;
+                    dst[1] = sv;
+                }
+                up = u;
+                res = rec;
+                left = rec;
+            } else {
+                res = make_int2(0, 0);
+                up = make_int2(0, 0);
+            }
+        }
+        __syncwarp();
+        for (int b = 0; b < nb; ++b) {
+            const int jbb = j0 + b * B;
+            if (jbb >= W) break;
+            const long long r3 = warp_block_score(&ps.smp[0][b * nslots], nslots, B, ps.hist);
+            const long long rs = warp_block_score(&ps.smp[1][b * nslots], nslots, B, ps.hist);
+            if (lane == 0) {
+                const unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
+                a.modes[((size_t)t * a.nby + ib / B) * a.nbx + jbb / B] = m;
+                ps.modes[br * nb + b] = m;
+                if (m) atomicAdd(a.counters + 2, 1ull);
+            }
+        }
+        __syncwarp();
     }
-    // sampled sites: (i, j) with i % n == 0 and j % n == 0
-    const bool sampled = inb && (i % n == 0) && (j % n == 0);
-    if (sampled) {
-        int slot = atomicAdd(cnt + 2, 1);
-        s3[2 * slot] = s3u;
-        s3[2 * slot + 1] = s3v;
-        ss[2 * slot] = ssu;
-        ss[2 * slot + 1] = ssv;
+}
+
+__device__ bool prep_tile(const SliceArgs& a, int t, int s, int c, WarpSmem& sm) {
+    const int lane = threadIdx.x, H = a.H, W = a.W;
+    const int nstrips = (H + 31) / 32;
+    const int i0 = 32 * s, j0 = 32 * c;
+    const int s_req = min(nstrips - 1, (i0 + 31 + a.R) >> 5);
+    const unsigned col_req = (unsigned)min(W, j0 + 32 + a.R);
+    if (!warp_wait_geq(a, a.progress + (size_t)(t - 1) * nstrips + s_req, col_req)) return false;
+    PrepSmem& ps = sm.prep;
+    const size_t sl = (size_t)H * W;
+    const int2 z = make_int2(0, 0);
+    // stage q(t) with a one-cell halo and slice t-1 reconstructed with the
+    // semi-Lagrangian reach (when it fits the window)
+    const int2* Qt = a.q + (size_t)t * sl;
+    for (int rr = 0; rr < 34; ++rr) {
+        const int i = i0 - 1 + rr;
+        for (int cc = lane; cc < 34; cc += 32) {
+            const int j = j0 - 1 + cc;
+            ps.qc[rr][cc] = (i >= 0 && i < H && j >= 0 && j < W) ? __ldg(Qt + (size_t)i * W + j) : z;
+        }
+    }
+    const bool staged = a.R <= kStageR;
+    const int Rw = staged ? a.R : 0;
+    const int span = 34 + 2 * Rw;
+    const int2* P = a.qhat + (size_t)(t - 1) * sl;
+    for (int rr = 0; rr < span; ++rr) {
+        const int i = i0 - 1 - Rw + rr;
+        for (int cc = lane; cc < span; cc += 32) {
+            const int j = j0 - 1 - Rw + cc;
+            ps.pp[rr * kPP + cc] = (i >= 0 && i < H && j >= 0 && j < W) ? __ldcg(P + (size_t)i * W + j) : z;
+        }
+    }
+    __syncwarp();
+    const int j = j0 + lane;
+    const bool colok = j < W;
+    const bool mop = a.pred == 2;
+    const SmemSlice Ps{ps.pp, i0 - 1 - Rw, j0 - 1 - Rw, kPP};
+    const GlobalSlice Pg{P, W};
+    unsigned sub = 0, steps = 0;
+    // pure SL: every vertex; MoP: the sampled sites first (for the decision)
+    for (int rr = 0; rr < 32; ++rr) {
+        const int i = i0 + rr;
+        if (i >= H) break;
+        if (!colok) continue;
+        if (mop && !((i % a.n) == 0 && (j % a.n) == 0)) continue;
+        int pu, pv;
+        const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                              : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+        const int2 p = make_int2(pu, pv);
+        ps.psl[rr][lane] = p;
+        a.psl[((size_t)t * H + i) * W + j] = p;
+        sub += md > 0;
+        steps += md;
+    }
+    __syncwarp();
+    if (mop) {
+        mop_tile(a, t, i0, j0, ps, Rw);
+        __syncwarp();
+        for (int rr = 0; rr < 32; ++rr) {
+            const int i = i0 + rr;
+            if (i >= H) break;
+            if (!colok || ((i % a.n) == 0 && (j % a.n) == 0)) continue;
+            if (!ps.modes[(rr / a.B) * (32 / a.B) + lane / a.B]) continue;
+            int pu, pv;
+            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+            a.psl[((size_t)t * H + i) * W + j] = make_int2(pu, pv);
+            sub += md > 0;
+            steps += md;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sub += __shfl_xor_sync(0xffffffffu, sub, o);
         steps += __shfl_xor_sync(0xffffffffu, steps, o);
     }
-    if ((tid & 31) == 0 && sub) {
+    if (lane == 0 && sub) {
         atomicAdd(a.counters + 0, (unsigned long long)sub);
         atomicAdd(a.counters + 1, (unsigned long long)steps);
     }
-    __syncthreads();
-    const int nslots = 2 * cnt[2];
-    long long r3 = block_score(s3, nslots, B, red, cnt);
-    long long rs = block_score(ss, nslots, B, red, cnt);
-    if (tid == 0) {
-        unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
-        a.modes[((size_t)t * a.nby + blockIdx.y) * a.nbx + blockIdx.x] = m;
-        if (m) atomicAdd(a.counters + 2, 1ull);
-    }
+    warp_publish(a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, 1u);
+    return true;
+}
+
+// prep(t, s, g): the tiles c = g, g + PG, g + 2 PG, ... of strip s, in order.
+__device__ bool prep_item(const SliceArgs& a, int t, int s, int g, WarpSmem& sm) {
+    for (int c = g; c < a.nchunks; c += a.prep_groups)
+        if (!prep_tile(a, t, s, c, sm)) return false;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
-// wave_kernel: one warp per strip of 32 rows of slice t; lane l handles row
-// 32*strip + l and at step k column k - l, so each lane receives the
-// reconstruction of (i-1, j) from lane l-1 one step after it was produced.
-// Row 32*strip - 1 comes from the previous strip through global memory,
-// published by its lane 31 with release stores and read after an acquire.
-// Strips take tickets in launch order, so a strip only ever waits for a
-// strip that started before it; every wait is bounded in time and sets the
-// status word on expiry.
+// wave(t, s)
 // ---------------------------------------------------------------------------
-struct StepIn {
-    int2 qv;
-    int xi;
-    unsigned pm;
-    int2 psl;
-    unsigned use_sl;
-    int2 nb[14];
-};
-
-__device__ __forceinline__ void load_step(const SliceArgs& a, int i, int j, StepIn& in) {
-    const int H = a.H, W = a.W, t = a.t;
-    in.xi = 0;
-    in.pm = 0;
-    in.use_sl = 0;
-    if (i >= H || j < 0 || j >= W) return;
-    const size_t v = ((size_t)t * H + i) * W + j;
-    in.qv = __ldg(a.q + v);
-    in.xi = __ldg(a.xi_part + (size_t)i * W + j);
-    if (in.xi > 0) {
-        in.pm = __ldg(a.pmask + (size_t)i * W + j);
-        const unsigned valid = nb_valid(H, W, a.T, t, i, j);
-        if (t >= 1 && (a.pred == 1 || (a.pred == 2 && a.modes[((size_t)t * a.nby + i / a.B) * a.nbx + j / a.B]))) {
-            in.use_sl = 1;
-            in.psl = __ldg(a.psl + (size_t)i * W + j);
+// Stages chunk c of strip s (rows i0..i0+31, columns 32c..32c+31) into b.
+__device__ void stage_chunk(const SliceArgs& a, int t, int i0, int c, ChunkBuf& b, bool need_sl) {
+    const int lane = threadIdx.x, H = a.H, W = a.W, T = a.T;
+    const int j = 32 * c + lane;
+    const size_t sl = (size_t)H * W;
+    const int2 z = make_int2(0, 0);
+    // inputs written before this kernel: asynchronous copies
+    const int2* Qt = a.q + (size_t)t * sl;
+    const int2* Qn = a.q + (size_t)(t + 1 < T ? t + 1 : t) * sl;
+    const size_t vb = (size_t)t * sl;
+    for (int rr = 0; rr < 33; ++rr) {
+        const int i = i0 + rr;
+        const bool ok = i < H && j < W;
+        const size_t off = ok ? (size_t)i * W + j : 0;
+        if (rr < 32) {
+            cp_async8(&b.cls[rr][lane], a.cls + vb + off, ok);
+            cp_async4(&b.cm[rr][lane], a.cls_m + vb + off, ok);
         }
-        if (in.pm) {
-            load_far_neighbours(a.q, a.qhat, H, W, t, i, j, valid, in.nb);
-        } else if (!in.use_sl) {
-            const size_t sl = (size_t)H * W;
-            const int2 z = make_int2(0, 0);
-            in.nb[0] = (valid & 1u) ? __ldg(a.qhat + v - sl - W - 1) : z;
-            in.nb[1] = (valid & 2u) ? __ldg(a.qhat + v - sl - W) : z;
-            in.nb[2] = (valid & 4u) ? __ldg(a.qhat + v - sl - 1) : z;
-            in.nb[3] = (valid & 8u) ? __ldg(a.qhat + v - sl) : z;
+        cp_async8(&b.qv[rr][lane], Qt + off, ok);
+        cp_async8(&b.qn[rr][lane], Qn + off, ok && t + 1 < T);
+        if (lane == 0) {
+            const int j32 = 32 * c + 32;
+            const bool ok32 = i < H && j32 < W;
+            const size_t off32 = ok32 ? (size_t)i * W + j32 : 0;
+            cp_async8(&b.qv[rr][32], Qt + off32, ok32);
+            cp_async8(&b.qn[rr][32], Qn + off32, ok32 && t + 1 < T);
         }
     }
-}
-
-#define CPT_PRED_EVAL(a, b)                                                                       \
-    if ((pm >> bit) & 1u) r = min(r, min_alg2(xi, nb[a].x, nb[a].y, nb[b].x, nb[b].y, qv.x, qv.y)); \
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // data written by this kernel: L2 loads, eight rows in flight at a time
+    if (t >= 1) {
+        const int2* P = a.qhat + (size_t)(t - 1) * sl;
+        const int jj = 32 * c - 1 + lane;  // columns -1..30 of the chunk
+        const int j31 = 32 * c + 31;
+        for (int r0 = 0; r0 < 33; r0 += 11) {
+            int2 tmp[11], t31[11];
+#pragma unroll
+            for (int u = 0; u < 11; ++u) {
+                const int i = i0 - 1 + r0 + u;
+                const bool rok = i >= 0 && i < H;
+                tmp[u] = (rok && jj >= 0 && jj < W) ? __ldcg(P + (size_t)i * W + jj) : z;
+                t31[u] = (lane == 0 && rok && j31 < W) ? __ldcg(P + (size_t)i * W + j31) : z;
+            }
+#pragma unroll
+            for (int u = 0; u < 11; ++u) {
+                b.qp[r0 + u][lane] = tmp[u];
+                if (lane == 0) b.qp[r0 + u][32] = t31[u];
+            }
+        }
+    } else {
+        for (int rr = 0; rr < 33; ++rr) {
+            b.qp[rr][lane] = z;
+            if (lane == 0) b.qp[rr][32] = z;
+        }
+    }
+    if (need_sl) {
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+            int2 tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + r0 + u;
+                tmp[u] = (i < H && j < W) ? __ldcg(a.psl + vb + (size_t)i * W + j) : z;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) b.psl[r0 + u][lane] = tmp[u];
+        }
+    }
+    if (a.pred == 2 && t >= 1) {
+        const int nbw = 32 / a.B;
+        for (int k = lane; k < nbw * nbw; k += 32) {
+            const int by = (i0 + (k / nbw) * a.B) / a.B, bx = (32 * c + (k % nbw) * a.B) / a.B;
+            b.modes[k] = (by < a.nby && bx < a.nbx) ? __ldcg(a.modes + ((size_t)t * a.nby + by) * a.nbx + bx) : 0;
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    // The 10 flagged faces through slice t-1 and original values only (bits
+    // 0..9) no longer depend on the wavefront: slice t-1 is final.  Evaluate
+    // them now and fold them into the staged bound.
+    if (t >= 1) {
+        for (int rr = 0; rr < 32; ++rr) {
+            const int i = i0 + rr;
+            if (i >= H || j >= W) break;
+            int2 cl = b.cls[rr][lane];
+            const unsigned mm = b.cm[rr][lane] & 0x3FFu, mf = (unsigned)cl.y & 0x3FFu;
+            if (cl.x <= 0 || (mm | mf) == 0) continue;
+            int2 nb[14];
+            nb[0] = b.qp[rr][lane];
+            nb[1] = b.qp[rr][lane + 1];
+            nb[2] = b.qp[rr + 1][lane];
+            nb[3] = b.qp[rr + 1][lane + 1];
+            nb[7] = b.qv[rr][lane + 1];
+            nb[8] = b.qv[rr + 1][lane];
+            nb[9] = b.qv[rr + 1][lane + 1];
+            nb[10] = b.qn[rr][lane];
+            nb[11] = b.qn[rr][lane + 1];
+            nb[12] = b.qn[rr + 1][lane];
+            nb[13] = b.qn[rr + 1][lane + 1];
+            const int2 qv = b.qv[rr][lane];
+            int xi = cl.x, bit = 0;
+#define CPT_T1_FACE(fa, fb)                                                                         \
+    if (bit < 10) {                                                                                \
+        if ((mf >> bit) & 1u) xi = min_alg2(xi, nb[fa].x, nb[fa].y, nb[fb].x, nb[fb].y, qv.x, qv.y); \
+        else if (((mm >> bit) & 1u) && m_zero(nb[fa], nb[fb], qv)) xi = 0;                          \
+    }                                                                                              \
     ++bit;
+            CPT_UNC_FACES(CPT_T1_FACE)
+#undef CPT_T1_FACE
+            cl.x = xi;
+            b.cls[rr][lane] = cl;
+        }
+    }
+}
 
-constexpr int kPublishEvery = 16;  // columns between progress publications
-
-__global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
+__device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x;
-    const int H = a.H, W = a.W, T = a.T, t = a.t;
+    const int lane = threadIdx.x, H = a.H, W = a.W;
     const int nstrips = (H + 31) / 32;
-    int s = 0;
-    if (lane == 0) s = (int)atomicAdd(a.ticket + t, 1u);
-    s = __shfl_sync(FULL, s, 0);
-    const int i = s * 32 + lane;
+    const int i0 = 32 * s, i = i0 + lane;
     const bool rowok = i < H;
     const size_t base = (size_t)t * H * W;
-    unsigned* prog_prev = a.progress + (size_t)t * nstrips + (s > 0 ? s - 1 : 0);
+    const unsigned* prog_prev = a.progress + (size_t)t * nstrips + (s > 0 ? s - 1 : 0);
+    const unsigned* prog_below = a.progress + (size_t)(t > 0 ? t - 1 : 0) * nstrips + s;
     unsigned* prog_me = a.progress + (size_t)t * nstrips + s;
+    const bool need_sl = t >= 1 && a.eps_int > 0 && a.pred != 0;
+    const bool sl_all = t >= 1 && a.pred == 1;
+    const int nbw = 32 / a.B;
     int2 left = make_int2(0, 0), up = left, res = left;
-    unsigned known = 0;
-    StepIn cur, nxt;
-    load_step(a, i, -lane, cur);
+    int fetched = 0;  // border columns staged in sm.border
     for (int k = 0; k < W + 31; ++k) {
         const int j = k - lane;
-        load_step(a, i, j + 1, nxt);
+        if ((k & 31) == 0 && k < W) {
+            const int c = k >> 5;
+            if (need_sl) {
+                if (!warp_wait_geq(a, a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, 1u)) return false;
+            } else if (t >= 1) {
+                // the strip of slice t-1 must have passed the chunk (Lorenzo and faces read it)
+                if (!warp_wait_geq(a, prog_below, (unsigned)min(W, 32 * c + 32))) return false;
+            }
+            stage_chunk(a, t, i0, c, sm.buf[c & 1], need_sl);
+            __syncwarp();
+        }
+        if (s > 0 && k < W && k >= fetched) {
+            const unsigned seen = warp_wait_geq(a, prog_prev, (unsigned)(k + 1));
+            if (!seen) return false;
+            const int avail = min(min(W, k + 32), (int)seen);
+            const int col = fetched + lane;
+            if (col < avail) sm.border[col & 63] = __ldcg(a.qhat + base + (size_t)(i0 - 1) * W + col);
+            fetched = avail;
+            __syncwarp();
+        }
         int2 fromprev;
         fromprev.x = __shfl_up_sync(FULL, res.x, 1);
         fromprev.y = __shfl_up_sync(FULL, res.y, 1);
         const int2 upleft = up;
-        int abort = 0;
-        if (lane == 0) {
-            if (s == 0 || j >= W) {
-                up = make_int2(0, 0);
-            } else {
-                if ((unsigned)j >= known) {
-                    unsigned long long t0 = 0;
-                    for (;;) {
-                        unsigned p = ld_acquire(prog_prev);
-                        if (p > (unsigned)j) { known = p; break; }
-                        if (*(volatile int*)a.status != 0) { abort = 1; break; }
-                        unsigned long long now = global_ns();
-                        if (t0 == 0) t0 = now;
-                        else if ((long long)(now - t0) > a.timeout_ns) {
-                            atomicCAS(a.status, 0, kStatusTimeout);
-                            abort = 1;
-                            break;
-                        }
-                    }
-                }
-                if (!abort) up = __ldcg(a.qhat + base + (size_t)(i - 1) * W + j);
-            }
-        } else {
-            up = fromprev;
-        }
-        abort = __shfl_sync(FULL, abort, 0);
-        if (abort) return;
+        if (lane == 0) up = (s > 0 && k < W) ? sm.border[k & 63] : make_int2(0, 0);
+        else up = fromprev;
         const bool active = rowok && j >= 0 && j < W;
         if (active) {
-            int xi = cur.xi;
-            const int2 qv = cur.qv;
-            if (xi > 0 && cur.pm) {
-                cur.nb[4] = upleft;
-                cur.nb[5] = up;
-                cur.nb[6] = left;
-                const int2* nb = cur.nb;
-                const unsigned pm = cur.pm;
-                int r = xi, bit = 0;
-                CPT_PRED_FACES(CPT_PRED_EVAL)
-                xi = r;
+            const ChunkBuf& b = sm.buf[(j >> 5) & 1];
+            const int cj = j & 31;
+            const int2 cl = b.cls[lane][cj];
+            int xi = cl.x;
+            const int2 qv = b.qv[lane][cj];
+            const int2 n0 = b.qp[lane][cj], n1 = b.qp[lane][cj + 1];
+            const int2 n2 = b.qp[lane + 1][cj], n3 = b.qp[lane + 1][cj + 1];
+            const unsigned mf = (unsigned)cl.y >> 10, mm = b.cm[lane][cj] >> 10;
+            if (xi > 0 && (mf | mm)) {
+                // the 14 faces through a raster predecessor (uncertain bits 10..23)
+                const int2 n7 = b.qv[lane][cj + 1], n8 = b.qv[lane + 1][cj], n9 = b.qv[lane + 1][cj + 1];
+                const int2 n10 = b.qn[lane][cj], n11 = b.qn[lane][cj + 1];
+                const int2 n12 = b.qn[lane + 1][cj], n13 = b.qn[lane + 1][cj + 1];
+                const int2 n4 = upleft, n5 = up, n6 = left;
+                // M = 0 checks: branch free, all in registers
+                unsigned hits = 0;
+                int bit = 0;
+#define CPT_NB(k) n##k
+#define CPT_PM(fa, fb)                                                                  \
+    if (bit >= 10) hits |= (m_zero(CPT_NB(fa), CPT_NB(fb), qv) ? 1u : 0u) << (bit - 10); \
+    ++bit;
+                CPT_UNC_FACES(CPT_PM)
+#undef CPT_PM
+#undef CPT_NB
+                if (hits & mm) xi = 0;
+                if (xi > 0 && mf) {
+                    int2* nb = sm.nbs[lane];
+                    nb[0] = n0; nb[1] = n1; nb[2] = n2; nb[3] = n3;
+                    nb[4] = n4; nb[5] = n5; nb[6] = n6;
+                    nb[7] = n7; nb[8] = n8; nb[9] = n9;
+                    nb[10] = n10; nb[11] = n11; nb[12] = n12; nb[13] = n13;
+                    for (unsigned m = mf; m && xi > 0; m &= m - 1) {
+                        const unsigned pr = unc_pair(__ffs(m) - 1 + 10);
+                        const int2 p0 = nb[pr & 15u], p1 = nb[pr >> 4];
+                        xi = min_alg2(xi, p0.x, p0.y, p1.x, p1.y, qv.x, qv.y);
+                    }
+                }
             }
             const int code = xi_code(xi);
             int2 rec = qv;
             unsigned sym = 0;
             if (code > 0) {
                 int pu, pv;
-                if (cur.use_sl) {
-                    pu = cur.psl.x;
-                    pv = cur.psl.y;
+                const bool use_sl = sl_all || (need_sl && a.pred == 2 && b.modes[(lane / a.B) * nbw + cj / a.B]);
+                if (use_sl) {
+                    const int2 p = b.psl[lane][cj];
+                    pu = p.x;
+                    pv = p.y;
                 } else {
-                    pu = up.x + left.x + cur.nb[3].x - upleft.x - cur.nb[1].x - cur.nb[2].x + cur.nb[0].x;
-                    pv = up.y + left.y + cur.nb[3].y - upleft.y - cur.nb[1].y - cur.nb[2].y + cur.nb[0].y;
+                    pu = up.x + left.x + n3.x - upleft.x - n1.x - n2.x + n0.x;
+                    pv = up.y + left.y + n3.y - upleft.y - n1.y - n2.y + n0.y;
                 }
-                unsigned su = quantize_code(qv.x, pu, code, rec.x);
-                unsigned sv = quantize_code(qv.y, pv, code, rec.y);
+                const unsigned su = quantize_code(qv.x, pu, code, rec.x);
+                const unsigned sv = quantize_code(qv.y, pv, code, rec.y);
                 sym = su | (sv << 16);
             }
             const size_t v = base + (size_t)i * W + j;
@@ -401,42 +655,84 @@ __global__ void __launch_bounds__(32) wave_kernel(SliceArgs a) {
             a.sym[v] = sym;
             if (a.xi_out) a.xi_out[v] = xi;
             res = rec;
-            if (lane == 31 && ((j % kPublishEvery) == kPublishEvery - 1 || j == W - 1))
-                st_release(prog_me, (unsigned)(j + 1));
         } else {
             res = make_int2(0, 0);
         }
         left = res;
-        cur = nxt;
+        // the last lane finished column k - 31: publish every kPublishEvery columns
+        const int jl = k - 31;
+        if (jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1))
+            warp_publish(prog_me, (unsigned)(jl + 1));
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem& sm = *reinterpret_cast<WarpSmem*>(smem_raw);
+    const int nstrips = (a.H + 31) / 32;
+    const unsigned per_strip = (unsigned)a.prep_groups + 1u;
+    const unsigned per_slice = (unsigned)nstrips * per_strip;
+    const unsigned total = per_slice * (unsigned)a.T;
+    for (;;) {
+        unsigned item = 0;
+        int stop = 0;
+        if (threadIdx.x == 0) {
+            item = atomicAdd(a.ticket, 1u);
+            stop = *(volatile int*)a.status != 0;
+        }
+        item = __shfl_sync(0xffffffffu, item, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (item >= total || stop) return;
+        const int t = (int)(item / per_slice);
+        const unsigned r = item % per_slice;
+        const int s = (int)(r / per_strip);
+        const int g = (int)(r % per_strip);
+        // slice 0 has no semi-Lagrangian work: its prep items are empty
+        bool ok = true;
+        if (g < a.prep_groups) {
+            if (t >= 1) ok = prep_item(a, t, s, g, sm);
+        } else {
+            ok = wave_item(a, t, s, sm);
+        }
+        if (!ok) return;
     }
 }
-#undef CPT_PRED_EVAL
 
 #undef CPT_FACE
+#undef CPT_UNC_MARK
 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-int wave_strips(int H) { return (H + 31) / 32; }
-
-void launch_pre(const SliceArgs& a, cudaStream_t s) {
-    dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
-    pre_kernel<<<grid, 256, 0, s>>>(a);
+void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
+                     unsigned* out_m, cudaStream_t s) {
+    dim3 grid((W + 31) / 32, (H + 7) / 8, T);
+    classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m);
 }
 
-void launch_sl(const SliceArgs& a, cudaStream_t s) {
-    dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
-    sl_kernel<<<grid, 256, 0, s>>>(a);
-}
-
-void launch_mop(const SliceArgs& a, cudaStream_t s) {
-    dim3 grid(a.nbx, a.nby);
-    size_t smem = sizeof(int2) * (a.B + 1) * (a.B + 1) + sizeof(unsigned) * 4 * a.B * a.B;
-    mop_kernel<<<grid, a.B * a.B, smem, s>>>(a);
-}
-
-void launch_wave(const SliceArgs& a, cudaStream_t s) {
-    wave_kernel<<<wave_strips(a.H), 32, 0, s>>>(a);
+cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s) {
+    const size_t smem = sizeof(WarpSmem);
+    cudaError_t e = cudaFuncSetAttribute(encode_pipeline_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    // With SL or MoP the prep tiles of a strip are split into PG round-robin
+    // groups: enough to keep up with the strip's wavefront, few enough that
+    // the resident warps hold the items of about eight slices at a time.
+    SliceArgs b = a;
+    const int warps = nsm * per_sm;
+    const int nstrips = (a.H + 31) / 32;
+    if (a.pred == 0 || a.T < 2 || a.eps_int <= 0) {
+        b.prep_groups = 0;
+    } else {
+        int pg = warps / (8 * nstrips) - 1;
+        b.prep_groups = pg < 1 ? 1 : (pg > a.nchunks ? a.nchunks : pg);
+    }
+    encode_pipeline_kernel<<<warps, 32, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 }  // namespace cpt

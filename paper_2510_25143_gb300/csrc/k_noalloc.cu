@@ -26,7 +26,7 @@
 //     before capturing any stream into a CUDA graph.
 #include <mutex>
 
-#include "../../include/cpt.h"
+#include "cpt.h"
 #include "cpt_internal.h"
 
 namespace cpt {

@@ -105,3 +105,15 @@ def test_street512_full_size():
     assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
     assert st["linf"] <= st["eps"]
     assert np.abs(x.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
+
+
+
+def test_exact_zero_determinants():
+    """Small-integer fields make exact zero determinants (M = 0 in Alg. 2) common
+    on faces through reconstructed vertices; every such vertex must still be
+    encoded exactly as the oracle does."""
+    rng = np.random.default_rng(77)
+    for _ in range(4):
+        uv = rng.integers(-2, 3, (5, 12, 13, 2)).astype(np.float32)
+        compare(uv, 0.6, "lorenzo", eb_mode="abs")
+        compare(uv, 0.6, "mop", eb_mode="abs", block=4)
