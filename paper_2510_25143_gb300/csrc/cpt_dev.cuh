@@ -380,4 +380,43 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+constexpr int kStatusTimeout = -6;
+constexpr int kStatusCorrupt = -4;
+
+// Pipeline waits: lane 0 polls `flag` (acquire) until it reaches `target`,
+// sleeping between polls; gives up when the status word is set or after
+// timeout_ns, setting the status to a timeout.  Returns the value seen
+// (broadcast to the warp), 0 when it gave up (targets are always >= 1).
+__device__ __forceinline__ unsigned warp_wait_geq(int* status, long long timeout_ns, const unsigned* flag,
+                                                  unsigned target) {
+    unsigned seen = 0;
+    if (threadIdx.x % 32 == 0) {
+        seen = ld_acquire(flag);
+        if (seen < target) {
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                __nanosleep(64);
+                seen = ld_acquire(flag);
+                if (seen >= target) break;
+                if (*(volatile int*)status != 0) { seen = 0; break; }
+                if ((long long)(global_ns() - t0) > timeout_ns) {
+                    atomicCAS(status, 0, kStatusTimeout);
+                    seen = 0;
+                    break;
+                }
+            }
+        }
+    }
+    seen = __shfl_sync(0xffffffffu, seen, 0);
+    __syncwarp();
+    return seen;
+}
+
+// Publishes that everything this warp wrote so far is visible.
+__device__ __forceinline__ void warp_publish(unsigned* flag, unsigned value) {
+    __threadfence();
+    __syncwarp();
+    if (threadIdx.x % 32 == 0) st_release(flag, value);
+}
+
 }  // namespace cpt

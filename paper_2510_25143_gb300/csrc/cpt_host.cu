@@ -570,6 +570,264 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     return CPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// decompression
+// ---------------------------------------------------------------------------
+struct Reader {
+    const uint8_t* p;
+    size_t n, at = 0;
+    bool bad = false;
+    uint32_t u32() {
+        if (n - at < 4 || at > n) { bad = true; return 0; }
+        uint32_t x = (uint32_t)p[at] | ((uint32_t)p[at + 1] << 8) | ((uint32_t)p[at + 2] << 16) | ((uint32_t)p[at + 3] << 24);
+        at += 4;
+        return x;
+    }
+    uint64_t u64() { uint64_t lo = u32(); return lo | ((uint64_t)u32() << 32); }
+    double f64() { uint64_t x = u64(); double d; std::memcpy(&d, &x, 8); return d; }
+    const uint8_t* take(size_t k) {
+        if (at > n || n - at < k) { bad = true; return nullptr; }
+        const uint8_t* q = p + at;
+        at += k;
+        return q;
+    }
+};
+
+// Host side of one Huffman stream: codebook -> decoding tables, sync points,
+// words; all checked for consistency.
+struct HuffHost {
+    uint64_t nsym = 0, nwords = 0;
+    std::vector<uint32_t> lut, first, count, base, sorted;
+    std::vector<unsigned long long> chunk_off;
+    const uint8_t* words = nullptr;
+};
+
+static bool parse_huff(Reader& r, uint32_t alphabet, HuffHost& h) {
+    h.nsym = r.u64();
+    const uint32_t nused = r.u32(), chunk = r.u32();
+    if (r.bad || chunk != (uint32_t)kChunkSyms || nused > alphabet) return false;
+    std::vector<uint8_t> len(alphabet, 0);
+    uint32_t prev = 0;
+    uint64_t kraft = 0;  // in units of 2^-24
+    for (uint32_t x = 0; x < nused; ++x) {
+        const uint32_t e = r.u32();
+        const uint32_t sy = e >> 8, l = e & 255u;
+        if (r.bad || sy >= alphabet || l == 0 || l > kMaxCodeLen || (x > 0 && sy <= prev)) return false;
+        len[sy] = (uint8_t)l;
+        prev = sy;
+        kraft += 1ull << (kMaxCodeLen - l);
+    }
+    if (kraft > (1ull << kMaxCodeLen) || (h.nsym > 0 && nused == 0)) return false;
+    const uint64_t nchunks = (h.nsym + kChunkSyms - 1) / kChunkSyms;
+    if (nchunks > (r.n - std::min(r.n, r.at)) / 8) return false;
+    h.chunk_off.resize(nchunks);
+    for (uint64_t c = 0; c < nchunks; ++c) h.chunk_off[c] = r.u64();
+    h.nwords = r.u64();
+    if (r.bad || h.nwords > (r.n - std::min(r.n, r.at)) / 4) return false;
+    h.words = r.take(4 * h.nwords);
+    if (!h.words) return false;
+    for (uint64_t c = 0; c < nchunks; ++c)
+        if (h.chunk_off[c] > h.nwords * 32 || (c > 0 && h.chunk_off[c] < h.chunk_off[c - 1])) return false;
+    // canonical decoding tables
+    h.first.assign(25, 0);
+    h.count.assign(25, 0);
+    h.base.assign(25, 0);
+    for (uint8_t l : len) if (l) h.count[l]++;
+    uint32_t code = 0, idx = 0;
+    for (int l = 1; l <= 24; ++l) {
+        code = (code + h.count[l - 1]) << 1;
+        h.first[l] = code;
+        h.base[l] = idx;
+        idx += h.count[l];
+    }
+    h.first[0] = 0;
+    h.sorted.resize(std::max<uint32_t>(idx, 1));
+    std::vector<uint32_t> fill(25, 0);
+    for (int l = 1; l <= 24; ++l)
+        for (uint32_t sy = 0; sy < alphabet; ++sy)
+            if (len[sy] == l) h.sorted[h.base[l] + fill[l]++] = sy;
+    h.lut.assign(4096, 0);
+    for (int l = 1; l <= 12; ++l)
+        for (uint32_t k = 0; k < h.count[l]; ++k) {
+            const uint32_t c = h.first[l] + k, sy = h.sorted[h.base[l] + k];
+            const uint32_t lo = c << (12 - l), span = 1u << (12 - l);
+            for (uint32_t x = 0; x < span; ++x) h.lut[lo + x] = (sy << 5) | (uint32_t)l;
+        }
+    return true;
+}
+
+template <typename Sym>
+static cpt_status decode_huff_stream(const HuffHost& hh, Sym* d_out, int* d_status, DevArena& ar, cudaStream_t s) {
+    if (hh.nsym == 0) return CPT_OK;
+    uint32_t *d_words, *d_tab;
+    unsigned long long* d_off;
+    CPT_CUDA(ar.alloc(&d_words, hh.nwords + 2));
+    CPT_CUDA(cudaMemsetAsync(d_words, 0, 4 * (hh.nwords + 2), s));
+    if (hh.nwords) CPT_CUDA(cudaMemcpyAsync(d_words, hh.words, 4 * hh.nwords, cudaMemcpyHostToDevice, s));
+    CPT_CUDA(ar.alloc(&d_off, hh.chunk_off.size()));
+    CPT_CUDA(cudaMemcpyAsync(d_off, hh.chunk_off.data(), 8 * hh.chunk_off.size(), cudaMemcpyHostToDevice, s));
+    const size_t ntab = 4096 + 3 * 25 + hh.sorted.size();
+    std::vector<uint32_t> tab;
+    tab.reserve(ntab);
+    tab.insert(tab.end(), hh.lut.begin(), hh.lut.end());
+    tab.insert(tab.end(), hh.first.begin(), hh.first.end());
+    tab.insert(tab.end(), hh.count.begin(), hh.count.end());
+    tab.insert(tab.end(), hh.base.begin(), hh.base.end());
+    tab.insert(tab.end(), hh.sorted.begin(), hh.sorted.end());
+    CPT_CUDA(ar.alloc(&d_tab, ntab));
+    CPT_CUDA(cudaMemcpyAsync(d_tab, tab.data(), 4 * ntab, cudaMemcpyHostToDevice, s));
+    HuffDecode h;
+    h.words = d_words;
+    h.nwords = hh.nwords;
+    h.nsym = hh.nsym;
+    h.chunk_off = d_off;
+    h.lut = d_tab;
+    h.first = d_tab + 4096;
+    h.count = d_tab + 4096 + 25;
+    h.base = d_tab + 4096 + 50;
+    h.sorted = d_tab + 4096 + 75;
+    if constexpr (sizeof(Sym) == 1) launch_huff_decode_u8(h, reinterpret_cast<uint8_t*>(d_out), d_status, s);
+    else launch_huff_decode_u16(h, reinterpret_cast<uint16_t*>(d_out), d_status, s);
+    // the host copies of words/tables must outlive the asynchronous copies
+    CPT_CUDA(cudaStreamSynchronize(s));
+    return CPT_OK;
+}
+
+static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out,
+                                  cpt_dims* dims_out, void* cuda_stream) {
+    if (!in) return fail(CPT_ERR_ARG, "null stream");
+    Reader r{in, in_bytes};
+    const uint8_t* magic = r.take(4);
+    if (!magic || std::memcmp(magic, "CPT1", 4) != 0) return fail(CPT_ERR_CORRUPT, "not a cpt stream");
+    const uint32_t ver = r.u32();
+    const int H = (int)r.u32(), W = (int)r.u32(), T = (int)r.u32();
+    const int k = (int)r.u32();
+    r.u32();  // eps'
+    const int pred = (int)r.u32(), B = (int)r.u32();
+    r.u32();  // sampling stride
+    const uint32_t radius = r.u32();
+    r.u32();
+    const double dx = r.f64(), dy = r.f64(), dt = r.f64();
+    r.f64();  // eps
+    const uint64_t n_ld = r.u64(), mode_bytes = r.u64();
+    if (r.bad || ver != kFormat || H < 2 || W < 2 || T < 1 || pred < 0 || pred > 2 || B < 1 ||
+        radius != (uint32_t)kRadius || k < -200 || k > 200 || !(dx > 0) || !(dy > 0) || !(dt > 0) ||
+        (long long)H * W > (1ll << 31) / 4)
+        return fail(CPT_ERR_CORRUPT, "bad stream header");
+    if (dims_out) {
+        dims_out->H = H; dims_out->W = W; dims_out->T = T;
+        dims_out->dx = dx; dims_out->dy = dy; dims_out->dt = dt;
+    }
+    if (!uv_out && !qhat_out) return CPT_OK;
+    const size_t N = (size_t)H * W * T;
+    const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
+    const size_t nblk = pred == 2 ? (size_t)T * nby * nbx : 0;
+    if (mode_bytes != (nblk + 7) / 8) return fail(CPT_ERR_CORRUPT, "bad mode section");
+    const uint8_t* modes = r.take(mode_bytes);
+    HuffHost hx, hd;
+    if (!modes || !parse_huff(r, 33, hx) || hx.nsym != N) return fail(CPT_ERR_CORRUPT, "bad bound-code stream");
+    if (!parse_huff(r, 2 * kRadius, hd)) return fail(CPT_ERR_CORRUPT, "bad residual stream");
+    if (n_ld > (r.n - std::min(r.n, r.at)) / 4) return fail(CPT_ERR_CORRUPT, "truncated verbatim values");
+    const uint8_t* ldp = r.take(4 * n_ld);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(CPT_ERR_CUDA, "no CUDA device available");
+    }
+    retain_pool_memory();
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    DevArena ar(s);
+    const int nsm = sm_count();
+    int* d_status;
+    uint8_t *d_qxi, *d_modes;
+    uint16_t* d_qd;
+    uint32_t* d_sym;
+    int32_t* d_ld;
+    int2 *d_raw, *d_qhat, *d_psl;
+    unsigned long long *d_cnt, *d_tmp;
+    CPT_CUDA(ar.alloc(&d_status, 1));
+    CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    CPT_CUDA(ar.alloc(&d_qxi, N));
+    CPT_CUDA(ar.alloc(&d_qd, hd.nsym));
+    CPT_CUDA(ar.alloc(&d_sym, N));
+    CPT_CUDA(ar.alloc(&d_ld, n_ld));
+    CPT_CUDA(ar.alloc(&d_raw, N));
+    CPT_CUDA(ar.alloc(&d_qhat, N));
+    CPT_CUDA(ar.alloc(&d_psl, pred != 0 ? N : 1));
+    CPT_CUDA(ar.alloc(&d_cnt, N));
+    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(N)));
+    CPT_CUDA(ar.alloc(&d_modes, std::max<size_t>(mode_bytes, 1)));
+    if (mode_bytes) CPT_CUDA(cudaMemcpyAsync(d_modes, modes, mode_bytes, cudaMemcpyHostToDevice, s));
+    if (n_ld) CPT_CUDA(cudaMemcpyAsync(d_ld, ldp, 4 * n_ld, cudaMemcpyHostToDevice, s));
+    cpt_status rc = decode_huff_stream<uint8_t>(hx, d_qxi, d_status, ar, s);
+    if (rc != CPT_OK) return rc;
+    launch_qd_count(d_qxi, N, d_cnt, d_status, s);
+    unsigned long long last_cnt = 0, last_off = 0;
+    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    launch_exclusive_scan_u64(d_cnt, N, d_tmp, s);
+    CPT_CUDA(cudaMemcpyAsync(&last_off, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    int status = 0;
+    CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (status != 0 || last_off + last_cnt != hd.nsym) return fail(CPT_ERR_CORRUPT, "bound codes do not match the residuals");
+    rc = decode_huff_stream<uint16_t>(hd, d_qd, d_status, ar, s);
+    if (rc != CPT_OK) return rc;
+    launch_gather_sym(d_qxi, d_cnt, d_qd, hd.nsym, N, d_sym, d_status, s);
+    launch_count_pack(d_qxi, d_sym, N, d_cnt, s);
+    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    launch_exclusive_scan_u64(d_cnt, N, d_tmp, s);
+    CPT_CUDA(cudaMemcpyAsync(&last_off, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    launch_gather_raw(d_qxi, d_sym, d_cnt, d_ld, n_ld, N, d_raw, d_status, s);
+    CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (status != 0 || ((last_off + last_cnt) & 0xFFFFFFFFull) != n_ld)
+        return fail(CPT_ERR_CORRUPT, "verbatim values do not match the codes");
+    // reconstruction pipeline
+    const int nstrips = (H + 31) / 32, nchunks = (W + 31) / 32;
+    unsigned *d_prog, *d_prep, *d_ticket;
+    CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
+    CPT_CUDA(ar.alloc(&d_prep, (size_t)T * nstrips * nchunks));
+    CPT_CUDA(ar.alloc(&d_ticket, 1));
+    CPT_CUDA(cudaMemsetAsync(d_prog, 0, sizeof(unsigned) * T * nstrips, s));
+    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * (size_t)T * nstrips * nchunks, s));
+    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
+    DecodeArgs a;
+    a.qxi = d_qxi;
+    a.sym = d_sym;
+    a.raw = d_raw;
+    a.psl = d_psl;
+    a.mode_bits = d_modes;
+    a.qhat = d_qhat;
+    a.progress = d_prog;
+    a.prep_done = d_prep;
+    a.ticket = d_ticket;
+    a.status = d_status;
+    a.H = H; a.W = W; a.T = T;
+    a.pred = pred; a.B = B; a.nby = nby; a.nbx = nbx; a.nchunks = nchunks;
+    a.prep_groups = 0;
+    a.cfl_x = std::ldexp(dt / dx, -k);
+    a.cfl_y = std::ldexp(dt / dy, -k);
+    // every reconstruction of a valid stream is below 2^24 in magnitude
+    a.R = (int)std::min(std::ceil(16777216.0 * std::max(a.cfl_x, a.cfl_y)) + 2.0, (double)std::max(H, W) + 2.0);
+    a.timeout_ns = 2000000000ll;
+    CPT_CUDA(launch_decode_pipeline(a, nsm, s));
+    CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (status == (int)CPT_ERR_TIMEOUT) return fail(CPT_ERR_TIMEOUT, "decoder wavefront wait timed out");
+    if (status != 0) return fail(CPT_ERR_CORRUPT, "corrupt stream");
+    if (qhat_out) CPT_CUDA(cudaMemcpyAsync(qhat_out, d_qhat, N * 8, cudaMemcpyDeviceToHost, s));
+    if (uv_out) {
+        const bool dev = is_device_pointer(uv_out) && !(reinterpret_cast<uintptr_t>(uv_out) & 7u);
+        float* dst = uv_out;
+        if (!dev) CPT_CUDA(ar.alloc(&dst, 2 * N));
+        launch_to_float(d_qhat, N, std::ldexp(1.0, -k), dst, s);
+        if (!dev) CPT_CUDA(cudaMemcpyAsync(uv_out, dst, N * 8, cudaMemcpyDefault, s));
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    CPT_CUDA(cudaGetLastError());
+    return CPT_OK;
+}
+
 }  // namespace cpt
 
 // ---------------------------------------------------------------------------
@@ -589,8 +847,7 @@ cpt_status cpt_compress(const float* uv, const cpt_dims* dims, const cpt_params*
 
 cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out, cpt_dims* dims_out,
                           void* cuda_stream) {
-    (void)in; (void)in_bytes; (void)uv_out; (void)qhat_out; (void)dims_out; (void)cuda_stream;
-    return cpt::fail(CPT_ERR_UNSUPPORTED, "decompression not built yet");
+    return cpt::decompress_impl(in, in_bytes, uv_out, qhat_out, dims_out, cuda_stream);
 }
 
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,

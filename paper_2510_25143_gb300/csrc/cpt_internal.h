@@ -48,6 +48,36 @@ struct SliceArgs {
     long long timeout_ns;
 };
 
+// Canonical Huffman decoding tables of one stream (device pointers).
+struct HuffDecode {
+    const uint32_t* words;          // code words, two zero words of padding after nwords
+    unsigned long long nwords;
+    unsigned long long nsym;
+    const unsigned long long* chunk_off;  // bit offset of every kChunkSyms-th symbol
+    const uint32_t* lut;            // [4096] (symbol << 5) | length for codes of <= 12 bits, else 0
+    const uint32_t* first;          // [25] first code of each length
+    const uint32_t* count;          // [25] codes of each length
+    const uint32_t* base;           // [25] index of the first symbol of each length in `sorted`
+    const uint32_t* sorted;         // symbols ordered by (length, symbol)
+};
+
+// Arguments of the decoder pipeline.
+struct DecodeArgs {
+    const uint8_t* qxi;       // [T][H][W] bound codes
+    const uint32_t* sym;      // [T][H][W] residual symbols, u | v << 16
+    const int2* raw;          // [T][H][W] verbatim values (lossless or unpredictable components)
+    int2* psl;                // [T][H][W] semi-Lagrangian predictions
+    const uint8_t* mode_bits; // MoP block modes as stored in the stream
+    int2* qhat;               // [T][H][W] reconstruction
+    unsigned* progress;
+    unsigned* prep_done;
+    unsigned* ticket;
+    int* status;
+    int H, W, T, pred, B, nby, nbx, nchunks, prep_groups, R;
+    double cfl_x, cfl_y;
+    long long timeout_ns;
+};
+
 // k_field.cu
 void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s);
 void launch_to_fixed(const float* uv, size_t n, double scale, int32_t* q, int nblocks, cudaStream_t s);
@@ -80,6 +110,17 @@ void launch_encode_u8(const uint8_t* x, size_t n, const uint32_t* table, const u
                       uint32_t* words, cudaStream_t s);
 void launch_encode_u16(const uint16_t* x, size_t n, const uint32_t* table, const unsigned long long* tile_off,
                        uint32_t* words, cudaStream_t s);
+// k_decode.cu
+void launch_huff_decode_u8(const HuffDecode& h, uint8_t* out, int* status, cudaStream_t s);
+void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cudaStream_t s);
+void launch_qd_count(const uint8_t* qxi, size_t N, unsigned long long* cnt, int* status, cudaStream_t s);
+void launch_gather_sym(const uint8_t* qxi, const unsigned long long* off, const uint16_t* qd, size_t n_qd, size_t N,
+                       uint32_t* sym, int* status, cudaStream_t s);
+void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned long long* off, const int32_t* ld,
+                       size_t n_ld, size_t N, int2* raw, int* status, cudaStream_t s);
+void launch_to_float(const int2* qhat, size_t N, double inv_scale, float* out, cudaStream_t s);
+cudaError_t launch_decode_pipeline(const DecodeArgs& a, int nsm, cudaStream_t s);
+
 constexpr int kTileSyms = 4096;     // symbols per encode tile
 constexpr int kChunkSyms = 16384;   // symbols per decode chunk (stream sync points)
 

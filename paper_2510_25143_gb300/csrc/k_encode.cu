@@ -32,7 +32,6 @@
 
 namespace cpt {
 
-constexpr int kStatusTimeout = -6;
 constexpr int kPublishEvery = 16;  // columns between progress publications of a strip
 constexpr int kHalo = 34;          // row stride of the staged slice t-1 halo tile
 
@@ -123,38 +122,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
     out_m[v] = um_m;
 }
 
-// ---------------------------------------------------------------------------
-// waits (lane 0 polls; the result is broadcast to the warp)
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned warp_wait_geq(const SliceArgs& a, const unsigned* flag, unsigned target) {
-    unsigned seen = 0;
-    if (threadIdx.x == 0) {
-        seen = ld_acquire(flag);
-        if (seen < target) {
-            const unsigned long long t0 = global_ns();
-            for (;;) {
-                __nanosleep(64);
-                seen = ld_acquire(flag);
-                if (seen >= target) break;
-                if (*(volatile int*)a.status != 0) { seen = 0; break; }
-                if ((long long)(global_ns() - t0) > a.timeout_ns) {
-                    atomicCAS(a.status, 0, kStatusTimeout);
-                    seen = 0;
-                    break;
-                }
-            }
-        }
-    }
-    seen = __shfl_sync(0xffffffffu, seen, 0);
-    __syncwarp();
-    return seen;  // 0 = gave up (target is always >= 1)
-}
-
-// Publishes that everything this warp wrote so far is visible.
-__device__ __forceinline__ void warp_publish(unsigned* flag, unsigned value) {
-    __threadfence();
-    __syncwarp();
-    if (threadIdx.x == 0) st_release(flag, value);
+    return warp_wait_geq(a.status, a.timeout_ns, flag, target);
 }
 
 // ---------------------------------------------------------------------------

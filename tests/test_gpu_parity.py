@@ -102,6 +102,8 @@ def test_street512_full_size():
     assert (g["qhat"][:3] == r["qhat"][:3]).all()
     qh, x, k = oracle.decompress(blob)
     assert (qh == g["qhat"]).all()
+    _, gq, _ = cpt.decompress(blob, want_q=True)
+    assert (gq == qh).all()
     assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
     assert st["linf"] <= st["eps"]
     assert np.abs(x.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
@@ -117,3 +119,57 @@ def test_exact_zero_determinants():
         uv = rng.integers(-2, 3, (5, 12, 13, 2)).astype(np.float32)
         compare(uv, 0.6, "lorenzo", eb_mode="abs")
         compare(uv, 0.6, "mop", eb_mode="abs", block=4)
+
+
+# ---------------------------------------------------------------------------
+# decompression (the inverse raster loop) through the C ABI
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pred", ["lorenzo", "sl", "mop"])
+@pytest.mark.parametrize("shape", [(64, 64, 8), (37, 45, 5), (2, 2, 3)])
+def test_decompress_matches_oracle(pred, shape):
+    H, W, T = shape
+    uv = synth.vortex_sum(H, W, T, seed=11 + H + W, n_vortex=3)
+    blob, st, g = cpt.compress(_dev(uv), 5e-3, pred=pred, debug=True)
+    out, qh, dims = cpt.decompress(blob, want_q=True)
+    oq, ouv, k = oracle.decompress(blob)
+    assert dims == (H, W, T)
+    assert (qh == oq).all() and (qh == g["qhat"]).all()
+    assert np.array_equal(out.view(np.uint32), ouv.view(np.uint32))
+    assert np.abs(out.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
+
+
+def test_decompress_to_device_tensor():
+    import torch
+    uv, eb = synth.workload("vortex64")
+    blob, _, _ = cpt.compress(_dev(uv), eb, pred="mop")
+    dst = torch.empty(uv.shape, dtype=torch.float32, device="cuda:0")
+    cpt.decompress(blob, out=dst)
+    _, ouv, _ = oracle.decompress(blob)
+    assert np.array_equal(dst.cpu().numpy().view(np.uint32), ouv.view(np.uint32))
+
+
+def test_decompress_rejects_malformed_streams():
+    uv, eb = synth.workload("vortex64")
+    blob, _, _ = cpt.compress(_dev(uv), eb, pred="lorenzo")
+    for bad in (b"XXXX" + blob[4:], blob[:50], blob[: len(blob) // 2], blob[:-3]):
+        with pytest.raises(cpt.CptError) as e:
+            cpt.decompress(bad)
+        assert e.value.status == cpt.ERR_CORRUPT
+    # a moved sync point of the bound-code stream is caught by the decoder
+    b = bytearray(blob)
+    off = 96 + 16 + 4 * 25  # header, stream header, at most 25 used codes
+    hdr_used = int.from_bytes(b[96 + 8:96 + 12], "little")
+    off = 96 + 16 + 4 * hdr_used + 8  # second sync point
+    v = int.from_bytes(b[off:off + 8], "little")
+    b[off:off + 8] = (v + 1).to_bytes(8, "little")
+    with pytest.raises(cpt.CptError) as e:
+        cpt.decompress(bytes(b))
+    assert e.value.status == cpt.ERR_CORRUPT
+
+
+def test_oracle_stream_decodes_on_gpu():
+    """Bytes written by the oracle decode on the GPU to the oracle's values."""
+    uv = synth.vortex_sum(40, 52, 6, seed=8)
+    r = oracle.compress(uv, 1e-2, pred="mop", block=8)
+    _, qh, _ = cpt.decompress(r["bytes"], want_q=True)
+    assert (qh == r["qhat"]).all()
