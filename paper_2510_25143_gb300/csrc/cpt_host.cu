@@ -828,6 +828,172 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     return CPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// trajectories
+// ---------------------------------------------------------------------------
+// Orders the crossed faces (indices in increasing face id, degree <= 2) into
+// trajectories: open paths start at their lowest-id end, closed loops at their
+// lowest-id face towards the lower-id neighbour; trajectories are listed by
+// their first face.
+static void order_trajectories(size_t n, const std::vector<unsigned>& deg, const std::vector<unsigned>& adj,
+                               std::vector<uint64_t>& order, std::vector<uint64_t>& offsets) {
+    std::vector<uint8_t> seen(n, 0);
+    std::vector<std::pair<uint64_t, std::vector<uint64_t>>> trajs;  // (first index, faces)
+    auto nbr = [&](size_t x, int slot) -> long long {
+        return (deg[x] > (unsigned)slot && adj[2 * x + slot] != 0xFFFFFFFFu) ? (long long)adj[2 * x + slot] : -1;
+    };
+    auto walk = [&](size_t start, bool loop) {
+        std::vector<uint64_t> path;
+        long long prev = -1, cur = (long long)start;
+        bool first = true;
+        while (cur >= 0 && !seen[cur]) {
+            seen[cur] = 1;
+            path.push_back((uint64_t)cur);
+            const long long n0 = nbr((size_t)cur, 0), n1 = nbr((size_t)cur, 1);
+            long long nxt = -1;
+            if (loop && first) {
+                nxt = (n0 >= 0 && (n1 < 0 || n0 < n1)) ? n0 : n1;
+            } else if (n0 >= 0 && n0 != prev && !seen[n0]) {
+                nxt = n0;
+            } else if (n1 >= 0 && n1 != prev && !seen[n1]) {
+                nxt = n1;
+            }
+            first = false;
+            prev = cur;
+            cur = nxt;
+        }
+        trajs.emplace_back(start, std::move(path));
+    };
+    for (size_t a = 0; a < n; ++a)
+        if (!seen[a] && deg[a] <= 1) walk(a, false);
+    for (size_t a = 0; a < n; ++a)
+        if (!seen[a]) walk(a, true);
+    std::stable_sort(trajs.begin(), trajs.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    order.clear();
+    offsets.assign(1, 0);
+    for (auto& tr : trajs) {
+        order.insert(order.end(), tr.second.begin(), tr.second.end());
+        offsets.push_back(order.size());
+    }
+}
+
+static cpt_status trajectories_impl(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
+                                    void* cuda_stream) {
+    if (!uv || !dims || !out) return fail(CPT_ERR_ARG, "null argument");
+    const int H = dims->H, W = dims->W, T = dims->T;
+    if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
+    if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(CPT_ERR_CUDA, "no CUDA device available");
+    }
+    retain_pool_memory();
+    const size_t N = (size_t)H * W * T, NV = 2 * N;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    DevArena ar(s);
+    const int nsm = sm_count();
+    const float* d_uv = uv;
+    if (!is_device_pointer(uv) || (reinterpret_cast<uintptr_t>(uv) & 15u)) {
+        float* tmp;
+        CPT_CUDA(ar.alloc(&tmp, NV));
+        CPT_CUDA(cudaMemcpyAsync(tmp, uv, NV * sizeof(float), cudaMemcpyDefault, s));
+        d_uv = tmp;
+    }
+    const int rblocks = nsm * 4;
+    RangePartial* d_part;
+    CPT_CUDA(ar.alloc(&d_part, rblocks));
+    launch_range(d_uv, NV, d_part, rblocks, s);
+    std::vector<RangePartial> part(rblocks);
+    CPT_CUDA(cudaMemcpyAsync(part.data(), d_part, sizeof(RangePartial) * rblocks, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    float am = 0.f;
+    unsigned bad_in = 0;
+    for (auto& p : part) { am = std::max(am, p.amax); bad_in |= p.bad; }
+    if (bad_in) return fail(CPT_ERR_ARG, "input holds a non-finite value");
+    int k = scale_log2;
+    if (scale_log2 == CPT_SCALE_AUTO) {
+        k = 0;
+        if (am > 0.f) { int e; std::frexp((double)am, &e); k = 23 - e; }
+    } else if (k < -200 || k > 200 || (am > 0.f && std::ldexp((double)am, k) >= 2147483520.0)) {
+        return fail(CPT_ERR_ARG, "scale exponent out of range for the data");
+    }
+    int32_t* d_q;
+    uint16_t* d_mask;
+    unsigned long long *d_n, *d_off, *d_tmp, *d_fid;
+    CPT_CUDA(ar.alloc(&d_q, NV));
+    CPT_CUDA(ar.alloc(&d_mask, N));
+    CPT_CUDA(ar.alloc(&d_n, 2));
+    CPT_CUDA(ar.alloc(&d_off, N));
+    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(N)));
+    CPT_CUDA(cudaMemsetAsync(d_n, 0, 2 * sizeof(unsigned long long), s));
+    launch_to_fixed(d_uv, NV, std::ldexp(1.0, k), d_q, nsm * 8, s);
+    launch_face_masks(d_q, H, W, T, d_mask, d_n, s);
+    launch_face_count(d_mask, N, d_off, s);
+    launch_exclusive_scan_u64(d_off, N, d_tmp, s);
+    unsigned long long nf = 0;
+    CPT_CUDA(cudaMemcpyAsync(&nf, d_n, 8, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (nf >= 0xFFFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many crossed faces");
+    unsigned *d_par, *d_deg, *d_adj;
+    double* d_xyt;
+    CPT_CUDA(ar.alloc(&d_fid, nf));
+    CPT_CUDA(ar.alloc(&d_par, nf));
+    CPT_CUDA(ar.alloc(&d_deg, nf));
+    CPT_CUDA(ar.alloc(&d_adj, 2 * nf));
+    CPT_CUDA(ar.alloc(&d_xyt, 3 * nf));
+    launch_face_compact(d_mask, d_off, N, d_fid, s);
+    launch_iota(d_par, nf, s);
+    CPT_CUDA(cudaMemsetAsync(d_deg, 0, 4 * std::max<size_t>(nf, 1), s));
+    CPT_CUDA(cudaMemsetAsync(d_adj, 0xFF, 8 * std::max<size_t>(nf, 1), s));
+    launch_tet_link(d_mask, d_off, H, W, T, d_par, d_deg, d_adj, d_n + 1, s);
+    launch_uf_flatten(d_par, nf, s);
+    launch_crossing_points(d_q, d_fid, nf, H, W, d_xyt, s);
+    std::vector<unsigned long long> fid(nf);
+    std::vector<unsigned> deg(nf), adj(2 * nf), par(nf);
+    std::vector<double> xyt(3 * nf);
+    unsigned long long bad = 0;
+    if (nf) {
+        CPT_CUDA(cudaMemcpyAsync(fid.data(), d_fid, 8 * nf, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(deg.data(), d_deg, 4 * nf, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(adj.data(), d_adj, 8 * nf, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(par.data(), d_par, 4 * nf, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(xyt.data(), d_xyt, 24 * nf, cudaMemcpyDeviceToHost, s));
+    }
+    CPT_CUDA(cudaMemcpyAsync(&bad, d_n + 1, 8, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    CPT_CUDA(cudaGetLastError());
+    std::vector<uint64_t> order, offs;
+    order_trajectories((size_t)nf, deg, adj, order, offs);
+    // the union-find components count the trajectories independently of the walk
+    uint64_t roots = 0;
+    for (size_t x = 0; x < nf; ++x) roots += par[x] == (unsigned)x;
+    cpt_trajs* tr = static_cast<cpt_trajs*>(std::calloc(1, sizeof(cpt_trajs)));
+    if (!tr) return fail(CPT_ERR_OOM, "host allocation failed");
+    tr->n_traj = offs.size() - 1;
+    tr->n_points = order.size();
+    tr->offsets = static_cast<uint64_t*>(std::malloc(sizeof(uint64_t) * offs.size()));
+    tr->face_ids = static_cast<uint64_t*>(std::malloc(sizeof(uint64_t) * std::max<size_t>(order.size(), 1)));
+    tr->xyt = static_cast<double*>(std::malloc(sizeof(double) * 3 * std::max<size_t>(order.size(), 1)));
+    if (!tr->offsets || !tr->face_ids || !tr->xyt) {
+        cpt_free_trajs(tr);
+        return fail(CPT_ERR_OOM, "host allocation failed");
+    }
+    std::memcpy(tr->offsets, offs.data(), sizeof(uint64_t) * offs.size());
+    for (size_t x = 0; x < order.size(); ++x) {
+        tr->face_ids[x] = fid[order[x]];
+        std::memcpy(tr->xyt + 3 * x, xyt.data() + 3 * order[x], 3 * sizeof(double));
+    }
+    tr->bad_tets = bad;
+    if (roots != tr->n_traj && bad == 0) {
+        cpt_free_trajs(tr);
+        return fail(CPT_ERR_CUDA, "trajectory components disagree");
+    }
+    *out = tr;
+    return CPT_OK;
+}
+
 }  // namespace cpt
 
 // ---------------------------------------------------------------------------
@@ -852,8 +1018,7 @@ cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int
 
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
                                     void* cuda_stream) {
-    (void)uv; (void)dims; (void)scale_log2; (void)out; (void)cuda_stream;
-    return cpt::fail(CPT_ERR_UNSUPPORTED, "trajectory extraction not built yet");
+    return cpt::trajectories_impl(uv, dims, scale_log2, out, cuda_stream);
 }
 
 void cpt_free(void* p) { std::free(p); }

@@ -121,6 +121,17 @@ void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned l
 void launch_to_float(const int2* qhat, size_t N, double inv_scale, float* out, cudaStream_t s);
 cudaError_t launch_decode_pipeline(const DecodeArgs& a, int nsm, cudaStream_t s);
 
+// k_traj.cu
+void launch_iota(unsigned* x, size_t n, cudaStream_t s);
+void launch_face_count(const uint16_t* mask, size_t N, unsigned long long* cnt, cudaStream_t s);
+void launch_face_compact(const uint16_t* mask, const unsigned long long* off, size_t N, unsigned long long* fid,
+                         cudaStream_t s);
+void launch_tet_link(const uint16_t* mask, const unsigned long long* off, int H, int W, int T, unsigned* par,
+                     unsigned* deg, unsigned* adj, unsigned long long* bad, cudaStream_t s);
+void launch_uf_flatten(unsigned* par, size_t n, cudaStream_t s);
+void launch_crossing_points(const int32_t* q, const unsigned long long* fid, size_t n, int H, int W, double* xyt,
+                            cudaStream_t s);
+
 constexpr int kTileSyms = 4096;     // symbols per encode tile
 constexpr int kChunkSyms = 16384;   // symbols per decode chunk (stream sync points)
 

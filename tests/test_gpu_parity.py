@@ -173,3 +173,53 @@ def test_oracle_stream_decodes_on_gpu():
     r = oracle.compress(uv, 1e-2, pred="mop", block=8)
     _, qh, _ = cpt.decompress(r["bytes"], want_q=True)
     assert (qh == r["qhat"]).all()
+
+
+# ---------------------------------------------------------------------------
+# trajectories (Sec. III-D, Thm. 2) through the C ABI
+# ---------------------------------------------------------------------------
+def _oracle_trajs(uv, k=None):
+    if k is None:
+        k = oracle.scale_exponent(float(np.abs(uv).max()))
+    return oracle.trajectories(oracle.to_fixed(uv, k))
+
+
+def _same_trajs(a, b):
+    ta, pa, ba = a
+    tb, pb, bb = b
+    assert ba == bb == 0
+    assert len(ta) == len(tb)
+    for x, y in zip(ta, tb):
+        assert np.array_equal(x, y)
+    for x, y in zip(pa, pb):
+        assert np.allclose(x, y, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["vortex64", "ragged", "ints", "linear", "birth", "centre"])
+def test_trajectories_match_oracle(case):
+    if case == "vortex64":
+        uv = synth.vortex_sum()
+    elif case == "ragged":
+        uv = synth.vortex_sum(37, 45, 5, seed=9, n_vortex=4)
+    elif case == "ints":
+        uv = np.random.default_rng(3).integers(-2, 3, (4, 9, 11, 2)).astype(np.float32)
+    elif case == "linear":
+        uv = synth.linear_field(24, 32, 8, 6.3, 1.7, 5.6, 1.45)
+    elif case == "birth":
+        uv = synth.birth_field(16, 32, 6, 15.5, 7.5, 6.0, 2)
+    else:
+        uv = synth.centre_field(20, 20, 5, 9.4, 10.7)
+    _same_trajs(cpt.extract_trajectories(_dev(uv)), _oracle_trajs(uv))
+
+
+def test_trajectories_preserved_by_roundtrip():
+    """Thm. 2: the decompressed field has the same trajectories, face by face."""
+    uv, eb = synth.workload("vortex64")
+    blob, st, _ = cpt.compress(_dev(uv), eb, pred="mop")
+    out, _, _ = cpt.decompress(blob)
+    k = st["scale_log2"]
+    t0 = cpt.extract_trajectories(_dev(uv), scale_log2=k)
+    t1 = cpt.extract_trajectories(_dev(out), scale_log2=k)
+    assert len(t0[0]) == len(t1[0]) > 0
+    for x, y in zip(t0[0], t1[0]):
+        assert np.array_equal(x, y)
