@@ -411,6 +411,26 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         a.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
     }
     a.timeout_ns = 2000000000ll;
+    // (t, s) in ticket order: by the diagonal A*t + s, then t
+    {
+        const int A = 1 + (31 + a.R) / 32;
+        std::vector<int2> ord;
+        ord.reserve((size_t)T * nstrips);
+        for (long long d = 0; d <= (long long)A * (T - 1) + nstrips - 1; ++d)
+            for (int t = 0; t < T; ++t) {
+                const long long sidx = d - (long long)A * t;
+                if (sidx >= 0 && sidx < nstrips) ord.push_back(make_int2(t, (int)sidx));
+            }
+        int2* d_order;
+        CPT_CUDA(ar.alloc(&d_order, ord.size()));
+        CPT_CUDA(cudaMemcpyAsync(d_order, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice, s));
+        a.order = d_order;
+        unsigned long long* d_lg;
+        CPT_CUDA(ar.alloc(&d_lg, kLog2Tab));
+        launch_log2_table(d_lg, kLog2Tab, s);
+        a.log2tab = d_lg;
+        CPT_CUDA(cudaStreamSynchronize(s));  // the host order table must outlive the copy
+    }
     tm.begin(3);
     launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, s);
     st.launches[3]++;

@@ -43,6 +43,8 @@ struct SliceArgs {
     int nby, nbx;
     int nchunks;            // ceil(W / 32)
     int prep_groups;        // prep items per strip (round-robin groups of its tiles)
+    const int2* order;      // [T * nstrips] (t, s) of the items in ticket order
+    const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
     long long timeout_ns;
@@ -90,6 +92,8 @@ void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, i
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, cudaStream_t s);
 cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s);
+void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);
+constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols
 size_t encode_smem_bytes();
 
 // k_entropy.cu

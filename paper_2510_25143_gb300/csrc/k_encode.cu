@@ -26,7 +26,8 @@
 //                (release/acquire progress words).
 // Every item waits only for items with smaller tickets, which were taken by
 // running warps, so the pipeline cannot deadlock; each wait is bounded in
-// time and sets the status word when it expires.
+// time and sets the status word when it expires.  (A prep group g of PG takes
+// the tiles c = g, g+PG, ...; PG is the number of chunks, one tile per item.)
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
 
@@ -180,7 +181,8 @@ __device__ __forceinline__ unsigned long long log2_q32(unsigned x) {
 // Score of one block and mode in Q32 bits per sample (Eq. 10 plus the
 // overflow penalty and the metadata term): H0 + 16 L/(n+L) + 1/(2 B^2).
 // smp holds nslots entries: a symbol, 0 for an overflow, 0xFFFFFFFF unused.
-__device__ long long warp_block_score(const unsigned* smp, int nslots, int B, unsigned* hist) {
+__device__ long long warp_block_score(const unsigned* smp, int nslots, int B, unsigned* hist,
+                                      const unsigned long long* __restrict__ lg) {
     const int lane = threadIdx.x;
     const unsigned lo = (unsigned)kRadius - 128u;
     for (int k = lane; k < 256; k += 32) hist[k] = 0;
@@ -204,13 +206,13 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
                     if (m < k) first = false;
                 }
             }
-            if (first) acc += (unsigned long long)c * log2_q32(c);
+            if (first) acc += (unsigned long long)c * __ldg(lg + c);
         }
     }
     __syncwarp();
     for (int k = lane; k < 256; k += 32) {
         unsigned h = hist[k];
-        if (h) acc += (unsigned long long)h * log2_q32(h);
+        if (h) acc += (unsigned long long)h * __ldg(lg + h);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -219,7 +221,7 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
     long long h0 = 0;
-    if (nv > 0) h0 = ((long long)nv * (long long)log2_q32(nv) - (long long)acc) / (long long)nv;
+    if (nv > 0) h0 = ((long long)nv * (long long)__ldg(lg + nv) - (long long)acc) / (long long)nv;
     long long pen = 0;
     if (nv + nf > 0) pen = (long long)(((unsigned long long)(16u * nf) << 32) / (unsigned long long)(nv + nf));
     long long meta = (long long)((1ull << 32) / (unsigned long long)(2 * B * B));
@@ -297,8 +299,8 @@ __device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps
         for (int b = 0; b < nb; ++b) {
             const int jbb = j0 + b * B;
             if (jbb >= W) break;
-            const long long r3 = warp_block_score(&ps.smp[0][b * nslots], nslots, B, ps.hist);
-            const long long rs = warp_block_score(&ps.smp[1][b * nslots], nslots, B, ps.hist);
+            const long long r3 = warp_block_score(&ps.smp[0][b * nslots], nslots, B, ps.hist, a.log2tab);
+            const long long rs = warp_block_score(&ps.smp[1][b * nslots], nslots, B, ps.hist, a.log2tab);
             if (lane == 0) {
                 const unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
                 a.modes[((size_t)t * a.nby + ib / B) * a.nbx + jbb / B] = m;
@@ -320,27 +322,39 @@ __device__ bool prep_tile(const SliceArgs& a, int t, int s, int c, WarpSmem& sm)
     PrepSmem& ps = sm.prep;
     const size_t sl = (size_t)H * W;
     const int2 z = make_int2(0, 0);
-    // stage q(t) with a one-cell halo and slice t-1 reconstructed with the
-    // semi-Lagrangian reach (when it fits the window)
+    // stage q(t) with a one-cell halo (asynchronous copies) and slice t-1
+    // reconstructed with the semi-Lagrangian reach when it fits the window
+    // (L2 loads, several rows in flight)
     const int2* Qt = a.q + (size_t)t * sl;
     for (int rr = 0; rr < 34; ++rr) {
         const int i = i0 - 1 + rr;
         for (int cc = lane; cc < 34; cc += 32) {
             const int j = j0 - 1 + cc;
-            ps.qc[rr][cc] = (i >= 0 && i < H && j >= 0 && j < W) ? __ldg(Qt + (size_t)i * W + j) : z;
+            const bool ok = i >= 0 && i < H && j >= 0 && j < W;
+            cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
         }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const bool staged = a.R <= kStageR;
     const int Rw = staged ? a.R : 0;
     const int span = 34 + 2 * Rw;
     const int2* P = a.qhat + (size_t)(t - 1) * sl;
-    for (int rr = 0; rr < span; ++rr) {
-        const int i = i0 - 1 - Rw + rr;
-        for (int cc = lane; cc < span; cc += 32) {
-            const int j = j0 - 1 - Rw + cc;
-            ps.pp[rr * kPP + cc] = (i >= 0 && i < H && j >= 0 && j < W) ? __ldcg(P + (size_t)i * W + j) : z;
+    for (int cc = lane; cc < span; cc += 32) {
+        const int j = j0 - 1 - Rw + cc;
+        const bool cok = j >= 0 && j < W;
+        for (int r0 = 0; r0 < span; r0 += 8) {
+            int2 tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int rr = r0 + u, i = i0 - 1 - Rw + rr;
+                tmp[u] = (rr < span && cok && i >= 0 && i < H) ? __ldcg(P + (size_t)i * W + j) : z;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (r0 + u < span) ps.pp[(r0 + u) * kPP + cc] = tmp[u];
         }
     }
+    cp_async_wait_all();
     __syncwarp();
     const int j = j0 + lane;
     const bool colok = j < W;
@@ -641,8 +655,7 @@ __global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
     WarpSmem& sm = *reinterpret_cast<WarpSmem*>(smem_raw);
     const int nstrips = (a.H + 31) / 32;
     const unsigned per_strip = (unsigned)a.prep_groups + 1u;
-    const unsigned per_slice = (unsigned)nstrips * per_strip;
-    const unsigned total = per_slice * (unsigned)a.T;
+    const unsigned total = (unsigned)nstrips * per_strip * (unsigned)a.T;
     for (;;) {
         unsigned item = 0;
         int stop = 0;
@@ -653,10 +666,9 @@ __global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
         item = __shfl_sync(0xffffffffu, item, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
         if (item >= total || stop) return;
-        const int t = (int)(item / per_slice);
-        const unsigned r = item % per_slice;
-        const int s = (int)(r / per_strip);
-        const int g = (int)(r % per_strip);
+        const int2 ts = __ldg(a.order + item / per_strip);
+        const int t = ts.x, s = ts.y;
+        const int g = (int)(item % per_strip);
         // slice 0 has no semi-Lagrangian work: its prep items are empty
         bool ok = true;
         if (g < a.prep_groups) {
@@ -671,9 +683,18 @@ __global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
 #undef CPT_FACE
 #undef CPT_UNC_MARK
 
+__global__ void __launch_bounds__(256) log2_table_kernel(unsigned long long* __restrict__ tab, int n) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        tab[x] = x >= 1 ? log2_q32((unsigned)x) : 0ull;
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s) {
+    log2_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(tab, n);
+}
+
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, cudaStream_t s) {
     dim3 grid((W + 31) / 32, (H + 7) / 8, T);
@@ -688,18 +709,10 @@ cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s) 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    // With SL or MoP the prep tiles of a strip are split into PG round-robin
-    // groups: enough to keep up with the strip's wavefront, few enough that
-    // the resident warps hold the items of about eight slices at a time.
+    // with SL or MoP every prep tile is an item of its own
     SliceArgs b = a;
     const int warps = nsm * per_sm;
-    const int nstrips = (a.H + 31) / 32;
-    if (a.pred == 0 || a.T < 2 || a.eps_int <= 0) {
-        b.prep_groups = 0;
-    } else {
-        int pg = warps / (8 * nstrips) - 1;
-        b.prep_groups = pg < 1 ? 1 : (pg > a.nchunks ? a.nchunks : pg);
-    }
+    b.prep_groups = (a.pred == 0 || a.T < 2 || a.eps_int <= 0) ? 0 : a.nchunks;
     encode_pipeline_kernel<<<warps, 32, smem, s>>>(b);
     return cudaGetLastError();
 }
