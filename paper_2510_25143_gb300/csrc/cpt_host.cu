@@ -411,6 +411,23 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         a.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
     }
     a.timeout_ns = 2000000000ll;
+    // prep units (SL and MoP): U x U squares of slices 1..T-1, in a ready queue
+    a.U = (prm->pred == CPT_PRED_MOP && B == 32) ? 32 : 16;
+    a.nur = (H + a.U - 1) / a.U;
+    a.nuc = (W + a.U - 1) / a.U;
+    a.n_units = 0;
+    if (want_sl) {
+        const unsigned long long nu = (unsigned long long)(T - 1) * a.nur * a.nuc;
+        if (nu >= 0xFFFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many prediction units");
+        a.n_units = (unsigned)nu;
+    }
+    unsigned* d_queue;
+    CPT_CUDA(ar.alloc(&d_queue, (size_t)a.n_units + 2));
+    CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * ((size_t)a.n_units + 2), s));
+    a.qhead = d_queue;
+    a.qtail = d_queue + 1;
+    a.qslot = d_queue + 2;
+    a.prep_warps = 0;
     // (t, s) in ticket order: by the diagonal A*t + s, then t
     {
         const int A = 1 + (31 + a.R) / 32;

@@ -32,8 +32,11 @@ struct SliceArgs {
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
     unsigned* progress;     // [T][nstrips] wavefront columns published per strip
-    unsigned* prep_done;    // [T][nstrips][nchunks] prep tiles finished
-    unsigned* ticket;       // work-item counter
+    unsigned* prep_done;    // [T][nstrips][nchunks] prep units finished per 32 x 32 tile
+    unsigned* ticket;       // wavefront item counter
+    unsigned* qslot;        // [n_units] ready queue of prep units (unit id + 1, 0 = not yet filled)
+    unsigned* qhead;        // next queue position to take
+    unsigned* qtail;        // next queue position to fill
     int* status;            // device status word (0 = ok)
     unsigned long long* counters;  // [4]: substep vertices, substeps, SL blocks, spare
     int H, W, T;
@@ -42,8 +45,11 @@ struct SliceArgs {
     int B, n;               // MoP block side (divides 32) and sampling stride
     int nby, nbx;
     int nchunks;            // ceil(W / 32)
-    int prep_groups;        // prep items per strip (round-robin groups of its tiles)
-    const int2* order;      // [T * nstrips] (t, s) of the items in ticket order
+    int U;                  // side of a prep unit (16, or 32 for MoP blocks of 32)
+    int nur, nuc;           // prep units per slice: rows, columns
+    unsigned n_units;       // prep units in total ((T - 1) * nur * nuc), 0 = no prep stage
+    int prep_warps;         // warps (CTAs) working the prep queue
+    const int2* order;      // [T * nstrips] (t, s) of the wavefront items in ticket order
     const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;

@@ -9,31 +9,34 @@
 // could still lower that bound.
 //
 // encode_pipeline_kernel (one persistent launch over all slices) does the
-// rest, pipelining consecutive slices.  Work items, taken by warps from one
-// ticket counter in this order:
-//   for t in 0..T-1, for strip s (32 rows) in 0..nstrips-1:
-//       prep(t, s, g) for g in 0..PG-1 (SL and MoP only), then wave(t, s)
-// prep(t, s, g)  the 32 x 32 tiles c = g, g+PG, ... of strip s of slice t, in
-//                column order: semi-Lagrangian predictions (Sec. VI-A) and
-//                MoP block modes (Sec. VI-B); each needs slice t-1
-//                reconstructed around the tile (waits on wave(t-1, .)).
+// rest, pipelining consecutive slices.  Its warps have one of two roles.
 // wave(t, s)     rows 32s..32s+31 of slice t: the flagged faces with the actual
 //                reconstructions, xi quantisation, prediction and residual
 //                quantisation with immediate write-back (Sec. V-A).  Lane l
 //                handles row 32s+l and, at step k, column k-l; the
 //                reconstruction of (i-1, j) arrives from lane l-1 by shuffle,
 //                the row above the strip from wave(t, s-1) through global memory
-//                (release/acquire progress words).
-// Every item waits only for items with smaller tickets, which were taken by
-// running warps, so the pipeline cannot deadlock; each wait is bounded in
-// time and sets the status word when it expires.  (A prep group g of PG takes
-// the tiles c = g, g+PG, ...; PG is the number of chunks, one tile per item.)
+//                (release/acquire progress words).  Wave warps take the (t, s)
+//                from a ticket counter ordered by the diagonal A*t + s,
+//                A = 1 + ceil((31+R)/32) (R: the semi-Lagrangian reach), which
+//                puts every wave an item depends on at a smaller ticket.
+// prep units     (SL and MoP only) U x U squares of slice t >= 1: semi-Lagrangian
+//                predictions (Sec. VI-A) and MoP block modes (Sec. VI-B).  A unit
+//                needs slice t-1 final around it; the wave of slice t-1 that
+//                makes it so appends it to a ready queue, and prep warps take the
+//                queue in order.  wave(t, s) waits for the units of each tile.
+// Waves wait only for waves with smaller tickets and for queued units; queued
+// units wait for nothing.  Every warp is resident, so the pipeline cannot
+// deadlock; each wait is bounded in time and sets the status word when it
+// expires.
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
 
 namespace cpt {
 
 constexpr int kPublishEvery = 16;  // columns between progress publications of a strip
+constexpr int kPrepShareSL = 50;   // percent of the warps working prep units (SL)
+constexpr int kPrepShareMoP = 45;  // (MoP)
 constexpr int kHalo = 34;          // row stride of the staged slice t-1 halo tile
 
 __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, int j) {
@@ -142,12 +145,13 @@ struct ChunkBuf {
 constexpr int kStageR = 8;                 // largest SL reach served from the staged window
 constexpr int kPP = 34 + 2 * kStageR;      // pitch of the staged slice t-1 window
 struct PrepSmem {
-    int2 qc[34][34];                       // q(t): rows i0-1..i0+32, columns j0-1..j0+32
-    int2 pp[kPP * kPP];                    // qhat(t-1): rows/cols -1-R..32+R around the tile
-    int2 psl[32][32];                      // SL predictions of the tile
+    int2 qc[34][34];                       // q(t): rows/cols -1..U around the unit
+    int2 pp[kPP * kPP];                    // qhat(t-1): rows/cols -1-R..U+R around the unit
+    int2 psl[32][32];                      // SL predictions of the unit
     unsigned smp[2][2048];                 // sampled symbols per mode (0xFFFFFFFF = none)
     unsigned hist[256];
-    unsigned char modes[64];               // decisions of the tile's blocks
+    unsigned short list[1024];             // sites (row * 32 + column) left for SL
+    unsigned char modes[64];               // decisions of the unit's blocks
 };
 struct WarpSmem {
     union {
@@ -159,7 +163,7 @@ struct WarpSmem {
 };
 
 // ---------------------------------------------------------------------------
-// prep(t, s, g): semi-Lagrangian predictions and MoP modes
+// prep units: semi-Lagrangian predictions and MoP modes
 // ---------------------------------------------------------------------------
 // log2(x) in Q32 for x >= 1: integer part from the bit length, then one
 // fraction bit per squaring of the Q31 mantissa (binary logarithm by
@@ -229,48 +233,52 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
     return h0 + pen + meta;
 }
 
-// MoP decisions of the blocks inside the tile (B divides 32), from the staged
-// window.  Lanes are grouped by block: lane l handles row l % B of block l / B
-// of a row of blocks; the 3DL micro-encoding runs as an anti-diagonal sweep
-// inside each block with the original slice t outside the block
-// (context-preserving candidate buffer).  The SL symbols come from psl.
-__device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps, int Rw) {
+// MoP decisions of the blocks inside a prep unit (B divides U), from the
+// staged window.  Lanes are grouped by block: lane l handles row l % B of
+// block l / B of the current group of 32 / B blocks; the 3DL micro-encoding
+// runs as an anti-diagonal sweep inside each block with the original slice t
+// outside the block (context-preserving candidate buffer).  The SL symbols of
+// the sampled sites come from psl.
+__device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps, int Rw) {
     const int lane = threadIdx.x, B = a.B, n = a.n, H = a.H, W = a.W;
-    const int nb = 32 / B;  // blocks per tile row
+    const int nbu = a.U / B, nbt = nbu * nbu;  // blocks per unit side, per unit
+    const int bpp = 32 / B;                    // blocks per pass
     const int code = xi_code(a.eps_int);
-    const int r = lane % B, bc = lane / B;
+    const int r = lane % B, bl = lane / B;
     const int nslots = 2 * B * B;
-    const int2* pp = ps.pp + (Rw + 1) * kPP + (Rw + 1);  // (0,0) = vertex (i0, j0) of slice t-1
-    for (int br = 0; br < nb; ++br) {
-        const int ib = i0 + br * B;
-        if (ib >= H) break;
-        const int i = ib + r, li = i - i0;
-        const int jb = j0 + bc * B;
-        for (int k = lane; k < nb * nslots; k += 32) {
+    const int2* pp = ps.pp + (Rw + 1) * kPP + (Rw + 1);  // (0,0) = vertex (r0, c0) of slice t-1
+    for (int b0 = 0; b0 < nbt; b0 += bpp) {
+        const int bi = b0 + bl;
+        const int ib = r0 + (bi / nbu) * B, jb = c0 + (bi % nbu) * B;
+        const int i = ib + r, li = i - r0;
+        const bool live = bi < nbt && i < H && jb < W;
+        for (int k = lane; k < bpp * nslots; k += 32) {
             ps.smp[0][k] = 0xFFFFFFFFu;
             ps.smp[1][k] = 0xFFFFFFFFu;
         }
         __syncwarp();
-        for (int jj = 0; jj < B; ++jj) {
-            const int j = jb + jj;
-            if (i < H && j < W && (i % n) == 0 && (j % n) == 0) {
-                const int2 qv = ps.qc[li + 1][j - j0 + 1];
-                const int2 p = ps.psl[li][j - j0];
-                int d;
-                unsigned* dst = &ps.smp[1][bc * nslots + 2 * (r * B + jj)];
-                dst[0] = quantize_code(qv.x, p.x, code, d);
-                dst[1] = quantize_code(qv.y, p.y, code, d);
+        if (live && (i % n) == 0) {
+            for (int jj = 0; jj < B; ++jj) {
+                const int j = jb + jj;
+                if (j < W && (j % n) == 0) {
+                    const int2 qv = ps.qc[li + 1][j - c0 + 1];
+                    const int2 p = ps.psl[li][j - c0];
+                    int d;
+                    unsigned* dst = &ps.smp[1][bl * nslots + 2 * (r * B + jj)];
+                    dst[0] = quantize_code(qv.x, p.x, code, d);
+                    dst[1] = quantize_code(qv.y, p.y, code, d);
+                }
             }
         }
         int2 res = make_int2(0, 0), up = res, left = res;
         for (int k = 0; k < 2 * B - 1; ++k) {
             const int jj = k - r;
-            const int j = jb + jj, lj = j - j0;
+            const int j = jb + jj, lj = j - c0;
             int2 fromprev;
             fromprev.x = __shfl_up_sync(0xffffffffu, res.x, 1);
             fromprev.y = __shfl_up_sync(0xffffffffu, res.y, 1);
             const int2 upleft_in = up;
-            if (jj >= 0 && jj < B && i < H && j < W) {
+            if (live && jj >= 0 && jj < B && j < W) {
                 const int2 u = r > 0 ? fromprev : ps.qc[li][lj + 1];
                 const int2 lft = jj > 0 ? left : ps.qc[li + 1][lj];
                 const int2 ul = (r > 0 && jj > 0) ? upleft_in : ps.qc[li][lj];
@@ -283,7 +291,7 @@ __device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps
                 const unsigned su = quantize_code(qv.x, pu, code, rec.x);
                 const unsigned sv = quantize_code(qv.y, pv, code, rec.y);
                 if ((i % n) == 0 && (j % n) == 0) {
-                    unsigned* dst = &ps.smp[0][bc * nslots + 2 * (r * B + jj)];
+                    unsigned* dst = &ps.smp[0][bl * nslots + 2 * (r * B + jj)];
                     dst[0] = su;
                     dst[1] = sv;
                 }
@@ -296,15 +304,17 @@ __device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps
             }
         }
         __syncwarp();
-        for (int b = 0; b < nb; ++b) {
-            const int jbb = j0 + b * B;
-            if (jbb >= W) break;
+        const int nbp = min(bpp, nbt - b0);
+        for (int b = 0; b < nbp; ++b) {
+            const int bb = b0 + b;
+            const int ibb = r0 + (bb / nbu) * B, jbb = c0 + (bb % nbu) * B;
+            if (ibb >= H || jbb >= W) continue;
             const long long r3 = warp_block_score(&ps.smp[0][b * nslots], nslots, B, ps.hist, a.log2tab);
             const long long rs = warp_block_score(&ps.smp[1][b * nslots], nslots, B, ps.hist, a.log2tab);
             if (lane == 0) {
                 const unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
-                a.modes[((size_t)t * a.nby + ib / B) * a.nbx + jbb / B] = m;
-                ps.modes[br * nb + b] = m;
+                a.modes[((size_t)t * a.nby + ibb / B) * a.nbx + jbb / B] = m;
+                ps.modes[bb] = m;
                 if (m) atomicAdd(a.counters + 2, 1ull);
             }
         }
@@ -312,106 +322,184 @@ __device__ void mop_tile(const SliceArgs& a, int t, int i0, int j0, PrepSmem& ps
     }
 }
 
-__device__ bool prep_tile(const SliceArgs& a, int t, int s, int c, WarpSmem& sm) {
-    const int lane = threadIdx.x, H = a.H, W = a.W;
-    const int nstrips = (H + 31) / 32;
-    const int i0 = 32 * s, j0 = 32 * c;
-    const int s_req = min(nstrips - 1, (i0 + 31 + a.R) >> 5);
-    const unsigned col_req = (unsigned)min(W, j0 + 32 + a.R);
-    if (!warp_wait_geq(a, a.progress + (size_t)(t - 1) * nstrips + s_req, col_req)) return false;
+// Prep units waiting for a tile: those of its U x U squares inside the slice.
+__device__ __forceinline__ unsigned tile_units(const SliceArgs& a, int i0, int j0) {
+    const int U = a.U;
+    return (unsigned)(((min(32, a.H - i0) + U - 1) / U) * ((min(32, a.W - j0) + U - 1) / U));
+}
+
+// Release-ordered add: everything this warp wrote before is visible to a
+// reader that acquires the counter.
+__device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
+    __threadfence();
+    __syncwarp();
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
+}
+
+// One prep unit: the U x U vertices from (r0, c0) of slice t >= 1.  Slice t-1
+// is final around it (the unit entered the ready queue after that).
+__device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& sm) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x, H = a.H, W = a.W, U = a.U;
+    const int uh = min(U, H - r0), uw = min(U, W - c0);
     PrepSmem& ps = sm.prep;
     const size_t sl = (size_t)H * W;
     const int2 z = make_int2(0, 0);
-    // stage q(t) with a one-cell halo (asynchronous copies) and slice t-1
-    // reconstructed with the semi-Lagrangian reach when it fits the window
-    // (L2 loads, several rows in flight)
-    const int2* Qt = a.q + (size_t)t * sl;
-    for (int rr = 0; rr < 34; ++rr) {
-        const int i = i0 - 1 + rr;
-        for (int cc = lane; cc < 34; cc += 32) {
-            const int j = j0 - 1 + cc;
-            const bool ok = i >= 0 && i < H && j >= 0 && j < W;
-            cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
+    const bool mop = a.pred == 2;
+    if (mop) {
+        // q(t) with a one-cell halo (asynchronous copies)
+        const int2* Qt = a.q + (size_t)t * sl;
+        for (int rr = 0; rr < U + 2; ++rr) {
+            const int i = r0 - 1 + rr;
+            for (int cc = lane; cc < U + 2; cc += 32) {
+                const int j = c0 - 1 + cc;
+                const bool ok = i >= 0 && i < H && j >= 0 && j < W;
+                cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
+            }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    const bool staged = a.R <= kStageR;
+    // slice t-1 around the unit, widened by the reach when it fits the window
+    // (L2 loads, several rows in flight)
+    const bool staged = U + 2 + 2 * a.R <= kPP;
     const int Rw = staged ? a.R : 0;
-    const int span = 34 + 2 * Rw;
+    const int span = U + 2 + 2 * Rw;
     const int2* P = a.qhat + (size_t)(t - 1) * sl;
     for (int cc = lane; cc < span; cc += 32) {
-        const int j = j0 - 1 - Rw + cc;
+        const int j = c0 - 1 - Rw + cc;
         const bool cok = j >= 0 && j < W;
-        for (int r0 = 0; r0 < span; r0 += 8) {
+        for (int r0w = 0; r0w < span; r0w += 8) {
             int2 tmp[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int rr = r0 + u, i = i0 - 1 - Rw + rr;
+                const int rr = r0w + u, i = r0 - 1 - Rw + rr;
                 tmp[u] = (rr < span && cok && i >= 0 && i < H) ? __ldcg(P + (size_t)i * W + j) : z;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (r0 + u < span) ps.pp[(r0 + u) * kPP + cc] = tmp[u];
+                if (r0w + u < span) ps.pp[(r0w + u) * kPP + cc] = tmp[u];
         }
     }
     cp_async_wait_all();
     __syncwarp();
-    const int j = j0 + lane;
-    const bool colok = j < W;
-    const bool mop = a.pred == 2;
-    const SmemSlice Ps{ps.pp, i0 - 1 - Rw, j0 - 1 - Rw, kPP};
+    const SmemSlice Ps{ps.pp, r0 - 1 - Rw, c0 - 1 - Rw, kPP};
     const GlobalSlice Pg{P, W};
+    int2* Psl = a.psl + (size_t)t * sl;
     unsigned sub = 0, steps = 0;
-    // pure SL: every vertex; MoP: the sampled sites first (for the decision)
-    for (int rr = 0; rr < 32; ++rr) {
-        const int i = i0 + rr;
-        if (i >= H) break;
-        if (!colok) continue;
-        if (mop && !((i % a.n) == 0 && (j % a.n) == 0)) continue;
-        int pu, pv;
-        const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
-                              : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-        const int2 p = make_int2(pu, pv);
-        ps.psl[rr][lane] = p;
-        a.psl[((size_t)t * H + i) * W + j] = p;
-        sub += md > 0;
-        steps += md;
-    }
-    __syncwarp();
-    if (mop) {
-        mop_tile(a, t, i0, j0, ps, Rw);
-        __syncwarp();
-        for (int rr = 0; rr < 32; ++rr) {
-            const int i = i0 + rr;
-            if (i >= H) break;
-            if (!colok || ((i % a.n) == 0 && (j % a.n) == 0)) continue;
-            if (!ps.modes[(rr / a.B) * (32 / a.B) + lane / a.B]) continue;
+    // semi-Lagrangian predictions, lanes over a compact list of sites: every
+    // vertex (pure SL) or the sampled sites (MoP, for the decisions)
+    {
+        const int st = mop ? a.n : 1;
+        const int fr = (st - r0 % st) % st, fc = (st - c0 % st) % st;
+        const int nr = uh > fr ? (uh - fr + st - 1) / st : 0;
+        const int nc = uw > fc ? (uw - fc + st - 1) / st : 0;
+        for (int k = lane; k < nr * nc; k += 32) {
+            const int li = fr + (k / nc) * st, lj = fc + (k % nc) * st;
+            const int i = r0 + li, j = c0 + lj;
             int pu, pv;
             const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
                                   : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-            a.psl[((size_t)t * H + i) * W + j] = make_int2(pu, pv);
+            const int2 p = make_int2(pu, pv);
+            if (mop) ps.psl[li][lj] = p;
+            Psl[(size_t)i * W + j] = p;
+            sub += md > 0;
+            steps += md;
+        }
+    }
+    __syncwarp();
+    if (mop) {
+        mop_unit(a, t, r0, c0, ps, Rw);
+        // the other vertices of the blocks that chose SL, gathered into a list
+        const int nbu = U / a.B;
+        int cnt = 0;
+        for (int base = 0; base < uh * uw; base += 32) {
+            const int k = base + lane;
+            const int li = k / uw, lj = k % uw;
+            const bool need = k < uh * uw && !(((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0) &&
+                              ps.modes[(li / a.B) * nbu + lj / a.B] != 0;
+            const unsigned bal = __ballot_sync(FULL, need);
+            if (need) ps.list[cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(li * 32 + lj);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int m = lane; m < cnt; m += 32) {
+            const unsigned v = ps.list[m];
+            const int i = r0 + (int)(v >> 5), j = c0 + (int)(v & 31u);
+            int pu, pv;
+            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+            Psl[(size_t)i * W + j] = make_int2(pu, pv);
             sub += md > 0;
             steps += md;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sub += __shfl_xor_sync(0xffffffffu, sub, o);
-        steps += __shfl_xor_sync(0xffffffffu, steps, o);
+        sub += __shfl_xor_sync(FULL, sub, o);
+        steps += __shfl_xor_sync(FULL, steps, o);
     }
     if (lane == 0 && sub) {
         atomicAdd(a.counters + 0, (unsigned long long)sub);
         atomicAdd(a.counters + 1, (unsigned long long)steps);
     }
-    warp_publish(a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, 1u);
-    return true;
+    const int nstrips = (H + 31) / 32;
+    warp_publish_add(a.prep_done + ((size_t)t * nstrips + (r0 >> 5)) * a.nchunks + (c0 >> 5), 1u);
 }
 
-// prep(t, s, g): the tiles c = g, g + PG, g + 2 PG, ... of strip s, in order.
-__device__ bool prep_item(const SliceArgs& a, int t, int s, int g, WarpSmem& sm) {
-    for (int c = g; c < a.nchunks; c += a.prep_groups)
-        if (!prep_tile(a, t, s, c, sm)) return false;
-    return true;
+// Units of slice t (t >= 1) that became ready when strip s of slice t-1
+// advanced from column p0 to p1.  Unit (ur, uc) needs slice t-1 final up to
+// row ur*U + U - 1 + R (strip s_req, whose progress bounds those of the strips
+// above) and column uc*U + U - 1 + R.  Each unit is queued exactly once.
+__device__ void enqueue_units(const SliceArgs& a, int t, int s, unsigned p0, unsigned p1) {
+    const int U = a.U, R = a.R, W = a.W, lane = threadIdx.x;
+    const int nstrips = (a.H + 31) / 32;
+    auto ready_cols = [&](unsigned p) -> int {  // unit columns whose need is met at progress p
+        if ((int)p >= W) return a.nuc;
+        const int v = (int)p - U - R;
+        return v < 0 ? 0 : min(a.nuc, v / U + 1);
+    };
+    auto first_row = [&](int sx) -> int {  // first unit row that needs strip sx or below
+        const int num = 32 * sx - U + 1 - R;
+        return num <= 0 ? 0 : min(a.nur, (num + U - 1) / U);
+    };
+    const int uc0 = ready_cols(p0), uc1 = ready_cols(p1);
+    const int ur0 = first_row(s), ur1 = s + 1 < nstrips ? first_row(s + 1) : a.nur;
+    if (uc1 <= uc0 || ur1 <= ur0) return;
+    const int ncol = uc1 - uc0;
+    const unsigned cnt = (unsigned)((ur1 - ur0) * ncol);
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.qtail, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned m = lane; m < cnt; m += 32) {
+        const int ur = ur0 + (int)(m / ncol), uc = uc0 + (int)(m % ncol);
+        const unsigned id = ((unsigned)(t - 1) * (unsigned)a.nur + (unsigned)ur) * (unsigned)a.nuc + (unsigned)uc;
+        if (base + m < a.n_units) st_release(a.qslot + base + m, id + 1u);
+        else atomicCAS(a.status, 0, kStatusCorrupt);  // cannot happen: every unit is queued once
+    }
+}
+
+// A prep warp: takes queue positions in order and works each unit once its
+// slot is filled.
+__device__ void prep_loop(const SliceArgs& a, WarpSmem& sm) {
+    for (;;) {
+        unsigned pos = 0;
+        int stop = 0;
+        if (threadIdx.x == 0) {
+            pos = atomicAdd(a.qhead, 1u);
+            stop = *(volatile int*)a.status != 0;
+        }
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (pos >= a.n_units || stop) return;
+        const unsigned v = warp_wait_geq(a, a.qslot + pos, 1u);
+        if (!v) return;
+        const unsigned id = v - 1u;
+        const int uc = (int)(id % (unsigned)a.nuc);
+        const unsigned rest = id / (unsigned)a.nuc;
+        const int ur = (int)(rest % (unsigned)a.nur);
+        const int t = (int)(rest / (unsigned)a.nur) + 1;
+        prep_unit(a, t, ur * a.U, uc * a.U, sm);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -546,12 +634,15 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const int nbw = 32 / a.B;
     int2 left = make_int2(0, 0), up = left, res = left;
     int fetched = 0;  // border columns staged in sm.border
+    const bool feeds = a.n_units > 0 && t + 1 < a.T;  // queues the prep units of slice t+1
+    unsigned published = 0;
     for (int k = 0; k < W + 31; ++k) {
         const int j = k - lane;
         if ((k & 31) == 0 && k < W) {
             const int c = k >> 5;
             if (need_sl) {
-                if (!warp_wait_geq(a, a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, 1u)) return false;
+                if (!warp_wait_geq(a, a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, tile_units(a, i0, 32 * c)))
+                    return false;
             } else if (t >= 1) {
                 // the strip of slice t-1 must have passed the chunk (Lorenzo and faces read it)
                 if (!warp_wait_geq(a, prog_below, (unsigned)min(W, 32 * c + 32))) return false;
@@ -644,8 +735,11 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         left = res;
         // the last lane finished column k - 31: publish every kPublishEvery columns
         const int jl = k - 31;
-        if (jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1))
+        if (jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1)) {
             warp_publish(prog_me, (unsigned)(jl + 1));
+            if (feeds) enqueue_units(a, t + 1, s, published, (unsigned)(jl + 1));
+            published = (unsigned)(jl + 1);
+        }
     }
     return true;
 }
@@ -653,9 +747,12 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
 __global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem& sm = *reinterpret_cast<WarpSmem*>(smem_raw);
+    if ((int)blockIdx.x < a.prep_warps) {
+        prep_loop(a, sm);
+        return;
+    }
     const int nstrips = (a.H + 31) / 32;
-    const unsigned per_strip = (unsigned)a.prep_groups + 1u;
-    const unsigned total = (unsigned)nstrips * per_strip * (unsigned)a.T;
+    const unsigned total = (unsigned)nstrips * (unsigned)a.T;
     for (;;) {
         unsigned item = 0;
         int stop = 0;
@@ -666,17 +763,8 @@ __global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
         item = __shfl_sync(0xffffffffu, item, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
         if (item >= total || stop) return;
-        const int2 ts = __ldg(a.order + item / per_strip);
-        const int t = ts.x, s = ts.y;
-        const int g = (int)(item % per_strip);
-        // slice 0 has no semi-Lagrangian work: its prep items are empty
-        bool ok = true;
-        if (g < a.prep_groups) {
-            if (t >= 1) ok = prep_item(a, t, s, g, sm);
-        } else {
-            ok = wave_item(a, t, s, sm);
-        }
-        if (!ok) return;
+        const int2 ts = __ldg(a.order + item);
+        if (!wave_item(a, ts.x, ts.y, sm)) return;
     }
 }
 
@@ -709,10 +797,15 @@ cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s) 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    // with SL or MoP every prep tile is an item of its own
+    // with SL or MoP a share of the warps works the prep queue
     SliceArgs b = a;
     const int warps = nsm * per_sm;
-    b.prep_groups = (a.pred == 0 || a.T < 2 || a.eps_int <= 0) ? 0 : a.nchunks;
+    b.prep_warps = 0;
+    if (a.n_units > 0) {
+        b.prep_warps = (int)((long long)warps * (a.pred == 1 ? kPrepShareSL : kPrepShareMoP) / 100);
+        if (b.prep_warps < 1) b.prep_warps = 1;
+        if (b.prep_warps > warps - 1) b.prep_warps = warps - 1;
+    }
     encode_pipeline_kernel<<<warps, 32, smem, s>>>(b);
     return cudaGetLastError();
 }
