@@ -360,7 +360,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     int *d_status, *d_xiout = nullptr;
     int2 *d_psl, *d_cls;
     unsigned* d_clsm;
-    unsigned *d_prog, *d_prep, *d_ticket;
+    unsigned *d_prep, *d_ticket;
     CPT_CUDA(ar.alloc(&d_qxi, N));
     CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
     CPT_CUDA(ar.alloc(&d_sym, N));
@@ -368,13 +368,11 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_clsm, N));
     CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
     CPT_CUDA(ar.alloc(&d_status, 1));
-    CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
     CPT_CUDA(ar.alloc(&d_prep, (size_t)T * nstrips * nchunks));
     CPT_CUDA(ar.alloc(&d_ticket, 1));
     if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
     CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
-    CPT_CUDA(cudaMemsetAsync(d_prog, 0, sizeof(unsigned) * T * nstrips, s));
     CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * T * nstrips * nchunks, s));
     CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
     SliceArgs a;
@@ -388,7 +386,6 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     a.qxi = d_qxi;
     a.sym = d_sym;
     a.xi_out = d_xiout;
-    a.progress = d_prog;
     a.prep_done = d_prep;
     a.ticket = d_ticket;
     a.status = d_status;
@@ -453,6 +450,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     st.launches[3]++;
     tm.end();
     tm.begin(4);
+    CPT_CUDA(cudaMemsetAsync(d_qhat, 0, NV * sizeof(int32_t), s));  // no reconstruction word present
     CPT_CUDA(launch_encode_pipeline(a, nsm, s));
     st.launches[4]++;
     tm.end();
@@ -557,6 +555,8 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(cudaEventRecord(ev1, s));
     CPT_CUDA(cudaStreamSynchronize(s));
     CPT_CUDA(cudaGetLastError());
+    if (dbg && dbg->qhat)  // reconstruction words -> values
+        for (size_t v = 0; v < N; ++v) dbg->qhat[2 * v + 1] ^= kQhatTag;
 
     uint8_t* buf = static_cast<uint8_t*>(std::malloc(bs.b.size()));
     if (!buf) return fail(CPT_ERR_OOM, "host allocation failed");

@@ -19,10 +19,14 @@ struct VerifyOut {
     double sq_err;
 };
 
+// The encoder's reconstruction array holds (x, y ^ kQhatTag) per vertex: a
+// written word is told from the zeroed array by bits 30 and 31 of y.
+constexpr int kQhatTag = 0x40000000;
+
 // Arguments of the encoder pipeline (one persistent launch over all slices).
 struct SliceArgs {
     const int2* q;          // original fixed point [T][H][W]
-    int2* qhat;             // reconstruction [T][H][W]
+    int2* qhat;             // reconstruction words [T][H][W] (tagged, zeroed before the launch)
     const uint16_t* mask;   // crossed-face masks [T][H][W]
     const int2* cls;        // [T][H][W] (bound over certain faces, faces needing the full Alg. 2)
     const unsigned* cls_m;  // [T][H][W] faces needing only the M = 0 check
@@ -31,7 +35,6 @@ struct SliceArgs {
     uint8_t* qxi;           // [T][H][W] bound codes
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
-    unsigned* progress;     // [T][nstrips] wavefront columns published per strip
     unsigned* prep_done;    // [T][nstrips][nchunks] prep units finished per 32 x 32 tile
     unsigned* ticket;       // wavefront item counter
     unsigned* qslot;        // [n_units] ready queue of prep units (unit id + 1, 0 = not yet filled)

@@ -37,7 +37,7 @@ namespace cpt {
 constexpr int kPublishEvery = 16;  // columns between progress publications of a strip
 constexpr int kPrepShareSL = 50;   // percent of the warps working prep units (SL)
 constexpr int kPrepShareMoP = 45;  // (MoP)
-constexpr int kHalo = 34;          // row stride of the staged slice t-1 halo tile
+constexpr int kNoSL = (int)0x80000000;  // psl marker: the block keeps 3DL (no prediction reaches it)
 
 __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, int j) {
     unsigned tm = t > 0, tp = t + 1 < T, im = i > 0, ip = i + 1 < H, jm = j > 0, jp = j + 1 < W;
@@ -131,16 +131,87 @@ __device__ __forceinline__ unsigned warp_wait_geq(const SliceArgs& a, const unsi
 }
 
 // ---------------------------------------------------------------------------
+// Reconstruction words.  Every reconstruction is written once, as one 64-bit
+// word (x, y ^ kQhatTag) with a strong store; bits 30 and 31 of its y half
+// differ (|y| < 2^30), those of the zeroed array do not.  A reader polls the
+// word itself: the value and its presence travel together, so no fence is
+// needed between the wave that writes it and the waves and prep units that
+// read it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_word(const int2* p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p));
+    return w;
+}
+__device__ __forceinline__ void st_word(int2* p, int2 v) {
+    const unsigned long long w =
+        (unsigned long long)(unsigned)v.x | ((unsigned long long)(unsigned)(v.y ^ kQhatTag) << 32);
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ bool word_ready(unsigned long long w) {
+    const int y = (int)(w >> 32);
+    return ((y >> 30) ^ (y >> 31)) & 1;
+}
+__device__ __forceinline__ int2 word_value(unsigned long long w) {
+    return make_int2((int)(unsigned)w, (int)(w >> 32) ^ kQhatTag);
+}
+
+// Re-reads *p until its word is ready, on the lanes with need; false (and the
+// status word set) when the time limit expires or another warp failed.
+__device__ bool poll_word(const SliceArgs& a, const int2* p, bool need, unsigned long long& w) {
+    if (__all_sync(0xffffffffu, !need || word_ready(w))) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (need && !word_ready(w)) w = ld_word(p);
+        if (__all_sync(0xffffffffu, !need || word_ready(w))) return true;
+        const bool late = (long long)(global_ns() - t0) > a.timeout_ns;
+        const bool failed = *(volatile int*)a.status != 0;
+        if (__any_sync(0xffffffffu, late || failed)) {
+            if (threadIdx.x == 0 && !failed) atomicCAS(a.status, 0, kStatusTimeout);
+            return false;
+        }
+        __nanosleep(32);
+    }
+}
+
+// Slice t-1 read through L2 for a semi-Lagrangian reach beyond the staged
+// window: each word is awaited (it is present once the unit is queued; the
+// wait is a bounded safeguard that sets the status word).
+struct TaggedSlice {
+    const int2* P;
+    int W;
+    int* status;
+    long long timeout_ns;
+    __device__ int2 at(int i, int j) const {
+        const int2* p = P + (size_t)i * W + j;
+        unsigned long long w = ld_word(p);
+        if (!word_ready(w)) {
+            const unsigned long long t0 = global_ns();
+            while (!word_ready(w)) {
+                if ((long long)(global_ns() - t0) > timeout_ns || *(volatile int*)status != 0) {
+                    atomicCAS(status, 0, kStatusTimeout);
+                    return make_int2(0, 0);
+                }
+                __nanosleep(32);
+                w = ld_word(p);
+            }
+        }
+        return word_value(w);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // shared memory of one worker warp (one warp per CTA)
 // ---------------------------------------------------------------------------
-struct ChunkBuf {
-    int2 cls[32][32];       // (bound over certain faces, faces needing the full Alg. 2)
-    unsigned cm[32][32];    // faces needing only the M = 0 check
-    int2 qv[33][kHalo];     // q(t): rows/cols 0..32 of the chunk
-    int2 qn[33][kHalo];     // q(t+1): rows/cols 0..32 of the chunk
-    int2 psl[32][32];
-    int2 qp[33][kHalo];     // reconstruction of slice t-1, rows/cols -1..31 of the chunk
-    uint8_t modes[64];      // MoP modes of the blocks covering the chunk
+// Read-only inputs of a wave, staged through a ring of four 16-column
+// sub-chunks: column j of the strip sits in ring column j & 63 (row pitch
+// kRing spreads the anti-diagonal reads over the banks).
+constexpr int kRing = 66;
+struct WaveSmem {
+    int2 cls[32][kRing];      // (bound over certain faces, faces needing the full Alg. 2)
+    unsigned cm[32][kRing];   // faces needing only the M = 0 check
+    int2 qv[33][kRing];       // q(t): rows 0..32 of the strip
+    int2 qn[33][kRing];       // q(t+1): rows 0..32 of the strip
 };
 constexpr int kStageR = 8;                 // largest SL reach served from the staged window
 constexpr int kPP = 34 + 2 * kStageR;      // pitch of the staged slice t-1 window
@@ -155,10 +226,9 @@ struct PrepSmem {
 };
 struct WarpSmem {
     union {
-        ChunkBuf buf[2];
+        WaveSmem wave;
         PrepSmem prep;
     };
-    int2 border[64];          // ring of the row above the strip
     int2 nbs[32][15];         // per-lane neighbour values for the face loops
 };
 
@@ -336,8 +406,10 @@ __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
     if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
 }
 
-// One prep unit: the U x U vertices from (r0, c0) of slice t >= 1.  Slice t-1
-// is final around it (the unit entered the ready queue after that).
+// One prep unit: the U x U vertices from (r0, c0) of slice t >= 1 (it enters
+// the ready queue once slice t-1 is reconstructed around it).  Leaves in psl
+// the SL prediction of every vertex that uses SL, and with MoP the marker
+// kNoSL on the vertices of blocks that keep 3DL.
 __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& sm) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x, H = a.H, W = a.W, U = a.U;
@@ -360,30 +432,36 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     // slice t-1 around the unit, widened by the reach when it fits the window
-    // (L2 loads, several rows in flight)
+    // (reconstruction words, several rows in flight)
     const bool staged = U + 2 + 2 * a.R <= kPP;
     const int Rw = staged ? a.R : 0;
     const int span = U + 2 + 2 * Rw;
     const int2* P = a.qhat + (size_t)(t - 1) * sl;
-    for (int cc = lane; cc < span; cc += 32) {
-        const int j = c0 - 1 - Rw + cc;
-        const bool cok = j >= 0 && j < W;
-        for (int r0w = 0; r0w < span; r0w += 8) {
-            int2 tmp[8];
+    for (int r0w = 0; r0w < span; r0w += 8) {
+        for (int cb = 0; cb < span; cb += 32) {
+            const int cc = cb + lane;
+            const int j = c0 - 1 - Rw + cc;
+            const bool cok = cc < span && j >= 0 && j < W;
+            unsigned long long tmp[8];
+            bool need[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int rr = r0w + u, i = r0 - 1 - Rw + rr;
-                tmp[u] = (rr < span && cok && i >= 0 && i < H) ? __ldcg(P + (size_t)i * W + j) : z;
+                need[u] = rr < span && cok && i >= 0 && i < H;
+                tmp[u] = need[u] ? ld_word(P + (size_t)i * W + j) : 0ull;
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (r0w + u < span) ps.pp[(r0w + u) * kPP + cc] = tmp[u];
+            for (int u = 0; u < 8; ++u) {
+                const int i = r0 - 1 - Rw + r0w + u;
+                if (!poll_word(a, P + (size_t)(need[u] ? i : 0) * W + (need[u] ? j : 0), need[u], tmp[u])) return;
+                if (r0w + u < span && cc < span) ps.pp[(r0w + u) * kPP + cc] = need[u] ? word_value(tmp[u]) : z;
+            }
         }
     }
     cp_async_wait_all();
     __syncwarp();
     const SmemSlice Ps{ps.pp, r0 - 1 - Rw, c0 - 1 - Rw, kPP};
-    const GlobalSlice Pg{P, W};
+    const TaggedSlice Pg{P, W, a.status, a.timeout_ns};
     int2* Psl = a.psl + (size_t)t * sl;
     unsigned sub = 0, steps = 0;
     // semi-Lagrangian predictions, lanes over a compact list of sites: every
@@ -422,6 +500,11 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
             cnt += __popc(bal);
         }
         __syncwarp();
+        // vertices of the blocks that kept 3DL: the marker instead of a prediction
+        for (int k = lane; k < uh * uw; k += 32) {
+            const int li = k / uw, lj = k % uw;
+            if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+        }
         for (int m = lane; m < cnt; m += 32) {
             const unsigned v = ps.list[m];
             const int i = r0 + (int)(v >> 5), j = c0 + (int)(v & 31u);
@@ -447,9 +530,11 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
 }
 
 // Units of slice t (t >= 1) that became ready when strip s of slice t-1
-// advanced from column p0 to p1.  Unit (ur, uc) needs slice t-1 final up to
-// row ur*U + U - 1 + R (strip s_req, whose progress bounds those of the strips
-// above) and column uc*U + U - 1 + R.  Each unit is queued exactly once.
+// advanced from column p0 to p1 (its last row done up to column p1 - 1).
+// Unit (ur, uc) needs slice t-1 up to row ur*U + U - 1 + R (strip s_req; the
+// strips above are further ahead) and column uc*U + U - 1 + R.  Each unit is
+// queued exactly once.  The queue orders the work only: a unit still awaits
+// each reconstruction word it reads.
 __device__ void enqueue_units(const SliceArgs& a, int t, int s, unsigned p0, unsigned p1) {
     const int U = a.U, R = a.R, W = a.W, lane = threadIdx.x;
     const int nstrips = (a.H + 31) / 32;
@@ -473,7 +558,7 @@ __device__ void enqueue_units(const SliceArgs& a, int t, int s, unsigned p0, uns
     for (unsigned m = lane; m < cnt; m += 32) {
         const int ur = ur0 + (int)(m / ncol), uc = uc0 + (int)(m % ncol);
         const unsigned id = ((unsigned)(t - 1) * (unsigned)a.nur + (unsigned)ur) * (unsigned)a.nuc + (unsigned)uc;
-        if (base + m < a.n_units) st_release(a.qslot + base + m, id + 1u);
+        if (base + m < a.n_units) st_relaxed(a.qslot + base + m, id + 1u);
         else atomicCAS(a.status, 0, kStatusCorrupt);  // cannot happen: every unit is queued once
     }
 }
@@ -505,188 +590,159 @@ __device__ void prep_loop(const SliceArgs& a, WarpSmem& sm) {
 // ---------------------------------------------------------------------------
 // wave(t, s)
 // ---------------------------------------------------------------------------
-// Stages chunk c of strip s (rows i0..i0+31, columns 32c..32c+31) into b.
-__device__ void stage_chunk(const SliceArgs& a, int t, int i0, int c, ChunkBuf& b, bool need_sl) {
-    const int lane = threadIdx.x, H = a.H, W = a.W, T = a.T;
-    const int j = 32 * c + lane;
-    const size_t sl = (size_t)H * W;
-    const int2 z = make_int2(0, 0);
-    // inputs written before this kernel: asynchronous copies
-    const int2* Qt = a.q + (size_t)t * sl;
-    const int2* Qn = a.q + (size_t)(t + 1 < T ? t + 1 : t) * sl;
-    const size_t vb = (size_t)t * sl;
-    for (int rr = 0; rr < 33; ++rr) {
+// Stages sub-chunk g (columns 16g..16g+15) of the strip's read-only inputs
+// into its ring slot: asynchronous copies, zero outside the slice.
+__device__ __forceinline__ void stage_sub(const SliceArgs& a, WaveSmem& w, const int2* cls, const unsigned* cm,
+                                          const int2* Qt, const int2* Qn, bool qn_ok, int i0, int g) {
+    const int lane = threadIdx.x, H = a.H, W = a.W;
+    const int j = 16 * g + (lane & 15), rc = j & 63;
+    const bool cok = j < W;
+    for (int rr = lane >> 4; rr < 33; rr += 2) {
         const int i = i0 + rr;
-        const bool ok = i < H && j < W;
+        const bool ok = cok && i < H;
         const size_t off = ok ? (size_t)i * W + j : 0;
         if (rr < 32) {
-            cp_async8(&b.cls[rr][lane], a.cls + vb + off, ok);
-            cp_async4(&b.cm[rr][lane], a.cls_m + vb + off, ok);
+            cp_async8(&w.cls[rr][rc], cls + off, ok);
+            cp_async4(&w.cm[rr][rc], cm + off, ok);
         }
-        cp_async8(&b.qv[rr][lane], Qt + off, ok);
-        cp_async8(&b.qn[rr][lane], Qn + off, ok && t + 1 < T);
-        if (lane == 0) {
-            const int j32 = 32 * c + 32;
-            const bool ok32 = i < H && j32 < W;
-            const size_t off32 = ok32 ? (size_t)i * W + j32 : 0;
-            cp_async8(&b.qv[rr][32], Qt + off32, ok32);
-            cp_async8(&b.qn[rr][32], Qn + off32, ok32 && t + 1 < T);
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    // data written by this kernel: L2 loads, eight rows in flight at a time
-    if (t >= 1) {
-        const int2* P = a.qhat + (size_t)(t - 1) * sl;
-        const int jj = 32 * c - 1 + lane;  // columns -1..30 of the chunk
-        const int j31 = 32 * c + 31;
-        for (int r0 = 0; r0 < 33; r0 += 11) {
-            int2 tmp[11], t31[11];
-#pragma unroll
-            for (int u = 0; u < 11; ++u) {
-                const int i = i0 - 1 + r0 + u;
-                const bool rok = i >= 0 && i < H;
-                tmp[u] = (rok && jj >= 0 && jj < W) ? __ldcg(P + (size_t)i * W + jj) : z;
-                t31[u] = (lane == 0 && rok && j31 < W) ? __ldcg(P + (size_t)i * W + j31) : z;
-            }
-#pragma unroll
-            for (int u = 0; u < 11; ++u) {
-                b.qp[r0 + u][lane] = tmp[u];
-                if (lane == 0) b.qp[r0 + u][32] = t31[u];
-            }
-        }
-    } else {
-        for (int rr = 0; rr < 33; ++rr) {
-            b.qp[rr][lane] = z;
-            if (lane == 0) b.qp[rr][32] = z;
-        }
-    }
-    if (need_sl) {
-        for (int r0 = 0; r0 < 32; r0 += 8) {
-            int2 tmp[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = i0 + r0 + u;
-                tmp[u] = (i < H && j < W) ? __ldcg(a.psl + vb + (size_t)i * W + j) : z;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) b.psl[r0 + u][lane] = tmp[u];
-        }
-    }
-    if (a.pred == 2 && t >= 1) {
-        const int nbw = 32 / a.B;
-        for (int k = lane; k < nbw * nbw; k += 32) {
-            const int by = (i0 + (k / nbw) * a.B) / a.B, bx = (32 * c + (k % nbw) * a.B) / a.B;
-            b.modes[k] = (by < a.nby && bx < a.nbx) ? __ldcg(a.modes + ((size_t)t * a.nby + by) * a.nbx + bx) : 0;
-        }
-    }
-    cp_async_wait_all();
-    __syncwarp();
-    // The 10 flagged faces through slice t-1 and original values only (bits
-    // 0..9) no longer depend on the wavefront: slice t-1 is final.  Evaluate
-    // them now and fold them into the staged bound.
-    if (t >= 1) {
-        for (int rr = 0; rr < 32; ++rr) {
-            const int i = i0 + rr;
-            if (i >= H || j >= W) break;
-            int2 cl = b.cls[rr][lane];
-            const unsigned mm = b.cm[rr][lane] & 0x3FFu, mf = (unsigned)cl.y & 0x3FFu;
-            if (cl.x <= 0 || (mm | mf) == 0) continue;
-            int2 nb[14];
-            nb[0] = b.qp[rr][lane];
-            nb[1] = b.qp[rr][lane + 1];
-            nb[2] = b.qp[rr + 1][lane];
-            nb[3] = b.qp[rr + 1][lane + 1];
-            nb[7] = b.qv[rr][lane + 1];
-            nb[8] = b.qv[rr + 1][lane];
-            nb[9] = b.qv[rr + 1][lane + 1];
-            nb[10] = b.qn[rr][lane];
-            nb[11] = b.qn[rr][lane + 1];
-            nb[12] = b.qn[rr + 1][lane];
-            nb[13] = b.qn[rr + 1][lane + 1];
-            const int2 qv = b.qv[rr][lane];
-            int xi = cl.x, bit = 0;
-#define CPT_T1_FACE(fa, fb)                                                                         \
-    if (bit < 10) {                                                                                \
-        if ((mf >> bit) & 1u) xi = min_alg2(xi, nb[fa].x, nb[fa].y, nb[fb].x, nb[fb].y, qv.x, qv.y); \
-        else if (((mm >> bit) & 1u) && m_zero(nb[fa], nb[fb], qv)) xi = 0;                          \
-    }                                                                                              \
-    ++bit;
-            CPT_UNC_FACES(CPT_T1_FACE)
-#undef CPT_T1_FACE
-            cl.x = xi;
-            b.cls[rr][lane] = cl;
-        }
+        cp_async8(&w.qv[rr][rc], Qt + off, ok);
+        cp_async8(&w.qn[rr][rc], Qn + off, ok && qn_ok);
     }
 }
 
+// wave(t, s).  Lane l owns row i = 32s + l and at step k handles column
+// j = k - l.  Its neighbours (indices of the 14-vertex neighbourhood):
+//   0..3   slice t-1 at (i-1, j-1), (i-1, j), (i, j-1), (i, j): own words read
+//          one step ahead, kept for two more steps, the row above from lane
+//          l-1 by shuffle (lane 0 reads row i-1 itself)
+//   4..6   (i-1, j-1), (i-1, j), (i, j-1) of slice t: registers and shuffles,
+//          lane 0 reads row i-1 (written by wave(t, s-1)) one step ahead
+//   7..13  original values from the staged ring.
+// All 24 uncertain faces are evaluated here with the actual reconstructions.
 __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x, H = a.H, W = a.W;
-    const int nstrips = (H + 31) / 32;
+    const int lane = threadIdx.x, H = a.H, W = a.W, T = a.T;
     const int i0 = 32 * s, i = i0 + lane;
     const bool rowok = i < H;
-    const size_t base = (size_t)t * H * W;
-    const unsigned* prog_prev = a.progress + (size_t)t * nstrips + (s > 0 ? s - 1 : 0);
-    const unsigned* prog_below = a.progress + (size_t)(t > 0 ? t - 1 : 0) * nstrips + s;
-    unsigned* prog_me = a.progress + (size_t)t * nstrips + s;
-    const bool need_sl = t >= 1 && a.eps_int > 0 && a.pred != 0;
-    const bool sl_all = t >= 1 && a.pred == 1;
-    const int nbw = 32 / a.B;
-    int2 left = make_int2(0, 0), up = left, res = left;
-    int fetched = 0;  // border columns staged in sm.border
-    const bool feeds = a.n_units > 0 && t + 1 < a.T;  // queues the prep units of slice t+1
+    const size_t sl = (size_t)H * W, base = (size_t)t * sl;
+    WaveSmem& w = sm.wave;
+    const int2* Qt = a.q + base;
+    const int2* Qn = a.q + (t + 1 < T ? base + sl : base);
+    const int2* cls = a.cls + base;
+    const unsigned* cm = a.cls_m + base;
+    const int2* Pm = a.qhat + (t >= 1 ? base - sl : base);  // slice t-1
+    int2* Pc = a.qhat + base;                                // slice t
+    const int2* Psl = a.psl + base;
+    const bool has_prev = t >= 1, has_above = s > 0;
+    const bool need_sl = has_prev && a.n_units > 0;  // SL predictions present for this slice
+    const bool mop = a.pred == 2;
+    const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
+    const int nsub = (W + 15) / 16;
+    const int2 z = make_int2(0, 0);
     unsigned published = 0;
+
+    // loads for step kk (column kk - lane)
+    unsigned long long wp = 0, wa = 0, wu = 0;
+    int2 pn = z;
+    auto issue = [&](int kk) {
+        const int jj = kk - lane;
+        const bool col = jj >= 0 && jj < W;
+        wp = 0;
+        wa = 0;
+        wu = 0;
+        if (has_prev && rowok && col) wp = ld_word(Pm + (size_t)i * W + jj);
+        if (lane == 0 && has_above && col) {
+            if (has_prev) wa = ld_word(Pm + (size_t)(i0 - 1) * W + jj);
+            wu = ld_word(Pc + (size_t)(i0 - 1) * W + jj);
+        }
+        if (need_sl && rowok && col) pn = __ldcg(Psl + (size_t)i * W + jj);
+    };
+
+    stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+    if (need_sl && !warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nchunks,
+                                  tile_units(a, i0, 0)))
+        return false;
+    issue(0);
+
+    int2 h0 = z, h1 = z, h2 = z;  // slice t-1 at (i, j), (i, j-1), (i, j-2)
+    int2 a0 = z, a1 = z;          // lane 0: slice t-1 at (i-1, j), (i-1, j-1)
+    int2 left = z, up = z, res = z;
     for (int k = 0; k < W + 31; ++k) {
         const int j = k - lane;
-        if ((k & 31) == 0 && k < W) {
-            const int c = k >> 5;
-            if (need_sl) {
-                if (!warp_wait_geq(a, a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, tile_units(a, i0, 32 * c)))
-                    return false;
-            } else if (t >= 1) {
-                // the strip of slice t-1 must have passed the chunk (Lorenzo and faces read it)
-                if (!warp_wait_geq(a, prog_below, (unsigned)min(W, 32 * c + 32))) return false;
-            }
-            stage_chunk(a, t, i0, c, sm.buf[c & 1], need_sl);
+        const bool col = j >= 0 && j < W;
+        // this step's words (issued one step ago)
+        if (!poll_word(a, Pm + (size_t)(rowok ? i : 0) * W + (col ? j : 0), has_prev && rowok && col, wp)) return false;
+        if (!poll_word(a, Pm + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0),
+                       lane == 0 && has_above && has_prev && col, wa))
+            return false;
+        if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), lane == 0 && has_above && col, wu))
+            return false;
+        const int2 pk = (has_prev && rowok && col) ? word_value(wp) : z;
+        const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(wa) : z;
+        const int2 uk = (lane == 0 && has_above && col) ? word_value(wu) : z;
+        const int2 pslk = pn;
+        // sub-chunk g + 1 of the inputs at step 16g - 1, when sub-chunk g is
+        // first read; its ring slot was last read at step 16g - 2
+        if (((k + 1) & 15) == 0) {
+            const int g = (k + 1) >> 4;
+            __syncwarp();
+            if (g + 1 < nsub) stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, g + 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
         }
-        if (s > 0 && k < W && k >= fetched) {
-            const unsigned seen = warp_wait_geq(a, prog_prev, (unsigned)(k + 1));
-            if (!seen) return false;
-            const int avail = min(min(W, k + 32), (int)seen);
-            const int col = fetched + lane;
-            if (col < avail) sm.border[col & 63] = __ldcg(a.qhat + base + (size_t)(i0 - 1) * W + col);
-            fetched = avail;
-            __syncwarp();
+        // the SL predictions of chunk c before lane 0 reads its first column
+        if (need_sl && ((k + 1) & 31) == 0 && ((k + 1) >> 5) < a.nchunks) {
+            const int c = (k + 1) >> 5;
+            if (!warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nchunks + c,
+                               tile_units(a, i0, 32 * c)))
+                return false;
         }
+        issue(k + 1);
+        // neighbours 0..3
+        h2 = h1;
+        h1 = h0;
+        h0 = pk;
+        a1 = a0;
+        a0 = ak;
+        int2 n0, n1;
+        n1.x = __shfl_up_sync(FULL, h1.x, 1);
+        n1.y = __shfl_up_sync(FULL, h1.y, 1);
+        n0.x = __shfl_up_sync(FULL, h2.x, 1);
+        n0.y = __shfl_up_sync(FULL, h2.y, 1);
+        if (lane == 0) {
+            n1 = a0;
+            n0 = a1;
+        }
+        const int2 n2 = h1, n3 = h0;
+        // neighbours 4..6
         int2 fromprev;
         fromprev.x = __shfl_up_sync(FULL, res.x, 1);
         fromprev.y = __shfl_up_sync(FULL, res.y, 1);
         const int2 upleft = up;
-        if (lane == 0) up = (s > 0 && k < W) ? sm.border[k & 63] : make_int2(0, 0);
-        else up = fromprev;
-        const bool active = rowok && j >= 0 && j < W;
-        if (active) {
-            const ChunkBuf& b = sm.buf[(j >> 5) & 1];
-            const int cj = j & 31;
-            const int2 cl = b.cls[lane][cj];
+        up = lane == 0 ? uk : fromprev;
+        if (rowok && col) {
+            const int rc = j & 63, rn = (j + 1) & 63;
+            const int2 cl = w.cls[lane][rc];
+            const unsigned mf = (unsigned)cl.y, mm = w.cm[lane][rc];
             int xi = cl.x;
-            const int2 qv = b.qv[lane][cj];
-            const int2 n0 = b.qp[lane][cj], n1 = b.qp[lane][cj + 1];
-            const int2 n2 = b.qp[lane + 1][cj], n3 = b.qp[lane + 1][cj + 1];
-            const unsigned mf = (unsigned)cl.y >> 10, mm = b.cm[lane][cj] >> 10;
+            const int2 qv = w.qv[lane][rc];
             if (xi > 0 && (mf | mm)) {
-                // the 14 faces through a raster predecessor (uncertain bits 10..23)
-                const int2 n7 = b.qv[lane][cj + 1], n8 = b.qv[lane + 1][cj], n9 = b.qv[lane + 1][cj + 1];
-                const int2 n10 = b.qn[lane][cj], n11 = b.qn[lane][cj + 1];
-                const int2 n12 = b.qn[lane + 1][cj], n13 = b.qn[lane + 1][cj + 1];
+                const int2 n7 = w.qv[lane][rn], n8 = w.qv[lane + 1][rc], n9 = w.qv[lane + 1][rn];
+                const int2 n10 = w.qn[lane][rc], n11 = w.qn[lane][rn];
+                const int2 n12 = w.qn[lane + 1][rc], n13 = w.qn[lane + 1][rn];
                 const int2 n4 = upleft, n5 = up, n6 = left;
-                // M = 0 checks: branch free, all in registers
+                // M = 0 checks of the 24 faces: branch free, all in registers
                 unsigned hits = 0;
                 int bit = 0;
 #define CPT_NB(k) n##k
-#define CPT_PM(fa, fb)                                                                  \
-    if (bit >= 10) hits |= (m_zero(CPT_NB(fa), CPT_NB(fb), qv) ? 1u : 0u) << (bit - 10); \
+#define CPT_PM(fa, fb)                                                   \
+    hits |= (m_zero(CPT_NB(fa), CPT_NB(fb), qv) ? 1u : 0u) << bit; \
     ++bit;
                 CPT_UNC_FACES(CPT_PM)
 #undef CPT_PM
@@ -699,7 +755,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
                     nb[7] = n7; nb[8] = n8; nb[9] = n9;
                     nb[10] = n10; nb[11] = n11; nb[12] = n12; nb[13] = n13;
                     for (unsigned m = mf; m && xi > 0; m &= m - 1) {
-                        const unsigned pr = unc_pair(__ffs(m) - 1 + 10);
+                        const unsigned pr = unc_pair(__ffs(m) - 1);
                         const int2 p0 = nb[pr & 15u], p1 = nb[pr >> 4];
                         xi = min_alg2(xi, p0.x, p0.y, p1.x, p1.y, qv.x, qv.y);
                     }
@@ -710,11 +766,9 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
             unsigned sym = 0;
             if (code > 0) {
                 int pu, pv;
-                const bool use_sl = sl_all || (need_sl && a.pred == 2 && b.modes[(lane / a.B) * nbw + cj / a.B]);
-                if (use_sl) {
-                    const int2 p = b.psl[lane][cj];
-                    pu = p.x;
-                    pv = p.y;
+                if (need_sl && (!mop || pslk.x != kNoSL)) {
+                    pu = pslk.x;
+                    pv = pslk.y;
                 } else {
                     pu = up.x + left.x + n3.x - upleft.x - n1.x - n2.x + n0.x;
                     pv = up.y + left.y + n3.y - upleft.y - n1.y - n2.y + n0.y;
@@ -724,20 +778,20 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
                 sym = su | (sv << 16);
             }
             const size_t v = base + (size_t)i * W + j;
-            a.qhat[v] = rec;
+            st_word(a.qhat + v, rec);
             a.qxi[v] = (uint8_t)code;
             a.sym[v] = sym;
             if (a.xi_out) a.xi_out[v] = xi;
             res = rec;
         } else {
-            res = make_int2(0, 0);
+            res = z;
         }
         left = res;
-        // the last lane finished column k - 31: publish every kPublishEvery columns
+        // the last lane finished column k - 31: queue the units of slice t+1
+        // that this makes ready
         const int jl = k - 31;
-        if (jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1)) {
-            warp_publish(prog_me, (unsigned)(jl + 1));
-            if (feeds) enqueue_units(a, t + 1, s, published, (unsigned)(jl + 1));
+        if (feeds && jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1)) {
+            enqueue_units(a, t + 1, s, published, (unsigned)(jl + 1));
             published = (unsigned)(jl + 1);
         }
     }

@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(256) face_mask_kernel(const int2* __restrict__
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(ncrossed, (unsigned long long)cnt);
 }
 
-// Verification: recompute the owned-face masks on the reconstruction and
-// compare with the original (slice faces = types 0,1; slab faces = 2..11);
-// also the largest |x_hat - x| with x_hat = qhat * 2^-k in float32.
+// Verification: recompute the owned-face masks on the encoder's reconstruction
+// words and compare with the original (slice faces = types 0,1; slab faces =
+// 2..11); also the largest |x_hat - x| with x_hat = qhat * 2^-k in float32.
 __global__ void __launch_bounds__(256) verify_kernel(const int2* __restrict__ qhat, const uint16_t* __restrict__ mask,
                                                      const float2* __restrict__ uv, int H, int W, int T,
                                                      double inv_scale, VerifyOut* __restrict__ out) {
@@ -117,6 +117,13 @@ __global__ void __launch_bounds__(256) verify_kernel(const int2* __restrict__ qh
     if (i < H && j < W) {
         int2 c[8];
         load_corners(qhat, H, W, T, t, i, j, c);
+        {   // the reconstruction words carry the tag in y (absent corners read as zero)
+            const bool r = j + 1 < W, d = i + 1 < H, n = t + 1 < T;
+            const bool has[8] = {true, r, d, r && d, n, n && r, n && d, n && r && d};
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (has[k]) c[k].y ^= kQhatTag;
+        }
         size_t v = ((size_t)t * H + i) * W + j;
         uint16_t m = owned_face_mask(c, owned_valid(H, W, T, t, i, j));
         unsigned x = (unsigned)(m ^ mask[v]);
