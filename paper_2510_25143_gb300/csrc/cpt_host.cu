@@ -368,12 +368,14 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_clsm, N));
     CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
     CPT_CUDA(ar.alloc(&d_status, 1));
-    CPT_CUDA(ar.alloc(&d_prep, (size_t)T * nstrips * nchunks));
+    const int Uh = (prm->pred == CPT_PRED_MOP && B == 32) ? 32 : 16;  // side of a prep unit
+    const size_t nprep = (size_t)T * nstrips * ((W + Uh - 1) / Uh);
+    CPT_CUDA(ar.alloc(&d_prep, nprep));
     CPT_CUDA(ar.alloc(&d_ticket, 1));
     if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
     CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
-    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * T * nstrips * nchunks, s));
+    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
     CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
     SliceArgs a;
     a.q = reinterpret_cast<const int2*>(d_q);
@@ -409,7 +411,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     }
     a.timeout_ns = 2000000000ll;
     // prep units (SL and MoP): U x U squares of slices 1..T-1, in a ready queue
-    a.U = (prm->pred == CPT_PRED_MOP && B == 32) ? 32 : 16;
+    a.U = Uh;
     a.nur = (H + a.U - 1) / a.U;
     a.nuc = (W + a.U - 1) / a.U;
     a.n_units = 0;

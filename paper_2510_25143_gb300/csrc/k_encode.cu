@@ -34,7 +34,7 @@
 
 namespace cpt {
 
-constexpr int kPublishEvery = 16;  // columns between progress publications of a strip
+constexpr int kPublishEvery = 16;  // steps between checks for prep units made ready
 constexpr int kPrepShareSL = 50;   // percent of the warps working prep units (SL)
 constexpr int kPrepShareMoP = 45;  // (MoP)
 constexpr int kNoSL = (int)0x80000000;  // psl marker: the block keeps 3DL (no prediction reaches it)
@@ -392,10 +392,9 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps
     }
 }
 
-// Prep units waiting for a tile: those of its U x U squares inside the slice.
-__device__ __forceinline__ unsigned tile_units(const SliceArgs& a, int i0, int j0) {
-    const int U = a.U;
-    return (unsigned)(((min(32, a.H - i0) + U - 1) / U) * ((min(32, a.W - j0) + U - 1) / U));
+// Prep units of one unit column of strip i0 / 32: its unit rows inside the slice.
+__device__ __forceinline__ unsigned strip_units(const SliceArgs& a, int i0) {
+    return (unsigned)((min(32, a.H - i0) + a.U - 1) / a.U);
 }
 
 // Release-ordered add: everything this warp wrote before is visible to a
@@ -526,40 +525,49 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
         atomicAdd(a.counters + 1, (unsigned long long)steps);
     }
     const int nstrips = (H + 31) / 32;
-    warp_publish_add(a.prep_done + ((size_t)t * nstrips + (r0 >> 5)) * a.nchunks + (c0 >> 5), 1u);
+    warp_publish_add(a.prep_done + ((size_t)t * nstrips + (r0 >> 5)) * a.nuc + c0 / U, 1u);
 }
 
-// Units of slice t (t >= 1) that became ready when strip s of slice t-1
-// advanced from column p0 to p1 (its last row done up to column p1 - 1).
-// Unit (ur, uc) needs slice t-1 up to row ur*U + U - 1 + R (strip s_req; the
-// strips above are further ahead) and column uc*U + U - 1 + R.  Each unit is
-// queued exactly once.  The queue orders the work only: a unit still awaits
-// each reconstruction word it reads.
-__device__ void enqueue_units(const SliceArgs& a, int t, int s, unsigned p0, unsigned p1) {
-    const int U = a.U, R = a.R, W = a.W, lane = threadIdx.x;
-    const int nstrips = (a.H + 31) / 32;
-    auto ready_cols = [&](unsigned p) -> int {  // unit columns whose need is met at progress p
-        if ((int)p >= W) return a.nuc;
-        const int v = (int)p - U - R;
+// Units of slice t (t >= 1) that became ready while wave(t-1, s) went from
+// step k0 to step k1 (after step k, lane l has finished columns <= k - l).
+// Unit (ur, uc) needs slice t-1 up to row r = min(H-1, ur*U + U - 1 + R) and
+// column c = min(W-1, uc*U + U - 1 + R); rows above r are further ahead.  It
+// is queued by the wave of the strip holding row r, at the step c + (r mod 32)
+// that finishes (r, c): every unit exactly once.  The queue orders the work
+// only: a unit still awaits each reconstruction word it reads.
+__device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) {
+    const int U = a.U, R = a.R, W = a.W, H = a.H, lane = threadIdx.x;
+    const int nstrips = (H + 31) / 32;
+    auto ready_cols = [&](int x) -> int {  // unit columns whose column need is <= x
+        if (x >= W - 1) return a.nuc;
+        const int v = x - U + 1 - R;
         return v < 0 ? 0 : min(a.nuc, v / U + 1);
     };
-    auto first_row = [&](int sx) -> int {  // first unit row that needs strip sx or below
+    auto first_row = [&](int sx) -> int {  // first unit row whose row need is in strip sx or below
         const int num = 32 * sx - U + 1 - R;
         return num <= 0 ? 0 : min(a.nur, (num + U - 1) / U);
     };
-    const int uc0 = ready_cols(p0), uc1 = ready_cols(p1);
     const int ur0 = first_row(s), ur1 = s + 1 < nstrips ? first_row(s + 1) : a.nur;
-    if (uc1 <= uc0 || ur1 <= ur0) return;
-    const int ncol = uc1 - uc0;
-    const unsigned cnt = (unsigned)((ur1 - ur0) * ncol);
+    auto need_lane = [&](int ur) { return min(H - 1, ur * U + U - 1 + R) - 32 * s; };
+    unsigned cnt = 0;
+    for (int ur = ur0; ur < ur1; ++ur) {
+        const int l = need_lane(ur);
+        cnt += (unsigned)max(0, ready_cols(k1 - l) - ready_cols(k0 - l));
+    }
+    if (cnt == 0) return;
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(a.qtail, cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (unsigned m = lane; m < cnt; m += 32) {
-        const int ur = ur0 + (int)(m / ncol), uc = uc0 + (int)(m % ncol);
-        const unsigned id = ((unsigned)(t - 1) * (unsigned)a.nur + (unsigned)ur) * (unsigned)a.nuc + (unsigned)uc;
-        if (base + m < a.n_units) st_relaxed(a.qslot + base + m, id + 1u);
-        else atomicCAS(a.status, 0, kStatusCorrupt);  // cannot happen: every unit is queued once
+    for (int ur = ur0; ur < ur1; ++ur) {
+        const int l = need_lane(ur);
+        const int lo = ready_cols(k0 - l), n = max(0, ready_cols(k1 - l) - lo);
+        for (int m = lane; m < n; m += 32) {
+            const unsigned id =
+                ((unsigned)(t - 1) * (unsigned)a.nur + (unsigned)ur) * (unsigned)a.nuc + (unsigned)(lo + m);
+            if (base + m < a.n_units) st_relaxed(a.qslot + base + m, id + 1u);
+            else atomicCAS(a.status, 0, kStatusCorrupt);  // cannot happen: every unit is queued once
+        }
+        base += (unsigned)n;
     }
 }
 
@@ -639,23 +647,32 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
     const int nsub = (W + 15) / 16;
     const int2 z = make_int2(0, 0);
-    unsigned published = 0;
+    int published = -1;  // last step whose ready units were queued
 
-    // loads for step kk (column kk - lane)
-    unsigned long long wp = 0, wa = 0, wu = 0;
-    int2 pn = z;
-    auto issue = [&](int kk) {
+    // loads for a step, issued two steps ahead (two alternating register sets)
+    struct Pf {
+        unsigned long long wp, wa, wu;  // slice t-1 at (i, j); lane 0: slice t-1 and t at (i-1, j)
+        int2 pn;                        // SL prediction at (i, j)
+    };
+    auto issue = [&](int kk, Pf& f) {
         const int jj = kk - lane;
         const bool col = jj >= 0 && jj < W;
-        wp = 0;
-        wa = 0;
-        wu = 0;
-        if (has_prev && rowok && col) wp = ld_word(Pm + (size_t)i * W + jj);
+        f.wp = 0;
+        f.wa = 0;
+        f.wu = 0;
+        if (has_prev && rowok && col) f.wp = ld_word(Pm + (size_t)i * W + jj);
         if (lane == 0 && has_above && col) {
-            if (has_prev) wa = ld_word(Pm + (size_t)(i0 - 1) * W + jj);
-            wu = ld_word(Pc + (size_t)(i0 - 1) * W + jj);
+            if (has_prev) f.wa = ld_word(Pm + (size_t)(i0 - 1) * W + jj);
+            f.wu = ld_word(Pc + (size_t)(i0 - 1) * W + jj);
         }
-        if (need_sl && rowok && col) pn = __ldcg(Psl + (size_t)i * W + jj);
+        if (need_sl && rowok && col) f.pn = __ldcg(Psl + (size_t)i * W + jj);
+    };
+    // the SL predictions of the unit column starting at column kk, before its
+    // first load (by lane 0)
+    auto await_sl = [&](int kk) -> bool {
+        if (!need_sl || kk % a.U != 0 || kk >= W) return true;
+        const int uc = kk / a.U;
+        return warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nuc + uc, strip_units(a, i0)) != 0;
     };
 
     stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 0);
@@ -664,28 +681,31 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncwarp();
-    if (need_sl && !warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nchunks,
-                                  tile_units(a, i0, 0)))
-        return false;
-    issue(0);
+    Pf fa, fb;
+    fa.pn = fb.pn = z;
+    if (!await_sl(0)) return false;
+    issue(0, fa);
+    if (!await_sl(1)) return false;
+    issue(1, fb);
 
     int2 h0 = z, h1 = z, h2 = z;  // slice t-1 at (i, j), (i, j-1), (i, j-2)
     int2 a0 = z, a1 = z;          // lane 0: slice t-1 at (i-1, j), (i-1, j-1)
     int2 left = z, up = z, res = z;
-    for (int k = 0; k < W + 31; ++k) {
+    auto step = [&](int k, Pf& f) -> bool {
         const int j = k - lane;
         const bool col = j >= 0 && j < W;
-        // this step's words (issued one step ago)
-        if (!poll_word(a, Pm + (size_t)(rowok ? i : 0) * W + (col ? j : 0), has_prev && rowok && col, wp)) return false;
+        // this step's words (issued two steps ago)
+        if (!poll_word(a, Pm + (size_t)(rowok ? i : 0) * W + (col ? j : 0), has_prev && rowok && col, f.wp))
+            return false;
         if (!poll_word(a, Pm + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0),
-                       lane == 0 && has_above && has_prev && col, wa))
+                       lane == 0 && has_above && has_prev && col, f.wa))
             return false;
-        if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), lane == 0 && has_above && col, wu))
+        if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), lane == 0 && has_above && col, f.wu))
             return false;
-        const int2 pk = (has_prev && rowok && col) ? word_value(wp) : z;
-        const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(wa) : z;
-        const int2 uk = (lane == 0 && has_above && col) ? word_value(wu) : z;
-        const int2 pslk = pn;
+        const int2 pk = (has_prev && rowok && col) ? word_value(f.wp) : z;
+        const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(f.wa) : z;
+        const int2 uk = (lane == 0 && has_above && col) ? word_value(f.wu) : z;
+        const int2 pslk = f.pn;
         // sub-chunk g + 1 of the inputs at step 16g - 1, when sub-chunk g is
         // first read; its ring slot was last read at step 16g - 2
         if (((k + 1) & 15) == 0) {
@@ -696,14 +716,8 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
         }
-        // the SL predictions of chunk c before lane 0 reads its first column
-        if (need_sl && ((k + 1) & 31) == 0 && ((k + 1) >> 5) < a.nchunks) {
-            const int c = (k + 1) >> 5;
-            if (!warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nchunks + c,
-                               tile_units(a, i0, 32 * c)))
-                return false;
-        }
-        issue(k + 1);
+        if (!await_sl(k + 2)) return false;
+        issue(k + 2, f);
         // neighbours 0..3
         h2 = h1;
         h1 = h0;
@@ -735,25 +749,28 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
             if (xi > 0 && (mf | mm)) {
                 const int2 n7 = w.qv[lane][rn], n8 = w.qv[lane + 1][rc], n9 = w.qv[lane + 1][rn];
                 const int2 n10 = w.qn[lane][rc], n11 = w.qn[lane][rn];
-                const int2 n12 = w.qn[lane + 1][rc], n13 = w.qn[lane + 1][rn];
+                const int2 n12 = w.qn[lane + 1][rc];  // (the uncertain faces do not use neighbour 13)
                 const int2 n4 = upleft, n5 = up, n6 = left;
-                // M = 0 checks of the 24 faces: branch free, all in registers
+                // M = 0 checks of the 24 faces, branch free: with d = n - q(v),
+                // M = d_a.x d_b.y - d_a.y d_b.x
+#define CPT_D(k) const long long dx##k = n##k.x - qv.x, dy##k = n##k.y - qv.y;
+                CPT_D(0) CPT_D(1) CPT_D(2) CPT_D(3) CPT_D(4) CPT_D(5) CPT_D(6)
+                CPT_D(7) CPT_D(8) CPT_D(9) CPT_D(10) CPT_D(11) CPT_D(12)
+#undef CPT_D
                 unsigned hits = 0;
                 int bit = 0;
-#define CPT_NB(k) n##k
-#define CPT_PM(fa, fb)                                                   \
-    hits |= (m_zero(CPT_NB(fa), CPT_NB(fb), qv) ? 1u : 0u) << bit; \
+#define CPT_PM(fa, fb)                                                       \
+    hits |= (dx##fa * dy##fb == dy##fa * dx##fb ? 1u : 0u) << bit; \
     ++bit;
                 CPT_UNC_FACES(CPT_PM)
 #undef CPT_PM
-#undef CPT_NB
                 if (hits & mm) xi = 0;
                 if (xi > 0 && mf) {
                     int2* nb = sm.nbs[lane];
                     nb[0] = n0; nb[1] = n1; nb[2] = n2; nb[3] = n3;
                     nb[4] = n4; nb[5] = n5; nb[6] = n6;
                     nb[7] = n7; nb[8] = n8; nb[9] = n9;
-                    nb[10] = n10; nb[11] = n11; nb[12] = n12; nb[13] = n13;
+                    nb[10] = n10; nb[11] = n11; nb[12] = n12;
                     for (unsigned m = mf; m && xi > 0; m &= m - 1) {
                         const unsigned pr = unc_pair(__ffs(m) - 1);
                         const int2 p0 = nb[pr & 15u], p1 = nb[pr >> 4];
@@ -789,16 +806,20 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         left = res;
         // the last lane finished column k - 31: queue the units of slice t+1
         // that this makes ready
-        const int jl = k - 31;
-        if (feeds && jl >= 0 && jl < W && ((jl % kPublishEvery) == kPublishEvery - 1 || jl == W - 1)) {
-            enqueue_units(a, t + 1, s, published, (unsigned)(jl + 1));
-            published = (unsigned)(jl + 1);
+        if (feeds && ((k + 1) % kPublishEvery == 0 || k == W + 30)) {
+            enqueue_units(a, t + 1, s, published, k);
+            published = k;
         }
+        return true;
+    };
+    for (int k = 0; k < W + 31; k += 2) {
+        if (!step(k, fa)) return false;
+        if (k + 1 < W + 31 && !step(k + 1, fb)) return false;
     }
     return true;
 }
 
-__global__ void __launch_bounds__(32) encode_pipeline_kernel(SliceArgs a) {
+__global__ void __maxnreg__(168) encode_pipeline_kernel(SliceArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem& sm = *reinterpret_cast<WarpSmem*>(smem_raw);
     if ((int)blockIdx.x < a.prep_warps) {
