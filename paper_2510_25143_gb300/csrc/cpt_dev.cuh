@@ -256,10 +256,76 @@ __device__ __forceinline__ unsigned quantize(int q, int p, int xiq, int& qhat) {
 // Euler substeps; every position is clamped to the domain before sampling;
 // the prediction is floor(p + 0.5).  P = reconstructed slice t-1 [H][W].
 // ---------------------------------------------------------------------------
+//
+// FP64 arithmetic is scarce on this part (about 20 SM cycles per warp
+// instruction, shared by the SM), so the steps that are exact by definition
+// run on the integer pipes from the IEEE binary64 bit layout: integer to
+// double conversion, comparisons of finite values, and floor / fractional
+// part of a non-negative position.  They return the very bits the FP64
+// instructions would; only the rounded products and sums stay in FP64.
+// ---------------------------------------------------------------------------
+// (double)n, exact: sign, exponent from the bit length, mantissa shifted up.
+__device__ __forceinline__ double i2d(int n) {
+    const unsigned neg = n < 0 ? 1u : 0u;
+    const unsigned m = neg ? 0u - (unsigned)n : (unsigned)n;
+    const int e = 31 - __clz(m | 1u);
+    const unsigned long long mant = ((unsigned long long)m << (52 - e)) & 0xFFFFFFFFFFFFFull;
+    const unsigned long long bits =
+        ((unsigned long long)neg << 63) | ((unsigned long long)(e + 1023) << 52) | mant;
+    return m ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// Position clamp to [0, hi] for finite x and hi >= 0: a finite double below
+// zero has the sign bit set (and is not -0.0); non-negative doubles order as
+// their bit patterns do.
 __device__ __forceinline__ double clamp_pos(double x, double hi) {
-    if (x < 0.0) return 0.0;
-    if (x > hi) return hi;
+    const long long b = __double_as_longlong(x);
+    if (b < 0 && b != (long long)0x8000000000000000ull) return 0.0;
+    if (b > __double_as_longlong(hi)) return hi;
     return x;
+}
+
+// |a| > |b| and a <= c for finite doubles, from their bit patterns
+__device__ __forceinline__ bool abs_greater(double a, double b) {
+    return (__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll) > (__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// floor(x) as an int and x - floor(x) (exact) for 0 <= x < 2^31.
+__device__ __forceinline__ int floor_frac(double x, double& frac) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) {  // x < 1 (including zero)
+        frac = __longlong_as_double((long long)b);
+        return 0;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 52 - e;  // fraction bits
+    const int ip = (int)(m >> sh);
+    const unsigned long long f = m & ((1ull << sh) - 1ull);  // fraction * 2^sh
+    if (f == 0) {
+        frac = 0.0;
+        return ip;
+    }
+    // f * 2^-sh, normalised: the leading bit of f moves to bit 52
+    const int lz = __clzll((long long)f) - 11;  // f < 2^52: lz >= 1
+    const unsigned long long mf = (f << lz) & 0xFFFFFFFFFFFFFull;
+    const int ef = 1023 + 52 - lz - sh;  // the leading bit of f is bit 52 - lz: value < 1, normal
+    frac = __longlong_as_double((long long)(((unsigned long long)ef << 52) | mf));
+    return ip;
+}
+
+// floor(x) as an int for finite |x| < 2^31
+__device__ __forceinline__ int floor_int(double x) {
+    const long long sb = __double_as_longlong(x);
+    const unsigned long long b = (unsigned long long)sb & 0x7FFFFFFFFFFFFFFFull;
+    const bool neg = sb < 0;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) return (neg && b != 0) ? -1 : 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 52 - e;
+    const int ip = (int)(m >> sh);
+    const bool fr = (m & ((1ull << sh) - 1ull)) != 0;
+    return neg ? (fr ? -ip - 1 : -ip) : ip;
 }
 
 struct Bil {
@@ -267,15 +333,15 @@ struct Bil {
     double w00, w10, w01, w11;
 };
 
+// bilinear stencil of a clamped (non-negative) position
 __device__ __forceinline__ Bil bil_weights(double x, double y, int H, int W) {
     Bil b;
-    double xf = floor(x), yf = floor(y);
-    b.x0 = (int)xf;
-    b.y0 = (int)yf;
+    double fx, fy;
+    b.x0 = floor_frac(x, fx);
+    b.y0 = floor_frac(y, fy);
     b.x1 = b.x0 + 1 < W ? b.x0 + 1 : W - 1;
     b.y1 = b.y0 + 1 < H ? b.y0 + 1 : H - 1;
-    double fx = x - xf, fy = y - yf;
-    double gx = 1.0 - fx, gy = 1.0 - fy;
+    const double gx = __dsub_rn(1.0, fx), gy = __dsub_rn(1.0, fy);
     b.w00 = __dmul_rn(gx, gy);
     b.w10 = __dmul_rn(fx, gy);
     b.w01 = __dmul_rn(gx, fy);
@@ -301,8 +367,8 @@ template <class Slice>
 __device__ __forceinline__ double bil_sample(const Bil& b, const Slice& P, int c) {
     const int2 a00 = P.at(b.y0, b.x0), a10 = P.at(b.y0, b.x1);
     const int2 a01 = P.at(b.y1, b.x0), a11 = P.at(b.y1, b.x1);
-    double f00 = (double)(c ? a00.y : a00.x), f10 = (double)(c ? a10.y : a10.x);
-    double f01 = (double)(c ? a01.y : a01.x), f11 = (double)(c ? a11.y : a11.x);
+    const double f00 = i2d(c ? a00.y : a00.x), f10 = i2d(c ? a10.y : a10.x);
+    const double f01 = i2d(c ? a01.y : a01.x), f11 = i2d(c ? a11.y : a11.x);
     double p = __dadd_rn(__dmul_rn(b.w00, f00), __dmul_rn(b.w10, f10));
     p = __dadd_rn(p, __dmul_rn(b.w01, f01));
     p = __dadd_rn(p, __dmul_rn(b.w11, f11));
@@ -314,39 +380,40 @@ template <class Slice>
 __device__ __forceinline__ int sl_predict(const Slice& P, int H, int W, int i, int j, double cfl_x,
                                           double cfl_y, int& pu, int& pv) {
     const int2 g = P.at(i, j);
-    double du = __dmul_rn((double)g.x, cfl_x);
-    double dv = __dmul_rn((double)g.y, cfl_y);
-    double dinf = fabs(du) > fabs(dv) ? fabs(du) : fabs(dv);
+    const double du = __dmul_rn(i2d(g.x), cfl_x);
+    const double dv = __dmul_rn(i2d(g.y), cfl_y);
+    const double dinf = abs_greater(du, dv) ? fabs(du) : fabs(dv);
+    const double jd = i2d(j), id = i2d(i);
     double xs, ys;
     int mode;
-    const double xmax = (double)(W - 1), ymax = (double)(H - 1);
-    if (dinf <= 2.0) {
-        double xh = clamp_pos(__dsub_rn((double)j, __dmul_rn(0.5, du)), xmax);
-        double yh = clamp_pos(__dsub_rn((double)i, __dmul_rn(0.5, dv)), ymax);
-        Bil b = bil_weights(xh, yh, H, W);
-        double uh = bil_sample(b, P, 0);
-        double vh = bil_sample(b, P, 1);
-        xs = clamp_pos(__dsub_rn((double)j, __dmul_rn(uh, cfl_x)), xmax);
-        ys = clamp_pos(__dsub_rn((double)i, __dmul_rn(vh, cfl_y)), ymax);
+    const double xmax = i2d(W - 1), ymax = i2d(H - 1);
+    if (__double_as_longlong(dinf) <= __double_as_longlong(2.0)) {  // dinf <= 2 (dinf >= 0)
+        const double xh = clamp_pos(__dsub_rn(jd, __dmul_rn(0.5, du)), xmax);
+        const double yh = clamp_pos(__dsub_rn(id, __dmul_rn(0.5, dv)), ymax);
+        const Bil b = bil_weights(xh, yh, H, W);
+        const double uh = bil_sample(b, P, 0);
+        const double vh = bil_sample(b, P, 1);
+        xs = clamp_pos(__dsub_rn(jd, __dmul_rn(uh, cfl_x)), xmax);
+        ys = clamp_pos(__dsub_rn(id, __dmul_rn(vh, cfl_y)), ymax);
         mode = 0;
     } else {
-        double nd = ceil(__ddiv_rn(dinf, 2.0));
-        int N = nd > 32.0 ? 32 : (int)nd;
-        double sx = __ddiv_rn(cfl_x, (double)N), sy = __ddiv_rn(cfl_y, (double)N);
-        xs = (double)j;
-        ys = (double)i;
-        for (int s = 0; s < N; ++s) {
-            Bil b = bil_weights(xs, ys, H, W);
-            double us = bil_sample(b, P, 0);
-            double vs = bil_sample(b, P, 1);
+        const double nd = ceil(__ddiv_rn(dinf, 2.0));
+        const int N = nd > 32.0 ? 32 : (int)nd;
+        const double sx = __ddiv_rn(cfl_x, i2d(N)), sy = __ddiv_rn(cfl_y, i2d(N));
+        xs = jd;
+        ys = id;
+        for (int st = 0; st < N; ++st) {
+            const Bil b = bil_weights(xs, ys, H, W);
+            const double us = bil_sample(b, P, 0);
+            const double vs = bil_sample(b, P, 1);
             xs = clamp_pos(__dsub_rn(xs, __dmul_rn(us, sx)), xmax);
             ys = clamp_pos(__dsub_rn(ys, __dmul_rn(vs, sy)), ymax);
         }
         mode = N;
     }
-    Bil b = bil_weights(xs, ys, H, W);
-    pu = (int)floor(__dadd_rn(bil_sample(b, P, 0), 0.5));
-    pv = (int)floor(__dadd_rn(bil_sample(b, P, 1), 0.5));
+    const Bil b = bil_weights(xs, ys, H, W);
+    pu = floor_int(__dadd_rn(bil_sample(b, P, 0), 0.5));
+    pv = floor_int(__dadd_rn(bil_sample(b, P, 1), 0.5));
     return mode;
 }
 

@@ -436,29 +436,40 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
     const int Rw = staged ? a.R : 0;
     const int span = U + 2 + 2 * Rw;
     const int2* P = a.qhat + (size_t)(t - 1) * sl;
-    for (int r0w = 0; r0w < span; r0w += 8) {
-        for (int cb = 0; cb < span; cb += 32) {
-            const int cc = cb + lane;
+    // asynchronous copies of the reconstruction words (an L1 line read before
+    // a word was written holds zero, which reads as "not ready"), then every
+    // word not ready yet is awaited through L2 and the tags are removed
+    for (int rr = 0; rr < span; ++rr) {
+        const int i = r0 - 1 - Rw + rr;
+        for (int cc = lane; cc < span; cc += 32) {
             const int j = c0 - 1 - Rw + cc;
-            const bool cok = cc < span && j >= 0 && j < W;
-            unsigned long long tmp[8];
-            bool need[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int rr = r0w + u, i = r0 - 1 - Rw + rr;
-                need[u] = rr < span && cok && i >= 0 && i < H;
-                tmp[u] = need[u] ? ld_word(P + (size_t)i * W + j) : 0ull;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = r0 - 1 - Rw + r0w + u;
-                if (!poll_word(a, P + (size_t)(need[u] ? i : 0) * W + (need[u] ? j : 0), need[u], tmp[u])) return;
-                if (r0w + u < span && cc < span) ps.pp[(r0w + u) * kPP + cc] = need[u] ? word_value(tmp[u]) : z;
-            }
+            const bool ok = i >= 0 && i < H && j >= 0 && j < W;
+            cp_async8(&ps.pp[rr * kPP + cc], P + (ok ? (size_t)i * W + j : 0), ok);
         }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     cp_async_wait_all();
     __syncwarp();
+    for (int k = lane; k < span * span; k += 32) {
+        const int rr = k / span, cc = k - rr * span;
+        const int i = r0 - 1 - Rw + rr, j = c0 - 1 - Rw + cc;
+        if (i < 0 || i >= H || j < 0 || j >= W) continue;  // zero-filled
+        int2& e = ps.pp[rr * kPP + cc];
+        unsigned long long wv = (unsigned long long)(unsigned)e.x | ((unsigned long long)(unsigned)e.y << 32);
+        if (!word_ready(wv)) {
+            const int2* p = P + (size_t)i * W + j;
+            const unsigned long long t0 = global_ns();
+            do {
+                if ((long long)(global_ns() - t0) > a.timeout_ns || *(volatile int*)a.status != 0) {
+                    atomicCAS(a.status, 0, kStatusTimeout);
+                    break;
+                }
+                wv = ld_word(p);
+            } while (!word_ready(wv));
+        }
+        e = word_value(wv);
+    }
+    if (__any_sync(FULL, *(volatile int*)a.status != 0)) return;
     const SmemSlice Ps{ps.pp, r0 - 1 - Rw, c0 - 1 - Rw, kPP};
     const TaggedSlice Pg{P, W, a.status, a.timeout_ns};
     int2* Psl = a.psl + (size_t)t * sl;
