@@ -42,12 +42,40 @@ STAGE_BYTES = {
     # classification of the incident faces: read q(t-1), q(t), q(t+1) 8 B each and
     # the masks of t and t-1 2 B each, write 8 B
     "incident_bounds": (36.0, "field"),
-    # the encoder pipeline (MoP/SL tiles and the wavefront) over the whole
-    # field: read the classification 8 B, q(t) 8 B and qhat(t-1) 8 B, write
-    # qhat 8 B, bound code 1 B, symbols 4 B
-    "wavefront": (37.0, "field"),
+    # the encoder pipeline (prep units and the wavefront) over the whole
+    # field: read the classification 8 + 4 B, q(t) 8 B and qhat(t-1) 8 B,
+    # write qhat 8 B, bound code 1 B, symbols 4 B
+    "wavefront": (41.0, "field"),
     "verify": (18.0, "field"),          # read qhat 8 B, mask 2 B, uv 8 B
 }
+
+
+# ncu summaries of the dominant kernel per predictor: DRAM bytes of one
+# launch, valid while the kernel sources hash as they did when captured
+PROFILES = {"mop": os.path.join(ROOT, "profiles", "encode_pipeline_street512_mop.md")}
+KERNEL_SOURCES = ["k_encode.cu", "cpt_dev.cuh", "cpt_internal.h"]
+
+
+def profiled_traffic(pred, workload):
+    """DRAM bytes per launch of the encoder pipeline from the committed ncu
+    summary, or None when there is none for this predictor and workload or the
+    kernel sources changed since it was taken."""
+    import hashlib
+    path = PROFILES.get(pred)
+    if workload != "street512" or not path or not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_25143_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    sha, nbytes = None, None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("source-sha256:"):
+            sha = line.split(":", 1)[1].strip()
+        elif line.startswith("dram-bytes-per-launch:"):
+            nbytes = float(line.split(":", 1)[1])
+    return nbytes if sha == h.hexdigest() else None
 
 
 def peaks():
@@ -112,6 +140,19 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def combine_ranks(ms_local, world, nbytes_per_rank, device="cpu"):
+    """Whole-job throughput of a replicas run: the slowest rank's time per step
+    (max over ranks) and the bytes all ranks processed in it."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * nbytes_per_rank / 1e6 / (ms / 1e3)
 
 
 def cpu_oracle_run(uv_sample, eb, pred, min_seconds):
@@ -203,12 +244,7 @@ def ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nbytes / 1e6 / (ms / 1e3)
+    ms, value = combine_ranks(e0.elapsed_time(e1) / args.steps, world, nbytes, device="cuda")
 
     # end to end through the public API with host buffers: the input is copied
     # from pinned host memory inside each call, the stream read back to host
@@ -223,12 +259,7 @@ def ours(args):
         e2e_blob, _ = step(pinned)
     ee1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = ee0.elapsed_time(ee1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * nbytes / 1e6 / (ms_e2e / 1e3)
+    ms_e2e, e2e_value = combine_ranks(ee0.elapsed_time(ee1) / args.steps, world, nbytes, device="cuda")
 
     # per-stage device time from the library's CUDA events on its stream
     stage_ms = {k: statistics.mean(s["ms_stage"][k] for s in stats) for k in stats[0]["ms_stage"]}
@@ -240,6 +271,7 @@ def ours(args):
     units = H * W * T if unit == "field" else H * W
     per_launch_ms = stage_ms[dom] / stage_launch[dom]
     achieved = per_vertex * units / (per_launch_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.pred, args.workload) if dom == "wavefront" else None
     last = stats[-1]
     ok = (last["verify_mismatch_slice"] == 0 and last["verify_mismatch_slab"] == 0 and last["linf"] <= last["eps"])
     line = {
@@ -255,7 +287,8 @@ def ours(args):
         "faces_per_s": round(last["faces"] / (stage_ms["face_masks"] / 1e3), 1) if stage_ms["face_masks"] else None,
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic,
                      "bytes_per_vertex": per_vertex, "units_per_launch": units,
                      "launch_ms": round(per_launch_ms, 5)},
         "e2e": {"value": round(e2e_value, 2), "unit": "MB/s", "h2d_bytes_per_step": nbytes,
