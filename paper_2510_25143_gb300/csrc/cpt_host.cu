@@ -369,7 +369,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
     CPT_CUDA(ar.alloc(&d_status, 1));
     const int Uh = (prm->pred == CPT_PRED_MOP && B == 32) ? 32 : 16;  // side of a prep unit
-    const size_t nprep = (size_t)T * nstrips * ((W + Uh - 1) / Uh);
+    const size_t nprep = (size_t)T * ((H + Uh - 1) / Uh) * ((W + Uh - 1) / Uh);
     CPT_CUDA(ar.alloc(&d_prep, nprep));
     CPT_CUDA(ar.alloc(&d_ticket, 1));
     if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));

@@ -35,7 +35,7 @@ struct SliceArgs {
     uint8_t* qxi;           // [T][H][W] bound codes
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
-    unsigned* prep_done;    // [T][nstrips][nuc] prep units finished per strip and unit column
+    unsigned* prep_done;    // [T][nur][nuc] 1 once the prep unit is done
     unsigned* ticket;       // wavefront item counter
     unsigned* qslot;        // [n_units] ready queue of prep units (unit id + 1, 0 = not yet filled)
     unsigned* qhead;        // next queue position to take

@@ -392,11 +392,6 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps
     }
 }
 
-// Prep units of one unit column of strip i0 / 32: its unit rows inside the slice.
-__device__ __forceinline__ unsigned strip_units(const SliceArgs& a, int i0) {
-    return (unsigned)((min(32, a.H - i0) + a.U - 1) / a.U);
-}
-
 // Release-ordered add: everything this warp wrote before is visible to a
 // reader that acquires the counter.
 __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
@@ -536,7 +531,8 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
         atomicAdd(a.counters + 1, (unsigned long long)steps);
     }
     const int nstrips = (H + 31) / 32;
-    warp_publish_add(a.prep_done + ((size_t)t * nstrips + (r0 >> 5)) * a.nuc + c0 / U, 1u);
+    (void)nstrips;
+    warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
 }
 
 // Units of slice t (t >= 1) that became ready while wave(t-1, s) went from
@@ -678,12 +674,17 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         }
         if (need_sl && rowok && col) f.pn = __ldcg(Psl + (size_t)i * W + jj);
     };
-    // the SL predictions of the unit column starting at column kk, before its
-    // first load (by lane 0)
+    // the SL predictions of unit (ur, uc) before the first load that reads
+    // them: the unit's first row (lane lu) reaches column uc*U at step uc*U + lu
     auto await_sl = [&](int kk) -> bool {
-        if (!need_sl || kk % a.U != 0 || kk >= W) return true;
-        const int uc = kk / a.U;
-        return warp_wait_geq(a, a.prep_done + ((size_t)t * ((H + 31) / 32) + s) * a.nuc + uc, strip_units(a, i0)) != 0;
+        if (!need_sl) return true;
+        for (int lu = 0; lu < 32 && i0 + lu < H; lu += a.U) {
+            const int c = kk - lu;
+            if (c < 0 || c % a.U != 0 || c >= W) continue;
+            const unsigned* f = a.prep_done + ((size_t)t * a.nur + (i0 + lu) / a.U) * a.nuc + c / a.U;
+            if (!warp_wait_geq(a, f, 1u)) return false;
+        }
+        return true;
     };
 
     stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 0);
