@@ -334,7 +334,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     int32_t *d_q, *d_qhat;
     CPT_CUDA(ar.alloc(&d_q, NV));
     CPT_CUDA(ar.alloc(&d_qhat, NV));
-    launch_to_fixed(d_uv, NV, std::ldexp(1.0, k), d_q, nsm * 8, s);
+    launch_to_fixed(d_uv, NV, k, d_q, nsm * 8, s);
     st.launches[0]++;
     tm.end();
 
@@ -531,7 +531,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         VerifyOut* d_vo;
         CPT_CUDA(ar.alloc(&d_vo, 1));
         CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
-        launch_verify(d_qhat, d_mask, d_uv, H, W, T, std::ldexp(1.0, -k), d_vo, s);
+        launch_verify(d_qhat, d_mask, d_uv, H, W, T, k, d_vo, s);
         st.launches[6]++;
         CPT_CUDA(cudaMemcpyAsync(&vo, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
         tm.end();
@@ -967,7 +967,7 @@ static cpt_status trajectories_impl(const float* uv, const cpt_dims* dims, int32
     CPT_CUDA(ar.alloc(&d_off, N));
     CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(N)));
     CPT_CUDA(cudaMemsetAsync(d_n, 0, 2 * sizeof(unsigned long long), s));
-    launch_to_fixed(d_uv, NV, std::ldexp(1.0, k), d_q, nsm * 8, s);
+    launch_to_fixed(d_uv, NV, k, d_q, nsm * 8, s);
     launch_face_masks(d_q, H, W, T, d_mask, d_n, s);
     launch_face_count(d_mask, N, d_off, s);
     launch_exclusive_scan_u64(d_off, N, d_tmp, s);

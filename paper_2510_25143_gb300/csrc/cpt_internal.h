@@ -91,11 +91,11 @@ struct DecodeArgs {
 
 // k_field.cu
 void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s);
-void launch_to_fixed(const float* uv, size_t n, double scale, int32_t* q, int nblocks, cudaStream_t s);
+void launch_to_fixed(const float* uv, size_t n, int k, int32_t* q, int nblocks, cudaStream_t s);  // q = rint(x 2^k)
 void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, unsigned long long* ncrossed,
                        cudaStream_t s);
-void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T,
-                   double inv_scale, VerifyOut* out, cudaStream_t s);
+void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T, int k,
+                   VerifyOut* out, cudaStream_t s);
 
 // k_encode.cu
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
