@@ -223,7 +223,8 @@ def ours(args):
     kw = dict(eb_mode="rel", pred=args.pred, verify=True)
 
     def step(src):
-        blob, st, _ = cpt.compress(src, eb, **kw)
+        # the stream stays in the library's host buffer (no Python copy)
+        blob, st, _ = cpt.compress(src, eb, copy=False, **kw)
         return blob, st
 
     for _ in range(args.warmup):

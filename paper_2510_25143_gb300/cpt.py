@@ -114,10 +114,41 @@ def _stats_dict(st):
     return d
 
 
+class Stream:
+    """A compressed stream left in the library's buffer (no copy): supports
+    len(), bytes(), memoryview() and numpy(); the buffer goes back to the
+    library when the object is released."""
+
+    def __init__(self, ptr, n):
+        self._ptr, self._n = ptr, n
+        self._arr = (C.c_uint8 * n).from_address(C.addressof(ptr.contents)) if n else (C.c_uint8 * 0)()
+
+    def __len__(self):
+        return self._n
+
+    def __bytes__(self):
+        return bytes(memoryview(self._arr))
+
+    def memoryview(self):
+        return memoryview(self._arr)
+
+    def numpy(self):
+        return np.frombuffer(self._arr, np.uint8)
+
+    def __del__(self):
+        if getattr(self, "_ptr", None):
+            try:
+                lib().cpt_free(self._ptr)
+            except Exception:  # interpreter shutdown
+                pass
+            self._ptr = None
+
+
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
-             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True):
+             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
-    or device).  Returns (bytes, stats dict, debug dict or None)."""
+    or device).  Returns (bytes, stats dict, debug dict or None); with
+    copy=False the stream comes back as a Stream over the library's buffer."""
     ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
     if stream is None:
         stream = dev_stream
@@ -139,8 +170,11 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
     rc = L.cpt_compress_ex(ptr, C.byref(dims), C.byref(prm), C.byref(out), C.byref(n), C.byref(st), dbgp)
     blob = None
     if out:
-        blob = C.string_at(out, n.value)
-        L.cpt_free(out)
+        if copy:
+            blob = C.string_at(out, n.value)
+            L.cpt_free(out)
+        else:
+            blob = Stream(out, n.value)
     if check:
         _check(rc)
     del keep

@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -178,75 +180,134 @@ static void canonical_table(const std::vector<uint8_t>& len, std::vector<uint32_
 // ---------------------------------------------------------------------------
 // byte stream (little endian)
 // ---------------------------------------------------------------------------
-struct Bytes {
-    std::vector<uint8_t> b;
-    void u32(uint32_t x) { for (int k = 0; k < 4; ++k) b.push_back((uint8_t)(x >> (8 * k))); }
+// Little-endian writer into a buffer sized in advance.
+struct Writer {
+    uint8_t* p;
+    size_t n = 0;
+    void u32(uint32_t x) { for (int k = 0; k < 4; ++k) p[n++] = (uint8_t)(x >> (8 * k)); }
     void u64(uint64_t x) { u32((uint32_t)x); u32((uint32_t)(x >> 32)); }
     void f64(double d) { uint64_t x; std::memcpy(&x, &d, 8); u64(x); }
-    void raw(const void* p, size_t n) {
-        const uint8_t* c = static_cast<const uint8_t*>(p);
-        b.insert(b.end(), c, c + n);
-    }
+    void raw(const void* src, size_t m) { std::memcpy(p + n, src, m); n += m; }
 };
 
 static constexpr uint32_t kMaxCodeLen = 24;
 static constexpr int kRadius = 32768;  // quantisation radius (symbol = c + kRadius)
 static constexpr uint32_t kFormat = 1;
 
-// One Huffman-coded stream: histogram -> codebook -> tile offsets -> words.
-template <typename Sym>
-static cpt_status encode_stream(const Sym* d_sym, size_t nsym, uint32_t alphabet, DevArena& ar, cudaStream_t s,
-                                Bytes& out) {
-    unsigned* d_hist;
-    CPT_CUDA(ar.alloc(&d_hist, alphabet));
-    CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * alphabet, s));
-    if constexpr (sizeof(Sym) == 1) launch_hist_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_hist, s);
-    else launch_hist_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_hist, s);
-    std::vector<unsigned> h(alphabet);
-    CPT_CUDA(cudaMemcpyAsync(h.data(), d_hist, sizeof(unsigned) * alphabet, cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
-    std::vector<uint64_t> freq(h.begin(), h.end());
+// ---------------------------------------------------------------------------
+// Pinned host memory.  Streams returned to the caller live in page-locked
+// blocks the library keeps (device copies into them run at full speed and
+// touch no fresh pages); cpt_free hands a block back for the next call.  A
+// per-thread staging block carries the small host <-> device exchanges of the
+// entropy stage.
+// ---------------------------------------------------------------------------
+class PinnedPool {
+    std::mutex mu_;
+    std::unordered_map<void*, size_t> live_;
+    std::multimap<size_t, void*> idle_;
+    size_t idle_bytes_ = 0;
+    static constexpr size_t kKeepIdle = (size_t)1 << 30;
+
+  public:
+    void* get(size_t n) {
+        n = (n + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+        std::lock_guard<std::mutex> g(mu_);
+        auto it = idle_.lower_bound(n);
+        if (it != idle_.end() && it->first <= 2 * n) {
+            void* p = it->second;
+            live_[p] = it->first;
+            idle_bytes_ -= it->first;
+            idle_.erase(it);
+            return p;
+        }
+        void* p = nullptr;
+        if (cudaMallocHost(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        live_[p] = n;
+        return p;
+    }
+    bool put(void* p) {
+        std::lock_guard<std::mutex> g(mu_);
+        auto it = live_.find(p);
+        if (it == live_.end()) return false;
+        idle_.emplace(it->second, p);
+        idle_bytes_ += it->second;
+        live_.erase(it);
+        while (idle_bytes_ > kKeepIdle && !idle_.empty()) {  // release the smallest idle blocks
+            auto f = idle_.begin();
+            idle_bytes_ -= f->first;
+            cudaFreeHost(f->second);
+            idle_.erase(f);
+        }
+        return true;
+    }
+};
+static PinnedPool& pinned_pool() {
+    static PinnedPool* pool = new PinnedPool();  // never destroyed: may outlive the CUDA context
+    return *pool;
+}
+
+struct Staging {
+    void* p = nullptr;
+    size_t n = 0;
+    void* get(size_t need) {
+        if (need <= n) return p;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        if (cudaMallocHost(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return nullptr;
+        }
+        n = need;
+        return p;
+    }
+};
+static thread_local Staging t_staging;
+
+// One Huffman stream: host-side code book and the device buffers of its
+// tile offsets and words.
+struct StreamPlan {
+    size_t nsym = 0;
+    uint32_t alphabet = 0;
+    std::vector<uint32_t> entries;  // (symbol << 8) | length of the used symbols, in symbol order
+    uint32_t* d_table = nullptr;    // [alphabet] (code << 5) | length
+    unsigned long long* d_tiles = nullptr;
+    unsigned long long* d_tmp = nullptr;
+    size_t nt = 0;
+    uint64_t nwords = 0;
+    std::vector<uint64_t> chunk_off;
+    uint32_t* d_words = nullptr;
+    size_t header_bytes() const { return 8 + 4 + 4 + 4 * entries.size() + 8 * chunk_off.size() + 8; }
+};
+
+// Code lengths and the device table of a stream from its histogram;
+// table_h: pinned [alphabet] scratch for the host -> device copy.
+static cpt_status plan_codebook(StreamPlan& sp, const unsigned* hist, uint32_t* table_h, cudaStream_t s) {
+    std::vector<uint64_t> freq(sp.alphabet);
+    for (uint32_t k = 0; k < sp.alphabet; ++k) freq[k] = hist[k];
     std::vector<uint8_t> len;
     if (!huffman_lengths(freq, kMaxCodeLen, len)) return fail(CPT_ERR_ARG, "alphabet too large for code length limit");
     std::vector<uint32_t> table;
     canonical_table(len, table);
-    uint32_t nused = 0;
-    for (uint8_t l : len) nused += l > 0;
-    out.u64(nsym);
-    out.u32(nused);
-    out.u32((uint32_t)kChunkSyms);
-    for (uint32_t sy = 0; sy < alphabet; ++sy)
-        if (len[sy]) out.u32((sy << 8) | len[sy]);
-    const size_t nt = (nsym + kTileSyms - 1) / kTileSyms;
-    uint32_t* d_table;
-    unsigned long long *d_tiles, *d_tmp;
-    CPT_CUDA(ar.alloc(&d_table, alphabet));
-    CPT_CUDA(ar.alloc(&d_tiles, nt + 1));
-    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(nt + 1)));
-    CPT_CUDA(cudaMemcpyAsync(d_table, table.data(), sizeof(uint32_t) * alphabet, cudaMemcpyHostToDevice, s));
-    CPT_CUDA(cudaMemsetAsync(d_tiles, 0, sizeof(unsigned long long) * (nt + 1), s));
-    if constexpr (sizeof(Sym) == 1) launch_tile_bits_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_table, d_tiles, s);
-    else launch_tile_bits_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_table, d_tiles, s);
-    launch_exclusive_scan_u64(d_tiles, nt + 1, d_tmp, s);
-    std::vector<unsigned long long> toff(nt + 1);
-    CPT_CUDA(cudaMemcpyAsync(toff.data(), d_tiles, sizeof(unsigned long long) * (nt + 1), cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
-    const uint64_t nbits = toff[nt];
-    const uint64_t nwords = (nbits + 31) / 32;
-    const size_t per_chunk = kChunkSyms / kTileSyms;
-    for (size_t c = 0; c * kChunkSyms < nsym; ++c) out.u64(toff[c * per_chunk]);
-    out.u64(nwords);
-    uint32_t* d_words;
-    CPT_CUDA(ar.alloc(&d_words, nwords + 1));
-    CPT_CUDA(cudaMemsetAsync(d_words, 0, sizeof(uint32_t) * (nwords + 1), s));
-    if constexpr (sizeof(Sym) == 1)
-        launch_encode_u8(reinterpret_cast<const uint8_t*>(d_sym), nsym, d_table, d_tiles, d_words, s);
-    else
-        launch_encode_u16(reinterpret_cast<const uint16_t*>(d_sym), nsym, d_table, d_tiles, d_words, s);
-    const size_t at = out.b.size();
-    out.b.resize(at + 4 * nwords);
-    if (nwords) CPT_CUDA(cudaMemcpyAsync(out.b.data() + at, d_words, 4 * nwords, cudaMemcpyDeviceToHost, s));
+    sp.entries.clear();
+    for (uint32_t sy = 0; sy < sp.alphabet; ++sy)
+        if (len[sy]) sp.entries.push_back((sy << 8) | len[sy]);
+    std::memcpy(table_h, table.data(), sizeof(uint32_t) * sp.alphabet);
+    CPT_CUDA(cudaMemcpyAsync(sp.d_table, table_h, sizeof(uint32_t) * sp.alphabet, cudaMemcpyHostToDevice, s));
     return CPT_OK;
+}
+
+static void write_stream_header(Writer& w, const StreamPlan& sp) {
+    w.u64(sp.nsym);
+    w.u32((uint32_t)sp.entries.size());
+    w.u32((uint32_t)kChunkSyms);
+    for (uint32_t e : sp.entries) w.u32(e);
+    for (uint64_t o : sp.chunk_off) w.u64(o);
+    w.u64(sp.nwords);
 }
 
 static bool is_device_pointer(const void* p) {
@@ -480,46 +541,126 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_qd, n_qd));
     CPT_CUDA(ar.alloc(&d_ld, n_ld));
     launch_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
-    Bytes bs;
-    bs.raw("CPT1", 4);
-    bs.u32(kFormat);
-    bs.u32((uint32_t)H);
-    bs.u32((uint32_t)W);
-    bs.u32((uint32_t)T);
-    bs.u32((uint32_t)k);
-    bs.u32((uint32_t)eps_int);
-    bs.u32((uint32_t)prm->pred);
-    bs.u32((uint32_t)B);
-    bs.u32((uint32_t)nstride);
-    bs.u32((uint32_t)kRadius);
-    bs.u32(0);
-    bs.f64(dx);
-    bs.f64(dy);
-    bs.f64(dt);
-    bs.f64(eps);
-    bs.u64(n_ld);
+    // both streams advance together: histograms (+ block modes) -> code books
+    // and tile bit counts -> layout of the output -> words, copied straight
+    // into the caller's buffer
+    StreamPlan sx, sd;
+    sx.nsym = N;
+    sx.alphabet = 33;
+    sd.nsym = n_qd;
+    sd.alphabet = 2 * kRadius;
     const size_t nblk = prm->pred == CPT_PRED_MOP ? (size_t)T * nby * nbx : 0;
     const size_t mode_bytes = (nblk + 7) / 8;
-    bs.u64(mode_bytes);
-    std::vector<uint8_t> modes_h((size_t)T * nby * nbx);
-    if (nblk) {
-        CPT_CUDA(cudaMemcpyAsync(modes_h.data(), d_modes, nblk, cudaMemcpyDeviceToHost, s));
-        CPT_CUDA(cudaStreamSynchronize(s));
-        std::vector<uint8_t> packed(mode_bytes, 0);
-        for (size_t x = 0; x < nblk; ++x)
-            if (modes_h[x]) {
-                packed[x >> 3] |= (uint8_t)(1u << (x & 7));
-                ++st.sl_blocks;
-            }
-        bs.raw(packed.data(), packed.size());
+    unsigned* d_hist;
+    CPT_CUDA(ar.alloc(&d_hist, sx.alphabet + sd.alphabet));
+    CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * (sx.alphabet + sd.alphabet), s));
+    launch_hist_u8(d_qxi, N, d_hist, s);
+    launch_hist_u16(d_qd, n_qd, d_hist + sx.alphabet, s);
+    sx.nt = (sx.nsym + kTileSyms - 1) / kTileSyms;
+    sd.nt = (sd.nsym + kTileSyms - 1) / kTileSyms;
+    // staging: histograms | block modes | tables | tile offsets
+    const size_t st_hist = sizeof(unsigned) * (sx.alphabet + sd.alphabet);
+    const size_t st_modes = (nblk + 15) & ~(size_t)15;
+    const size_t st_tab = sizeof(uint32_t) * (sx.alphabet + sd.alphabet);
+    const size_t st_toff = sizeof(unsigned long long) * (sx.nt + 1 + sd.nt + 1);
+    uint8_t* stage = static_cast<uint8_t*>(t_staging.get(st_hist + st_modes + st_tab + st_toff + 64));
+    if (!stage) return fail(CPT_ERR_OOM, "pinned staging allocation failed");
+    unsigned* hist_h = reinterpret_cast<unsigned*>(stage);
+    uint8_t* modes_h = stage + st_hist;
+    uint32_t* tab_h = reinterpret_cast<uint32_t*>(stage + st_hist + st_modes);
+    unsigned long long* toff_h = reinterpret_cast<unsigned long long*>(stage + st_hist + st_modes + st_tab);
+    CPT_CUDA(cudaMemcpyAsync(hist_h, d_hist, st_hist, cudaMemcpyDeviceToHost, s));
+    if (nblk) CPT_CUDA(cudaMemcpyAsync(modes_h, d_modes, nblk, cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    for (StreamPlan* sp : {&sx, &sd}) {
+        CPT_CUDA(ar.alloc(&sp->d_table, sp->alphabet));
+        CPT_CUDA(ar.alloc(&sp->d_tiles, sp->nt + 1));
+        CPT_CUDA(ar.alloc(&sp->d_tmp, scan_temp_elems(sp->nt + 1)));
     }
-    cpt_status rc = encode_stream<uint8_t>(d_qxi, N, 33, ar, s, bs);
+    cpt_status rc = plan_codebook(sx, hist_h, tab_h, s);
     if (rc != CPT_OK) return rc;
-    rc = encode_stream<uint16_t>(d_qd, n_qd, 2 * kRadius, ar, s, bs);
+    rc = plan_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet, s);
     if (rc != CPT_OK) return rc;
-    const size_t at = bs.b.size();
-    bs.b.resize(at + 4 * n_ld);
-    if (n_ld) CPT_CUDA(cudaMemcpyAsync(bs.b.data() + at, d_ld, 4 * n_ld, cudaMemcpyDeviceToHost, s));
+    for (StreamPlan* sp : {&sx, &sd}) CPT_CUDA(cudaMemsetAsync(sp->d_tiles, 0, sizeof(unsigned long long) * (sp->nt + 1), s));
+    launch_tile_bits_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, s);
+    launch_tile_bits_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, s);
+    launch_exclusive_scan_u64(sx.d_tiles, sx.nt + 1, sx.d_tmp, s);
+    launch_exclusive_scan_u64(sd.d_tiles, sd.nt + 1, sd.d_tmp, s);
+    CPT_CUDA(cudaMemcpyAsync(toff_h, sx.d_tiles, sizeof(unsigned long long) * (sx.nt + 1), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaMemcpyAsync(toff_h + sx.nt + 1, sd.d_tiles, sizeof(unsigned long long) * (sd.nt + 1),
+                             cudaMemcpyDeviceToHost, s));
+    // block modes as bits (host) while the tile counts run
+    std::vector<uint8_t> packed(mode_bytes, 0);
+    CPT_CUDA(cudaStreamSynchronize(s));
+    for (size_t x = 0; x < nblk; ++x)
+        if (modes_h[x]) {
+            packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+            ++st.sl_blocks;
+        }
+    {
+        const unsigned long long* to = toff_h;
+        for (StreamPlan* sp : {&sx, &sd}) {
+            sp->nwords = (to[sp->nt] + 31) / 32;
+            const size_t per_chunk = kChunkSyms / kTileSyms;
+            sp->chunk_off.clear();
+            for (size_t c = 0; c * kChunkSyms < sp->nsym; ++c) sp->chunk_off.push_back(to[c * per_chunk]);
+            to += sp->nt + 1;
+        }
+    }
+    // layout: header | mode bits | stream Q_xi | stream Q_d | L_d
+    const size_t kHeaderBytes = 4 + 11 * 4 + 4 * 8 + 8 + 8;
+    const size_t off_x = kHeaderBytes + mode_bytes;
+    const size_t off_xw = off_x + sx.header_bytes();
+    const size_t off_d = off_xw + 4 * sx.nwords;
+    const size_t off_dw = off_d + sd.header_bytes();
+    const size_t off_ld = off_dw + 4 * sd.nwords;
+    const size_t total = off_ld + 4 * n_ld;
+    uint8_t* obuf = static_cast<uint8_t*>(pinned_pool().get(total));
+    const bool obuf_pinned = obuf != nullptr;
+    if (!obuf) obuf = static_cast<uint8_t*>(std::malloc(total));
+    if (!obuf) return fail(CPT_ERR_OOM, "host allocation failed");
+    struct OutGuard {  // released on any error before it is handed to the caller
+        uint8_t* p;
+        bool pinned;
+        ~OutGuard() {
+            if (p && !(pinned && pinned_pool().put(p))) std::free(p);
+        }
+    } og{obuf, obuf_pinned};
+    Writer w{obuf};
+    w.raw("CPT1", 4);
+    w.u32(kFormat);
+    w.u32((uint32_t)H);
+    w.u32((uint32_t)W);
+    w.u32((uint32_t)T);
+    w.u32((uint32_t)k);
+    w.u32((uint32_t)eps_int);
+    w.u32((uint32_t)prm->pred);
+    w.u32((uint32_t)B);
+    w.u32((uint32_t)nstride);
+    w.u32((uint32_t)kRadius);
+    w.u32(0);
+    w.f64(dx);
+    w.f64(dy);
+    w.f64(dt);
+    w.f64(eps);
+    w.u64(n_ld);
+    w.u64(mode_bytes);
+    if (w.n != kHeaderBytes) return fail(CPT_ERR_ARG, "internal: header size");
+    if (mode_bytes) w.raw(packed.data(), mode_bytes);
+    write_stream_header(w, sx);
+    if (w.n != off_xw) return fail(CPT_ERR_ARG, "internal: stream layout");
+    w.n = off_d;
+    write_stream_header(w, sd);
+    if (w.n != off_dw) return fail(CPT_ERR_ARG, "internal: stream layout");
+    for (StreamPlan* sp : {&sx, &sd}) {
+        CPT_CUDA(ar.alloc(&sp->d_words, sp->nwords + 1));
+        CPT_CUDA(cudaMemsetAsync(sp->d_words, 0, sizeof(uint32_t) * (sp->nwords + 1), s));
+    }
+    launch_encode_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, sx.d_words, s);
+    launch_encode_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, sd.d_words, s);
+    if (sx.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_xw, sx.d_words, 4 * sx.nwords, cudaMemcpyDeviceToHost, s));
+    if (sd.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_dw, sd.d_words, 4 * sd.nwords, cudaMemcpyDeviceToHost, s));
+    if (n_ld) CPT_CUDA(cudaMemcpyAsync(obuf + off_ld, d_ld, 4 * n_ld, cudaMemcpyDeviceToHost, s));
     st.launches[5] += 9;
     tm.end();
 
@@ -560,11 +701,9 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     if (dbg && dbg->qhat)  // reconstruction words -> values
         for (size_t v = 0; v < N; ++v) dbg->qhat[2 * v + 1] ^= kQhatTag;
 
-    uint8_t* buf = static_cast<uint8_t*>(std::malloc(bs.b.size()));
-    if (!buf) return fail(CPT_ERR_OOM, "host allocation failed");
-    std::memcpy(buf, bs.b.data(), bs.b.size());
-    *out = buf;
-    *out_bytes = bs.b.size();
+    *out = obuf;
+    *out_bytes = total;
+    og.p = nullptr;  // handed to the caller
 
     float ms_total = 0.f;
     cudaEventElapsedTime(&ms_total, ev0, ev1);
@@ -580,8 +719,8 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     st.blocks = prm->pred == CPT_PRED_MOP ? (uint64_t)T * nby * nbx : 0;
     st.n_ld = n_ld;
     st.n_qd = n_qd;
-    st.out_bytes = bs.b.size();
-    st.ratio = (double)(NV * 4) / (double)bs.b.size();
+    st.out_bytes = total;
+    st.ratio = (double)(NV * 4) / (double)total;
     // lossless and unpredictable counts from the compaction totals
     {
         std::vector<unsigned> hx(33, 0);
@@ -1060,7 +1199,9 @@ cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32
     return cpt::trajectories_impl(uv, dims, scale_log2, out, cuda_stream);
 }
 
-void cpt_free(void* p) { std::free(p); }
+void cpt_free(void* p) {
+    if (p && !cpt::pinned_pool().put(p)) std::free(p);
+}
 
 void cpt_free_trajs(cpt_trajs* t) {
     if (!t) return;

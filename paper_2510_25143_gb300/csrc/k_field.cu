@@ -100,39 +100,50 @@ struct TaggedLoad {
     }
 };
 
-template <class Load, class Visit>
-__device__ __forceinline__ void face_rows(const Load& ld, int H, int W, int T, int t, int ib, int j0, Visit visit) {
+template <class Load, class Pre, class Visit>
+__device__ __forceinline__ void face_rows(const Load& ld, int H, int W, int T, int t, int ib, int j0, Pre pre,
+                                          Visit visit) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, j = j0 + lane;
     const bool colok = j < W, nx = t + 1 < T;
     const size_t sl = (size_t)H * W, base = (size_t)t * sl;
     const int2 z = make_int2(0, 0);
-    int2 A = z, Ap = z;
-    if (colok && ib < H) {
-        A = ld(base + (size_t)ib * W + j);
-        if (nx) Ap = ld(base + sl + (size_t)ib * W + j);
-    }
+    // rows i (A), i + 1 (D) and i + 2 (Dn, loaded one row ahead)
+    auto load_row = [&](int r, int2& v, int2& vp) {
+        v = z;
+        vp = z;
+        if (colok && r < H) {
+            v = ld(base + (size_t)r * W + j);
+            if (nx) vp = ld(base + sl + (size_t)r * W + j);
+        }
+    };
+    int2 A, Ap, D, Dp;
+    load_row(ib, A, Ap);
+    load_row(ib + 1, D, Dp);
     unsigned cA = sign_class(A.x, A.y), cAp = sign_class(Ap.x, Ap.y);
     const int ie = min(H, ib + kFaceRows);
     for (int i = ib; i < ie; ++i) {
-        int2 D = z, Dp = z;
-        if (colok && i + 1 < H) {
-            D = ld(base + (size_t)(i + 1) * W + j);
-            if (nx) Dp = ld(base + sl + (size_t)(i + 1) * W + j);
-        }
+        int2 Dn, Dnp;
+        load_row(i + 2 < ib + kFaceRows + 1 ? i + 2 : H, Dn, Dnp);
+        const auto P = pre(i, j);
         const unsigned cD = sign_class(D.x, D.y), cDp = sign_class(Dp.x, Dp.y);
         const unsigned cR = __shfl_down_sync(FULL, cA, 1), cG = __shfl_down_sync(FULL, cD, 1);
         const unsigned cRp = __shfl_down_sync(FULL, cAp, 1), cGp = __shfl_down_sync(FULL, cDp, 1);
         const bool owner = lane < 31 && colok;
-        // candidates: no strict sign shared by the three corners (corner 0 is A)
-        const unsigned cc[8] = {cA, cR, cD, cG, cAp, cRp, cDp, cGp};
-        unsigned cand = 0;
-#define CPT_C(ty, a, b, c) cand |= ((cc[a] & cc[b] & cc[c]) == 0u ? 1u : 0u) << (ty);
-        CPT_OWNED_FACES(CPT_C)
-#undef CPT_C
-        cand = owner ? cand & owned_valid(H, W, T, t, i, j) : 0u;
+        // a strict sign shared by all existing corners rules out every owned
+        // face at once (absent corners count as sharing every sign)
+        const bool r = j + 1 < W, d = i + 1 < H;
+        const unsigned all = cA & (r ? cR : 15u) & (d ? cD : 15u) & (r && d ? cG : 15u) &
+                             (nx ? cAp & (r ? cRp : 15u) & (d ? cDp : 15u) & (r && d ? cGp : 15u) : 15u);
         unsigned m = 0;
-        if (__any_sync(FULL, cand != 0)) {
+        if (__any_sync(FULL, owner && all == 0u)) {
+            // candidates: no strict sign shared by the three corners (corner 0 is A)
+            const unsigned cc[8] = {cA, cR, cD, cG, cAp, cRp, cDp, cGp};
+            unsigned cand = 0;
+#define CPT_C(ty, a, b, c) cand |= ((cc[a] & cc[b] & cc[c]) == 0u ? 1u : 0u) << (ty);
+            CPT_OWNED_FACES(CPT_C)
+#undef CPT_C
+            cand = (owner && all == 0u) ? cand & owned_valid(H, W, T, t, i, j) : 0u;
             int2 c[8];
             c[0] = A; c[2] = D; c[4] = Ap; c[6] = Dp;
             c[1].x = __shfl_down_sync(FULL, A.x, 1); c[1].y = __shfl_down_sync(FULL, A.y, 1);
@@ -146,9 +157,11 @@ __device__ __forceinline__ void face_rows(const Load& ld, int H, int W, int T, i
 #undef CPT_X
             }
         }
-        visit(i, j, FaceRowOut{(uint16_t)m, owner}, A);
+        visit(i, j, FaceRowOut{(uint16_t)m, owner}, A, P);
         A = D;
         Ap = Dp;
+        D = Dn;
+        Dp = Dnp;
         cA = cD;
         cAp = cDp;
     }
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(256) face_mask_kernel(const int2* __restrict__
     int t, ib, j0;
     if (face_item(H, W, T, item, t, ib, j0)) {
         const size_t base = (size_t)t * H * W;
-        face_rows(PlainLoad{q}, H, W, T, t, ib, j0, [&](int i, int j, FaceRowOut o, int2) {
+        face_rows(PlainLoad{q}, H, W, T, t, ib, j0, [](int, int) { return 0; }, [&](int i, int j, FaceRowOut o, int2, int) {
             if (o.owner) {
                 mask[base + (size_t)i * W + j] = o.m;
                 cnt += __popc(o.m);
@@ -221,13 +234,26 @@ __global__ void __launch_bounds__(256) verify_kernel(const int2* __restrict__ qh
     int t, ib, j0;
     if (face_item(H, W, T, item, t, ib, j0)) {
         const size_t base = (size_t)t * H * W;
-        face_rows(TaggedLoad{qhat}, H, W, T, t, ib, j0, [&](int i, int j, FaceRowOut o, int2 A) {
+        // the original mask and values of the row, loaded before its faces are evaluated
+        struct Orig {
+            unsigned m;
+            float2 x;
+        };
+        auto pre = [&](int i, int j) {
+            Orig r{0u, make_float2(0.f, 0.f)};
+            if (j < W && (threadIdx.x & 31) < 31) {
+                const size_t v = base + (size_t)i * W + j;
+                r.m = mask[v];
+                r.x = __ldcs(uv + v);
+            }
+            return r;
+        };
+        face_rows(TaggedLoad{qhat}, H, W, T, t, ib, j0, pre, [&](int i, int j, FaceRowOut o, int2 A, Orig P) {
             if (!o.owner) return;
-            const size_t v = base + (size_t)i * W + j;
-            const unsigned x = (unsigned)(o.m ^ mask[v]);
+            const unsigned x = (unsigned)o.m ^ P.m;
             ms += __popc(x & 3u);
             mb += __popc(x & ~3u);
-            const float2 ov = __ldcs(uv + v);
+            const float2 ov = P.x;
             // x_hat = qhat * 2^-k, exact in FP32 (|qhat| < 2^24)
             const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.x), g1), g2);
             const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.y), g1), g2);

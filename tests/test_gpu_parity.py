@@ -53,6 +53,20 @@ def test_ragged_shapes(shape, pred):
     compare(uv, 5e-3, pred)
 
 
+def test_stream_without_copy_matches_bytes():
+    """The zero-copy stream object holds the same bytes; its buffer goes back
+    to the library and is reused by the next call."""
+    uv, eb = synth.workload("vortex64")
+    d = _dev(uv)
+    ref, _, _ = cpt.compress(d, eb, pred="mop")
+    for _ in range(3):
+        blob, st, _ = cpt.compress(d, eb, pred="mop", copy=False)
+        assert len(blob) == len(ref) == st["out_bytes"]
+        assert bytes(blob) == ref
+        assert blob.numpy().tobytes() == ref
+        del blob
+
+
 def test_sl_nonunit_spacing_and_host_input():
     uv = synth.vortex_sum(48, 40, 6, seed=3, drift=2.5)
     compare(uv, 2e-2, "sl", dx=0.5, dy=2.0, dt=3.0, host_input=True)
