@@ -115,11 +115,63 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
         nb[12] = (valid & (1u << 12)) ? __ldg(q + v + sl + W) : z;
         nb[13] = (valid & (1u << 13)) ? __ldg(q + v + sl + W + 1) : z;
         const int2 qv = __ldg(q + v);
-        CPT_CERT_FACES(CPT_FACE)
-        if (xi > 0) {
-            const int E = 1 << (31 - __clz(eps_int));
-            int bit = 0;
-            CPT_UNC_FACES(CPT_UNC_MARK)
+        const int E = 1 << (31 - __clz(eps_int));
+        // Fast path (exact): every existing neighbour keeps the vertex's strict
+        // sign of u (or of v), with margin E where its value may still change,
+        // and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on every face unless
+        // M = 0, and no uncertain face needs the full Alg. 2: it is class 1
+        // when |M| <= D, else class 0.  M = det(n_a - q, n_b - q).
+        bool fast = false;
+#pragma unroll
+        for (int c = 0; c < 2 && !fast; ++c) {
+            const int x0 = c ? qv.y : qv.x;
+            if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 14; ++k) {
+                const int m = is_uncertain(k) ? E : 0, x = c ? nb[k].y : nb[k].x;
+                const bool same = x0 > 0 ? x > m : x < -m;
+                ok &= !((valid >> k) & 1u) || same;
+            }
+            fast = ok;
+        }
+        if (fast) {
+            // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
+            int dx[14], dy[14], l1[14];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) {
+                dx[k] = nb[k].x - qv.x;
+                dy[k] = nb[k].y - qv.y;
+                l1[k] = abs(dx[k]) + abs(dy[k]);
+            }
+            bool mz = false;
+#define CPT_CERT_M(a, b) \
+    mz |= ((valid >> (a)) & (valid >> (b)) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b];
+            CPT_CERT_FACES(CPT_CERT_M)
+#undef CPT_CERT_M
+            if (mz) {
+                xi = 0;
+            } else {
+                const int lg = 31 - __clz(E);
+                int bit = 0;
+#define CPT_UNC_FAST(a, b)                                                                                  \
+    if ((valid >> (a)) & (valid >> (b)) & 1u) {                                                             \
+        long long M = (long long)dx[a] * dy[b] - (long long)dy[a] * dx[b];                                  \
+        M = M < 0 ? -M : M;                                                                                 \
+        long long D = (long long)((is_uncertain(a) ? l1[b] : 0) + (is_uncertain(b) ? l1[a] : 0)) << lg;    \
+        if (is_uncertain(a) && is_uncertain(b)) D += 2ll << (2 * lg);                                       \
+        if (M <= D) um_m |= 1u << bit;                                                                      \
+    }                                                                                                       \
+    ++bit;
+                CPT_UNC_FACES(CPT_UNC_FAST)
+#undef CPT_UNC_FAST
+            }
+        } else {
+            CPT_CERT_FACES(CPT_FACE)
+            if (xi > 0) {
+                int bit = 0;
+                CPT_UNC_FACES(CPT_UNC_MARK)
+            }
         }
     }
     out[v] = make_int2(xi, (int)um_full);
@@ -765,14 +817,14 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
                 const int2 n4 = upleft, n5 = up, n6 = left;
                 // M = 0 checks of the 24 faces, branch free: with d = n - q(v),
                 // M = d_a.x d_b.y - d_a.y d_b.x
-#define CPT_D(k) const long long dx##k = n##k.x - qv.x, dy##k = n##k.y - qv.y;
+#define CPT_D(k) const int dx##k = n##k.x - qv.x, dy##k = n##k.y - qv.y;
                 CPT_D(0) CPT_D(1) CPT_D(2) CPT_D(3) CPT_D(4) CPT_D(5) CPT_D(6)
                 CPT_D(7) CPT_D(8) CPT_D(9) CPT_D(10) CPT_D(11) CPT_D(12)
 #undef CPT_D
                 unsigned hits = 0;
                 int bit = 0;
 #define CPT_PM(fa, fb)                                                       \
-    hits |= (dx##fa * dy##fb == dy##fa * dx##fb ? 1u : 0u) << bit; \
+    hits |= ((long long)dx##fa * dy##fb == (long long)dy##fa * dx##fb ? 1u : 0u) << bit; \
     ++bit;
                 CPT_UNC_FACES(CPT_PM)
 #undef CPT_PM
