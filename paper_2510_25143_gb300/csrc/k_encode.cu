@@ -219,7 +219,7 @@ __device__ bool poll_word(const SliceArgs& a, const int2* p, bool need, unsigned
         const bool late = (long long)(global_ns() - t0) > a.timeout_ns;
         const bool failed = *(volatile int*)a.status != 0;
         if (__any_sync(0xffffffffu, late || failed)) {
-            if (threadIdx.x == 0 && !failed) atomicCAS(a.status, 0, kStatusTimeout);
+            if ((threadIdx.x & 31u) == 0 && !failed) atomicCAS(a.status, 0, kStatusTimeout);
             return false;
         }
         __nanosleep(32);
@@ -309,7 +309,7 @@ __device__ __forceinline__ unsigned long long log2_q32(unsigned x) {
 // smp holds nslots entries: a symbol, 0 for an overflow, 0xFFFFFFFF unused.
 __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, unsigned* hist,
                                       const unsigned long long* __restrict__ lg) {
-    const int lane = threadIdx.x;
+    const int lane = (int)(threadIdx.x & 31u);
     const unsigned lo = (unsigned)kRadius - 128u;
     for (int k = lane; k < 256; k += 32) hist[k] = 0;
     __syncwarp();
@@ -362,7 +362,7 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
 // outside the block (context-preserving candidate buffer).  The SL symbols of
 // the sampled sites come from psl.
 __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps, int Rw) {
-    const int lane = threadIdx.x, B = a.B, n = a.n, H = a.H, W = a.W;
+    const int lane = (int)(threadIdx.x & 31u), B = a.B, n = a.n, H = a.H, W = a.W;
     const int nbu = a.U / B, nbt = nbu * nbu;  // blocks per unit side, per unit
     const int bpp = 32 / B;                    // blocks per pass
     const int code = xi_code(a.eps_int);
@@ -449,7 +449,7 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps
 __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
     __threadfence();
     __syncwarp();
-    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
+    if ((threadIdx.x & 31u) == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
 }
 
 // One prep unit: the U x U vertices from (r0, c0) of slice t >= 1 (it enters
@@ -458,7 +458,7 @@ __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
 // kNoSL on the vertices of blocks that keep 3DL.
 __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& sm) {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x, H = a.H, W = a.W, U = a.U;
+    const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, U = a.U;
     const int uh = min(U, H - r0), uw = min(U, W - c0);
     PrepSmem& ps = sm.prep;
     const size_t sl = (size_t)H * W;
@@ -595,7 +595,7 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
 // that finishes (r, c): every unit exactly once.  The queue orders the work
 // only: a unit still awaits each reconstruction word it reads.
 __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) {
-    const int U = a.U, R = a.R, W = a.W, H = a.H, lane = threadIdx.x;
+    const int U = a.U, R = a.R, W = a.W, H = a.H, lane = (int)(threadIdx.x & 31u);
     const int nstrips = (H + 31) / 32;
     auto ready_cols = [&](int x) -> int {  // unit columns whose column need is <= x
         if (x >= W - 1) return a.nuc;
@@ -636,7 +636,7 @@ __device__ void prep_loop(const SliceArgs& a, WarpSmem& sm) {
     for (;;) {
         unsigned pos = 0;
         int stop = 0;
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31u) == 0) {
             pos = atomicAdd(a.qhead, 1u);
             stop = *(volatile int*)a.status != 0;
         }
@@ -661,7 +661,7 @@ __device__ void prep_loop(const SliceArgs& a, WarpSmem& sm) {
 // into its ring slot: asynchronous copies, zero outside the slice.
 __device__ __forceinline__ void stage_sub(const SliceArgs& a, WaveSmem& w, const int2* cls, const unsigned* cm,
                                           const int2* Qt, const int2* Qn, bool qn_ok, int i0, int g) {
-    const int lane = threadIdx.x, H = a.H, W = a.W;
+    const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W;
     const int j = 16 * g + (lane & 15), rc = j & 63;
     const bool cok = j < W;
     for (int rr = lane >> 4; rr < 33; rr += 2) {
@@ -688,7 +688,7 @@ __device__ __forceinline__ void stage_sub(const SliceArgs& a, WaveSmem& w, const
 // All 24 uncertain faces are evaluated here with the actual reconstructions.
 __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x, H = a.H, W = a.W, T = a.T;
+    const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, T = a.T;
     const int i0 = 32 * s, i = i0 + lane;
     const bool rowok = i < H;
     const size_t sl = (size_t)H * W, base = (size_t)t * sl;
@@ -883,10 +883,15 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     return true;
 }
 
+// Every warp is an independent worker with its own shared-memory slice; a
+// CTA holds kWarpsPerCta of them so that they sit on different SM
+// sub-partitions (one-warp CTAs can share one).
+constexpr int kWarpsPerCta = 3;
 __global__ void __maxnreg__(168) encode_pipeline_kernel(SliceArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem& sm = *reinterpret_cast<WarpSmem*>(smem_raw);
-    if ((int)blockIdx.x < a.prep_warps) {
+    const int wid = (int)(threadIdx.x >> 5);
+    WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[wid];
+    if ((int)blockIdx.x * kWarpsPerCta + wid < a.prep_warps) {
         prep_loop(a, sm);
         return;
     }
@@ -895,7 +900,7 @@ __global__ void __maxnreg__(168) encode_pipeline_kernel(SliceArgs a) {
     for (;;) {
         unsigned item = 0;
         int stop = 0;
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31u) == 0) {
             item = atomicAdd(a.ticket, 1u);
             stop = *(volatile int*)a.status != 0;
         }
@@ -929,23 +934,23 @@ void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T
 }
 
 cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s) {
-    const size_t smem = sizeof(WarpSmem);
+    const size_t smem = sizeof(WarpSmem) * kWarpsPerCta;
     cudaError_t e = cudaFuncSetAttribute(encode_pipeline_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32 * kWarpsPerCta, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     // with SL or MoP a share of the warps works the prep queue
     SliceArgs b = a;
-    const int warps = nsm * per_sm;
+    const int warps = nsm * per_sm * kWarpsPerCta;
     b.prep_warps = 0;
     if (a.n_units > 0) {
         b.prep_warps = (int)((long long)warps * (a.pred == 1 ? kPrepShareSL : kPrepShareMoP) / 100);
         if (b.prep_warps < 1) b.prep_warps = 1;
         if (b.prep_warps > warps - 1) b.prep_warps = warps - 1;
     }
-    encode_pipeline_kernel<<<warps, 32, smem, s>>>(b);
+    encode_pipeline_kernel<<<nsm * per_sm, 32 * kWarpsPerCta, smem, s>>>(b);
     return cudaGetLastError();
 }
 
