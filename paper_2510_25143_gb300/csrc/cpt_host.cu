@@ -191,6 +191,9 @@ struct Writer {
 };
 
 static constexpr uint32_t kMaxCodeLen = 24;
+static constexpr long long kOrderStrip = 32;         // wave ticket order: strip weight
+static constexpr long long kOrderSliceLorenzo = 2;   // slice weight without prep units
+static constexpr long long kOrderSlackPrep = 64;     // extra slice weight with prep units
 static constexpr int kRadius = 32768;  // quantisation radius (symbol = c + kRadius)
 static constexpr uint32_t kFormat = 1;
 
@@ -488,16 +491,23 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     a.qtail = d_queue + 1;
     a.qslot = d_queue + 2;
     a.prep_warps = 0;
-    // (t, s) in ticket order: by the diagonal A*t + s, then t
+    // (t, s) in ticket order: by key = Ks s + Kt t, then t.  A wave depends on
+    // the waves above it and, through its prep units, on slice t-1 down to
+    // (31 + R) / 32 strips below it, so Kt exceeds Ks times that with prep
+    // units (Kt > Ks * strips below); without them any Kt > 0 keeps
+    // dependencies at smaller tickets, and a small Kt lets consecutive slices
+    // run a few steps apart.
     {
-        const int A = 1 + (31 + a.R) / 32;
+        const long long below = (31 + a.R) / 32;
+        const long long Kt = a.n_units > 0 ? kOrderStrip * below + kOrderSlackPrep : kOrderSliceLorenzo;
         std::vector<int2> ord;
         ord.reserve((size_t)T * nstrips);
-        for (long long d = 0; d <= (long long)A * (T - 1) + nstrips - 1; ++d)
-            for (int t = 0; t < T; ++t) {
-                const long long sidx = d - (long long)A * t;
-                if (sidx >= 0 && sidx < nstrips) ord.push_back(make_int2(t, (int)sidx));
-            }
+        for (int t = 0; t < T; ++t)
+            for (int sx = 0; sx < nstrips; ++sx) ord.push_back(make_int2(t, sx));
+        std::stable_sort(ord.begin(), ord.end(), [&](int2 p, int2 q) {
+            const long long kp = kOrderStrip * p.y + Kt * p.x, kq = kOrderStrip * q.y + Kt * q.x;
+            return kp != kq ? kp < kq : p.x < q.x;
+        });
         int2* d_order;
         CPT_CUDA(ar.alloc(&d_order, ord.size()));
         CPT_CUDA(cudaMemcpyAsync(d_order, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice, s));
