@@ -34,7 +34,7 @@
 
 namespace cpt {
 
-constexpr int kPublishEvery = 16;  // steps between checks for prep units made ready
+constexpr int kPublishEvery = 8;   // steps between checks for prep units made ready
 constexpr int kPrepShareSL = 50;   // percent of the warps working prep units (SL)
 constexpr int kPrepShareMoP = 45;  // (MoP)
 constexpr int kNoSL = (int)0x80000000;  // psl marker: the block keeps 3DL (no prediction reaches it)
