@@ -432,7 +432,9 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_clsm, N));
     CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
     CPT_CUDA(ar.alloc(&d_status, 1));
-    const int Uh = (prm->pred == CPT_PRED_MOP && B == 32) ? 32 : 16;  // side of a prep unit
+    // side of a prep unit: MoP blocks fit whole units (16, or 32 for B = 32);
+    // pure SL uses 8 (a smaller unit enters the queue earlier and is done sooner)
+    const int Uh = prm->pred == CPT_PRED_MOP ? (B == 32 ? 32 : 16) : 8;
     const size_t nprep = (size_t)T * ((H + Uh - 1) / Uh) * ((W + Uh - 1) / Uh);
     CPT_CUDA(ar.alloc(&d_prep, nprep));
     CPT_CUDA(ar.alloc(&d_ticket, 1));

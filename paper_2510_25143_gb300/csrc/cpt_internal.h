@@ -48,7 +48,7 @@ struct SliceArgs {
     int B, n;               // MoP block side (divides 32) and sampling stride
     int nby, nbx;
     int nchunks;            // ceil(W / 32)
-    int U;                  // side of a prep unit (16, or 32 for MoP blocks of 32)
+    int U;                  // side of a prep unit (8 for SL; 16, or 32 for MoP blocks of 32)
     int nur, nuc;           // prep units per slice: rows, columns
     unsigned n_units;       // prep units in total ((T - 1) * nur * nuc), 0 = no prep stage
     int prep_warps;         // warps (CTAs) working the prep queue

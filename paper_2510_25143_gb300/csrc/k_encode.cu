@@ -20,7 +20,8 @@
 //                from a ticket counter ordered by the diagonal A*t + s,
 //                A = 1 + ceil((31+R)/32) (R: the semi-Lagrangian reach), which
 //                puts every wave an item depends on at a smaller ticket.
-// prep units     (SL and MoP only) U x U squares of slice t >= 1: semi-Lagrangian
+// prep units     (SL and MoP only) U x U squares of slice t >= 1 (U = 8 for SL, 16
+//                or 32 for MoP): semi-Lagrangian
 //                predictions (Sec. VI-A) and MoP block modes (Sec. VI-B).  A unit
 //                needs slice t-1 final around it; the wave of slice t-1 that
 //                makes it so appends it to a ready queue, and prep warps take the
