@@ -94,6 +94,13 @@ def _declare(L):
                              C.c_int, C.c_int, C.c_int, C.c_int, P(P(C.c_uint8)), P(C.c_size_t),
                              P(i32), P(i32), P(i64), P(C.c_uint8), P(C.c_uint8), P(C.c_uint16),
                              P(C.c_uint32), P(Stats)]
+    L.o_compress2.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, dbl, dbl, dbl, C.c_int, dbl,
+                              C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_uint16), P(P(C.c_uint8)),
+                              P(C.c_size_t), P(i32), P(i32), P(i64), P(C.c_uint8), P(C.c_uint8),
+                              P(C.c_uint16), P(C.c_uint32), P(Stats)]
+    L.o_net_params.argtypes = []
+    L.o_net_forward.argtypes = [P(C.c_uint16), P(i32), C.c_int, C.c_int, P(C.c_float)]
+    L.o_net_predict.argtypes = [P(C.c_uint16), P(i32), C.c_int, C.c_int, P(i32)]
     L.o_decompress.argtypes = [P(C.c_uint8), C.c_size_t, P(C.c_int), P(i32), P(C.c_float)]
     L.o_free.argtypes = [C.c_void_p]
     L.o_trajectories.argtypes = [P(i32), C.c_int, C.c_int, C.c_int, P(u64), P(u64), P(P(u64)),
@@ -212,17 +219,43 @@ def huff_lengths(freq, maxlen=24):
     return out
 
 
-PRED = {"lorenzo": 0, "sl": 1, "mop": 2}
+PRED = {"lorenzo": 0, "sl": 1, "mop": 2, "learned": 3}
+
+
+def net_params():
+    """Number of bfloat16 parameters of the learned predictor."""
+    return int(lib().o_net_params())
+
+
+def net_forward(model, prev):
+    """Learned predictor output y float32 [2][H][W] for a reconstructed slice
+    prev int32 [H][W][2] and bfloat16 parameters model (uint16 bits)."""
+    prev = np.ascontiguousarray(prev, np.int32)
+    model = np.ascontiguousarray(model, np.uint16)
+    H, W, _ = prev.shape
+    y = np.empty((2, H, W), np.float32)
+    lib().o_net_forward(_p(model, C.c_uint16), _p(prev, C.c_int32), H, W, _p(y, C.c_float))
+    return y
+
+
+def net_predict(model, prev):
+    """Learned predictions int32 [H][W][2] of a slice from prev int32 [H][W][2]."""
+    prev = np.ascontiguousarray(prev, np.int32)
+    model = np.ascontiguousarray(model, np.uint16)
+    H, W, _ = prev.shape
+    out = np.empty((H, W, 2), np.int32)
+    lib().o_net_predict(_p(model, C.c_uint16), _p(prev, C.c_int32), H, W, _p(out, C.c_int32))
+    return out
 
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.0, dy=1.0,
-             dt=1.0, t_end=None, debug=True):
+             dt=1.0, t_end=None, debug=True, model=None):
     """Runs the oracle compressor on uv float32 [T][H][W][2].
 
     Returns a dict with the stream bytes (when t_end is None) and, with debug,
     the fixed-point input q, the reconstruction qhat, per-vertex bounds xi,
     their codes qxi, block modes, crossed-face masks, per-vertex symbols qd
-    and the run statistics."""
+    and the run statistics.  pred="learned" needs model (bfloat16 bits)."""
     uv = np.ascontiguousarray(uv, np.float32)
     T, H, W, two = uv.shape
     assert two == 2
@@ -238,8 +271,9 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.
                  modes=np.empty((T, nby, nbx), np.uint8), mask=np.empty((T, H, W), np.uint16),
                  qd=np.empty((T, H, W, 2), np.uint32))
     te = T if t_end is None else int(t_end)
-    rc = L.o_compress(_p(uv, C.c_float), H, W, T, dx, dy, dt, 1 if eb_mode == "rel" else 0,
-                      float(eb), PRED[pred], block, stride, te,
+    m = None if model is None else np.ascontiguousarray(model, np.uint16)
+    rc = L.o_compress2(_p(uv, C.c_float), H, W, T, dx, dy, dt, 1 if eb_mode == "rel" else 0,
+                      float(eb), PRED[pred], block, stride, te, _p(m, C.c_uint16),
                       C.byref(out) if t_end is None else None,
                       C.byref(nbytes) if t_end is None else None,
                       _p(d.get("q"), C.c_int32), _p(d.get("qhat"), C.c_int32),

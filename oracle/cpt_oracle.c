@@ -28,6 +28,9 @@
  *       iff 1000*R_SL < 997*R_3DL.
  *   R12 stream v1, canonical length-limited (24-bit) Huffman by package-merge.
  *   R13 trajectories = connected components of crossed faces joined by tets.
+ *   L1  learned predictor (not in the paper; predictor 3): a 3-layer 3x3 conv
+ *       net, bfloat16 weights, float32 fused multiply-add chains in a fixed
+ *       order, prediction = qhat(t-1) + rint(clamp(y, -2, 2) * 2^23).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no -ffast-math, no FMA).
  */
@@ -715,6 +718,86 @@ typedef struct {
 /* Micro-encodes block (by,bx) of slice t under 3DL or SL and returns its Q32
  * score (Sec. VI-B).  Qcur is the current array (slice t-1 reconstructed,
  * slice t original), q the original field, xiq the quantiser half width. */
+/* ------------------------------------------------------------------------ */
+/* Learned predictor (predictor 3; an extension, the paper has none).  A     */
+/* 3-layer 3x3 convolutional net, 2 -> 32 -> 32 -> 2 channels, ReLU after    */
+/* the first two layers, zero padding at the field boundary, maps the        */
+/* reconstructed slice t-1 scaled by 2^-23 to the change y of each component. */
+/* Parameters are bfloat16: w1[32][2][3][3] b1[32] w2[32][32][3][3] b2[32]     */
+/* w3[2][32][3][3] b3[2].  Every output is a chain of float32 fused           */
+/* multiply-adds starting from the bias, over (input channel, ky, kx) in that */
+/* order, padding included as zero inputs, so any IEEE implementation gives   */
+/* the same bits.  Prediction: qhat(t-1) + rint(clamp(y, -2, 2) * 2^23).      */
+/* ------------------------------------------------------------------------ */
+#define NET_C 32
+#define NET_PARAMS (NET_C * 2 * 9 + NET_C + NET_C * NET_C * 9 + NET_C + 2 * NET_C * 9 + 2)
+
+int o_net_params(void) { return NET_PARAMS; }
+
+static float bf16f(uint16_t h) {
+    uint32_t x = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &x, 4);
+    return f;
+}
+
+/* out[co][i][j] = act(b[co] + sum over (ci, ky, kx) of w[co][ci][ky][kx] * in[ci][i+ky-1][j+kx-1]) */
+static void net_conv(const float* in, int cin, int H, int W, const uint16_t* w, const uint16_t* b, int cout,
+                     int relu, float* out) {
+    for (int co = 0; co < cout; ++co)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                float acc = bf16f(b[co]);
+                for (int ci = 0; ci < cin; ++ci)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int ii = i + ky - 1, jj = j + kx - 1;
+                            float v = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? in[((i64)ci * H + ii) * W + jj] : 0.0f;
+                            acc = fmaf(bf16f(w[((co * cin + ci) * 3 + ky) * 3 + kx]), v, acc);
+                        }
+                out[((i64)co * H + i) * W + j] = relu ? (acc > 0.0f ? acc : 0.0f) : acc;
+            }
+}
+
+/* y = net(prev * 2^-23) for a whole slice: y[2][H][W] (float). */
+void o_net_forward(const uint16_t* model, const int32_t* prev, int H, int W, float* y) {
+    const uint16_t* w1 = model;
+    const uint16_t* b1 = w1 + NET_C * 2 * 9;
+    const uint16_t* w2 = b1 + NET_C;
+    const uint16_t* b2 = w2 + NET_C * NET_C * 9;
+    const uint16_t* w3 = b2 + NET_C;
+    const uint16_t* b3 = w3 + 2 * NET_C * 9;
+    i64 hw = (i64)H * W;
+    float* x = (float*)malloc(sizeof(float) * 2 * hw);
+    float* h1 = (float*)malloc(sizeof(float) * NET_C * hw);
+    float* h2 = (float*)malloc(sizeof(float) * NET_C * hw);
+    if (!x || !h1 || !h2) { free(x); free(h1); free(h2); for (i64 k = 0; k < 2 * hw; ++k) y[k] = 0.0f; return; }
+    for (i64 v = 0; v < hw; ++v) {  /* 2^-23 scaling of |q| < 2^24: exact */
+        x[v] = (float)prev[2 * v] * 0x1p-23f;
+        x[hw + v] = (float)prev[2 * v + 1] * 0x1p-23f;
+    }
+    net_conv(x, 2, H, W, w1, b1, NET_C, 1, h1);
+    net_conv(h1, NET_C, H, W, w2, b2, NET_C, 1, h2);
+    net_conv(h2, NET_C, H, W, w3, b3, 2, 0, y);
+    free(x); free(h1); free(h2);
+}
+
+/* The learned prediction of every vertex of a slice: pred[H][W][2]. */
+void o_net_predict(const uint16_t* model, const int32_t* prev, int H, int W, int32_t* pred) {
+    i64 hw = (i64)H * W;
+    float* y = (float*)malloc(sizeof(float) * 2 * hw);
+    if (!y) { for (i64 v = 0; v < 2 * hw; ++v) pred[v] = prev[v]; return; }
+    o_net_forward(model, prev, H, W, y);
+    for (i64 v = 0; v < hw; ++v)
+        for (int c = 0; c < 2; ++c) {
+            float d = y[c * hw + v];
+            if (!(d == d)) d = 0.0f;
+            d = d < -2.0f ? -2.0f : (d > 2.0f ? 2.0f : d);
+            pred[2 * v + c] = prev[2 * v + c] + (int32_t)rintf(d * 0x1p23f);
+        }
+    free(y);
+}
+
 static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx, int B, int n,
                            int mode, i64 xiq, double cfl_x, double cfl_y, int32_t* cand,
                            uint32_t* hist) {
@@ -786,12 +869,12 @@ static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 x
  * (T*nby*nbx block modes), mask (crossed faces), qd (N*2 per-vertex symbols,
  * 0xFFFFFFFF where absent).  t_end < T stops after slice t_end-1 (the bytes
  * are then not produced). */
-int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, double d_t,
-               int eb_mode, double eb, int pred, int B, int n, int t_end, uint8_t** out,
-               size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
-               uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out,
-               o_stats* st) {
-    if (H < 2 || W < 2 || T < 1 || B < 1 || n < 1 || pred < 0 || pred > 2) return O_ERR_ARG;
+int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, double d_t,
+                int eb_mode, double eb, int pred, int B, int n, int t_end, const uint16_t* model,
+                uint8_t** out, size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
+                uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out, o_stats* st) {
+    if (H < 2 || W < 2 || T < 1 || B < 1 || n < 1 || pred < 0 || pred > 3) return O_ERR_ARG;
+    if (pred == 3 && !model) return O_ERR_ARG;
     if (!(d_x > 0) || !(d_y > 0) || !(d_t > 0) || !(eb >= 0)) return O_ERR_ARG;
     i64 N = (i64)H * W * T;
     o_stats S;
@@ -810,8 +893,9 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
     int32_t* ld = (int32_t*)malloc(sizeof(int32_t) * 2 * N);
     int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     uint8_t* modes = (uint8_t*)calloc((size_t)T * nby * nbx, 1);
-    if (!q || !Q || !mask || !qxi || !qd || !ld || !modes) {
-        free(q); free(Q); free(mask); free(qxi); free(qd); free(ld); free(modes);
+    int32_t* npred = pred == 3 ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
+    if (!q || !Q || !mask || !qxi || !qd || !ld || !modes || (pred == 3 && !npred)) {
+        free(q); free(Q); free(mask); free(qxi); free(qd); free(ld); free(modes); free(npred);
         return O_ERR_OOM;
     }
     o_to_fixed(uv, 2 * N, S.k, q);
@@ -832,6 +916,8 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
         else if (pred == 2)
             S.blocks += (u64)nby * nbx;
         const int32_t* prev = t >= 1 ? Q + 2 * vid(H, W, t - 1, 0, 0) : NULL;
+        /* learned: the whole slice's predictions from the finished slice t-1 */
+        if (pred == 3 && t >= 1) o_net_predict(model, prev, H, W, npred);
         for (int i = 0; i < H; ++i)
             for (int j = 0; j < W; ++j) {
                 i64 v = vid(H, W, t, i, j);
@@ -849,7 +935,10 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
                 i64 xiq = (i64)1 << (code - 1);
                 int use_sl = t >= 1 && (pred == 1 || (pred == 2 && tm[(i / B) * nbx + (j / B)]));
                 i64 pu = 0, pv = 0;
-                if (use_sl) {
+                if (pred == 3 && t >= 1) {
+                    pu = npred[2 * ((i64)i * W + j)];
+                    pv = npred[2 * ((i64)i * W + j) + 1];
+                } else if (use_sl) {
                     int md = o_sl_predict(prev, H, W, i, j, cfl_x, cfl_y, &pu, &pv);
                     if (md > 0) { S.substep_vertices++; S.substeps_total += (u64)md; }
                 } else {
@@ -902,6 +991,11 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
             }
             buf_put(&b, &byte, 1);
         }
+        if (pred == 3) {  /* the model: parameter count, then the bfloat16 parameters (4-byte padded) */
+            put_u32(&b, NET_PARAMS);
+            for (int x = 0; x < NET_PARAMS; x += 2)
+                put_u32(&b, (uint32_t)model[x] | (x + 1 < NET_PARAMS ? (uint32_t)model[x + 1] << 16 : 0u));
+        }
         uint32_t* xs = (uint32_t*)malloc(sizeof(uint32_t) * (N ? N : 1));
         if (!xs) rc = O_ERR_OOM;
         if (!rc) {
@@ -925,8 +1019,18 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
     if (mask_out) memcpy(mask_out, mask, sizeof(uint16_t) * N);
     if (modes_out) memcpy(modes_out, modes, (size_t)T * nby * nbx);
     if (st) *st = S;
-    free(q); free(Q); free(mask); free(qxi); free(qd); free(ld); free(modes);
+    free(q); free(Q); free(mask); free(qxi); free(qd); free(ld); free(modes); free(npred);
     return rc;
+}
+
+int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, double d_t,
+               int eb_mode, double eb, int pred, int B, int n, int t_end, uint8_t** out,
+               size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
+               uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out,
+               o_stats* st) {
+    if (pred == 3) return O_ERR_ARG;
+    return o_compress2(uv, H, W, T, d_x, d_y, d_t, eb_mode, eb, pred, B, n, t_end, NULL, out, out_bytes, q_out,
+                       qhat_out, xi_out, qxi_out, modes_out, mask_out, qd_out, st);
 }
 
 void o_free(void* p) { free(p); }
@@ -942,7 +1046,7 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     int pred = (int)rd_u32(in + 28), B = (int)rd_u32(in + 32);
     double d_x = rd_f64(in + 48), d_y = rd_f64(in + 56), d_t = rd_f64(in + 64);
     u64 nld = rd_u64(in + 80), mode_bytes = rd_u64(in + 88);
-    if (H < 2 || W < 2 || T < 1 || B < 1 || pred < 0 || pred > 2) return O_ERR_CORRUPT;
+    if (H < 2 || W < 2 || T < 1 || B < 1 || pred < 0 || pred > 3) return O_ERR_CORRUPT;
     if (dims) { dims[0] = H; dims[1] = W; dims[2] = T; dims[3] = k; }
     if (!qhat_out && !uv_out) return O_OK;
     i64 N = (i64)H * W * T;
@@ -951,6 +1055,15 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     if (nbytes - off < mode_bytes) return O_ERR_CORRUPT;
     const uint8_t* mb = in + off;
     off += mode_bytes;
+    uint16_t model[NET_PARAMS];
+    if (pred == 3) {
+        if (nbytes - off < 4 || rd_u32(in + off) != NET_PARAMS) return O_ERR_CORRUPT;
+        off += 4;
+        size_t mbytes = 4 * (size_t)((NET_PARAMS + 1) / 2);
+        if (nbytes - off < mbytes) return O_ERR_CORRUPT;
+        for (int x = 0; x < NET_PARAMS; ++x) model[x] = (uint16_t)(rd_u32(in + off + 4 * (x / 2)) >> (16 * (x & 1)));
+        off += mbytes;
+    }
     uint32_t* xs = (uint32_t*)malloc(sizeof(uint32_t) * N);
     int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * 2 * N);
     if (!xs || !Q) { free(xs); free(Q); return O_ERR_OOM; }
@@ -969,8 +1082,11 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     const uint8_t* ldp = in + off;
     double cfl_x = o_cfl(d_t, d_x, k), cfl_y = o_cfl(d_t, d_y, k);
     u64 iq = 0, il = 0;
+    int32_t* npred = pred == 3 ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
+    if (pred == 3 && !npred) rc = O_ERR_OOM;
     for (int t = 0; t < T && !rc; ++t) {
         const int32_t* prev = t >= 1 ? Q + 2 * vid(H, W, t - 1, 0, 0) : NULL;
+        if (pred == 3 && t >= 1) o_net_predict(model, prev, H, W, npred);
         for (int i = 0; i < H && !rc; ++i)
             for (int j = 0; j < W; ++j) {
                 i64 v = vid(H, W, t, i, j);
@@ -988,7 +1104,10 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
                 int blk_sl = pred == 2 && ((mb[bidx >> 3] >> (bidx & 7)) & 1u);
                 int use_sl = t >= 1 && (pred == 1 || blk_sl);
                 i64 pu, pv;
-                if (use_sl) {
+                if (pred == 3 && t >= 1) {
+                    pu = npred[2 * ((i64)i * W + j)];
+                    pv = npred[2 * ((i64)i * W + j) + 1];
+                } else if (use_sl) {
                     o_sl_predict(prev, H, W, i, j, cfl_x, cfl_y, &pu, &pv);
                 } else {
                     pu = o_lorenzo(Q, H, W, t, i, j, 0);
@@ -1011,7 +1130,7 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
         if (uv_out)
             for (i64 x = 0; x < 2 * N; ++x) uv_out[x] = (float)ldexp((double)Q[x], -k);
     }
-    free(xs); free(Q); free(qd);
+    free(xs); free(Q); free(qd); free(npred);
     return rc;
 }
 
