@@ -219,7 +219,7 @@ def huff_lengths(freq, maxlen=24):
     return out
 
 
-PRED = {"lorenzo": 0, "sl": 1, "mop": 2, "learned": 3}
+PRED = {"lorenzo": 0, "sl": 1, "mop": 2, "learned": 3, "learned_mop": 4}
 
 
 def net_params():

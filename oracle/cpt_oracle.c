@@ -798,9 +798,11 @@ void o_net_predict(const uint16_t* model, const int32_t* prev, int H, int W, int
     free(y);
 }
 
+/* Score of one block (Sec. VI) with mode 0 = 3DL, 1 = SL, 2 = the learned
+ * predictions npred of the slice (the learned mixture). */
 static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx, int B, int n,
-                           int mode, i64 xiq, double cfl_x, double cfl_y, int32_t* cand,
-                           uint32_t* hist) {
+                           int mode, i64 xiq, double cfl_x, double cfl_y, const int32_t* npred,
+                           int32_t* cand, uint32_t* hist) {
     int i0 = by * B, j0 = bx * B;
     int i1 = i0 + B < H ? i0 + B : H, j1 = j0 + B < W ? j0 + B : W;
     const int32_t* prev = Q + 2 * vid(H, W, t - 1, 0, 0);
@@ -819,9 +821,13 @@ static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx
             int sampled = (i % n == 0) && (j % n == 0);
             i64 pu = 0, pv = 0;
             if (mode == 1) o_sl_predict(prev, H, W, i, j, cfl_x, cfl_y, &pu, &pv);
+            if (mode == 2) {
+                pu = npred[2 * ((i64)i * W + j)];
+                pv = npred[2 * ((i64)i * W + j) + 1];
+            }
             for (int c = 0; c < 2; ++c) {
                 i64 p;
-                if (mode == 1) {
+                if (mode != 0) {
                     p = c == 0 ? pu : pv;
                 } else {
                     /* Lorenzo on the candidate buffer (slice t) and slice t-1 */
@@ -844,7 +850,8 @@ static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx
 }
 
 static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 xiq, double cfl_x,
-                      double cfl_y, uint8_t* modes /* nby*nbx */, o_stats* st) {
+                      double cfl_y, const int32_t* npred /* NULL: SL */, uint8_t* modes /* nby*nbx */,
+                      o_stats* st) {
     int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * 2 * (B + 1) * (B + 1));
     uint32_t* hist = (uint32_t*)calloc(2 * QRADIUS, sizeof(uint32_t));
@@ -852,9 +859,9 @@ static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 x
         for (int bx = 0; bx < nbx; ++bx) {
             i64 r3, rs;
             memset(hist, 0, sizeof(uint32_t) * 2 * QRADIUS);
-            r3 = mop_block_score(Q, H, W, t, by, bx, B, n, 0, xiq, cfl_x, cfl_y, cand, hist);
+            r3 = mop_block_score(Q, H, W, t, by, bx, B, n, 0, xiq, cfl_x, cfl_y, npred, cand, hist);
             memset(hist, 0, sizeof(uint32_t) * 2 * QRADIUS);
-            rs = mop_block_score(Q, H, W, t, by, bx, B, n, 1, xiq, cfl_x, cfl_y, cand, hist);
+            rs = mop_block_score(Q, H, W, t, by, bx, B, n, npred ? 2 : 1, xiq, cfl_x, cfl_y, npred, cand, hist);
             uint8_t m = (1000 * rs < 997 * r3) ? 1 : 0;
             modes[by * nbx + bx] = m;
             st->sl_blocks += m;
@@ -873,8 +880,9 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
                 int eb_mode, double eb, int pred, int B, int n, int t_end, const uint16_t* model,
                 uint8_t** out, size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
                 uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out, o_stats* st) {
-    if (H < 2 || W < 2 || T < 1 || B < 1 || n < 1 || pred < 0 || pred > 3) return O_ERR_ARG;
-    if (pred == 3 && !model) return O_ERR_ARG;
+    if (H < 2 || W < 2 || T < 1 || B < 1 || n < 1 || pred < 0 || pred > 4) return O_ERR_ARG;
+    const int has_net = pred == 3 || pred == 4, has_modes = pred == 2 || pred == 4;
+    if (has_net && !model) return O_ERR_ARG;
     if (!(d_x > 0) || !(d_y > 0) || !(d_t > 0) || !(eb >= 0)) return O_ERR_ARG;
     i64 N = (i64)H * W * T;
     o_stats S;
@@ -893,8 +901,8 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
     int32_t* ld = (int32_t*)malloc(sizeof(int32_t) * 2 * N);
     int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     uint8_t* modes = (uint8_t*)calloc((size_t)T * nby * nbx, 1);
-    int32_t* npred = pred == 3 ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
-    if (!q || !Q || !mask || !qxi || !qd || !ld || !modes || (pred == 3 && !npred)) {
+    int32_t* npred = has_net ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
+    if (!q || !Q || !mask || !qxi || !qd || !ld || !modes || (has_net && !npred)) {
         free(q); free(Q); free(mask); free(qxi); free(qd); free(ld); free(modes); free(npred);
         return O_ERR_OOM;
     }
@@ -911,13 +919,13 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
     if (qd_out) for (i64 v = 0; v < 2 * N; ++v) qd_out[v] = 0xFFFFFFFFu;
     for (int t = 0; t < t_end; ++t) {
         uint8_t* tm = modes + (size_t)t * nby * nbx;
-        if (pred == 2 && t >= 1 && xiq_eps >= 1)
-            mop_modes(Q, H, W, t, B, n, xiq_eps, cfl_x, cfl_y, tm, &S);
-        else if (pred == 2)
-            S.blocks += (u64)nby * nbx;
         const int32_t* prev = t >= 1 ? Q + 2 * vid(H, W, t - 1, 0, 0) : NULL;
         /* learned: the whole slice's predictions from the finished slice t-1 */
-        if (pred == 3 && t >= 1) o_net_predict(model, prev, H, W, npred);
+        if (has_net && t >= 1) o_net_predict(model, prev, H, W, npred);
+        if (has_modes && t >= 1 && xiq_eps >= 1)
+            mop_modes(Q, H, W, t, B, n, xiq_eps, cfl_x, cfl_y, pred == 4 ? npred : NULL, tm, &S);
+        else if (has_modes)
+            S.blocks += (u64)nby * nbx;
         for (int i = 0; i < H; ++i)
             for (int j = 0; j < W; ++j) {
                 i64 v = vid(H, W, t, i, j);
@@ -933,9 +941,10 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
                     continue;
                 }
                 i64 xiq = (i64)1 << (code - 1);
-                int use_sl = t >= 1 && (pred == 1 || (pred == 2 && tm[(i / B) * nbx + (j / B)]));
+                const int blk = has_modes && tm[(i / B) * nbx + (j / B)];
+                int use_sl = t >= 1 && (pred == 1 || (pred == 2 && blk));
                 i64 pu = 0, pv = 0;
-                if (pred == 3 && t >= 1) {
+                if (t >= 1 && (pred == 3 || (pred == 4 && blk))) {
                     pu = npred[2 * ((i64)i * W + j)];
                     pv = npred[2 * ((i64)i * W + j) + 1];
                 } else if (use_sl) {
@@ -980,7 +989,7 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
         put_f64(&b, d_t);
         put_f64(&b, S.eps);
         put_u64(&b, nld);
-        u64 nblk = pred == 2 ? (u64)T * nby * nbx : 0;
+        u64 nblk = has_modes ? (u64)T * nby * nbx : 0;
         u64 mode_bytes = (nblk + 7) / 8;
         put_u64(&b, mode_bytes);
         for (u64 x = 0; x < mode_bytes; ++x) {
@@ -991,7 +1000,7 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
             }
             buf_put(&b, &byte, 1);
         }
-        if (pred == 3) {  /* the model: parameter count, then the bfloat16 parameters (4-byte padded) */
+        if (has_net) {  /* the model: parameter count, then the bfloat16 parameters (4-byte padded) */
             put_u32(&b, NET_PARAMS);
             for (int x = 0; x < NET_PARAMS; x += 2)
                 put_u32(&b, (uint32_t)model[x] | (x + 1 < NET_PARAMS ? (uint32_t)model[x + 1] << 16 : 0u));
@@ -1028,7 +1037,7 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
                size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
                uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out,
                o_stats* st) {
-    if (pred == 3) return O_ERR_ARG;
+    if (pred == 3 || pred == 4) return O_ERR_ARG;
     return o_compress2(uv, H, W, T, d_x, d_y, d_t, eb_mode, eb, pred, B, n, t_end, NULL, out, out_bytes, q_out,
                        qhat_out, xi_out, qxi_out, modes_out, mask_out, qd_out, st);
 }
@@ -1046,7 +1055,8 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     int pred = (int)rd_u32(in + 28), B = (int)rd_u32(in + 32);
     double d_x = rd_f64(in + 48), d_y = rd_f64(in + 56), d_t = rd_f64(in + 64);
     u64 nld = rd_u64(in + 80), mode_bytes = rd_u64(in + 88);
-    if (H < 2 || W < 2 || T < 1 || B < 1 || pred < 0 || pred > 3) return O_ERR_CORRUPT;
+    if (H < 2 || W < 2 || T < 1 || B < 1 || pred < 0 || pred > 4) return O_ERR_CORRUPT;
+    const int has_net = pred == 3 || pred == 4;
     if (dims) { dims[0] = H; dims[1] = W; dims[2] = T; dims[3] = k; }
     if (!qhat_out && !uv_out) return O_OK;
     i64 N = (i64)H * W * T;
@@ -1056,7 +1066,7 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     const uint8_t* mb = in + off;
     off += mode_bytes;
     uint16_t model[NET_PARAMS];
-    if (pred == 3) {
+    if (has_net) {
         if (nbytes - off < 4 || rd_u32(in + off) != NET_PARAMS) return O_ERR_CORRUPT;
         off += 4;
         size_t mbytes = 4 * (size_t)((NET_PARAMS + 1) / 2);
@@ -1082,11 +1092,11 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     const uint8_t* ldp = in + off;
     double cfl_x = o_cfl(d_t, d_x, k), cfl_y = o_cfl(d_t, d_y, k);
     u64 iq = 0, il = 0;
-    int32_t* npred = pred == 3 ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
-    if (pred == 3 && !npred) rc = O_ERR_OOM;
+    int32_t* npred = has_net ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
+    if (has_net && !npred) rc = O_ERR_OOM;
     for (int t = 0; t < T && !rc; ++t) {
         const int32_t* prev = t >= 1 ? Q + 2 * vid(H, W, t - 1, 0, 0) : NULL;
-        if (pred == 3 && t >= 1) o_net_predict(model, prev, H, W, npred);
+        if (has_net && t >= 1) o_net_predict(model, prev, H, W, npred);
         for (int i = 0; i < H && !rc; ++i)
             for (int j = 0; j < W; ++j) {
                 i64 v = vid(H, W, t, i, j);
@@ -1101,10 +1111,10 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
                 }
                 i64 xiq = (i64)1 << (code - 1), w = 2 * xiq + 1;
                 u64 bidx = ((u64)t * nby + (u64)(i / B)) * nbx + (u64)(j / B);
-                int blk_sl = pred == 2 && ((mb[bidx >> 3] >> (bidx & 7)) & 1u);
-                int use_sl = t >= 1 && (pred == 1 || blk_sl);
+                int blk = (pred == 2 || pred == 4) && ((mb[bidx >> 3] >> (bidx & 7)) & 1u);
+                int use_sl = t >= 1 && (pred == 1 || (pred == 2 && blk));
                 i64 pu, pv;
-                if (pred == 3 && t >= 1) {
+                if (t >= 1 && (pred == 3 || (pred == 4 && blk))) {
                     pu = npred[2 * ((i64)i * W + j)];
                     pv = npred[2 * ((i64)i * W + j) + 1];
                 } else if (use_sl) {

@@ -132,3 +132,59 @@ def test_learned_needs_a_model():
     uv = synth.vortex_sum(8, 8, 2, seed=1, n_vortex=1)
     with pytest.raises(RuntimeError):
         oracle.compress(uv, 1e-2, pred="learned")
+
+
+# ---------------------------------------------------------------------------
+# the learned mixture: per block (Sec. VI's selection) 3DL or the net
+# ---------------------------------------------------------------------------
+def _lorenzo(Q, t, i, j, c):
+    """3DL from the reconstruction (zero outside the field), Eq. of Sec. V-B."""
+    def at(tt, ii, jj):
+        return int(Q[tt, ii, jj, c]) if tt >= 0 and ii >= 0 and jj >= 0 else 0
+    return (at(t, i - 1, j) + at(t, i, j - 1) + at(t - 1, i, j) - at(t, i - 1, j - 1) - at(t - 1, i - 1, j)
+            - at(t - 1, i, j - 1) + at(t - 1, i - 1, j - 1))
+
+
+def test_learned_mop_codes_follow_block_modes():
+    """Every predicted vertex is quantised against the prediction its block's
+    mode names: the net's (mode 1) or 3DL's (mode 0).  The zero net
+    (prediction = previous slice) on a slowly drifting field wins some
+    blocks and loses others."""
+    uv = synth.vortex_sum(24, 20, 4, seed=12, n_vortex=3, drift=0.1)
+    model = np.zeros(oracle.net_params(), np.uint16)
+    model[:576] = random_model(5, 0.02)[:576]  # hidden layers do not reach the output
+    B = 8
+    r = oracle.compress(uv, 3e-3, pred="learned_mop", model=model, block=B)
+    qh, q, qxi, qd, modes = r["qhat"], r["q"], r["qxi"], r["qd"], r["modes"]
+    T, H, W, _ = q.shape
+    assert modes[1:].any() and not modes[1:].all()
+    for t in range(1, T):
+        npred = oracle.net_predict(model, qh[t - 1])
+        for i in range(H):
+            for j in range(W):
+                code = int(qxi[t, i, j])
+                if code == 0:
+                    continue
+                for c in range(2):
+                    p = int(npred[i, j, c]) if modes[t, i // B, j // B] else _lorenzo(qh, t, i, j, c)
+                    sym, rec = oracle.quantize(int(q[t, i, j, c]), p, 1 << (code - 1))
+                    assert sym == qd[t, i, j, c] and rec == qh[t, i, j, c]
+
+
+def test_learned_mop_with_useless_net_is_lorenzo():
+    """A net whose predictions are noise of large amplitude loses every
+    block: the codes are plain 3DL's."""
+    uv = synth.vortex_sum(20, 24, 5, seed=13, n_vortex=3)
+    r = oracle.compress(uv, 1e-2, pred="learned_mop", model=random_model(15, 0.5))
+    l = oracle.compress(uv, 1e-2, pred="lorenzo")
+    assert not r["modes"].any()
+    assert (r["qd"] == l["qd"]).all() and (r["qhat"] == l["qhat"]).all() and (r["qxi"] == l["qxi"]).all()
+
+
+def test_learned_mop_roundtrip():
+    uv = synth.vortex_sum(33, 30, 5, seed=14, n_vortex=4)
+    r = oracle.compress(uv, 5e-3, pred="learned_mop", model=random_model(6, 0.02))
+    qhat, uvh, k = oracle.decompress(r["bytes"])
+    assert (qhat == r["qhat"]).all()
+    assert np.abs(uvh.astype(np.float64) - uv).max() <= r["stats"]["eps"]
+    assert (oracle.face_masks(qhat) == r["mask"]).all()
