@@ -10,6 +10,8 @@ the GPU path.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 # workload name -> (H, W, T, relative error bound)
@@ -17,6 +19,7 @@ WORKLOADS = {
     "vortex64": (64, 64, 8, 1e-2),
     "street512": (512, 512, 100, 1e-3),
     "jets721": (721, 1440, 48, 1e-3),
+    "turb1024": (1024, 1024, 200, 1e-3),
 }
 
 
@@ -118,6 +121,66 @@ def zonal_jets(H=721, W=1440, T=48, seed=1002, n_eddy=200, cell_m=27750.0, step_
     return out
 
 
+def turbulence(H=1024, W=1024, T=200, seed=1004, k0=4.0, umax=1.5, substeps=2):
+    """2-D decaying turbulence on a periodic H x W grid, in cells per step.
+    Initial state: random phases, energy spectrum E(k) ~ k^-3 above the
+    wavenumber k0 (cycles per domain) and rising as k^2 below it, velocity
+    scaled to max |u| = umax.  The vorticity w is then carried by its
+    own streamfunction (w = -lap psi, u = d psi / dy, v = -d psi / dx):
+    pseudo-spectral, Heun steps (`substeps` per output step), 2/3 dealiasing
+    and k^8 hyperviscosity; float32 FFTs."""
+    import scipy.fft as sf
+    workers = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    ky = (2 * np.pi * np.fft.fftfreq(H)).astype(np.float32)[:, None]
+    kx = (2 * np.pi * np.fft.rfftfreq(W)).astype(np.float32)[None, :]
+    k2 = ky * ky + kx * kx
+    k2[0, 0] = 1.0
+    # shell index in cycles per domain (square domain: H for rows)
+    kc = np.sqrt((ky * H / (2 * np.pi)) ** 2 + (kx * W / (2 * np.pi)) ** 2)
+    E = np.where(kc >= k0, np.maximum(kc, 1e-6) ** -3.0, (kc / k0) ** 2 * k0 ** -3.0)
+    E[0, 0] = 0.0
+    amp = np.sqrt(E / np.maximum(kc, 1e-6) ** 3).astype(np.float32)
+    phase = rng.uniform(0, 2 * np.pi, amp.shape).astype(np.float32)
+    psi_h = amp * np.exp(1j * phase).astype(np.complex64)
+    w_h = (k2 * psi_h).astype(np.complex64)
+    w_h[0, 0] = 0.0
+    kmax = np.float32(2.0 / 3.0 * np.pi)
+    dealias = ((np.abs(ky) < kmax) & (np.abs(kx) < kmax)).astype(np.float32)
+    dt = np.float32(1.0 / substeps)
+    nu = np.float32(1.0 / kmax ** 8)
+    damp = np.exp(-nu * k2 ** 4 * dt).astype(np.float32)
+
+    def velocity(wh):
+        ph = wh / k2
+        u = sf.irfft2(1j * ky * ph, s=(H, W), workers=workers)
+        v = sf.irfft2(-1j * kx * ph, s=(H, W), workers=workers)
+        return u, v
+
+    def rhs(wh):
+        u, v = velocity(wh)
+        wx = sf.irfft2(1j * kx * wh, s=(H, W), workers=workers)
+        wy = sf.irfft2(1j * ky * wh, s=(H, W), workers=workers)
+        return -sf.rfft2(u * wx + v * wy, workers=workers) * dealias
+
+    u, v = velocity(w_h)
+    scale = np.float32(umax / max(np.abs(u).max(), np.abs(v).max()))
+    w_h = (w_h * scale).astype(np.complex64)
+    out = np.empty((T, H, W, 2), np.float32)
+    for t in range(T):
+        u, v = velocity(w_h)
+        out[t, :, :, 0] = u
+        out[t, :, :, 1] = v
+        if t == T - 1:
+            break
+        for _ in range(substeps):
+            k1 = rhs(w_h)
+            w1 = (w_h + dt * k1) * damp
+            k2s = rhs(w1)
+            w_h = ((w_h + 0.5 * dt * k1) * damp + 0.5 * dt * k2s).astype(np.complex64)
+    return out
+
+
 def workload(name):
     """Returns (uv, relative error bound) for a named workload."""
     if name == "vortex64":
@@ -126,6 +189,8 @@ def workload(name):
         return vortex_street(512, 512, 100, seed=1001), 1e-3
     if name == "jets721":
         return zonal_jets(721, 1440, 48, seed=1002), 1e-3
+    if name == "turb1024":
+        return turbulence(1024, 1024, 200, seed=1004), 1e-3
     raise KeyError(name)
 
 
