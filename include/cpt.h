@@ -50,18 +50,40 @@ typedef struct {
 
 typedef enum { CPT_EB_ABS = 0, CPT_EB_REL = 1 } cpt_eb_mode;
 
-/* Predictors: 3-D Lorenzo (3DL), semi-Lagrangian (SL, Sec. VI-A) and the
- * block-wise mixture of both (MoP, Sec. VI). */
-typedef enum { CPT_PRED_LORENZO = 0, CPT_PRED_SL = 1, CPT_PRED_MOP = 2 } cpt_pred;
+/* Predictors: 3-D Lorenzo (3DL), semi-Lagrangian (SL, Sec. VI-A), the
+ * block-wise mixture of both (MoP, Sec. VI), and a learned predictor (an
+ * extension; the paper has none): a 3-layer 3x3 convolutional net,
+ * 2 -> 32 -> 32 -> 2 channels with ReLU after the first two layers and zero
+ * padding at the field boundary, maps the reconstructed slice t-1 scaled by
+ * 2^-23 to y, and the prediction of a component is qhat(t-1) +
+ * rint(clamp(y, -2, 2) * 2^23).  Its CPT_NET_PARAMS parameters are bfloat16,
+ * laid out w1[32][2][3][3] b1[32] w2[32][32][3][3] b2[32] w3[2][32][3][3] b3[2];
+ * every output is a chain of float32 fused multiply-adds from the bias over
+ * (input channel, ky, kx) in that order, so the encoder, the decoder and any
+ * IEEE reimplementation agree bit for bit.  Slice 0 uses 3DL.  The model is
+ * stored in the stream.  The learned mixture (CPT_PRED_LEARNED_MOP) chooses
+ * per block between 3DL and the net by the MoP rule (Sec. VI-B) with the net
+ * in the place of SL: the plain predictor stays the fallback of every block. */
+typedef enum {
+    CPT_PRED_LORENZO = 0,
+    CPT_PRED_SL = 1,
+    CPT_PRED_MOP = 2,
+    CPT_PRED_LEARNED = 3,
+    CPT_PRED_LEARNED_MOP = 4
+} cpt_pred;
+#define CPT_NET_PARAMS 10434
 
 /* Compression parameters.
  *   mode/eb  : eps = eb (ABS, data units) or eb * (max - min over u and v) (REL)
  *   pred     : predictor
- *   block    : MoP block side B (0 = 16; 4, 8, 16 or 32); stride: MoP sampling
+ *   block    : MoP block side B (0 = 16; 4, 8, 16 or 32; also the learned
+ *              mixture's); stride: MoP sampling
  *              stride n (0 = 2)
  *   cuda_stream : cudaStream_t to run on (NULL = the legacy default stream)
  *   verify   : nonzero = recompute every face predicate on the reconstruction
- *              and check the pointwise bound before returning (Thm. 1/2)   */
+ *              and check the pointwise bound before returning (Thm. 1/2)
+ *   model    : the learned predictor's parameters (CPT_PRED_LEARNED and
+ *              CPT_PRED_LEARNED_MOP; copied by the call)                    */
 typedef struct {
     cpt_eb_mode mode;
     double eb;
@@ -70,6 +92,7 @@ typedef struct {
     int32_t stride;
     int32_t verify;
     void* cuda_stream;
+    const uint16_t* model;  /* host bfloat16 [CPT_NET_PARAMS]: the learned predictor (CPT_PRED_LEARNED) */
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's
@@ -185,6 +208,36 @@ cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32
  * CPT_ERR_CUDA. */
 cpt_status cpt_fixed_point_noalloc(const float* uv, const cpt_dims* dims, int32_t* q, int32_t* scale_log2,
                                    void* cuda_stream);
+
+/* Learned predictor (an extension; the paper has none).
+ *
+ * cpt_net_predict: the predictions int32 [H][W][2] of a slice from the
+ * reconstructed previous slice prev int32 [H][W][2] (host arrays), computed
+ * by the same device code as the compressor's prep units.
+ *
+ * cpt_net_gradients: loss and gradients of the training objective at the
+ * float32 parameters params [CPT_NET_PARAMS] (host): the network runs with
+ * params rounded to bfloat16, and the loss is the mean over the n pairs, the
+ * H*W vertices and both components of (y - d)^2, where
+ * d = clamp((next - prev) * 2^-23, -2, 2); prev and next are int32
+ * [n][H][W][2] fixed-point slices (host).  grad_out: host float
+ * [CPT_NET_PARAMS] (d loss / d parameter, through the rounding as if it
+ * were the identity).
+ *
+ * cpt_train_predictor: trains the network on the n pairs with Adam
+ * (learning rate lr, beta1 0.9, beta2 0.999, epsilon 1e-8) for `steps` full
+ * batches, entirely on the GPU, starting from init (host bfloat16, or NULL
+ * for a seeded initialisation); writes the bfloat16 model to model_out (host)
+ * and, when loss_out is not NULL, the loss before each step (host float
+ * [steps]).
+ * Errors: CPT_ERR_ARG (sizes < 1, null pointers), CPT_ERR_OOM, CPT_ERR_CUDA. */
+cpt_status cpt_net_predict(const uint16_t* model, const int32_t* prev, int32_t H, int32_t W, int32_t* pred_out,
+                           void* cuda_stream);
+cpt_status cpt_net_gradients(const float* params, const int32_t* prev, const int32_t* next, int32_t n, int32_t H,
+                             int32_t W, float* grad_out, float* loss_out, void* cuda_stream);
+cpt_status cpt_train_predictor(const int32_t* prev, const int32_t* next, int32_t n, int32_t H, int32_t W,
+                               int32_t steps, float lr, uint32_t seed, const uint16_t* init, uint16_t* model_out,
+                               float* loss_out, void* cuda_stream);
 
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);

@@ -17,7 +17,8 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CORRUPT, ERR_VERIFY, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-PRED = {"lorenzo": 0, "sl": 1, "mop": 2}
+PRED = {"lorenzo": 0, "sl": 1, "mop": 2, "learned": 3, "learned_mop": 4}
+NET_PARAMS = 10434
 EB_MODE = {"abs": 0, "rel": 1}
 STAGES = ["range_fixed", "face_masks", "mop_sl", "incident_bounds", "wavefront", "entropy", "verify", "host"]
 
@@ -29,7 +30,8 @@ class Dims(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
-                ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("model", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -83,6 +85,13 @@ def lib():
             L.cpt_version.restype = C.c_uint32
             L.cpt_fixed_point_noalloc.restype = C.c_int
             L.cpt_fixed_point_noalloc.argtypes = [C.c_void_p, P(Dims), C.c_void_p, C.c_void_p, C.c_void_p]
+            vp, i32 = C.c_void_p, C.c_int32
+            L.cpt_net_predict.restype = C.c_int
+            L.cpt_net_predict.argtypes = [vp, vp, i32, i32, vp, vp]
+            L.cpt_net_gradients.restype = C.c_int
+            L.cpt_net_gradients.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
+            L.cpt_train_predictor.restype = C.c_int
+            L.cpt_train_predictor.argtypes = [vp, vp, i32, i32, i32, i32, C.c_float, C.c_uint32, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -145,15 +154,19 @@ class Stream:
 
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
-             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True):
+             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
     or device).  Returns (bytes, stats dict, debug dict or None); with
-    copy=False the stream comes back as a Stream over the library's buffer."""
+    copy=False the stream comes back as a Stream over the library's buffer.
+    pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
+    bfloat16 bits."""
     ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
     if stream is None:
         stream = dev_stream
     dims = Dims(H, W, T, dx, dy, dt)
-    prm = Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream)
+    mdl = None if model is None else _model_array(model)
+    prm = Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
+                 None if mdl is None else mdl.ctypes.data)
     out = C.POINTER(C.c_uint8)()
     n = C.c_size_t(0)
     st = Stats()
@@ -177,7 +190,7 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
             blob = Stream(out, n.value)
     if check:
         _check(rc)
-    del keep
+    del keep, mdl
     s = _stats_dict(st)
     s["status"] = rc
     return blob, s, dbg_arrays
@@ -240,3 +253,64 @@ def fixed_point_noalloc(uv, q, k, stream=None):
         stream = torch.cuda.current_stream(uv.device).cuda_stream
     dims = Dims(H, W, T, 1.0, 1.0, 1.0)
     return lib().cpt_fixed_point_noalloc(uv.data_ptr(), C.byref(dims), q.data_ptr(), k.data_ptr(), stream)
+
+
+# ---------------------------------------------------------------------------
+# learned predictor (an extension of the method)
+# ---------------------------------------------------------------------------
+def _model_array(model):
+    m = np.ascontiguousarray(model, np.uint16)
+    if m.shape != (NET_PARAMS,):
+        raise ValueError(f"model must hold {NET_PARAMS} bfloat16 values")
+    return m
+
+
+def _pairs(prev, nxt=None):
+    p = np.ascontiguousarray(prev, np.int32)
+    if p.ndim == 3:
+        p = p[None]
+    assert p.ndim == 4 and p.shape[3] == 2
+    if nxt is None:
+        return p, None
+    q = np.ascontiguousarray(nxt, np.int32).reshape(p.shape)
+    return p, q
+
+
+def net_predict(model, prev, stream=None):
+    """Learned predictions int32 [H][W][2] of a slice from the reconstructed
+    previous slice prev int32 [H][W][2] (fixed point), on the GPU."""
+    m = _model_array(model)
+    p, _ = _pairs(prev)
+    _, H, W, _ = p.shape
+    out = np.empty((H, W, 2), np.int32)
+    _check(lib().cpt_net_predict(m.ctypes.data, p.ctypes.data, H, W, out.ctypes.data, stream))
+    return out
+
+
+def net_gradients(params, prev, nxt, stream=None):
+    """(loss, gradient float32 [NET_PARAMS]) of the training objective at the
+    float32 parameters over the pairs prev -> nxt (int32 [n][H][W][2])."""
+    P = np.ascontiguousarray(params, np.float32)
+    assert P.shape == (NET_PARAMS,)
+    p, q = _pairs(prev, nxt)
+    n, H, W, _ = p.shape
+    g = np.empty(NET_PARAMS, np.float32)
+    loss = C.c_float(0.0)
+    _check(lib().cpt_net_gradients(P.ctypes.data, p.ctypes.data, q.ctypes.data, n, H, W, g.ctypes.data,
+                                   C.addressof(loss), stream))
+    return float(loss.value), g
+
+
+def train_predictor(prev, nxt, steps, lr=1e-3, seed=0, init=None, stream=None):
+    """Trains the learned predictor on the GPU with Adam over the pairs
+    prev -> nxt (int32 [n][H][W][2]).  Returns (bfloat16 model uint16
+    [NET_PARAMS], loss before each step float32 [steps])."""
+    p, q = _pairs(prev, nxt)
+    n, H, W, _ = p.shape
+    ini = None if init is None else _model_array(init)
+    model = np.empty(NET_PARAMS, np.uint16)
+    losses = np.empty(int(steps), np.float32)
+    _check(lib().cpt_train_predictor(p.ctypes.data, q.ctypes.data, n, H, W, int(steps), float(lr), int(seed) & 0xFFFFFFFF,
+                                     None if ini is None else ini.ctypes.data, model.ctypes.data,
+                                     losses.ctypes.data, stream))
+    return model, losses

@@ -313,6 +313,44 @@ static void write_stream_header(Writer& w, const StreamPlan& sp) {
     w.u64(sp.nwords);
 }
 
+// bfloat16 bits -> float (exact)
+static float bf16_to_float(uint16_t h) {
+    const uint32_t x = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &x, 4);
+    return f;
+}
+
+// The learned predictor's parameters on the device: float, each layer's
+// weights transposed to [ci][ky][kx][co] (see NetDev).  d: kNetDevFloats.
+static cpt_status upload_net_f32(const float* m, float* d, NetDev* nd, cudaStream_t s) {
+    std::vector<float> h(kNetDevFloats);
+    size_t o = 0, src = 0;
+    auto layer = [&](int cin, int cout, const float** wt, const float** b) {
+        const size_t wo = o;
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int k = 0; k < 9; ++k) h[wo + ((size_t)ci * 9 + k) * cout + co] = m[src++];
+        o += (size_t)cin * 9 * cout;
+        const size_t bo = o;
+        for (int co = 0; co < cout; ++co) h[o++] = m[src++];
+        *wt = d + wo;
+        *b = d + bo;
+    };
+    layer(2, kNetC, &nd->w1t, &nd->b1);
+    layer(kNetC, kNetC, &nd->w2t, &nd->b2);
+    layer(kNetC, 2, &nd->w3t, &nd->b3);
+    CPT_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(float) * kNetDevFloats, cudaMemcpyHostToDevice, s));
+    CPT_CUDA(cudaStreamSynchronize(s));  // h is released on return
+    return CPT_OK;
+}
+
+static cpt_status upload_net(const uint16_t* model, float* d, NetDev* nd, cudaStream_t s) {
+    std::vector<float> m(kNetParams);
+    for (int x = 0; x < kNetParams; ++x) m[x] = bf16_to_float(model[x]);
+    return upload_net_f32(m.data(), d, nd, s);
+}
+
 static bool is_device_pointer(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -339,7 +377,10 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
     if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
     if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
-    if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+    if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_LEARNED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+    const bool has_net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
+    const bool has_modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
+    if (has_net && !prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
     const int B = prm->block > 0 ? prm->block : 16;
     const int nstride = prm->stride > 0 ? prm->stride : 2;
     if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
@@ -416,7 +457,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     // ---- stage 4: the encoder pipeline (MoP / SL, incident-face bounds, wavefront)
     const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     const int nstrips = (H + 31) / 32, nchunks = (W + 31) / 32;
-    if (prm->pred == CPT_PRED_MOP && (32 % B != 0 || B < 4))
+    if (has_modes && (32 % B != 0 || B < 4))
         return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
     const bool want_sl = prm->pred != CPT_PRED_LORENZO && T > 1 && eps_int > 0;
     uint8_t *d_qxi, *d_modes;
@@ -434,7 +475,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(ar.alloc(&d_status, 1));
     // side of a prep unit: MoP blocks fit whole units (16, or 32 for B = 32);
     // pure SL uses 8 (a smaller unit enters the queue earlier and is done sooner)
-    const int Uh = prm->pred == CPT_PRED_MOP ? (B == 32 ? 32 : 16) : 8;
+    const int Uh = has_modes ? (B == 32 ? 32 : 16) : 8;
     const size_t nprep = (size_t)T * ((H + Uh - 1) / Uh) * ((W + Uh - 1) / Uh);
     CPT_CUDA(ar.alloc(&d_prep, nprep));
     CPT_CUDA(ar.alloc(&d_ticket, 1));
@@ -470,12 +511,20 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     // at most that times CFL, the bilinear stencil adds one cell, and one
     // more cell covers rounding of the positions.
     a.R = 0;
-    if (want_sl) {
+    if (want_sl && has_net) {
+        a.R = kNetReach;  // the net's receptive field: 3 cells around a vertex
+    } else if (want_sl) {
         const double qmax = std::ceil((double)am * std::ldexp(1.0, k)) + (eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)eps_int))) : 0.0);
         const double reach = std::ceil(qmax * std::max(a.cfl_x, a.cfl_y)) + 2.0;
         a.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
     }
     a.timeout_ns = 2000000000ll;
+    if (has_net) {
+        float* d_net;
+        CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
+        cpt_status rc = upload_net(prm->model, d_net, &a.net, s);
+        if (rc != CPT_OK) return rc;
+    }
     // prep units (SL and MoP): U x U squares of slices 1..T-1, in a ready queue
     a.U = Uh;
     a.nur = (H + a.U - 1) / a.U;
@@ -561,7 +610,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     sx.alphabet = 33;
     sd.nsym = n_qd;
     sd.alphabet = 2 * kRadius;
-    const size_t nblk = prm->pred == CPT_PRED_MOP ? (size_t)T * nby * nbx : 0;
+    const size_t nblk = has_modes ? (size_t)T * nby * nbx : 0;
     const size_t mode_bytes = (nblk + 7) / 8;
     unsigned* d_hist;
     CPT_CUDA(ar.alloc(&d_hist, sx.alphabet + sd.alphabet));
@@ -621,7 +670,8 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     }
     // layout: header | mode bits | stream Q_xi | stream Q_d | L_d
     const size_t kHeaderBytes = 4 + 11 * 4 + 4 * 8 + 8 + 8;
-    const size_t off_x = kHeaderBytes + mode_bytes;
+    const size_t model_bytes = has_net ? 4 + 4 * (size_t)((kNetParams + 1) / 2) : 0;
+    const size_t off_x = kHeaderBytes + mode_bytes + model_bytes;
     const size_t off_xw = off_x + sx.header_bytes();
     const size_t off_d = off_xw + 4 * sx.nwords;
     const size_t off_dw = off_d + sd.header_bytes();
@@ -659,6 +709,11 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     w.u64(mode_bytes);
     if (w.n != kHeaderBytes) return fail(CPT_ERR_ARG, "internal: header size");
     if (mode_bytes) w.raw(packed.data(), mode_bytes);
+    if (model_bytes) {  // the model: parameter count, then the bfloat16 parameters two per word
+        w.u32((uint32_t)kNetParams);
+        for (int x = 0; x < kNetParams; x += 2)
+            w.u32((uint32_t)prm->model[x] | (x + 1 < kNetParams ? (uint32_t)prm->model[x + 1] << 16 : 0u));
+    }
     write_stream_header(w, sx);
     if (w.n != off_xw) return fail(CPT_ERR_ARG, "internal: stream layout");
     w.n = off_d;
@@ -728,7 +783,7 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
     }
     st.crossed_faces = cnt_h[0];
-    st.blocks = prm->pred == CPT_PRED_MOP ? (uint64_t)T * nby * nbx : 0;
+    st.blocks = has_modes ? (uint64_t)T * nby * nbx : 0;
     st.n_ld = n_ld;
     st.n_qd = n_qd;
     st.out_bytes = total;
@@ -900,7 +955,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     const double dx = r.f64(), dy = r.f64(), dt = r.f64();
     r.f64();  // eps
     const uint64_t n_ld = r.u64(), mode_bytes = r.u64();
-    if (r.bad || ver != kFormat || H < 2 || W < 2 || T < 1 || pred < 0 || pred > 2 || B < 1 ||
+    if (r.bad || ver != kFormat || H < 2 || W < 2 || T < 1 || pred < 0 || pred > 4 || B < 1 ||
         radius != (uint32_t)kRadius || k < -200 || k > 200 || !(dx > 0) || !(dy > 0) || !(dt > 0) ||
         (long long)H * W > (1ll << 31) / 4)
         return fail(CPT_ERR_CORRUPT, "bad stream header");
@@ -911,9 +966,20 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     if (!uv_out && !qhat_out) return CPT_OK;
     const size_t N = (size_t)H * W * T;
     const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
-    const size_t nblk = pred == 2 ? (size_t)T * nby * nbx : 0;
+    const size_t nblk = (pred == 2 || pred == 4) ? (size_t)T * nby * nbx : 0;
     if (mode_bytes != (nblk + 7) / 8) return fail(CPT_ERR_CORRUPT, "bad mode section");
     const uint8_t* modes = r.take(mode_bytes);
+    std::vector<uint16_t> model;
+    if (pred == 3 || pred == 4) {  // the learned predictor's parameters
+        if (r.u32() != (uint32_t)kNetParams || r.bad) return fail(CPT_ERR_CORRUPT, "bad model section");
+        model.resize(kNetParams);
+        for (int x = 0; x < kNetParams; x += 2) {
+            const uint32_t wv = r.u32();
+            model[x] = (uint16_t)(wv & 0xFFFFu);
+            if (x + 1 < kNetParams) model[x + 1] = (uint16_t)(wv >> 16);
+        }
+        if (r.bad) return fail(CPT_ERR_CORRUPT, "truncated model section");
+    }
     HuffHost hx, hd;
     if (!modes || !parse_huff(r, 33, hx) || hx.nsym != N) return fail(CPT_ERR_CORRUPT, "bad bound-code stream");
     if (!parse_huff(r, 2 * kRadius, hd)) return fail(CPT_ERR_CORRUPT, "bad residual stream");
@@ -999,6 +1065,13 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     a.cfl_y = std::ldexp(dt / dy, -k);
     // every reconstruction of a valid stream is below 2^24 in magnitude
     a.R = (int)std::min(std::ceil(16777216.0 * std::max(a.cfl_x, a.cfl_y)) + 2.0, (double)std::max(H, W) + 2.0);
+    if (pred == 3 || pred == 4) {
+        a.R = kNetReach;
+        float* d_net;
+        CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
+        cpt_status rc = upload_net(model.data(), d_net, &a.net, s);
+        if (rc != CPT_OK) return rc;
+    }
     a.timeout_ns = 2000000000ll;
     CPT_CUDA(launch_decode_pipeline(a, nsm, s));
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1184,6 +1257,149 @@ static cpt_status trajectories_impl(const float* uv, const cpt_dims* dims, int32
     return CPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// learned predictor (an extension; the paper has none): inference and
+// training entry points
+// ---------------------------------------------------------------------------
+static cpt_status net_dims_ok(int n, int H, int W) {
+    if (n < 1 || H < 1 || W < 1) return fail(CPT_ERR_ARG, "need n, H, W >= 1");
+    if ((long long)n * H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "training set too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(CPT_ERR_CUDA, "no CUDA device");
+    }
+    return CPT_OK;
+}
+
+static cpt_status net_predict_impl(const uint16_t* model, const int32_t* prev, int H, int W, int32_t* out,
+                                   void* stream) {
+    if (!model || !prev || !out) return fail(CPT_ERR_ARG, "null argument");
+    cpt_status rc = net_dims_ok(1, H, W);
+    if (rc != CPT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevArena ar(s);
+    float* d_net;
+    int32_t *d_prev, *d_out;
+    const size_t nv = 2 * (size_t)H * W;
+    CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
+    CPT_CUDA(ar.alloc(&d_prev, nv));
+    CPT_CUDA(ar.alloc(&d_out, nv));
+    NetDev nd;
+    if ((rc = upload_net(model, d_net, &nd, s)) != CPT_OK) return rc;
+    CPT_CUDA(cudaMemcpyAsync(d_prev, prev, sizeof(int32_t) * nv, cudaMemcpyDefault, s));
+    launch_net_predict(nd, d_prev, H, W, d_out, s);
+    CPT_CUDA(cudaGetLastError());
+    CPT_CUDA(cudaMemcpyAsync(out, d_out, sizeof(int32_t) * nv, cudaMemcpyDefault, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    return CPT_OK;
+}
+
+// Device state of a training run over n pairs (prev, next).
+struct NetTrainer {
+    float *ws = nullptr, *part = nullptr, *grad = nullptr, *P = nullptr;
+    double* lpart = nullptr;
+    NetTrainPtrs w{};
+    int nblk = 0;
+};
+
+static cpt_status net_trainer_setup(DevArena& ar, const int32_t* prev, const int32_t* next, int n, int H, int W,
+                                    NetTrainer* tr, cudaStream_t s) {
+    const size_t nv = 2 * (size_t)n * H * W;
+    int32_t *d_prev, *d_next;
+    CPT_CUDA(ar.alloc(&d_prev, nv));
+    CPT_CUDA(ar.alloc(&d_next, nv));
+    CPT_CUDA(cudaMemcpyAsync(d_prev, prev, sizeof(int32_t) * nv, cudaMemcpyDefault, s));
+    CPT_CUDA(cudaMemcpyAsync(d_next, next, sizeof(int32_t) * nv, cudaMemcpyDefault, s));
+    tr->nblk = net_wgrad_blocks(n, H, W, sm_count());
+    CPT_CUDA(ar.alloc(&tr->ws, net_train_floats(n, H, W)));
+    CPT_CUDA(ar.alloc(&tr->part, (size_t)tr->nblk * kNetPartRec));
+    CPT_CUDA(ar.alloc(&tr->lpart, 1216));
+    CPT_CUDA(ar.alloc(&tr->grad, kNetParams));
+    CPT_CUDA(ar.alloc(&tr->P, kNetParams));
+    CPT_CUDA(ar.alloc(&tr->w.fwd, kNetDevFloats));
+    CPT_CUDA(ar.alloc(&tr->w.bwd2, kNetW2));
+    CPT_CUDA(ar.alloc(&tr->w.bwd3, kNetW3));
+    CPT_CUDA(ar.alloc(&tr->w.bits, kNetParams));
+    const size_t P = (size_t)n * H * W;
+    CPT_CUDA(launch_net_inputs(d_prev, d_next, n, H, W, tr->ws, tr->ws + 2 * P, s));
+    return CPT_OK;
+}
+
+static cpt_status net_gradients_impl(const float* params, const int32_t* prev, const int32_t* next, int n, int H,
+                                     int W, float* grad_out, float* loss_out, void* stream) {
+    if (!params || !prev || !next || !grad_out) return fail(CPT_ERR_ARG, "null argument");
+    cpt_status rc = net_dims_ok(n, H, W);
+    if (rc != CPT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevArena ar(s);
+    NetTrainer tr;
+    if ((rc = net_trainer_setup(ar, prev, next, n, H, W, &tr, s)) != CPT_OK) return rc;
+    float* d_loss;
+    CPT_CUDA(ar.alloc(&d_loss, 1));
+    CPT_CUDA(cudaMemcpyAsync(tr.P, params, sizeof(float) * kNetParams, cudaMemcpyDefault, s));
+    CPT_CUDA(net_train_pass(tr.P, tr.ws, n, H, W, tr.nblk, tr.part, tr.lpart, tr.w, tr.grad, d_loss, s));
+    CPT_CUDA(cudaMemcpyAsync(grad_out, tr.grad, sizeof(float) * kNetParams, cudaMemcpyDefault, s));
+    float loss = 0.0f;
+    CPT_CUDA(cudaMemcpyAsync(&loss, d_loss, sizeof(float), cudaMemcpyDefault, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    if (loss_out) *loss_out = loss;
+    return CPT_OK;
+}
+
+// Seeded initialisation: uniform(-a, a) with a = sqrt(6 / fan_in) for the
+// first two layers (fan_in = 18, 288), zero last layer (the untrained net
+// predicts qhat(t-1)) and zero biases.  Uniforms from splitmix64(seed * 2^32 + j).
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+static void net_seeded_init(uint32_t seed, float* P) {
+    std::fill(P, P + kNetParams, 0.0f);
+    const double a1 = std::sqrt(6.0 / 18.0), a2 = std::sqrt(6.0 / 288.0);
+    auto uni = [&](int j) { return (double)(splitmix64(((uint64_t)seed << 32) + (uint64_t)j) >> 11) * 0x1p-53; };
+    for (int j = 0; j < kNetW1; ++j) P[j] = (float)((2.0 * uni(j) - 1.0) * a1);
+    const int o2 = kNetW1 + kNetC;
+    for (int j = 0; j < kNetW2; ++j) P[o2 + j] = (float)((2.0 * uni(o2 + j) - 1.0) * a2);
+}
+
+static cpt_status net_train_impl(const int32_t* prev, const int32_t* next, int n, int H, int W, int steps, float lr,
+                                 uint32_t seed, const uint16_t* init, uint16_t* model_out, float* loss_out,
+                                 void* stream) {
+    if (!prev || !next || !model_out) return fail(CPT_ERR_ARG, "null argument");
+    if (steps < 1 || !(lr > 0.0f) || !std::isfinite(lr)) return fail(CPT_ERR_ARG, "need steps >= 1 and lr > 0");
+    cpt_status rc = net_dims_ok(n, H, W);
+    if (rc != CPT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevArena ar(s);
+    NetTrainer tr;
+    if ((rc = net_trainer_setup(ar, prev, next, n, H, W, &tr, s)) != CPT_OK) return rc;
+    std::vector<float> P0(kNetParams);
+    if (init)
+        for (int j = 0; j < kNetParams; ++j) P0[j] = bf16_to_float(init[j]);
+    else
+        net_seeded_init(seed, P0.data());
+    float *d_m, *d_v, *d_loss;
+    CPT_CUDA(ar.alloc(&d_m, kNetParams));
+    CPT_CUDA(ar.alloc(&d_v, kNetParams));
+    CPT_CUDA(ar.alloc(&d_loss, steps));
+    CPT_CUDA(cudaMemsetAsync(d_m, 0, sizeof(float) * kNetParams, s));
+    CPT_CUDA(cudaMemsetAsync(d_v, 0, sizeof(float) * kNetParams, s));
+    CPT_CUDA(cudaMemcpyAsync(tr.P, P0.data(), sizeof(float) * kNetParams, cudaMemcpyHostToDevice, s));
+    for (int k = 1; k <= steps; ++k) {
+        CPT_CUDA(net_train_pass(tr.P, tr.ws, n, H, W, tr.nblk, tr.part, tr.lpart, tr.w, tr.grad, d_loss + (k - 1), s));
+        CPT_CUDA(launch_adam(tr.P, d_m, d_v, tr.grad, lr, k, s));
+    }
+    CPT_CUDA(launch_net_prep_weights(tr.P, tr.w, s));
+    CPT_CUDA(cudaMemcpyAsync(model_out, tr.w.bits, sizeof(uint16_t) * kNetParams, cudaMemcpyDefault, s));
+    if (loss_out) CPT_CUDA(cudaMemcpyAsync(loss_out, d_loss, sizeof(float) * steps, cudaMemcpyDefault, s));
+    CPT_CUDA(cudaStreamSynchronize(s));  // P0 is released on return
+    return CPT_OK;
+}
+
 }  // namespace cpt
 
 // ---------------------------------------------------------------------------
@@ -1209,6 +1425,22 @@ cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
                                     void* cuda_stream) {
     return cpt::trajectories_impl(uv, dims, scale_log2, out, cuda_stream);
+}
+
+cpt_status cpt_net_predict(const uint16_t* model, const int32_t* prev, int32_t H, int32_t W, int32_t* pred_out,
+                           void* cuda_stream) {
+    return cpt::net_predict_impl(model, prev, H, W, pred_out, cuda_stream);
+}
+
+cpt_status cpt_net_gradients(const float* params, const int32_t* prev, const int32_t* next, int32_t n, int32_t H,
+                             int32_t W, float* grad_out, float* loss_out, void* cuda_stream) {
+    return cpt::net_gradients_impl(params, prev, next, n, H, W, grad_out, loss_out, cuda_stream);
+}
+
+cpt_status cpt_train_predictor(const int32_t* prev, const int32_t* next, int32_t n, int32_t H, int32_t W,
+                               int32_t steps, float lr, uint32_t seed, const uint16_t* init, uint16_t* model_out,
+                               float* loss_out, void* cuda_stream) {
+    return cpt::net_train_impl(prev, next, n, H, W, steps, lr, seed, init, model_out, loss_out, cuda_stream);
 }
 
 void cpt_free(void* p) {

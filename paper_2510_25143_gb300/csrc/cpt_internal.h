@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "cpt_net.cuh"
+
 namespace cpt {
 
 struct RangePartial {
@@ -44,7 +46,8 @@ struct SliceArgs {
     unsigned long long* counters;  // [4]: substep vertices, substeps, SL blocks, spare
     int H, W, T;
     int eps_int;
-    int pred;               // 0 3DL, 1 SL, 2 MoP
+    int pred;               // 0 3DL, 1 SL, 2 MoP, 3 learned
+    NetDev net;             // learned predictor parameters (pred 3)
     int B, n;               // MoP block side (divides 32) and sampling stride
     int nby, nbx;
     int nchunks;            // ceil(W / 32)
@@ -87,6 +90,7 @@ struct DecodeArgs {
     int H, W, T, pred, B, nby, nbx, nchunks, prep_groups, R;
     double cfl_x, cfl_y;
     long long timeout_ns;
+    NetDev net;               // learned predictor parameters (pred 3)
 };
 
 // k_field.cu
@@ -144,6 +148,25 @@ void launch_tet_link(const uint16_t* mask, const unsigned long long* off, int H,
 void launch_uf_flatten(unsigned* par, size_t n, cudaStream_t s);
 void launch_crossing_points(const int32_t* q, const unsigned long long* fid, size_t n, int H, int W, double* xyt,
                             cudaStream_t s);
+
+// learned predictor (an extension; the paper has none)
+struct NetTrainPtrs {
+    float* fwd;      // kNetDevFloats: bfloat16-rounded weights in the NetDev layout
+    float* bwd2;     // [32][9][32]: transposed, flipped layer-2 weights (input gradient)
+    float* bwd3;     // [2][9][32]: the same for layer 3
+    uint16_t* bits;  // kNetParams: the bfloat16 model
+};
+constexpr int kNetPartRec = kNetC * kNetC * 9 + kNetC;  // largest per-block gradient record
+void launch_net_predict(const NetDev& nd, const int32_t* prev, int H, int W, int32_t* out, cudaStream_t s);
+size_t net_train_floats(int n, int H, int W);
+int net_wgrad_blocks(int n, int H, int W, int nsm);
+cudaError_t launch_net_inputs(const int32_t* prev, const int32_t* next, int n, int H, int W, float* x0, float* d,
+                              cudaStream_t s);
+cudaError_t net_train_pass(const float* P, float* ws, int n, int H, int W, int nblk, float* part, double* lpart,
+                           const NetTrainPtrs& w, float* grad, float* loss_dev, cudaStream_t s);
+cudaError_t launch_adam(float* P, float* m, float* v, const float* g, float lr, int step, cudaStream_t s);
+cudaError_t launch_net_prep_weights(const float* P, const NetTrainPtrs& w, cudaStream_t s);
+NetDev net_dev_view(const float* fwd);
 
 constexpr int kTileSyms = 4096;     // symbols per encode tile
 constexpr int kChunkSyms = 16384;   // symbols per decode chunk (stream sync points)

@@ -121,20 +121,23 @@ struct DChunk {
     uint8_t code[32][32];   // bound code, bit 7 = the vertex uses its SL prediction
 };
 struct DSmem {
-    DChunk buf[2];
+    union {
+        DChunk buf[2];        // waves
+        NetScratch<8> net;    // prep tiles of the learned predictor
+    };
     int2 border[64];
 };
 
 __device__ __forceinline__ bool uses_sl(const DecodeArgs& a, int t, int i, int j) {
     if (t < 1) return false;
-    if (a.pred == 1) return true;
-    if (a.pred != 2) return false;
+    if (a.pred == 1 || a.pred == 3) return true;
+    if (a.pred != 2 && a.pred != 4) return false;
     const size_t bidx = ((size_t)t * a.nby + i / a.B) * a.nbx + j / a.B;
     return (a.mode_bits[bidx >> 3] >> (bidx & 7)) & 1u;
 }
 
-// SL predictions of tile (t, s, c) for the vertices that use them.
-__device__ bool dprep_tile(const DecodeArgs& a, int t, int s, int c) {
+// SL (or learned) predictions of tile (t, s, c) for the vertices that use them.
+__device__ bool dprep_tile(const DecodeArgs& a, int t, int s, int c, DSmem& sm) {
     const int lane = threadIdx.x, H = a.H, W = a.W;
     const int nstrips = (H + 31) / 32;
     const int i0 = 32 * s, j0 = 32 * c;
@@ -142,6 +145,19 @@ __device__ bool dprep_tile(const DecodeArgs& a, int t, int s, int c) {
     const unsigned col_req = (unsigned)min(W, j0 + 32 + a.R);
     if (!warp_wait_geq(a.status, a.timeout_ns, a.progress + (size_t)(t - 1) * nstrips + s_req, col_req)) return false;
     const GlobalSlice P{a.qhat + (size_t)(t - 1) * H * W, W};
+    if (a.pred == 3 || a.pred == 4) {
+        // learned predictor: the tile's 8 x 8 sub-tiles
+        auto prev = [&](int i, int j) -> int2 {
+            return (i >= 0 && i < H && j >= 0 && j < W) ? P.at(i, j) : make_int2(0, 0);
+        };
+        for (int r0 = i0; r0 < min(H, i0 + 32); r0 += 8)
+            for (int c0 = j0; c0 < min(W, j0 + 32); c0 += 8) {
+                auto out = [&](int li, int lj, int2 p) { a.psl[((size_t)t * H + r0 + li) * W + c0 + lj] = p; };
+                net_tile<8>(a.net, sm.net, r0, c0, H, W, prev, out);
+            }
+        warp_publish(a.prep_done + ((size_t)t * nstrips + s) * a.nchunks + c, 1u);
+        return true;
+    }
     const int j = j0 + lane;
     if (j < W) {
         for (int rr = 0; rr < 32; ++rr) {
@@ -318,7 +334,7 @@ __global__ void __launch_bounds__(32) decode_pipeline_kernel(DecodeArgs a) {
         bool ok = true;
         if (g < a.prep_groups) {
             if (t >= 1)
-                for (int c = g; c < a.nchunks && ok; c += a.prep_groups) ok = dprep_tile(a, t, s, c);
+                for (int c = g; c < a.nchunks && ok; c += a.prep_groups) ok = dprep_tile(a, t, s, c, sm);
         } else {
             ok = dwave_item(a, t, s, sm);
         }

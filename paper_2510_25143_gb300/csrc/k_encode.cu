@@ -32,6 +32,7 @@
 // expires.
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
+#include "cpt_net.cuh"
 
 namespace cpt {
 
@@ -269,13 +270,18 @@ struct WaveSmem {
 constexpr int kStageR = 8;                 // largest SL reach served from the staged window
 constexpr int kPP = 34 + 2 * kStageR;      // pitch of the staged slice t-1 window
 struct PrepSmem {
-    int2 qc[34][34];                       // q(t): rows/cols -1..U around the unit
     int2 pp[kPP * kPP];                    // qhat(t-1): rows/cols -1-R..U+R around the unit
-    int2 psl[32][32];                      // SL predictions of the unit
-    unsigned smp[2][2048];                 // sampled symbols per mode (0xFFFFFFFF = none)
-    unsigned hist[256];
-    unsigned short list[1024];             // sites (row * 32 + column) left for SL
-    unsigned char modes[64];               // decisions of the unit's blocks
+    union {
+        struct {                           // SL and MoP
+            int2 qc[34][34];               // q(t): rows/cols -1..U around the unit
+            int2 psl[32][32];              // SL predictions of the unit
+            unsigned smp[2][2048];         // sampled symbols per mode (0xFFFFFFFF = none)
+            unsigned hist[256];
+            unsigned short list[1024];     // sites (row * 32 + column) left for SL
+            unsigned char modes[64];       // decisions of the unit's blocks
+        };
+        NetScratch<8> net;                 // learned predictor (8 x 8 units)
+    };
 };
 struct WarpSmem {
     union {
@@ -521,6 +527,46 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
     const SmemSlice Ps{ps.pp, r0 - 1 - Rw, c0 - 1 - Rw, kPP};
     const TaggedSlice Pg{P, W, a.status, a.timeout_ns};
     int2* Psl = a.psl + (size_t)t * sl;
+    if (a.pred == 3 || a.pred == 4) {
+        // learned predictor: the unit's 8 x 8 tiles from the staged window (reach 3)
+        auto prev = [&](int i, int j) -> int2 { return Ps.at(i, j); };
+        for (int tr = 0; tr < uh; tr += 8)
+            for (int tc = 0; tc < uw; tc += 8) {
+                auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
+                net_tile<8>(a.net, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
+            }
+        if (a.pred == 4) {
+            // the learned mixture: block modes as MoP's with the net in SL's
+            // place; the scratch of the net gives way to q(t) and the samples
+            __threadfence();  // the predictions are read back through L2 by other lanes
+            __syncwarp();
+            const int2* Qt = a.q + (size_t)t * sl;
+            for (int rr = 0; rr < U + 2; ++rr) {
+                const int i = r0 - 1 + rr;
+                for (int cc = lane; cc < U + 2; cc += 32) {
+                    const int j = c0 - 1 + cc;
+                    const bool ok = i >= 0 && i < H && j >= 0 && j < W;
+                    cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            for (int k = lane; k < uh * uw; k += 32) {
+                const int li = k / uw, lj = k % uw;
+                if (((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0)
+                    ps.psl[li][lj] = __ldcg(Psl + (size_t)(r0 + li) * W + c0 + lj);
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            mop_unit(a, t, r0, c0, ps, Rw);
+            const int nbu = U / a.B;
+            for (int k = lane; k < uh * uw; k += 32) {
+                const int li = k / uw, lj = k % uw;
+                if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+            }
+        }
+        warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
+        return;
+    }
     unsigned sub = 0, steps = 0;
     // semi-Lagrangian predictions, lanes over a compact list of sites: every
     // vertex (pure SL) or the sampled sites (MoP, for the decisions)
@@ -703,7 +749,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const int2* Psl = a.psl + base;
     const bool has_prev = t >= 1, has_above = s > 0;
     const bool need_sl = has_prev && a.n_units > 0;  // SL predictions present for this slice
-    const bool mop = a.pred == 2;
+    const bool mop = a.pred == 2 || a.pred == 4;  // psl carries the 3DL marker
     const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
     const int nsub = (W + 15) / 16;
     const int2 z = make_int2(0, 0);

@@ -16,11 +16,12 @@ def _dev(uv):
 
 
 def compare(uv, eb, pred="lorenzo", eb_mode="rel", block=16, stride=2, dx=1.0, dy=1.0, dt=1.0,
-            host_input=False):
+            host_input=False, model=None):
     src = uv if host_input else _dev(uv)
     blob, st, g = cpt.compress(src, eb, eb_mode=eb_mode, pred=pred, block=block, stride=stride,
-                               dx=dx, dy=dy, dt=dt, debug=True)
-    r = oracle.compress(uv, eb, eb_mode=eb_mode, pred=pred, block=block, stride=stride, dx=dx, dy=dy, dt=dt)
+                               dx=dx, dy=dy, dt=dt, debug=True, model=model)
+    r = oracle.compress(uv, eb, eb_mode=eb_mode, pred=pred, block=block, stride=stride, dx=dx, dy=dy, dt=dt,
+                        model=model)
     assert st["scale_log2"] == r["stats"]["k"] and st["eps_int"] == r["stats"]["eps_int"]
     assert (g["q"] == r["q"]).all()
     assert (g["mask"] == r["mask"]).all()
@@ -28,7 +29,7 @@ def compare(uv, eb, pred="lorenzo", eb_mode="rel", block=16, stride=2, dx=1.0, d
     assert (g["qxi"] == r["qxi"]).all()
     nz = r["qxi"] > 0
     assert (g["sym"][nz] == r["qd"][nz]).all()
-    if pred == "mop":
+    if pred in ("mop", "learned_mop"):
         assert (g["modes"] == r["modes"]).all()
     assert (g["qhat"] == r["qhat"]).all()
     assert blob == r["bytes"]
