@@ -302,10 +302,101 @@ def ours(args):
         line["cpu_baseline"] = {"value": round(cmbs, 4), "unit": "MB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {args.cpu_slices} of {T} slices of {args.workload}, whole "
                                           f"method, repeated for >= {args.cpu_seconds:.0f} s"}
+    if rank == 0 and world == 1 and not args.no_learned:
+        same = args.workload == "street512" and args.pred == "mop"
+        line["learned_vs_plain"] = learned_vs_plain(args, blob if same else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def learned_vs_plain(args, street_blob):
+    """Compression ratio and MB/s of the plain and the learned predictors on
+    2-D decaying turbulence (1024 x 1024 x 200, rel. bound 1e-3).  The net
+    is trained on the GPU on decompressed slices of the vortex street and the
+    zonal-jet field (plain MoP), 256 x 256 crops; a second net is trained on
+    the first slices of the turbulence field itself (its own plain MoP
+    reconstruction).  Ratios count the model stored in the stream."""
+    import numpy as np
+    import torch
+    from paper_2510_25143_gb300 import cpt, synth
+
+    def crops(qh, ts, side=256):
+        T, H, W, _ = qh.shape
+        i0, j0 = (H - side) // 2, (W - side) // 2
+        prev = np.stack([qh[t - 1, i0:i0 + side, j0:j0 + side] for t in ts])
+        nxt = np.stack([qh[t, i0:i0 + side, j0:j0 + side] for t in ts])
+        return prev, nxt
+
+    t0 = time.time()
+    if street_blob is None:
+        street, seb = synth.workload("street512")
+        street_blob, _, _ = cpt.compress(torch.from_numpy(street).cuda(), seb, pred="mop")
+        del street
+    _, q_street, _ = cpt.decompress(bytes(street_blob), want_q=True)
+    jets, jeb = synth.workload("jets721")
+    jblob, _, _ = cpt.compress(torch.from_numpy(jets).cuda(), jeb, pred="mop")
+    _, q_jets, _ = cpt.decompress(jblob, want_q=True)
+    p1, n1 = crops(q_street, range(10, 100, 10))
+    p2, n2 = crops(q_jets, range(5, 48, 5))
+    prev, nxt = np.concatenate([p1, p2]), np.concatenate([n1, n2])
+    del q_street, q_jets, jets
+    uv, eb = synth.workload("turb1024")
+    gen_s = time.time() - t0
+    d_uv = torch.from_numpy(uv).cuda()
+    stream = torch.cuda.current_stream()
+
+    def train(pv, nx):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        model, losses = cpt.train_predictor(pv, nx, steps=args.train_steps, lr=1e-3, seed=1,
+                                            stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return model, {"pairs": int(pv.shape[0]), "positions": int(pv.shape[0] * pv.shape[1] * pv.shape[2]),
+                       "steps": args.train_steps, "lr": 1e-3, "ms": round(e0.elapsed_time(e1), 1),
+                       "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+
+    model, train_info = train(prev, nxt)
+    train_info["data"] = ("decompressed slices of street512 (t = 10..90 step 10) and jets721 (t = 5..45 "
+                          "step 5), plain MoP, central 256 x 256 crops")
+
+    def run(pred, m=None, reps=3):
+        blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ok = st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
+        return {"ratio": round(uv.nbytes / len(blob), 4), "MB/s": round(uv.nbytes / (ms / 1e3) / 1e6, 1),
+                "ms": round(ms, 2), "preserved": bool(ok), "psnr": round(st["psnr"], 3)}, blob
+
+    res = {}
+    for pred in ("lorenzo", "sl", "mop"):
+        res[pred], blob = run(pred)
+        if pred == "mop":
+            _, q_turb, _ = cpt.decompress(bytes(blob), want_q=True)
+    res["learned"], _ = run("learned", model)
+    res["learned_mop"], _ = run("learned_mop", model)
+    own_prev, own_next = crops(q_turb, range(1, 9), side=512)
+    own, own_info = train(own_prev, own_next)
+    own_info["data"] = "its own plain MoP reconstruction, slices 0..8, central 512 x 512 crops"
+    res["learned_own"], _ = run("learned", own)
+    res["learned_mop_own"], _ = run("learned_mop", own)
+    best_plain = max(res[k]["ratio"] for k in ("lorenzo", "sl", "mop"))
+    best_learned = max(res[k]["ratio"] for k in ("learned", "learned_mop", "learned_own", "learned_mop_own"))
+    T, H, W, _ = uv.shape
+    return {"workload": "turb1024", "H": H, "W": W, "T": T, "rel_eb": eb, "input_bytes": uv.nbytes,
+            "data": "synthetic 2-D decaying turbulence (k^-3 spectrum, self-advected)",
+            "train": train_info, "train_own": own_info, "results": res,
+            "learned_gain_vs_best_plain": round(best_learned / best_plain, 4),
+            "setup_s": round(gen_s, 1)}
 
 
 def main():
@@ -319,6 +410,8 @@ def main():
     p.add_argument("--cpu-slices", type=int, default=4)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
+    p.add_argument("--train-steps", type=int, default=500)
     args = p.parse_args()
     if args.impl == "reference":
         reference_arm(args)
