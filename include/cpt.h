@@ -83,7 +83,17 @@ typedef enum {
  *   verify   : nonzero = recompute every face predicate on the reconstruction
  *              and check the pointwise bound before returning (Thm. 1/2)
  *   model    : the learned predictor's parameters (CPT_PRED_LEARNED and
- *              CPT_PRED_LEARNED_MOP; copied by the call)                    */
+ *              CPT_PRED_LEARNED_MOP; copied by the call)
+ *   tune     : nonzero = pick the encoder pipeline's schedule by timing a
+ *              few candidates on the first call of each size class (the
+ *              choice is cached for the process); 0 = use `schedule`
+ *   schedule : the encoder pipeline's schedule when tune is 0; zeros give the
+ *              defaults.  [0] percent of the warps that compute predictions
+ *              (SL, MoP, learned), [1] side of a pure-SL prediction unit (8
+ *              or 16), [2] slice weight of the wave order without prediction
+ *              units (3DL), [3] extra slice weight of the wave order with
+ *              them.  The schedule orders and places work only: the stream
+ *              does not depend on it.                                         */
 typedef struct {
     cpt_eb_mode mode;
     double eb;
@@ -93,6 +103,8 @@ typedef struct {
     int32_t verify;
     void* cuda_stream;
     const uint16_t* model;  /* host bfloat16 [CPT_NET_PARAMS]: the learned predictor (CPT_PRED_LEARNED) */
+    int32_t tune;
+    int32_t schedule[4];
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's
@@ -151,6 +163,45 @@ typedef struct {
  * params->verify is set; *out is still produced). */
 cpt_status cpt_compress(const float* uv, const cpt_dims* dims, const cpt_params* params,
                         uint8_t** out, size_t* out_bytes, cpt_stats* stats);
+
+/* Statistics of a batch (cpt_compress_batch). */
+typedef struct {
+    double ms_total;          /* the whole call (CUDA events on the stream) */
+    double ms_pipeline;       /* the encoder pipeline launches, summed over groups */
+    double ms_tune;           /* schedule candidates timed by the autotuner (0 when cached or off) */
+    uint32_t groups;          /* groups of fields (one pipeline launch each) */
+    uint32_t launches;        /* kernels launched, autotuning runs excluded */
+    int32_t schedule[4];      /* the schedule used (cpt_params.schedule) */
+    uint64_t device_budget;   /* device bytes a group may hold */
+    uint64_t in_bytes, out_bytes;
+    double ms_phase[8];       /* host wall time of each phase up to its synchronisation: 0 input and
+                                 range, 1 fixed point, masks and classification, 2 pipeline (and
+                                 autotuning), 3 compaction, 4 histograms, 5 code books and tile
+                                 counts, 6 stream layout, words and verification, 7 unused */
+} cpt_batch_stats;
+
+/* Compresses nfields independent fields with one set of parameters.  Each
+ * field's stream is byte for byte the one cpt_compress gives for it alone.
+ * The fields are taken in order into groups whose device memory fits
+ * device_budget (0 = 60 % of the free device memory; a group holds at least
+ * one field); every phase of the method runs for all fields of a group
+ * between the same host synchronisations, and the encoder pipeline (Alg. 3's
+ * raster loop with its prediction units) of all fields of a group is one
+ * persistent launch whose wave items and prediction units come from one
+ * ticket order and one ready queue, so small and short fields fill the
+ * warps that one field's slice-to-slice dependencies leave idle.
+ *   uv[f]       : float32 [T][H][W][2] of field f, host or device
+ *   dims[f]     : its grid
+ *   out[f]      : receives a library-allocated host buffer (cpt_free each)
+ *   stats       : nullable [nfields]; ms_total is the whole call's time,
+ *                 ms_stage[4] the shared pipeline launch of the field's group
+ *   batch_stats : nullable
+ * Errors: as cpt_compress; on any error but CPT_ERR_VERIFY no output is
+ * returned (every out[f] is NULL).  CPT_ERR_VERIFY: every stream is
+ * returned, and stats tell which field failed. */
+cpt_status cpt_compress_batch(const float* const* uv, const cpt_dims* dims, int32_t nfields, const cpt_params* params,
+                              size_t device_budget, uint8_t** out, size_t* out_bytes, cpt_stats* stats,
+                              cpt_batch_stats* batch_stats);
 
 /* cpt_compress plus optional copies of the intermediate arrays (dbg nullable). */
 cpt_status cpt_compress_ex(const float* uv, const cpt_dims* dims, const cpt_params* params,

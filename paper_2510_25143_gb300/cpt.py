@@ -31,7 +31,14 @@ class Dims(C.Structure):
 class Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
                 ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("model", C.c_void_p)]
+                ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 4)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("ms_total", C.c_double), ("ms_pipeline", C.c_double), ("ms_tune", C.c_double),
+                ("groups", C.c_uint32), ("launches", C.c_uint32), ("schedule", C.c_int32 * 4),
+                ("device_budget", C.c_uint64), ("in_bytes", C.c_uint64), ("out_bytes", C.c_uint64),
+                ("ms_phase", C.c_double * 8)]
 
 
 class Stats(C.Structure):
@@ -73,6 +80,9 @@ def lib():
                                           P(Stats), P(Debug)]
             L.cpt_compress.restype = C.c_int
             L.cpt_compress.argtypes = [C.c_void_p, P(Dims), P(Params), P(P(C.c_uint8)), P(C.c_size_t), P(Stats)]
+            L.cpt_compress_batch.restype = C.c_int
+            L.cpt_compress_batch.argtypes = [P(C.c_void_p), P(Dims), C.c_int32, P(Params), C.c_size_t,
+                                             P(P(C.c_uint8)), P(C.c_size_t), P(Stats), P(BatchStats)]
             L.cpt_decompress.restype = C.c_int
             L.cpt_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, P(Dims), C.c_void_p]
             L.cpt_extract_trajectories.restype = C.c_int
@@ -153,20 +163,27 @@ class Stream:
             self._ptr = None
 
 
+def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule):
+    sch = (C.c_int32 * 4)(*(schedule or (0, 0, 0, 0)))
+    return Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
+                  None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch)
+
+
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
-             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None):
+             dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None, tune=False,
+             schedule=None):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
     or device).  Returns (bytes, stats dict, debug dict or None); with
     copy=False the stream comes back as a Stream over the library's buffer.
     pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
-    bfloat16 bits."""
+    bfloat16 bits.  tune=True lets the library pick the encoder pipeline's
+    schedule; schedule=(prep_share, sl_unit, slice_weight, slack) fixes it."""
     ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
     if stream is None:
         stream = dev_stream
     dims = Dims(H, W, T, dx, dy, dt)
     mdl = None if model is None else _model_array(model)
-    prm = Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
-                 None if mdl is None else mdl.ctypes.data)
+    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule)
     out = C.POINTER(C.c_uint8)()
     n = C.c_size_t(0)
     st = Stats()
@@ -194,6 +211,51 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
     s = _stats_dict(st)
     s["status"] = rc
     return blob, s, dbg_arrays
+
+
+def compress_batch(fields, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
+                   dx=1.0, dy=1.0, dt=1.0, check=True, copy=True, model=None, tune=False, schedule=None,
+                   device_budget=0):
+    """Compresses a list of float32 fields [T][H][W][2] (numpy arrays or torch
+    tensors, host or device) with one set of parameters in one batched call.
+    Returns (list of streams, list of stats dicts, batch stats dict); each
+    stream equals compress() of that field alone."""
+    n = len(fields)
+    ptrs, dims, keep = (C.c_void_p * n)(), (Dims * n)(), []
+    dev_stream = None
+    for f, uv in enumerate(fields):
+        ptr, (T, H, W), kp, ds = _ptr_and_shape(uv)
+        ptrs[f] = ptr
+        dims[f] = Dims(H, W, T, dx, dy, dt)
+        keep.append(kp)
+        dev_stream = dev_stream or ds
+    if stream is None:
+        stream = dev_stream
+    mdl = None if model is None else _model_array(model)
+    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule)
+    outs = (C.POINTER(C.c_uint8) * n)()
+    nb = (C.c_size_t * n)()
+    sts = (Stats * n)()
+    bst = BatchStats()
+    L = lib()
+    rc = L.cpt_compress_batch(ptrs, dims, n, C.byref(prm), int(device_budget), outs, nb, sts, C.byref(bst))
+    blobs = []
+    for f in range(n):
+        if not outs[f]:
+            blobs.append(None)
+        elif copy:
+            blobs.append(C.string_at(outs[f], nb[f]))
+            L.cpt_free(outs[f])
+        else:
+            blobs.append(Stream(outs[f], nb[f]))
+    if check:
+        _check(rc)
+    del keep, mdl
+    b = {f: getattr(bst, f) for f, _ in BatchStats._fields_ if f not in ("schedule", "ms_phase")}
+    b["schedule"] = tuple(bst.schedule)
+    b["ms_phase"] = [round(x, 3) for x in bst.ms_phase]
+    b["status"] = rc
+    return blobs, [_stats_dict(sts[f]) for f in range(n)], b
 
 
 def decompress(blob, out=None, *, stream=None, want_q=False):

@@ -2,11 +2,14 @@
 // buffers, the launch schedule of the compressor (Alg. 3), the canonical
 // Huffman codebooks and the byte stream.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <tuple>
 #include <mutex>
 #include <unordered_map>
 #include <string>
@@ -209,7 +212,7 @@ class PinnedPool {
     std::unordered_map<void*, size_t> live_;
     std::multimap<size_t, void*> idle_;
     size_t idle_bytes_ = 0;
-    static constexpr size_t kKeepIdle = (size_t)1 << 30;
+    static constexpr size_t kKeepIdle = (size_t)8 << 30;  // a batch's streams are reused by the next batch
 
   public:
     void* get(size_t n) {
@@ -370,448 +373,878 @@ static int sm_count() {
 // ---------------------------------------------------------------------------
 // compression (Alg. 3)
 // ---------------------------------------------------------------------------
-static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
-                                size_t* out_bytes, cpt_stats* stats, const cpt_debug* dbg) {
-    if (!uv || !dims || !prm || !out || !out_bytes) return fail(CPT_ERR_ARG, "null argument");
-    const int H = dims->H, W = dims->W, T = dims->T;
-    if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
-    if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
-    if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
-    if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_LEARNED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+// One field of a compression call.  Its work is split at the host
+// synchronisations of the method (range -> fixed-point scale; compaction
+// totals; histograms -> code books; tile offsets -> stream layout), so that a
+// call over many fields runs each phase for every field before it waits once,
+// and runs the encoder pipeline of all its fields in one launch.  A field's
+// kernels, their order and their arguments are the same whether it is
+// compressed alone or in a batch.
+struct FieldJob {
+    // inputs
+    const float* uv = nullptr;
+    cpt_dims dims{};
+    const cpt_params* prm = nullptr;
+    const cpt_debug* dbg = nullptr;
+    cudaStream_t s = nullptr;
+    DevArena ar;
+    StageTimer tm;
+    cpt_stats st{};
+    // derived sizes and options
+    int H = 0, W = 0, T = 0, B = 16, nstride = 2;
+    double dx = 1, dy = 1, dt = 1;
+    size_t N = 0, NV = 0;
+    bool has_net = false, has_modes = false, want_sl = false;
+    // pinned small host values (assigned by the driver)
+    RangePartial* part_h = nullptr;  // [rblocks]
+    unsigned long long* small_h = nullptr;  // [0] last count, [1] last offset, [2..9] counters
+    VerifyOut* vo_h = nullptr;
+    // phase results
+    const float* d_uv = nullptr;
+    RangePartial* d_part = nullptr;
+    int rblocks = 0;
+    float mn = 0, mx = 0, am = 0;
+    int k = 0, eps_int = 0;
+    double eps = 0;
+    int32_t *d_q = nullptr, *d_qhat = nullptr;
+    uint16_t* d_mask = nullptr;
+    unsigned long long* d_cnt64 = nullptr;  // [0] crossed faces, [1..4] encoder counters
+    uint8_t *d_qxi = nullptr, *d_modes = nullptr;
+    uint32_t* d_sym = nullptr;
+    int* d_xiout = nullptr;
+    int2 *d_psl = nullptr, *d_cls = nullptr;
+    unsigned *d_clsm = nullptr, *d_prep = nullptr;
+    size_t nprep_alloc = 0;
+    int nby = 0, nbx = 0, nstrips = 0;
+    double qmax = 0;  // bound on |reconstruction| for the semi-Lagrangian reach
+    SliceArgs a{};
+    unsigned long long *d_off = nullptr, *d_stmp = nullptr;
+    size_t n_qd = 0, n_ld = 0, nblk = 0, mode_bytes = 0;
+    uint16_t* d_qd = nullptr;
+    int32_t* d_ld = nullptr;
+    StreamPlan sx, sd;
+    unsigned* d_hist = nullptr;
+    size_t st_hist = 0, st_modes = 0, st_tab = 0, st_toff = 0;
+    uint8_t* stage_h = nullptr;  // pinned staging of the entropy stage (assigned by the driver)
+    VerifyOut* d_vo = nullptr;
+    uint8_t* obuf = nullptr;
+    bool obuf_pinned = false;
+    size_t total = 0;
+
+    FieldJob(cudaStream_t st_, bool timing) : s(st_), ar(st_), tm(st_, timing) { std::memset(&st, 0, sizeof(st)); }
+    ~FieldJob() { release_output(); }
+    void release_output() {
+        if (obuf && !(obuf_pinned && pinned_pool().put(obuf))) std::free(obuf);
+        obuf = nullptr;
+    }
+    size_t staging_bytes() const { return st_hist + st_modes + st_tab + st_toff + 64; }
+    // device bytes a field holds at its peak (for grouping a batch)
+    static size_t device_bytes(const cpt_dims& d, bool host_input) {
+        const size_t n = (size_t)d.H * d.W * d.T;
+        return n * (72 + (host_input ? 8 : 0)) + ((size_t)64 << 20);
+    }
+
+    // ---- phase 0: argument checks, input on the device, range partials
+    cpt_status begin(int nsm) {
+        if (!uv) return fail(CPT_ERR_ARG, "null argument");
+        H = dims.H; W = dims.W; T = dims.T;
+        if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
+        if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
+        if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
+        if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_LEARNED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+        has_net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
+        has_modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
+        if (has_net && !prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
+        B = prm->block > 0 ? prm->block : 16;
+        nstride = prm->stride > 0 ? prm->stride : 2;
+        if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
+        if (has_modes && (32 % B != 0 || B < 4)) return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
+        dx = dims.dx > 0 ? dims.dx : 1.0;
+        dy = dims.dy > 0 ? dims.dy : 1.0;
+        dt = dims.dt > 0 ? dims.dt : 1.0;
+        N = (size_t)H * W * T;
+        NV = 2 * N;
+        // input on the device, 16-byte aligned
+        d_uv = uv;
+        if (!is_device_pointer(uv) || (reinterpret_cast<uintptr_t>(uv) & 15u)) {
+            float* tmp;
+            CPT_CUDA(ar.alloc(&tmp, NV));
+            CPT_CUDA(cudaMemcpyAsync(tmp, uv, NV * sizeof(float), cudaMemcpyDefault, s));
+            d_uv = tmp;
+        }
+        // ---- stage 0: range, scale, fixed point
+        tm.begin(0);
+        rblocks = nsm * 4;
+        CPT_CUDA(ar.alloc(&d_part, rblocks));
+        launch_range(d_uv, NV, d_part, rblocks, s);
+        st.launches[0]++;
+        CPT_CUDA(cudaMemcpyAsync(part_h, d_part, sizeof(RangePartial) * rblocks, cudaMemcpyDeviceToHost, s));
+        return CPT_OK;
+    }
+
+    // ---- phase 1 (after the range partials arrived): scale and bound,
+    // fixed point, crossed-face masks, the pipeline's buffers and arguments,
+    // incident-face classification
+    cpt_status plan(int nsm, const unsigned long long* d_log2, const NetDev* net, const PipeTuning& tune) {
+        mn = INFINITY; mx = -INFINITY; am = 0.f;
+        unsigned bad = 0;
+        for (int x = 0; x < rblocks; ++x) {
+            const RangePartial& p = part_h[x];
+            mn = std::min(mn, p.mn); mx = std::max(mx, p.mx); am = std::max(am, p.amax); bad |= p.bad;
+        }
+        if (bad) return fail(CPT_ERR_ARG, "input holds a non-finite value");
+        k = 0;
+        if (am > 0.f) { int e; std::frexp((double)am, &e); k = 23 - e; }
+        eps = prm->mode == CPT_EB_REL ? prm->eb * ((double)mx - (double)mn) : prm->eb;
+        const double ef = std::floor(std::ldexp(eps, k) - 0.5);
+        eps_int = !(ef > 0) ? 0 : (ef > 8388608.0 ? 8388608 : (int)ef);
+        st.scale_log2 = k;
+        st.eps_int = eps_int;
+        st.eps = eps;
+        CPT_CUDA(ar.alloc(&d_q, NV));
+        CPT_CUDA(ar.alloc(&d_qhat, NV));
+        launch_to_fixed(d_uv, NV, k, d_q, nsm * 8, s);
+        st.launches[0]++;
+        tm.end();
+
+        // ---- stage 1: crossed-face masks (C)
+        tm.begin(1);
+        CPT_CUDA(ar.alloc(&d_mask, N));
+        CPT_CUDA(ar.alloc(&d_cnt64, 8));
+        CPT_CUDA(cudaMemsetAsync(d_cnt64, 0, 8 * sizeof(unsigned long long), s));
+        launch_face_masks(d_q, H, W, T, d_mask, d_cnt64, s);
+        st.launches[1]++;
+        tm.end();
+
+        // ---- the encoder pipeline's buffers (MoP / SL, incident-face bounds, wavefront)
+        nby = (H + B - 1) / B;
+        nbx = (W + B - 1) / B;
+        nstrips = (H + 31) / 32;
+        const int nchunks = (W + 31) / 32;
+        want_sl = prm->pred != CPT_PRED_LORENZO && T > 1 && eps_int > 0;
+        CPT_CUDA(ar.alloc(&d_qxi, N));
+        CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
+        CPT_CUDA(ar.alloc(&d_sym, N));
+        CPT_CUDA(ar.alloc(&d_cls, N));
+        CPT_CUDA(ar.alloc(&d_clsm, N));
+        CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
+        if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
+        CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
+        SliceArgs& A = a;
+        std::memset(&A, 0, sizeof(A));
+        A.q = reinterpret_cast<const int2*>(d_q);
+        A.qhat = reinterpret_cast<int2*>(d_qhat);
+        A.mask = d_mask;
+        A.cls = d_cls;
+        A.cls_m = d_clsm;
+        A.psl = d_psl;
+        A.modes = d_modes;
+        A.qxi = d_qxi;
+        A.sym = d_sym;
+        A.xi_out = d_xiout;
+        A.counters = d_cnt64 + 1;
+        A.H = H; A.W = W; A.T = T;
+        A.eps_int = eps_int;
+        A.pred = (int)prm->pred;
+        A.B = B; A.n = nstride; A.nby = nby; A.nbx = nbx;
+        A.nchunks = nchunks;
+        A.cfl_x = std::ldexp(dt / dx, -k);
+        A.cfl_y = std::ldexp(dt / dy, -k);
+        // Reach of the semi-Lagrangian back-trace into slice t-1: no
+        // reconstruction exceeds max|q| + E in magnitude, every displacement is
+        // at most that times CFL, the bilinear stencil adds one cell, and one
+        // more cell covers rounding of the positions.
+        A.R = 0;
+        if (want_sl && has_net) {
+            A.R = kNetReach;  // the net's receptive field: 3 cells around a vertex
+        } else if (want_sl) {
+            qmax = std::ceil((double)am * std::ldexp(1.0, k)) +
+                   (eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)eps_int))) : 0.0);
+            const double reach = std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0;
+            A.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
+        }
+        if (has_net) A.net = *net;
+        A.log2tab = d_log2;
+        // prep units (SL and MoP): U x U squares of slices 1..T-1; the
+        // progress flags are sized for the smallest unit a schedule may pick
+        const int Umin = has_modes ? (B == 32 ? 32 : 16) : 8;
+        nprep_alloc = (size_t)T * ((H + Umin - 1) / Umin) * ((W + Umin - 1) / Umin);
+        CPT_CUDA(ar.alloc(&d_prep, nprep_alloc));
+        A.prep_done = d_prep;
+        cpt_status rc = set_units(tune);
+        if (rc != CPT_OK) return rc;
+
+        tm.begin(3);
+        launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, s);
+        st.launches[3]++;
+        tm.end();
+        return CPT_OK;
+    }
+
+    // Side of the prep units under a schedule: MoP blocks fit whole units
+    // (16, or 32 for B = 32); pure SL and the learned predictor use 8 unless
+    // the schedule asks for 16 (pure SL).
+    cpt_status set_units(const PipeTuning& tune) {
+        SliceArgs& A = a;
+        int U = has_modes ? (B == 32 ? 32 : 16) : 8;
+        if (prm->pred == CPT_PRED_SL && tune.sl_unit == 16) U = 16;
+        A.U = U;
+        A.nur = (H + U - 1) / U;
+        A.nuc = (W + U - 1) / U;
+        A.n_units = 0;
+        if (want_sl) {
+            const unsigned long long nu = (unsigned long long)(T - 1) * A.nur * A.nuc;
+            if (nu >= 0x7FFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many prediction units");
+            A.n_units = (unsigned)nu;
+        }
+        return CPT_OK;
+    }
+
+    // Ticket keys of this field's wavefront items (t, s): Ks s + Kt t, then t.
+    // A wave depends on the waves above it and, through its prep units, on
+    // slice t-1 down to (31 + R) / 32 strips below it, so Kt exceeds Ks times
+    // that with prep units (Kt > Ks * strips below); without them any Kt > 0
+    // keeps dependencies at smaller tickets, and a small Kt lets consecutive
+    // slices run a few steps apart.
+    void ticket_keys(const PipeTuning& tune, std::vector<long long>& key) const {
+        const long long below = (31 + a.R) / 32;
+        const long long slack = tune.slack > 0 ? tune.slack : kOrderSlackPrep;
+        const long long kl = tune.slice_weight > 0 ? tune.slice_weight : kOrderSliceLorenzo;
+        const long long Kt = a.n_units > 0 ? kOrderStrip * below + slack : kl;
+        key.resize((size_t)T * nstrips);
+        for (int t = 0; t < T; ++t)
+            for (int sx = 0; sx < nstrips; ++sx) key[(size_t)t * nstrips + sx] = kOrderStrip * sx + Kt * t;
+    }
+
+    // Resets what the encoder pipeline reads and writes back (before every launch).
+    cpt_status reset_pipeline() {
+        CPT_CUDA(cudaMemsetAsync(d_qhat, 0, NV * sizeof(int32_t), s));  // no reconstruction word present
+        CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep_alloc, s));
+        CPT_CUDA(cudaMemsetAsync(d_cnt64 + 1, 0, 4 * sizeof(unsigned long long), s));
+        return CPT_OK;
+    }
+
+    // ---- phase 2 (after the pipeline): compaction counts
+    cpt_status compact() {
+        tm.begin(5);
+        CPT_CUDA(ar.alloc(&d_off, N));
+        CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(N)));
+        launch_count_pack(d_qxi, d_sym, N, d_off, s);
+        CPT_CUDA(cudaMemcpyAsync(&small_h[0], d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
+        launch_exclusive_scan_u64(d_off, N, d_stmp, s);
+        CPT_CUDA(cudaMemcpyAsync(&small_h[1], d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(&small_h[2], d_cnt64, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        return CPT_OK;
+    }
+
+    // ---- phase 3 (after the totals arrived): scatter, histograms
+    cpt_status scatter_hist() {
+        const unsigned long long tot = small_h[1] + small_h[0];
+        n_qd = (size_t)(tot >> 32);
+        n_ld = (size_t)(tot & 0xFFFFFFFFull);
+        CPT_CUDA(ar.alloc(&d_qd, n_qd));
+        CPT_CUDA(ar.alloc(&d_ld, n_ld));
+        launch_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
+        // both streams advance together: histograms (+ block modes) -> code books
+        // and tile bit counts -> layout of the output -> words, copied straight
+        // into the caller's buffer
+        sx.nsym = N;
+        sx.alphabet = 33;
+        sd.nsym = n_qd;
+        sd.alphabet = 2 * kRadius;
+        nblk = has_modes ? (size_t)T * nby * nbx : 0;
+        mode_bytes = (nblk + 7) / 8;
+        CPT_CUDA(ar.alloc(&d_hist, sx.alphabet + sd.alphabet));
+        CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * (sx.alphabet + sd.alphabet), s));
+        launch_hist_u8(d_qxi, N, d_hist, s);
+        launch_hist_u16(d_qd, n_qd, d_hist + sx.alphabet, s);
+        sx.nt = (sx.nsym + kTileSyms - 1) / kTileSyms;
+        sd.nt = (sd.nsym + kTileSyms - 1) / kTileSyms;
+        // staging: histograms | block modes | tables | tile offsets
+        st_hist = sizeof(unsigned) * (sx.alphabet + sd.alphabet);
+        st_modes = (nblk + 15) & ~(size_t)15;
+        st_tab = sizeof(uint32_t) * (sx.alphabet + sd.alphabet);
+        st_toff = sizeof(unsigned long long) * (sx.nt + 1 + sd.nt + 1);
+        return CPT_OK;
+    }
+    cpt_status copy_hist() {
+        unsigned* hist_h = reinterpret_cast<unsigned*>(stage_h);
+        uint8_t* modes_h = stage_h + st_hist;
+        CPT_CUDA(cudaMemcpyAsync(hist_h, d_hist, st_hist, cudaMemcpyDeviceToHost, s));
+        if (nblk) CPT_CUDA(cudaMemcpyAsync(modes_h, d_modes, nblk, cudaMemcpyDeviceToHost, s));
+        return CPT_OK;
+    }
+
+    // ---- phase 4 (after the histograms arrived): code books, tile bit counts
+    cpt_status codebooks() {
+        unsigned* hist_h = reinterpret_cast<unsigned*>(stage_h);
+        uint32_t* tab_h = reinterpret_cast<uint32_t*>(stage_h + st_hist + st_modes);
+        unsigned long long* toff_h = reinterpret_cast<unsigned long long*>(stage_h + st_hist + st_modes + st_tab);
+        for (StreamPlan* sp : {&sx, &sd}) {
+            CPT_CUDA(ar.alloc(&sp->d_table, sp->alphabet));
+            CPT_CUDA(ar.alloc(&sp->d_tiles, sp->nt + 1));
+            CPT_CUDA(ar.alloc(&sp->d_tmp, scan_temp_elems(sp->nt + 1)));
+        }
+        cpt_status rc = plan_codebook(sx, hist_h, tab_h, s);
+        if (rc != CPT_OK) return rc;
+        rc = plan_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet, s);
+        if (rc != CPT_OK) return rc;
+        for (StreamPlan* sp : {&sx, &sd})
+            CPT_CUDA(cudaMemsetAsync(sp->d_tiles, 0, sizeof(unsigned long long) * (sp->nt + 1), s));
+        launch_tile_bits_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, s);
+        launch_tile_bits_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, s);
+        launch_exclusive_scan_u64(sx.d_tiles, sx.nt + 1, sx.d_tmp, s);
+        launch_exclusive_scan_u64(sd.d_tiles, sd.nt + 1, sd.d_tmp, s);
+        CPT_CUDA(cudaMemcpyAsync(toff_h, sx.d_tiles, sizeof(unsigned long long) * (sx.nt + 1), cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaMemcpyAsync(toff_h + sx.nt + 1, sd.d_tiles, sizeof(unsigned long long) * (sd.nt + 1),
+                                 cudaMemcpyDeviceToHost, s));
+        return CPT_OK;
+    }
+
+    // ---- phase 5 (after the tile offsets arrived): layout, header, words,
+    // verification, debug copies
+    cpt_status write_stream() {
+        const uint8_t* modes_h = stage_h + st_hist;
+        const unsigned long long* toff_h =
+            reinterpret_cast<const unsigned long long*>(stage_h + st_hist + st_modes + st_tab);
+        // block modes as bits
+        std::vector<uint8_t> packed(mode_bytes, 0);
+        for (size_t x = 0; x < nblk; ++x)
+            if (modes_h[x]) {
+                packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+                ++st.sl_blocks;
+            }
+        {
+            const unsigned long long* to = toff_h;
+            for (StreamPlan* sp : {&sx, &sd}) {
+                sp->nwords = (to[sp->nt] + 31) / 32;
+                const size_t per_chunk = kChunkSyms / kTileSyms;
+                sp->chunk_off.clear();
+                for (size_t c = 0; c * kChunkSyms < sp->nsym; ++c) sp->chunk_off.push_back(to[c * per_chunk]);
+                to += sp->nt + 1;
+            }
+        }
+        // layout: header | mode bits | model | stream Q_xi | stream Q_d | L_d
+        const size_t kHeaderBytes = 4 + 11 * 4 + 4 * 8 + 8 + 8;
+        const size_t model_bytes = has_net ? 4 + 4 * (size_t)((kNetParams + 1) / 2) : 0;
+        const size_t off_x = kHeaderBytes + mode_bytes + model_bytes;
+        const size_t off_xw = off_x + sx.header_bytes();
+        const size_t off_d = off_xw + 4 * sx.nwords;
+        const size_t off_dw = off_d + sd.header_bytes();
+        const size_t off_ld = off_dw + 4 * sd.nwords;
+        total = off_ld + 4 * n_ld;
+        obuf = static_cast<uint8_t*>(pinned_pool().get(total));
+        obuf_pinned = obuf != nullptr;
+        if (!obuf) obuf = static_cast<uint8_t*>(std::malloc(total));
+        if (!obuf) return fail(CPT_ERR_OOM, "host allocation failed");
+        Writer w{obuf};
+        w.raw("CPT1", 4);
+        w.u32(kFormat);
+        w.u32((uint32_t)H);
+        w.u32((uint32_t)W);
+        w.u32((uint32_t)T);
+        w.u32((uint32_t)k);
+        w.u32((uint32_t)eps_int);
+        w.u32((uint32_t)prm->pred);
+        w.u32((uint32_t)B);
+        w.u32((uint32_t)nstride);
+        w.u32((uint32_t)kRadius);
+        w.u32(0);
+        w.f64(dx);
+        w.f64(dy);
+        w.f64(dt);
+        w.f64(eps);
+        w.u64(n_ld);
+        w.u64(mode_bytes);
+        if (w.n != kHeaderBytes) return fail(CPT_ERR_ARG, "internal: header size");
+        if (mode_bytes) w.raw(packed.data(), mode_bytes);
+        if (model_bytes) {  // the model: parameter count, then the bfloat16 parameters two per word
+            w.u32((uint32_t)kNetParams);
+            for (int x = 0; x < kNetParams; x += 2)
+                w.u32((uint32_t)prm->model[x] | (x + 1 < kNetParams ? (uint32_t)prm->model[x + 1] << 16 : 0u));
+        }
+        write_stream_header(w, sx);
+        if (w.n != off_xw) return fail(CPT_ERR_ARG, "internal: stream layout");
+        w.n = off_d;
+        write_stream_header(w, sd);
+        if (w.n != off_dw) return fail(CPT_ERR_ARG, "internal: stream layout");
+        for (StreamPlan* sp : {&sx, &sd}) {
+            CPT_CUDA(ar.alloc(&sp->d_words, sp->nwords + 1));
+            CPT_CUDA(cudaMemsetAsync(sp->d_words, 0, sizeof(uint32_t) * (sp->nwords + 1), s));
+        }
+        launch_encode_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, sx.d_words, s);
+        launch_encode_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, sd.d_words, s);
+        if (sx.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_xw, sx.d_words, 4 * sx.nwords, cudaMemcpyDeviceToHost, s));
+        if (sd.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_dw, sd.d_words, 4 * sd.nwords, cudaMemcpyDeviceToHost, s));
+        if (n_ld) CPT_CUDA(cudaMemcpyAsync(obuf + off_ld, d_ld, 4 * n_ld, cudaMemcpyDeviceToHost, s));
+        st.launches[5] += 9;
+        tm.end();
+
+        // ---- stage 6: verification (Eq. 4 on every face, pointwise bound)
+        std::memset(vo_h, 0, sizeof(VerifyOut));
+        if (prm->verify) {
+            tm.begin(6);
+            CPT_CUDA(ar.alloc(&d_vo, 1));
+            CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
+            launch_verify(d_qhat, d_mask, d_uv, H, W, T, k, d_vo, s);
+            st.launches[6]++;
+            CPT_CUDA(cudaMemcpyAsync(vo_h, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
+            tm.end();
+        }
+        // ---- debug copies
+        if (dbg) {
+            if (dbg->q) CPT_CUDA(cudaMemcpyAsync(dbg->q, d_q, NV * 4, cudaMemcpyDeviceToHost, s));
+            if (dbg->qhat) CPT_CUDA(cudaMemcpyAsync(dbg->qhat, d_qhat, NV * 4, cudaMemcpyDeviceToHost, s));
+            if (dbg->xi) CPT_CUDA(cudaMemcpyAsync(dbg->xi, d_xiout, N * 4, cudaMemcpyDeviceToHost, s));
+            if (dbg->qxi) CPT_CUDA(cudaMemcpyAsync(dbg->qxi, d_qxi, N, cudaMemcpyDeviceToHost, s));
+            if (dbg->mask) CPT_CUDA(cudaMemcpyAsync(dbg->mask, d_mask, N * 2, cudaMemcpyDeviceToHost, s));
+            if (dbg->modes)
+                CPT_CUDA(cudaMemcpyAsync(dbg->modes, d_modes, (size_t)T * nby * nbx, cudaMemcpyDeviceToHost, s));
+            if (dbg->sym) {
+                std::vector<uint32_t> tmp(N);
+                CPT_CUDA(cudaMemcpyAsync(tmp.data(), d_sym, N * 4, cudaMemcpyDeviceToHost, s));
+                CPT_CUDA(cudaStreamSynchronize(s));
+                for (size_t v = 0; v < N; ++v) {
+                    dbg->sym[2 * v] = (uint16_t)(tmp[v] & 0xFFFFu);
+                    dbg->sym[2 * v + 1] = (uint16_t)(tmp[v] >> 16);
+                }
+            }
+        }
+        return CPT_OK;
+    }
+
+    // ---- phase 6 (after everything arrived): statistics and the verdict
+    cpt_status finish(double ms_total, double ms_pipeline, uint8_t** out, size_t* out_bytes, cpt_stats* stats) {
+        if (dbg && dbg->qhat)  // reconstruction words -> values
+            for (size_t v = 0; v < N; ++v) dbg->qhat[2 * v + 1] ^= kQhatTag;
+        tm.collect(&st);
+        st.ms_stage[4] += ms_pipeline;
+        st.launches[4]++;
+        st.ms_total = ms_total;
+        {
+            const unsigned long long Hl = H, Wl = W, Tl = T;
+            const unsigned long long E = Hl * (Wl - 1) + Wl * (Hl - 1) + (Hl - 1) * (Wl - 1);
+            st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
+        }
+        st.crossed_faces = small_h[2];
+        st.blocks = has_modes ? (uint64_t)T * nby * nbx : 0;
+        st.n_ld = n_ld;
+        st.n_qd = n_qd;
+        st.out_bytes = total;
+        st.ratio = (double)(NV * 4) / (double)total;
+        const VerifyOut& vo = *vo_h;
+        st.verify_mismatch_slice = vo.mismatch_slice;
+        st.verify_mismatch_slab = vo.mismatch_slab;
+        double linf;
+        std::memcpy(&linf, &vo.linf_bits, 8);
+        st.linf = linf;
+        if (prm->verify) {
+            const double mse = vo.sq_err / (double)NV;
+            const double range = (double)mx - (double)mn;
+            st.psnr = mse > 0 ? 20.0 * std::log10(range) - 10.0 * std::log10(mse) : INFINITY;
+        }
+        // lossless vertices: n_ld minus the unpredictable components; n_qd = 2 * (N - lossless)
+        st.lossless_vertices = N - n_qd / 2;
+        st.unpredictable = n_ld - 2 * st.lossless_vertices;
+        if (stats) *stats = st;
+        *out = obuf;
+        *out_bytes = total;
+        obuf = nullptr;  // handed to the caller
+        // The pointwise bound holds for eps >= half a fixed-point unit; below that
+        // every value is stored losslessly and the error is the rounding to 2^-k.
+        const double bound = std::max(eps, std::ldexp(0.5, -k));
+        if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= bound)))
+            return fail(CPT_ERR_VERIFY, "reconstruction changed a face predicate or exceeded the bound");
+        return CPT_OK;
+    }
+};
+
+// Process-wide cache of autotuned schedules, keyed by the predictor, the
+// block side and the size class of the launch.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, PipeTuning> g_tune_cache;
+
+// Candidate schedules of the encoder pipeline for a predictor.
+static std::vector<PipeTuning> tuning_candidates(int pred) {
+    std::vector<PipeTuning> c;
+    if (pred == CPT_PRED_LORENZO) {
+        for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0});
+    } else if (pred == CPT_PRED_SL) {
+        for (int u : {8, 16})
+            for (int share : {40, 55}) c.push_back({share, u, 0, 0});
+    } else if (pred == CPT_PRED_LEARNED) {
+        for (int share : {50, 65, 80}) c.push_back({share, 0, 0, 0});
+    } else {
+        for (int share : {35, 45, 55})
+            for (int slack : {64, 128}) c.push_back({share, 0, 0, slack});
+    }
+    return c;
+}
+
+// One compression call over jobs[0..n): every phase for every field, one host
+// synchronisation between phases, one pipeline launch for all fields.
+struct PipeTimes {
+    double ms_pipeline = 0, ms_tune = 0;
+    PipeTuning used{};
+    double ms_phase[8] = {0};  // host wall time of each phase, its synchronisation included
+};
+
+static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, cudaStream_t s, bool tune_req,
+                           PipeTuning tune, PipeTimes* times) {
+    const int nsm = sm_count();
+    auto clk = std::chrono::steady_clock::now();
+    auto mark = [&](int phase) {
+        const auto now = std::chrono::steady_clock::now();
+        if (times) times->ms_phase[phase] += std::chrono::duration<double, std::milli>(now - clk).count();
+        clk = now;
+    };
+    // pinned small values of every field
+    const size_t per_rb = sizeof(RangePartial) * (size_t)nsm * 4;
+    const size_t per_job = ((per_rb + 15) & ~(size_t)15) + 16 * 8 + sizeof(VerifyOut) + 16;
+    static thread_local Staging t_small;
+    uint8_t* small = static_cast<uint8_t*>(t_small.get(per_job * (size_t)n));
+    if (!small) return fail(CPT_ERR_OOM, "pinned staging allocation failed");
+    for (int f = 0; f < n; ++f) {
+        uint8_t* b = small + per_job * f;
+        jobs[f]->part_h = reinterpret_cast<RangePartial*>(b);
+        jobs[f]->small_h = reinterpret_cast<unsigned long long*>(b + ((per_rb + 15) & ~(size_t)15));
+        jobs[f]->vo_h = reinterpret_cast<VerifyOut*>(b + ((per_rb + 15) & ~(size_t)15) + 16 * 8);
+    }
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->begin(nsm);
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    mark(0);
+
+    // call-wide device state: the log2 table, the learned predictor, the
+    // pipeline's queue, ticket and status
+    DevArena ar(s);
+    unsigned long long* d_lg;
+    CPT_CUDA(ar.alloc(&d_lg, kLog2Tab));
+    launch_log2_table(d_lg, kLog2Tab, s);
+    NetDev net{};
     const bool has_net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
-    const bool has_modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
-    if (has_net && !prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
-    const int B = prm->block > 0 ? prm->block : 16;
-    const int nstride = prm->stride > 0 ? prm->stride : 2;
-    if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
-    const double dx = dims->dx > 0 ? dims->dx : 1.0, dy = dims->dy > 0 ? dims->dy : 1.0;
-    const double dt = dims->dt > 0 ? dims->dt : 1.0;
-    const size_t N = (size_t)H * W * T, NV = 2 * N;
-    cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
+    if (has_net) {
+        if (!prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
+        float* d_net;
+        CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
+        cpt_status rc = upload_net(prm->model, d_net, &net, s);
+        if (rc != CPT_OK) return rc;
+    }
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->plan(nsm, d_lg, &net, tune);
+        if (rc != CPT_OK) return rc;
+    }
+    mark(1);
+    size_t max_queue = 0, max_items = 0;
+    for (int f = 0; f < n; ++f) {
+        max_queue += jobs[f]->nprep_alloc;
+        max_items += (size_t)jobs[f]->T * jobs[f]->nstrips;
+    }
+    if (max_queue >= 0x7FFFFFFFull || max_items >= 0x7FFFFFFFull)
+        return fail(CPT_ERR_UNSUPPORTED, "too many pipeline items in one launch");
+    unsigned *d_queue, *d_ticket;
+    int* d_status;
+    int4* d_order;
+    SliceArgs* d_fields;
+    CPT_CUDA(ar.alloc(&d_queue, max_queue + 2));
+    CPT_CUDA(ar.alloc(&d_ticket, 1));
+    CPT_CUDA(ar.alloc(&d_status, 1));
+    CPT_CUDA(ar.alloc(&d_order, max_items));
+    CPT_CUDA(ar.alloc(&d_fields, (size_t)n));
+    std::vector<int4> order;
+    std::vector<SliceArgs> fields((size_t)n);
+    PipeArgs P{};
+
+    cudaEvent_t e0, e1;
+    CPT_CUDA(cudaEventCreate(&e0));
+    CPT_CUDA(cudaEventCreate(&e1));
+    struct EvG { cudaEvent_t a, b; ~EvG() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{e0, e1};
+
+    // Sets up and launches the pipeline over every field under a schedule;
+    // *ms: the launch's device time (CUDA events around the kernel).
+    auto launch = [&](const PipeTuning& tu, double* ms) -> cpt_status {
+        unsigned qlen = 0;
+        for (int f = 0; f < n; ++f) {
+            cpt_status rc = jobs[f]->set_units(tu);
+            if (rc != CPT_OK) return rc;
+            jobs[f]->a.unit_base = qlen;
+            qlen += jobs[f]->a.n_units;
+        }
+        // ticket order: each field's items by its own key, merged by key
+        // (then field, then t); a field's relative order is kept
+        struct Item { long long key; int f, t, sx; };
+        std::vector<Item> items;
+        items.reserve(max_items);
+        std::vector<long long> key;
+        for (int f = 0; f < n; ++f) {
+            jobs[f]->ticket_keys(tu, key);
+            const int ns = jobs[f]->nstrips;
+            for (int t = 0; t < jobs[f]->T; ++t)
+                for (int sx = 0; sx < ns; ++sx) items.push_back({key[(size_t)t * ns + sx], f, t, sx});
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item& p, const Item& q) {
+            if (p.key != q.key) return p.key < q.key;
+            if (p.f != q.f) return p.f < q.f;
+            return p.t < q.t;
+        });
+        order.resize(items.size());
+        for (size_t x = 0; x < items.size(); ++x) order[x] = make_int4(items[x].f, items[x].t, items[x].sx, 0);
+        for (int f = 0; f < n; ++f) {
+            SliceArgs& A = jobs[f]->a;
+            A.qslot = d_queue + 2;
+            A.qtail = d_queue + 1;
+            A.status = d_status;
+            A.queue_len = qlen;
+            A.timeout_ns = 2000000000ll;
+            fields[f] = A;
+            cpt_status rc = jobs[f]->reset_pipeline();
+            if (rc != CPT_OK) return rc;
+        }
+        CPT_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int4) * order.size(), cudaMemcpyHostToDevice, s));
+        CPT_CUDA(cudaMemcpyAsync(d_fields, fields.data(), sizeof(SliceArgs) * n, cudaMemcpyHostToDevice, s));
+        CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * ((size_t)qlen + 2), s));
+        CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
+        CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        P.one = fields[0];
+        P.fields = d_fields;
+        P.nfields = n;
+        P.order = d_order;
+        P.total_items = (unsigned)order.size();
+        P.ticket = d_ticket;
+        P.qhead = d_queue;
+        P.queue_len = qlen;
+        P.status = d_status;
+        P.timeout_ns = 2000000000ll;
+        CPT_CUDA(cudaEventRecord(e0, s));
+        CPT_CUDA(launch_encode_pipeline(P, (int)prm->pred, nsm, tu, s));
+        CPT_CUDA(cudaEventRecord(e1, s));
+        CPT_CUDA(cudaStreamSynchronize(s));  // the host tables outlive their copies
+        float m = 0.f;
+        CPT_CUDA(cudaEventElapsedTime(&m, e0, e1));
+        *ms = m;
+        int status = 0;
+        CPT_CUDA(cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (status != 0) return fail((cpt_status)status, "wavefront wait timed out");
+        return CPT_OK;
+    };
+
+    if (tune_req) {
+        size_t nv = 0;
+        for (int f = 0; f < n; ++f) nv += jobs[f]->N;
+        const int cls = (int)std::lround(std::log2((double)std::max<size_t>(nv, 1)));
+        const int B0 = jobs[0]->B;
+        const auto ck = std::make_tuple((int)prm->pred, B0, cls, n > 1 ? 1 : 0);
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(ck);
+            if (it != g_tune_cache.end()) { tune = it->second; hit = true; }
+        }
+        if (!hit) {
+            double best = INFINITY;
+            PipeTuning bt{};
+            for (const PipeTuning& c : tuning_candidates((int)prm->pred)) {
+                double ms = 0;
+                cpt_status rc = launch(c, &ms);
+                if (rc != CPT_OK) return rc;
+                if (times) times->ms_tune += ms;
+                if (ms < best) { best = ms; bt = c; }
+            }
+            tune = bt;
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune_cache[ck] = tune;
+        }
+    }
+    double ms_pipe = 0;
+    {
+        cpt_status rc = launch(tune, &ms_pipe);
+        if (rc != CPT_OK) return rc;
+    }
+    if (times) {
+        times->ms_pipeline = ms_pipe;
+        times->used = tune;
+    }
+    mark(2);
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->compact();
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    mark(3);
+    size_t stage_total = 0;
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->scatter_hist();
+        if (rc != CPT_OK) return rc;
+        stage_total += (jobs[f]->staging_bytes() + 63) & ~(size_t)63;
+    }
+    uint8_t* stage = static_cast<uint8_t*>(t_staging.get(stage_total));
+    if (!stage) return fail(CPT_ERR_OOM, "pinned staging allocation failed");
+    for (int f = 0; f < n; ++f) {
+        jobs[f]->stage_h = stage;
+        stage += (jobs[f]->staging_bytes() + 63) & ~(size_t)63;
+        cpt_status rc = jobs[f]->copy_hist();
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    mark(4);
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->codebooks();
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    mark(5);
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->write_stream();
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaStreamSynchronize(s));
+    mark(6);
+    return CPT_OK;
+}
+
+static cpt_status check_device() {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
         return fail(CPT_ERR_CUDA, "no CUDA device available");
     }
     retain_pool_memory();
-    cpt_stats st;
-    std::memset(&st, 0, sizeof(st));
-    StageTimer tm(s, true);
+    return CPT_OK;
+}
+
+static PipeTuning tuning_of(const cpt_params* prm) {
+    return PipeTuning{prm->schedule[0], prm->schedule[1], prm->schedule[2], prm->schedule[3]};
+}
+
+static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
+                                size_t* out_bytes, cpt_stats* stats, const cpt_debug* dbg) {
+    if (!uv || !dims || !prm || !out || !out_bytes) return fail(CPT_ERR_ARG, "null argument");
+    cpt_status rc = check_device();
+    if (rc != CPT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
     cudaEvent_t ev0, ev1;
     CPT_CUDA(cudaEventCreate(&ev0));
     CPT_CUDA(cudaEventCreate(&ev1));
     struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
-    DevArena ar(s);
+    FieldJob job(s, true);
+    job.uv = uv;
+    job.dims = *dims;
+    job.prm = prm;
+    job.dbg = dbg;
     CPT_CUDA(cudaEventRecord(ev0, s));
-
-    // input on the device, 16-byte aligned
-    const float* d_uv = uv;
-    if (!is_device_pointer(uv) || (reinterpret_cast<uintptr_t>(uv) & 15u)) {
-        float* tmp;
-        CPT_CUDA(ar.alloc(&tmp, NV));
-        CPT_CUDA(cudaMemcpyAsync(tmp, uv, NV * sizeof(float), cudaMemcpyDefault, s));
-        d_uv = tmp;
-    }
-    const int nsm = sm_count();
-
-    // ---- stage 0: range, scale, fixed point
-    tm.begin(0);
-    const int rblocks = nsm * 4;
-    RangePartial* d_part;
-    CPT_CUDA(ar.alloc(&d_part, rblocks));
-    launch_range(d_uv, NV, d_part, rblocks, s);
-    st.launches[0]++;
-    std::vector<RangePartial> part(rblocks);
-    CPT_CUDA(cudaMemcpyAsync(part.data(), d_part, sizeof(RangePartial) * rblocks, cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
-    float mn = INFINITY, mx = -INFINITY, am = 0.f;
-    unsigned bad = 0;
-    for (auto& p : part) { mn = std::min(mn, p.mn); mx = std::max(mx, p.mx); am = std::max(am, p.amax); bad |= p.bad; }
-    if (bad) return fail(CPT_ERR_ARG, "input holds a non-finite value");
-    int k = 0;
-    if (am > 0.f) { int e; std::frexp((double)am, &e); k = 23 - e; }
-    const double eps = prm->mode == CPT_EB_REL ? prm->eb * ((double)mx - (double)mn) : prm->eb;
-    double ef = std::floor(std::ldexp(eps, k) - 0.5);
-    int eps_int = !(ef > 0) ? 0 : (ef > 8388608.0 ? 8388608 : (int)ef);
-    st.scale_log2 = k;
-    st.eps_int = eps_int;
-    st.eps = eps;
-    int32_t *d_q, *d_qhat;
-    CPT_CUDA(ar.alloc(&d_q, NV));
-    CPT_CUDA(ar.alloc(&d_qhat, NV));
-    launch_to_fixed(d_uv, NV, k, d_q, nsm * 8, s);
-    st.launches[0]++;
-    tm.end();
-
-    // ---- stage 1: crossed-face masks (C)
-    tm.begin(1);
-    uint16_t* d_mask;
-    unsigned long long* d_cnt64;  // [0] crossed faces, [1..4] encoder counters
-    CPT_CUDA(ar.alloc(&d_mask, N));
-    CPT_CUDA(ar.alloc(&d_cnt64, 8));
-    CPT_CUDA(cudaMemsetAsync(d_cnt64, 0, 8 * sizeof(unsigned long long), s));
-    launch_face_masks(d_q, H, W, T, d_mask, d_cnt64, s);
-    st.launches[1]++;
-    tm.end();
-
-    // ---- stage 4: the encoder pipeline (MoP / SL, incident-face bounds, wavefront)
-    const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
-    const int nstrips = (H + 31) / 32, nchunks = (W + 31) / 32;
-    if (has_modes && (32 % B != 0 || B < 4))
-        return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
-    const bool want_sl = prm->pred != CPT_PRED_LORENZO && T > 1 && eps_int > 0;
-    uint8_t *d_qxi, *d_modes;
-    uint32_t* d_sym;
-    int *d_status, *d_xiout = nullptr;
-    int2 *d_psl, *d_cls;
-    unsigned* d_clsm;
-    unsigned *d_prep, *d_ticket;
-    CPT_CUDA(ar.alloc(&d_qxi, N));
-    CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
-    CPT_CUDA(ar.alloc(&d_sym, N));
-    CPT_CUDA(ar.alloc(&d_cls, N));
-    CPT_CUDA(ar.alloc(&d_clsm, N));
-    CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
-    CPT_CUDA(ar.alloc(&d_status, 1));
-    // side of a prep unit: MoP blocks fit whole units (16, or 32 for B = 32);
-    // pure SL uses 8 (a smaller unit enters the queue earlier and is done sooner)
-    const int Uh = has_modes ? (B == 32 ? 32 : 16) : 8;
-    const size_t nprep = (size_t)T * ((H + Uh - 1) / Uh) * ((W + Uh - 1) / Uh);
-    CPT_CUDA(ar.alloc(&d_prep, nprep));
-    CPT_CUDA(ar.alloc(&d_ticket, 1));
-    if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
-    CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
-    CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
-    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
-    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
-    SliceArgs a;
-    a.q = reinterpret_cast<const int2*>(d_q);
-    a.qhat = reinterpret_cast<int2*>(d_qhat);
-    a.mask = d_mask;
-    a.cls = d_cls;
-    a.cls_m = d_clsm;
-    a.psl = d_psl;
-    a.modes = d_modes;
-    a.qxi = d_qxi;
-    a.sym = d_sym;
-    a.xi_out = d_xiout;
-    a.prep_done = d_prep;
-    a.ticket = d_ticket;
-    a.status = d_status;
-    a.counters = d_cnt64 + 1;
-    a.H = H; a.W = W; a.T = T;
-    a.eps_int = eps_int;
-    a.pred = (int)prm->pred;
-    a.B = B; a.n = nstride; a.nby = nby; a.nbx = nbx;
-    a.nchunks = nchunks;
-    a.cfl_x = std::ldexp(dt / dx, -k);
-    a.cfl_y = std::ldexp(dt / dy, -k);
-    // Reach of the semi-Lagrangian back-trace into slice t-1: no
-    // reconstruction exceeds max|q| + E in magnitude, every displacement is
-    // at most that times CFL, the bilinear stencil adds one cell, and one
-    // more cell covers rounding of the positions.
-    a.R = 0;
-    if (want_sl && has_net) {
-        a.R = kNetReach;  // the net's receptive field: 3 cells around a vertex
-    } else if (want_sl) {
-        const double qmax = std::ceil((double)am * std::ldexp(1.0, k)) + (eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)eps_int))) : 0.0);
-        const double reach = std::ceil(qmax * std::max(a.cfl_x, a.cfl_y)) + 2.0;
-        a.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
-    }
-    a.timeout_ns = 2000000000ll;
-    if (has_net) {
-        float* d_net;
-        CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
-        cpt_status rc = upload_net(prm->model, d_net, &a.net, s);
-        if (rc != CPT_OK) return rc;
-    }
-    // prep units (SL and MoP): U x U squares of slices 1..T-1, in a ready queue
-    a.U = Uh;
-    a.nur = (H + a.U - 1) / a.U;
-    a.nuc = (W + a.U - 1) / a.U;
-    a.n_units = 0;
-    if (want_sl) {
-        const unsigned long long nu = (unsigned long long)(T - 1) * a.nur * a.nuc;
-        if (nu >= 0xFFFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many prediction units");
-        a.n_units = (unsigned)nu;
-    }
-    unsigned* d_queue;
-    CPT_CUDA(ar.alloc(&d_queue, (size_t)a.n_units + 2));
-    CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * ((size_t)a.n_units + 2), s));
-    a.qhead = d_queue;
-    a.qtail = d_queue + 1;
-    a.qslot = d_queue + 2;
-    a.prep_warps = 0;
-    // (t, s) in ticket order: by key = Ks s + Kt t, then t.  A wave depends on
-    // the waves above it and, through its prep units, on slice t-1 down to
-    // (31 + R) / 32 strips below it, so Kt exceeds Ks times that with prep
-    // units (Kt > Ks * strips below); without them any Kt > 0 keeps
-    // dependencies at smaller tickets, and a small Kt lets consecutive slices
-    // run a few steps apart.
-    {
-        const long long below = (31 + a.R) / 32;
-        const long long Kt = a.n_units > 0 ? kOrderStrip * below + kOrderSlackPrep : kOrderSliceLorenzo;
-        std::vector<int2> ord;
-        ord.reserve((size_t)T * nstrips);
-        for (int t = 0; t < T; ++t)
-            for (int sx = 0; sx < nstrips; ++sx) ord.push_back(make_int2(t, sx));
-        std::stable_sort(ord.begin(), ord.end(), [&](int2 p, int2 q) {
-            const long long kp = kOrderStrip * p.y + Kt * p.x, kq = kOrderStrip * q.y + Kt * q.x;
-            return kp != kq ? kp < kq : p.x < q.x;
-        });
-        int2* d_order;
-        CPT_CUDA(ar.alloc(&d_order, ord.size()));
-        CPT_CUDA(cudaMemcpyAsync(d_order, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice, s));
-        a.order = d_order;
-        unsigned long long* d_lg;
-        CPT_CUDA(ar.alloc(&d_lg, kLog2Tab));
-        launch_log2_table(d_lg, kLog2Tab, s);
-        a.log2tab = d_lg;
-        CPT_CUDA(cudaStreamSynchronize(s));  // the host order table must outlive the copy
-    }
-    tm.begin(3);
-    launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, s);
-    st.launches[3]++;
-    tm.end();
-    tm.begin(4);
-    CPT_CUDA(cudaMemsetAsync(d_qhat, 0, NV * sizeof(int32_t), s));  // no reconstruction word present
-    CPT_CUDA(launch_encode_pipeline(a, nsm, s));
-    st.launches[4]++;
-    tm.end();
-
-    // ---- stage 5: compaction + entropy coding
-    tm.begin(5);
-    unsigned long long *d_off, *d_stmp;
-    CPT_CUDA(ar.alloc(&d_off, N));
-    CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(N)));
-    launch_count_pack(d_qxi, d_sym, N, d_off, s);
-    unsigned long long last_cnt = 0, last_off = 0;
-    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    launch_exclusive_scan_u64(d_off, N, d_stmp, s);
-    CPT_CUDA(cudaMemcpyAsync(&last_off, d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    int status = 0;
-    unsigned long long cnt_h[8];
-    CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaMemcpyAsync(cnt_h, d_cnt64, sizeof(cnt_h), cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
-    if (status != 0) return fail((cpt_status)status, "wavefront wait timed out");
-    const unsigned long long tot = last_off + last_cnt;
-    const size_t n_qd = (size_t)(tot >> 32), n_ld = (size_t)(tot & 0xFFFFFFFFull);
-    uint16_t* d_qd;
-    int32_t* d_ld;
-    CPT_CUDA(ar.alloc(&d_qd, n_qd));
-    CPT_CUDA(ar.alloc(&d_ld, n_ld));
-    launch_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
-    // both streams advance together: histograms (+ block modes) -> code books
-    // and tile bit counts -> layout of the output -> words, copied straight
-    // into the caller's buffer
-    StreamPlan sx, sd;
-    sx.nsym = N;
-    sx.alphabet = 33;
-    sd.nsym = n_qd;
-    sd.alphabet = 2 * kRadius;
-    const size_t nblk = has_modes ? (size_t)T * nby * nbx : 0;
-    const size_t mode_bytes = (nblk + 7) / 8;
-    unsigned* d_hist;
-    CPT_CUDA(ar.alloc(&d_hist, sx.alphabet + sd.alphabet));
-    CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * (sx.alphabet + sd.alphabet), s));
-    launch_hist_u8(d_qxi, N, d_hist, s);
-    launch_hist_u16(d_qd, n_qd, d_hist + sx.alphabet, s);
-    sx.nt = (sx.nsym + kTileSyms - 1) / kTileSyms;
-    sd.nt = (sd.nsym + kTileSyms - 1) / kTileSyms;
-    // staging: histograms | block modes | tables | tile offsets
-    const size_t st_hist = sizeof(unsigned) * (sx.alphabet + sd.alphabet);
-    const size_t st_modes = (nblk + 15) & ~(size_t)15;
-    const size_t st_tab = sizeof(uint32_t) * (sx.alphabet + sd.alphabet);
-    const size_t st_toff = sizeof(unsigned long long) * (sx.nt + 1 + sd.nt + 1);
-    uint8_t* stage = static_cast<uint8_t*>(t_staging.get(st_hist + st_modes + st_tab + st_toff + 64));
-    if (!stage) return fail(CPT_ERR_OOM, "pinned staging allocation failed");
-    unsigned* hist_h = reinterpret_cast<unsigned*>(stage);
-    uint8_t* modes_h = stage + st_hist;
-    uint32_t* tab_h = reinterpret_cast<uint32_t*>(stage + st_hist + st_modes);
-    unsigned long long* toff_h = reinterpret_cast<unsigned long long*>(stage + st_hist + st_modes + st_tab);
-    CPT_CUDA(cudaMemcpyAsync(hist_h, d_hist, st_hist, cudaMemcpyDeviceToHost, s));
-    if (nblk) CPT_CUDA(cudaMemcpyAsync(modes_h, d_modes, nblk, cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
-    for (StreamPlan* sp : {&sx, &sd}) {
-        CPT_CUDA(ar.alloc(&sp->d_table, sp->alphabet));
-        CPT_CUDA(ar.alloc(&sp->d_tiles, sp->nt + 1));
-        CPT_CUDA(ar.alloc(&sp->d_tmp, scan_temp_elems(sp->nt + 1)));
-    }
-    cpt_status rc = plan_codebook(sx, hist_h, tab_h, s);
+    FieldJob* jp = &job;
+    PipeTimes pt;
+    rc = run_jobs(&jp, 1, prm, s, prm->tune != 0, tuning_of(prm), &pt);
     if (rc != CPT_OK) return rc;
-    rc = plan_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet, s);
-    if (rc != CPT_OK) return rc;
-    for (StreamPlan* sp : {&sx, &sd}) CPT_CUDA(cudaMemsetAsync(sp->d_tiles, 0, sizeof(unsigned long long) * (sp->nt + 1), s));
-    launch_tile_bits_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, s);
-    launch_tile_bits_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, s);
-    launch_exclusive_scan_u64(sx.d_tiles, sx.nt + 1, sx.d_tmp, s);
-    launch_exclusive_scan_u64(sd.d_tiles, sd.nt + 1, sd.d_tmp, s);
-    CPT_CUDA(cudaMemcpyAsync(toff_h, sx.d_tiles, sizeof(unsigned long long) * (sx.nt + 1), cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaMemcpyAsync(toff_h + sx.nt + 1, sd.d_tiles, sizeof(unsigned long long) * (sd.nt + 1),
-                             cudaMemcpyDeviceToHost, s));
-    // block modes as bits (host) while the tile counts run
-    std::vector<uint8_t> packed(mode_bytes, 0);
-    CPT_CUDA(cudaStreamSynchronize(s));
-    for (size_t x = 0; x < nblk; ++x)
-        if (modes_h[x]) {
-            packed[x >> 3] |= (uint8_t)(1u << (x & 7));
-            ++st.sl_blocks;
-        }
-    {
-        const unsigned long long* to = toff_h;
-        for (StreamPlan* sp : {&sx, &sd}) {
-            sp->nwords = (to[sp->nt] + 31) / 32;
-            const size_t per_chunk = kChunkSyms / kTileSyms;
-            sp->chunk_off.clear();
-            for (size_t c = 0; c * kChunkSyms < sp->nsym; ++c) sp->chunk_off.push_back(to[c * per_chunk]);
-            to += sp->nt + 1;
-        }
-    }
-    // layout: header | mode bits | stream Q_xi | stream Q_d | L_d
-    const size_t kHeaderBytes = 4 + 11 * 4 + 4 * 8 + 8 + 8;
-    const size_t model_bytes = has_net ? 4 + 4 * (size_t)((kNetParams + 1) / 2) : 0;
-    const size_t off_x = kHeaderBytes + mode_bytes + model_bytes;
-    const size_t off_xw = off_x + sx.header_bytes();
-    const size_t off_d = off_xw + 4 * sx.nwords;
-    const size_t off_dw = off_d + sd.header_bytes();
-    const size_t off_ld = off_dw + 4 * sd.nwords;
-    const size_t total = off_ld + 4 * n_ld;
-    uint8_t* obuf = static_cast<uint8_t*>(pinned_pool().get(total));
-    const bool obuf_pinned = obuf != nullptr;
-    if (!obuf) obuf = static_cast<uint8_t*>(std::malloc(total));
-    if (!obuf) return fail(CPT_ERR_OOM, "host allocation failed");
-    struct OutGuard {  // released on any error before it is handed to the caller
-        uint8_t* p;
-        bool pinned;
-        ~OutGuard() {
-            if (p && !(pinned && pinned_pool().put(p))) std::free(p);
-        }
-    } og{obuf, obuf_pinned};
-    Writer w{obuf};
-    w.raw("CPT1", 4);
-    w.u32(kFormat);
-    w.u32((uint32_t)H);
-    w.u32((uint32_t)W);
-    w.u32((uint32_t)T);
-    w.u32((uint32_t)k);
-    w.u32((uint32_t)eps_int);
-    w.u32((uint32_t)prm->pred);
-    w.u32((uint32_t)B);
-    w.u32((uint32_t)nstride);
-    w.u32((uint32_t)kRadius);
-    w.u32(0);
-    w.f64(dx);
-    w.f64(dy);
-    w.f64(dt);
-    w.f64(eps);
-    w.u64(n_ld);
-    w.u64(mode_bytes);
-    if (w.n != kHeaderBytes) return fail(CPT_ERR_ARG, "internal: header size");
-    if (mode_bytes) w.raw(packed.data(), mode_bytes);
-    if (model_bytes) {  // the model: parameter count, then the bfloat16 parameters two per word
-        w.u32((uint32_t)kNetParams);
-        for (int x = 0; x < kNetParams; x += 2)
-            w.u32((uint32_t)prm->model[x] | (x + 1 < kNetParams ? (uint32_t)prm->model[x + 1] << 16 : 0u));
-    }
-    write_stream_header(w, sx);
-    if (w.n != off_xw) return fail(CPT_ERR_ARG, "internal: stream layout");
-    w.n = off_d;
-    write_stream_header(w, sd);
-    if (w.n != off_dw) return fail(CPT_ERR_ARG, "internal: stream layout");
-    for (StreamPlan* sp : {&sx, &sd}) {
-        CPT_CUDA(ar.alloc(&sp->d_words, sp->nwords + 1));
-        CPT_CUDA(cudaMemsetAsync(sp->d_words, 0, sizeof(uint32_t) * (sp->nwords + 1), s));
-    }
-    launch_encode_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, sx.d_words, s);
-    launch_encode_u16(d_qd, sd.nsym, sd.d_table, sd.d_tiles, sd.d_words, s);
-    if (sx.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_xw, sx.d_words, 4 * sx.nwords, cudaMemcpyDeviceToHost, s));
-    if (sd.nwords) CPT_CUDA(cudaMemcpyAsync(obuf + off_dw, sd.d_words, 4 * sd.nwords, cudaMemcpyDeviceToHost, s));
-    if (n_ld) CPT_CUDA(cudaMemcpyAsync(obuf + off_ld, d_ld, 4 * n_ld, cudaMemcpyDeviceToHost, s));
-    st.launches[5] += 9;
-    tm.end();
-
-    // ---- stage 6: verification (Eq. 4 on every face, pointwise bound)
-    VerifyOut vo;
-    std::memset(&vo, 0, sizeof(vo));
-    if (prm->verify) {
-        tm.begin(6);
-        VerifyOut* d_vo;
-        CPT_CUDA(ar.alloc(&d_vo, 1));
-        CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
-        launch_verify(d_qhat, d_mask, d_uv, H, W, T, k, d_vo, s);
-        st.launches[6]++;
-        CPT_CUDA(cudaMemcpyAsync(&vo, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
-        tm.end();
-    }
-    // ---- debug copies
-    if (dbg) {
-        if (dbg->q) CPT_CUDA(cudaMemcpyAsync(dbg->q, d_q, NV * 4, cudaMemcpyDeviceToHost, s));
-        if (dbg->qhat) CPT_CUDA(cudaMemcpyAsync(dbg->qhat, d_qhat, NV * 4, cudaMemcpyDeviceToHost, s));
-        if (dbg->xi) CPT_CUDA(cudaMemcpyAsync(dbg->xi, d_xiout, N * 4, cudaMemcpyDeviceToHost, s));
-        if (dbg->qxi) CPT_CUDA(cudaMemcpyAsync(dbg->qxi, d_qxi, N, cudaMemcpyDeviceToHost, s));
-        if (dbg->mask) CPT_CUDA(cudaMemcpyAsync(dbg->mask, d_mask, N * 2, cudaMemcpyDeviceToHost, s));
-        if (dbg->modes) CPT_CUDA(cudaMemcpyAsync(dbg->modes, d_modes, (size_t)T * nby * nbx, cudaMemcpyDeviceToHost, s));
-        if (dbg->sym) {
-            std::vector<uint32_t> tmp(N);
-            CPT_CUDA(cudaMemcpyAsync(tmp.data(), d_sym, N * 4, cudaMemcpyDeviceToHost, s));
-            CPT_CUDA(cudaStreamSynchronize(s));
-            for (size_t v = 0; v < N; ++v) {
-                dbg->sym[2 * v] = (uint16_t)(tmp[v] & 0xFFFFu);
-                dbg->sym[2 * v + 1] = (uint16_t)(tmp[v] >> 16);
-            }
-        }
-    }
     CPT_CUDA(cudaEventRecord(ev1, s));
     CPT_CUDA(cudaStreamSynchronize(s));
     CPT_CUDA(cudaGetLastError());
-    if (dbg && dbg->qhat)  // reconstruction words -> values
-        for (size_t v = 0; v < N; ++v) dbg->qhat[2 * v + 1] ^= kQhatTag;
-
-    *out = obuf;
-    *out_bytes = total;
-    og.p = nullptr;  // handed to the caller
-
     float ms_total = 0.f;
     cudaEventElapsedTime(&ms_total, ev0, ev1);
-    tm.collect(&st);
-    st.ms_total = ms_total;
-    st.faces = 0;
-    {
-        const unsigned long long Hl = H, Wl = W, Tl = T;
-        const unsigned long long E = Hl * (Wl - 1) + Wl * (Hl - 1) + (Hl - 1) * (Wl - 1);
-        st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
+    return job.finish(ms_total, pt.ms_pipeline, out, out_bytes, stats);
+}
+
+// Many fields, one set of parameters: fields are taken in order into groups
+// whose device memory fits the budget; each group is one run of every phase
+// with one pipeline launch.
+static cpt_status compress_batch_impl(const float* const* uv, const cpt_dims* dims, int nfields,
+                                      const cpt_params* prm, size_t budget, uint8_t** out, size_t* out_bytes,
+                                      cpt_stats* stats, cpt_batch_stats* bst) {
+    if (!uv || !dims || !prm || !out || !out_bytes || nfields < 1) return fail(CPT_ERR_ARG, "null argument or no field");
+    for (int f = 0; f < nfields; ++f) {
+        out[f] = nullptr;
+        out_bytes[f] = 0;
+        if (!uv[f]) return fail(CPT_ERR_ARG, "null field");
     }
-    st.crossed_faces = cnt_h[0];
-    st.blocks = has_modes ? (uint64_t)T * nby * nbx : 0;
-    st.n_ld = n_ld;
-    st.n_qd = n_qd;
-    st.out_bytes = total;
-    st.ratio = (double)(NV * 4) / (double)total;
-    // lossless and unpredictable counts from the compaction totals
-    {
-        std::vector<unsigned> hx(33, 0);
-        (void)hx;
+    cpt_status rc = check_device();
+    if (rc != CPT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        CPT_CUDA(cudaMemGetInfo(&fr, &tot));
+        budget = fr / 10 * 6;
     }
-    st.verify_mismatch_slice = vo.mismatch_slice;
-    st.verify_mismatch_slab = vo.mismatch_slab;
-    double linf;
-    std::memcpy(&linf, &vo.linf_bits, 8);
-    st.linf = linf;
-    if (prm->verify) {
-        double mse = vo.sq_err / (double)NV;
-        double range = (double)mx - (double)mn;
-        st.psnr = mse > 0 ? 20.0 * std::log10(range) - 10.0 * std::log10(mse) : INFINITY;
+    cpt_batch_stats b;
+    std::memset(&b, 0, sizeof(b));
+    b.device_budget = budget;
+    cudaEvent_t ev0, ev1;
+    CPT_CUDA(cudaEventCreate(&ev0));
+    CPT_CUDA(cudaEventCreate(&ev1));
+    struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
+    CPT_CUDA(cudaEventRecord(ev0, s));
+    auto release_all = [&]() {
+        for (int f = 0; f < nfields; ++f) {
+            if (out[f] && !pinned_pool().put(out[f])) std::free(out[f]);
+            out[f] = nullptr;
+            out_bytes[f] = 0;
+        }
+    };
+    cpt_status verdict = CPT_OK;
+    int first = 0;
+    while (first < nfields) {
+        // the next group: at least one field, then as many as fit the budget
+        int last = first;
+        size_t need = 0;
+        while (last < nfields) {
+            const size_t m = FieldJob::device_bytes(dims[last], !is_device_pointer(uv[last]));
+            if (last > first && need + m > budget) break;
+            need += m;
+            ++last;
+        }
+        std::vector<std::unique_ptr<FieldJob>> jobs;
+        std::vector<FieldJob*> jp;
+        for (int f = first; f < last; ++f) {
+            jobs.emplace_back(new FieldJob(s, true));
+            FieldJob& j = *jobs.back();
+            j.uv = uv[f];
+            j.dims = dims[f];
+            j.prm = prm;
+            jp.push_back(&j);
+        }
+        PipeTimes pt;
+        rc = run_jobs(jp.data(), (int)jp.size(), prm, s, prm->tune != 0, tuning_of(prm), &pt);
+        if (rc != CPT_OK) {
+            const std::string msg = g_last_error;
+            jobs.clear();
+            release_all();
+            return fail(rc, "field group " + std::to_string(first) + ".." + std::to_string(last - 1) + ": " + msg);
+        }
+        CPT_CUDA(cudaStreamSynchronize(s));
+        CPT_CUDA(cudaGetLastError());
+        b.ms_pipeline += pt.ms_pipeline;
+        b.ms_tune += pt.ms_tune;
+        for (int x = 0; x < 8; ++x) b.ms_phase[x] += pt.ms_phase[x];
+        b.groups++;
+        b.schedule[0] = pt.used.prep_share;
+        b.schedule[1] = pt.used.sl_unit;
+        b.schedule[2] = pt.used.slice_weight;
+        b.schedule[3] = pt.used.slack;
+        for (int f = first; f < last; ++f) {
+            FieldJob& j = *jobs[f - first];
+            cpt_stats st1;
+            cpt_status r1 = j.finish(0.0, pt.ms_pipeline, &out[f], &out_bytes[f], &st1);
+            if (r1 == CPT_ERR_VERIFY && verdict == CPT_OK) verdict = r1;
+            else if (r1 != CPT_OK && r1 != CPT_ERR_VERIFY) { jobs.clear(); release_all(); return r1; }
+            for (int x = 0; x < 8; ++x)
+                if (x != 4) b.launches += st1.launches[x];
+            b.in_bytes += 8ull * j.N;
+            b.out_bytes += st1.out_bytes;
+            if (stats) stats[f] = st1;
+        }
+        b.launches += 1;  // one pipeline launch for the group
+        first = last;
     }
-    // lossless vertices: n_ld minus the unpredictable components; n_qd = 2 * (N - lossless)
-    st.lossless_vertices = N - n_qd / 2;
-    st.unpredictable = n_ld - 2 * st.lossless_vertices;
-    if (stats) *stats = st;
-    // The pointwise bound holds for eps >= half a fixed-point unit; below that
-    // every value is stored losslessly and the error is the rounding to 2^-k.
-    const double bound = std::max(eps, std::ldexp(0.5, -k));
-    if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= bound)))
-        return fail(CPT_ERR_VERIFY, "reconstruction changed a face predicate or exceeded the bound");
+    CPT_CUDA(cudaEventRecord(ev1, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    b.ms_total = ms;
+    if (stats)
+        for (int f = 0; f < nfields; ++f) stats[f].ms_total = ms;
+    if (bst) *bst = b;
+    if (verdict != CPT_OK) return fail(verdict, "a reconstruction changed a face predicate or exceeded the bound");
     return CPT_OK;
 }
 
@@ -1415,6 +1848,12 @@ cpt_status cpt_compress_ex(const float* uv, const cpt_dims* dims, const cpt_para
 cpt_status cpt_compress(const float* uv, const cpt_dims* dims, const cpt_params* params, uint8_t** out,
                         size_t* out_bytes, cpt_stats* stats) {
     return cpt::compress_impl(uv, dims, params, out, out_bytes, stats, nullptr);
+}
+
+cpt_status cpt_compress_batch(const float* const* uv, const cpt_dims* dims, int32_t nfields, const cpt_params* params,
+                              size_t device_budget, uint8_t** out, size_t* out_bytes, cpt_stats* stats,
+                              cpt_batch_stats* batch_stats) {
+    return cpt::compress_batch_impl(uv, dims, nfields, params, device_budget, out, out_bytes, stats, batch_stats);
 }
 
 cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out, cpt_dims* dims_out,

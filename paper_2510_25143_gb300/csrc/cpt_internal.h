@@ -38,11 +38,9 @@ struct SliceArgs {
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
     unsigned* prep_done;    // [T][nur][nuc] 1 once the prep unit is done
-    unsigned* ticket;       // wavefront item counter
-    unsigned* qslot;        // [n_units] ready queue of prep units (unit id + 1, 0 = not yet filled)
-    unsigned* qhead;        // next queue position to take
+    unsigned* qslot;        // [queue_len] ready queue of prep units of the launch (global unit id + 1, 0 = not yet filled)
     unsigned* qtail;        // next queue position to fill
-    int* status;            // device status word (0 = ok)
+    int* status;            // device status word of the launch (0 = ok)
     unsigned long long* counters;  // [4]: substep vertices, substeps, SL blocks, spare
     int H, W, T;
     int eps_int;
@@ -53,13 +51,40 @@ struct SliceArgs {
     int nchunks;            // ceil(W / 32)
     int U;                  // side of a prep unit (8 for SL; 16, or 32 for MoP blocks of 32)
     int nur, nuc;           // prep units per slice: rows, columns
-    unsigned n_units;       // prep units in total ((T - 1) * nur * nuc), 0 = no prep stage
-    int prep_warps;         // warps (CTAs) working the prep queue
-    const int2* order;      // [T * nstrips] (t, s) of the wavefront items in ticket order
+    unsigned n_units;       // prep units of this field ((T - 1) * nur * nuc), 0 = no prep stage
+    unsigned unit_base;     // global id of this field's first prep unit in the launch's queue
+    unsigned queue_len;     // prep units of the whole launch (every field)
     const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
     long long timeout_ns;
+};
+
+// One launch of the encoder pipeline over one or more fields (a batch): the
+// wavefront items of every field in one ticket order and one ready queue of
+// prep units.  Each field's items keep their relative order, so every item
+// still waits only for items with smaller tickets.
+struct PipeArgs {
+    SliceArgs one;            // the field of a single-field launch (read from parameter space)
+    const SliceArgs* fields;  // [nfields] device copies
+    int nfields;
+    const int4* order;        // [total_items] (field, t, s, 0) in ticket order
+    unsigned total_items;
+    unsigned* ticket;         // wavefront item counter
+    unsigned* qhead;          // next queue position to take
+    unsigned queue_len;       // prep units of every field
+    int* status;              // device status word (0 = ok)
+    long long timeout_ns;
+    int prep_warps;           // warps working the prep queue
+};
+
+// Scheduling parameters of the encoder pipeline.  They order and place the
+// work only; the output does not depend on them.
+struct PipeTuning {
+    int prep_share;    // percent of the warps working prep units (0 = default for the predictor)
+    int sl_unit;       // side of a pure-SL prep unit: 8 or 16 (0 = default 8)
+    int slice_weight;  // slice weight of the ticket order without prep units (0 = default)
+    int slack;         // extra slice weight of the ticket order with prep units (0 = default)
 };
 
 // Canonical Huffman decoding tables of one stream (device pointers).
@@ -104,7 +129,7 @@ void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, i
 // k_encode.cu
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, cudaStream_t s);
-cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s);
+cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s);
 void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);
 constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols
 size_t encode_smem_bytes();

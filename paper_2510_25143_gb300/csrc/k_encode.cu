@@ -289,7 +289,20 @@ struct WarpSmem {
         PrepSmem prep;
     };
     int2 nbs[32][15];         // per-lane neighbour values for the face loops
+    SliceArgs args;           // the field of the current item (copied from the launch's field table)
 };
+
+// Copies the arguments of field f into the warp's shared slot.
+__device__ __forceinline__ const SliceArgs& load_field(const SliceArgs* __restrict__ fields, int f, WarpSmem& sm) {
+    static_assert(sizeof(SliceArgs) % 4 == 0, "field arguments copied as words");
+    constexpr int kWords = (int)(sizeof(SliceArgs) / 4);
+    const unsigned* src = reinterpret_cast<const unsigned*>(fields + f);
+    unsigned* dst = reinterpret_cast<unsigned*>(&sm.args);
+    __syncwarp();
+    for (int k = (int)(threadIdx.x & 31u); k < kWords; k += 32) dst[k] = __ldg(src + k);
+    __syncwarp();
+    return sm.args;
+}
 
 // ---------------------------------------------------------------------------
 // prep units: semi-Lagrangian predictions and MoP modes
@@ -670,7 +683,7 @@ __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) 
         for (int m = lane; m < n; m += 32) {
             const unsigned id =
                 ((unsigned)(t - 1) * (unsigned)a.nur + (unsigned)ur) * (unsigned)a.nuc + (unsigned)(lo + m);
-            if (base + m < a.n_units) st_relaxed(a.qslot + base + m, id + 1u);
+            if (base + m < a.queue_len) st_relaxed(a.qslot + base + m, a.unit_base + id + 1u);
             else atomicCAS(a.status, 0, kStatusCorrupt);  // cannot happen: every unit is queued once
         }
         base += (unsigned)n;
@@ -678,21 +691,36 @@ __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) 
 }
 
 // A prep warp: takes queue positions in order and works each unit once its
-// slot is filled.
-__device__ void prep_loop(const SliceArgs& a, WarpSmem& sm) {
+// slot is filled.  A slot holds the unit's global id + 1; its field is the
+// last one whose first unit id does not exceed it.  kBatch: the field's
+// arguments are copied into the warp's shared slot; otherwise the launch has
+// one field, read from parameter space.
+template <bool kBatch>
+__device__ void prep_loop(const PipeArgs& p, WarpSmem& sm) {
     for (;;) {
         unsigned pos = 0;
         int stop = 0;
         if ((threadIdx.x & 31u) == 0) {
-            pos = atomicAdd(a.qhead, 1u);
-            stop = *(volatile int*)a.status != 0;
+            pos = atomicAdd(p.qhead, 1u);
+            stop = *(volatile int*)p.status != 0;
         }
         pos = __shfl_sync(0xffffffffu, pos, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
-        if (pos >= a.n_units || stop) return;
-        const unsigned v = warp_wait_geq(a, a.qslot + pos, 1u);
+        if (pos >= p.queue_len || stop) return;
+        const unsigned v = warp_wait_geq(p.status, p.timeout_ns, p.one.qslot + pos, 1u);
         if (!v) return;
-        const unsigned id = v - 1u;
+        const unsigned gid = v - 1u;
+        int lo = 0;
+        if (kBatch) {
+            int hi = p.nfields - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&p.fields[mid].unit_base) <= gid) lo = mid;
+                else hi = mid - 1;
+            }
+        }
+        const SliceArgs& a = kBatch ? load_field(p.fields, lo, sm) : p.one;
+        const unsigned id = gid - a.unit_base;
         const int uc = (int)(id % (unsigned)a.nuc);
         const unsigned rest = id / (unsigned)a.nuc;
         const int ur = (int)(rest % (unsigned)a.nur);
@@ -754,6 +782,11 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const int nsub = (W + 15) / 16;
     const int2 z = make_int2(0, 0);
     int published = -1;  // last step whose ready units were queued
+    // outputs (a refers to the warp's shared slot: keep the pointers in registers)
+    int2* const out_qhat = a.qhat;
+    uint8_t* const out_qxi = a.qxi;
+    uint32_t* const out_sym = a.sym;
+    int* const out_xi = a.xi_out;
 
     // loads for a step, issued two steps ahead (two alternating register sets)
     struct Pf {
@@ -906,10 +939,10 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
                 sym = su | (sv << 16);
             }
             const size_t v = base + (size_t)i * W + j;
-            st_word(a.qhat + v, rec);
-            a.qxi[v] = (uint8_t)code;
-            a.sym[v] = sym;
-            if (a.xi_out) a.xi_out[v] = xi;
+            st_word(out_qhat + v, rec);
+            out_qxi[v] = (uint8_t)code;
+            out_sym[v] = sym;
+            if (out_xi) out_xi[v] = xi;
             res = rec;
         } else {
             res = z;
@@ -934,28 +967,37 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
 // CTA holds kWarpsPerCta of them so that they sit on different SM
 // sub-partitions (one-warp CTAs can share one).
 constexpr int kWarpsPerCta = 3;
-__global__ void __maxnreg__(168) encode_pipeline_kernel(SliceArgs a) {
+static_assert(sizeof(WarpSmem) * kWarpsPerCta <= 227 * 1024, "shared memory of one CTA");
+template <bool kBatch>
+__global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ PipeArgs p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = (int)(threadIdx.x >> 5);
     WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[wid];
-    if ((int)blockIdx.x * kWarpsPerCta + wid < a.prep_warps) {
-        prep_loop(a, sm);
+    if ((int)blockIdx.x * kWarpsPerCta + wid < p.prep_warps) {
+        prep_loop<kBatch>(p, sm);
         return;
     }
-    const int nstrips = (a.H + 31) / 32;
-    const unsigned total = (unsigned)nstrips * (unsigned)a.T;
+    int cur = -1;  // field whose arguments sit in the warp's slot
     for (;;) {
         unsigned item = 0;
         int stop = 0;
         if ((threadIdx.x & 31u) == 0) {
-            item = atomicAdd(a.ticket, 1u);
-            stop = *(volatile int*)a.status != 0;
+            item = atomicAdd(p.ticket, 1u);
+            stop = *(volatile int*)p.status != 0;
         }
         item = __shfl_sync(0xffffffffu, item, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
-        if (item >= total || stop) return;
-        const int2 ts = __ldg(a.order + item);
-        if (!wave_item(a, ts.x, ts.y, sm)) return;
+        if (item >= p.total_items || stop) return;
+        const int4 fts = __ldg(p.order + item);
+        if (kBatch) {
+            if (fts.x != cur) {
+                load_field(p.fields, fts.x, sm);
+                cur = fts.x;
+            }
+            if (!wave_item(sm.args, fts.y, fts.z, sm)) return;
+        } else {
+            if (!wave_item(p.one, fts.y, fts.z, sm)) return;
+        }
     }
 }
 
@@ -980,24 +1022,27 @@ void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T
     classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m);
 }
 
-cudaError_t launch_encode_pipeline(const SliceArgs& a, int nsm, cudaStream_t s) {
+cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s) {
     const size_t smem = sizeof(WarpSmem) * kWarpsPerCta;
-    cudaError_t e = cudaFuncSetAttribute(encode_pipeline_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool batch = p.nfields > 1;
+    auto kern = batch ? encode_pipeline_kernel<true> : encode_pipeline_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pipeline_kernel, 32 * kWarpsPerCta, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kWarpsPerCta, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     // with SL or MoP a share of the warps works the prep queue
-    SliceArgs b = a;
+    PipeArgs b = p;
     const int warps = nsm * per_sm * kWarpsPerCta;
     b.prep_warps = 0;
-    if (a.n_units > 0) {
-        b.prep_warps = (int)((long long)warps * (a.pred == 1 ? kPrepShareSL : kPrepShareMoP) / 100);
+    if (p.queue_len > 0) {
+        const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
+        b.prep_warps = (int)((long long)warps * share / 100);
         if (b.prep_warps < 1) b.prep_warps = 1;
         if (b.prep_warps > warps - 1) b.prep_warps = warps - 1;
     }
-    encode_pipeline_kernel<<<nsm * per_sm, 32 * kWarpsPerCta, smem, s>>>(b);
+    kern<<<nsm * per_sm, 32 * kWarpsPerCta, smem, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -182,6 +182,62 @@ def turbulence(H=1024, W=1024, T=200, seed=1004, k0=4.0, umax=1.5, substeps=2):
     return out
 
 
+def batch_specs(n=64, seed=2000):
+    """The uneven batch: n vortex-sum fields, each side 128 * 2^U[0,3] cells
+    rounded to a multiple of 16 (H and W drawn apart), T ~ U{10..200} steps,
+    random drift U[0.2, 1.5] cells per step, one vortex per 2048 cells (at
+    least 6), radii U[4, 10], random signs, N(0, 1e-3) noise; field f has
+    seed `seed + 1 + f`.  Returns a list of dicts (H, W, T, seed, n_vortex,
+    drift)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for f in range(n):
+        H = max(16, int(round(128 * 2.0 ** rng.uniform(0, 3) / 16)) * 16)
+        W = max(16, int(round(128 * 2.0 ** rng.uniform(0, 3) / 16)) * 16)
+        T = int(rng.integers(10, 201))
+        specs.append(dict(H=H, W=W, T=T, seed=seed + 1 + f, n_vortex=max(6, (H * W) // 2048),
+                          drift=float(rng.uniform(0.2, 1.5))))
+    return specs
+
+
+def vortex_sum_device(H, W, T, seed, n_vortex, drift, noise=1e-3, device="cuda"):
+    """The vortex-sum field of `vortex_sum` (same parameter draws, untruncated
+    Gaussians) generated on a torch device: each vortex's streamfunction
+    factors into a row and a column profile, so u and v of a slice are two
+    [H, K] x [K, W] products; float64 profiles and products, float32 output;
+    noise from a torch generator seeded with `seed`.  For inputs too large to
+    draw quickly on the host."""
+    import torch
+    rng = np.random.default_rng(seed)
+    mx, my = min(8.0, W / 4.0), min(8.0, H / 4.0)
+    cx = rng.uniform(mx, W - mx, n_vortex)
+    cy = rng.uniform(my, H - my, n_vortex)
+    R = rng.uniform(4, 10, n_vortex)
+    s = rng.choice([-1.0, 1.0], n_vortex)
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    i = torch.arange(H, dtype=f64, device=dev)[:, None]
+    j = torch.arange(W, dtype=f64, device=dev)[None, :]
+    Rt = torch.tensor(R, dtype=f64, device=dev)
+    st = torch.tensor(s, dtype=f64, device=dev)
+    yy = i - torch.tensor(cy, dtype=f64, device=dev)[None, :]       # [H, K]
+    ey = torch.exp(-yy * yy / (2.0 * Rt * Rt))
+    out = torch.empty((T, H, W, 2), dtype=torch.float32, device=dev)
+    for t in range(T):
+        xx = j.T - torch.tensor(cx + drift * t, dtype=f64, device=dev)[None, :]  # [W, K]
+        ex = torch.exp(-xx * xx / (2.0 * Rt * Rt))
+        # u = sum_k -s_k (y/R_k) e_k, v = sum_k s_k (x/R_k) e_k
+        u = (-(st / Rt) * yy * ey) @ ex.T
+        v = (st * ey) @ ((xx / Rt) * ex).T
+        u += noise * torch.randn((H, W), generator=g, dtype=f64, device=dev)
+        v += noise * torch.randn((H, W), generator=g, dtype=f64, device=dev)
+        out[t, :, :, 0] = u.to(torch.float32)
+        out[t, :, :, 1] = v.to(torch.float32)
+    return out
+
+
 def workload(name):
     """Returns (uv, relative error bound) for a named workload."""
     if name == "vortex64":
