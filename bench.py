@@ -220,7 +220,8 @@ def ours(args):
     nbytes = uv.nbytes
     d_uv = torch.from_numpy(uv).cuda()
     stream = torch.cuda.current_stream()
-    kw = dict(eb_mode="rel", pred=args.pred, verify=True)
+    # the pipeline's schedule is autotuned on the first (warm-up) call
+    kw = dict(eb_mode="rel", pred=args.pred, verify=True, tune=True)
 
     def step(src):
         # the stream stays in the library's host buffer (no Python copy)
@@ -427,12 +428,13 @@ def learned_vs_plain(args, street_blob):
                           "step 5), plain MoP, central 256 x 256 crops")
 
     def run(pred, m=None, reps=3):
-        blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False)
+        # the first call autotunes the pipeline's schedule (cached)
+        blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False)
+            blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps

@@ -873,7 +873,9 @@ static std::vector<PipeTuning> tuning_candidates(int pred) {
         for (int u : {8, 16})
             for (int share : {40, 55}) c.push_back({share, u, 0, 0});
     } else if (pred == CPT_PRED_LEARNED) {
-        for (int share : {50, 65, 80}) c.push_back({share, 0, 0, 0});
+        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 0});
+    } else if (pred == CPT_PRED_LEARNED_MOP) {
+        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 64});
     } else {
         for (int share : {35, 45, 55})
             for (int slack : {64, 128}) c.push_back({share, 0, 0, slack});

@@ -17,7 +17,8 @@ constexpr int kNetParams = kNetW1 + kNetC + kNetW2 + kNetC + kNetW3 + 2;  // 104
 constexpr int kNetReach = 3;  // rows/columns of slice t-1 beyond a vertex that its prediction reads
 
 // Device copy of the parameters as float, each layer's weights transposed so
-// that the output channels of one (input channel, ky, kx) are contiguous:
+// that the output channels of one (input channel, ky, kx) are contiguous (and
+// every weight block starts on a 16-byte boundary):
 // wt[((ci * 3 + ky) * 3 + kx) * COUT + co] = w[co][ci][ky][kx].
 struct NetDev {
     const float* w1t;  // [2][3][3][32]
@@ -31,33 +32,74 @@ constexpr int kNetDevFloats = kNetParams;  // same count, transposed weights the
 
 // One layer over an OH x OW output region whose (0, 0) sits at global
 // (gy0, gx0); in is the CIN x (OH+2) x (OW+2) window around it.  Outputs at
-// positions outside the H x W field are 0 (the next layer's padding).
+// positions outside the H x W field are 0 (the next layer's padding).  Each
+// lane computes two positions (p and p + 32) for a group of up to 16 output
+// channels at a time, so that every weight it loads (four channels at a
+// time, contiguous in the transposed layout) feeds two fused multiply-adds
+// per channel; each output's chain keeps the order bias, then (input
+// channel, ky, kx).
 template <int CIN, int COUT, bool RELU>
 __device__ __forceinline__ void net_layer(const float* __restrict__ in, const float* __restrict__ wt,
                                           const float* __restrict__ b, float* __restrict__ out, int OH, int OW,
                                           int gy0, int gx0, int H, int W) {
+    constexpr int G = COUT < 16 ? COUT : 16;  // output channels per pass
+    static_assert(COUT % G == 0 && G % 2 == 0, "output channels in groups of pairs or quads");
     const int lane = (int)(threadIdx.x & 31u);
-    const int IH = OH + 2, IW = OW + 2;
-    for (int p = lane; p < OH * OW; p += 32) {
-        const int oy = p / OW, ox = p - (p / OW) * OW;
-        const int gy = gy0 + oy, gx = gx0 + ox;
-        const bool inside = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        float acc[COUT];
+    const int IH = OH + 2, IW = OW + 2, NP = OH * OW;
+    for (int p0 = lane; p0 < NP; p0 += 64) {
+        const int p1 = p0 + 32;
+        const bool has1 = p1 < NP;
+        const int q1 = has1 ? p1 : p0;  // the second slot reads a valid position either way
+        const int oy0 = p0 / OW, ox0 = p0 - oy0 * OW;
+        const int oy1 = q1 / OW, ox1 = q1 - oy1 * OW;
+        const int g0y = gy0 + oy0, g0x = gx0 + ox0, g1y = gy0 + oy1, g1x = gx0 + ox1;
+        const bool in0 = g0y >= 0 && g0y < H && g0x >= 0 && g0x < W;
+        const bool in1 = g1y >= 0 && g1y < H && g1x >= 0 && g1x < W;
+#pragma unroll 1
+        for (int cg = 0; cg < COUT; cg += G) {
+            float acc0[G], acc1[G];
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = __ldg(b + co);
-        for (int ci = 0; ci < CIN; ++ci)
+            for (int c = 0; c < G; ++c) acc0[c] = acc1[c] = __ldg(b + cg + c);
+            for (int ci = 0; ci < CIN; ++ci)
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
+                for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const float v = in[(ci * IH + oy + ky) * IW + ox + kx];
-                    const float* wp = wt + ((ci * 3 + ky) * 3 + kx) * COUT;
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const float v0 = in[(ci * IH + oy0 + ky) * IW + ox0 + kx];
+                        const float v1 = in[(ci * IH + oy1 + ky) * IW + ox1 + kx];
+                        const float* wp = wt + ((ci * 3 + ky) * 3 + kx) * COUT + cg;
+                        if constexpr (G % 4 == 0) {
 #pragma unroll
-                    for (int co = 0; co < COUT; ++co) acc[co] = __fmaf_rn(__ldg(wp + co), v, acc[co]);
-                }
+                            for (int c = 0; c < G; c += 4) {
+                                const float4 w = __ldg(reinterpret_cast<const float4*>(wp + c));
+                                acc0[c] = __fmaf_rn(w.x, v0, acc0[c]);
+                                acc0[c + 1] = __fmaf_rn(w.y, v0, acc0[c + 1]);
+                                acc0[c + 2] = __fmaf_rn(w.z, v0, acc0[c + 2]);
+                                acc0[c + 3] = __fmaf_rn(w.w, v0, acc0[c + 3]);
+                                acc1[c] = __fmaf_rn(w.x, v1, acc1[c]);
+                                acc1[c + 1] = __fmaf_rn(w.y, v1, acc1[c + 1]);
+                                acc1[c + 2] = __fmaf_rn(w.z, v1, acc1[c + 2]);
+                                acc1[c + 3] = __fmaf_rn(w.w, v1, acc1[c + 3]);
+                            }
+                        } else {
 #pragma unroll
-        for (int co = 0; co < COUT; ++co)
-            out[(co * OH + oy) * OW + ox] = inside ? (RELU ? (acc[co] > 0.0f ? acc[co] : 0.0f) : acc[co]) : 0.0f;
+                            for (int c = 0; c < G; c += 2) {
+                                const float2 w = __ldg(reinterpret_cast<const float2*>(wp + c));
+                                acc0[c] = __fmaf_rn(w.x, v0, acc0[c]);
+                                acc0[c + 1] = __fmaf_rn(w.y, v0, acc0[c + 1]);
+                                acc1[c] = __fmaf_rn(w.x, v1, acc1[c]);
+                                acc1[c + 1] = __fmaf_rn(w.y, v1, acc1[c + 1]);
+                            }
+                        }
+                    }
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                out[((cg + c) * OH + oy0) * OW + ox0] = in0 ? (RELU ? (acc0[c] > 0.0f ? acc0[c] : 0.0f) : acc0[c]) : 0.0f;
+                if (has1)
+                    out[((cg + c) * OH + oy1) * OW + ox1] =
+                        in1 ? (RELU ? (acc1[c] > 0.0f ? acc1[c] : 0.0f) : acc1[c]) : 0.0f;
+            }
+        }
     }
 }
 
@@ -74,7 +116,7 @@ struct NetScratch {
 // reconstructed slice t-1 value (zero outside the field); out(li, lj, pred)
 // receives each prediction inside the field.  One warp.
 template <int U, class Prev, class Out>
-__device__ void net_tile(const NetDev& nd, NetScratch<U>& s, int r0, int c0, int H, int W, const Prev& prev,
+__device__ __forceinline__ void net_tile(const NetDev& nd, NetScratch<U>& s, int r0, int c0, int H, int W, const Prev& prev,
                          const Out& out) {
     const int lane = (int)(threadIdx.x & 31u);
     constexpr int XS = U + 6;

@@ -310,7 +310,7 @@ __device__ bool dwave_item(const DecodeArgs& a, int t, int s, DSmem& sm) {
     return true;
 }
 
-__global__ void __launch_bounds__(32) decode_pipeline_kernel(DecodeArgs a) {
+__global__ void __maxnreg__(192) decode_pipeline_kernel(DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DSmem& sm = *reinterpret_cast<DSmem*>(smem_raw);
     const int nstrips = (a.H + 31) / 32;
