@@ -375,6 +375,27 @@ def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
             "identical_to_single_calls": bool(identical)}
 
 
+def rate_summary(g):
+    """Entropy of the residual symbols, the share of zero codes and the
+    zero-code runs, from the library's rate diagnostics (code histograms and
+    run lengths of the Q_d stream)."""
+    import numpy as np
+    from paper_2510_25143_gb300 import cpt
+    h = g["qd_hist"].astype(np.float64)
+    n = h.sum()
+    p = h[h > 0] / n
+    zr = g["zero_runs"].astype(np.float64)
+    L = np.arange(1, cpt.RUN_MAX + 1)
+    nzero = float((L * zr[1:-1]).sum() + zr[0])
+    nruns = float(zr[1:].sum())
+    long_zeros = float((L[31:] * zr[32:-1]).sum() + zr[0])
+    return {"qd_symbols": int(n), "qd_h0_bits": round(float(-(p * np.log2(p)).sum()), 4) if n else 0.0,
+            "p_zero_code": round(float(h[32768] / n), 4) if n else 0.0, "zero_runs": int(nruns),
+            "mean_zero_run": round(nzero / nruns, 2) if nruns else 0.0,
+            "zeros_in_runs_ge_32": round(long_zeros / nzero, 4) if nzero else 0.0,
+            "lossless_vertex_share": round(float(g["qxi_hist"][0] / g["qxi_hist"].sum()), 4)}
+
+
 def learned_vs_plain(args, street_blob):
     """Compression ratio and MB/s of the plain and the learned predictors on
     2-D decaying turbulence (1024 x 1024 x 200, rel. bound 1e-3).  The net
@@ -428,8 +449,10 @@ def learned_vs_plain(args, street_blob):
                           "step 5), plain MoP, central 256 x 256 crops")
 
     def run(pred, m=None, reps=3):
-        # the first call autotunes the pipeline's schedule (cached)
-        blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True)
+        # the first call autotunes the pipeline's schedule (cached) and
+        # returns the rate diagnostics
+        blob, st, g = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True, rates=True)
+        rates = rate_summary(g)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -440,7 +463,7 @@ def learned_vs_plain(args, street_blob):
         ms = e0.elapsed_time(e1) / reps
         ok = st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
         return {"ratio": round(uv.nbytes / len(blob), 4), "MB/s": round(uv.nbytes / (ms / 1e3) / 1e6, 1),
-                "ms": round(ms, 2), "preserved": bool(ok), "psnr": round(st["psnr"], 3)}, blob
+                "ms": round(ms, 2), "preserved": bool(ok), "psnr": round(st["psnr"], 3), "rates": rates}, blob
 
     res = {}
     for pred in ("lorenzo", "sl", "mop"):

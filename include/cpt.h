@@ -141,7 +141,16 @@ typedef struct {
  *   sym   uint16 [T][H][W][2] residual symbols Q_d (0 = unpredictable;
  *                             unspecified where qxi == 0)
  *   mask  uint16 [T][H][W]    crossed-face bits of the 12 faces owned by each vertex
- *   modes uint8 [T][ceil(H/B)][ceil(W/B)]  1 = SL block                       */
+ *   modes uint8 [T][ceil(H/B)][ceil(W/B)]  1 = SL block
+ * Rate diagnostics (the code distributions behind the ratios, Sec. VII-E):
+ *   qxi_hist  uint32 [33]     counts of the bound codes Q_xi
+ *   qd_hist   uint32 [65536]  counts of the residual symbols Q_d (symbol = code
+ *                             + 32768; 0 = unpredictable)
+ *   zero_runs uint64 [4098]   maximal runs of the zero code (symbol 32768) in
+ *                             the Q_d stream (raster order, u then v of each
+ *                             vertex that has symbols): [L] runs of length L
+ *                             for 1 <= L <= 4096, [4097] longer runs, [0]
+ *                             their total length                            */
 typedef struct {
     int32_t* q;
     int32_t* qhat;
@@ -150,6 +159,9 @@ typedef struct {
     uint16_t* sym;
     uint16_t* mask;
     uint8_t* modes;
+    uint32_t* qxi_hist;
+    uint32_t* qd_hist;
+    uint64_t* zero_runs;
 } cpt_debug;
 
 /* Compresses uv (Alg. 3 with Alg. 1, 2, 4 and Sec. VI).

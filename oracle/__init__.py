@@ -289,6 +289,31 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.
     return d
 
 
+def qd_stream(res):
+    """The residual-symbol stream Q_d of an oracle compression (debug=True):
+    the u and v symbols of every vertex with a nonzero bound code, in raster
+    order (the order in which Alg. 3 emits them)."""
+    return res["qd"][res["qxi"] > 0].reshape(-1)
+
+
+def zero_runs(qd, zero_sym=QRADIUS, run_max=4096):
+    """Rate diagnostics: the maximal runs of the zero quantisation code
+    (symbol zero_sym) in a symbol stream.  bins[L] counts the runs of length
+    L for 1 <= L <= run_max, bins[run_max + 1] the longer runs and bins[0]
+    their total length (so sum(L * bins[L]) + bins[0] is the number of zero
+    codes)."""
+    z = np.concatenate([[False], np.asarray(qd) == zero_sym, [False]]).astype(np.int8)
+    d = np.diff(z)
+    lengths = np.flatnonzero(d == -1) - np.flatnonzero(d == 1)
+    bins = np.zeros(run_max + 2, np.uint64)
+    short = lengths[lengths <= run_max]
+    np.add.at(bins, short, 1)
+    long_ = lengths[lengths > run_max]
+    bins[run_max + 1] = len(long_)
+    bins[0] = int(long_.sum())
+    return bins
+
+
 def decompress(blob):
     """Returns (qhat int32 [T][H][W][2], uv float32 [T][H][W][2], k)."""
     buf = np.frombuffer(blob, np.uint8).copy()

@@ -53,7 +53,10 @@ class Stats(C.Structure):
 
 class Debug(C.Structure):
     _fields_ = [("q", C.c_void_p), ("qhat", C.c_void_p), ("xi", C.c_void_p), ("qxi", C.c_void_p),
-                ("sym", C.c_void_p), ("mask", C.c_void_p), ("modes", C.c_void_p)]
+                ("sym", C.c_void_p), ("mask", C.c_void_p), ("modes", C.c_void_p),
+                ("qxi_hist", C.c_void_p), ("qd_hist", C.c_void_p), ("zero_runs", C.c_void_p)]
+
+RUN_MAX = 4096  # zero_runs bins: [L] for 1 <= L <= RUN_MAX, [RUN_MAX + 1] longer runs, [0] their total length
 
 
 class Trajs(C.Structure):
@@ -171,13 +174,15 @@ def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedul
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
              dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None, tune=False,
-             schedule=None):
+             schedule=None, rates=False):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
     or device).  Returns (bytes, stats dict, debug dict or None); with
     copy=False the stream comes back as a Stream over the library's buffer.
     pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
     bfloat16 bits.  tune=True lets the library pick the encoder pipeline's
-    schedule; schedule=(prep_share, sl_unit, slice_weight, slack) fixes it."""
+    schedule; schedule=(prep_share, sl_unit, slice_weight, slack) fixes it.
+    rates=True (or debug=True) returns the rate diagnostics in the debug
+    dict: qxi_hist [33], qd_hist [65536] and zero_runs [RUN_MAX + 2]."""
     ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)
     if stream is None:
         stream = dev_stream
@@ -189,13 +194,17 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
     st = Stats()
     dbg_arrays = None
     dbgp = None
+    if debug or rates:
+        dbg_arrays = dict(qxi_hist=np.zeros(33, np.uint32), qd_hist=np.zeros(65536, np.uint32),
+                          zero_runs=np.zeros(RUN_MAX + 2, np.uint64))
     if debug:
         nby, nbx = -(-H // block), -(-W // block)
-        dbg_arrays = dict(q=np.zeros((T, H, W, 2), np.int32), qhat=np.zeros((T, H, W, 2), np.int32),
+        dbg_arrays.update(q=np.zeros((T, H, W, 2), np.int32), qhat=np.zeros((T, H, W, 2), np.int32),
                           xi=np.zeros((T, H, W), np.int32), qxi=np.zeros((T, H, W), np.uint8),
                           sym=np.zeros((T, H, W, 2), np.uint16), mask=np.zeros((T, H, W), np.uint16),
                           modes=np.zeros((T, nby, nbx), np.uint8))
-        dbgp = C.byref(Debug(*(dbg_arrays[f].ctypes.data for f, _ in Debug._fields_)))
+    if dbg_arrays is not None:
+        dbgp = C.byref(Debug(*(dbg_arrays[f].ctypes.data if f in dbg_arrays else None for f, _ in Debug._fields_)))
     L = lib()
     rc = L.cpt_compress_ex(ptr, C.byref(dims), C.byref(prm), C.byref(out), C.byref(n), C.byref(st), dbgp)
     blob = None

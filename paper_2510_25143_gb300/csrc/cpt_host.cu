@@ -685,6 +685,8 @@ struct FieldJob {
             CPT_CUDA(ar.alloc(&sp->d_tiles, sp->nt + 1));
             CPT_CUDA(ar.alloc(&sp->d_tmp, scan_temp_elems(sp->nt + 1)));
         }
+        if (dbg && dbg->qxi_hist) std::memcpy(dbg->qxi_hist, hist_h, sizeof(unsigned) * sx.alphabet);
+        if (dbg && dbg->qd_hist) std::memcpy(dbg->qd_hist, hist_h + sx.alphabet, sizeof(unsigned) * sd.alphabet);
         cpt_status rc = plan_codebook(sx, hist_h, tab_h, s);
         if (rc != CPT_OK) return rc;
         rc = plan_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet, s);
@@ -791,7 +793,16 @@ struct FieldJob {
             CPT_CUDA(cudaMemcpyAsync(vo_h, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
             tm.end();
         }
-        // ---- debug copies
+        // ---- debug copies and rate diagnostics
+        if (dbg && dbg->zero_runs) {
+            unsigned long long* d_bins;
+            uint8_t* d_ws;
+            CPT_CUDA(ar.alloc(&d_bins, kRunBins));
+            CPT_CUDA(ar.alloc(&d_ws, zero_runs_ws_bytes(n_qd)));
+            CPT_CUDA(launch_zero_runs(d_qd, n_qd, (unsigned)kRadius, d_bins, d_ws, sm_count(), s));
+            CPT_CUDA(cudaMemcpyAsync(dbg->zero_runs, d_bins, sizeof(unsigned long long) * kRunBins,
+                                     cudaMemcpyDeviceToHost, s));
+        }
         if (dbg) {
             if (dbg->q) CPT_CUDA(cudaMemcpyAsync(dbg->q, d_q, NV * 4, cudaMemcpyDeviceToHost, s));
             if (dbg->qhat) CPT_CUDA(cudaMemcpyAsync(dbg->qhat, d_qhat, NV * 4, cudaMemcpyDeviceToHost, s));

@@ -193,6 +193,14 @@ cudaError_t launch_adam(float* P, float* m, float* v, const float* g, float lr, 
 cudaError_t launch_net_prep_weights(const float* P, const NetTrainPtrs& w, cudaStream_t s);
 NetDev net_dev_view(const float* fwd);
 
+// k_rates.cu (rate diagnostics): bins [L] = maximal zero-code runs of length L
+// (1 <= L <= kRunMax), [kRunMax + 1] = longer runs, [0] = their total length
+constexpr int kRunMax = 4096;
+constexpr int kRunBins = kRunMax + 2;
+size_t zero_runs_ws_bytes(size_t n);
+cudaError_t launch_zero_runs(const uint16_t* qd, size_t n, unsigned zero_sym, unsigned long long* bins, void* ws,
+                             int nsm, cudaStream_t s);
+
 constexpr int kTileSyms = 4096;     // symbols per encode tile
 constexpr int kChunkSyms = 16384;   // symbols per decode chunk (stream sync points)
 
