@@ -92,8 +92,9 @@ typedef enum {
  *              (SL, MoP, learned), [1] side of a pure-SL prediction unit (8
  *              or 16), [2] slice weight of the wave order without prediction
  *              units (3DL), [3] extra slice weight of the wave order with
- *              them.  The schedule orders and places work only: the stream
- *              does not depend on it.                                         */
+ *              them, [4] worker warps per SM (0 = as many as shared memory
+ *              and registers allow), [5] reserved (0).  The schedule orders and places work only: the
+ *              stream does not depend on it.                                  */
 typedef struct {
     cpt_eb_mode mode;
     double eb;
@@ -104,7 +105,7 @@ typedef struct {
     void* cuda_stream;
     const uint16_t* model;  /* host bfloat16 [CPT_NET_PARAMS]: the learned predictor (CPT_PRED_LEARNED) */
     int32_t tune;
-    int32_t schedule[4];
+    int32_t schedule[6];
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's
@@ -183,7 +184,7 @@ typedef struct {
     double ms_tune;           /* schedule candidates timed by the autotuner (0 when cached or off) */
     uint32_t groups;          /* groups of fields (one pipeline launch each) */
     uint32_t launches;        /* kernels launched, autotuning runs excluded */
-    int32_t schedule[4];      /* the schedule used (cpt_params.schedule) */
+    int32_t schedule[6];      /* the schedule used (cpt_params.schedule) */
     uint64_t device_budget;   /* device bytes a group may hold */
     uint64_t in_bytes, out_bytes;
     double ms_phase[8];       /* host wall time of each phase up to its synchronisation: 0 input and

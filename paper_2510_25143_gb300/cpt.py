@@ -31,12 +31,12 @@ class Dims(C.Structure):
 class Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
                 ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 4)]
+                ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 6)]
 
 
 class BatchStats(C.Structure):
     _fields_ = [("ms_total", C.c_double), ("ms_pipeline", C.c_double), ("ms_tune", C.c_double),
-                ("groups", C.c_uint32), ("launches", C.c_uint32), ("schedule", C.c_int32 * 4),
+                ("groups", C.c_uint32), ("launches", C.c_uint32), ("schedule", C.c_int32 * 6),
                 ("device_budget", C.c_uint64), ("in_bytes", C.c_uint64), ("out_bytes", C.c_uint64),
                 ("ms_phase", C.c_double * 8)]
 
@@ -167,7 +167,7 @@ class Stream:
 
 
 def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule):
-    sch = (C.c_int32 * 4)(*(schedule or (0, 0, 0, 0)))
+    sch = (C.c_int32 * 6)(*(tuple(schedule or ()) + (0,) * 6)[:6])
     return Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
                   None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch)
 
@@ -180,7 +180,8 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
     copy=False the stream comes back as a Stream over the library's buffer.
     pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
     bfloat16 bits.  tune=True lets the library pick the encoder pipeline's
-    schedule; schedule=(prep_share, sl_unit, slice_weight, slack) fixes it.
+    schedule; schedule=(prep_share, sl_unit, slice_weight, slack, warps_per_sm)
+    fixes it (zeros: defaults).
     rates=True (or debug=True) returns the rate diagnostics in the debug
     dict: qxi_hist [33], qd_hist [65536] and zero_runs [RUN_MAX + 2]."""
     ptr, (T, H, W), keep, dev_stream = _ptr_and_shape(uv)

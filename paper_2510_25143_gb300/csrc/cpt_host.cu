@@ -412,7 +412,7 @@ struct FieldJob {
     uint8_t *d_qxi = nullptr, *d_modes = nullptr;
     uint32_t* d_sym = nullptr;
     int* d_xiout = nullptr;
-    int2 *d_psl = nullptr, *d_cls = nullptr;
+    int2 *d_psl = nullptr, *d_cls = nullptr, *d_qdiag = nullptr;
     unsigned *d_clsm = nullptr, *d_prep = nullptr;
     size_t nprep_alloc = 0;
     int nby = 0, nbx = 0, nstrips = 0;
@@ -441,7 +441,7 @@ struct FieldJob {
     // device bytes a field holds at its peak (for grouping a batch)
     static size_t device_bytes(const cpt_dims& d, bool host_input) {
         const size_t n = (size_t)d.H * d.W * d.T;
-        return n * (72 + (host_input ? 8 : 0)) + ((size_t)64 << 20);
+        return n * (84 + (host_input ? 8 : 0)) + ((size_t)64 << 20);
     }
 
     // ---- phase 0: argument checks, input on the device, range partials
@@ -525,8 +525,13 @@ struct FieldJob {
         CPT_CUDA(ar.alloc(&d_qxi, N));
         CPT_CUDA(ar.alloc(&d_modes, (size_t)T * nby * nbx));
         CPT_CUDA(ar.alloc(&d_sym, N));
-        CPT_CUDA(ar.alloc(&d_cls, N));
-        CPT_CUDA(ar.alloc(&d_clsm, N));
+        const size_t ND = diag_elems(H, W, T);  // strip-diagonal layout, zero padding
+        CPT_CUDA(ar.alloc(&d_cls, ND));
+        CPT_CUDA(ar.alloc(&d_clsm, ND));
+        CPT_CUDA(ar.alloc(&d_qdiag, ND));
+        CPT_CUDA(cudaMemsetAsync(d_cls, 0, ND * sizeof(int2), s));
+        CPT_CUDA(cudaMemsetAsync(d_clsm, 0, ND * sizeof(unsigned), s));
+        CPT_CUDA(cudaMemsetAsync(d_qdiag, 0, ND * sizeof(int2), s));
         CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
         if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
         CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));
@@ -537,6 +542,7 @@ struct FieldJob {
         A.mask = d_mask;
         A.cls = d_cls;
         A.cls_m = d_clsm;
+        A.qd = d_qdiag;
         A.psl = d_psl;
         A.modes = d_modes;
         A.qxi = d_qxi;
@@ -575,7 +581,7 @@ struct FieldJob {
         if (rc != CPT_OK) return rc;
 
         tm.begin(3);
-        launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, s);
+        launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, d_qdiag, s);
         st.launches[3]++;
         tm.end();
         return CPT_OK;
@@ -877,19 +883,23 @@ static std::map<std::tuple<int, int, int, int>, PipeTuning> g_tune_cache;
 
 // Candidate schedules of the encoder pipeline for a predictor.
 static std::vector<PipeTuning> tuning_candidates(int pred) {
+    // {prep share %, pure-SL unit side, 3DL slice weight, slack, warps per SM (0 = as many as fit)}
     std::vector<PipeTuning> c;
     if (pred == CPT_PRED_LORENZO) {
-        for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0});
+        for (int w : {3, 0})
+            for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, w});
     } else if (pred == CPT_PRED_SL) {
+        for (int share : {45, 50}) c.push_back({share, 8, 0, 0, 3});
         for (int u : {8, 16})
-            for (int share : {40, 55}) c.push_back({share, u, 0, 0});
+            for (int share : {25, 35, 50}) c.push_back({share, u, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED) {
-        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 0});
+        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED_MOP) {
-        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 64});
+        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 64, 0});
     } else {
-        for (int share : {35, 45, 55})
-            for (int slack : {64, 128}) c.push_back({share, 0, 0, slack});
+        for (int share : {35, 45}) c.push_back({share, 0, 0, 64, 3});
+        for (int share : {25, 35, 45, 55})
+            for (int slack : {64, 128}) c.push_back({share, 0, 0, slack, 0});
     }
     return c;
 }
@@ -1128,7 +1138,7 @@ static cpt_status check_device() {
 }
 
 static PipeTuning tuning_of(const cpt_params* prm) {
-    return PipeTuning{prm->schedule[0], prm->schedule[1], prm->schedule[2], prm->schedule[3]};
+    return PipeTuning{prm->schedule[0], prm->schedule[1], prm->schedule[2], prm->schedule[3], prm->schedule[4]};
 }
 
 static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
@@ -1234,6 +1244,7 @@ static cpt_status compress_batch_impl(const float* const* uv, const cpt_dims* di
         b.schedule[1] = pt.used.sl_unit;
         b.schedule[2] = pt.used.slice_weight;
         b.schedule[3] = pt.used.slack;
+        b.schedule[4] = pt.used.warps_per_sm;
         for (int f = first; f < last; ++f) {
             FieldJob& j = *jobs[f - first];
             cpt_stats st1;

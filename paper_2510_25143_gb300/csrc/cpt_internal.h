@@ -30,8 +30,12 @@ struct SliceArgs {
     const int2* q;          // original fixed point [T][H][W]
     int2* qhat;             // reconstruction words [T][H][W] (tagged, zeroed before the launch)
     const uint16_t* mask;   // crossed-face masks [T][H][W]
-    const int2* cls;        // [T][H][W] (bound over certain faces, faces needing the full Alg. 2)
-    const unsigned* cls_m;  // [T][H][W] faces needing only the M = 0 check
+    // Strip-diagonal layout [T][nstrips][W + 31][32] (zero padding): element
+    // (t, s, k, l) holds vertex (32 s + l, k - l), the vertex lane l of
+    // wave(t, s) handles at step k, so that a wave's loads are contiguous.
+    const int2* cls;        // (bound over certain faces, faces needing the full Alg. 2)
+    const unsigned* cls_m;  // faces needing only the M = 0 check
+    const int2* qd;         // the original fixed point q
     int2* psl;              // [T][H][W] semi-Lagrangian predictions (where needed)
     uint8_t* modes;         // [T][nby][nbx] block modes (1 = SL)
     uint8_t* qxi;           // [T][H][W] bound codes
@@ -85,6 +89,7 @@ struct PipeTuning {
     int sl_unit;       // side of a pure-SL prep unit: 8 or 16 (0 = default 8)
     int slice_weight;  // slice weight of the ticket order without prep units (0 = default)
     int slack;         // extra slice weight of the ticket order with prep units (0 = default)
+    int warps_per_sm;  // worker warps per SM (0 = as many as shared memory and registers allow)
 };
 
 // Canonical Huffman decoding tables of one stream (device pointers).
@@ -127,8 +132,10 @@ void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, i
                    VerifyOut* out, cudaStream_t s);
 
 // k_encode.cu
+// out, out_m and qd in the strip-diagonal layout (see SliceArgs), zeroed before
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
-                     unsigned* out_m, cudaStream_t s);
+                     unsigned* out_m, int2* qd, cudaStream_t s);
+inline size_t diag_elems(int H, int W, int T) { return (size_t)T * ((H + 31) / 32) * (W + 31) * 32; }
 cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s);
 void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);
 constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols

@@ -30,6 +30,9 @@
 // units wait for nothing.  Every warp is resident, so the pipeline cannot
 // deadlock; each wait is bounded in time and sets the status word when it
 // expires.
+#include <algorithm>
+#include <type_traits>
+
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
 #include "cpt_net.cuh"
@@ -81,7 +84,7 @@ __device__ __forceinline__ unsigned unc_pair(int f) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
                                                        int H, int W, int T, int eps_int, int2* __restrict__ out,
-                                                       unsigned* __restrict__ out_m) {
+                                                       unsigned* __restrict__ out_m, int2* __restrict__ qd) {
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
     const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
     const int t = blockIdx.z;
@@ -176,8 +179,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
             }
         }
     }
-    out[v] = make_int2(xi, (int)um_full);
-    out_m[v] = um_m;
+    // strip-diagonal position of (t, i, j): strip i / 32, step j + i % 32, lane i % 32
+    const size_t dv = (((size_t)t * ((H + 31) >> 5) + (i >> 5)) * (size_t)(W + 31) + (j + (i & 31))) * 32 + (i & 31);
+    out[dv] = make_int2(xi, (int)um_full);
+    out_m[dv] = um_m;
+    qd[dv] = __ldg(q + v);
 }
 
 __device__ __forceinline__ unsigned warp_wait_geq(const SliceArgs& a, const unsigned* flag, unsigned target) {
@@ -255,45 +261,64 @@ struct TaggedSlice {
 };
 
 // ---------------------------------------------------------------------------
-// shared memory of one worker warp (one warp per CTA)
+// shared memory of one worker warp, sized by the predictor: prediction units
+// of side at most UMAX (SL and MoP with blocks up to 16: 16; MoP blocks of
+// 32: 32; none for 3DL) and, with NET, the learned predictor's scratch.  The
+// smaller the slice, the more worker warps an SM holds.
 // ---------------------------------------------------------------------------
-// Read-only inputs of a wave, staged through a ring of four 16-column
-// sub-chunks: column j of the strip sits in ring column j & 63 (row pitch
-// kRing spreads the anti-diagonal reads over the banks).
-constexpr int kRing = 66;
-struct WaveSmem {
-    int2 cls[32][kRing];      // (bound over certain faces, faces needing the full Alg. 2)
-    unsigned cm[32][kRing];   // faces needing only the M = 0 check
-    int2 qv[33][kRing];       // q(t): rows 0..32 of the strip
-    int2 qn[33][kRing];       // q(t+1): rows 0..32 of the strip
-};
-constexpr int kStageR = 8;                 // largest SL reach served from the staged window
-constexpr int kPP = 34 + 2 * kStageR;      // pitch of the staged slice t-1 window
+constexpr int kStageR = 8;  // largest SL reach served from the staged window
+template <int UMAX, bool NET>
 struct PrepSmem {
-    int2 pp[kPP * kPP];                    // qhat(t-1): rows/cols -1-R..U+R around the unit
+    static constexpr int kPitch = UMAX + 2 + 2 * kStageR;  // pitch of the staged slice t-1 window
+    int2 pp[kPitch * kPitch];              // qhat(t-1): rows/cols -1-R..U+R around the unit
     union {
         struct {                           // SL and MoP
-            int2 qc[34][34];               // q(t): rows/cols -1..U around the unit
-            int2 psl[32][32];              // SL predictions of the unit
-            unsigned smp[2][2048];         // sampled symbols per mode (0xFFFFFFFF = none)
+            int2 qc[UMAX + 2][UMAX + 2];   // q(t): rows/cols -1..U around the unit
+            int2 psl[UMAX][UMAX];          // SL predictions of the unit
+            unsigned smp[2][64 * UMAX];    // sampled symbols per mode (0xFFFFFFFF = none)
             unsigned hist[256];
-            unsigned short list[1024];     // sites (row * 32 + column) left for SL
+            unsigned short list[UMAX * UMAX];  // sites (row * 32 + column) left for SL
             unsigned char modes[64];       // decisions of the unit's blocks
         };
-        NetScratch<8> net;                 // learned predictor (8 x 8 units)
+        typename std::conditional<NET, NetScratch<8>, char>::type net;  // learned predictor (8 x 8 tiles)
     };
 };
-struct WarpSmem {
+// A wave's read-only inputs, staged from the strip-diagonal arrays in chunks
+// of kChunk steps (each step's 32 lanes contiguous), two chunks ahead, into
+// three slots (slot = chunk mod 3): during chunk g the steps read chunks g
+// and g + 1 (neighbours at steps k + 1, k + 2), while g + 2 is in flight.
+constexpr int kChunk = 8;
+struct alignas(16) WaveRing {
+    int2 cl[3][kChunk][32];      // classification
+    unsigned cm[3][kChunk][32];  // faces needing only the M = 0 check
+    int2 q[3][kChunk][32];       // q(t)
+    int2 qn[3][kChunk][32];      // q(t+1)
+    int2 qb[3][kChunk];          // q(t) of the next strip's first row at column (consumer step - 31)
+    int2 nb[3][kChunk];          // q(t+1) of the same
+};
+template <int UMAX, bool NET>
+struct alignas(16) WarpSmem {
+    static constexpr int kUmax = UMAX;
+    static constexpr bool kNet = NET;
     union {
-        WaveSmem wave;
-        PrepSmem prep;
+        PrepSmem<UMAX, NET> prep;  // prediction units
+        WaveRing ring;             // waves
     };
-    int2 nbs[32][15];         // per-lane neighbour values for the face loops
-    SliceArgs args;           // the field of the current item (copied from the launch's field table)
+    int2 nbs[32][15];  // per-lane neighbour values for the face loops
+    SliceArgs args;    // the field of the current item (copied from the launch's field table)
+};
+template <>
+struct alignas(16) WarpSmem<0, false> {  // 3DL: no prediction units
+    static constexpr int kUmax = 0;
+    static constexpr bool kNet = false;
+    WaveRing ring;
+    int2 nbs[32][15];
+    SliceArgs args;
 };
 
 // Copies the arguments of field f into the warp's shared slot.
-__device__ __forceinline__ const SliceArgs& load_field(const SliceArgs* __restrict__ fields, int f, WarpSmem& sm) {
+template <class Sm>
+__device__ __forceinline__ const SliceArgs& load_field(const SliceArgs* __restrict__ fields, int f, Sm& sm) {
     static_assert(sizeof(SliceArgs) % 4 == 0, "field arguments copied as words");
     constexpr int kWords = (int)(sizeof(SliceArgs) / 4);
     const unsigned* src = reinterpret_cast<const unsigned*>(fields + f);
@@ -381,7 +406,9 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
 // runs as an anti-diagonal sweep inside each block with the original slice t
 // outside the block (context-preserving candidate buffer).  The SL symbols of
 // the sampled sites come from psl.
-__device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PrepSmem& ps, int Rw) {
+template <class PS>
+__device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int Rw) {
+    constexpr int kPP = PS::kPitch;
     const int lane = (int)(threadIdx.x & 31u), B = a.B, n = a.n, H = a.H, W = a.W;
     const int nbu = a.U / B, nbt = nbu * nbu;  // blocks per unit side, per unit
     const int bpp = 32 / B;                    // blocks per pass
@@ -476,11 +503,13 @@ __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
 // the ready queue once slice t-1 is reconstructed around it).  Leaves in psl
 // the SL prediction of every vertex that uses SL, and with MoP the marker
 // kNoSL on the vertices of blocks that keep 3DL.
-__device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& sm) {
+template <class Sm>
+__device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
     const unsigned FULL = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, U = a.U;
     const int uh = min(U, H - r0), uw = min(U, W - c0);
-    PrepSmem& ps = sm.prep;
+    auto& ps = sm.prep;
+    constexpr int kPP = std::remove_reference<decltype(ps)>::type::kPitch;
     const size_t sl = (size_t)H * W;
     const int2 z = make_int2(0, 0);
     const bool mop = a.pred == 2;
@@ -540,45 +569,47 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, WarpSmem& s
     const SmemSlice Ps{ps.pp, r0 - 1 - Rw, c0 - 1 - Rw, kPP};
     const TaggedSlice Pg{P, W, a.status, a.timeout_ns};
     int2* Psl = a.psl + (size_t)t * sl;
-    if (a.pred == 3 || a.pred == 4) {
-        // learned predictor: the unit's 8 x 8 tiles from the staged window (reach 3)
-        auto prev = [&](int i, int j) -> int2 { return Ps.at(i, j); };
-        for (int tr = 0; tr < uh; tr += 8)
-            for (int tc = 0; tc < uw; tc += 8) {
-                auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
-                net_tile<8>(a.net, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
-            }
-        if (a.pred == 4) {
-            // the learned mixture: block modes as MoP's with the net in SL's
-            // place; the scratch of the net gives way to q(t) and the samples
-            __threadfence();  // the predictions are read back through L2 by other lanes
-            __syncwarp();
-            const int2* Qt = a.q + (size_t)t * sl;
-            for (int rr = 0; rr < U + 2; ++rr) {
-                const int i = r0 - 1 + rr;
-                for (int cc = lane; cc < U + 2; cc += 32) {
-                    const int j = c0 - 1 + cc;
-                    const bool ok = i >= 0 && i < H && j >= 0 && j < W;
-                    cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
+    if constexpr (Sm::kNet) {
+        if (a.pred == 3 || a.pred == 4) {
+            // learned predictor: the unit's 8 x 8 tiles from the staged window (reach 3)
+            auto prev = [&](int i, int j) -> int2 { return Ps.at(i, j); };
+            for (int tr = 0; tr < uh; tr += 8)
+                for (int tc = 0; tc < uw; tc += 8) {
+                    auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
+                    net_tile<8>(a.net, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
+                }
+            if (a.pred == 4) {
+                // the learned mixture: block modes as MoP's with the net in SL's
+                // place; the scratch of the net gives way to q(t) and the samples
+                __threadfence();  // the predictions are read back through L2 by other lanes
+                __syncwarp();
+                const int2* Qt = a.q + (size_t)t * sl;
+                for (int rr = 0; rr < U + 2; ++rr) {
+                    const int i = r0 - 1 + rr;
+                    for (int cc = lane; cc < U + 2; cc += 32) {
+                        const int j = c0 - 1 + cc;
+                        const bool ok = i >= 0 && i < H && j >= 0 && j < W;
+                        cp_async8(&ps.qc[rr][cc], Qt + (ok ? (size_t)i * W + j : 0), ok);
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                for (int k = lane; k < uh * uw; k += 32) {
+                    const int li = k / uw, lj = k % uw;
+                    if (((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0)
+                        ps.psl[li][lj] = __ldcg(Psl + (size_t)(r0 + li) * W + c0 + lj);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                mop_unit(a, t, r0, c0, ps, Rw);
+                const int nbu = U / a.B;
+                for (int k = lane; k < uh * uw; k += 32) {
+                    const int li = k / uw, lj = k % uw;
+                    if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
                 }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            for (int k = lane; k < uh * uw; k += 32) {
-                const int li = k / uw, lj = k % uw;
-                if (((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0)
-                    ps.psl[li][lj] = __ldcg(Psl + (size_t)(r0 + li) * W + c0 + lj);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            mop_unit(a, t, r0, c0, ps, Rw);
-            const int nbu = U / a.B;
-            for (int k = lane; k < uh * uw; k += 32) {
-                const int li = k / uw, lj = k % uw;
-                if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
-            }
+            warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
+            return;
         }
-        warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
-        return;
     }
     unsigned sub = 0, steps = 0;
     // semi-Lagrangian predictions, lanes over a compact list of sites: every
@@ -695,8 +726,8 @@ __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) 
 // last one whose first unit id does not exceed it.  kBatch: the field's
 // arguments are copied into the warp's shared slot; otherwise the launch has
 // one field, read from parameter space.
-template <bool kBatch>
-__device__ void prep_loop(const PipeArgs& p, WarpSmem& sm) {
+template <bool kBatch, class Sm>
+__device__ void prep_loop(const PipeArgs& p, Sm& sm) {
     for (;;) {
         unsigned pos = 0;
         int stop = 0;
@@ -732,23 +763,33 @@ __device__ void prep_loop(const PipeArgs& p, WarpSmem& sm) {
 // ---------------------------------------------------------------------------
 // wave(t, s)
 // ---------------------------------------------------------------------------
-// Stages sub-chunk g (columns 16g..16g+15) of the strip's read-only inputs
-// into its ring slot: asynchronous copies, zero outside the slice.
-__device__ __forceinline__ void stage_sub(const SliceArgs& a, WaveSmem& w, const int2* cls, const unsigned* cm,
-                                          const int2* Qt, const int2* Qn, bool qn_ok, int i0, int g) {
-    const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W;
-    const int j = 16 * g + (lane & 15), rc = j & 63;
-    const bool cok = j < W;
-    for (int rr = lane >> 4; rr < 33; rr += 2) {
-        const int i = i0 + rr;
-        const bool ok = cok && i < H;
-        const size_t off = ok ? (size_t)i * W + j : 0;
-        if (rr < 32) {
-            cp_async8(&w.cls[rr][rc], cls + off, ok);
-            cp_async4(&w.cm[rr][rc], cm + off, ok);
-        }
-        cp_async8(&w.qv[rr][rc], Qt + off, ok);
-        cp_async8(&w.qn[rr][rc], Qn + off, ok && qn_ok);
+// Stages chunk g of a wave's inputs (steps kChunk g ..) into slot g % 3:
+// contiguous 16-byte copies of the strip-diagonal arrays, zero past the
+// strip's last step.  Dn, Db and Dnb must be readable pointers even when their
+// data does not exist (has_next, below_ok false): the copies then read nothing.
+__device__ __forceinline__ void stage_chunk(WaveRing& r, int g, const int2* cls, const unsigned* cm, const int2* Dq,
+                                            const int2* Dn, const int2* Db, const int2* Dnb, bool has_next,
+                                            bool below_ok, int W) {
+    const int lane = (int)(threadIdx.x & 31u), slot = g % 3, k0 = g * kChunk, nsteps = W + 31;
+    for (int p = lane; p < kChunk * 16; p += 32) {  // 8-byte elements: 16 pieces per step
+        const int st = p >> 4, e = (p & 15) * 2, k = k0 + st;
+        const bool ok = k < nsteps;
+        const size_t off = ok ? (size_t)k * 32 + e : 0;
+        cp_async16(&r.cl[slot][st][e], cls + off, ok);
+        cp_async16(&r.q[slot][st][e], Dq + off, ok);
+        cp_async16(&r.qn[slot][st][e], Dn + off, ok && has_next);
+    }
+    for (int p = lane; p < kChunk * 8; p += 32) {  // 4-byte elements: 8 pieces per step
+        const int st = p >> 3, e = (p & 7) * 4, k = k0 + st;
+        const bool ok = k < nsteps;
+        cp_async16(&r.cm[slot][st][e], cm + (ok ? (size_t)k * 32 + e : 0), ok);
+    }
+    if (lane < kChunk) {  // lane 31 of consumer step k reads column k - 31 of the next strip's first row
+        const int jj = k0 + lane - 31;
+        const bool ok = below_ok && jj >= 0 && jj < W;
+        const size_t off = ok ? (size_t)jj * 32 : 0;
+        cp_async8(&r.qb[slot][lane], Db + off, ok);
+        cp_async8(&r.nb[slot][lane], Dnb + off, ok && has_next);
     }
 }
 
@@ -759,19 +800,28 @@ __device__ __forceinline__ void stage_sub(const SliceArgs& a, WaveSmem& w, const
 //          l-1 by shuffle (lane 0 reads row i-1 itself)
 //   4..6   (i-1, j-1), (i-1, j), (i, j-1) of slice t: registers and shuffles,
 //          lane 0 reads row i-1 (written by wave(t, s-1)) one step ahead
-//   7..13  original values from the staged ring.
+//   7..12  original values of slices t and t+1 from the staged ring: (i, j+1)
+//          is this lane's element of step k + 1, (i+1, j) and (i+1, j+1) lane
+//          l+1's of steps k + 1 and k + 2 (lane 31: the next strip's first row).
+// The classification of (i, j) comes from the ring as well.
 // All 24 uncertain faces are evaluated here with the actual reconstructions.
-__device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
+template <class Sm>
+__device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     const unsigned FULL = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, T = a.T;
     const int i0 = 32 * s, i = i0 + lane;
-    const bool rowok = i < H;
+    const bool rowok = i < H, below_ok = i0 + 32 < H;
     const size_t sl = (size_t)H * W, base = (size_t)t * sl;
-    WaveSmem& w = sm.wave;
-    const int2* Qt = a.q + base;
-    const int2* Qn = a.q + (t + 1 < T ? base + sl : base);
-    const int2* cls = a.cls + base;
-    const unsigned* cm = a.cls_m + base;
+    // strip-diagonal inputs of this wave and of the same strip of slice t+1
+    const int nstrips = (H + 31) >> 5;
+    const size_t dstride = (size_t)(W + 31) * 32;  // one strip
+    const size_t db = ((size_t)t * nstrips + s) * dstride;
+    const int2* cls = a.cls + db;
+    const unsigned* cm = a.cls_m + db;
+    const int2* Dq = a.qd + db;
+    const int2* Dn = t + 1 < T ? a.qd + db + (size_t)nstrips * dstride : Dq;  // slice t+1
+    const int2* Db = below_ok ? Dq + dstride : Dq;   // the next strip's first row (lane 0)
+    const int2* Dnb = below_ok ? Dn + dstride : Dq;
     const int2* Pm = a.qhat + (t >= 1 ? base - sl : base);  // slice t-1
     int2* Pc = a.qhat + base;                                // slice t
     const int2* Psl = a.psl + base;
@@ -779,7 +829,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
     const bool need_sl = has_prev && a.n_units > 0;  // SL predictions present for this slice
     const bool mop = a.pred == 2 || a.pred == 4;  // psl carries the 3DL marker
     const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
-    const int nsub = (W + 15) / 16;
+    const bool has_next = t + 1 < T;
     const int2 z = make_int2(0, 0);
     int published = -1;  // last step whose ready units were queued
     // outputs (a refers to the warp's shared slot: keep the pointers in registers)
@@ -819,12 +869,12 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         return true;
     };
 
-    stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, 1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    WaveRing& ring = sm.ring;
     __syncwarp();
+    stage_chunk(ring, 0, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    stage_chunk(ring, 1, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     Pf fa, fb;
     fa.pn = fb.pn = z;
     if (!await_sl(0)) return false;
@@ -850,12 +900,11 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(f.wa) : z;
         const int2 uk = (lane == 0 && has_above && col) ? word_value(f.wu) : z;
         const int2 pslk = f.pn;
-        // sub-chunk g + 1 of the inputs at step 16g - 1, when sub-chunk g is
-        // first read; its ring slot was last read at step 16g - 2
-        if (((k + 1) & 15) == 0) {
-            const int g = (k + 1) >> 4;
+        // chunk g of the staged inputs starts: stage g + 2 over the slot of
+        // g - 1 (no longer read), then wait for g and g + 1
+        if (k % kChunk == 0) {
             __syncwarp();
-            if (g + 1 < nsub) stage_sub(a, w, cls, cm, Qt, Qn, t + 1 < T, i0, g + 1);
+            stage_chunk(ring, k / kChunk + 2, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
@@ -885,16 +934,20 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         const int2 upleft = up;
         up = lane == 0 ? uk : fromprev;
         if (rowok && col) {
-            const int rc = j & 63, rn = (j + 1) & 63;
-            const int2 cl = w.cls[lane][rc];
-            const unsigned mf = (unsigned)cl.y, mm = w.cm[lane][rc];
+            const int s0 = (k / kChunk) % 3, r0 = k % kChunk;
+            const int s1 = ((k + 1) / kChunk) % 3, r1 = (k + 1) % kChunk;
+            const int2 cl = ring.cl[s0][r0][lane];
+            const unsigned mf = (unsigned)cl.y, mm = ring.cm[s0][r0][lane];
             int xi = cl.x;
-            const int2 qv = w.qv[lane][rc];
+            const int2 qv = ring.q[s0][r0][lane];
             if (xi > 0 && (mf | mm)) {
-                const int2 n7 = w.qv[lane][rn], n8 = w.qv[lane + 1][rc], n9 = w.qv[lane + 1][rn];
-                const int2 n10 = w.qn[lane][rc], n11 = w.qn[lane][rn];
-                const int2 n12 = w.qn[lane + 1][rc];  // (the uncertain faces do not use neighbour 13)
-                const int2 n4 = upleft, n5 = up, n6 = left;
+                const int s2 = ((k + 2) / kChunk) % 3, r2 = (k + 2) % kChunk;
+                const int2 n7 = ring.q[s1][r1][lane];
+                const int2 n8 = lane < 31 ? ring.q[s1][r1][lane + 1] : ring.qb[s0][r0];
+                const int2 n9 = lane < 31 ? ring.q[s2][r2][lane + 1] : ring.qb[s1][r1];
+                const int2 n10 = ring.qn[s0][r0][lane], n11 = ring.qn[s1][r1][lane];
+                const int2 n12 = lane < 31 ? ring.qn[s1][r1][lane + 1] : ring.nb[s0][r0];
+                const int2 n4 = upleft, n5 = up, n6 = left;  // (the uncertain faces do not use neighbour 13)
                 // M = 0 checks of the 24 faces, branch free: with d = n - q(v),
                 // M = d_a.x d_b.y - d_a.y d_b.x
 #define CPT_D(k) const int dx##k = n##k.x - qv.x, dy##k = n##k.y - qv.y;
@@ -960,21 +1013,22 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, WarpSmem& sm) {
         if (!step(k, fa)) return false;
         if (k + 1 < W + 31 && !step(k + 1, fb)) return false;
     }
+    cp_async_wait_all();  // no copy into the ring outlives the item
     return true;
 }
 
-// Every warp is an independent worker with its own shared-memory slice; a
-// CTA holds kWarpsPerCta of them so that they sit on different SM
-// sub-partitions (one-warp CTAs can share one).
-constexpr int kWarpsPerCta = 3;
-static_assert(sizeof(WarpSmem) * kWarpsPerCta <= 227 * 1024, "shared memory of one CTA");
-template <bool kBatch>
+// Every warp is an independent worker with its own shared-memory slice; one
+// CTA per SM holds as many of them as the slices and the registers allow, so
+// that they spread over the SM's sub-partitions.
+constexpr int kMaxWarpsPerCta = 12;  // 168 registers x 32 lanes x 12 <= 64 K registers
+template <bool kBatch, int UMAX, bool NET>
 __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ PipeArgs p) {
+    using Sm = WarpSmem<UMAX, NET>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int wid = (int)(threadIdx.x >> 5);
-    WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[wid];
-    if ((int)blockIdx.x * kWarpsPerCta + wid < p.prep_warps) {
-        prep_loop<kBatch>(p, sm);
+    const int wid = (int)(threadIdx.x >> 5), wpc = (int)(blockDim.x >> 5);
+    Sm& sm = reinterpret_cast<Sm*>(smem_raw)[wid];
+    if ((int)blockIdx.x * wpc + wid < p.prep_warps) {
+        if constexpr (UMAX > 0) prep_loop<kBatch>(p, sm);
         return;
     }
     int cur = -1;  // field whose arguments sit in the warp's slot
@@ -1017,24 +1071,35 @@ void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s) {
 }
 
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
-                     unsigned* out_m, cudaStream_t s) {
+                     unsigned* out_m, int2* qd, cudaStream_t s) {
     dim3 grid((W + 31) / 32, (H + 7) / 8, T);
-    classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m);
+    classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m, qd);
 }
 
-cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s) {
-    const size_t smem = sizeof(WarpSmem) * kWarpsPerCta;
+template <int UMAX, bool NET>
+static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s) {
+    const size_t slice = sizeof(WarpSmem<UMAX, NET>);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int wpc = (int)std::min<size_t>((size_t)kMaxWarpsPerCta, (size_t)optin / slice);
+    if (tune.warps_per_sm > 0) wpc = std::min(wpc, tune.warps_per_sm);
+    if (wpc < 1) return cudaErrorInvalidConfiguration;
     const bool batch = p.nfields > 1;
-    auto kern = batch ? encode_pipeline_kernel<true> : encode_pipeline_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = batch ? encode_pipeline_kernel<true, UMAX, NET> : encode_pipeline_kernel<false, UMAX, NET>;
+    const size_t smem = slice * wpc;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kWarpsPerCta, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, smem);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;  // every worker must be resident
+    if (tune.warps_per_sm > 0) per_sm = 1;                 // exactly that many warps per SM
     // with SL or MoP a share of the warps works the prep queue
     PipeArgs b = p;
-    const int warps = nsm * per_sm * kWarpsPerCta;
+    const int warps = nsm * per_sm * wpc;
     b.prep_warps = 0;
     if (p.queue_len > 0) {
         const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
@@ -1042,8 +1107,19 @@ cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const P
         if (b.prep_warps < 1) b.prep_warps = 1;
         if (b.prep_warps > warps - 1) b.prep_warps = warps - 1;
     }
-    kern<<<nsm * per_sm, 32 * kWarpsPerCta, smem, s>>>(b);
+    kern<<<nsm * per_sm, 32 * wpc, smem, s>>>(b);
     return cudaGetLastError();
+}
+
+// The shared-memory layout of the predictor: 3DL none; SL and MoP with blocks
+// up to 16: units of 16; the learned predictors: units of 16 and the net's
+// scratch; MoP blocks of 32: units of 32 (with room for the net).
+cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s) {
+    const int B = p.one.B;
+    if (pred == 0) return launch_pipeline_t<0, false>(p, pred, nsm, tune, s);
+    if (pred == 1 || (pred == 2 && B <= 16)) return launch_pipeline_t<16, false>(p, pred, nsm, tune, s);
+    if ((pred == 3 || pred == 4) && B <= 16) return launch_pipeline_t<16, true>(p, pred, nsm, tune, s);
+    return launch_pipeline_t<32, true>(p, pred, nsm, tune, s);
 }
 
 }  // namespace cpt

@@ -60,9 +60,9 @@ def test_batch_host_inputs_and_round_trip():
 
 
 @pytest.mark.parametrize("pred,schedules", [
-    ("lorenzo", [(0, 0, 1, 0), (0, 0, 8, 0)]),
-    ("sl", [(30, 16, 0, 0), (70, 8, 0, 0)]),
-    ("mop", [(30, 0, 0, 32), (60, 0, 0, 128)]),
+    ("lorenzo", [(0, 0, 1, 0, 4), (0, 0, 8, 0, 0)]),
+    ("sl", [(30, 16, 0, 0, 2), (70, 8, 0, 0, 0)]),
+    ("mop", [(30, 0, 0, 32, 3), (60, 0, 0, 128, 0)]),
 ])
 def test_schedule_does_not_change_bytes(pred, schedules):
     fields = _fields(seed=80, drift=1.3)
@@ -70,7 +70,7 @@ def test_schedule_does_not_change_bytes(pred, schedules):
     for sch in schedules:
         blobs, _, b = cpt.compress_batch([_dev(uv) for uv in fields], 4e-3, pred=pred, schedule=sch)
         assert blobs == ref, sch
-        assert b["schedule"] == sch
+        assert b["schedule"][:len(sch)] == tuple(sch)
     one, _, _ = cpt.compress(_dev(fields[1]), 4e-3, pred=pred, schedule=schedules[-1])
     assert one == ref[1]
 
@@ -80,7 +80,7 @@ def test_autotune_keeps_bytes():
     ref, _, _ = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop")
     tuned, _, b = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop", tune=True)
     assert tuned == ref
-    assert b["schedule"][0] in (35, 45, 55) and b["schedule"][3] in (64, 128)
+    assert b["schedule"][0] in (25, 35, 45, 55) and b["schedule"][3] in (64, 128)
     again, _, b2 = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop", tune=True)
     assert again == ref and b2["ms_tune"] == 0.0 and b2["schedule"] == b["schedule"]  # cached
 
