@@ -13,6 +13,7 @@
 #include <mutex>
 #include <unordered_map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cpt.h"
@@ -290,21 +291,21 @@ struct StreamPlan {
     size_t header_bytes() const { return 8 + 4 + 4 + 4 * entries.size() + 8 * chunk_off.size() + 8; }
 };
 
-// Code lengths and the device table of a stream from its histogram;
-// table_h: pinned [alphabet] scratch for the host -> device copy.
-static cpt_status plan_codebook(StreamPlan& sp, const unsigned* hist, uint32_t* table_h, cudaStream_t s) {
+// Code lengths, the code book entries and the code table (into table_h:
+// pinned [alphabet], later copied to the device) of a stream from its
+// histogram.  Host only, touches nothing but sp and table_h (thread safe).
+static bool build_codebook(StreamPlan& sp, const unsigned* hist, uint32_t* table_h) {
     std::vector<uint64_t> freq(sp.alphabet);
     for (uint32_t k = 0; k < sp.alphabet; ++k) freq[k] = hist[k];
     std::vector<uint8_t> len;
-    if (!huffman_lengths(freq, kMaxCodeLen, len)) return fail(CPT_ERR_ARG, "alphabet too large for code length limit");
+    if (!huffman_lengths(freq, kMaxCodeLen, len)) return false;
     std::vector<uint32_t> table;
     canonical_table(len, table);
     sp.entries.clear();
     for (uint32_t sy = 0; sy < sp.alphabet; ++sy)
         if (len[sy]) sp.entries.push_back((sy << 8) | len[sy]);
     std::memcpy(table_h, table.data(), sizeof(uint32_t) * sp.alphabet);
-    CPT_CUDA(cudaMemcpyAsync(sp.d_table, table_h, sizeof(uint32_t) * sp.alphabet, cudaMemcpyHostToDevice, s));
-    return CPT_OK;
+    return true;
 }
 
 static void write_stream_header(Writer& w, const StreamPlan& sp) {
@@ -682,6 +683,12 @@ struct FieldJob {
     }
 
     // ---- phase 4 (after the histograms arrived): code books, tile bit counts
+    // host part (thread safe across fields): both code books from the histograms
+    bool host_codebooks() {
+        const unsigned* hist_h = reinterpret_cast<const unsigned*>(stage_h);
+        uint32_t* tab_h = reinterpret_cast<uint32_t*>(stage_h + st_hist + st_modes);
+        return build_codebook(sx, hist_h, tab_h) && build_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet);
+    }
     cpt_status codebooks() {
         unsigned* hist_h = reinterpret_cast<unsigned*>(stage_h);
         uint32_t* tab_h = reinterpret_cast<uint32_t*>(stage_h + st_hist + st_modes);
@@ -693,10 +700,9 @@ struct FieldJob {
         }
         if (dbg && dbg->qxi_hist) std::memcpy(dbg->qxi_hist, hist_h, sizeof(unsigned) * sx.alphabet);
         if (dbg && dbg->qd_hist) std::memcpy(dbg->qd_hist, hist_h + sx.alphabet, sizeof(unsigned) * sd.alphabet);
-        cpt_status rc = plan_codebook(sx, hist_h, tab_h, s);
-        if (rc != CPT_OK) return rc;
-        rc = plan_codebook(sd, hist_h + sx.alphabet, tab_h + sx.alphabet, s);
-        if (rc != CPT_OK) return rc;
+        CPT_CUDA(cudaMemcpyAsync(sx.d_table, tab_h, sizeof(uint32_t) * sx.alphabet, cudaMemcpyHostToDevice, s));
+        CPT_CUDA(cudaMemcpyAsync(sd.d_table, tab_h + sx.alphabet, sizeof(uint32_t) * sd.alphabet,
+                                 cudaMemcpyHostToDevice, s));
         for (StreamPlan* sp : {&sx, &sd})
             CPT_CUDA(cudaMemsetAsync(sp->d_tiles, 0, sizeof(unsigned long long) * (sp->nt + 1), s));
         launch_tile_bits_u8(d_qxi, sx.nsym, sx.d_table, sx.d_tiles, s);
@@ -1112,6 +1118,22 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
     }
     CPT_CUDA(cudaStreamSynchronize(s));
     mark(4);
+    {   // the fields' code books on host threads (package-merge is the host's share of the method)
+        const int nth = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+        std::vector<char> ok((size_t)n, 1);
+        auto work = [&](int w) {
+            for (int f = w; f < n; f += nth) ok[f] = jobs[f]->host_codebooks() ? 1 : 0;
+        };
+        if (nth == 1) {
+            work(0);
+        } else {
+            std::vector<std::thread> pool;
+            for (int w = 0; w < nth; ++w) pool.emplace_back(work, w);
+            for (auto& th : pool) th.join();
+        }
+        for (int f = 0; f < n; ++f)
+            if (!ok[f]) return fail(CPT_ERR_ARG, "alphabet too large for code length limit");
+    }
     for (int f = 0; f < n; ++f) {
         cpt_status rc = jobs[f]->codebooks();
         if (rc != CPT_OK) return rc;
