@@ -263,6 +263,25 @@ def ours(args):
     torch.cuda.synchronize()
     ms_e2e, e2e_value = combine_ranks(ee0.elapsed_time(ee1) / args.steps, world, nbytes, device="cuda")
 
+    # decompression through the C ABI into a device buffer (the stream is
+    # parsed on the host, decoded and reconstructed on the GPU)
+    host_blob = bytes(blob)
+    d_out = torch.empty_like(d_uv)
+    cpt.decompress(host_blob, out=d_out)
+    torch.cuda.synchronize()
+    de0, de1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    de0.record(stream)
+    for _ in range(args.steps):
+        cpt.decompress(host_blob, out=d_out)
+    de1.record(stream)
+    torch.cuda.synchronize()
+    ms_dec = de0.elapsed_time(de1) / args.steps
+    exact = bool(torch.equal(d_out, torch.from_numpy(cpt.decompress(host_blob)[0]).cuda()))
+    decompress = {"value": round(nbytes / 1e6 / (ms_dec / 1e3), 2), "unit": "MB/s (output bytes)",
+                  "ms": round(ms_dec, 3), "input": "stream in host memory, output on the device",
+                  "deterministic": exact}
+    del d_out
+
     # per-stage device time from the library's CUDA events on its stream
     stage_ms = {k: statistics.mean(s["ms_stage"][k] for s in stats) for k in stats[0]["ms_stage"]}
     stage_launch = {k: stats[0]["launches"][k] for k in stats[0]["launches"]}
@@ -295,6 +314,7 @@ def ours(args):
                      "launch_ms": round(per_launch_ms, 5)},
         "e2e": {"value": round(e2e_value, 2), "unit": "MB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": len(e2e_blob)},
+        "decompress": decompress,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

@@ -303,6 +303,17 @@ cpt_status cpt_train_predictor(const int32_t* prev, const int32_t* next, int32_t
                                int32_t steps, float lr, uint32_t seed, const uint16_t* init, uint16_t* model_out,
                                float* loss_out, void* cuda_stream);
 
+/* Failure injection for tests of the bounded waits (the paper has no
+ * counterpart).  The next compression on the calling thread runs its encoder
+ * pipeline without the wave item of this ticket (an index into the pipeline's
+ * ticket order) and with every wait limited to timeout_ns: the items that
+ * depend on the skipped one wait until the limit, set the kernel's status
+ * word and stop, and the call returns CPT_ERR_TIMEOUT with the device left
+ * usable.  No fault, trap or unbounded wait is involved.  ticket < 0 clears a
+ * pending injection.
+ * Errors: CPT_ERR_ARG (ticket >= 2^32 - 1, limit outside [1 ms, 10 s]). */
+cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns);
+
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);

@@ -96,6 +96,8 @@ def lib():
             L.cpt_error_string.argtypes = [C.c_int]
             L.cpt_last_error.restype = C.c_char_p
             L.cpt_version.restype = C.c_uint32
+            L.cpt_inject_wave_stall.restype = C.c_int
+            L.cpt_inject_wave_stall.argtypes = [C.c_int64, C.c_int64]
             L.cpt_fixed_point_noalloc.restype = C.c_int
             L.cpt_fixed_point_noalloc.argtypes = [C.c_void_p, P(Dims), C.c_void_p, C.c_void_p, C.c_void_p]
             vp, i32 = C.c_void_p, C.c_int32
@@ -311,6 +313,13 @@ def extract_trajectories(uv, scale_log2=None, stream=None):
     L.cpt_free_trajs(out)
     del keep
     return ([faces[offs[a]:offs[a + 1]] for a in range(n)], [xyt[offs[a]:offs[a + 1]] for a in range(n)], bad)
+
+
+def inject_wave_stall(ticket, timeout_s=0.2):
+    """Failure injection for tests: the next compression on this thread skips
+    the wave item with this ticket and limits every wait to timeout_s, so it
+    returns ERR_TIMEOUT.  ticket=None clears a pending injection."""
+    _check(lib().cpt_inject_wave_stall(-1 if ticket is None else int(ticket), int(timeout_s * 1e9)))
 
 
 def fixed_point_noalloc(uv, q, k, stream=None):

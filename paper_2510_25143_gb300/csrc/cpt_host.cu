@@ -882,6 +882,14 @@ struct FieldJob {
     }
 };
 
+// Failure injection for tests (per host thread): the next compression's
+// encoder pipeline skips the wave with this ticket and waits at most this long.
+struct WaveStall {
+    long long ticket = -1;
+    long long timeout_ns = 0;
+};
+static thread_local WaveStall t_stall;
+
 // Process-wide cache of autotuned schedules, keyed by the predictor, the
 // block side and the size class of the launch.
 static std::mutex g_tune_mu;
@@ -991,6 +999,11 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
     CPT_CUDA(cudaEventCreate(&e1));
     struct EvG { cudaEvent_t a, b; ~EvG() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{e0, e1};
 
+    // a pending failure injection applies to this call's launches
+    const WaveStall stall = t_stall;
+    t_stall = WaveStall{};
+    const long long timeout_ns = stall.ticket >= 0 ? stall.timeout_ns : 2000000000ll;
+
     // Sets up and launches the pipeline over every field under a schedule;
     // *ms: the launch's device time (CUDA events around the kernel).
     auto launch = [&](const PipeTuning& tu, double* ms) -> cpt_status {
@@ -1026,7 +1039,7 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
             A.qtail = d_queue + 1;
             A.status = d_status;
             A.queue_len = qlen;
-            A.timeout_ns = 2000000000ll;
+            A.timeout_ns = timeout_ns;
             fields[f] = A;
             cpt_status rc = jobs[f]->reset_pipeline();
             if (rc != CPT_OK) return rc;
@@ -1045,7 +1058,8 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
         P.qhead = d_queue;
         P.queue_len = qlen;
         P.status = d_status;
-        P.timeout_ns = 2000000000ll;
+        P.timeout_ns = timeout_ns;
+        P.skip_item = stall.ticket >= 0 ? (unsigned)stall.ticket : ~0u;
         CPT_CUDA(cudaEventRecord(e0, s));
         CPT_CUDA(launch_encode_pipeline(P, (int)prm->pred, nsm, tu, s));
         CPT_CUDA(cudaEventRecord(e1, s));
@@ -1910,6 +1924,14 @@ cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
                                     void* cuda_stream) {
     return cpt::trajectories_impl(uv, dims, scale_log2, out, cuda_stream);
+}
+
+cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns) {
+    if (ticket >= 0 && (ticket > 0xFFFFFFFEll || timeout_ns < 1000000 || timeout_ns > 10000000000ll))
+        return cpt::fail(CPT_ERR_ARG, "ticket must fit 32 bits and the limit lie in [1 ms, 10 s]");
+    cpt::t_stall.ticket = ticket < 0 ? -1 : ticket;
+    cpt::t_stall.timeout_ns = timeout_ns;
+    return CPT_OK;
 }
 
 cpt_status cpt_net_predict(const uint16_t* model, const int32_t* prev, int32_t H, int32_t W, int32_t* pred_out,

@@ -80,6 +80,7 @@ struct PipeArgs {
     int* status;              // device status word (0 = ok)
     long long timeout_ns;
     int prep_warps;           // warps working the prep queue
+    unsigned skip_item;       // failure injection: the ticket of a wave that never runs (~0u = none)
 };
 
 // Scheduling parameters of the encoder pipeline.  They order and place the

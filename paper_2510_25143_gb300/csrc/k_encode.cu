@@ -877,9 +877,16 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     asm volatile("cp.async.commit_group;" ::: "memory");
     Pf fa, fb;
     fa.pn = fb.pn = z;
-    if (!await_sl(0)) return false;
+    // on a failed wait the item gives up after its copies into the ring land
+    if (!await_sl(0)) {
+        cp_async_wait_all();
+        return false;
+    }
     issue(0, fa);
-    if (!await_sl(1)) return false;
+    if (!await_sl(1)) {
+        cp_async_wait_all();
+        return false;
+    }
     issue(1, fb);
 
     int2 h0 = z, h1 = z, h2 = z;  // slice t-1 at (i, j), (i, j-1), (i, j-2)
@@ -1010,8 +1017,10 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
         return true;
     };
     for (int k = 0; k < W + 31; k += 2) {
-        if (!step(k, fa)) return false;
-        if (k + 1 < W + 31 && !step(k + 1, fb)) return false;
+        if (!step(k, fa) || (k + 1 < W + 31 && !step(k + 1, fb))) {
+            cp_async_wait_all();
+            return false;
+        }
     }
     cp_async_wait_all();  // no copy into the ring outlives the item
     return true;
@@ -1042,6 +1051,7 @@ __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ 
         item = __shfl_sync(0xffffffffu, item, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
         if (item >= p.total_items || stop) return;
+        if (item == p.skip_item) continue;  // failure injection: this wave never runs
         const int4 fts = __ldg(p.order + item);
         if (kBatch) {
             if (fts.x != cur) {
