@@ -372,6 +372,47 @@ static int sm_count() {
 }
 
 // ---------------------------------------------------------------------------
+// the encoder pipeline's ticket order (also used to decode)
+// ---------------------------------------------------------------------------
+// Ticket keys of a field's wavefront items (t, s): Ks s + Kt t, then t.  A
+// wave depends on the waves above it and, through its prep units, on slice
+// t-1 down to (31 + R) / 32 strips below it, so Kt exceeds Ks times that with
+// prep units (Kt > Ks * strips below); without them any Kt > 0 keeps
+// dependencies at smaller tickets, and a small Kt lets consecutive slices run
+// a few steps apart.
+static void pipeline_keys(int T, int nstrips, int R, unsigned n_units, const PipeTuning& tune,
+                          std::vector<long long>& key) {
+    const long long below = (31 + R) / 32;
+    const long long slack = tune.slack > 0 ? tune.slack : kOrderSlackPrep;
+    const long long kl = tune.slice_weight > 0 ? tune.slice_weight : kOrderSliceLorenzo;
+    const long long Kt = n_units > 0 ? kOrderStrip * below + slack : kl;
+    key.resize((size_t)T * nstrips);
+    for (int t = 0; t < T; ++t)
+        for (int sx = 0; sx < nstrips; ++sx) key[(size_t)t * nstrips + sx] = kOrderStrip * sx + Kt * t;
+}
+
+// One field's items (field index f) in ticket order.
+static void pipeline_order(int T, int nstrips, int R, unsigned n_units, const PipeTuning& tune, int f,
+                           std::vector<int4>& order) {
+    std::vector<long long> key;
+    pipeline_keys(T, nstrips, R, n_units, tune, key);
+    std::vector<int2> ts;
+    ts.reserve(key.size());
+    for (int t = 0; t < T; ++t)
+        for (int sx = 0; sx < nstrips; ++sx) ts.push_back(make_int2(t, sx));
+    std::stable_sort(ts.begin(), ts.end(), [&](int2 p, int2 q) {
+        const long long kp = key[(size_t)p.x * nstrips + p.y], kq = key[(size_t)q.x * nstrips + q.y];
+        return kp != kq ? kp < kq : p.x < q.x;
+    });
+    order.resize(ts.size());
+    for (size_t x = 0; x < ts.size(); ++x) order[x] = make_int4(f, ts[x].x, ts[x].y, 0);
+}
+
+// The decoder's schedule (its prediction units carry no MoP decisions and its
+// waves no face work).
+static const PipeTuning kDecodeSchedule = {0, 0, 0, 0, 0};
+
+// ---------------------------------------------------------------------------
 // compression (Alg. 3)
 // ---------------------------------------------------------------------------
 // One field of a compression call.  Its work is split at the host
@@ -607,20 +648,8 @@ struct FieldJob {
         return CPT_OK;
     }
 
-    // Ticket keys of this field's wavefront items (t, s): Ks s + Kt t, then t.
-    // A wave depends on the waves above it and, through its prep units, on
-    // slice t-1 down to (31 + R) / 32 strips below it, so Kt exceeds Ks times
-    // that with prep units (Kt > Ks * strips below); without them any Kt > 0
-    // keeps dependencies at smaller tickets, and a small Kt lets consecutive
-    // slices run a few steps apart.
     void ticket_keys(const PipeTuning& tune, std::vector<long long>& key) const {
-        const long long below = (31 + a.R) / 32;
-        const long long slack = tune.slack > 0 ? tune.slack : kOrderSlackPrep;
-        const long long kl = tune.slice_weight > 0 ? tune.slice_weight : kOrderSliceLorenzo;
-        const long long Kt = a.n_units > 0 ? kOrderStrip * below + slack : kl;
-        key.resize((size_t)T * nstrips);
-        for (int t = 0; t < T; ++t)
-            for (int sx = 0; sx < nstrips; ++sx) key[(size_t)t * nstrips + sx] = kOrderStrip * sx + Kt * t;
+        pipeline_keys(T, nstrips, a.R, a.n_units, tune, key);
     }
 
     // Resets what the encoder pipeline reads and writes back (before every launch).
@@ -1440,9 +1469,9 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     const uint32_t ver = r.u32();
     const int H = (int)r.u32(), W = (int)r.u32(), T = (int)r.u32();
     const int k = (int)r.u32();
-    r.u32();  // eps'
+    const uint32_t eps_hdr = r.u32();  // eps'
     const int pred = (int)r.u32(), B = (int)r.u32();
-    r.u32();  // sampling stride
+    const int stride_hdr = (int)r.u32();  // MoP sampling stride
     const uint32_t radius = r.u32();
     r.u32();
     const double dx = r.f64(), dy = r.f64(), dt = r.f64();
@@ -1450,6 +1479,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     const uint64_t n_ld = r.u64(), mode_bytes = r.u64();
     if (r.bad || ver != kFormat || H < 2 || W < 2 || T < 1 || pred < 0 || pred > 4 || B < 1 ||
         radius != (uint32_t)kRadius || k < -200 || k > 200 || !(dx > 0) || !(dy > 0) || !(dt > 0) ||
+        eps_hdr > 8388608u || stride_hdr < 1 || ((pred == 2 || pred == 4) && (B < 4 || 32 % B != 0)) ||
         (long long)H * W > (1ll << 31) / 4)
         return fail(CPT_ERR_CORRUPT, "bad stream header");
     if (dims_out) {
@@ -1492,7 +1522,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     uint16_t* d_qd;
     uint32_t* d_sym;
     int32_t* d_ld;
-    int2 *d_raw, *d_qhat, *d_psl;
+    int2 *d_dcs, *d_draw, *d_qhat, *d_psl;
     unsigned long long *d_cnt, *d_tmp;
     CPT_CUDA(ar.alloc(&d_status, 1));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
@@ -1500,7 +1530,11 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(ar.alloc(&d_qd, hd.nsym));
     CPT_CUDA(ar.alloc(&d_sym, N));
     CPT_CUDA(ar.alloc(&d_ld, n_ld));
-    CPT_CUDA(ar.alloc(&d_raw, N));
+    const size_t ND = diag_elems(H, W, T);  // strip-diagonal inputs of the pipeline, zero padding
+    CPT_CUDA(ar.alloc(&d_dcs, ND));
+    CPT_CUDA(ar.alloc(&d_draw, ND));
+    CPT_CUDA(cudaMemsetAsync(d_dcs, 0, ND * sizeof(int2), s));
+    CPT_CUDA(cudaMemsetAsync(d_draw, 0, ND * sizeof(int2), s));
     CPT_CUDA(ar.alloc(&d_qhat, N));
     CPT_CUDA(ar.alloc(&d_psl, pred != 0 ? N : 1));
     CPT_CUDA(ar.alloc(&d_cnt, N));
@@ -1526,51 +1560,100 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
     launch_exclusive_scan_u64(d_cnt, N, d_tmp, s);
     CPT_CUDA(cudaMemcpyAsync(&last_off, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    launch_gather_raw(d_qxi, d_sym, d_cnt, d_ld, n_ld, N, d_raw, d_status, s);
+    launch_gather_raw(d_qxi, d_sym, d_cnt, d_ld, n_ld, H, W, T, d_dcs, d_draw, d_status, s);
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaStreamSynchronize(s));
     if (status != 0 || ((last_off + last_cnt) & 0xFFFFFFFFull) != n_ld)
         return fail(CPT_ERR_CORRUPT, "verbatim values do not match the codes");
-    // reconstruction pipeline
-    const int nstrips = (H + 31) / 32, nchunks = (W + 31) / 32;
-    unsigned *d_prog, *d_prep, *d_ticket;
-    CPT_CUDA(ar.alloc(&d_prog, (size_t)T * nstrips));
-    CPT_CUDA(ar.alloc(&d_prep, (size_t)T * nstrips * nchunks));
-    CPT_CUDA(ar.alloc(&d_ticket, 1));
-    CPT_CUDA(cudaMemsetAsync(d_prog, 0, sizeof(unsigned) * T * nstrips, s));
-    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * (size_t)T * nstrips * nchunks, s));
-    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
-    DecodeArgs a;
-    a.qxi = d_qxi;
-    a.sym = d_sym;
-    a.raw = d_raw;
-    a.psl = d_psl;
-    a.mode_bits = d_modes;
-    a.qhat = d_qhat;
-    a.progress = d_prog;
-    a.prep_done = d_prep;
-    a.ticket = d_ticket;
-    a.status = d_status;
-    a.H = H; a.W = W; a.T = T;
-    a.pred = pred; a.B = B; a.nby = nby; a.nbx = nbx; a.nchunks = nchunks;
-    a.prep_groups = 0;
-    a.cfl_x = std::ldexp(dt / dx, -k);
-    a.cfl_y = std::ldexp(dt / dy, -k);
-    // every reconstruction of a valid stream is below 2^24 in magnitude
-    a.R = (int)std::min(std::ceil(16777216.0 * std::max(a.cfl_x, a.cfl_y)) + 2.0, (double)std::max(H, W) + 2.0);
-    if (pred == 3 || pred == 4) {
-        a.R = kNetReach;
+    // reconstruction: the encoder's pipeline in decoding mode.  Waves rebuild
+    // qhat from the symbols in raster order, prediction units give the SL or
+    // learned predictions, MoP block modes come from the stream.
+    const int eps_int = (int)eps_hdr;
+    const bool has_net = pred == 3 || pred == 4, has_modes = pred == 2 || pred == 4;
+    const bool want_sl = pred != 0 && T > 1 && eps_int > 0;
+    const int nstrips = (H + 31) / 32;
+    SliceArgs A;
+    std::memset(&A, 0, sizeof(A));
+    unsigned long long* d_ctr;
+    CPT_CUDA(ar.alloc(&d_ctr, 8));
+    CPT_CUDA(cudaMemsetAsync(d_ctr, 0, 8 * sizeof(unsigned long long), s));
+    CPT_CUDA(cudaMemsetAsync(d_qhat, 0, N * sizeof(int2), s));  // no reconstruction word present
+    A.qhat = d_qhat;
+    A.cls = d_dcs;
+    A.cls_m = reinterpret_cast<const unsigned*>(d_dcs);  // (not read when decoding)
+    A.qd = d_draw;
+    A.psl = d_psl;
+    A.mode_bits = d_modes;
+    A.decode = 1;
+    A.counters = d_ctr + 1;
+    A.H = H; A.W = W; A.T = T;
+    A.eps_int = eps_int;
+    A.pred = pred;
+    A.B = B; A.n = stride_hdr; A.nby = nby; A.nbx = nbx;
+    A.nchunks = (W + 31) / 32;
+    A.cfl_x = std::ldexp(dt / dx, -k);
+    A.cfl_y = std::ldexp(dt / dy, -k);
+    // Reach of the back-trace: |qhat| <= 2^23 + E for every stream (the
+    // fixed-point scale keeps |q| <= 2^23, the quantiser moves a value by at
+    // most E), so no displacement exceeds that times CFL.
+    if (want_sl && has_net) {
+        A.R = kNetReach;
+    } else if (want_sl) {
+        const double qmax = 8388608.0 + (eps_int > 0 ? std::ldexp(1.0, 31 - __builtin_clz((unsigned)eps_int)) : 0.0);
+        A.R = (int)std::min(std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0, (double)std::max(H, W) + 2.0);
+    }
+    if (has_net) {
         float* d_net;
         CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
-        cpt_status rc = upload_net(model.data(), d_net, &a.net, s);
-        if (rc != CPT_OK) return rc;
+        cpt_status rc2 = upload_net(model.data(), d_net, &A.net, s);
+        if (rc2 != CPT_OK) return rc2;
     }
-    a.timeout_ns = 2000000000ll;
-    CPT_CUDA(launch_decode_pipeline(a, nsm, s));
+    A.U = has_modes ? (B == 32 ? 32 : 16) : 8;
+    A.nur = (H + A.U - 1) / A.U;
+    A.nuc = (W + A.U - 1) / A.U;
+    const unsigned long long nu = want_sl ? (unsigned long long)(T - 1) * A.nur * A.nuc : 0ull;
+    if (nu >= 0x7FFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many prediction units");
+    A.n_units = (unsigned)nu;
+    unsigned *d_prep, *d_queue, *d_ticket;
+    const size_t nprep = (size_t)T * A.nur * A.nuc;
+    CPT_CUDA(ar.alloc(&d_prep, nprep));
+    CPT_CUDA(ar.alloc(&d_queue, (size_t)A.n_units + 2));
+    CPT_CUDA(ar.alloc(&d_ticket, 1));
+    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
+    CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * ((size_t)A.n_units + 2), s));
+    CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
+    CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    A.prep_done = d_prep;
+    A.qslot = d_queue + 2;
+    A.qtail = d_queue + 1;
+    A.status = d_status;
+    A.queue_len = A.n_units;
+    A.timeout_ns = 2000000000ll;
+    const PipeTuning tune = kDecodeSchedule;
+    std::vector<int4> order;
+    pipeline_order(T, nstrips, A.R, A.n_units, tune, 0, order);
+    int4* d_order;
+    CPT_CUDA(ar.alloc(&d_order, order.size()));
+    CPT_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int4) * order.size(), cudaMemcpyHostToDevice, s));
+    PipeArgs P;
+    std::memset(&P, 0, sizeof(P));
+    P.one = A;
+    P.fields = nullptr;  // one field: read from parameter space
+    P.nfields = 1;
+    P.order = d_order;
+    P.total_items = (unsigned)order.size();
+    P.ticket = d_ticket;
+    P.qhead = d_queue;
+    P.queue_len = A.n_units;
+    P.status = d_status;
+    P.timeout_ns = A.timeout_ns;
+    P.skip_item = ~0u;
+    CPT_CUDA(launch_encode_pipeline(P, pred, nsm, tune, s));
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CPT_CUDA(cudaStreamSynchronize(s));
+    CPT_CUDA(cudaStreamSynchronize(s));  // (the host order table outlives its copy)
     if (status == (int)CPT_ERR_TIMEOUT) return fail(CPT_ERR_TIMEOUT, "decoder wavefront wait timed out");
     if (status != 0) return fail(CPT_ERR_CORRUPT, "corrupt stream");
+    launch_untag(d_qhat, N, s);
     if (qhat_out) CPT_CUDA(cudaMemcpyAsync(qhat_out, d_qhat, N * 8, cudaMemcpyDeviceToHost, s));
     if (uv_out) {
         const bool dev = is_device_pointer(uv_out) && !(reinterpret_cast<uintptr_t>(uv_out) & 7u);

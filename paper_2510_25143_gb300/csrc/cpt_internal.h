@@ -62,6 +62,11 @@ struct SliceArgs {
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
     long long timeout_ns;
+    // Decoding: the same pipeline rebuilds qhat from a stream.  cls then holds
+    // (bound code, residual symbols u | v << 16) and qd the verbatim values,
+    // both strip-diagonal; MoP block modes come from the stream's bits.
+    int decode;
+    const uint8_t* mode_bits;  // [ceil(T * nby * nbx / 8)] 1 = SL block (decode)
 };
 
 // One launch of the encoder pipeline over one or more fields (a batch): the
@@ -106,24 +111,6 @@ struct HuffDecode {
     const uint32_t* sorted;         // symbols ordered by (length, symbol)
 };
 
-// Arguments of the decoder pipeline.
-struct DecodeArgs {
-    const uint8_t* qxi;       // [T][H][W] bound codes
-    const uint32_t* sym;      // [T][H][W] residual symbols, u | v << 16
-    const int2* raw;          // [T][H][W] verbatim values (lossless or unpredictable components)
-    int2* psl;                // [T][H][W] semi-Lagrangian predictions
-    const uint8_t* mode_bits; // MoP block modes as stored in the stream
-    int2* qhat;               // [T][H][W] reconstruction
-    unsigned* progress;
-    unsigned* prep_done;
-    unsigned* ticket;
-    int* status;
-    int H, W, T, pred, B, nby, nbx, nchunks, prep_groups, R;
-    double cfl_x, cfl_y;
-    long long timeout_ns;
-    NetDev net;               // learned predictor parameters (pred 3)
-};
-
 // k_field.cu
 void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s);
 void launch_to_fixed(const float* uv, size_t n, int k, int32_t* q, int nblocks, cudaStream_t s);  // q = rint(x 2^k)
@@ -166,10 +153,12 @@ void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cud
 void launch_qd_count(const uint8_t* qxi, size_t N, unsigned long long* cnt, int* status, cudaStream_t s);
 void launch_gather_sym(const uint8_t* qxi, const unsigned long long* off, const uint16_t* qd, size_t n_qd, size_t N,
                        uint32_t* sym, int* status, cudaStream_t s);
+// the decoder's inputs of the pipeline, strip-diagonal (zeroed before): dcs =
+// (bound code, residual symbols), draw = verbatim values from L_d
 void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned long long* off, const int32_t* ld,
-                       size_t n_ld, size_t N, int2* raw, int* status, cudaStream_t s);
+                       size_t n_ld, int H, int W, int T, int2* dcs, int2* draw, int* status, cudaStream_t s);
+void launch_untag(int2* qhat, size_t N, cudaStream_t s);  // reconstruction words -> values
 void launch_to_float(const int2* qhat, size_t N, double inv_scale, float* out, cudaStream_t s);
-cudaError_t launch_decode_pipeline(const DecodeArgs& a, int nsm, cudaStream_t s);
 
 // k_traj.cu
 void launch_iota(unsigned* x, size_t n, cudaStream_t s);

@@ -499,6 +499,21 @@ __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
     if ((threadIdx.x & 31u) == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
 }
 
+// Decoding: the modes of the unit's blocks from the stream's mode bits.
+__device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, unsigned char* modes) {
+    const int nbu = a.U / a.B;
+    for (int bb = (int)(threadIdx.x & 31u); bb < nbu * nbu; bb += 32) {
+        const int ib = r0 / a.B + bb / nbu, jb = c0 / a.B + bb % nbu;
+        unsigned char m = 0;
+        if (ib < a.nby && jb < a.nbx) {
+            const size_t x = ((size_t)t * a.nby + ib) * a.nbx + jb;
+            m = (unsigned char)((__ldg(a.mode_bits + (x >> 3)) >> (x & 7)) & 1u);
+        }
+        modes[bb] = m;
+    }
+    __syncwarp();
+}
+
 // One prep unit: the U x U vertices from (r0, c0) of slice t >= 1 (it enters
 // the ready queue once slice t-1 is reconstructed around it).  Leaves in psl
 // the SL prediction of every vertex that uses SL, and with MoP the marker
@@ -513,7 +528,8 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
     const size_t sl = (size_t)H * W;
     const int2 z = make_int2(0, 0);
     const bool mop = a.pred == 2;
-    if (mop) {
+    const bool dec = a.decode != 0;  // decoding: the block modes come from the stream
+    if (mop && !dec) {
         // q(t) with a one-cell halo (asynchronous copies)
         const int2* Qt = a.q + (size_t)t * sl;
         for (int rr = 0; rr < U + 2; ++rr) {
@@ -578,7 +594,14 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
                     auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
                     net_tile<8>(a.net, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
                 }
-            if (a.pred == 4) {
+            if (a.pred == 4 && dec) {
+                unit_modes_from_bits(a, t, r0, c0, ps.modes);
+                const int nbu = U / a.B;
+                for (int k = lane; k < uh * uw; k += 32) {
+                    const int li = k / uw, lj = k % uw;
+                    if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+                }
+            } else if (a.pred == 4) {
                 // the learned mixture: block modes as MoP's with the net in SL's
                 // place; the scratch of the net gives way to q(t) and the samples
                 __threadfence();  // the predictions are read back through L2 by other lanes
@@ -613,8 +636,8 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
     }
     unsigned sub = 0, steps = 0;
     // semi-Lagrangian predictions, lanes over a compact list of sites: every
-    // vertex (pure SL) or the sampled sites (MoP, for the decisions)
-    {
+    // vertex (pure SL) or the sampled sites (MoP encoding, for the decisions)
+    if (!(mop && dec)) {
         const int st = mop ? a.n : 1;
         const int fr = (st - r0 % st) % st, fc = (st - c0 % st) % st;
         const int nr = uh > fr ? (uh - fr + st - 1) / st : 0;
@@ -634,15 +657,17 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
     }
     __syncwarp();
     if (mop) {
-        mop_unit(a, t, r0, c0, ps, Rw);
-        // the other vertices of the blocks that chose SL, gathered into a list
+        if (dec) unit_modes_from_bits(a, t, r0, c0, ps.modes);
+        else mop_unit(a, t, r0, c0, ps, Rw);
+        // the other vertices of the blocks that chose SL (decoding: all of
+        // them), gathered into a list
         const int nbu = U / a.B;
         int cnt = 0;
         for (int base = 0; base < uh * uw; base += 32) {
             const int k = base + lane;
             const int li = k / uw, lj = k % uw;
-            const bool need = k < uh * uw && !(((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0) &&
-                              ps.modes[(li / a.B) * nbu + lj / a.B] != 0;
+            const bool sampled = !dec && ((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0;
+            const bool need = k < uh * uw && !sampled && ps.modes[(li / a.B) * nbu + lj / a.B] != 0;
             const unsigned bal = __ballot_sync(FULL, need);
             if (need) ps.list[cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(li * 32 + lj);
             cnt += __popc(bal);
@@ -769,7 +794,7 @@ __device__ void prep_loop(const PipeArgs& p, Sm& sm) {
 // data does not exist (has_next, below_ok false): the copies then read nothing.
 __device__ __forceinline__ void stage_chunk(WaveRing& r, int g, const int2* cls, const unsigned* cm, const int2* Dq,
                                             const int2* Dn, const int2* Db, const int2* Dnb, bool has_next,
-                                            bool below_ok, int W) {
+                                            bool below_ok, bool with_cm, int W) {
     const int lane = (int)(threadIdx.x & 31u), slot = g % 3, k0 = g * kChunk, nsteps = W + 31;
     for (int p = lane; p < kChunk * 16; p += 32) {  // 8-byte elements: 16 pieces per step
         const int st = p >> 4, e = (p & 15) * 2, k = k0 + st;
@@ -779,7 +804,7 @@ __device__ __forceinline__ void stage_chunk(WaveRing& r, int g, const int2* cls,
         cp_async16(&r.q[slot][st][e], Dq + off, ok);
         cp_async16(&r.qn[slot][st][e], Dn + off, ok && has_next);
     }
-    for (int p = lane; p < kChunk * 8; p += 32) {  // 4-byte elements: 8 pieces per step
+    for (int p = lane; with_cm && p < kChunk * 8; p += 32) {  // 4-byte elements: 8 pieces per step
         const int st = p >> 3, e = (p & 7) * 4, k = k0 + st;
         const bool ok = k < nsteps;
         cp_async16(&r.cm[slot][st][e], cm + (ok ? (size_t)k * 32 + e : 0), ok);
@@ -830,6 +855,8 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     const bool mop = a.pred == 2 || a.pred == 4;  // psl carries the 3DL marker
     const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
     const bool has_next = t + 1 < T;
+    const bool dec = a.decode != 0;  // decoding: reconstruct from the stream's symbols
+    const bool stage_next = has_next && !dec, stage_below = below_ok && !dec;
     const int2 z = make_int2(0, 0);
     int published = -1;  // last step whose ready units were queued
     // outputs (a refers to the warp's shared slot: keep the pointers in registers)
@@ -871,9 +898,9 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
 
     WaveRing& ring = sm.ring;
     __syncwarp();
-    stage_chunk(ring, 0, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
+    stage_chunk(ring, 0, cls, cm, Dq, Dn, Db, Dnb, stage_next, stage_below, !dec, W);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    stage_chunk(ring, 1, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
+    stage_chunk(ring, 1, cls, cm, Dq, Dn, Db, Dnb, stage_next, stage_below, !dec, W);
     asm volatile("cp.async.commit_group;" ::: "memory");
     Pf fa, fb;
     fa.pn = fb.pn = z;
@@ -911,7 +938,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
         // g - 1 (no longer read), then wait for g and g + 1
         if (k % kChunk == 0) {
             __syncwarp();
-            stage_chunk(ring, k / kChunk + 2, cls, cm, Dq, Dn, Db, Dnb, has_next, below_ok, W);
+            stage_chunk(ring, k / kChunk + 2, cls, cm, Dq, Dn, Db, Dnb, stage_next, stage_below, !dec, W);
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
@@ -940,7 +967,31 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
         fromprev.y = __shfl_up_sync(FULL, res.y, 1);
         const int2 upleft = up;
         up = lane == 0 ? uk : fromprev;
-        if (rowok && col) {
+        if (rowok && col && dec) {
+            // decoding: qhat = prediction + code * width per component with a
+            // symbol, else the verbatim value
+            const int s0 = (k / kChunk) % 3, r0 = k % kChunk;
+            const int2 cs = ring.cl[s0][r0][lane];
+            const int code = cs.x;
+            const unsigned sy = (unsigned)cs.y;
+            int2 rec = ring.q[s0][r0][lane];
+            if (code > 0) {
+                int pu, pv;
+                if (need_sl && (!mop || pslk.x != kNoSL)) {
+                    pu = pslk.x;
+                    pv = pslk.y;
+                } else {
+                    pu = up.x + left.x + n3.x - upleft.x - n1.x - n2.x + n0.x;
+                    pv = up.y + left.y + n3.y - upleft.y - n1.y - n2.y + n0.y;
+                }
+                const unsigned w = (2u << (code - 1)) + 1u;
+                const unsigned su = sy & 0xFFFFu, sv = sy >> 16;
+                if (su) rec.x = (int)((unsigned)pu + (su - (unsigned)kRadius) * w);
+                if (sv) rec.y = (int)((unsigned)pv + (sv - (unsigned)kRadius) * w);
+            }
+            st_word(out_qhat + base + (size_t)i * W + j, rec);
+            res = rec;
+        } else if (rowok && col) {
             const int s0 = (k / kChunk) % 3, r0 = k % kChunk;
             const int s1 = ((k + 1) / kChunk) % 3, r1 = (k + 1) % kChunk;
             const int2 cl = ring.cl[s0][r0][lane];
