@@ -314,6 +314,15 @@ cpt_status cpt_train_predictor(const int32_t* prev, const int32_t* next, int32_t
  * Errors: CPT_ERR_ARG (ticket >= 2^32 - 1, limit outside [1 ms, 10 s]). */
 cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns);
 
+/* Failure injection for tests of the verification (the paper has no
+ * counterpart).  The next single-field compression with verification on the
+ * calling thread adds delta to the u component of the reconstruction of
+ * vertex `vertex` (global id (t*H + i)*W + j) after the encoder pipeline and
+ * before the verification, which must then report the changed predicates or
+ * the broken bound (CPT_ERR_VERIFY); the stream itself is unaffected.
+ * vertex < 0 clears a pending injection.  Always CPT_OK. */
+cpt_status cpt_inject_verify_fault(int64_t vertex, int32_t delta);
+
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);

@@ -96,6 +96,8 @@ def lib():
             L.cpt_error_string.argtypes = [C.c_int]
             L.cpt_last_error.restype = C.c_char_p
             L.cpt_version.restype = C.c_uint32
+            L.cpt_inject_verify_fault.restype = C.c_int
+            L.cpt_inject_verify_fault.argtypes = [C.c_int64, C.c_int32]
             L.cpt_inject_wave_stall.restype = C.c_int
             L.cpt_inject_wave_stall.argtypes = [C.c_int64, C.c_int64]
             L.cpt_fixed_point_noalloc.restype = C.c_int
@@ -320,6 +322,13 @@ def inject_wave_stall(ticket, timeout_s=0.2):
     the wave item with this ticket and limits every wait to timeout_s, so it
     returns ERR_TIMEOUT.  ticket=None clears a pending injection."""
     _check(lib().cpt_inject_wave_stall(-1 if ticket is None else int(ticket), int(timeout_s * 1e9)))
+
+
+def inject_verify_fault(vertex, delta):
+    """Failure injection for tests: the next compression on this thread adds
+    delta to the u component of one reconstructed vertex before verifying.
+    vertex=None clears a pending injection."""
+    _check(lib().cpt_inject_verify_fault(-1 if vertex is None else int(vertex), int(delta)))
 
 
 def fixed_point_noalloc(uv, q, k, stream=None):

@@ -415,6 +415,14 @@ static const PipeTuning kDecodeSchedule = {0, 0, 0, 0, 0};
 // ---------------------------------------------------------------------------
 // compression (Alg. 3)
 // ---------------------------------------------------------------------------
+// Failure injection for tests (per host thread): the next compression adds
+// delta to the u component of one reconstructed vertex before verification.
+struct VerifyFault {
+    long long vertex = -1;
+    int delta = 0;
+};
+static thread_local VerifyFault t_vfault;
+
 // One field of a compression call.  Its work is split at the host
 // synchronisations of the method (range -> fixed-point scale; compaction
 // totals; histograms -> code books; tile offsets -> stream layout), so that a
@@ -472,6 +480,7 @@ struct FieldJob {
     uint8_t* obuf = nullptr;
     bool obuf_pinned = false;
     size_t total = 0;
+    VerifyFault vfault;  // failure injection (tests)
 
     FieldJob(cudaStream_t st_, bool timing) : s(st_), ar(st_), tm(st_, timing) { std::memset(&st, 0, sizeof(st)); }
     ~FieldJob() { release_output(); }
@@ -825,6 +834,16 @@ struct FieldJob {
 
         // ---- stage 6: verification (Eq. 4 on every face, pointwise bound)
         std::memset(vo_h, 0, sizeof(VerifyOut));
+        if (prm->verify && vfault.vertex >= 0 && (size_t)vfault.vertex < N) {
+            // failure injection (tests): one corrupted reconstruction word
+            int2 w;
+            int2* p = reinterpret_cast<int2*>(d_qhat) + vfault.vertex;
+            CPT_CUDA(cudaMemcpyAsync(&w, p, sizeof(int2), cudaMemcpyDeviceToHost, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+            w.x += vfault.delta;
+            CPT_CUDA(cudaMemcpyAsync(p, &w, sizeof(int2), cudaMemcpyHostToDevice, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+        }
         if (prm->verify) {
             tm.begin(6);
             CPT_CUDA(ar.alloc(&d_vo, 1));
@@ -1221,6 +1240,8 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     job.dims = *dims;
     job.prm = prm;
     job.dbg = dbg;
+    job.vfault = t_vfault;
+    t_vfault = VerifyFault{};
     CPT_CUDA(cudaEventRecord(ev0, s));
     FieldJob* jp = &job;
     PipeTimes pt;
@@ -1410,9 +1431,8 @@ static bool parse_huff(Reader& r, uint32_t alphabet, HuffHost& h) {
     h.first[0] = 0;
     h.sorted.resize(std::max<uint32_t>(idx, 1));
     std::vector<uint32_t> fill(25, 0);
-    for (int l = 1; l <= 24; ++l)
-        for (uint32_t sy = 0; sy < alphabet; ++sy)
-            if (len[sy] == l) h.sorted[h.base[l] + fill[l]++] = sy;
+    for (uint32_t sy = 0; sy < alphabet; ++sy)  // by length, then symbol
+        if (len[sy]) h.sorted[h.base[len[sy]] + fill[len[sy]]++] = sy;
     h.lut.assign(4096, 0);
     for (int l = 1; l <= 12; ++l)
         for (uint32_t k = 0; k < h.count[l]; ++k) {
@@ -2007,6 +2027,12 @@ cpt_status cpt_decompress(const uint8_t* in, size_t in_bytes, float* uv_out, int
 cpt_status cpt_extract_trajectories(const float* uv, const cpt_dims* dims, int32_t scale_log2, cpt_trajs** out,
                                     void* cuda_stream) {
     return cpt::trajectories_impl(uv, dims, scale_log2, out, cuda_stream);
+}
+
+cpt_status cpt_inject_verify_fault(int64_t vertex, int32_t delta) {
+    cpt::t_vfault.vertex = vertex < 0 ? -1 : vertex;
+    cpt::t_vfault.delta = delta;
+    return CPT_OK;
 }
 
 cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns) {

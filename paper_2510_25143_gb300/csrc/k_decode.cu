@@ -1,9 +1,9 @@
 // Decoder kernels: canonical Huffman decoding from the stream's sync points,
 // expansion of the bound codes, residual symbols and verbatim values to the
-// vertices, and the reconstruction (the inverse of the raster loop of Alg. 3:
-// bounds come from the stream, so there is no face work), pipelined over
-// slices like the encoder: SL prep tiles and per-strip warp-systolic
-// wavefronts.  A malformed stream sets the status word to a corruption code;
+// vertices (in the strip-diagonal layout of the encoder's pipeline, which
+// then runs in decoding mode: the inverse of the raster loop of Alg. 3, with
+// bounds from the stream and no face work), and the conversion back to
+// float.  A malformed stream sets the status word to a corruption code;
 // nothing reads or writes out of bounds.
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"

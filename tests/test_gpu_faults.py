@@ -41,3 +41,31 @@ def test_injection_arguments():
     uv = synth.vortex_sum(32, 32, 3, seed=4)
     blob, _, _ = cpt.compress(_dev(uv), 1e-2)
     assert blob == oracle.compress(uv, 1e-2)["bytes"]
+
+
+def test_verification_catches_a_corrupted_reconstruction():
+    """The verification is not vacuous: one reconstructed value pushed past
+    the bound, or moved across a crossed face, is reported."""
+    import numpy as np
+    uv = synth.vortex_sum(48, 56, 5, seed=6)
+    d = _dev(uv)
+    blob, st, g = cpt.compress(d, 1e-2, pred="mop", debug=True)
+    assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
+    T, H, W, _ = uv.shape
+    # (1) far past the pointwise bound at an interior vertex
+    v = (2 * H + H // 2) * W + W // 2
+    cpt.inject_verify_fault(v, 1 << 20)
+    b2, s2, _ = cpt.compress(d, 1e-2, pred="mop", check=False)
+    assert s2["status"] == cpt.ERR_VERIFY and s2["linf"] > s2["eps"]
+    assert b2 == blob  # the stream does not change
+    # (2) a vertex of a crossed face flipped to the other side of the origin
+    crossed = np.flatnonzero(g["mask"].reshape(-1))
+    v = int(crossed[len(crossed) // 2])
+    qv = int(g["qhat"].reshape(-1, 2)[v, 0])
+    cpt.inject_verify_fault(v, -2 * qv if qv != 0 else 1 << 10)
+    _, s3, _ = cpt.compress(d, 1e-2, pred="mop", check=False)
+    assert s3["status"] == cpt.ERR_VERIFY
+    assert s3["verify_mismatch_slice"] + s3["verify_mismatch_slab"] > 0 or s3["linf"] > s3["eps"]
+    # nothing pending afterwards
+    _, s4, _ = cpt.compress(d, 1e-2, pred="mop")
+    assert s4["verify_mismatch_slice"] == 0 and s4["linf"] <= s4["eps"]
