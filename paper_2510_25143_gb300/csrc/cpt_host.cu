@@ -1386,6 +1386,7 @@ struct Reader {
 struct HuffHost {
     uint64_t nsym = 0, nwords = 0;
     std::vector<uint32_t> lut, first, count, base, sorted;
+    std::vector<unsigned long long> lut3;  // up to three codes per 12-bit window
     std::vector<unsigned long long> chunk_off;
     const uint8_t* words = nullptr;
 };
@@ -1440,6 +1441,22 @@ static bool parse_huff(Reader& r, uint32_t alphabet, HuffHost& h) {
             const uint32_t lo = c << (12 - l), span = 1u << (12 - l);
             for (uint32_t x = 0; x < span; ++x) h.lut[lo + x] = (sy << 5) | (uint32_t)l;
         }
+    // the complete codes at the start of each 12-bit window, up to three
+    h.lut3.assign(4096, 0ull);
+    for (uint32_t v = 0; v < 4096; ++v) {
+        unsigned long long e = 0;
+        uint32_t pos = 0, cnt = 0;
+        while (cnt < 3 && pos < 12) {
+            const uint32_t rest = (v << pos) & 4095u;  // the window's bits from pos on, left aligned
+            const uint32_t le = h.lut[rest];
+            const uint32_t l = le & 31u;
+            if (le == 0 || pos + l > 12) break;
+            e |= (unsigned long long)(le >> 5) << (7 + 16 * cnt);
+            pos += l;
+            ++cnt;
+        }
+        h.lut3[v] = e | cnt | ((unsigned long long)pos << 2);
+    }
     return true;
 }
 
@@ -1453,6 +1470,9 @@ static cpt_status decode_huff_stream(const HuffHost& hh, Sym* d_out, int* d_stat
     if (hh.nwords) CPT_CUDA(cudaMemcpyAsync(d_words, hh.words, 4 * hh.nwords, cudaMemcpyHostToDevice, s));
     CPT_CUDA(ar.alloc(&d_off, hh.chunk_off.size()));
     CPT_CUDA(cudaMemcpyAsync(d_off, hh.chunk_off.data(), 8 * hh.chunk_off.size(), cudaMemcpyHostToDevice, s));
+    unsigned long long* d_lut3;
+    CPT_CUDA(ar.alloc(&d_lut3, 4096));
+    CPT_CUDA(cudaMemcpyAsync(d_lut3, hh.lut3.data(), 8 * 4096, cudaMemcpyHostToDevice, s));
     const size_t ntab = 4096 + 3 * 25 + hh.sorted.size();
     std::vector<uint32_t> tab;
     tab.reserve(ntab);
@@ -1473,6 +1493,7 @@ static cpt_status decode_huff_stream(const HuffHost& hh, Sym* d_out, int* d_stat
     h.count = d_tab + 4096 + 25;
     h.base = d_tab + 4096 + 50;
     h.sorted = d_tab + 4096 + 75;
+    h.lut3 = d_lut3;
     if constexpr (sizeof(Sym) == 1) launch_huff_decode_u8(h, reinterpret_cast<uint8_t*>(d_out), d_status, s);
     else launch_huff_decode_u16(h, reinterpret_cast<uint16_t*>(d_out), d_status, s);
     // the host copies of words/tables must outlive the asynchronous copies

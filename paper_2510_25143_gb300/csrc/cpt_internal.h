@@ -109,6 +109,10 @@ struct HuffDecode {
     const uint32_t* count;          // [25] codes of each length
     const uint32_t* base;           // [25] index of the first symbol of each length in `sorted`
     const uint32_t* sorted;         // symbols ordered by (length, symbol)
+    // [4096] for each 12-bit window, the complete codes at its start (up to
+    // three): count | total length << 2 | symbol k << (7 + 16 k); count 0 =
+    // the first code is longer than 12 bits
+    const unsigned long long* lut3;
 };
 
 // k_field.cu

@@ -11,39 +11,94 @@
 namespace cpt {
 
 // ---------------------------------------------------------------------------
-// Huffman decoding: one thread per chunk of kChunkSyms symbols, starting at
-// the chunk's recorded bit offset; codes are read most significant bit first.
+// Huffman decoding: one thread per chunk of kChunkSyms symbols (the stream's
+// sync points), codes read most significant bit first.  The bits pass
+// through a 64-bit register buffer refilled a word at a time; one lookup of
+// the window's first 12 bits yields up to three complete short codes
+// (lut3), codes longer than 12 bits take the canonical tables.  Symbols
+// leave in 32-bit words.  The tables sit in shared memory.
 // ---------------------------------------------------------------------------
 template <typename Out>
-__global__ void __launch_bounds__(128) huff_decode_kernel(HuffDecode h, Out* __restrict__ out, int* __restrict__ status) {
+__global__ void __launch_bounds__(64) huff_decode_kernel(HuffDecode h, Out* __restrict__ out, int* __restrict__ status) {
+    __shared__ unsigned long long lut3[4096];
+    __shared__ uint32_t first[25], count[25], base[25];
+    for (int k = threadIdx.x; k < 4096; k += blockDim.x) lut3[k] = __ldg(h.lut3 + k);
+    if (threadIdx.x < 25) {
+        first[threadIdx.x] = __ldg(h.first + threadIdx.x);
+        count[threadIdx.x] = __ldg(h.count + threadIdx.x);
+        base[threadIdx.x] = __ldg(h.base + threadIdx.x);
+    }
+    __syncthreads();
     const unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long nchunks = (h.nsym + kChunkSyms - 1) / kChunkSyms;
     if (c >= nchunks) return;
     const unsigned long long nbits = h.nwords * 32ull;
+    const unsigned long long nw = h.nwords + 2;  // words has two zero words of padding
     unsigned long long p = h.chunk_off[c];
+    if (p > nbits) { atomicCAS(status, 0, kStatusCorrupt); return; }
+    // buf holds the stream's bits from p on, left aligned; nb of them are valid
+    unsigned long long wi = p >> 5;
+    unsigned long long buf = (((unsigned long long)__ldg(h.words + wi) << 32) | __ldg(h.words + wi + 1)) << (p & 31);
+    int nb = 64 - (int)(p & 31);
+    wi += 2;
     const unsigned long long x0 = c * kChunkSyms;
-    const unsigned long long x1 = min(h.nsym, x0 + kChunkSyms);
-    for (unsigned long long x = x0; x < x1; ++x) {
-        if (p >= nbits) { atomicCAS(status, 0, kStatusCorrupt); return; }
-        const unsigned long long wi = p >> 5;  // words has two zero words of padding
-        const unsigned long long w64 = (((unsigned long long)h.words[wi] << 32) | h.words[wi + 1]) << (p & 31);
-        const unsigned w24 = (unsigned)(w64 >> 40);
-        unsigned e = h.lut[w24 >> 12];
-        if (e == 0) {
-            for (int l = 13; l <= 24; ++l) {
-                const unsigned code = w24 >> (24 - l);
-                const unsigned k = code - h.first[l];
-                if (code >= h.first[l] && k < h.count[l]) {
-                    e = (h.sorted[h.base[l] + k] << 5) | (unsigned)l;
+    const unsigned n = (unsigned)(min(h.nsym, x0 + kChunkSyms) - x0);  // symbols of this chunk
+    Out* o = out + x0;  // 4-byte aligned: kChunkSyms * sizeof(Out) is
+    constexpr unsigned kPerWord = 4 / sizeof(Out);
+    uint32_t word = 0;  // symbols of the current output word
+    unsigned x = 0, inw = 0;
+    unsigned long long used = 0;  // bits consumed
+    const unsigned long long avail = nbits - p;
+    auto emit = [&](uint32_t sym) {
+        word |= sym << (8 * sizeof(Out) * inw);
+        if (++inw == kPerWord) {
+            *reinterpret_cast<uint32_t*>(o + x + 1 - kPerWord) = word;
+            word = 0;
+            inw = 0;
+        }
+        ++x;
+    };
+    while (x < n) {
+        if (nb <= 32) {  // keeps >= 24 valid bits (the longest code) before every lookup
+            const unsigned long long w = wi < nw ? __ldg(h.words + wi) : 0u;
+            buf |= w << (32 - nb);
+            nb += 32;
+            ++wi;
+        }
+        const unsigned long long e = lut3[(unsigned)(buf >> 52)];
+        const unsigned cnt = (unsigned)(e & 3u);
+        if (cnt > 0 && x + cnt <= n) {
+            const unsigned len = (unsigned)(e >> 2) & 31u;
+            emit((uint32_t)(e >> 7) & 0xFFFFu);
+            if (cnt > 1) emit((uint32_t)(e >> 23) & 0xFFFFu);
+            if (cnt > 2) emit((uint32_t)(e >> 39) & 0xFFFFu);
+            buf <<= len;
+            nb -= (int)len;
+            used += len;
+        } else {  // one code: longer than 12 bits, or the chunk's last symbols
+            const unsigned w24 = (unsigned)(buf >> 40);
+            unsigned sym = 0, l = 0;
+            for (unsigned ll = 1; ll <= 24; ++ll) {
+                const unsigned code = w24 >> (24 - ll);
+                const unsigned k = code - first[ll];
+                if (code >= first[ll] && k < count[ll]) {
+                    sym = __ldg(h.sorted + base[ll] + k);
+                    l = ll;
                     break;
                 }
             }
-            if (e == 0) { atomicCAS(status, 0, kStatusCorrupt); return; }
+            if (l == 0) { atomicCAS(status, 0, kStatusCorrupt); return; }
+            emit(sym);
+            buf <<= l;
+            nb -= (int)l;
+            used += l;
         }
-        p += e & 31u;
-        out[x] = (Out)(e >> 5);
+        if (used > avail) { atomicCAS(status, 0, kStatusCorrupt); return; }
     }
-    if (p > nbits || (c + 1 < nchunks && p != h.chunk_off[c + 1])) atomicCAS(status, 0, kStatusCorrupt);
+    for (unsigned q = 0; q < inw; ++q)  // the last, partial word
+        o[x - inw + q] = (Out)(word >> (8 * sizeof(Out) * q));
+    p += used;
+    if (c + 1 < nchunks && p != h.chunk_off[c + 1]) atomicCAS(status, 0, kStatusCorrupt);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,11 +184,11 @@ __global__ void __launch_bounds__(256) to_float_kernel(const int2* __restrict__ 
 // ---------------------------------------------------------------------------
 void launch_huff_decode_u8(const HuffDecode& h, uint8_t* out, int* status, cudaStream_t s) {
     const unsigned long long nchunks = (h.nsym + kChunkSyms - 1) / kChunkSyms;
-    if (nchunks) huff_decode_kernel<uint8_t><<<(unsigned)((nchunks + 127) / 128), 128, 0, s>>>(h, out, status);
+    if (nchunks) huff_decode_kernel<uint8_t><<<(unsigned)((nchunks + 63) / 64), 64, 0, s>>>(h, out, status);
 }
 void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cudaStream_t s) {
     const unsigned long long nchunks = (h.nsym + kChunkSyms - 1) / kChunkSyms;
-    if (nchunks) huff_decode_kernel<uint16_t><<<(unsigned)((nchunks + 127) / 128), 128, 0, s>>>(h, out, status);
+    if (nchunks) huff_decode_kernel<uint16_t><<<(unsigned)((nchunks + 63) / 64), 64, 0, s>>>(h, out, status);
 }
 void launch_qd_count(const uint8_t* qxi, size_t N, unsigned long long* cnt, int* status, cudaStream_t s) {
     qd_count_kernel<<<1216, 256, 0, s>>>(qxi, N, cnt, status);
