@@ -131,10 +131,8 @@ inline size_t diag_elems(int H, int W, int T) { return (size_t)T * ((H + 31) / 3
 cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s);
 void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);
 constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols
-size_t encode_smem_bytes();
 
 // k_entropy.cu
-struct EntropyBufs;
 size_t scan_temp_elems(size_t n);
 void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s);
 void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long long* tmp, cudaStream_t s);

@@ -8,28 +8,32 @@
 // raster predecessor, whose reconstructions lie within +-E of the originals)
 // could still lower that bound.
 //
-// encode_pipeline_kernel (one persistent launch over all slices) does the
-// rest, pipelining consecutive slices.  Its warps have one of two roles.
+// encode_pipeline_kernel (one persistent launch over all slices of one field
+// or of a batch of fields) does the rest, pipelining consecutive slices.  Its
+// warps have one of two roles.
 // wave(t, s)     rows 32s..32s+31 of slice t: the flagged faces with the actual
 //                reconstructions, xi quantisation, prediction and residual
 //                quantisation with immediate write-back (Sec. V-A).  Lane l
 //                handles row 32s+l and, at step k, column k-l; the
 //                reconstruction of (i-1, j) arrives from lane l-1 by shuffle,
-//                the row above the strip from wave(t, s-1) through global memory
-//                (release/acquire progress words).  Wave warps take the (t, s)
-//                from a ticket counter ordered by the diagonal A*t + s,
-//                A = 1 + ceil((31+R)/32) (R: the semi-Lagrangian reach), which
-//                puts every wave an item depends on at a smaller ticket.
-// prep units     (SL and MoP only) U x U squares of slice t >= 1 (U = 8 for SL, 16
-//                or 32 for MoP): semi-Lagrangian
-//                predictions (Sec. VI-A) and MoP block modes (Sec. VI-B).  A unit
-//                needs slice t-1 final around it; the wave of slice t-1 that
-//                makes it so appends it to a ready queue, and prep warps take the
-//                queue in order.  wave(t, s) waits for the units of each tile.
+//                the row above the strip from wave(t, s-1) and slice t-1 from
+//                the waves of t-1 as tagged reconstruction words polled in
+//                global memory.  The read-only inputs come from strip-diagonal
+//                copies staged two chunks ahead into a shared-memory ring.
+//                Wave warps take (field, t, s) from a ticket counter whose
+//                order puts every wave an item depends on at a smaller ticket.
+// prep units     (SL, MoP and the learned predictors) U x U squares of slice
+//                t >= 1: semi-Lagrangian or learned predictions (Sec. VI-A) and
+//                MoP block modes (Sec. VI-B).  A unit needs slice t-1 final
+//                around it; the wave of slice t-1 that makes it so appends it
+//                to a ready queue, and prep warps take the queue in order.
+//                wave(t, s) waits for the units of each unit column.
+// In decoding mode the same waves rebuild the reconstruction from the
+// stream's codes (no face work) and MoP units read their modes.
 // Waves wait only for waves with smaller tickets and for queued units; queued
-// units wait for nothing.  Every warp is resident, so the pipeline cannot
-// deadlock; each wait is bounded in time and sets the status word when it
-// expires.
+// units wait for nothing but words already written.  Every warp is resident,
+// so the pipeline cannot deadlock; each wait is bounded in time and sets the
+// status word when it expires.
 #include <algorithm>
 #include <type_traits>
 
