@@ -31,7 +31,8 @@ struct NetDev {
 constexpr int kNetDevFloats = kNetParams;  // same count, transposed weights then biases per layer
 
 // One layer over an OH x OW output region whose (0, 0) sits at global
-// (gy0, gx0); in is the CIN x (OH+2) x (OW+2) window around it.  Outputs at
+// (gy0, gx0); in is the CIN x (OH+2) x (OW+2) window around it.  The weights
+// and biases may sit in global or shared memory (plain loads).  Outputs at
 // positions outside the H x W field are 0 (the next layer's padding).  Each
 // lane computes two positions (p and p + 32) for a group of up to 16 output
 // channels at a time, so that every weight it loads (four channels at a
@@ -59,7 +60,7 @@ __device__ __forceinline__ void net_layer(const float* __restrict__ in, const fl
         for (int cg = 0; cg < COUT; cg += G) {
             float acc0[G], acc1[G];
 #pragma unroll
-            for (int c = 0; c < G; ++c) acc0[c] = acc1[c] = __ldg(b + cg + c);
+            for (int c = 0; c < G; ++c) acc0[c] = acc1[c] = b[cg + c];
             for (int ci = 0; ci < CIN; ++ci)
 #pragma unroll
                 for (int ky = 0; ky < 3; ++ky)
@@ -71,7 +72,7 @@ __device__ __forceinline__ void net_layer(const float* __restrict__ in, const fl
                         if constexpr (G % 4 == 0) {
 #pragma unroll
                             for (int c = 0; c < G; c += 4) {
-                                const float4 w = __ldg(reinterpret_cast<const float4*>(wp + c));
+                                const float4 w = *reinterpret_cast<const float4*>(wp + c);
                                 acc0[c] = __fmaf_rn(w.x, v0, acc0[c]);
                                 acc0[c + 1] = __fmaf_rn(w.y, v0, acc0[c + 1]);
                                 acc0[c + 2] = __fmaf_rn(w.z, v0, acc0[c + 2]);
@@ -84,7 +85,7 @@ __device__ __forceinline__ void net_layer(const float* __restrict__ in, const fl
                         } else {
 #pragma unroll
                             for (int c = 0; c < G; c += 2) {
-                                const float2 w = __ldg(reinterpret_cast<const float2*>(wp + c));
+                                const float2 w = *reinterpret_cast<const float2*>(wp + c);
                                 acc0[c] = __fmaf_rn(w.x, v0, acc0[c]);
                                 acc0[c + 1] = __fmaf_rn(w.y, v0, acc0[c + 1]);
                                 acc1[c] = __fmaf_rn(w.x, v1, acc1[c]);

@@ -523,7 +523,7 @@ __device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, 
 // the SL prediction of every vertex that uses SL, and with MoP the marker
 // kNoSL on the vertices of blocks that keep 3DL.
 template <class Sm>
-__device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
+__device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, const float* w2s) {
     const unsigned FULL = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, U = a.U;
     const int uh = min(U, H - r0), uw = min(U, W - c0);
@@ -591,12 +591,16 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm) {
     int2* Psl = a.psl + (size_t)t * sl;
     if constexpr (Sm::kNet) {
         if (a.pred == 3 || a.pred == 4) {
-            // learned predictor: the unit's 8 x 8 tiles from the staged window (reach 3)
+            // learned predictor: the unit's 8 x 8 tiles from the staged window
+            // (reach 3), the second layer's weights from the CTA's shared copy
+            NetDev nd = a.net;
+            nd.w2t = w2s;
+            nd.b2 = w2s + kNetW2;
             auto prev = [&](int i, int j) -> int2 { return Ps.at(i, j); };
             for (int tr = 0; tr < uh; tr += 8)
                 for (int tc = 0; tc < uw; tc += 8) {
                     auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
-                    net_tile<8>(a.net, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
+                    net_tile<8>(nd, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
                 }
             if (a.pred == 4 && dec) {
                 unit_modes_from_bits(a, t, r0, c0, ps.modes);
@@ -756,7 +760,7 @@ __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) 
 // arguments are copied into the warp's shared slot; otherwise the launch has
 // one field, read from parameter space.
 template <bool kBatch, class Sm>
-__device__ void prep_loop(const PipeArgs& p, Sm& sm) {
+__device__ void prep_loop(const PipeArgs& p, Sm& sm, const float* w2s) {
     for (;;) {
         unsigned pos = 0;
         int stop = 0;
@@ -785,7 +789,7 @@ __device__ void prep_loop(const PipeArgs& p, Sm& sm) {
         const unsigned rest = id / (unsigned)a.nuc;
         const int ur = (int)(rest % (unsigned)a.nur);
         const int t = (int)(rest / (unsigned)a.nur) + 1;
-        prep_unit(a, t, ur * a.U, uc * a.U, sm);
+        prep_unit(a, t, ur * a.U, uc * a.U, sm, w2s);
     }
 }
 
@@ -1091,8 +1095,18 @@ __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = (int)(threadIdx.x >> 5), wpc = (int)(blockDim.x >> 5);
     Sm& sm = reinterpret_cast<Sm*>(smem_raw)[wid];
+    // the learned net's second-layer weights and biases, one copy per CTA
+    // after the warps' slices (every field of a launch shares the model)
+    float* w2s = reinterpret_cast<float*>(smem_raw + sizeof(Sm) * wpc);
+    if constexpr (NET) {
+        if (p.one.pred == 3 || p.one.pred == 4) {
+            for (int k = (int)threadIdx.x; k < kNetW2 + kNetC; k += (int)blockDim.x)
+                w2s[k] = k < kNetW2 ? __ldg(p.one.net.w2t + k) : __ldg(p.one.net.b2 + (k - kNetW2));
+        }
+        __syncthreads();
+    }
     if ((int)blockIdx.x * wpc + wid < p.prep_warps) {
-        if constexpr (UMAX > 0) prep_loop<kBatch>(p, sm);
+        if constexpr (UMAX > 0) prep_loop<kBatch>(p, sm, w2s);
         return;
     }
     int cur = -1;  // field whose arguments sit in the warp's slot
@@ -1149,12 +1163,13 @@ static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    int wpc = (int)std::min<size_t>((size_t)kMaxWarpsPerCta, (size_t)optin / slice);
+    const size_t wshared = NET ? sizeof(float) * (kNetW2 + kNetC) : 0;  // the net's shared weights
+    int wpc = (int)std::min<size_t>((size_t)kMaxWarpsPerCta, ((size_t)optin - wshared) / slice);
     if (tune.warps_per_sm > 0) wpc = std::min(wpc, tune.warps_per_sm);
     if (wpc < 1) return cudaErrorInvalidConfiguration;
     const bool batch = p.nfields > 1;
     auto kern = batch ? encode_pipeline_kernel<true, UMAX, NET> : encode_pipeline_kernel<false, UMAX, NET>;
-    const size_t smem = slice * wpc;
+    const size_t smem = slice * wpc + wshared;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
