@@ -387,9 +387,6 @@ def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
              for st in stats)
     out_bytes = sum(len(x) for x in blobs)
     sizes = [d["H"] * d["W"] * d["T"] for d in specs]
-    # device time per stage summed over the fields (each field's own launches;
-    # the pipeline is one launch for all)
-    stage_sum = {k: round(sum(st["ms_stage"][k] for st in stats), 2) for k in stats[0]["ms_stage"] if k != "wavefront"}
     return {"workload": f"batch{n_fields}", "fields": n_fields, "input_bytes": nbytes, "rel_eb": eb, "pred": pred,
             "data": "synthetic vortex-sum fields, sides 128..1024 (multiples of 16), 10..200 steps, drawn on the GPU",
             "smallest_vertices": min(sizes), "largest_vertices": max(sizes),
@@ -397,7 +394,7 @@ def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
             "batch_host_ms": round(host_batch, 2), "single_calls_MB/s": round(nbytes / 1e6 / (ms_single / 1e3), 1),
             "single_calls_ms": round(ms_single, 2), "speedup": round(ms_single / ms_batch, 3),
             "first_call_ms": round(ms_first, 2), "tune_ms": round(b0["ms_tune"], 2),
-            "pipeline_ms": round(b["ms_pipeline"], 2), "host_phase_ms": b["ms_phase"][:7], "stage_ms_sum": stage_sum,
+            "pipeline_ms": round(b["ms_pipeline"], 2), "host_phase_ms": b["ms_phase"][:7],
             "groups": b["groups"], "schedule": list(b["schedule"]),
             "launches": b["launches"], "ratio": round(nbytes / out_bytes, 4), "preserved": bool(ok),
             "identical_to_single_calls": bool(identical)}

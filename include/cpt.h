@@ -207,7 +207,11 @@ typedef struct {
  *   dims[f]     : its grid
  *   out[f]      : receives a library-allocated host buffer (cpt_free each)
  *   stats       : nullable [nfields]; ms_total is the whole call's time,
- *                 ms_stage[4] the shared pipeline launch of the field's group
+ *                 ms_stage[4] the shared pipeline launch of the field's group;
+ *                 the other ms_stage entries are event intervals on the
+ *                 group's one stream, which also hold the other fields'
+ *                 launches of the same phase and the host waits between
+ *                 phases (ms_phase of batch_stats is the per-phase split)
  *   batch_stats : nullable
  * Errors: as cpt_compress; on any error but CPT_ERR_VERIFY no output is
  * returned (every out[f] is NULL).  CPT_ERR_VERIFY: every stream is

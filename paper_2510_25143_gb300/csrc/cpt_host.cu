@@ -445,7 +445,7 @@ struct FieldJob {
     double dx = 1, dy = 1, dt = 1;
     size_t N = 0, NV = 0;
     bool has_net = false, has_modes = false, want_sl = false;
-    // pinned small host values (assigned by the driver)
+    // pinned small host values (assigned by run_jobs)
     RangePartial* part_h = nullptr;  // [rblocks]
     unsigned long long* small_h = nullptr;  // [0] last count, [1] last offset, [2..9] counters
     VerifyOut* vo_h = nullptr;
@@ -475,7 +475,7 @@ struct FieldJob {
     StreamPlan sx, sd;
     unsigned* d_hist = nullptr;
     size_t st_hist = 0, st_modes = 0, st_tab = 0, st_toff = 0;
-    uint8_t* stage_h = nullptr;  // pinned staging of the entropy stage (assigned by the driver)
+    uint8_t* stage_h = nullptr;  // pinned staging of the entropy stage (assigned by run_jobs)
     VerifyOut* d_vo = nullptr;
     uint8_t* obuf = nullptr;
     bool obuf_pinned = false;
