@@ -86,6 +86,22 @@ def test_small_integer_fields_degenerate_sos(seed):
     compare(uv, 0.4, "mop", eb_mode="abs", block=4)
 
 
+@pytest.mark.parametrize("shift,noise", [(1.0, 0.0), (1.0, 2e-4), (0.0, 2e-4)])
+def test_mop_carried_and_static_patterns(shift, noise):
+    """Fields on which the MoP choice is fixed by the predictors' exactness
+    (SL in every interior block of a pattern the flow carries, 3DL on a static
+    one); small noise breaks the degenerate faces that make the noiseless
+    carried field lossless, so the codes and both predictors run."""
+    from test_oracle_pins import _pattern_field
+    uv = _pattern_field(5, 70, 90, shift=shift)
+    uv = uv + np.random.default_rng(12).normal(0.0, noise, uv.shape).astype(np.float32)
+    _, st, g, r = compare(uv, 1e-3, "mop")
+    if shift:
+        assert (g["modes"][1:, 1:-1, 1:-1] == 1).all()
+    else:
+        assert st["sl_blocks"] < st["blocks"] // 10
+
+
 def test_zero_and_constant_fields():
     compare(np.zeros((3, 6, 7, 2), np.float32), 1e-2, "mop")
     c = np.ones((3, 6, 7, 2), np.float32) * 0.25

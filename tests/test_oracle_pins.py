@@ -420,6 +420,93 @@ def test_score_matches_entropy():
 
 
 # ---------------------------------------------------------------------------
+# MoP block choice (Sec. VI-B) on fields where one predictor is exact
+# ---------------------------------------------------------------------------
+def _pattern_field(T, H, W, shift, a=0.02):
+    """u = 1 + a h(x - shift t, y), v = a g(x - shift t, y): a smooth pattern
+    (wavelengths 6 and 7 cells) carried in x by `shift` cells per step; the
+    flow itself moves one cell per step in x (|u - 1| <= a)."""
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    uv = np.empty((T, H, W, 2), np.float32)
+    for t in range(T):
+        xs = x - shift * t
+        h = np.sin(2 * np.pi * xs / 6 + 0.3) * np.cos(2 * np.pi * y / 7 + 1.1)
+        g = np.cos(2 * np.pi * xs / 6 - 0.7) * np.sin(2 * np.pi * y / 7 + 0.4)
+        uv[t, :, :, 0] = 1.0 + a * h
+        uv[t, :, :, 1] = a * g
+    return uv
+
+
+def _interior_modes(res, B=16):
+    m = res["modes"]
+    return m[1:, 1:-1, 1:-1]
+
+
+def test_mop_prefers_sl_when_the_flow_carries_the_field():
+    """A pattern moved one cell per step by a flow of speed 1: the RK2
+    departure point (Eqs. 7-8) of an interior vertex is the vertex one cell
+    upstream up to a*|h| <= 0.02 cells, so SL misses by at most that offset
+    times the pattern's slope (a * 2 pi / 6) plus the bilinear error, about
+    eps = 1e-3 * range in the worst case and a twentieth of it typically,
+    while the 3-D Lorenzo error is the pattern's mixed third difference,
+    several eps.  Every interior block of every slice t >= 1 must pick SL."""
+    uv = _pattern_field(4, 64, 80, shift=1.0)
+    res = oracle.compress(uv, 1e-3, pred="mop", block=16)
+    assert (res["modes"][0] == 0).all()  # slice 0 has no slice t-1
+    assert (_interior_modes(res) == 1).all()
+    # the premise, on the fixed-point field
+    q, e, k = res["q"], res["stats"]["eps_int"], res["stats"]["k"]
+    c = oracle.cfl(1.0, 1.0, k)
+    sl_err, lz_err = [], []
+    for t in (1, 3):
+        for i in range(17, 47, 3):
+            for j in range(17, 63, 3):
+                pu, pv, mode = oracle.sl_predict(q[t - 1], i, j, c, c)
+                assert mode == 0
+                sl_err += [abs(pu - q[t, i, j, 0]), abs(pv - q[t, i, j, 1])]
+                lz_err += [abs(oracle.lorenzo(q, t, i, j, ch) - q[t, i, j, ch]) for ch in (0, 1)]
+    assert max(sl_err) < e / 2 and np.median(sl_err) < e / 8
+    assert np.median(lz_err) > 2 * e and min(lz_err) > max(sl_err)
+
+
+def test_mop_prefers_3dl_on_a_static_field():
+    """The same pattern held still: every 3-D Lorenzo term of slice t-1
+    cancels its slice-t partner up to the reconstruction error, while SL still
+    traces one cell upstream and misses by the pattern's one-cell change
+    (about 20 eps).  Every block must keep 3DL."""
+    uv = _pattern_field(4, 64, 80, shift=0.0)
+    res = oracle.compress(uv, 1e-3, pred="mop", block=16)
+    assert (res["modes"] == 0).all()
+
+
+def test_mop_tie_keeps_3dl():
+    """A uniform flow: both predictors are exact, the scores are equal and the
+    switching margin (SL must be 0.3 % cheaper) keeps 3DL in every block."""
+    uv = np.zeros((3, 40, 48, 2), np.float32)
+    uv[..., 0], uv[..., 1] = 0.75, -0.5
+    res = oracle.compress(uv, 1e-3, pred="mop", block=16)
+    assert (res["modes"] == 0).all()
+    assert res["stats"]["sl_blocks"] == 0
+
+
+def test_time_constant_field_is_lossless():
+    """Alg. 2 returns 0 on a face whose values make M = 0.  In a field that
+    does not change in time the edge from (t, i, j) to (t + 1, i, j) joins
+    equal values, so every face through it is degenerate, and every vertex
+    lies on such an edge: Alg. 4 gives xi = 0 everywhere and the whole field
+    is stored verbatim (while no face is crossed)."""
+    uv = _pattern_field(3, 20, 24, shift=0.0)
+    res = oracle.compress(uv, 1e-3, pred="lorenzo")
+    assert res["stats"]["crossed_faces"] == 0
+    assert (res["xi"] == 0).all() and res["stats"]["lossless_vertices"] == 3 * 20 * 24
+    assert (res["qhat"] == res["q"]).all()
+    # one step of change in time breaks the degeneracy of the interior vertices
+    uv[1:, :, :, 0] += np.float32(0.001) * np.arange(1, 3, dtype=np.float32)[:, None, None]
+    uv[1:, :, :, 1] -= np.float32(0.0007) * np.arange(1, 3, dtype=np.float32)[:, None, None]
+    assert (oracle.compress(uv, 1e-3, pred="lorenzo")["xi"][:, 2:-2, 2:-2] > 0).any()
+
+
+# ---------------------------------------------------------------------------
 # Canonical length-limited Huffman (package-merge)
 # ---------------------------------------------------------------------------
 def _huffman_cost(freq):
