@@ -5,6 +5,9 @@ restatement of the compressor of "Time-Varying Vector Field Compression with
 Preserved Critical Point Trajectories" (Alg. 1-4, Sec. VI).  Only the tests,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this module.  The CUDA library never links or calls it.
+
+Parity unpinned: the stream's byte layout, which the paper does not fix; it is
+pinned only through the round trip and the invariants.
 """
 from __future__ import annotations
 

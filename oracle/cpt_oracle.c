@@ -32,6 +32,11 @@
  *       net, bfloat16 weights, float32 fused multiply-add chains in a fixed
  *       order, prediction = qhat(t-1) + rint(clamp(y, -2, 2) * 2^23).
  *
+ * Parity unpinned: the byte layout of the stream (R12) has no worked example
+ * in the paper; the tests pin it only through the round trip, the invariants
+ * (every face predicate kept, |x - x_hat| <= eps) and the optimality of the
+ * Huffman code lengths.  Every other step has a pin of its own.
+ *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no -ffast-math, no FMA).
  */
 #include <math.h>
