@@ -102,6 +102,33 @@ def test_mop_carried_and_static_patterns(shift, noise):
         assert st["sl_blocks"] < st["blocks"] // 10
 
 
+def test_invalid_arguments_are_rejected():
+    """Inputs outside the method's domain come back as status codes, with no
+    stream, and the library stays usable."""
+    good = synth.vortex_sum(9, 10, 2, seed=13)
+    nan, inf = good.copy(), good.copy()
+    nan[1, 4, 5, 0] = np.nan
+    inf[0, 0, 0, 1] = -np.inf
+    cases = [
+        (np.zeros((2, 1, 5, 2), np.float32), 1e-2, {}, cpt.ERR_ARG),      # H < 2
+        (np.zeros((2, 5, 1, 2), np.float32), 1e-2, {}, cpt.ERR_ARG),      # W < 2
+        (np.zeros((0, 5, 5, 2), np.float32), 1e-2, {}, cpt.ERR_ARG),      # no slice
+        (good, -1e-3, {}, cpt.ERR_ARG),                                     # negative bound
+        (good, float("inf"), {}, cpt.ERR_ARG),
+        (good, float("nan"), {}, cpt.ERR_ARG),
+        (nan, 1e-2, {}, cpt.ERR_ARG),                                       # non-finite data
+        (inf, 1e-2, {"pred": "sl"}, cpt.ERR_ARG),
+        (good, 1e-2, {"block": 40}, cpt.ERR_ARG),                          # block side
+        (good, 1e-2, {"pred": "mop", "block": 6}, cpt.ERR_UNSUPPORTED),   # MoP blocks must tile 32
+        (good, 1e-2, {"pred": "learned"}, cpt.ERR_ARG),                    # no model
+    ]
+    for uv, eb, kw, want in cases:
+        with pytest.raises(cpt.CptError) as e:
+            cpt.compress(_dev(uv), eb, **kw)
+        assert e.value.status == want, (uv.shape, eb, kw)
+    compare(good, 1e-2, "mop")
+
+
 def test_zero_and_constant_fields():
     compare(np.zeros((3, 6, 7, 2), np.float32), 1e-2, "mop")
     c = np.ones((3, 6, 7, 2), np.float32) * 0.25
