@@ -327,6 +327,23 @@ cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns);
  * vertex < 0 clears a pending injection.  Always CPT_OK. */
 cpt_status cpt_inject_verify_fault(int64_t vertex, int32_t delta);
 
+/* Inspection of the encoder pipeline's schedule (host only, no device work):
+ * the order in which the wave items of one launch over nfields fields take
+ * their tickets.  A wave item (f, t, s) encodes rows 32s..32s+31 of slice t of
+ * field f (Alg. 3's raster loop, one strip); it waits only for items with
+ * smaller tickets: the strip above, the strips of slice t-1 under its faces
+ * and its Lorenzo stencil, and those that complete the footprint of the
+ * prediction units it reads (rows up to 32s + 31 + R of slice t-1).
+ *   fields   : [nfields][4] int32: T, H, R (the units' reach, 0 without
+ *              units), with_units (0 / 1)
+ *   schedule : cpt_params.schedule or NULL (defaults)
+ *   items    : [n_items][3] int32 (field, t, s) in ticket order, or NULL to
+ *              query n_items only
+ * Errors: CPT_ERR_ARG (null fields or n_items, T or H < 1, R < 0, 2^31 items
+ * or more). */
+cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int32_t* schedule, int32_t* items,
+                              uint64_t* n_items);
+
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);

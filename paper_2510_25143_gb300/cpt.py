@@ -109,6 +109,8 @@ def lib():
             L.cpt_net_gradients.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
             L.cpt_train_predictor.restype = C.c_int
             L.cpt_train_predictor.argtypes = [vp, vp, i32, i32, i32, i32, C.c_float, C.c_uint32, vp, vp, vp, vp]
+            L.cpt_pipeline_order.restype = C.c_int
+            L.cpt_pipeline_order.argtypes = [i32, vp, vp, vp, P(C.c_uint64)]
             _lib = L
     return _lib
 
@@ -322,6 +324,24 @@ def inject_wave_stall(ticket, timeout_s=0.2):
     the wave item with this ticket and limits every wait to timeout_s, so it
     returns ERR_TIMEOUT.  ticket=None clears a pending injection."""
     _check(lib().cpt_inject_wave_stall(-1 if ticket is None else int(ticket), int(timeout_s * 1e9)))
+
+
+def pipeline_order(fields, schedule=None):
+    """Ticket order of the encoder pipeline's wave items for fields given as
+    (T, H, R, with_units) tuples (host only): int32 [n_items][3] rows
+    (field, t, strip)."""
+    f = np.ascontiguousarray(np.asarray(fields, np.int32).reshape(-1, 4))
+    sch = None
+    if schedule is not None:
+        sch = np.zeros(6, np.int32)
+        sch[:len(schedule)] = schedule
+    n = C.c_uint64(0)
+    L = lib()
+    _check(L.cpt_pipeline_order(len(f), f.ctypes.data, None if sch is None else sch.ctypes.data, None, C.byref(n)))
+    out = np.empty((n.value, 3), np.int32)
+    _check(L.cpt_pipeline_order(len(f), f.ctypes.data, None if sch is None else sch.ctypes.data,
+                                out.ctypes.data, C.byref(n)))
+    return out
 
 
 def inject_verify_fault(vertex, delta):

@@ -391,21 +391,33 @@ static void pipeline_keys(int T, int nstrips, int R, unsigned n_units, const Pip
         for (int sx = 0; sx < nstrips; ++sx) key[(size_t)t * nstrips + sx] = kOrderStrip * sx + Kt * t;
 }
 
-// One field's items (field index f) in ticket order.
-static void pipeline_order(int T, int nstrips, int R, unsigned n_units, const PipeTuning& tune, int f,
-                           std::vector<int4>& order) {
+// The wave items of one pipeline launch in ticket order: each field's items
+// by its own key, merged by key (then field, then t), so every field keeps
+// its own relative order.  Item x is (field, t, strip, 0).
+struct OrderField {
+    int T, nstrips, R;
+    unsigned n_units;
+};
+static void merged_order(const std::vector<OrderField>& fs, const PipeTuning& tune, std::vector<int4>& order) {
+    struct Item { long long key; int f, t, sx; };
+    std::vector<Item> items;
+    size_t total = 0;
+    for (const OrderField& g : fs) total += (size_t)g.T * g.nstrips;
+    items.reserve(total);
     std::vector<long long> key;
-    pipeline_keys(T, nstrips, R, n_units, tune, key);
-    std::vector<int2> ts;
-    ts.reserve(key.size());
-    for (int t = 0; t < T; ++t)
-        for (int sx = 0; sx < nstrips; ++sx) ts.push_back(make_int2(t, sx));
-    std::stable_sort(ts.begin(), ts.end(), [&](int2 p, int2 q) {
-        const long long kp = key[(size_t)p.x * nstrips + p.y], kq = key[(size_t)q.x * nstrips + q.y];
-        return kp != kq ? kp < kq : p.x < q.x;
+    for (int f = 0; f < (int)fs.size(); ++f) {
+        const OrderField& g = fs[f];
+        pipeline_keys(g.T, g.nstrips, g.R, g.n_units, tune, key);
+        for (int t = 0; t < g.T; ++t)
+            for (int sx = 0; sx < g.nstrips; ++sx) items.push_back({key[(size_t)t * g.nstrips + sx], f, t, sx});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& p, const Item& q) {
+        if (p.key != q.key) return p.key < q.key;
+        if (p.f != q.f) return p.f < q.f;
+        return p.t < q.t;
     });
-    order.resize(ts.size());
-    for (size_t x = 0; x < ts.size(); ++x) order[x] = make_int4(f, ts[x].x, ts[x].y, 0);
+    order.resize(items.size());
+    for (size_t x = 0; x < items.size(); ++x) order[x] = make_int4(items[x].f, items[x].t, items[x].sx, 0);
 }
 
 // The decoder's schedule (its prediction units carry no MoP decisions and its
@@ -655,10 +667,6 @@ struct FieldJob {
             A.n_units = (unsigned)nu;
         }
         return CPT_OK;
-    }
-
-    void ticket_keys(const PipeTuning& tune, std::vector<long long>& key) const {
-        pipeline_keys(T, nstrips, a.R, a.n_units, tune, key);
     }
 
     // Resets what the encoder pipeline reads and writes back (before every launch).
@@ -1062,25 +1070,10 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
             jobs[f]->a.unit_base = qlen;
             qlen += jobs[f]->a.n_units;
         }
-        // ticket order: each field's items by its own key, merged by key
-        // (then field, then t); a field's relative order is kept
-        struct Item { long long key; int f, t, sx; };
-        std::vector<Item> items;
-        items.reserve(max_items);
-        std::vector<long long> key;
-        for (int f = 0; f < n; ++f) {
-            jobs[f]->ticket_keys(tu, key);
-            const int ns = jobs[f]->nstrips;
-            for (int t = 0; t < jobs[f]->T; ++t)
-                for (int sx = 0; sx < ns; ++sx) items.push_back({key[(size_t)t * ns + sx], f, t, sx});
-        }
-        std::stable_sort(items.begin(), items.end(), [](const Item& p, const Item& q) {
-            if (p.key != q.key) return p.key < q.key;
-            if (p.f != q.f) return p.f < q.f;
-            return p.t < q.t;
-        });
-        order.resize(items.size());
-        for (size_t x = 0; x < items.size(); ++x) order[x] = make_int4(items[x].f, items[x].t, items[x].sx, 0);
+        // ticket order of the launch
+        std::vector<OrderField> ofs((size_t)n);
+        for (int f = 0; f < n; ++f) ofs[f] = {jobs[f]->T, jobs[f]->nstrips, jobs[f]->a.R, jobs[f]->a.n_units};
+        merged_order(ofs, tu, order);
         for (int f = 0; f < n; ++f) {
             SliceArgs& A = jobs[f]->a;
             A.qslot = d_queue + 2;
@@ -1672,7 +1665,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     A.timeout_ns = 2000000000ll;
     const PipeTuning tune = kDecodeSchedule;
     std::vector<int4> order;
-    pipeline_order(T, nstrips, A.R, A.n_units, tune, 0, order);
+    merged_order({OrderField{T, nstrips, A.R, A.n_units}}, tune, order);
     int4* d_order;
     CPT_CUDA(ar.alloc(&d_order, order.size()));
     CPT_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int4) * order.size(), cudaMemcpyHostToDevice, s));
@@ -2061,6 +2054,33 @@ cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns) {
         return cpt::fail(CPT_ERR_ARG, "ticket must fit 32 bits and the limit lie in [1 ms, 10 s]");
     cpt::t_stall.ticket = ticket < 0 ? -1 : ticket;
     cpt::t_stall.timeout_ns = timeout_ns;
+    return CPT_OK;
+}
+
+cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int32_t* schedule, int32_t* items,
+                              uint64_t* n_items) {
+    if (nfields < 1 || !fields || !n_items) return cpt::fail(CPT_ERR_ARG, "null argument or no field");
+    std::vector<cpt::OrderField> fs((size_t)nfields);
+    unsigned long long total = 0;
+    for (int f = 0; f < nfields; ++f) {
+        const int32_t* g = fields + 4 * (size_t)f;
+        if (g[0] < 1 || g[1] < 1 || g[2] < 0) return cpt::fail(CPT_ERR_ARG, "need T, H >= 1 and R >= 0");
+        fs[f] = {g[0], (g[1] + 31) / 32, g[2], g[3] ? 1u : 0u};
+        total += (unsigned long long)fs[f].T * fs[f].nstrips;
+    }
+    if (total >= 0x7FFFFFFFull) return cpt::fail(CPT_ERR_ARG, "too many wave items");
+    *n_items = total;
+    if (!items) return CPT_OK;
+    const cpt::PipeTuning tune = schedule ? cpt::PipeTuning{schedule[0], schedule[1], schedule[2], schedule[3],
+                                                            schedule[4]}
+                                          : cpt::PipeTuning{};
+    std::vector<int4> order;
+    cpt::merged_order(fs, tune, order);
+    for (size_t x = 0; x < order.size(); ++x) {
+        items[3 * x] = order[x].x;
+        items[3 * x + 1] = order[x].y;
+        items[3 * x + 2] = order[x].z;
+    }
     return CPT_OK;
 }
 
