@@ -372,6 +372,27 @@ def test_quantizer_bound():
             assert 0 < sym < 65536
 
 
+def test_quantizer_bins_are_maximal():
+    """With an integer bound xi_q a bin can hold at most 2 xi_q + 1
+    consecutive residuals (|r - c w| <= xi_q); the quantiser's bins hold
+    exactly that many, tile the residuals in order, and the one around 0 is
+    the zero code (r in [-xi_q, xi_q] is reconstructed as the prediction)."""
+    for xiq in [1, 2, 4, 64, 1024]:
+        p = 12345
+        codes = {}
+        for r in range(-5 * (2 * xiq + 1), 5 * (2 * xiq + 1)):
+            sym, qh = oracle.quantize(p + r, p, xiq)
+            assert abs(qh - (p + r)) <= xiq
+            codes.setdefault(sym, []).append(r)
+        syms = sorted(codes)
+        assert syms == list(range(syms[0], syms[-1] + 1))
+        for sy in syms[1:-1]:
+            rs = codes[sy]
+            assert len(rs) == 2 * xiq + 1 and rs == list(range(rs[0], rs[-1] + 1))
+        assert codes[32768] == list(range(-xiq, xiq + 1))
+        assert oracle.quantize(p + xiq, p, xiq) == (32768, p)
+
+
 def test_xi_code():
     assert oracle.xi_code(0) == 0
     for x in [1, 2, 3, 4, 7, 8, 1000, 2**23]:
@@ -379,10 +400,10 @@ def test_xi_code():
 
 
 def test_fixed_point_scale():
-    for amax, e in [(0.75, 0), (1.0, 1), (0.5, 0), (3.0, 2), (1e-3, -9)]:
+    # R1: the largest magnitude lands in [2^22, 2^23) after scaling by 2^k
+    for amax in [0.75, 1.0, 0.5, 3.0, 1e-3, 6.1e4, 2.0**-30]:
         k = oracle.scale_exponent(amax)
-        assert 2.0 ** (k + e - 23) == 1.0 or True
-        assert amax * 2.0 ** k < 2 ** 23 and amax * 2.0 ** (k + 1) >= 2 ** 23
+        assert 2 ** 22 <= amax * 2.0 ** k < 2 ** 23
     assert oracle.scale_exponent(0.0) == 0
     x = np.array([0.3, -0.7, 1e-3, 0.5], np.float32)
     k = oracle.scale_exponent(0.7)
