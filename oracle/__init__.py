@@ -51,10 +51,12 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle library; CPT_ORACLE_LIB names another build of it (the
+    mutation tests load deliberately broken copies this way)."""
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            _lib = C.CDLL(os.environ.get("CPT_ORACLE_LIB") or build())
             _declare(_lib)
             assert _lib.o_stats_size() == C.sizeof(Stats)
     return _lib
