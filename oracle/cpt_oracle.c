@@ -1152,14 +1152,6 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
 /* ------------------------------------------------------------------------ */
 /* Trajectories (Sec. IV, Thm. 2; reading R13).                                */
 /* ------------------------------------------------------------------------ */
-static i64 uf_find(i64* par, i64 x) {
-    while (par[x] != x) {
-        par[x] = par[par[x]];
-        x = par[x];
-    }
-    return x;
-}
-
 static i64 lower_bound_u64(const u64* a, i64 n, u64 key) {
     i64 lo = 0, hi = n;
     while (lo < hi) {
@@ -1216,14 +1208,13 @@ int o_trajectories(const int32_t* q, int H, int W, int T, u64* n_traj_out, u64* 
     for (i64 v = 0; v < N; ++v)
         for (int b = 0; b < 12; ++b) nf += (mask[v] >> b) & 1u;
     u64* fid = (u64*)malloc(sizeof(u64) * (nf ? nf : 1));
-    i64* par = (i64*)malloc(sizeof(i64) * (nf ? nf : 1));
     i64* nb = (i64*)malloc(sizeof(i64) * 2 * (nf ? nf : 1));
-    if (!fid || !par || !nb) { free(mask); free(fid); free(par); free(nb); return O_ERR_OOM; }
+    if (!fid || !nb) { free(mask); free(fid); free(nb); return O_ERR_OOM; }
     i64 x = 0;
     for (i64 v = 0; v < N; ++v)
         for (int b = 0; b < 12; ++b)
             if ((mask[v] >> b) & 1u) fid[x++] = (u64)v * 12 + (u64)b;
-    for (i64 a = 0; a < nf; ++a) { par[a] = a; nb[2 * a] = nb[2 * a + 1] = -1; }
+    for (i64 a = 0; a < nf; ++a) nb[2 * a] = nb[2 * a + 1] = -1;
     u64 bad = 0;
     for (int t = 0; t + 1 < T; ++t)
         for (int i = 0; i + 1 < H; ++i)
@@ -1242,8 +1233,6 @@ int o_trajectories(const int32_t* q, int H, int W, int T, u64* n_traj_out, u64* 
                     i64 a = hit[0], c = hit[1];
                     if (nb[2 * a] < 0) nb[2 * a] = c; else nb[2 * a + 1] = c;
                     if (nb[2 * c] < 0) nb[2 * c] = a; else nb[2 * c + 1] = a;
-                    i64 ra = uf_find(par, a), rc = uf_find(par, c);
-                    if (ra != rc) { if (ra < rc) par[rc] = ra; else par[ra] = rc; }
                 }
     /* walk each component */
     uint8_t* seen = (uint8_t*)calloc(nf ? nf : 1, 1);
@@ -1251,7 +1240,7 @@ int o_trajectories(const int32_t* q, int H, int W, int T, u64* n_traj_out, u64* 
     u64* offs = (u64*)malloc(sizeof(u64) * (nf + 1));
     double* xyt = (double*)malloc(sizeof(double) * 3 * (nf ? nf : 1));
     if (!seen || !order || !offs || !xyt) {
-        free(mask); free(fid); free(par); free(nb); free(seen); free(order); free(offs); free(xyt);
+        free(mask); free(fid); free(nb); free(seen); free(order); free(offs); free(xyt);
         return O_ERR_OOM;
     }
     u64 ntraj = 0, pos = 0;
@@ -1320,7 +1309,7 @@ int o_trajectories(const int32_t* q, int H, int W, int T, u64* n_traj_out, u64* 
     if (faces_out) *faces_out = order; else free(order);
     if (offsets_out) *offsets_out = offs; else free(offs);
     if (xyt_out) *xyt_out = xyt; else free(xyt);
-    free(mask); free(fid); free(par); free(nb); free(seen);
+    free(mask); free(fid); free(nb); free(seen);
     return O_OK;
 }
 

@@ -7,6 +7,7 @@ and the pin tests run against it in a subprocess (CPT_ORACLE_LIB); some pin
 must fail.  The committed oracle is never modified."""
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 
@@ -61,6 +62,22 @@ MUTANTS = [
      "pen = (i64)(((u64)16 * n_fail << 32)", "pen = (i64)(((u64)8 * n_fail << 32)"),
     ("ilog2-mantissa", "Eq. 10 (entropy estimate)",
      "u64 y = ((u64)x << 31) >> e;", "u64 y = ((u64)x << 30) >> e;"),
+    ("eps-prime-rounding", "Alg. 3 (eps' of the fixed-point field)",
+     "double e = floor(ldexp(eps, k) - 0.5);", "double e = floor(ldexp(eps, k));"),
+    ("to-fixed-floor", "Alg. 3 (fixed point)",
+     "q[n] = (int32_t)rint(ldexp((double)uv[n], k));", "q[n] = (int32_t)floor(ldexp((double)uv[n], k));"),
+    ("face-valid-boundary", "Sec. III-C (mesh boundary)",
+     "if (tt >= T || ii >= H || jj >= W) return 0;", "if (tt >= T || ii >= H || jj > W) return 0;"),
+    ("alg4-third-vertex-skipped", "Alg. 4 (every incident face)",
+     "    i64 self = vid(H, W, t, i, j);\n    for (int type = 0; type < 12; ++type)\n        for (int k = 0; k < 3; ++k) {",
+     "    i64 self = vid(H, W, t, i, j);\n    for (int type = 0; type < 12; ++type)\n        for (int k = 0; k < 2; ++k) {"),
+    ("rk2-full-step-midpoint", "Eqs. 7-8 (midpoint)",
+     "double xh = clampd((double)j - 0.5 * du, (double)(W - 1));",
+     "double xh = clampd((double)j - 1.0 * du, (double)(W - 1));"),
+    ("trajectory-reverse-link-dropped", "Thm. 2 (faces joined through tets)",
+     "if (nb[2 * c] < 0) nb[2 * c] = a; else nb[2 * c + 1] = a;", "(void)0;"),
+    ("trajectory-walk-start", "Thm. 2 (paths from their ends)",
+     "if (pass == 0 && deg == 2) continue;", "if (pass == 0 && deg != 2) continue;"),
     ("huffman-lengths-to-heavy-leaves", "Sec. VII-E (Huffman stage)",
      "for (size_t x = 0; x < leaves; ++x) len[lv[x].sym]++;",
      "for (size_t x = 0; x < leaves; ++x) len[lv[n - 1 - x].sym]++;"),
@@ -88,7 +105,7 @@ def _run_pins(so):
 
 @pytest.mark.timeout(900)
 def test_every_mutant_fails_a_pin(tmp_path):
-    if not shutil_which("gcc"):
+    if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     libs = {name: _build(str(tmp_path), name, old, new) for name, _, old, new in MUTANTS}
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
@@ -99,13 +116,8 @@ def test_every_mutant_fails_a_pin(tmp_path):
 
 def test_unmutated_copy_passes(tmp_path):
     """Control: the same build route without a mutation passes every pin."""
-    if not shutil_which("gcc"):
+    if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     so = _build(str(tmp_path), "control", "int o_xi_code(i64 xi)", "int o_xi_code(i64 xi)")
     rc, out = _run_pins(so)
     assert rc == 0, out
-
-
-def shutil_which(x):
-    import shutil
-    return shutil.which(x)

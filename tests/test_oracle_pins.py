@@ -214,6 +214,92 @@ def test_linear_field_single_trajectory(saddle):
     assert F.shape == (12, 3, 3)
 
 
+def _face_triples(fids, H, W):
+    F = oracle.face_table()
+    out = []
+    for fid in fids:
+        owner, ty = divmod(int(fid), 12)
+        t, rem = divmod(owner, H * W)
+        i, j = divmod(rem, W)
+        out.append(tuple(sorted(((t + F[ty][k][0]) * H + i + F[ty][k][1]) * W + j + F[ty][k][2]
+                                for k in range(3))))
+    return out
+
+
+@pytest.mark.parametrize("case", ["smooth_noise", "small_ints"])
+def test_trajectories_are_the_components_of_crossed_faces(case):
+    """R13 by brute force: the trajectories are the connected components of
+    the crossed faces, two faces joined when they bound one tetrahedron of the
+    prism split (the mesh rebuilt here from the paper), each listed as a path
+    whose consecutive faces share a tetrahedron."""
+    if case == "smooth_noise":  # many critical points: smoothed Gaussian noise
+        from scipy.ndimage import gaussian_filter
+        r = np.random.default_rng(31).normal(size=(5, 16, 18, 2))
+        uv = gaussian_filter(r, (0.8, 1.5, 1.5, 0)).astype(np.float32)
+    else:
+        uv = np.random.default_rng(32).integers(-2, 3, (4, 7, 8, 2)).astype(np.float32)
+    T, H, W, _ = uv.shape
+    k = oracle.scale_exponent(np.abs(uv).max())
+    q = oracle.to_fixed(uv, k)
+    trajs, _, bad = oracle.trajectories(q)
+    assert bad == 0
+    m = oracle.face_masks(q)
+    crossed = set()
+    for owner in np.flatnonzero(m.reshape(-1)):
+        for ty in range(12):
+            if (int(m.reshape(-1)[owner]) >> ty) & 1:
+                crossed.add(_face_triples([owner * 12 + ty], H, W)[0])
+    _, tets = _paper_mesh(H, W, T)
+    adj = {f: set() for f in crossed}
+    for tet in tets:
+        hit = [f for f in tet if f in crossed]
+        assert len(hit) in (0, 2)  # Lemma 1
+        if hit:
+            adj[hit[0]].add(hit[1])
+            adj[hit[1]].add(hit[0])
+    comps, seen = [], set()
+    for f in sorted(crossed):
+        if f in seen:
+            continue
+        stack, comp = [f], set()
+        while stack:
+            g = stack.pop()
+            if g in comp:
+                continue
+            comp.add(g)
+            stack += list(adj[g] - comp)
+        seen |= comp
+        comps.append(frozenset(comp))
+    assert len(comps) > 5
+    got = [_face_triples(tr, H, W) for tr in trajs]
+    assert sorted(map(frozenset, got), key=sorted) == sorted(comps, key=sorted)
+    for path in got:
+        assert len(set(path)) == len(path)
+        for a, b in zip(path, path[1:]):
+            assert b in adj[a]
+
+
+def test_eps_prime_is_the_largest_safe_integer_bound():
+    """R2: fixed-point rounding moves a value by at most 1/2 unit, so a
+    reconstruction within eps' units of q stays within eps of x when
+    eps' + 1/2 <= eps * 2^k; eps' is the largest such integer (0 when none is
+    positive, at most 2^23)."""
+    rng = np.random.default_rng(33)
+    for _ in range(4000):
+        k = int(rng.integers(-10, 40))
+        eps = float(rng.uniform(0, 3) * 2.0 ** (-k) * 10.0 ** rng.integers(-1, 3))
+        e = oracle.eps_int(eps, k)
+        S = Fraction(2) ** k
+        limit = Fraction(eps) * S
+        assert 0 <= e <= 2 ** 23
+        if 0 < e < 2 ** 23:
+            assert e + Fraction(1, 2) <= limit < e + Fraction(3, 2)
+        elif e == 0:
+            assert limit < Fraction(3, 2)
+        else:
+            assert limit >= 2 ** 23 + Fraction(1, 2)
+
+
 def test_centre_field():
     H, W, T = 20, 20, 5
     uv = synth.centre_field(H, W, T, 9.4, 10.7)
