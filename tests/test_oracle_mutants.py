@@ -15,7 +15,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cpt_oracle.c")
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rates.py"]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rates.py", "tests/test_oracle_learned.py"]
 
 # (name, the passage it breaks, original text, mutated text)
 MUTANTS = [
@@ -78,6 +78,16 @@ MUTANTS = [
      "if (nb[2 * c] < 0) nb[2 * c] = a; else nb[2 * c + 1] = a;", "(void)0;"),
     ("trajectory-walk-start", "Thm. 2 (paths from their ends)",
      "if (pass == 0 && deg == 2) continue;", "if (pass == 0 && deg != 2) continue;"),
+    ("net-relu-dropped", "learned predictor (ReLU after layers 1 and 2)",
+     "out[((i64)co * H + i) * W + j] = relu ? (acc > 0.0f ? acc : 0.0f) : acc;",
+     "out[((i64)co * H + i) * W + j] = acc;"),
+    ("net-kernel-transposed", "learned predictor (3 x 3 kernel taps)",
+     "acc = fmaf(bf16f(w[((co * cin + ci) * 3 + ky) * 3 + kx]), v, acc);",
+     "acc = fmaf(bf16f(w[((co * cin + ci) * 3 + kx) * 3 + ky]), v, acc);"),
+    ("net-clamp", "learned predictor (output clamp)",
+     "d = d < -2.0f ? -2.0f : (d > 2.0f ? 2.0f : d);", "d = d < -1.0f ? -1.0f : (d > 1.0f ? 1.0f : d);"),
+    ("net-parameter-layout", "learned predictor (parameter layout)",
+     "const uint16_t* w2 = b1 + NET_C;", "const uint16_t* w2 = b1 + NET_C - 1;"),
     ("huffman-lengths-to-heavy-leaves", "Sec. VII-E (Huffman stage)",
      "for (size_t x = 0; x < leaves; ++x) len[lv[x].sym]++;",
      "for (size_t x = 0; x < leaves; ++x) len[lv[n - 1 - x].sym]++;"),
