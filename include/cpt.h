@@ -344,6 +344,15 @@ cpt_status cpt_inject_verify_fault(int64_t vertex, int32_t delta);
 cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int32_t* schedule, int32_t* items,
                               uint64_t* n_items);
 
+/* The code lengths of the library's entropy stage (host only): an optimal
+ * prefix code with no code longer than maxlen for the symbol frequencies
+ * freq[nsym] (package-merge; symbols of frequency 0 get length 0, a single
+ * used symbol length 1).  The stream's canonical codes follow from these
+ * lengths (Sec. VII-E, the Huffman stage of the lossless back end).
+ * Errors: CPT_ERR_ARG (null arrays with nsym > 0, maxlen outside [1, 32], more
+ * used symbols than 2^maxlen). */
+cpt_status cpt_huffman_lengths(const uint64_t* freq, uint32_t nsym, int32_t maxlen, uint8_t* len);
+
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);

@@ -109,6 +109,8 @@ def lib():
             L.cpt_net_gradients.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
             L.cpt_train_predictor.restype = C.c_int
             L.cpt_train_predictor.argtypes = [vp, vp, i32, i32, i32, i32, C.c_float, C.c_uint32, vp, vp, vp, vp]
+            L.cpt_huffman_lengths.restype = C.c_int
+            L.cpt_huffman_lengths.argtypes = [vp, C.c_uint32, i32, vp]
             L.cpt_pipeline_order.restype = C.c_int
             L.cpt_pipeline_order.argtypes = [i32, vp, vp, vp, P(C.c_uint64)]
             _lib = L
@@ -324,6 +326,16 @@ def inject_wave_stall(ticket, timeout_s=0.2):
     the wave item with this ticket and limits every wait to timeout_s, so it
     returns ERR_TIMEOUT.  ticket=None clears a pending injection."""
     _check(lib().cpt_inject_wave_stall(-1 if ticket is None else int(ticket), int(timeout_s * 1e9)))
+
+
+def huffman_lengths(freq, maxlen=24):
+    """Code lengths of the library's entropy stage for symbol frequencies
+    (host only): uint8 array like freq."""
+    f = np.ascontiguousarray(freq, np.uint64)
+    out = np.zeros(f.size, np.uint8)
+    _check(lib().cpt_huffman_lengths(f.ctypes.data if f.size else None, f.size, int(maxlen),
+                                     out.ctypes.data if f.size else None))
+    return out
 
 
 def pipeline_order(fields, schedule=None):

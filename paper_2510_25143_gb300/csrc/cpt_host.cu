@@ -2057,6 +2057,16 @@ cpt_status cpt_inject_wave_stall(int64_t ticket, int64_t timeout_ns) {
     return CPT_OK;
 }
 
+cpt_status cpt_huffman_lengths(const uint64_t* freq, uint32_t nsym, int32_t maxlen, uint8_t* len) {
+    if ((!freq && nsym) || (!len && nsym) || maxlen < 1 || maxlen > 32)
+        return cpt::fail(CPT_ERR_ARG, "null argument or code length limit outside [1, 32]");
+    std::vector<uint64_t> f(freq, freq + nsym);
+    std::vector<uint8_t> l;
+    if (!cpt::huffman_lengths(f, maxlen, l)) return cpt::fail(CPT_ERR_ARG, "alphabet too large for the limit");
+    std::copy(l.begin(), l.end(), len);
+    return CPT_OK;
+}
+
 cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int32_t* schedule, int32_t* items,
                               uint64_t* n_items) {
     if (nfields < 1 || !fields || !n_items) return cpt::fail(CPT_ERR_ARG, "null argument or no field");
