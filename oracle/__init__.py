@@ -6,8 +6,8 @@ Preserved Critical Point Trajectories" (Alg. 1-4, Sec. VI).  Only the tests,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this module.  The CUDA library never links or calls it.
 
-Parity unpinned: the stream's byte layout, which the paper does not fix; it is
-pinned only through the round trip and the invariants.
+The stream's byte layout is not fixed by the paper (reading R12); the tests
+pin the writer to R12's description with a decoder written from it alone.
 """
 from __future__ import annotations
 

@@ -32,10 +32,10 @@
  *       net, bfloat16 weights, float32 fused multiply-add chains in a fixed
  *       order, prediction = qhat(t-1) + rint(clamp(y, -2, 2) * 2^23).
  *
- * Parity unpinned: the byte layout of the stream (R12) has no worked example
- * in the paper; the tests pin it only through the round trip, the invariants
- * (every face predicate kept, |x - x_hat| <= eps) and the optimality of the
- * Huffman code lengths.  Every other step has a pin of its own.
+ * The paper fixes no byte layout for the stream; R12 is this project's.  The
+ * tests pin the writer to R12's description with a decoder written from it
+ * alone, besides the round trip, the invariants and the optimality of the
+ * Huffman code lengths.  Every step has a pin of its own.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no -ffast-math, no FMA).
  */
