@@ -15,7 +15,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cpt_oracle.c")
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rates.py", "tests/test_oracle_learned.py"]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rates.py", "tests/test_oracle_learned.py",
+        "tests/test_stream_layout.py"]
 
 # (name, the passage it breaks, original text, mutated text)
 MUTANTS = [
@@ -88,6 +89,14 @@ MUTANTS = [
      "d = d < -2.0f ? -2.0f : (d > 2.0f ? 2.0f : d);", "d = d < -1.0f ? -1.0f : (d > 1.0f ? 1.0f : d);"),
     ("net-parameter-layout", "learned predictor (parameter layout)",
      "const uint16_t* w2 = b1 + NET_C;", "const uint16_t* w2 = b1 + NET_C - 1;"),
+    ("stream-bit-order", "reading R12 (codes most significant bit first)",
+     "if ((c >> k) & 1u) words[pos >> 5] |= 1u << (31 - (pos & 31));",
+     "if ((c >> k) & 1u) words[pos >> 5] |= 1u << (pos & 31);"),
+    ("stream-canonical-order", "reading R12 (canonical codes)",
+     "        if (len[s]) code[s] = next[len[s]]++;",
+     "        if (len[s]) code[s] = next[len[s]]++ ^ 1u;"),
+    ("stream-sync-offset", "reading R12 (sync points)",
+     "if (x % HUFF_CHUNK == 0) put_u64(b, nbits);", "if (x % HUFF_CHUNK == 0) put_u64(b, nbits + (x > 0));"),
     ("huffman-lengths-to-heavy-leaves", "Sec. VII-E (Huffman stage)",
      "for (size_t x = 0; x < leaves; ++x) len[lv[x].sym]++;",
      "for (size_t x = 0; x < leaves; ++x) len[lv[n - 1 - x].sym]++;"),
