@@ -225,7 +225,13 @@ cpt_status cpt_compress_ex(const float* uv, const cpt_dims* dims, const cpt_para
                            uint8_t** out, size_t* out_bytes, cpt_stats* stats,
                            const cpt_debug* dbg);
 
-/* Decompresses a stream produced by cpt_compress.
+/* Decompresses a stream produced by cpt_compress: the decompressor D of the
+ * problem statement (Sec. IV-A), whose output x_hat = D(C(x)) keeps every
+ * face predicate of the original (the face invariance of Eq. 4) and the
+ * pointwise error constraint |x_hat - x| <= eps of the same section.  It
+ * repeats Alg. 3's raster loop: each vertex gets the compressor's prediction
+ * (Sec. VI) from the values already reconstructed plus its dequantised
+ * residual, or its verbatim value.
  *   uv_out : caller-allocated float32 [T][H][W][2], host or device; NULL only
  *            fills dims_out (a cheap header query)
  *   qhat_out : nullable host int32 [T][H][W][2] copy of the fixed-point values

@@ -23,7 +23,16 @@
 //     caller;
 //   * the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     before capturing any stream into a CUDA graph.
+//     before capturing any stream into a CUDA graph.  The address is kept
+//     together with the CUDA context it belongs to: after cudaDeviceReset or
+//     any other teardown of the context, the module (and the array) may be
+//     loaded at another address, so a call in a new context looks it up
+//     again (once more, with the same advice about graph capture);
+//   * an error already pending on the calling thread (cudaPeekAtLastError)
+//     is not cleared: the call returns CPT_ERR_CUDA without launching, and
+//     the caller's own error check still sees it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "cpt.h"
@@ -136,25 +145,49 @@ __global__ void __launch_bounds__(256) noalloc_fixed_kernel(const float4* __rest
     }
 }
 
-// Device address of g_noalloc_partials, looked up once per device.
+// The current CUDA context, through the driver's cuCtxGetCurrent (found via
+// the runtime, so the library needs no link against libcuda).
+static bool current_context(CUcontext* ctx) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    static GetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetCurrent>(f);
+    }();
+    *ctx = nullptr;
+    return fn && fn(ctx) == CUDA_SUCCESS && *ctx;
+}
+
+// Device address of g_noalloc_partials, looked up once per device and
+// context (a context created after a reset may load the module elsewhere).
 static RangePartial* noalloc_scratch(int dev, cudaError_t* err) {
     static std::mutex mu;
     static RangePartial* addr[64] = {nullptr};
+    static CUcontext owner[64] = {nullptr};
     *err = cudaSuccess;
     if (dev < 0 || dev >= 64) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
+    // no context may be current yet before the runtime's first use of the
+    // device; the lookup below then creates the primary context
+    CUcontext ctx = nullptr;
+    current_context(&ctx);
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) {
-            *err = e;
-            return nullptr;
-        }
-        addr[dev] = static_cast<RangePartial*>(p);
+    if (ctx && addr[dev] && owner[dev] == ctx) return addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !current_context(&ctx)) {
+        *err = e != cudaSuccess ? e : cudaErrorDeviceUninitialized;
+        addr[dev] = nullptr;
+        owner[dev] = nullptr;
+        return nullptr;
     }
+    addr[dev] = static_cast<RangePartial*>(p);
+    owner[dev] = ctx;
     return addr[dev];
 }
 
@@ -163,26 +196,36 @@ static RangePartial* noalloc_scratch(int dev, cudaError_t* err) {
 extern "C" cpt_status cpt_fixed_point_noalloc(const float* uv, const cpt_dims* dims, int32_t* q, int32_t* scale_log2,
                                               void* cuda_stream) {
     using namespace cpt;
+    constexpr size_t kMaxValues = (size_t)kNoAllocMaxBlocks * kNoAllocPerBlock;  // 2^28 floats
     if (!uv || !dims || !q || !scale_log2) return CPT_ERR_ARG;
     if (dims->H < 1 || dims->W < 1 || dims->T < 1) return CPT_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(uv) | reinterpret_cast<uintptr_t>(q)) & 15u) return CPT_ERR_ARG;
-    const size_t nvals = 2 * (size_t)dims->H * dims->W * dims->T;
+    // 2*H*W*T without wrap-around: every factor and partial product is checked
+    // against the limit before the next multiplication
+    const size_t H = (size_t)dims->H, W = (size_t)dims->W, T = (size_t)dims->T;
+    if (H > kMaxValues || W > kMaxValues || T > kMaxValues) return CPT_ERR_ARG;
+    if (H * W > kMaxValues) return CPT_ERR_ARG;
+    if (H * W * T > kMaxValues / 2) return CPT_ERR_ARG;
+    const size_t nvals = 2 * H * W * T;
     const size_t nblocks = (nvals + kNoAllocPerBlock - 1) / kNoAllocPerBlock;
     if (nblocks > (size_t)kNoAllocMaxBlocks) return CPT_ERR_ARG;  // beyond the scratch array
+    // an error left pending by earlier work stays the caller's to see
+    if (cudaPeekAtLastError() != cudaSuccess) return CPT_ERR_CUDA;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return CPT_ERR_CUDA;
-    }
+    if (cudaGetDevice(&dev) != cudaSuccess) return CPT_ERR_CUDA;
     cudaError_t e;
     RangePartial* part = noalloc_scratch(dev, &e);
     if (!part) return CPT_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const size_t n4 = nvals / 4;            // whole float4 groups
     const int ntail = (int)(nvals - 4 * n4);  // 0 or 2 trailing values
+    // stop at the first launch that fails: a later kernel would read partials
+    // the failed one never wrote
     noalloc_range_kernel<<<(unsigned)nblocks, kNoAllocThreads, 0, s>>>(reinterpret_cast<const float4*>(uv), n4,
                                                                       uv + 4 * n4, ntail, part);
+    if (cudaGetLastError() != cudaSuccess) return CPT_ERR_CUDA;
     noalloc_scale_kernel<<<1, 256, 0, s>>>(part, (int)nblocks, scale_log2);
+    if (cudaGetLastError() != cudaSuccess) return CPT_ERR_CUDA;
     noalloc_fixed_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const float4*>(uv), n4, uv + 4 * n4, ntail, scale_log2,
                                               reinterpret_cast<int4*>(q), q + 4 * n4);
     if (cudaGetLastError() != cudaSuccess) return CPT_ERR_CUDA;
