@@ -137,6 +137,17 @@ def face_count(H, W, T):
     return lib().o_face_count(H, W, T)
 
 
+def value_range(uv):
+    """(min, max, max |x|) over u and v pooled, in double (Alg. 3's range
+    for the relative bound and the fixed-point scale)."""
+    uv = np.ascontiguousarray(uv, np.float32)
+    mn, mx, am = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().o_range(_p(uv, C.c_float), uv.size, C.byref(mn), C.byref(mx), C.byref(am))
+    if rc != 0:
+        raise ValueError("non-finite value in the field")
+    return mn.value, mx.value, am.value
+
+
 def scale_exponent(amax):
     return lib().o_scale_exponent(float(amax))
 

@@ -238,8 +238,43 @@ def vortex_sum_device(H, W, T, seed, n_vortex, drift, noise=1e-3, device="cuda")
     return out
 
 
+def _cache_path(name):
+    """File that holds a generated workload between processes: in the system's
+    temporary directory (never inside the repository), named after the
+    workload and a hash of this module's source, so that an edited generator
+    never reads a stale field.  CPT_SYNTH_CACHE=0 turns the cache off."""
+    import hashlib
+    import tempfile
+    if os.environ.get("CPT_SYNTH_CACHE", "1") == "0":
+        return None
+    with open(os.path.abspath(__file__), "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return os.path.join(tempfile.gettempdir(), f"cpt_synth_{name}_{h}.npy")
+
+
+def _cached(name, make):
+    path = _cache_path(name)
+    if path and os.path.exists(path):
+        try:
+            return np.load(path)
+        except Exception:
+            pass
+    uv = make()
+    if path:
+        tmp = f"{path[:-4]}.{os.getpid()}.tmp.npy"
+        try:
+            np.save(tmp, uv)
+            os.replace(tmp, path)
+        except Exception:
+            if os.path.exists(tmp):
+                os.unlink(tmp)
+    return uv
+
+
 def workload(name):
-    """Returns (uv, relative error bound) for a named workload."""
+    """Returns (uv, relative error bound) for a named workload.  The slow
+    spectral turbulence field is generated once per machine and kept in a
+    temporary file (see _cache_path)."""
     if name == "vortex64":
         return vortex_sum(64, 64, 8, seed=1000), 1e-2
     if name == "street512":
@@ -247,7 +282,7 @@ def workload(name):
     if name == "jets721":
         return zonal_jets(721, 1440, 48, seed=1002), 1e-3
     if name == "turb1024":
-        return turbulence(1024, 1024, 200, seed=1004), 1e-3
+        return _cached(name, lambda: turbulence(1024, 1024, 200, seed=1004)), 1e-3
     raise KeyError(name)
 
 

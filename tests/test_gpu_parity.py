@@ -146,44 +146,6 @@ def test_large_bound():
     compare(uv, 10.0, "lorenzo", eb_mode="abs")
 
 
-def _full_size(uv, eb, pred, t_end):
-    """A full-size workload in the benchmark's launch configuration (autotuned
-    schedule): fixed point and crossed-face masks everywhere, bounds, codes,
-    block modes and reconstructions of the first slices against the oracle
-    (which stops after them), the whole stream through the oracle's decoder
-    and the GPU's, and the invariants (Thm. 1/2, L-inf)."""
-    blob, st, g = cpt.compress(_dev(uv), eb, pred=pred, debug=True, tune=True)
-    r = oracle.compress(uv, eb, pred=pred, t_end=t_end)
-    assert (g["q"] == r["q"]).all()
-    assert (g["mask"] == r["mask"]).all()
-    for f in ("xi", "qxi"):
-        assert (g[f][:t_end] == r[f][:t_end]).all()
-    assert (g["qhat"][:t_end] == r["qhat"][:t_end]).all()
-    if pred == "mop":
-        assert (g["modes"][:t_end] == r["modes"][:t_end]).all()
-    qh, x, k = oracle.decompress(blob)
-    assert (qh == g["qhat"]).all()
-    _, gq, _ = cpt.decompress(blob, want_q=True)
-    assert (gq == qh).all()
-    assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
-    assert st["linf"] <= st["eps"]
-    assert np.abs(x.astype(np.float64) - uv.astype(np.float64)).max() <= st["eps"]
-
-
-def test_street512_full_size():
-    """512 x 512 x 100 vortex street, MoP at rel. 1e-3 (the benchmark)."""
-    uv, eb = synth.workload("street512")
-    _full_size(uv, eb, "mop", 3)
-
-
-@pytest.mark.parametrize("eb", [1e-3, 1e-4])
-def test_jets721_full_size(eb):
-    """721 x 1440 x 48 zonal jets and eddies at rel. 1e-3 and 1e-4, MoP."""
-    uv, _ = synth.workload("jets721")
-    _full_size(uv, eb, "mop", 2)
-
-
-
 def test_exact_zero_determinants():
     """Small-integer fields make exact zero determinants (M = 0 in Alg. 2) common
     on faces through reconstructed vertices; every such vertex must still be
