@@ -6,7 +6,11 @@ of the workload, no collective on the data path).
 A step is one cpt_compress call over the whole hot path on the workload:
 range + fixed point, crossed-face masks, MoP block selection with the
 semi-Lagrangian predictions, incident-face bounds, the wavefront encoder,
-entropy coding and full verification of every face predicate.
+entropy coding and full verification of every face predicate.  The default
+workload is 2-D decaying turbulence, 1024 x 1024 x 200, relative bound 1e-3,
+plain MoP; the same line carries the learned predictors on that workload,
+the other workloads (vortex street, zonal jets at two bounds, the small
+vortex sum) and the batched call.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,49 +37,74 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic bytes per vertex of each stage's kernels (the minimum traffic
-# the method needs; see the design notes): stage -> (bytes per vertex, units
-# per launch: "field" = H*W*T vertices, "slice" = H*W vertices).
+# the method needs), with the units one launch processes: "field" = H*W*T
+# vertices, "slice" = H*W vertices.
 STAGE_BYTES = {
     "range_fixed": (12.0, "field"),     # two launches: read 8 B; read 8 B + write 8 B
-    "face_masks": (10.0, "field"),      # read q 8 B, write mask 2 B
-    "mop_sl": (24.0, "slice"),          # read qhat(t-1) 8 B, q(t) 8 B, write SL prediction 8 B
-    # classification of the incident faces: read q(t-1), q(t), q(t+1) 8 B each and
-    # the masks of t and t-1 2 B each, write 8 B
-    "incident_bounds": (36.0, "field"),
-    # the encoder pipeline (prep units and the wavefront) over the whole
-    # field: read the classification 8 + 4 B, q(t) 8 B and qhat(t-1) 8 B,
-    # write qhat 8 B, bound code 1 B, symbols 4 B
-    "wavefront": (41.0, "field"),
-    "verify": (18.0, "field"),          # read qhat 8 B, mask 2 B, uv 8 B
+    "face_masks": (10.0, "field"),      # read q 8 B (each slice once), write the mask 2 B
+    "mop_sl": (24.0, "slice"),          # read qhat(t-1) 8 B, q(t) 8 B, write the SL prediction 8 B
+    # classification of the incident faces: read q 8 B and the masks 2 B (each
+    # slice once), write the classification 12 B and the strip-diagonal copy
+    # of q 8 B
+    "incident_bounds": (30.0, "field"),
+    # the encoder (bounds, predictions, quantisation with write-back): read q
+    # 8 B, the owners' masks 2 B and qhat(t-1) 8 B, write the bound code 1 B,
+    # the symbols 4 B and qhat 8 B
+    "wavefront": (31.0, "field"),
+    "verify": (18.0, "field"),          # read qhat 8 B, the mask 2 B and the input 8 B
+}
+KERNEL_NAMES = {"range_fixed": "range_kernel + to_fixed_kernel", "face_masks": "face_mask_kernel",
+                "incident_bounds": "classify_kernel", "wavefront": "encode_pipeline_kernel",
+                "verify": "verify_kernel", "mop_sl": "mop/SL prediction"}
+
+# ncu summaries: DRAM bytes of one launch of a kernel, valid while its
+# sources hash as they did when captured.  (stage, predictor) -> file
+PROFILES = {
+    ("wavefront", "mop"): "encode_pipeline_turb1024_mop.md",
+    ("face_masks", None): "face_mask_turb1024.md",
+    ("verify", None): "verify_turb1024.md",
+}
+KERNEL_SOURCES = {
+    "wavefront": ["k_encode.cu", "cpt_dev.cuh", "cpt_internal.h"],
+    "face_masks": ["k_field.cu", "cpt_dev.cuh", "cpt_internal.h"],
+    "verify": ["k_field.cu", "cpt_dev.cuh", "cpt_internal.h"],
 }
 
 
-# ncu summaries of the dominant kernel per predictor: DRAM bytes of one
-# launch, valid while the kernel sources hash as they did when captured
-PROFILES = {"mop": os.path.join(ROOT, "profiles", "encode_pipeline_street512_mop.md")}
-KERNEL_SOURCES = ["k_encode.cu", "cpt_dev.cuh", "cpt_internal.h"]
-
-
-def profiled_traffic(pred, workload):
-    """DRAM bytes per launch of the encoder pipeline from the committed ncu
-    summary, or None when there is none for this predictor and workload or the
-    kernel sources changed since it was taken."""
+def sources_sha(stage):
     import hashlib
-    path = PROFILES.get(pred)
-    if workload != "street512" or not path or not os.path.exists(path):
-        return None
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[stage]:
         with open(os.path.join(ROOT, "paper_2510_25143_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    sha, nbytes = None, None
+    return h.hexdigest()
+
+
+def profiled_traffic(stage, pred, workload, H, W, T):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    summary, scaled to this launch's vertices when the summary was taken on
+    fewer slices of the same workload; None when there is none or the kernel
+    sources changed since it was taken."""
+    name = PROFILES.get((stage, pred)) or PROFILES.get((stage, None))
+    if not name:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    meta = {}
     for line in open(path):
         line = line.strip()
-        if line.startswith("source-sha256:"):
-            sha = line.split(":", 1)[1].strip()
-        elif line.startswith("dram-bytes-per-launch:"):
-            nbytes = float(line.split(":", 1)[1])
-    return nbytes if sha == h.hexdigest() else None
+        if ":" in line and not line.startswith(("|", "#")):
+            key, val = line.split(":", 1)
+            meta[key.strip()] = val.strip()
+    try:
+        if meta.get("source-sha256") != sources_sha(stage) or meta.get("workload") != workload:
+            return None
+        nbytes = float(meta["dram-bytes-per-launch"])
+        verts = float(meta["vertices-per-launch"])
+    except (KeyError, ValueError):
+        return None
+    return nbytes * (H * W * T) / verts
 
 
 def peaks():
@@ -155,37 +184,79 @@ def combine_ranks(ms_local, world, nbytes_per_rank, device="cpu"):
     return ms, world * nbytes_per_rank / 1e6 / (ms / 1e3)
 
 
-def cpu_oracle_run(uv_sample, eb, pred, min_seconds):
-    """Times the oracle as it stands on uv_sample, repeating for >= min_seconds."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_run(uv_sample, eb_abs, pred, min_seconds):
+    """Times the oracle as it stands on uv_sample (absolute bound eb_abs, the
+    workload's bound), repeating for >= min_seconds on one host thread."""
     import oracle
     oracle.lib()
     reps, t0 = 0, time.perf_counter()
-    res = None
     while True:
-        res = oracle.compress(uv_sample, eb, pred=pred, debug=False)
+        oracle.compress(uv_sample, eb_abs, eb_mode="abs", pred=pred, debug=False)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
-    mbs = reps * uv_sample.nbytes / 1e6 / el
-    return mbs, el / reps, res
+    return reps * uv_sample.nbytes / 1e6 / el, el / reps, reps
+
+
+def cpu_parallel_stages(uv, threads):
+    """The oracle's two embarrassingly parallel stages on all host cores
+    (slab by slab, host threads; the oracle's own functions): the crossed-face
+    masks of the whole field and a verification of the same amount of work
+    (the fixed-point field checked against its own masks and values)."""
+    import oracle
+    oracle.lib_par()
+    _, _, amax = oracle.value_range(uv)
+    k = oracle.scale_exponent(amax)
+    q = oracle.to_fixed(uv, k)
+    t0 = time.perf_counter()
+    m = oracle.face_masks_par(q, threads)
+    t_mask = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    a, b, _ = oracle.verify_par(q, m, uv, k, threads)
+    t_ver = time.perf_counter() - t0
+    assert a == 0 and b == 0
+    return t_mask * 1e3, t_ver * 1e3
+
+
+def load_workload(args):
+    """(uv, relative bound) of the named workload, optionally cut to its
+    first --slices slices (for profiling a smaller case of the same field)."""
+    from paper_2510_25143_gb300 import synth
+    uv, eb = synth.workload(args.workload)
+    if args.slices:
+        uv = uv[: args.slices].copy()
+    return uv, eb
 
 
 def reference_arm(args):
+    """The oracle, as it stands, on one host thread: each step compresses a
+    bounded sample (the first --cpu-slices slices) of the workload with the
+    workload's own absolute bound (the whole field's relative bound)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2510_25143_gb300 import synth
-    uv, eb = synth.workload(args.workload)
-    sample = uv[: args.cpu_slices].copy()
     import oracle
+    uv, eb = load_workload(args)
+    vmin, vmax, _ = oracle.value_range(uv)
+    eps = eb * (vmax - vmin)
+    sample = uv[: args.cpu_slices].copy()
+    T_full = uv.shape[0]
+    del uv
     oracle.lib()
     for _ in range(args.warmup):
-        oracle.compress(sample, eb, pred=args.pred, debug=False)
+        oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False)
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = oracle.compress(sample, eb, pred=args.pred, debug=False)
+        last = oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False)
     el = time.perf_counter() - t0
     ms = el / args.steps * 1e3
     value = sample.nbytes / 1e6 / (ms / 1e3)
@@ -194,20 +265,39 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "H": H, "W": W, "T_sample": T, "rel_eb": eb, "pred": args.pred},
+        "config": {"workload": args.workload, "H": H, "W": W, "T": T_full, "T_sample": T, "rel_eb": eb,
+                   "pred": args.pred},
         "ratio": round(sample.nbytes / len(last["bytes"]), 4),
-        "cpu_baseline": {"value": round(value, 4), "unit": "MB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {T} of {uv.shape[0]} slices of {args.workload}, whole method per step"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MB/s", "cores": 1, "host_cores": host_cores(),
+                         "kind": "oracle",
+                         "sample": f"first {T} of {T_full} slices of {args.workload} with the whole field's "
+                                   f"bound, whole method per step, 1 of {host_cores()} host cores"},
         "e2e": {"value": round(value, 4), "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def stage_roofline(stage, stats, H, W, T, peak, peak_kind, pred, workload):
+    """Achieved algorithmic GB/s of one stage's kernel from the library's CUDA
+    events (mean over the timed calls), against the measured HBM peak."""
+    launches = stats[0]["launches"].get(stage, 0)
+    if not launches:
+        return None
+    ms = statistics.mean(s["ms_stage"][stage] for s in stats) / launches
+    per_vertex, unit = STAGE_BYTES[stage]
+    units = H * W * T if unit == "field" else H * W
+    achieved = per_vertex * units / (ms / 1e3) / 1e9
+    return {"kernel": KERNEL_NAMES[stage], "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic(stage, pred, workload, H, W, T) if stage in KERNEL_SOURCES else None,
+            "bytes_per_vertex": per_vertex, "units_per_launch": units, "launch_ms": round(ms, 5)}
 
 
 def ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2510_25143_gb300 import cpt, synth
+    from paper_2510_25143_gb300 import cpt
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,7 +305,7 @@ def ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    uv, eb = synth.workload(args.workload)
+    uv, eb = load_workload(args)
     T, H, W, _ = uv.shape
     nbytes = uv.nbytes
     d_uv = torch.from_numpy(uv).cuda()
@@ -235,18 +325,19 @@ def ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     stats = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
+        ev[0].record(stream)
+        for k in range(args.steps):
             blob, st = step(d_uv)
             stats.append(st)
-        e1.record(stream)
+            ev[k + 1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms, value = combine_ranks(e0.elapsed_time(e1) / args.steps, world, nbytes, device="cuda")
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms, value = combine_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, world, nbytes, device="cuda")
 
     # end to end through the public API with host buffers: the input is copied
     # from pinned host memory inside each call, the stream read back to host
@@ -262,6 +353,7 @@ def ours(args):
     ee1.record(stream)
     torch.cuda.synchronize()
     ms_e2e, e2e_value = combine_ranks(ee0.elapsed_time(ee1) / args.steps, world, nbytes, device="cuda")
+    del pinned
 
     # decompression through the C ABI into a device buffer (the stream is
     # parsed on the host, decoded and reconstructed on the GPU)
@@ -276,23 +368,18 @@ def ours(args):
     de1.record(stream)
     torch.cuda.synchronize()
     ms_dec = de0.elapsed_time(de1) / args.steps
-    exact = bool(torch.equal(d_out, torch.from_numpy(cpt.decompress(host_blob)[0]).cuda()))
     decompress = {"value": round(nbytes / 1e6 / (ms_dec / 1e3), 2), "unit": "MB/s (output bytes)",
                   "ms": round(ms_dec, 3), "input": "stream in host memory, output on the device",
-                  "deterministic": exact}
+                  "exact": bool(torch.equal(d_out.cpu(), torch.from_numpy(cpt.decompress(host_blob)[0])))}
     del d_out
 
     # per-stage device time from the library's CUDA events on its stream
     stage_ms = {k: statistics.mean(s["ms_stage"][k] for s in stats) for k in stats[0]["ms_stage"]}
-    stage_launch = {k: stats[0]["launches"][k] for k in stats[0]["launches"]}
     launches = sum(sum(s["launches"].values()) for s in stats)
     peak, peak_kind = peaks()
-    dom = max((k for k in STAGE_BYTES if stage_launch.get(k)), key=lambda k: stage_ms[k])
-    per_vertex, unit = STAGE_BYTES[dom]
-    units = H * W * T if unit == "field" else H * W
-    per_launch_ms = stage_ms[dom] / stage_launch[dom]
-    achieved = per_vertex * units / (per_launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic(args.pred, args.workload) if dom == "wavefront" else None
+    roof = {k: stage_roofline(k, stats, H, W, T, peak, peak_kind, args.pred, args.workload) for k in STAGE_BYTES}
+    roof = {k: v for k, v in roof.items() if v is not None}
+    dom = max(roof, key=lambda k: stage_ms[k])
     last = stats[-1]
     ok = (last["verify_mismatch_slice"] == 0 and last["verify_mismatch_slab"] == 0 and last["linf"] <= last["eps"])
     line = {
@@ -302,36 +389,104 @@ def ours(args):
         "config": {"workload": args.workload, "H": H, "W": W, "T": T, "rel_eb": eb, "pred": args.pred,
                    "input_bytes": nbytes, "l2": "input (%.0f MB) larger than L2 (129 MB), no flush" % (nbytes / 1e6),
                    "parallelism": f"replicas x{world}"},
+        "step_ms_median": round(statistics.median(per_step), 3),
         "ratio": round(last["ratio"], 4),
         "preserved": bool(ok), "fc_t": last["verify_mismatch_slice"], "fc_s": last["verify_mismatch_slab"],
         "linf": last["linf"], "eps": last["eps"], "psnr": round(last["psnr"], 3),
+        "faces": last["faces"],
         "faces_per_s": round(last["faces"] / (stage_ms["face_masks"] / 1e3), 1) if stage_ms["face_masks"] else None,
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic,
-                     "bytes_per_vertex": per_vertex, "units_per_launch": units,
-                     "launch_ms": round(per_launch_ms, 5)},
+        "roofline": roof[dom],
+        "kernel_rooflines": {k: v for k, v in roof.items() if k != dom},
         "e2e": {"value": round(e2e_value, 2), "unit": "MB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": len(e2e_blob)},
         "decompress": decompress,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    del blob, e2e_blob
     if rank == 0 and world == 1 and not args.no_cpu:
-        cmbs, per_run, res = cpu_oracle_run(uv[: args.cpu_slices].copy(), eb, args.pred, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": round(cmbs, 4), "unit": "MB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"first {args.cpu_slices} of {T} slices of {args.workload}, whole "
-                                          f"method, repeated for >= {args.cpu_seconds:.0f} s"}
+        import oracle
+        vmin, vmax, _ = oracle.value_range(uv)
+        sample = uv[: args.cpu_slices].copy()
+        cmbs, per_run, reps = cpu_oracle_run(sample, eb * (vmax - vmin), args.pred, args.cpu_seconds)
+        n = host_cores()
+        line["cpu_baseline"] = {
+            "value": round(cmbs, 4), "unit": "MB/s", "cores": 1, "host_cores": n, "kind": "oracle",
+            "sample": f"first {args.cpu_slices} of {T} slices of {args.workload} with the whole field's bound, "
+                      f"whole method, {reps} runs, 1 of {n} host cores"}
+        if not args.no_cpu_all:
+            ms_mask, ms_ver = cpu_parallel_stages(uv, n)
+            line["cpu_baseline"]["all_cores"] = {
+                "threads": n, "sample": f"whole {args.workload} field",
+                "face_masks_ms": round(ms_mask, 1), "verify_ms": round(ms_ver, 1),
+                "face_masks_MB/s": round(nbytes / 1e6 / (ms_mask / 1e3), 1),
+                "verify_MB/s": round(nbytes / 1e6 / (ms_ver / 1e3), 1),
+                "gpu_face_masks_ms": round(stage_ms["face_masks"], 4), "gpu_verify_ms": round(stage_ms["verify"], 4)}
+    del d_uv
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_learned and args.workload == "turb1024" and not args.slices:
+        line["learned_vs_plain"] = learned_vs_plain(args, uv, eb, line)
+    del uv
+    if rank == 0 and world == 1 and not args.no_workloads:
+        line["workloads"] = other_workloads(args)
     if rank == 0 and world == 1 and not args.no_batch:
         line["batch"] = batch_vs_single(args)
-    if rank == 0 and world == 1 and not args.no_learned:
-        same = args.workload == "street512" and args.pred == "mop"
-        line["learned_vs_plain"] = learned_vs_plain(args, blob if same else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def timed_compress(d_uv, eb, pred, reps, model=None, rates=False):
+    """The first call autotunes the pipeline's schedule (cached) and returns
+    the rate diagnostics if asked; then reps timed calls (CUDA events on the
+    current stream, device-resident input)."""
+    import torch
+    from paper_2510_25143_gb300 import cpt
+    _, st, g = cpt.compress(d_uv, eb, pred=pred, model=model, copy=False, tune=True, rates=rates)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    blob = None
+    for _ in range(reps):
+        blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=model, copy=False, tune=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = d_uv.numel() * 4
+    ok = st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
+    res = {"ratio": round(nbytes / len(blob), 4), "MB/s": round(nbytes / (ms / 1e3) / 1e6, 1), "ms": round(ms, 3),
+           "pipeline_ms": round(st["ms_stage"]["wavefront"], 3), "preserved": bool(ok),
+           "psnr": round(st["psnr"], 3)}
+    return res, blob, g
+
+
+def other_workloads(args, reps=5):
+    """The remaining workloads, each compressed on the GPU from device memory
+    with the autotuned schedule: the small vortex sum (64 x 64 x 8, rel. 1e-2,
+    every plain predictor), the vortex street (512 x 512 x 100, rel. 1e-3,
+    every plain predictor) and the zonal jets (721 x 1440 x 48, MoP at rel.
+    1e-3 and 1e-4)."""
+    import torch
+    from paper_2510_25143_gb300 import synth
+    out = {}
+    for name, ebs, preds in (("vortex64", (None,), ("lorenzo", "sl", "mop")),
+                             ("street512", (None,), ("lorenzo", "sl", "mop")),
+                             ("jets721", (1e-3, 1e-4), ("mop",))):
+        uv, eb0 = synth.workload(name)
+        d_uv = torch.from_numpy(uv).cuda()
+        T, H, W, _ = uv.shape
+        for eb in ebs:
+            eb = eb0 if eb is None else eb
+            key = name if len(ebs) == 1 else f"{name}_rel{eb:g}"
+            out[key] = {"H": H, "W": W, "T": T, "rel_eb": eb, "input_bytes": uv.nbytes}
+            for pred in preds:
+                out[key][pred], _, _ = timed_compress(d_uv, eb, pred, reps)
+        del d_uv
+        torch.cuda.empty_cache()
+    return out
 
 
 def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
@@ -363,7 +518,6 @@ def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
     # streams stay in the library's buffers (no Python copy is timed), and
     # the buffers of one repetition are reused by the next
     (_, _, b0), ms_first, _ = timed(lambda: cpt.compress_batch(fields, eb, pred=pred, tune=True, copy=False))
-    # each repetition's streams go back to the library before the next one
     best = None
     blobs = None
     for rep in range(reps):
@@ -381,11 +535,10 @@ def batch_vs_single(args, n_fields=64, eb=1e-3, pred="mop", reps=2):
         singles = None
         singles, ms, _ = timed(lambda: [cpt.compress(f, eb, pred=pred, copy=False)[0] for f in fields])
         ms_single = ms if ms_single is None else min(ms_single, ms)
-    blobs = batch_bytes
-    identical = all(bytes(x) == bytes(y) for x, y in zip(blobs, singles))
+    identical = all(x == bytes(y) for x, y in zip(batch_bytes, singles))
     ok = all(st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
              for st in stats)
-    out_bytes = sum(len(x) for x in blobs)
+    out_bytes = sum(len(x) for x in batch_bytes)
     sizes = [d["H"] * d["W"] * d["T"] for d in specs]
     return {"workload": f"batch{n_fields}", "fields": n_fields, "input_bytes": nbytes, "rel_eb": eb, "pred": pred,
             "data": "synthetic vortex-sum fields, sides 128..1024 (multiples of 16), 10..200 steps, drawn on the GPU",
@@ -421,13 +574,14 @@ def rate_summary(g):
             "lossless_vertex_share": round(float(g["qxi_hist"][0] / g["qxi_hist"].sum()), 4)}
 
 
-def learned_vs_plain(args, street_blob):
+def learned_vs_plain(args, uv, eb, line):
     """Compression ratio and MB/s of the plain and the learned predictors on
-    2-D decaying turbulence (1024 x 1024 x 200, rel. bound 1e-3).  The net
-    is trained on the GPU on decompressed slices of the vortex street and the
-    zonal-jet field (plain MoP), 256 x 256 crops; a second net is trained on
-    the first slices of the turbulence field itself (its own plain MoP
-    reconstruction).  Ratios count the model stored in the stream."""
+    2-D decaying turbulence (1024 x 1024 x 200, rel. bound 1e-3).  Net A is
+    trained on the GPU on decompressed slices of the vortex street and the
+    zonal jets (plain MoP; central 256 x 256 crops); net B on the turbulence
+    field's own first slices, whole 1024 x 1024 slices (its plain MoP
+    reconstruction of slices 0..8).  Ratios count the model stored in the
+    stream."""
     import numpy as np
     import torch
     from paper_2510_25143_gb300 import cpt, synth
@@ -440,68 +594,49 @@ def learned_vs_plain(args, street_blob):
         return prev, nxt
 
     t0 = time.time()
-    if street_blob is None:
-        street, seb = synth.workload("street512")
-        street_blob, _, _ = cpt.compress(torch.from_numpy(street).cuda(), seb, pred="mop")
-        del street
-    _, q_street, _ = cpt.decompress(bytes(street_blob), want_q=True)
+    street, seb = synth.workload("street512")
+    sblob, _, _ = cpt.compress(torch.from_numpy(street).cuda(), seb, pred="mop")
+    _, q_street, _ = cpt.decompress(sblob, want_q=True)
     jets, jeb = synth.workload("jets721")
     jblob, _, _ = cpt.compress(torch.from_numpy(jets).cuda(), jeb, pred="mop")
     _, q_jets, _ = cpt.decompress(jblob, want_q=True)
     p1, n1 = crops(q_street, range(10, 100, 10))
     p2, n2 = crops(q_jets, range(5, 48, 5))
     prev, nxt = np.concatenate([p1, p2]), np.concatenate([n1, n2])
-    del q_street, q_jets, jets
-    uv, eb = synth.workload("turb1024")
+    del q_street, q_jets, jets, street
     gen_s = time.time() - t0
     d_uv = torch.from_numpy(uv).cuda()
     stream = torch.cuda.current_stream()
 
-    def train(pv, nx):
+    def train(pv, nx, steps):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        model, losses = cpt.train_predictor(pv, nx, steps=args.train_steps, lr=1e-3, seed=1,
-                                            stream=stream.cuda_stream)
+        model, losses = cpt.train_predictor(pv, nx, steps=steps, lr=1e-3, seed=1, stream=stream.cuda_stream)
         e1.record(stream)
         torch.cuda.synchronize()
         return model, {"pairs": int(pv.shape[0]), "positions": int(pv.shape[0] * pv.shape[1] * pv.shape[2]),
-                       "steps": args.train_steps, "lr": 1e-3, "ms": round(e0.elapsed_time(e1), 1),
+                       "steps": steps, "lr": 1e-3, "ms": round(e0.elapsed_time(e1), 1),
                        "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
 
-    model, train_info = train(prev, nxt)
+    model, train_info = train(prev, nxt, args.train_steps)
     train_info["data"] = ("decompressed slices of street512 (t = 10..90 step 10) and jets721 (t = 5..45 "
                           "step 5), plain MoP, central 256 x 256 crops")
-
-    def run(pred, m=None, reps=3):
-        # the first call autotunes the pipeline's schedule (cached) and
-        # returns the rate diagnostics
-        blob, st, g = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True, rates=True)
-        rates = rate_summary(g)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            blob, st, _ = cpt.compress(d_uv, eb, pred=pred, model=m, copy=False, tune=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        ok = st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
-        return {"ratio": round(uv.nbytes / len(blob), 4), "MB/s": round(uv.nbytes / (ms / 1e3) / 1e6, 1),
-                "ms": round(ms, 2), "preserved": bool(ok), "psnr": round(st["psnr"], 3), "rates": rates}, blob
-
     res = {}
     for pred in ("lorenzo", "sl", "mop"):
-        res[pred], blob = run(pred)
+        res[pred], blob, g = timed_compress(d_uv, eb, pred, 3, rates=True)
+        res[pred]["rates"] = rate_summary(g)
         if pred == "mop":
             _, q_turb, _ = cpt.decompress(bytes(blob), want_q=True)
-    res["learned"], _ = run("learned", model)
-    res["learned_mop"], _ = run("learned_mop", model)
-    own_prev, own_next = crops(q_turb, range(1, 9), side=512)
-    own, own_info = train(own_prev, own_next)
-    own_info["data"] = "its own plain MoP reconstruction, slices 0..8, central 512 x 512 crops"
-    res["learned_own"], _ = run("learned", own)
-    res["learned_mop_own"], _ = run("learned_mop", own)
+    for name, pred in (("learned", "learned"), ("learned_mop", "learned_mop")):
+        res[name], _, g = timed_compress(d_uv, eb, pred, 3, model=model, rates=True)
+        res[name]["rates"] = rate_summary(g)
+    own, own_info = train(np.ascontiguousarray(q_turb[0:8]), np.ascontiguousarray(q_turb[1:9]), args.train_steps)
+    own_info["data"] = "its own plain MoP reconstruction, slices 0..8, whole 1024 x 1024 slices"
+    del q_turb
+    for name, pred in (("learned_own", "learned"), ("learned_mop_own", "learned_mop")):
+        res[name], _, g = timed_compress(d_uv, eb, pred, 3, model=own, rates=True)
+        res[name]["rates"] = rate_summary(g)
     best_plain = max(res[k]["ratio"] for k in ("lorenzo", "sl", "mop"))
     best_learned = max(res[k]["ratio"] for k in ("learned", "learned_mop", "learned_own", "learned_mop_own"))
     T, H, W, _ = uv.shape
@@ -518,12 +653,15 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="street512")
+    p.add_argument("--workload", default="turb1024", choices=["turb1024", "street512", "jets721", "vortex64"])
+    p.add_argument("--slices", type=int, default=0, help="cut the workload to its first N slices (profiling)")
     p.add_argument("--pred", default="mop", choices=["lorenzo", "sl", "mop"])
-    p.add_argument("--cpu-slices", type=int, default=4)
+    p.add_argument("--cpu-slices", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-cpu-all", action="store_true", help="skip the all-core timing of the oracle's stages")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
+    p.add_argument("--no-workloads", action="store_true", help="skip the other workloads")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-single comparison")
     p.add_argument("--train-steps", type=int, default=500)
     args = p.parse_args()

@@ -50,6 +50,64 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_PAR_SRC = os.path.join(_HERE, "cpt_oracle_par.c")
+_PAR_LIB_PATH = os.path.join(_BUILD, "liboracle_par.so")
+_lib_par = None
+
+
+def build_par(force: bool = False) -> str:
+    """Compiles the all-core harness of the oracle's parallel stages (the
+    oracle's source included unchanged, run on slabs by host threads)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_PAR_SRC))
+    if force or not os.path.exists(_PAR_LIB_PATH) or os.path.getmtime(_PAR_LIB_PATH) < newest:
+        tmp = _PAR_LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-pthread",
+                               "-fPIC", "-shared", "-I", _HERE, "-o", tmp, _PAR_SRC, "-lm"])
+        os.replace(tmp, _PAR_LIB_PATH)
+    return _PAR_LIB_PATH
+
+
+def lib_par():
+    global _lib_par
+    with _lock:
+        if _lib_par is None:
+            L = C.CDLL(build_par())
+            P = C.POINTER
+            L.o_face_masks_par.argtypes = [P(C.c_int32), C.c_int, C.c_int, C.c_int, P(C.c_uint16), C.c_int]
+            L.o_verify_par.argtypes = [P(C.c_int32), P(C.c_uint16), P(C.c_float), C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, P(C.c_uint64), P(C.c_uint64), P(C.c_double)]
+            _lib_par = L
+    return _lib_par
+
+
+def face_masks_par(q, nthreads):
+    """face_masks(q) computed slab by slab on nthreads host threads."""
+    q = np.ascontiguousarray(q, np.int32)
+    T, H, W, _ = q.shape
+    m = np.zeros((T, H, W), np.uint16)
+    rc = lib_par().o_face_masks_par(_p(q, C.c_int32), H, W, T, _p(m, C.c_uint16), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle face masks failed: {rc}")
+    return m
+
+
+def verify_par(qhat, mask, uv, k, nthreads):
+    """Verification of a reconstruction qhat (exponent k) against the
+    original's masks and values on nthreads host threads: (mismatching slice
+    faces, mismatching slab faces, max |x_hat - x|)."""
+    qhat = np.ascontiguousarray(qhat, np.int32)
+    mask = np.ascontiguousarray(mask, np.uint16)
+    uv = np.ascontiguousarray(uv, np.float32)
+    T, H, W, _ = qhat.shape
+    a, b, l = C.c_uint64(), C.c_uint64(), C.c_double()
+    rc = lib_par().o_verify_par(_p(qhat, C.c_int32), _p(mask, C.c_uint16), _p(uv, C.c_float), H, W, T, int(k),
+                                int(nthreads), C.byref(a), C.byref(b), C.byref(l))
+    if rc != 0:
+        raise RuntimeError(f"oracle verification failed: {rc}")
+    return a.value, b.value, l.value
+
+
 def lib():
     """The oracle library; CPT_ORACLE_LIB names another build of it (the
     mutation tests load deliberately broken copies this way)."""
