@@ -2,6 +2,7 @@
 // Convert_FixedPoint), conversion to fixed point, the crossed-face masks of
 // the space-time mesh (Alg. 3 face loop with Alg. 1) and the verification of
 // a reconstruction (Eq. 4 on every face plus the pointwise bound).
+#include <algorithm>
 #include <cmath>
 
 #include "cpt_dev.cuh"
@@ -69,151 +70,112 @@ __global__ void __launch_bounds__(256) to_fixed_kernel(const float4* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Face masks and verification.  A warp walks kFaceRows rows of one slice over
-// 32 columns: lane l reads column j0 + l and owns it for l < 31 (lane 31
-// supplies the right-hand corners).  Per row each lane loads its vertex at
-// (t, i+1) and (t+1, i+1); (t, i) and (t+1, i) are the previous row's.  The
-// right-hand corners come from lane l+1 by shuffle.  A face whose three
-// vertices share one strict sign of u or of v cannot contain the origin, also
-// after perturbation; only the remaining candidates (rare) take the exact SoS
-// test, with the corner values fetched by shuffle.
+// Face masks and verification (Eq. 2 under SoS on every face, Alg. 3's face
+// loop; Eq. 4 for the verification).  A warp walks kFaceRows rows of one
+// slice over 64 columns, two adjacent columns per lane (one 16-byte load per
+// lane and slice when W is even); lanes 0..30 own their columns, lane 31's
+// two columns are the next strip's first and only supply right-hand corners,
+// so strips advance by 62 columns.  Per row it loads row i + 1 of slices t
+// and t + 1 (prefetched one row ahead); rows i and i + 1 give the 2 x 2 x 2
+// corner cube of each owned vertex.
+//
+// Filter: a face whose three vertices share one strict sign of u or of v
+// cannot contain the origin, also after perturbation.  Each vertex value
+// becomes a sign word whose byte sign bits are u < 0, v < 0, u > 0, v > 0;
+// the AND of the eight corner words keeps the strict signs the whole cube
+// shares, which rules out every owned face at once.  The cube's AND is built
+// from column pairs (t and t + 1), row pairs and the right neighbour (one
+// shuffle per lane).  Only vertices whose cube shares no sign take the exact
+// test: the candidate faces (the AND of their three corner words has no sign
+// bit) go through the SoS predicate.  Absent corners (outside the field) use
+// a word with every sign bit set; faces through them are not valid.
 // ---------------------------------------------------------------------------
-constexpr int kFaceRows = 16;
+constexpr int kFaceRows = 32;
+constexpr int kStrip = 62;  // owned columns of a warp (lanes 0..30)
+constexpr unsigned kSignBits = 0x80808080u;
+constexpr unsigned kNoCorner = 0xffffffffu;
 
-struct FaceRowOut {
-    uint16_t m;     // owned-face mask of the lane's vertex
-    bool owner;     // the lane owns a vertex in this row
-};
+__device__ __forceinline__ unsigned sign_word(int u, int v) {
+    unsigned a, b;
+    // bytes (u.b3, v.b3, u.b3, v.b3) and the same of (-u, -v); |u|, |v| < 2^31
+    asm("prmt.b32 %0, %1, %2, 0x7373;" : "=r"(a) : "r"(u), "r"(v));
+    asm("prmt.b32 %0, %1, %2, 0x7373;" : "=r"(b) : "r"(-u), "r"(-v));
+    return (a & 0x0000ffffu) | (b & 0xffff0000u);
+}
 
-// Loader: (t, i, j) inside the field -> value; q reads the array, Tagged the
-// encoder's reconstruction words.
-struct PlainLoad {
-    const int2* q;
-    __device__ __forceinline__ int2 operator()(size_t v) const { return __ldg(q + v); }
-};
-struct TaggedLoad {
-    const int2* q;
-    __device__ __forceinline__ int2 operator()(size_t v) const {
-        int2 x = __ldg(q + v);
-        x.y ^= kQhatTag;
-        return x;
-    }
-};
-
-template <class Load, class Pre, class Visit>
-__device__ __forceinline__ void face_rows(const Load& ld, int H, int W, int T, int t, int ib, int j0, Pre pre,
-                                          Visit visit) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, j = j0 + lane;
-    const bool colok = j < W, nx = t + 1 < T;
-    const size_t sl = (size_t)H * W, base = (size_t)t * sl;
-    const int2 z = make_int2(0, 0);
-    // rows i (A), i + 1 (D) and i + 2 (Dn, loaded one row ahead)
-    auto load_row = [&](int r, int2& v, int2& vp) {
-        v = z;
-        vp = z;
-        if (colok && r < H) {
-            v = ld(base + (size_t)r * W + j);
-            if (nx) vp = ld(base + sl + (size_t)r * W + j);
-        }
-    };
-    int2 A, Ap, D, Dp;
-    load_row(ib, A, Ap);
-    load_row(ib + 1, D, Dp);
-    unsigned cA = sign_class(A.x, A.y), cAp = sign_class(Ap.x, Ap.y);
-    const int ie = min(H, ib + kFaceRows);
-    for (int i = ib; i < ie; ++i) {
-        int2 Dn, Dnp;
-        load_row(i + 2 < ib + kFaceRows + 1 ? i + 2 : H, Dn, Dnp);
-        const auto P = pre(i, j);
-        const unsigned cD = sign_class(D.x, D.y), cDp = sign_class(Dp.x, Dp.y);
-        const unsigned cR = __shfl_down_sync(FULL, cA, 1), cG = __shfl_down_sync(FULL, cD, 1);
-        const unsigned cRp = __shfl_down_sync(FULL, cAp, 1), cGp = __shfl_down_sync(FULL, cDp, 1);
-        const bool owner = lane < 31 && colok;
-        // a strict sign shared by all existing corners rules out every owned
-        // face at once (absent corners count as sharing every sign)
-        const bool r = j + 1 < W, d = i + 1 < H;
-        const unsigned all = cA & (r ? cR : 15u) & (d ? cD : 15u) & (r && d ? cG : 15u) &
-                             (nx ? cAp & (r ? cRp : 15u) & (d ? cDp : 15u) & (r && d ? cGp : 15u) : 15u);
-        unsigned m = 0;
-        if (__any_sync(FULL, owner && all == 0u)) {
-            // candidates: no strict sign shared by the three corners (corner 0 is A)
-            const unsigned cc[8] = {cA, cR, cD, cG, cAp, cRp, cDp, cGp};
-            unsigned cand = 0;
-#define CPT_C(ty, a, b, c) cand |= ((cc[a] & cc[b] & cc[c]) == 0u ? 1u : 0u) << (ty);
-            CPT_OWNED_FACES(CPT_C)
+// Owned-face mask of one vertex from its eight corners (index bit0 = +j,
+// bit1 = +i, bit2 = +t), their sign words and the valid face types.
+__device__ __forceinline__ unsigned exact_mask(const int2* c, const unsigned* w, unsigned valid) {
+    unsigned cand = 0;
+#define CPT_C(ty, a, b, cc) cand |= (((w[a] & w[b] & w[cc]) & kSignBits) == 0u ? 1u : 0u) << (ty);
+    CPT_OWNED_FACES(CPT_C)
 #undef CPT_C
-            cand = (owner && all == 0u) ? cand & owned_valid(H, W, T, t, i, j) : 0u;
-            int2 c[8];
-            c[0] = A; c[2] = D; c[4] = Ap; c[6] = Dp;
-            c[1].x = __shfl_down_sync(FULL, A.x, 1); c[1].y = __shfl_down_sync(FULL, A.y, 1);
-            c[3].x = __shfl_down_sync(FULL, D.x, 1); c[3].y = __shfl_down_sync(FULL, D.y, 1);
-            c[5].x = __shfl_down_sync(FULL, Ap.x, 1); c[5].y = __shfl_down_sync(FULL, Ap.y, 1);
-            c[7].x = __shfl_down_sync(FULL, Dp.x, 1); c[7].y = __shfl_down_sync(FULL, Dp.y, 1);
-            if (cand) {
-#define CPT_X(ty, a, b, cidx) \
-    if (((cand >> (ty)) & 1u) && face_crossed(c[a], c[b], c[cidx])) m |= 1u << (ty);
-                CPT_OWNED_FACES(CPT_X)
+    cand &= valid;
+    unsigned m = 0;
+    if (cand) {
+#define CPT_X(ty, a, b, cc) \
+    if (((cand >> (ty)) & 1u) && face_crossed(c[a], c[b], c[cc])) m |= 1u << (ty);
+        CPT_OWNED_FACES(CPT_X)
 #undef CPT_X
+    }
+    return m;
+}
+
+// One row of a lane's two columns c0, c0 + 1 at one slice.  kVec: W even,
+// so (row * W + c0) is even and the pair is one aligned 16-byte load.
+// kTag: the encoder's reconstruction words.
+struct RowVals {
+    int2 v0, v1;
+};
+
+template <bool kVec, bool kTag>
+__device__ __forceinline__ RowVals load_row(const int2* __restrict__ q, size_t row_base, int c0, int W, bool ok) {
+    RowVals r;
+    r.v0 = r.v1 = make_int2(0, 0);
+    if (ok) {
+        if (kVec) {
+            if (c0 < W) {
+                const int4 x = __ldg(reinterpret_cast<const int4*>(q + row_base + c0));
+                r.v0 = make_int2(x.x, x.y);
+                r.v1 = make_int2(x.z, x.w);
             }
+        } else {
+            if (c0 < W) r.v0 = __ldg(q + row_base + c0);
+            if (c0 + 1 < W) r.v1 = __ldg(q + row_base + c0 + 1);
         }
-        visit(i, j, FaceRowOut{(uint16_t)m, owner}, A, P);
-        A = D;
-        Ap = Dp;
-        D = Dn;
-        Dp = Dnp;
-        cA = cD;
-        cAp = cDp;
+        if (kTag) {
+            r.v0.y ^= kQhatTag;
+            r.v1.y ^= kQhatTag;
+        }
     }
+    return r;
 }
 
-// Work item -> (t, first row, first column); items run in slice order so that
-// slice t+1, read again as slice t, is still in L2.
-__device__ __forceinline__ bool face_item(int H, int W, int T, long long item, int& t, int& ib, int& j0) {
-    const int nj = (W + 30) / 31, ni = (H + kFaceRows - 1) / kFaceRows;
-    const long long per_t = (long long)ni * nj;
-    if (item >= per_t * T) return false;
-    t = (int)(item / per_t);
-    const long long r = item % per_t;
-    ib = (int)(r / nj) * kFaceRows;
-    j0 = (int)(r % nj) * 31;
-    return true;
+struct RowWords {
+    unsigned w0, w1;
+};
+__device__ __forceinline__ RowWords row_words(const RowVals& r, bool ok, bool ok0, bool ok1) {
+    RowWords w;
+    w.w0 = ok && ok0 ? sign_word(r.v0.x, r.v0.y) : kNoCorner;
+    w.w1 = ok && ok1 ? sign_word(r.v1.x, r.v1.y) : kNoCorner;
+    return w;
 }
 
-__global__ void __launch_bounds__(256) face_mask_kernel(const int2* __restrict__ q, int H, int W, int T,
-                                                        uint16_t* __restrict__ mask,
-                                                        unsigned long long* __restrict__ ncrossed) {
-    const long long item = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    unsigned cnt = 0;
-    int t, ib, j0;
-    if (face_item(H, W, T, item, t, ib, j0)) {
-        const size_t base = (size_t)t * H * W;
-        face_rows(PlainLoad{q}, H, W, T, t, ib, j0, [](int, int) { return 0; }, [&](int i, int j, FaceRowOut o, int2, int) {
-            if (o.owner) {
-                mask[base + (size_t)i * W + j] = o.m;
-                cnt += __popc(o.m);
-            }
-        });
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    __shared__ unsigned sc[8];
-    if ((threadIdx.x & 31) == 0) sc[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long tot = 0;
-        for (int w = 0; w < 8; ++w) tot += sc[w];
-        if (tot) atomicAdd(ncrossed, tot);
-    }
-}
+struct ErrMax {
+    float s, e;  // |s|, e * sign(s)
+};
+
+struct FaceAcc {
+    unsigned long long crossed;
+    unsigned ms, mb;
+    ErrMax em;
+    float sq;
+};
 
 // Exact |x_hat - x| for floats: s + e = x_hat - x exactly (TwoSum; no
 // contraction in this build).  Pairs compare by (|s|, e with the sign of s)
 // like the exact differences; the largest is rounded to double once, which
 // equals the largest of the differences rounded to double one by one.
-struct ErrMax {
-    float s, e;  // |s|, e * sign(s)
-};
 __device__ __forceinline__ ErrMax err_pair(float xh, float x) {
     const float s = __fsub_rn(xh, x);
     const float bb = __fsub_rn(s, xh);
@@ -224,60 +186,255 @@ __device__ __forceinline__ ErrMax err_max(ErrMax a, ErrMax b) {
     return (b.s > a.s || (b.s == a.s && b.e > a.e)) ? b : a;
 }
 
-__global__ void __launch_bounds__(256) verify_kernel(const int2* __restrict__ qhat, const uint16_t* __restrict__ mask,
-                                                     const float2* __restrict__ uv, int H, int W, int T,
-                                                     float g1, float g2, VerifyOut* __restrict__ out) {
-    const long long item = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    unsigned ms = 0, mb = 0;
-    ErrMax em{0.f, 0.f};
-    float sq = 0.f;
-    int t, ib, j0;
-    if (face_item(H, W, T, item, t, ib, j0)) {
-        const size_t base = (size_t)t * H * W;
-        // the original mask and values of the row, loaded before its faces are evaluated
-        struct Orig {
-            unsigned m;
-            float2 x;
-        };
-        auto pre = [&](int i, int j) {
-            Orig r{0u, make_float2(0.f, 0.f)};
-            if (j < W && (threadIdx.x & 31) < 31) {
-                const size_t v = base + (size_t)i * W + j;
-                r.m = mask[v];
-                r.x = __ldcs(uv + v);
-            }
-            return r;
-        };
-        face_rows(TaggedLoad{qhat}, H, W, T, t, ib, j0, pre, [&](int i, int j, FaceRowOut o, int2 A, Orig P) {
-            if (!o.owner) return;
-            const unsigned x = (unsigned)o.m ^ P.m;
-            ms += __popc(x & 3u);
-            mb += __popc(x & ~3u);
-            const float2 ov = P.x;
-            // x_hat = qhat * 2^-k, exact in FP32 (|qhat| < 2^24)
-            const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.x), g1), g2);
-            const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.y), g1), g2);
-            const ErrMax e0 = err_pair(a, ov.x), e1 = err_pair(b, ov.y);
-            em = err_max(em, err_max(e0, e1));
-            sq = __fadd_rn(sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
-        });
+// A corner value for the exact test (zero and an all-signs word outside the
+// field; faces through such corners are not valid).
+template <bool kTag>
+__device__ __forceinline__ int2 corner(const int2* __restrict__ q, int H, int W, int T, int t, int i, int j,
+                                       unsigned& w) {
+    if (t >= T || i >= H || j >= W) {
+        w = kNoCorner;
+        return make_int2(0, 0);
     }
+    int2 x = __ldg(q + ((size_t)t * H + i) * W + j);
+    if (kTag) x.y ^= kQhatTag;
+    w = sign_word(x.x, x.y);
+    return x;
+}
+
+// Verification: the original masks (two per word) and values of a lane's
+// owned vertices in one row.
+template <bool kVec>
+__device__ __forceinline__ void orig_row(const uint16_t* __restrict__ mask_in, const float2* __restrict__ uv,
+                                         size_t vrow, int c0, bool own0, bool own1, unsigned& om, float4& ox) {
+    om = 0;
+    ox = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kVec) {
+        if (own0) {
+            om = __ldg(reinterpret_cast<const unsigned*>(mask_in + vrow + c0));
+            ox = __ldcs(reinterpret_cast<const float4*>(uv + vrow + c0));
+        }
+    } else {
+        if (own0) {
+            om = __ldg(mask_in + vrow + c0);
+            const float2 a = __ldcs(uv + vrow + c0);
+            ox.x = a.x;
+            ox.y = a.y;
+        }
+        if (own1) {
+            om |= (unsigned)__ldg(mask_in + vrow + c0 + 1) << 16;
+            const float2 b = __ldcs(uv + vrow + c0 + 1);
+            ox.z = b.x;
+            ox.w = b.y;
+        }
+    }
+}
+
+// The warp's deferred vertices: the 2 x 2 x 2 cube shares no strict sign.
+// Entries (row - ib) << 6 | (column - j0); every owned vertex of an item fits.
+constexpr int kQueueCap = kFaceRows * kStrip;
+
+// One work item: rows [ib, ib + kFaceRows) of slice t, columns [j0, j0 + 62).
+// The rows are streamed with the sign filter only; vertices that pass it
+// are queued and get the exact test afterwards, one per lane, their corners
+// read again (from L2).
+template <bool kVerify, bool kVec>
+__device__ __forceinline__ void face_item_rows(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
+                                               int j0, uint16_t* __restrict__ mask_out,
+                                               const uint16_t* __restrict__ mask_in,
+                                               const float2* __restrict__ uv, float g1, float g2, FaceAcc& acc,
+                                               uint16_t* __restrict__ queue) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int c0 = j0 + 2 * lane, c1 = c0 + 1;
+    const bool in0 = c0 < W, in1 = c1 < W;             // columns inside the field
+    const bool own0 = in0 && lane < 31, own1 = in1 && lane < 31;
+    const bool nx = t + 1 < T;
+    const size_t sl = (size_t)H * W, base = (size_t)t * sl;
+    const int ie = min(H, ib + kFaceRows);
+    int nq = 0;
+    // rows i (A: slice t, P: slice t + 1) and i + 1 (D, Dp)
+    RowVals A = load_row<kVec, kVerify>(q, base + (size_t)ib * W, c0, W, true);
+    RowVals P = load_row<kVec, kVerify>(q, base + sl + (size_t)ib * W, c0, W, nx);
+    RowVals D = load_row<kVec, kVerify>(q, base + (size_t)(ib + 1) * W, c0, W, ib + 1 < H);
+    RowVals Dp = load_row<kVec, kVerify>(q, base + sl + (size_t)(ib + 1) * W, c0, W, nx && ib + 1 < H);
+    RowWords wa = row_words(A, true, in0, in1), wp = row_words(P, nx, in0, in1);
+    unsigned col0 = wa.w0 & wp.w0, col1 = wa.w1 & wp.w1;
+    unsigned omN = 0;
+    float4 oxN = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kVerify) orig_row<kVec>(mask_in, uv, base + (size_t)ib * W, c0, own0, own1, omN, oxN);
+    for (int i = ib; i < ie; ++i) {
+        const bool dn = i + 1 < H, nn = i + 2 < min(H, ib + kFaceRows + 1);
+        // prefetch row i + 2
+        RowVals N = load_row<kVec, kVerify>(q, base + (size_t)(i + 2) * W, c0, W, nn);
+        RowVals Np = load_row<kVec, kVerify>(q, base + sl + (size_t)(i + 2) * W, c0, W, nn && nx);
+        const size_t vrow = base + (size_t)i * W;
+        // verification: the original masks and values of row i (loaded one
+        // row ahead), and those of row i + 1 for the next iteration
+        const unsigned om = omN;
+        const float4 ox = oxN;
+        if (kVerify && dn && i + 1 < ie) orig_row<kVec>(mask_in, uv, vrow + W, c0, own0, own1, omN, oxN);
+        const RowWords wd = row_words(D, dn, in0, in1), wdp = row_words(Dp, dn && nx, in0, in1);
+        const unsigned dcol0 = wd.w0 & wdp.w0, dcol1 = wd.w1 & wdp.w1;
+        const unsigned vp0 = col0 & dcol0, vp1 = col1 & dcol1;
+        const unsigned right = __shfl_down_sync(FULL, vp0, 1);
+        const bool need0 = own0 && ((vp0 & vp1 & kSignBits) == 0u);
+        const bool need1 = own1 && ((vp1 & right & kSignBits) == 0u);
+        const unsigned b0 = __ballot_sync(FULL, need0), b1 = __ballot_sync(FULL, need1);
+        if (b0 | b1) {
+            int pos = nq + __popc(b0 & lt) + __popc(b1 & lt);
+            const uint16_t e = (uint16_t)(((i - ib) << 6) | (2 * lane));
+            if (need0) queue[pos++] = e;
+            if (need1) queue[pos] = (uint16_t)(e + 1);
+            nq += __popc(b0) + __popc(b1);
+        }
+        if (kVerify) {
+            // a queued vertex is counted after its exact test
+            const unsigned x = om & ~((need0 ? 0x0000ffffu : 0u) | (need1 ? 0xffff0000u : 0u));
+            acc.ms += __popc(x & 0x00030003u);
+            acc.mb += __popc(x & 0x0ffc0ffcu);
+            // x_hat = qhat * 2^-k, exact in FP32 (|qhat| < 2^24)
+            if (own0) {
+                const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.v0.x), g1), g2);
+                const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.v0.y), g1), g2);
+                const ErrMax e0 = err_pair(a, ox.x), e1 = err_pair(b, ox.y);
+                acc.em = err_max(acc.em, err_max(e0, e1));
+                acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
+            }
+            if (own1) {
+                const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.v1.x), g1), g2);
+                const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.v1.y), g1), g2);
+                const ErrMax e0 = err_pair(a, ox.z), e1 = err_pair(b, ox.w);
+                acc.em = err_max(acc.em, err_max(e0, e1));
+                acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
+            }
+        } else {
+            // every owned face of a vertex that passes no test is uncrossed
+            if (kVec) {
+                if (own0) *reinterpret_cast<unsigned*>(mask_out + vrow + c0) = 0u;
+            } else {
+                if (own0) mask_out[vrow + c0] = 0;
+                if (own1) mask_out[vrow + c1] = 0;
+            }
+        }
+        A = D;
+        P = Dp;
+        D = N;
+        Dp = Np;
+        wa = wd;
+        wp = wdp;
+        col0 = dcol0;
+        col1 = dcol1;
+    }
+    if (nq == 0) return;
+    __syncwarp();
+    // the exact test of the queued vertices, one per lane
+    for (int k = lane; k < nq; k += 32) {
+        const unsigned e = queue[k];
+        const int i = ib + (int)(e >> 6), j = j0 + (int)(e & 63u);
+        int2 c[8];
+        unsigned w[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) c[n] = corner<kVerify>(q, H, W, T, t + (n >> 2), i + ((n >> 1) & 1), j + (n & 1), w[n]);
+        const unsigned m = exact_mask(c, w, owned_valid(H, W, T, t, i, j));
+        const size_t v = base + (size_t)i * W + j;
+        if (kVerify) {
+            const unsigned x = m ^ (unsigned)mask_in[v];
+            acc.ms += __popc(x & 3u);
+            acc.mb += __popc(x & 0xffcu);
+        } else {
+            mask_out[v] = (uint16_t)m;
+            acc.crossed += __popc(m);
+        }
+    }
+    __syncwarp();
+}
+
+struct FaceGrid {
+    int nstrips, nchunks;
+    long long items;
+};
+__host__ __device__ inline FaceGrid face_grid(int H, int W, int T) {
+    FaceGrid g;
+    g.nstrips = (W + kStrip - 1) / kStrip;
+    g.nchunks = (H + kFaceRows - 1) / kFaceRows;
+    g.items = (long long)T * g.nchunks * g.nstrips;
+    return g;
+}
+
+// Work items run in slice order (then row chunk, then strip) over a grid of
+// warps, so that slice t + 1, read again as slice t, is still in L2.
+template <bool kVerify, bool kVec>
+__global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q, int H, int W, int T,
+                                                   uint16_t* __restrict__ mask_out,
+                                                   const uint16_t* __restrict__ mask_in,
+                                                   const float2* __restrict__ uv, float g1, float g2,
+                                                   unsigned long long* __restrict__ ncrossed,
+                                                   VerifyOut* __restrict__ vout) {
+    const FaceGrid g = face_grid(H, W, T);
+    const long long per_t = (long long)g.nchunks * g.nstrips;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    __shared__ uint16_t s_queue[8][kQueueCap];
+    FaceAcc acc{0ull, 0u, 0u, ErrMax{0.f, 0.f}, 0.f};
+    for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < g.items;
+         item += nwarps) {
+        const int t = (int)(item / per_t);
+        const long long r = item - (long long)t * per_t;
+        const int ib = (int)(r / g.nstrips) * kFaceRows;
+        const int j0 = (int)(r % g.nstrips) * kStrip;
+        face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
+                                      s_queue[threadIdx.x >> 5]);
+    }
+    // warp, then block reduction; one set of atomics per block
+    __shared__ unsigned long long s_c[8];
+    __shared__ unsigned s_ms[8], s_mb[8];
+    __shared__ float s_s[8], s_e[8], s_q[8];
+    const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        ms += __shfl_xor_sync(0xffffffffu, ms, o);
-        mb += __shfl_xor_sync(0xffffffffu, mb, o);
-        sq = __fadd_rn(sq, __shfl_xor_sync(0xffffffffu, sq, o));
-        ErrMax p{__shfl_xor_sync(0xffffffffu, em.s, o), __shfl_xor_sync(0xffffffffu, em.e, o)};
-        em = err_max(em, p);
+        if (kVerify) {
+            acc.ms += __shfl_xor_sync(0xffffffffu, acc.ms, o);
+            acc.mb += __shfl_xor_sync(0xffffffffu, acc.mb, o);
+            acc.sq = __fadd_rn(acc.sq, __shfl_xor_sync(0xffffffffu, acc.sq, o));
+            ErrMax p{__shfl_xor_sync(0xffffffffu, acc.em.s, o), __shfl_xor_sync(0xffffffffu, acc.em.e, o)};
+            acc.em = err_max(acc.em, p);
+        } else {
+            acc.crossed += __shfl_xor_sync(0xffffffffu, acc.crossed, o);
+        }
     }
     if ((threadIdx.x & 31) == 0) {
-        if (ms) atomicAdd(&out->mismatch_slice, (unsigned long long)ms);
-        if (mb) atomicAdd(&out->mismatch_slab, (unsigned long long)mb);
-        // the exact largest difference rounded once; >= 0, so its bit pattern
-        // orders like an unsigned integer
-        const double err = (double)em.s + (double)em.e;
-        if (err > 0.0) atomicMax(&out->linf_bits, (unsigned long long)__double_as_longlong(err));
-        if (sq > 0.f) atomicAdd(&out->sq_err, (double)sq);
+        s_c[w] = acc.crossed;
+        s_ms[w] = acc.ms;
+        s_mb[w] = acc.mb;
+        s_s[w] = acc.em.s;
+        s_e[w] = acc.em.e;
+        s_q[w] = acc.sq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        if (kVerify) {
+            unsigned long long ms = 0, mb = 0;
+            ErrMax em{0.f, 0.f};
+            double sq = 0.0;
+            for (int k = 0; k < nw; ++k) {
+                ms += s_ms[k];
+                mb += s_mb[k];
+                em = err_max(em, ErrMax{s_s[k], s_e[k]});
+                sq += (double)s_q[k];
+            }
+            if (ms) atomicAdd(&vout->mismatch_slice, ms);
+            if (mb) atomicAdd(&vout->mismatch_slab, mb);
+            // the exact largest difference rounded once; >= 0, so its bit
+            // pattern orders like an unsigned integer
+            const double err = (double)em.s + (double)em.e;
+            if (err > 0.0) atomicMax(&vout->linf_bits, (unsigned long long)__double_as_longlong(err));
+            if (sq > 0.0) atomicAdd(&vout->sq_err, sq);
+        } else {
+            unsigned long long c = 0;
+            for (int k = 0; k < nw; ++k) c += s_c[k];
+            if (c) atomicAdd(ncrossed, c);
+        }
     }
 }
 
@@ -298,22 +455,49 @@ void launch_to_fixed(const float* uv, size_t n, int k, int32_t* q, int nblocks, 
                                             reinterpret_cast<int4*>(q), q + 4 * n4);
 }
 
+// One wave of resident blocks (8 warps each) walks the work items; one set
+// of atomics per block.
+template <bool kVerify, bool kVec>
 static unsigned face_blocks(int H, int W, int T) {
-    const long long items = (long long)T * ((H + kFaceRows - 1) / kFaceRows) * ((W + 30) / 31);
-    return (unsigned)((items + 7) / 8);
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+            nsm = 152;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, face_kernel<kVerify, kVec>, 256, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        resident = nsm * per_sm;
+    }
+    const long long want = (face_grid(H, W, T).items + 7) / 8;
+    return (unsigned)std::max(1ll, std::min(want, (long long)resident));
 }
 
 void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, unsigned long long* ncrossed,
                        cudaStream_t s) {
-    face_mask_kernel<<<face_blocks(H, W, T), 256, 0, s>>>(reinterpret_cast<const int2*>(q), H, W, T, mask, ncrossed);
+    const int2* q2 = reinterpret_cast<const int2*>(q);
+    if (W % 2 == 0)
+        face_kernel<false, true><<<face_blocks<false, true>(H, W, T), 256, 0, s>>>(q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f,
+                                                                      ncrossed, nullptr);
+    else
+        face_kernel<false, false><<<face_blocks<false, false>(H, W, T), 256, 0, s>>>(q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f,
+                                                                       ncrossed, nullptr);
 }
 
 void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T, int k,
                    VerifyOut* out, cudaStream_t s) {
     const int a = -k / 2, b = -k - a;
-    verify_kernel<<<face_blocks(H, W, T), 256, 0, s>>>(reinterpret_cast<const int2*>(qhat), mask,
-                                                       reinterpret_cast<const float2*>(uv), H, W, T,
-                                                       std::ldexp(1.0f, a), std::ldexp(1.0f, b), out);
+    const int2* q2 = reinterpret_cast<const int2*>(qhat);
+    const float2* x2 = reinterpret_cast<const float2*>(uv);
+    const float g1 = std::ldexp(1.0f, a), g2 = std::ldexp(1.0f, b);
+    if (W % 2 == 0)
+        face_kernel<true, true><<<face_blocks<true, true>(H, W, T), 256, 0, s>>>(q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr,
+                                                                     out);
+    else
+        face_kernel<true, false><<<face_blocks<true, false>(H, W, T), 256, 0, s>>>(q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr,
+                                                                      out);
 }
 
 }  // namespace cpt
