@@ -106,6 +106,10 @@ typedef struct {
     const uint16_t* model;  /* host bfloat16 [CPT_NET_PARAMS]: the learned predictor (CPT_PRED_LEARNED) */
     int32_t tune;
     int32_t schedule[6];
+    int32_t zstd_level;     /* 0 = off; 1..ZSTD_maxCLevel(): the finished stream is wrapped in a
+                             * ZSTD frame on the host (the lossless stage after the Huffman coder,
+                             * Alg. 3 lossless_comp); see cpt_zstd_wrap.  The stream inside is
+                             * byte for byte the stream without the option. */
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's
@@ -132,6 +136,7 @@ typedef struct {
     double psnr;
     double ratio;             /* input bytes / output bytes */
     uint64_t out_bytes;
+    uint64_t raw_bytes;       /* bytes of the stream before the optional ZSTD frame */
 } cpt_stats;
 
 /* Optional host outputs of cpt_compress_ex (each pointer may be NULL).
@@ -360,6 +365,21 @@ cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int3
 cpt_status cpt_huffman_lengths(const uint64_t* freq, uint32_t nsym, int32_t maxlen, uint8_t* len);
 
 /* Releases a buffer returned by cpt_compress(_ex) or a cpt_trajs (deep). */
+/* Optional lossless back end (Alg. 3, lossless_comp: the general-purpose
+ * lossless stage after the Huffman coder; the paper uses ZSTD).  Host only,
+ * no GPU needed.  libzstd.so.1 is loaded at run time; without it both calls
+ * return CPT_ERR_UNSUPPORTED.
+ * cpt_zstd_wrap: in (any bytes, normally a stream of cpt_compress) becomes
+ *   the container "CPTZ", u32 version 1, u64 in_bytes, one ZSTD frame
+ *   (little-endian); level 1..ZSTD_maxCLevel(), else CPT_ERR_ARG.
+ * cpt_zstd_unwrap: the bytes inside such a container; CPT_ERR_CORRUPT when
+ *   in is not one or its frame does not decode to the stated size.
+ * *out is library-allocated (cpt_free).  cpt_decompress accepts containers
+ * directly.  Compression with cpt_params.zstd_level > 0 returns the
+ * container; cpt_stats.raw_bytes is then the size of the stream inside. */
+cpt_status cpt_zstd_wrap(const uint8_t* in, size_t in_bytes, int32_t level, uint8_t** out, size_t* out_bytes);
+cpt_status cpt_zstd_unwrap(const uint8_t* in, size_t in_bytes, uint8_t** out, size_t* out_bytes);
+
 void cpt_free(void* p);
 void cpt_free_trajs(cpt_trajs* t);
 

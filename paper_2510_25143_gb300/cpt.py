@@ -31,7 +31,8 @@ class Dims(C.Structure):
 class Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
                 ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 6)]
+                ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 6),
+                ("zstd_level", C.c_int32)]
 
 
 class BatchStats(C.Structure):
@@ -48,7 +49,7 @@ class Stats(C.Structure):
                 ("unpredictable", C.c_uint64), ("sl_blocks", C.c_uint64), ("blocks", C.c_uint64),
                 ("n_ld", C.c_uint64), ("n_qd", C.c_uint64), ("verify_mismatch_slice", C.c_uint64),
                 ("verify_mismatch_slab", C.c_uint64), ("linf", C.c_double), ("psnr", C.c_double),
-                ("ratio", C.c_double), ("out_bytes", C.c_uint64)]
+                ("ratio", C.c_double), ("out_bytes", C.c_uint64), ("raw_bytes", C.c_uint64)]
 
 
 class Debug(C.Structure):
@@ -91,6 +92,8 @@ def lib():
             L.cpt_extract_trajectories.restype = C.c_int
             L.cpt_extract_trajectories.argtypes = [C.c_void_p, P(Dims), C.c_int32, P(P(Trajs)), C.c_void_p]
             L.cpt_free.argtypes = [C.c_void_p]
+            L.cpt_zstd_wrap.argtypes = [C.c_void_p, C.c_size_t, C.c_int32, P(P(C.c_uint8)), P(C.c_size_t)]
+            L.cpt_zstd_unwrap.argtypes = [C.c_void_p, C.c_size_t, P(P(C.c_uint8)), P(C.c_size_t)]
             L.cpt_free_trajs.argtypes = [P(Trajs)]
             L.cpt_error_string.restype = C.c_char_p
             L.cpt_error_string.argtypes = [C.c_int]
@@ -174,20 +177,21 @@ class Stream:
             self._ptr = None
 
 
-def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule):
+def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd=0):
     sch = (C.c_int32 * 6)(*(tuple(schedule or ()) + (0,) * 6)[:6])
     return Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
-                  None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch)
+                  None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch, int(zstd))
 
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
              dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None, tune=False,
-             schedule=None, rates=False):
+             schedule=None, rates=False, zstd=0):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
     or device).  Returns (bytes, stats dict, debug dict or None); with
     copy=False the stream comes back as a Stream over the library's buffer.
     pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
-    bfloat16 bits.  tune=True lets the library pick the encoder pipeline's
+    bfloat16 bits.  zstd=L > 0 returns the stream wrapped in a ZSTD frame
+    (level L, host side).  tune=True lets the library pick the encoder pipeline's
     schedule; schedule=(prep_share, sl_unit, slice_weight, slack, warps_per_sm)
     fixes it (zeros: defaults).
     rates=True (or debug=True) returns the rate diagnostics in the debug
@@ -197,7 +201,7 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
         stream = dev_stream
     dims = Dims(H, W, T, dx, dy, dt)
     mdl = None if model is None else _model_array(model)
-    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule)
+    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd)
     out = C.POINTER(C.c_uint8)()
     n = C.c_size_t(0)
     st = Stats()
@@ -361,6 +365,26 @@ def inject_verify_fault(vertex, delta):
     delta to the u component of one reconstructed vertex before verifying.
     vertex=None clears a pending injection."""
     _check(lib().cpt_inject_verify_fault(-1 if vertex is None else int(vertex), int(delta)))
+
+
+def zstd_wrap(blob, level=3):
+    """The optional ZSTD container around a stream (host only): bytes."""
+    src = bytes(blob)
+    out, n = C.POINTER(C.c_uint8)(), C.c_size_t(0)
+    _check(lib().cpt_zstd_wrap(src, len(src), int(level), C.byref(out), C.byref(n)))
+    r = C.string_at(out, n.value)
+    lib().cpt_free(out)
+    return r
+
+
+def zstd_unwrap(blob):
+    """The stream inside a ZSTD container (host only): bytes."""
+    src = bytes(blob)
+    out, n = C.POINTER(C.c_uint8)(), C.c_size_t(0)
+    _check(lib().cpt_zstd_unwrap(src, len(src), C.byref(out), C.byref(n)))
+    r = C.string_at(out, n.value)
+    lib().cpt_free(out)
+    return r
 
 
 def fixed_point_noalloc(uv, q, k, stream=None):

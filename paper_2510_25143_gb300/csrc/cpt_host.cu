@@ -30,6 +30,12 @@ static cpt_status fail(cpt_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+cpt_status fail_status(cpt_status s, const char* msg) { return fail(s, msg); }
+
+// cpt_zstd.cu: the optional ZSTD container of a finished stream (host only)
+bool is_zstd_container(const uint8_t* in, size_t n);
+cpt_status zstd_wrap(const uint8_t* in, size_t n, int level, uint8_t** out, size_t* out_n);
+cpt_status zstd_unwrap(const uint8_t* in, size_t n, uint8_t** out, size_t* out_n);
 
 #define CPT_CUDA(call)                                                                                  \
     do {                                                                                                \
@@ -910,6 +916,7 @@ struct FieldJob {
         st.n_ld = n_ld;
         st.n_qd = n_qd;
         st.out_bytes = total;
+        st.raw_bytes = total;
         st.ratio = (double)(NV * 4) / (double)total;
         const VerifyOut& vo = *vo_h;
         st.verify_mismatch_slice = vo.mismatch_slice;
@@ -959,17 +966,19 @@ static std::vector<PipeTuning> tuning_candidates(int pred) {
         for (int w : {3, 0})
             for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, w});
     } else if (pred == CPT_PRED_SL) {
-        for (int share : {45, 50}) c.push_back({share, 8, 0, 0, 3});
+        // large slices are bound by the throughput of the prediction units:
+        // shares up to 75 % of the warps pay there; small ones by the lag
+        c.push_back({45, 8, 0, 0, 3});
         for (int u : {8, 16})
-            for (int share : {25, 35, 50}) c.push_back({share, u, 0, 0, 0});
+            for (int share : {35, 55, 65, 75}) c.push_back({share, u, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED) {
-        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 0, 0});
+        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED_MOP) {
-        for (int share : {45, 65, 80}) c.push_back({share, 0, 0, 64, 0});
+        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 64, 0});
     } else {
-        for (int share : {35, 45}) c.push_back({share, 0, 0, 64, 3});
-        for (int share : {25, 35, 45, 55})
-            for (int slack : {64, 128}) c.push_back({share, 0, 0, slack, 0});
+        c.push_back({45, 0, 0, 64, 3});
+        for (int share : {35, 55, 65, 70, 75, 80}) c.push_back({share, 0, 0, 64, 0});
+        c.push_back({75, 0, 0, 128, 0});
     }
     return c;
 }
@@ -1204,6 +1213,25 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
     return CPT_OK;
 }
 
+// The optional ZSTD container around a finished stream: replaces *out (the
+// stream goes back to the pool) and updates the statistics.
+static cpt_status wrap_output(const cpt_params* prm, uint8_t** out, size_t* out_bytes, cpt_stats* stats,
+                              size_t input_bytes) {
+    if (prm->zstd_level <= 0 || !*out) return CPT_OK;
+    uint8_t* z = nullptr;
+    size_t zn = 0;
+    const cpt_status rc = zstd_wrap(*out, *out_bytes, prm->zstd_level, &z, &zn);
+    if (rc != CPT_OK) return rc;
+    if (!pinned_pool().put(*out)) std::free(*out);
+    *out = z;
+    *out_bytes = zn;
+    if (stats) {
+        stats->out_bytes = zn;
+        stats->ratio = (double)input_bytes / (double)zn;
+    }
+    return CPT_OK;
+}
+
 static cpt_status check_device() {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1245,7 +1273,16 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     CPT_CUDA(cudaGetLastError());
     float ms_total = 0.f;
     cudaEventElapsedTime(&ms_total, ev0, ev1);
-    return job.finish(ms_total, pt.ms_pipeline, out, out_bytes, stats);
+    rc = job.finish(ms_total, pt.ms_pipeline, out, out_bytes, stats);
+    if (rc != CPT_OK && rc != CPT_ERR_VERIFY) return rc;
+    const cpt_status rz = wrap_output(prm, out, out_bytes, stats, job.NV * 4);
+    if (rz != CPT_OK) {
+        cpt_free(*out);
+        *out = nullptr;
+        *out_bytes = 0;
+        return rz;
+    }
+    return rc;
 }
 
 // Many fields, one set of parameters: fields are taken in order into groups
@@ -1330,6 +1367,8 @@ static cpt_status compress_batch_impl(const float* const* uv, const cpt_dims* di
             cpt_status r1 = j.finish(0.0, pt.ms_pipeline, &out[f], &out_bytes[f], &st1);
             if (r1 == CPT_ERR_VERIFY && verdict == CPT_OK) verdict = r1;
             else if (r1 != CPT_OK && r1 != CPT_ERR_VERIFY) { jobs.clear(); release_all(); return r1; }
+            const cpt_status rz = wrap_output(prm, &out[f], &out_bytes[f], &st1, 8ull * j.N);
+            if (rz != CPT_OK) { jobs.clear(); release_all(); return rz; }
             for (int x = 0; x < 8; ++x)
                 if (x != 4) b.launches += st1.launches[x];
             b.in_bytes += 8ull * j.N;
@@ -1497,6 +1536,19 @@ static cpt_status decode_huff_stream(const HuffHost& hh, Sym* d_out, int* d_stat
 static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_out, int32_t* qhat_out,
                                   cpt_dims* dims_out, void* cuda_stream) {
     if (!in) return fail(CPT_ERR_ARG, "null stream");
+    if (is_zstd_container(in, in_bytes)) {  // the optional ZSTD frame around a stream
+        uint8_t* raw = nullptr;
+        size_t rn = 0;
+        const cpt_status rz = zstd_unwrap(in, in_bytes, &raw, &rn);
+        if (rz != CPT_OK) return rz;
+        if (is_zstd_container(raw, rn)) {
+            std::free(raw);
+            return fail(CPT_ERR_CORRUPT, "nested zstd container");
+        }
+        const cpt_status rc = decompress_impl(raw, rn, uv_out, qhat_out, dims_out, cuda_stream);
+        std::free(raw);
+        return rc;
+    }
     Reader r{in, in_bytes};
     const uint8_t* magic = r.take(4);
     if (!magic || std::memcmp(magic, "CPT1", 4) != 0) return fail(CPT_ERR_CORRUPT, "not a cpt stream");

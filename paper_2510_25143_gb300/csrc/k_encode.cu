@@ -44,8 +44,8 @@
 namespace cpt {
 
 constexpr int kPublishEvery = 8;   // steps between checks for prep units made ready
-constexpr int kPrepShareSL = 50;   // percent of the warps working prep units (SL)
-constexpr int kPrepShareMoP = 45;  // (MoP)
+constexpr int kPrepShareSL = 65;   // percent of the warps working prep units (SL)
+constexpr int kPrepShareMoP = 65;  // (MoP and the learned predictors)
 constexpr int kNoSL = (int)0x80000000;  // psl marker: the block keeps 3DL (no prediction reaches it)
 
 __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, int j) {
