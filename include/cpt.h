@@ -93,8 +93,11 @@ typedef enum {
  *              or 16), [2] slice weight of the wave order without prediction
  *              units (3DL), [3] extra slice weight of the wave order with
  *              them, [4] worker warps per SM (0 = as many as shared memory
- *              and registers allow), [5] reserved (0).  The schedule orders and places work only: the
- *              stream does not depend on it.                                  */
+ *              and registers allow), [5] warp layout: 0 = whole CTAs per role
+ *              (every warp slot the larger role's size), 1 = prediction and
+ *              wave warps in every CTA, each slot of its own size.  The
+ *              schedule orders and places work only: the stream does not
+ *              depend on it.                                                  */
 typedef struct {
     cpt_eb_mode mode;
     double eb;
@@ -110,6 +113,13 @@ typedef struct {
                              * ZSTD frame on the host (the lossless stage after the Huffman coder,
                              * Alg. 3 lossless_comp); see cpt_zstd_wrap.  The stream inside is
                              * byte for byte the stream without the option. */
+    int32_t repair;         /* nonzero: when the verification finds a changed face predicate or a
+                             * value past the bound (which exact integer bounds rule out; only a
+                             * fault can cause it), the vertices of the changed faces and the
+                             * vertices past the bound are stored losslessly and the field is
+                             * encoded again, up to 3 rounds (reading R14 of the verification
+                             * policy the paper leaves open); the stream returned then verifies.
+                             * The slices before the earliest forced vertex encode as before. */
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's
@@ -137,6 +147,9 @@ typedef struct {
     double ratio;             /* input bytes / output bytes */
     uint64_t out_bytes;
     uint64_t raw_bytes;       /* bytes of the stream before the optional ZSTD frame */
+    uint64_t forced_vertices; /* vertices stored losslessly by the repair (cpt_params.repair) */
+    int32_t repair_rounds;    /* encodings repeated by the repair (0 = none needed) */
+    int32_t reserved0;
 } cpt_stats;
 
 /* Optional host outputs of cpt_compress_ex (each pointer may be NULL).

@@ -160,7 +160,7 @@ def _declare(L):
     L.o_compress2.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, dbl, dbl, dbl, C.c_int, dbl,
                               C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_uint16), P(P(C.c_uint8)),
                               P(C.c_size_t), P(i32), P(i32), P(i64), P(C.c_uint8), P(C.c_uint8),
-                              P(C.c_uint16), P(C.c_uint32), P(Stats)]
+                              P(C.c_uint16), P(C.c_uint32), P(Stats), P(C.c_uint8)]
     L.o_net_params.argtypes = []
     L.o_net_forward.argtypes = [P(C.c_uint16), P(i32), C.c_int, C.c_int, P(C.c_float)]
     L.o_net_predict.argtypes = [P(C.c_uint16), P(i32), C.c_int, C.c_int, P(i32)]
@@ -323,13 +323,15 @@ def net_predict(model, prev):
 
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.0, dy=1.0,
-             dt=1.0, t_end=None, debug=True, model=None):
+             dt=1.0, t_end=None, debug=True, model=None, force=None):
     """Runs the oracle compressor on uv float32 [T][H][W][2].
 
     Returns a dict with the stream bytes (when t_end is None) and, with debug,
     the fixed-point input q, the reconstruction qhat, per-vertex bounds xi,
     their codes qxi, block modes, crossed-face masks, per-vertex symbols qd
-    and the run statistics.  pred="learned" needs model (bfloat16 bits)."""
+    and the run statistics.  pred="learned" needs model (bfloat16 bits).
+    force: optional bool [T][H][W], vertices stored losslessly (the repair of
+    a failed verification, reading R14)."""
     uv = np.ascontiguousarray(uv, np.float32)
     T, H, W, two = uv.shape
     assert two == 2
@@ -346,6 +348,8 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.
                  qd=np.empty((T, H, W, 2), np.uint32))
     te = T if t_end is None else int(t_end)
     m = None if model is None else np.ascontiguousarray(model, np.uint16)
+    fz = None if force is None else np.ascontiguousarray(force, np.uint8).reshape(-1)
+    assert fz is None or fz.size == T * H * W
     rc = L.o_compress2(_p(uv, C.c_float), H, W, T, dx, dy, dt, 1 if eb_mode == "rel" else 0,
                       float(eb), PRED[pred], block, stride, te, _p(m, C.c_uint16),
                       C.byref(out) if t_end is None else None,
@@ -353,7 +357,7 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, dx=1.
                       _p(d.get("q"), C.c_int32), _p(d.get("qhat"), C.c_int32),
                       _p(d.get("xi"), C.c_int64), _p(d.get("qxi"), C.c_uint8),
                       _p(d.get("modes"), C.c_uint8), _p(d.get("mask"), C.c_uint16),
-                      _p(d.get("qd"), C.c_uint32), C.byref(st))
+                      _p(d.get("qd"), C.c_uint32), C.byref(st), _p(fz, C.c_uint8))
     if rc != 0:
         raise RuntimeError(f"oracle compress failed: {rc}")
     if t_end is None:

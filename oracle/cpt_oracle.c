@@ -884,7 +884,8 @@ static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 x
 int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, double d_t,
                 int eb_mode, double eb, int pred, int B, int n, int t_end, const uint16_t* model,
                 uint8_t** out, size_t* out_bytes, int32_t* q_out, int32_t* qhat_out, int64_t* xi_out,
-                uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out, o_stats* st) {
+                uint8_t* qxi_out, uint8_t* modes_out, uint16_t* mask_out, uint32_t* qd_out, o_stats* st,
+                const uint8_t* force) {
     if (H < 2 || W < 2 || T < 1 || B < 1 || n < 1 || pred < 0 || pred > 4) return O_ERR_ARG;
     const int has_net = pred == 3 || pred == 4, has_modes = pred == 2 || pred == 4;
     if (has_net && !model) return O_ERR_ARG;
@@ -936,6 +937,9 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
                 i64 v = vid(H, W, t, i, j);
                 int crossed;
                 i64 xi = derive_min_eb(Q, mask, H, W, T, t, i, j, eps_int, &crossed);
+                /* reading R14 (repair of a failed verification): a forced vertex is
+                 * stored losslessly */
+                if (force && force[v]) xi = 0;
                 if (xi_out) xi_out[v] = xi;
                 int code = o_xi_code(xi);
                 qxi[v] = (uint8_t)code;
@@ -1044,7 +1048,7 @@ int o_compress(const float* uv, int H, int W, int T, double d_x, double d_y, dou
                o_stats* st) {
     if (pred == 3 || pred == 4) return O_ERR_ARG;
     return o_compress2(uv, H, W, T, d_x, d_y, d_t, eb_mode, eb, pred, B, n, t_end, NULL, out, out_bytes, q_out,
-                       qhat_out, xi_out, qxi_out, modes_out, mask_out, qd_out, st);
+                       qhat_out, xi_out, qxi_out, modes_out, mask_out, qd_out, st, NULL);
 }
 
 void o_free(void* p) { free(p); }

@@ -428,7 +428,7 @@ static void merged_order(const std::vector<OrderField>& fs, const PipeTuning& tu
 
 // The decoder's schedule (its prediction units carry no MoP decisions and its
 // waves no face work).
-static const PipeTuning kDecodeSchedule = {0, 0, 0, 0, 0};
+static const PipeTuning kDecodeSchedule = {0, 0, 0, 0, 0, 0};
 
 // ---------------------------------------------------------------------------
 // compression (Alg. 3)
@@ -499,6 +499,7 @@ struct FieldJob {
     bool obuf_pinned = false;
     size_t total = 0;
     VerifyFault vfault;  // failure injection (tests)
+    const uint8_t* force_h = nullptr;  // repair: [N] host flags of vertices to store losslessly
 
     FieldJob(cudaStream_t st_, bool timing) : s(st_), ar(st_), tm(st_, timing) { std::memset(&st, 0, sizeof(st)); }
     ~FieldJob() { release_output(); }
@@ -652,7 +653,40 @@ struct FieldJob {
         tm.begin(3);
         launch_classify(d_q, d_mask, H, W, T, eps_int, d_cls, d_clsm, d_qdiag, s);
         st.launches[3]++;
+        if (force_h) {  // repair: the flagged vertices are stored losslessly
+            uint8_t* d_force;
+            CPT_CUDA(ar.alloc(&d_force, N));
+            CPT_CUDA(cudaMemcpyAsync(d_force, force_h, N, cudaMemcpyHostToDevice, s));
+            launch_force_lossless(d_force, H, W, T, d_cls, s);
+            st.launches[3]++;
+        }
         tm.end();
+        return CPT_OK;
+    }
+
+    // Repair (after a failed verification): ORs into flags_h [N] the vertices
+    // of the faces whose predicate the reconstruction changed and the
+    // vertices past the pointwise bound.
+    cpt_status repair_flags(uint8_t* flags_h) {
+        int32_t* d_rec;
+        uint16_t* d_mrec;
+        uint8_t* d_fl;
+        unsigned long long* d_n;
+        CPT_CUDA(ar.alloc(&d_rec, NV));
+        CPT_CUDA(ar.alloc(&d_mrec, N));
+        CPT_CUDA(ar.alloc(&d_fl, N));
+        CPT_CUDA(ar.alloc(&d_n, 1));
+        CPT_CUDA(cudaMemcpyAsync(d_rec, d_qhat, NV * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        launch_untag(reinterpret_cast<int2*>(d_rec), N, s);
+        CPT_CUDA(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), s));
+        CPT_CUDA(cudaMemsetAsync(d_fl, 0, N, s));
+        launch_face_masks(d_rec, H, W, T, d_mrec, d_n, s);
+        const double bound = std::max(eps, std::ldexp(0.5, -k));
+        launch_repair_flags(d_rec, d_uv, d_mask, d_mrec, H, W, T, k, bound, d_fl, s);
+        std::vector<uint8_t> fl(N);
+        CPT_CUDA(cudaMemcpyAsync(fl.data(), d_fl, N, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        for (size_t v = 0; v < N; ++v) flags_h[v] |= fl[v];
         return CPT_OK;
     }
 
@@ -1243,7 +1277,8 @@ static cpt_status check_device() {
 }
 
 static PipeTuning tuning_of(const cpt_params* prm) {
-    return PipeTuning{prm->schedule[0], prm->schedule[1], prm->schedule[2], prm->schedule[3], prm->schedule[4]};
+    return PipeTuning{prm->schedule[0], prm->schedule[1], prm->schedule[2], prm->schedule[3], prm->schedule[4],
+                      prm->schedule[5]};
 }
 
 static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
@@ -1274,6 +1309,46 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
     float ms_total = 0.f;
     cudaEventElapsedTime(&ms_total, ev0, ev1);
     rc = job.finish(ms_total, pt.ms_pipeline, out, out_bytes, stats);
+    if (rc == CPT_ERR_VERIFY && prm->repair) {
+        // reading R14: store the vertices of the changed faces (and those past
+        // the bound) losslessly and encode again, at most kRepairRounds times
+        constexpr int kRepairRounds = 3;
+        std::vector<uint8_t> force(job.N, 0);
+        cpt_status rf = job.repair_flags(force.data());
+        for (int round = 1; rf == CPT_OK && rc == CPT_ERR_VERIFY && round <= kRepairRounds; ++round) {
+            cpt_free(*out);
+            *out = nullptr;
+            *out_bytes = 0;
+            FieldJob again(s, true);
+            again.uv = uv;
+            again.dims = *dims;
+            again.prm = prm;
+            again.dbg = dbg;
+            again.force_h = force.data();
+            FieldJob* ap = &again;
+            PipeTimes pt2;
+            CPT_CUDA(cudaEventRecord(ev0, s));
+            rc = run_jobs(&ap, 1, prm, s, prm->tune != 0, tuning_of(prm), &pt2);
+            if (rc != CPT_OK) return rc;
+            CPT_CUDA(cudaEventRecord(ev1, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+            cudaEventElapsedTime(&ms_total, ev0, ev1);
+            rc = again.finish(ms_total, pt2.ms_pipeline, out, out_bytes, stats);
+            if (stats) {
+                stats->repair_rounds = round;
+                uint64_t nf = 0;
+                for (uint8_t f : force) nf += f;
+                stats->forced_vertices = nf;
+            }
+            if (rc == CPT_ERR_VERIFY && round < kRepairRounds) rf = again.repair_flags(force.data());
+        }
+        if (rf != CPT_OK) {
+            cpt_free(*out);
+            *out = nullptr;
+            *out_bytes = 0;
+            return rf;
+        }
+    }
     if (rc != CPT_OK && rc != CPT_ERR_VERIFY) return rc;
     const cpt_status rz = wrap_output(prm, out, out_bytes, stats, job.NV * 4);
     if (rz != CPT_OK) {
@@ -1361,6 +1436,7 @@ static cpt_status compress_batch_impl(const float* const* uv, const cpt_dims* di
         b.schedule[2] = pt.used.slice_weight;
         b.schedule[3] = pt.used.slack;
         b.schedule[4] = pt.used.warps_per_sm;
+        b.schedule[5] = pt.used.mixed;
         for (int f = first; f < last; ++f) {
             FieldJob& j = *jobs[f - first];
             cpt_stats st1;

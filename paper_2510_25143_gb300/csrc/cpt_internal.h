@@ -84,7 +84,11 @@ struct PipeArgs {
     unsigned queue_len;       // prep units of every field
     int* status;              // device status word (0 = ok)
     long long timeout_ns;
-    int prep_warps;           // warps working the prep queue
+    int prep_warps;           // layout 0: warps working the prep queue (the first ones of the grid)
+    int prep_per_cta;         // layout 1: warps of each CTA working the prep queue (the first ones)
+    int mixed;                // 0: every warp has a slot of one size, whole CTAs per role;
+                              // 1: prep and wave slots of their own sizes in every CTA
+    unsigned slot_bytes;      // layout 0: bytes of a warp's slot
     unsigned skip_item;       // failure injection: the ticket of a wave that never runs (~0u = none)
 };
 
@@ -96,6 +100,8 @@ struct PipeTuning {
     int slice_weight;  // slice weight of the ticket order without prep units (0 = default)
     int slack;         // extra slice weight of the ticket order with prep units (0 = default)
     int warps_per_sm;  // worker warps per SM (0 = as many as shared memory and registers allow)
+    int mixed;         // 1: prep and wave warps in every CTA, each with a slot of its own size;
+                       // 0: whole CTAs per role, every slot the size of the larger one
 };
 
 // Canonical Huffman decoding tables of one stream (device pointers).
@@ -122,6 +128,12 @@ void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, un
                        cudaStream_t s);
 void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T, int k,
                    VerifyOut* out, cudaStream_t s);
+// repair of a failed verification: flags (zeroed before) of the vertices of
+// changed faces and of vertices past the bound (qhat untagged); the flagged
+// vertices' classification set to lossless (strip-diagonal cls)
+void launch_repair_flags(const int32_t* qhat, const float* uv, const uint16_t* m_orig, const uint16_t* m_rec, int H,
+                         int W, int T, int k, double bound, uint8_t* flags, cudaStream_t s);
+void launch_force_lossless(const uint8_t* flags, int H, int W, int T, int2* cls, cudaStream_t s);
 
 // k_encode.cu
 // out, out_m and qd in the strip-diagonal layout (see SliceArgs), zeroed before

@@ -279,7 +279,7 @@ struct PrepSmem {
         struct {                           // SL and MoP
             int2 qc[UMAX + 2][UMAX + 2];   // q(t): rows/cols -1..U around the unit
             int2 psl[UMAX][UMAX];          // SL predictions of the unit
-            unsigned smp[2][64 * UMAX];    // sampled symbols per mode (0xFFFFFFFF = none)
+            uint16_t smp[2][64 * UMAX];    // sampled symbols per mode, 2 B^2 slots per block
             unsigned hist[256];
             unsigned short list[UMAX * UMAX];  // sites (row * 32 + column) left for SL
             unsigned char modes[64];       // decisions of the unit's blocks
@@ -291,7 +291,7 @@ struct PrepSmem {
 // of kChunk steps (each step's 32 lanes contiguous), two chunks ahead, into
 // three slots (slot = chunk mod 3): during chunk g the steps read chunks g
 // and g + 1 (neighbours at steps k + 1, k + 2), while g + 2 is in flight.
-constexpr int kChunk = 8;
+constexpr int kChunk = 4;
 struct alignas(16) WaveRing {
     int2 cl[3][kChunk][32];      // classification
     unsigned cm[3][kChunk][32];  // faces needing only the M = 0 check
@@ -300,25 +300,28 @@ struct alignas(16) WaveRing {
     int2 qb[3][kChunk];          // q(t) of the next strip's first row at column (consumer step - 31)
     int2 nb[3][kChunk];          // q(t+1) of the same
 };
+// The shared memory of a warp depends on its role: a prep warp holds a
+// prediction unit's windows (PrepSlot), a wave warp the staging ring and the
+// neighbour values of its face loops (WaveSlot).  A CTA holds its prep warps'
+// slots, then its wave warps' slots, then (learned predictor) the net's
+// second-layer weights.
 template <int UMAX, bool NET>
-struct alignas(16) WarpSmem {
+struct alignas(16) PrepSlot {
     static constexpr int kUmax = UMAX;
     static constexpr bool kNet = NET;
-    union {
-        PrepSmem<UMAX, NET> prep;  // prediction units
-        WaveRing ring;             // waves
-    };
+    PrepSmem<UMAX, NET> prep;
+    SliceArgs args;  // the field of the current unit (copied from the launch's field table)
+};
+struct alignas(16) WaveSlot {
+    WaveRing ring;
     int2 nbs[32][15];  // per-lane neighbour values for the face loops
     SliceArgs args;    // the field of the current item (copied from the launch's field table)
 };
-template <>
-struct alignas(16) WarpSmem<0, false> {  // 3DL: no prediction units
-    static constexpr int kUmax = 0;
-    static constexpr bool kNet = false;
-    WaveRing ring;
-    int2 nbs[32][15];
-    SliceArgs args;
-};
+template <int UMAX, bool NET>
+constexpr size_t prep_slot_bytes() {
+    if constexpr (UMAX > 0) return sizeof(PrepSlot<UMAX, NET>);
+    else return 0;
+}
 
 // Copies the arguments of field f into the warp's shared slot.
 template <class Sm>
@@ -355,8 +358,8 @@ __device__ __forceinline__ unsigned long long log2_q32(unsigned x) {
 
 // Score of one block and mode in Q32 bits per sample (Eq. 10 plus the
 // overflow penalty and the metadata term): H0 + 16 L/(n+L) + 1/(2 B^2).
-// smp holds nslots entries: a symbol, 0 for an overflow, 0xFFFFFFFF unused.
-__device__ long long warp_block_score(const unsigned* smp, int nslots, int B, unsigned* hist,
+// smp holds the nslots symbols of the block's sampled sites (0 = overflow).
+__device__ long long warp_block_score(const uint16_t* smp, int nslots, int B, unsigned* hist,
                                       const unsigned long long* __restrict__ lg) {
     const int lane = (int)(threadIdx.x & 31u);
     const unsigned lo = (unsigned)kRadius - 128u;
@@ -365,8 +368,7 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
     unsigned nv = 0, nf = 0;
     unsigned long long acc = 0;
     for (int k = lane; k < nslots; k += 32) {
-        unsigned x = smp[k];
-        if (x == 0xFFFFFFFFu) continue;
+        const unsigned x = smp[k];
         if (x == 0) { ++nf; continue; }
         ++nv;
         if (x - lo < 256u) {
@@ -376,7 +378,7 @@ __device__ long long warp_block_score(const unsigned* smp, int nslots, int B, un
             unsigned c = 0;
             bool first = true;
             for (int m = 0; m < nslots; ++m) {
-                if (smp[m] == x) {
+                if ((unsigned)smp[m] == x) {
                     ++c;
                     if (m < k) first = false;
                 }
@@ -418,17 +420,25 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
     const int bpp = 32 / B;                    // blocks per pass
     const int code = xi_code(a.eps_int);
     const int r = lane % B, bl = lane / B;
-    const int nslots = 2 * B * B;
+    const int nslots = 2 * B * B;  // room per block; a block's sampled sites fill the first ones
     const int2* pp = ps.pp + (Rw + 1) * kPP + (Rw + 1);  // (0,0) = vertex (r0, c0) of slice t-1
+    // sampled sites of the block at (ib, jb): rows and columns from the
+    // first multiple of n, every n-th; slot of a site in row r, column jj
+    auto sampled = [&](int ib, int jb, int& fr, int& fc, int& nrs, int& ncs) {
+        const int ih = min(B, H - ib), iw = min(B, W - jb);
+        fr = (n - ib % n) % n;
+        fc = (n - jb % n) % n;
+        nrs = ih > fr ? (ih - fr + n - 1) / n : 0;
+        ncs = iw > fc ? (iw - fc + n - 1) / n : 0;
+    };
     for (int b0 = 0; b0 < nbt; b0 += bpp) {
         const int bi = b0 + bl;
         const int ib = r0 + (bi / nbu) * B, jb = c0 + (bi % nbu) * B;
         const int i = ib + r, li = i - r0;
         const bool live = bi < nbt && i < H && jb < W;
-        for (int k = lane; k < bpp * nslots; k += 32) {
-            ps.smp[0][k] = 0xFFFFFFFFu;
-            ps.smp[1][k] = 0xFFFFFFFFu;
-        }
+        int fr = 0, fc = 0, nrs = 0, ncs = 0;
+        if (live) sampled(ib, jb, fr, fc, nrs, ncs);
+        auto slot = [&](int jj) { return bl * nslots + 2 * (((r - fr) / n) * ncs + (jj - fc) / n); };
         __syncwarp();
         if (live && (i % n) == 0) {
             for (int jj = 0; jj < B; ++jj) {
@@ -437,9 +447,9 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
                     const int2 qv = ps.qc[li + 1][j - c0 + 1];
                     const int2 p = ps.psl[li][j - c0];
                     int d;
-                    unsigned* dst = &ps.smp[1][bl * nslots + 2 * (r * B + jj)];
-                    dst[0] = quantize_code(qv.x, p.x, code, d);
-                    dst[1] = quantize_code(qv.y, p.y, code, d);
+                    uint16_t* dst = &ps.smp[1][slot(jj)];
+                    dst[0] = (uint16_t)quantize_code(qv.x, p.x, code, d);
+                    dst[1] = (uint16_t)quantize_code(qv.y, p.y, code, d);
                 }
             }
         }
@@ -464,9 +474,9 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
                 const unsigned su = quantize_code(qv.x, pu, code, rec.x);
                 const unsigned sv = quantize_code(qv.y, pv, code, rec.y);
                 if ((i % n) == 0 && (j % n) == 0) {
-                    unsigned* dst = &ps.smp[0][bl * nslots + 2 * (r * B + jj)];
-                    dst[0] = su;
-                    dst[1] = sv;
+                    uint16_t* dst = &ps.smp[0][slot(jj)];
+                    dst[0] = (uint16_t)su;
+                    dst[1] = (uint16_t)sv;
                 }
                 up = u;
                 res = rec;
@@ -482,8 +492,11 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
             const int bb = b0 + b;
             const int ibb = r0 + (bb / nbu) * B, jbb = c0 + (bb % nbu) * B;
             if (ibb >= H || jbb >= W) continue;
-            const long long r3 = warp_block_score(&ps.smp[0][b * nslots], nslots, B, ps.hist, a.log2tab);
-            const long long rs = warp_block_score(&ps.smp[1][b * nslots], nslots, B, ps.hist, a.log2tab);
+            int frb, fcb, nrb, ncb;
+            sampled(ibb, jbb, frb, fcb, nrb, ncb);
+            const int used = 2 * nrb * ncb;
+            const long long r3 = warp_block_score(&ps.smp[0][b * nslots], used, B, ps.hist, a.log2tab);
+            const long long rs = warp_block_score(&ps.smp[1][b * nslots], used, B, ps.hist, a.log2tab);
             if (lane == 0) {
                 const unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
                 a.modes[((size_t)t * a.nby + ibb / B) * a.nbx + jbb / B] = m;
@@ -1085,19 +1098,25 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     return true;
 }
 
-// Every warp is an independent worker with its own shared-memory slice; one
-// CTA per SM holds as many of them as the slices and the registers allow, so
-// that they spread over the SM's sub-partitions.
+// Every warp is an independent worker with its own shared-memory slot; one
+// CTA per SM holds as many of them as the slots and the registers allow.
+// Two layouts: (0) every slot has the size of the larger role's and the first
+// prep_warps warps of the grid work the prep queue, so whole SMs run the
+// waves undisturbed; (1) the first prep_per_cta warps of every CTA work the
+// prep queue with prep-sized slots, the others the waves with wave-sized
+// slots (more warps fit, but the waves share every SM).
 constexpr int kMaxWarpsPerCta = 12;  // 168 registers x 32 lanes x 12 <= 64 K registers
 template <bool kBatch, int UMAX, bool NET>
 __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ PipeArgs p) {
-    using Sm = WarpSmem<UMAX, NET>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = (int)(threadIdx.x >> 5), wpc = (int)(blockDim.x >> 5);
-    Sm& sm = reinterpret_cast<Sm*>(smem_raw)[wid];
+    const bool mixed = p.mixed != 0;
+    const int np = UMAX > 0 && mixed ? p.prep_per_cta : 0;
+    constexpr size_t kPrepBytes = prep_slot_bytes<UMAX, NET>();
     // the learned net's second-layer weights and biases, one copy per CTA
-    // after the warps' slices (every field of a launch shares the model)
-    float* w2s = reinterpret_cast<float*>(smem_raw + sizeof(Sm) * wpc);
+    // after the warps' slots (every field of a launch shares the model)
+    float* w2s = reinterpret_cast<float*>(
+        smem_raw + (mixed ? kPrepBytes * np + sizeof(WaveSlot) * (wpc - np) : (size_t)p.slot_bytes * wpc));
     if constexpr (NET) {
         if (p.one.pred == 3 || p.one.pred == 4) {
             for (int k = (int)threadIdx.x; k < kNetW2 + kNetC; k += (int)blockDim.x)
@@ -1105,10 +1124,16 @@ __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ 
         }
         __syncthreads();
     }
-    if ((int)blockIdx.x * wpc + wid < p.prep_warps) {
-        if constexpr (UMAX > 0) prep_loop<kBatch>(p, sm, w2s);
-        return;
+    unsigned char* const slot =
+        mixed ? (wid < np ? smem_raw + kPrepBytes * wid : smem_raw + kPrepBytes * np + sizeof(WaveSlot) * (wid - np))
+              : smem_raw + (size_t)p.slot_bytes * wid;
+    if constexpr (UMAX > 0) {
+        if (mixed ? wid < np : (int)blockIdx.x * wpc + wid < p.prep_warps) {
+            prep_loop<kBatch>(p, *reinterpret_cast<PrepSlot<UMAX, NET>*>(slot), w2s);
+            return;
+        }
     }
+    WaveSlot& sm = *reinterpret_cast<WaveSlot*>(slot);
     int cur = -1;  // field whose arguments sit in the warp's slot
     for (;;) {
         unsigned item = 0;
@@ -1157,19 +1182,34 @@ void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T
 
 template <int UMAX, bool NET>
 static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s) {
-    const size_t slice = sizeof(WarpSmem<UMAX, NET>);
+    const size_t pslot = prep_slot_bytes<UMAX, NET>(), wslot = sizeof(WaveSlot);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const size_t wshared = NET ? sizeof(float) * (kNetW2 + kNetC) : 0;  // the net's shared weights
-    int wpc = (int)std::min<size_t>((size_t)kMaxWarpsPerCta, ((size_t)optin - wshared) / slice);
-    if (tune.warps_per_sm > 0) wpc = std::min(wpc, tune.warps_per_sm);
+    // with SL, MoP or the learned predictor a share of the warps works the
+    // prep queue; the most warps whose slots fit the shared memory
+    const bool prep = UMAX > 0 && p.queue_len > 0;
+    const bool mixed = prep && tune.mixed != 0;
+    const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
+    const size_t uslot = std::max(pslot, wslot);  // layout 0: one slot size
+    int wmax = kMaxWarpsPerCta;
+    if (tune.warps_per_sm > 0) wmax = std::min(wmax, tune.warps_per_sm);
+    int wpc = 0, np = 0;
+    for (int w = wmax; w >= (mixed ? 2 : 1) && !wpc; --w) {
+        const int n = mixed ? std::max(1, std::min(w - 1, (int)((w * share + 50) / 100))) : 0;
+        const size_t need = mixed ? pslot * n + wslot * (w - n) : uslot * w;
+        if (need + wshared <= (size_t)optin) {
+            wpc = w;
+            np = n;
+        }
+    }
     if (wpc < 1) return cudaErrorInvalidConfiguration;
     const bool batch = p.nfields > 1;
     auto kern = batch ? encode_pipeline_kernel<true, UMAX, NET> : encode_pipeline_kernel<false, UMAX, NET>;
-    const size_t smem = slice * wpc + wshared;
+    const size_t smem = (mixed ? pslot * np + wslot * (wpc - np) : uslot * wpc) + wshared;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1177,15 +1217,14 @@ static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;  // every worker must be resident
     if (tune.warps_per_sm > 0) per_sm = 1;                 // exactly that many warps per SM
-    // with SL or MoP a share of the warps works the prep queue
     PipeArgs b = p;
-    const int warps = nsm * per_sm * wpc;
+    b.mixed = mixed ? 1 : 0;
+    b.prep_per_cta = np;
+    b.slot_bytes = (unsigned)uslot;
     b.prep_warps = 0;
-    if (p.queue_len > 0) {
-        const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
-        b.prep_warps = (int)((long long)warps * share / 100);
-        if (b.prep_warps < 1) b.prep_warps = 1;
-        if (b.prep_warps > warps - 1) b.prep_warps = warps - 1;
+    if (prep && !mixed) {
+        const int warps = nsm * per_sm * wpc;
+        b.prep_warps = std::max(1, std::min(warps - 1, (int)((long long)warps * share / 100)));
     }
     kern<<<nsm * per_sm, 32 * wpc, smem, s>>>(b);
     return cudaGetLastError();

@@ -439,6 +439,70 @@ __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q
 }
 
 // ---------------------------------------------------------------------------
+// Repair of a failed verification (reading R14: the paper leaves the policy
+// open).  flags[v] = 1 for every vertex of a face whose predicate differs
+// between the original and the reconstruction, and for every vertex whose
+// reconstruction breaks the pointwise bound; force_lossless_kernel then
+// sets the classification of the flagged vertices to "lossless" (bound 0,
+// no face left to evaluate) for the next encoding.
+// ---------------------------------------------------------------------------
+__device__ __constant__ const unsigned char kFaceCorner[12][3] = {
+#define CPT_FC(ty, a, b, c) {a, b, c},
+    CPT_OWNED_FACES(CPT_FC)
+#undef CPT_FC
+};
+
+__global__ void __launch_bounds__(256) repair_flags_kernel(const int2* __restrict__ qhat, const float2* __restrict__ uv,
+                                                           const uint16_t* __restrict__ m_orig,
+                                                           const uint16_t* __restrict__ m_rec, int H, int W, int T,
+                                                           int k, double bound, uint8_t* __restrict__ flags) {
+    const size_t N = (size_t)H * W * T;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+        const unsigned diff = (unsigned)(m_orig[v] ^ m_rec[v]);
+        const int j = (int)(v % (size_t)W);
+        const size_t r = v / (size_t)W;
+        const int i = (int)(r % (size_t)H), t = (int)(r / (size_t)H);
+        for (unsigned d = diff; d; d &= d - 1) {
+            const int ty = __ffs(d) - 1;
+            for (int c = 0; c < 3; ++c) {
+                const int n = kFaceCorner[ty][c];
+                const int tt = t + (n >> 2), ii = i + ((n >> 1) & 1), jj = j + (n & 1);
+                if (tt < T && ii < H && jj < W) flags[((size_t)tt * H + ii) * W + jj] = 1;
+            }
+        }
+        const int2 q = qhat[v];
+        const float2 x = uv[v];
+        const double eu = fabs(ldexp((double)q.x, -k) - (double)x.x), ev = fabs(ldexp((double)q.y, -k) - (double)x.y);
+        if (!(eu <= bound) || !(ev <= bound)) flags[v] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) force_lossless_kernel(const uint8_t* __restrict__ flags, int H, int W, int T,
+                                                             int2* __restrict__ cls) {
+    const size_t N = (size_t)H * W * T;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+        if (!flags[v]) continue;
+        const int j = (int)(v % (size_t)W);
+        const size_t r = v / (size_t)W;
+        const int i = (int)(r % (size_t)H), t = (int)(r / (size_t)H);
+        // strip-diagonal position of (t, i, j): strip i / 32, step j + i % 32, lane i % 32
+        const size_t dv =
+            (((size_t)t * ((H + 31) >> 5) + (i >> 5)) * (size_t)(W + 31) + (j + (i & 31))) * 32 + (i & 31);
+        cls[dv] = make_int2(0, 0);
+    }
+}
+
+void launch_repair_flags(const int32_t* qhat, const float* uv, const uint16_t* m_orig, const uint16_t* m_rec, int H,
+                         int W, int T, int k, double bound, uint8_t* flags, cudaStream_t s) {
+    repair_flags_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const int2*>(qhat), reinterpret_cast<const float2*>(uv),
+                                             m_orig, m_rec, H, W, T, k, bound, flags);
+}
+
+void launch_force_lossless(const uint8_t* flags, int H, int W, int T, int2* cls, cudaStream_t s) {
+    force_lossless_kernel<<<1216, 256, 0, s>>>(flags, H, W, T, cls);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s) {

@@ -69,3 +69,70 @@ def test_verification_catches_a_corrupted_reconstruction():
     # nothing pending afterwards
     _, s4, _ = cpt.compress(d, 1e-2, pred="mop")
     assert s4["verify_mismatch_slice"] == 0 and s4["linf"] <= s4["eps"]
+
+
+def _expected_force(r0, uv, v, delta, eps):
+    """The vertices a repair must store losslessly, from the oracle alone: the
+    oracle's reconstruction with the injected change at vertex v, the faces
+    whose predicate that changes (their three vertices each) and the vertices
+    past the pointwise bound."""
+    import numpy as np
+    T, H, W, _ = uv.shape
+    qh = r0["qhat"].copy()
+    qh.reshape(-1, 2)[v, 0] += delta
+    diff = oracle.face_masks(qh) ^ r0["mask"]
+    faces = oracle.face_table()  # [type][vertex][(dt, di, dj)]
+    force = np.zeros((T, H, W), bool)
+    for t, i, j in np.argwhere(diff != 0):
+        d = int(diff[t, i, j])
+        for ty in range(12):
+            if (d >> ty) & 1:
+                for dt, di, dj in faces[ty]:
+                    force[t + dt, i + di, j + dj] = True
+    k = r0["stats"]["k"]
+    bound = max(eps, np.ldexp(0.5, -k))
+    err = np.abs(np.ldexp(qh.astype(np.float64), -k) - uv.astype(np.float64)).max(axis=3)
+    force |= err > bound
+    return force
+
+
+@pytest.mark.parametrize("case", ["crossed_face", "past_bound"])
+def test_repair_after_a_failed_verification(case):
+    """Reading R14's repair: an injected fault makes the first verification
+    fail; the vertices of the changed faces (and those past the bound) are
+    stored losslessly and the field is encoded again.  The stream returned
+    equals the oracle's with the same vertices forced (computed from the
+    oracle), verifies, and decodes identically on both sides."""
+    import numpy as np
+    uv = synth.vortex_sum(48, 56, 5, seed=6)
+    d = _dev(uv)
+    eb = 1e-2
+    r0 = oracle.compress(uv, eb, pred="mop")
+    T, H, W, _ = uv.shape
+    if case == "crossed_face":
+        crossed = np.flatnonzero(r0["mask"].reshape(-1))
+        v = int(crossed[len(crossed) // 2])
+        qv = int(r0["qhat"].reshape(-1, 2)[v, 0])
+        delta = -2 * qv if qv != 0 else 1 << 10
+    else:
+        v = (2 * H + H // 2) * W + W // 2
+        delta = 1 << 20
+    force = _expected_force(r0, uv, v, delta, r0["stats"]["eps"])
+    assert force.any()
+    cpt.inject_verify_fault(v, delta)
+    blob, st, _ = cpt.compress(d, eb, pred="mop", repair=True)
+    assert st["status"] == cpt.OK and st["repair_rounds"] == 1
+    assert st["forced_vertices"] == int(force.sum())
+    assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0 and st["linf"] <= st["eps"]
+    ref = oracle.compress(uv, eb, pred="mop", force=force)
+    assert blob == ref["bytes"]
+    qo, xo, _ = oracle.decompress(blob)
+    out, qg, _ = cpt.decompress(blob, want_q=True)
+    assert (qg == qo).all() and np.array_equal(out.view(np.uint32), xo.view(np.uint32))
+    assert (oracle.face_masks(qo) == r0["mask"]).all()
+    # without repair the same fault is reported, and nothing stays pending
+    cpt.inject_verify_fault(v, delta)
+    _, s2, _ = cpt.compress(d, eb, pred="mop", check=False)
+    assert s2["status"] == cpt.ERR_VERIFY
+    b3, s3, _ = cpt.compress(d, eb, pred="mop", repair=True)
+    assert s3["repair_rounds"] == 0 and b3 == r0["bytes"]

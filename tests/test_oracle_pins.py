@@ -694,3 +694,23 @@ def test_xi_zero_where_face_crossed():
             if m[t, i, j] >> ty & 1:
                 for e in F[ty]:
                     assert xi[t + e[0], i + e[1], j + e[2]] == 0
+
+
+def test_forced_vertices_are_lossless_and_the_stream_decodes():
+    """Repair reading R14: a forced vertex is stored losslessly (bound code 0,
+    reconstruction = input); forcing none changes no byte; the stream decodes
+    to the reconstruction and keeps every face predicate."""
+    uv = synth.vortex_sum(30, 34, 4, seed=17)
+    base = oracle.compress(uv, 1e-2, pred="mop")
+    none = oracle.compress(uv, 1e-2, pred="mop", force=np.zeros((4, 30, 34), bool))
+    assert none["bytes"] == base["bytes"]
+    force = np.zeros((4, 30, 34), bool)
+    force[1, 10:13, 7:9] = True
+    force[3, 29, 33] = True
+    r = oracle.compress(uv, 1e-2, pred="mop", force=force)
+    assert (r["qxi"][force] == 0).all() and (r["xi"][force] == 0).all()
+    assert (r["qhat"][force] == r["q"][force]).all()
+    assert (r["qhat"][:1] == base["qhat"][:1]).all()  # slices before the first forced vertex unchanged
+    qh, _, _ = oracle.decompress(r["bytes"])
+    assert (qh == r["qhat"]).all()
+    assert (oracle.face_masks(qh) == r["mask"]).all()
