@@ -370,6 +370,20 @@ static bool is_device_pointer(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// fb with cfl = 2^(1 - fb), 0 <= fb <= 26 and max(H, W) 2^fb + 2^31 < 2^53,
+// else -1: the conditions under which the semi-Lagrangian RK2 midpoint is
+// exact in fixed point with fb fractional bits (sl_predict_fix)
+static int sl_fixed_bits(double cfl, int H, int W) {
+    if (!(cfl > 0) || !std::isfinite(cfl)) return -1;
+    int e = 0;
+    const double m = std::frexp(cfl, &e);  // cfl = m 2^e, m in [0.5, 1)
+    if (m != 0.5) return -1;               // not a power of two
+    const int fb = 2 - e;                  // cfl = 2^(e-1) = 2^(1 - fb)
+    if (fb < 0 || fb > 26) return -1;
+    if (std::ldexp((double)std::max(H, W), fb) + 2147483648.0 >= 9007199254740992.0) return -1;
+    return fb;
+}
+
 static int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -626,6 +640,9 @@ struct FieldJob {
         A.nchunks = nchunks;
         A.cfl_x = std::ldexp(dt / dx, -k);
         A.cfl_y = std::ldexp(dt / dy, -k);
+        A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
+        A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
+        if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
         // Reach of the semi-Lagrangian back-trace into slice t-1: no
         // reconstruction exceeds max|q| + E in magnitude, every displacement is
         // at most that times CFL, the bilinear stencil adds one cell, and one
@@ -720,12 +737,14 @@ struct FieldJob {
     // ---- phase 2 (after the pipeline): compaction counts
     cpt_status compact() {
         tm.begin(5);
-        CPT_CUDA(ar.alloc(&d_off, N));
-        CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(N)));
-        launch_count_pack(d_qxi, d_sym, N, d_off, s);
-        CPT_CUDA(cudaMemcpyAsync(&small_h[0], d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
-        launch_exclusive_scan_u64(d_off, N, d_stmp, s);
-        CPT_CUDA(cudaMemcpyAsync(&small_h[1], d_off + N - 1, 8, cudaMemcpyDeviceToHost, s));
+        const size_t nt = compact_tiles(N);
+        CPT_CUDA(ar.alloc(&d_off, nt + 1));
+        CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(nt + 1)));
+        CPT_CUDA(cudaMemsetAsync(d_off + nt, 0, sizeof(unsigned long long), s));
+        launch_tile_count(d_qxi, d_sym, N, d_off, s);
+        launch_exclusive_scan_u64(d_off, nt + 1, d_stmp, s);  // [nt]: the totals
+        small_h[0] = 0;
+        CPT_CUDA(cudaMemcpyAsync(&small_h[1], d_off + nt, 8, cudaMemcpyDeviceToHost, s));
         CPT_CUDA(cudaMemcpyAsync(&small_h[2], d_cnt64, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         return CPT_OK;
     }
@@ -737,7 +756,7 @@ struct FieldJob {
         n_ld = (size_t)(tot & 0xFFFFFFFFull);
         CPT_CUDA(ar.alloc(&d_qd, n_qd));
         CPT_CUDA(ar.alloc(&d_ld, n_ld));
-        launch_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
+        launch_tile_scatter(d_qxi, d_sym, d_q, d_off, N, d_qd, d_ld, s);
         // both streams advance together: histograms (+ block modes) -> code books
         // and tile bit counts -> layout of the output -> words, copied straight
         // into the caller's buffer
@@ -1755,6 +1774,9 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     A.nchunks = (W + 31) / 32;
     A.cfl_x = std::ldexp(dt / dx, -k);
     A.cfl_y = std::ldexp(dt / dy, -k);
+    A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
+    A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
+    if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
     // Reach of the back-trace: |qhat| <= 2^23 + E for every stream (the
     // fixed-point scale keeps |q| <= 2^23, the quantiser moves a value by at
     // most E), so no displacement exceeds that times CFL.

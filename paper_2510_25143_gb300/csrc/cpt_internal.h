@@ -61,6 +61,7 @@ struct SliceArgs {
     const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
+    int sl_fbx, sl_fby;     // CFL = 2^(1 - fb) with an exact fixed-point RK2 midpoint; -1 = general FP64 path
     long long timeout_ns;
     // Decoding: the same pipeline rebuilds qhat from a stream.  cls then holds
     // (bound code, residual symbols u | v << 16) and qd the verbatim values,
@@ -148,8 +149,14 @@ constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols
 size_t scan_temp_elems(size_t n);
 void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s);
 void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long long* tmp, cudaStream_t s);
-void launch_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q, const unsigned long long* off,
-                    size_t N, uint16_t* qd_out, int32_t* ld_out, cudaStream_t s);
+// compaction in tiles: counts per tile, then (after an exclusive scan of the
+// tile counts, with one extra element for the total) the scatter
+size_t compact_tiles(size_t N);
+void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* tile_cnt,
+                       cudaStream_t s);
+void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q,
+                         const unsigned long long* tile_off, size_t N, uint16_t* qd_out, int32_t* ld_out,
+                         cudaStream_t s);
 void launch_hist_u8(const uint8_t* x, size_t n, unsigned* hist /*33*/, cudaStream_t s);
 void launch_hist_u16(const uint16_t* x, size_t n, unsigned* hist /*65536*/, cudaStream_t s);
 // code table entries: (code << 5) | len, len <= 24

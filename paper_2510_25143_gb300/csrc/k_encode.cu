@@ -82,87 +82,117 @@ __device__ __forceinline__ unsigned unc_pair(int f) {
 
 
 // ---------------------------------------------------------------------------
-// classify_kernel: one thread per vertex; out[v] = (bound over the certain
-// faces, 0 = lossless; uncertain faces that need the full Alg. 2), out_m[v] =
-// uncertain faces of which only M = 0 must be checked
+// classify_kernel: out[v] = (bound over the certain faces, 0 = lossless;
+// uncertain faces that need the full Alg. 2), out_m[v] = uncertain faces of
+// which only M = 0 must be checked, in the strip-diagonal layout.  A block
+// covers 32 columns x 32 rows of one slice.  Most vertices take the exact
+// fast path (below); the others are queued in shared memory and classified
+// at the end of the block with the full Alg. 2, one per thread, so that a
+// rare slow vertex does not hold up the 31 fast ones of its warp.
 // ---------------------------------------------------------------------------
+constexpr int kClsRows = 32;
+
+__device__ __forceinline__ void load_nb(const int2* __restrict__ q, size_t v, size_t sl, int W, unsigned valid,
+                                        int2 nb[14]) {
+    const int2 z = make_int2(0, 0);
+    nb[0] = (valid & (1u << 0)) ? __ldg(q + v - sl - W - 1) : z;
+    nb[1] = (valid & (1u << 1)) ? __ldg(q + v - sl - W) : z;
+    nb[2] = (valid & (1u << 2)) ? __ldg(q + v - sl - 1) : z;
+    nb[3] = (valid & (1u << 3)) ? __ldg(q + v - sl) : z;
+    nb[4] = (valid & (1u << 4)) ? __ldg(q + v - W - 1) : z;
+    nb[5] = (valid & (1u << 5)) ? __ldg(q + v - W) : z;
+    nb[6] = (valid & (1u << 6)) ? __ldg(q + v - 1) : z;
+    nb[7] = (valid & (1u << 7)) ? __ldg(q + v + 1) : z;
+    nb[8] = (valid & (1u << 8)) ? __ldg(q + v + W) : z;
+    nb[9] = (valid & (1u << 9)) ? __ldg(q + v + W + 1) : z;
+    nb[10] = (valid & (1u << 10)) ? __ldg(q + v + sl) : z;
+    nb[11] = (valid & (1u << 11)) ? __ldg(q + v + sl + 1) : z;
+    nb[12] = (valid & (1u << 12)) ? __ldg(q + v + sl + W) : z;
+    nb[13] = (valid & (1u << 13)) ? __ldg(q + v + sl + W + 1) : z;
+}
+
+__device__ __forceinline__ void store_cls(int2* __restrict__ out, unsigned* __restrict__ out_m,
+                                          int2* __restrict__ qd, const int2* __restrict__ q, int H, int W, int t,
+                                          int i, int j, size_t v, int xi, unsigned um_full, unsigned um_m) {
+    // strip-diagonal position of (t, i, j): strip i / 32, step j + i % 32, lane i % 32
+    const size_t dv = (((size_t)t * ((H + 31) >> 5) + (i >> 5)) * (size_t)(W + 31) + (j + (i & 31))) * 32 + (i & 31);
+    out[dv] = make_int2(xi, (int)um_full);
+    out_m[dv] = um_m;
+    qd[dv] = __ldg(q + v);
+}
+
 __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
                                                        int H, int W, int T, int eps_int, int2* __restrict__ out,
                                                        unsigned* __restrict__ out_m, int2* __restrict__ qd) {
-    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+    __shared__ unsigned short s_slow[32 * kClsRows];  // (row in the block) * 32 + lane
+    __shared__ int s_nslow;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 32 + lane;
+    const int ib = blockIdx.y * kClsRows;
     const int t = blockIdx.z;
-    if (i >= H || j >= W) return;
     const size_t sl = (size_t)H * W;
-    const size_t v = ((size_t)t * H + i) * W + j;
-    bool crossed = false;
+    if (threadIdx.x == 0) s_nslow = 0;
+    __syncthreads();
+    for (int rr = threadIdx.x >> 5; rr < kClsRows; rr += 8) {
+        const int i = ib + rr;
+        bool slow = false;
+        if (i < H && j < W) {
+            const size_t v = ((size_t)t * H + i) * W + j;
+            bool crossed = false;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        const int ot = t + kOwners[o].dt, oi = i + kOwners[o].di, oj = j + kOwners[o].dj;
-        if (ot >= 0 && oi >= 0 && oj >= 0)
-            crossed |= (__ldg(mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
-    }
-    int xi = 0;
-    unsigned um_full = 0, um_m = 0;
-    if (!crossed && eps_int > 0) {
-        xi = eps_int;
-        const unsigned valid = nb_valid(H, W, T, t, i, j);
-        const int2 z = make_int2(0, 0);
-        int2 nb[14];
-        nb[0] = (valid & (1u << 0)) ? __ldg(q + v - sl - W - 1) : z;
-        nb[1] = (valid & (1u << 1)) ? __ldg(q + v - sl - W) : z;
-        nb[2] = (valid & (1u << 2)) ? __ldg(q + v - sl - 1) : z;
-        nb[3] = (valid & (1u << 3)) ? __ldg(q + v - sl) : z;
-        nb[4] = (valid & (1u << 4)) ? __ldg(q + v - W - 1) : z;
-        nb[5] = (valid & (1u << 5)) ? __ldg(q + v - W) : z;
-        nb[6] = (valid & (1u << 6)) ? __ldg(q + v - 1) : z;
-        nb[7] = (valid & (1u << 7)) ? __ldg(q + v + 1) : z;
-        nb[8] = (valid & (1u << 8)) ? __ldg(q + v + W) : z;
-        nb[9] = (valid & (1u << 9)) ? __ldg(q + v + W + 1) : z;
-        nb[10] = (valid & (1u << 10)) ? __ldg(q + v + sl) : z;
-        nb[11] = (valid & (1u << 11)) ? __ldg(q + v + sl + 1) : z;
-        nb[12] = (valid & (1u << 12)) ? __ldg(q + v + sl + W) : z;
-        nb[13] = (valid & (1u << 13)) ? __ldg(q + v + sl + W + 1) : z;
-        const int2 qv = __ldg(q + v);
-        const int E = 1 << (31 - __clz(eps_int));
-        // Fast path (exact): every existing neighbour keeps the vertex's strict
-        // sign of u (or of v), with margin E where its value may still change,
-        // and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on every face unless
-        // M = 0, and no uncertain face needs the full Alg. 2: it is class 1
-        // when |M| <= D, else class 0.  M = det(n_a - q, n_b - q).
-        bool fast = false;
-#pragma unroll
-        for (int c = 0; c < 2 && !fast; ++c) {
-            const int x0 = c ? qv.y : qv.x;
-            if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
-            bool ok = true;
-#pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                const int m = is_uncertain(k) ? E : 0, x = c ? nb[k].y : nb[k].x;
-                const bool same = x0 > 0 ? x > m : x < -m;
-                ok &= !((valid >> k) & 1u) || same;
+            for (int o = 0; o < 8; ++o) {
+                const int ot = t + kOwners[o].dt, oi = i + kOwners[o].di, oj = j + kOwners[o].dj;
+                if (ot >= 0 && oi >= 0 && oj >= 0)
+                    crossed |= (__ldg(mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
             }
-            fast = ok;
-        }
-        if (fast) {
-            // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
-            int dx[14], dy[14], l1[14];
+            int xi = 0;
+            unsigned um_m = 0;
+            if (!crossed && eps_int > 0) {
+                xi = eps_int;
+                const unsigned valid = nb_valid(H, W, T, t, i, j);
+                int2 nb[14];
+                load_nb(q, v, sl, W, valid, nb);
+                const int2 qv = __ldg(q + v);
+                const int E = 1 << (31 - __clz(eps_int));
+                // Fast path (exact): every existing neighbour keeps the vertex's
+                // strict sign of u (or of v), with margin E where its value may
+                // still change, and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on
+                // every face unless M = 0, and no uncertain face needs the full
+                // Alg. 2: it is class 1 when |M| <= D, else class 0.
+                // M = det(n_a - q, n_b - q).
+                bool fast = false;
 #pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                dx[k] = nb[k].x - qv.x;
-                dy[k] = nb[k].y - qv.y;
-                l1[k] = abs(dx[k]) + abs(dy[k]);
-            }
-            bool mz = false;
+                for (int c = 0; c < 2 && !fast; ++c) {
+                    const int x0 = c ? qv.y : qv.x;
+                    if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
+                    bool ok = true;
+#pragma unroll
+                    for (int k = 0; k < 14; ++k) {
+                        const int m = is_uncertain(k) ? E : 0, x = c ? nb[k].y : nb[k].x;
+                        const bool same = x0 > 0 ? x > m : x < -m;
+                        ok &= !((valid >> k) & 1u) || same;
+                    }
+                    fast = ok;
+                }
+                if (fast) {
+                    // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
+                    int dx[14], dy[14], l1[14];
+#pragma unroll
+                    for (int k = 0; k < 14; ++k) {
+                        dx[k] = nb[k].x - qv.x;
+                        dy[k] = nb[k].y - qv.y;
+                        l1[k] = abs(dx[k]) + abs(dy[k]);
+                    }
+                    bool mz = false;
 #define CPT_CERT_M(a, b) \
     mz |= ((valid >> (a)) & (valid >> (b)) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b];
-            CPT_CERT_FACES(CPT_CERT_M)
+                    CPT_CERT_FACES(CPT_CERT_M)
 #undef CPT_CERT_M
-            if (mz) {
-                xi = 0;
-            } else {
-                const int lg = 31 - __clz(E);
-                int bit = 0;
+                    if (mz) {
+                        xi = 0;
+                    } else {
+                        const int lg = 31 - __clz(E);
+                        int bit = 0;
 #define CPT_UNC_FAST(a, b)                                                                                  \
     if ((valid >> (a)) & (valid >> (b)) & 1u) {                                                             \
         long long M = (long long)dx[a] * dy[b] - (long long)dy[a] * dx[b];                                  \
@@ -172,22 +202,46 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
         if (M <= D) um_m |= 1u << bit;                                                                      \
     }                                                                                                       \
     ++bit;
-                CPT_UNC_FACES(CPT_UNC_FAST)
+                        CPT_UNC_FACES(CPT_UNC_FAST)
 #undef CPT_UNC_FAST
+                    }
+                } else {
+                    slow = true;
+                }
             }
-        } else {
-            CPT_CERT_FACES(CPT_FACE)
-            if (xi > 0) {
-                int bit = 0;
-                CPT_UNC_FACES(CPT_UNC_MARK)
-            }
+            if (!slow) store_cls(out, out_m, qd, q, H, W, t, i, j, v, xi, 0u, um_m);
+        }
+        // queue the slow vertices of the warp (one shared atomic per warp)
+        const unsigned bal = __ballot_sync(0xffffffffu, slow);
+        if (bal) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s_nslow, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (slow) s_slow[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(rr * 32 + lane);
         }
     }
-    // strip-diagonal position of (t, i, j): strip i / 32, step j + i % 32, lane i % 32
-    const size_t dv = (((size_t)t * ((H + 31) >> 5) + (i >> 5)) * (size_t)(W + 31) + (j + (i & 31))) * 32 + (i & 31);
-    out[dv] = make_int2(xi, (int)um_full);
-    out_m[dv] = um_m;
-    qd[dv] = __ldg(q + v);
+    __syncthreads();
+    // the full Alg. 2 over the 12 certain faces and the classes of the 24
+    // uncertain ones for the queued vertices, one per thread
+    const int nslow = s_nslow;
+    for (int k = threadIdx.x; k < nslow; k += blockDim.x) {
+        const unsigned e = s_slow[k];
+        const int i = ib + (int)(e >> 5), jj = blockIdx.x * 32 + (int)(e & 31u);
+        const size_t v = ((size_t)t * H + i) * W + jj;
+        const unsigned valid = nb_valid(H, W, T, t, i, jj);
+        int2 nb[14];
+        load_nb(q, v, sl, W, valid, nb);
+        const int2 qv = __ldg(q + v);
+        const int E = 1 << (31 - __clz(eps_int));
+        int xi = eps_int;
+        unsigned um_full = 0, um_m = 0;
+        CPT_CERT_FACES(CPT_FACE)
+        if (xi > 0) {
+            int bit = 0;
+            CPT_UNC_FACES(CPT_UNC_MARK)
+        }
+        store_cls(out, out_m, qd, q, H, W, t, i, jj, v, xi, um_full, um_m);
+    }
 }
 
 __device__ __forceinline__ unsigned warp_wait_geq(const SliceArgs& a, const unsigned* flag, unsigned target) {
@@ -531,6 +585,14 @@ __device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, 
     __syncwarp();
 }
 
+// The semi-Lagrangian prediction of vertex (i, j): the fixed-point midpoint
+// variant when the CFL numbers allow it (same result, fewer FP64 operations).
+template <class Slice>
+__device__ __forceinline__ int sl_pred(const SliceArgs& a, const Slice& P, int i, int j, int& pu, int& pv) {
+    if (a.sl_fbx >= 0) return sl_predict_fix(P, a.H, a.W, i, j, a.sl_fbx, a.sl_fby, a.cfl_x, a.cfl_y, pu, pv);
+    return sl_predict(P, a.H, a.W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+}
+
 // One prep unit: the U x U vertices from (r0, c0) of slice t >= 1 (it enters
 // the ready queue once slice t-1 is reconstructed around it).  Leaves in psl
 // the SL prediction of every vertex that uses SL, and with MoP the marker
@@ -667,8 +729,7 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             const int li = fr + (k / nc) * st, lj = fc + (k % nc) * st;
             const int i = r0 + li, j = c0 + lj;
             int pu, pv;
-            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
-                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+            const int md = staged ? sl_pred(a, Ps, i, j, pu, pv) : sl_pred(a, Pg, i, j, pu, pv);
             const int2 p = make_int2(pu, pv);
             if (mop) ps.psl[li][lj] = p;
             Psl[(size_t)i * W + j] = p;
@@ -703,8 +764,7 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             const unsigned v = ps.list[m];
             const int i = r0 + (int)(v >> 5), j = c0 + (int)(v & 31u);
             int pu, pv;
-            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
-                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+            const int md = staged ? sl_pred(a, Ps, i, j, pu, pv) : sl_pred(a, Pg, i, j, pu, pv);
             Psl[(size_t)i * W + j] = make_int2(pu, pv);
             sub += md > 0;
             steps += md;
@@ -1176,7 +1236,7 @@ void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s) {
 
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, int2* qd, cudaStream_t s) {
-    dim3 grid((W + 31) / 32, (H + 7) / 8, T);
+    dim3 grid((W + 31) / 32, (H + kClsRows - 1) / kClsRows, T);
     classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m, qd);
 }
 

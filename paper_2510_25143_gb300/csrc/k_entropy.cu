@@ -99,57 +99,134 @@ void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long
 // ---------------------------------------------------------------------------
 // compaction of Q_d (2 symbols per vertex with a nonzero bound code) and L_d
 // (both values of a lossless vertex, or the value of an unpredictable
-// component), counts packed as (n_qd << 32) | n_ld
+// component), counts packed as (n_qd << 32) | n_ld.  Tiles of kCmpTile
+// vertices: one pass counts per tile, a scan of the tile counts gives each
+// tile's offsets, and the scatter pass recounts its tile with a block scan.
+// q is read only for the values that go to L_d.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) count_pack_kernel(const uint8_t* __restrict__ qxi,
-                                                         const uint32_t* __restrict__ sym, size_t N,
-                                                         unsigned long long* __restrict__ cnt) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        unsigned long long c;
-        if (qxi[v]) {
-            uint32_t s = sym[v];
-            c = (2ull << 32) | (unsigned long long)(((s & 0xFFFFu) == 0) + ((s >> 16) == 0));
-        } else {
-            c = 2ull;
+constexpr int kCmpThreads = 256;
+constexpr int kCmpPer = 16;
+constexpr int kCmpTile = kCmpThreads * kCmpPer;  // 4096 vertices
+
+__device__ __forceinline__ unsigned long long vertex_count(unsigned code, uint32_t s) {
+    return code ? (2ull << 32) | (unsigned long long)(((s & 0xFFFFu) == 0) + ((s >> 16) == 0)) : 2ull;
+}
+
+// the 16 consecutive vertices of a thread: codes and symbols (zero past N)
+__device__ __forceinline__ void load16(const uint8_t* __restrict__ qxi, const uint32_t* __restrict__ sym, size_t N,
+                                       size_t base, unsigned char c[kCmpPer], uint32_t s[kCmpPer]) {
+    if (base + kCmpPer <= N) {
+        const uint4 cv = __ldcs(reinterpret_cast<const uint4*>(qxi + base));
+        const unsigned cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int k = 0; k < kCmpPer; ++k) c[k] = (unsigned char)(cw[k >> 2] >> (8 * (k & 3)));
+#pragma unroll
+        for (int k = 0; k < kCmpPer; k += 4) {
+            const uint4 sv = __ldcs(reinterpret_cast<const uint4*>(sym + base + k));
+            s[k] = sv.x;
+            s[k + 1] = sv.y;
+            s[k + 2] = sv.z;
+            s[k + 3] = sv.w;
         }
-        cnt[v] = c;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kCmpPer; ++k) {
+            const bool ok = base + k < N;
+            c[k] = ok ? qxi[base + k] : (unsigned char)0;
+            s[k] = ok ? sym[base + k] : 0u;
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(const uint8_t* __restrict__ qxi, const uint32_t* __restrict__ sym,
-                                                      const int2* __restrict__ q,
-                                                      const unsigned long long* __restrict__ off, size_t N,
-                                                      uint16_t* __restrict__ qd, int32_t* __restrict__ ld) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        unsigned long long o = off[v];
-        size_t pq = (size_t)(o >> 32), pl = (size_t)(o & 0xFFFFFFFFull);
-        int2 x = q[v];
-        if (qxi[v]) {
-            uint32_t s = sym[v];
-            uint16_t su = (uint16_t)(s & 0xFFFFu), sv = (uint16_t)(s >> 16);
+__global__ void __launch_bounds__(kCmpThreads) tile_count_kernel(const uint8_t* __restrict__ qxi,
+                                                                 const uint32_t* __restrict__ sym, size_t N,
+                                                                 unsigned long long* __restrict__ tile_cnt) {
+    __shared__ unsigned long long wt[32], tot;
+    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    unsigned char c[kCmpPer];
+    uint32_t sy[kCmpPer];
+    load16(qxi, sym, N, base, c, sy);
+    unsigned long long n = 0;
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k)
+        if (base + k < N) n += vertex_count(c[k], sy[k]);
+    block_exclusive_scan(n, wt, &tot);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kCmpThreads) tile_scatter_kernel(const uint8_t* __restrict__ qxi,
+                                                                   const uint32_t* __restrict__ sym,
+                                                                   const int2* __restrict__ q,
+                                                                   const unsigned long long* __restrict__ tile_off,
+                                                                   size_t N, uint16_t* __restrict__ qd,
+                                                                   int32_t* __restrict__ ld) {
+    __shared__ unsigned long long wt[32], tot;
+    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    unsigned char c[kCmpPer];
+    uint32_t sy[kCmpPer];
+    load16(qxi, sym, N, base, c, sy);
+    unsigned long long n = 0;
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k)
+        if (base + k < N) n += vertex_count(c[k], sy[k]);
+    const unsigned long long o = block_exclusive_scan(n, wt, &tot) + tile_off[blockIdx.x];
+    size_t pq = (size_t)(o >> 32), pl = (size_t)(o & 0xFFFFFFFFull);
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k) {
+        const size_t v = base + k;
+        if (v >= N) break;
+        if (c[k]) {
+            const uint16_t su = (uint16_t)(sy[k] & 0xFFFFu), sv = (uint16_t)(sy[k] >> 16);
             qd[pq] = su;
             qd[pq + 1] = sv;
-            if (su == 0) ld[pl++] = x.x;
-            if (sv == 0) ld[pl] = x.y;
+            pq += 2;
+            if (su == 0) ld[pl++] = __ldg(q + v).x;
+            if (sv == 0) ld[pl++] = __ldg(q + v).y;
         } else {
+            const int2 x = __ldg(q + v);
             ld[pl] = x.x;
             ld[pl + 1] = x.y;
+            pl += 2;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// histograms
+// histograms: each thread reads 16 bytes at a time and adds runs of equal
+// symbols with one shared-memory atomic per run
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) hist_u8_kernel(const uint8_t* __restrict__ x, size_t n,
                                                       unsigned* __restrict__ hist) {
-    __shared__ unsigned h[64];
-    if (threadIdx.x < 64) h[threadIdx.x] = 0;
+    __shared__ unsigned h[4][64];  // one copy per pair of warps
+    for (int k = threadIdx.x; k < 4 * 64; k += blockDim.x) h[k >> 6][k & 63] = 0;
     __syncthreads();
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-        atomicAdd(&h[x[k] & 63], 1u);
+    unsigned* hh = h[(threadIdx.x >> 6) & 3];
+    unsigned cur = 0, cnt = 0;
+    auto add = [&](unsigned b) {
+        if (b == cur) {
+            ++cnt;
+        } else {
+            if (cnt) atomicAdd(&hh[cur & 63], cnt);
+            cur = b;
+            cnt = 1;
+        }
+    };
+    const size_t n16 = n / 16;
+    const uint4* x4 = reinterpret_cast<const uint4*>(x);
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n16; k += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcs(x4 + k);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) add((w[e >> 2] >> (8 * (e & 3))) & 0xFFu);
+    }
+    if (blockIdx.x == 0)
+        for (size_t k = 16 * n16 + threadIdx.x; k < n; k += blockDim.x) add(x[k]);
+    if (cnt) atomicAdd(&hh[cur & 63], cnt);
     __syncthreads();
-    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x < 33) {
+        const unsigned t = h[0][threadIdx.x] + h[1][threadIdx.x] + h[2][threadIdx.x] + h[3][threadIdx.x];
+        if (t) atomicAdd(&hist[threadIdx.x], t);
+    }
 }
 
 constexpr int kHistWin = 8192;  // privatised bins around the zero residual symbol
@@ -160,24 +237,64 @@ __global__ void __launch_bounds__(512) hist_u16_kernel(const uint16_t* __restric
     for (int k = threadIdx.x; k < kHistWin; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const int lo = kRadius - kHistWin / 2;
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        int s = x[k];
-        unsigned r = (unsigned)(s - lo);
-        if (r < (unsigned)kHistWin) atomicAdd(&h[r], 1u);
-        else atomicAdd(&hist[s], 1u);
+    unsigned cur = 0, cnt = 0;
+    auto flush = [&]() {
+        if (!cnt) return;
+        const unsigned r = cur - (unsigned)lo;
+        if (r < (unsigned)kHistWin) atomicAdd(&h[r], cnt);
+        else atomicAdd(&hist[cur], cnt);
+    };
+    auto add = [&](unsigned sy) {
+        if (sy == cur) {
+            ++cnt;
+        } else {
+            flush();
+            cur = sy;
+            cnt = 1;
+        }
+    };
+    const size_t n8 = n / 8;
+    const uint4* x4 = reinterpret_cast<const uint4*>(x);
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n8; k += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcs(x4 + k);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) add((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
     }
+    if (blockIdx.x == 0)
+        for (size_t k = 8 * n8 + threadIdx.x; k < n; k += blockDim.x) add(x[k]);
+    flush();
     __syncthreads();
     for (int k = threadIdx.x; k < kHistWin; k += blockDim.x)
         if (h[k]) atomicAdd(&hist[lo + k], h[k]);
+}
+
+// per-vertex counts (the decoder's layout of the verbatim values needs each
+// vertex's offset)
+__global__ void __launch_bounds__(256) count_pack_kernel(const uint8_t* __restrict__ qxi,
+                                                         const uint32_t* __restrict__ sym, size_t N,
+                                                         unsigned long long* __restrict__ cnt) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x)
+        cnt[v] = vertex_count(qxi[v], qxi[v] ? sym[v] : 0u);
 }
 
 void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s) {
     count_pack_kernel<<<1216, 256, 0, s>>>(qxi, sym, N, cnt);
 }
 
-void launch_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q, const unsigned long long* off,
-                    size_t N, uint16_t* qd_out, int32_t* ld_out, cudaStream_t s) {
-    scatter_kernel<<<1216, 256, 0, s>>>(qxi, sym, reinterpret_cast<const int2*>(q), off, N, qd_out, ld_out);
+size_t compact_tiles(size_t N) { return (N + kCmpTile - 1) / kCmpTile; }
+
+void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* tile_cnt,
+                       cudaStream_t s) {
+    if (N) tile_count_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(qxi, sym, N, tile_cnt);
+}
+
+void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q,
+                         const unsigned long long* tile_off, size_t N, uint16_t* qd_out, int32_t* ld_out,
+                         cudaStream_t s) {
+    if (N)
+        tile_scatter_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(
+            qxi, sym, reinterpret_cast<const int2*>(q), tile_off, N, qd_out, ld_out);
 }
 
 void launch_hist_u8(const uint8_t* x, size_t n, unsigned* hist, cudaStream_t s) {

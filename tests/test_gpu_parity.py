@@ -73,6 +73,17 @@ def test_sl_nonunit_spacing_and_host_input():
     compare(uv, 2e-2, "sl", dx=0.5, dy=2.0, dt=3.0, host_input=True)
 
 
+@pytest.mark.parametrize("spacing", [(0.5, 0.25, 1.0), (0.125, 0.125, 1.0), (1.0, 1.0, 2.0)])
+def test_sl_power_of_two_spacing(spacing):
+    """CFL numbers that are powers of two take the fixed-point midpoint of the
+    semi-Lagrangian back-trace (exact, so the same predictions); large ones
+    make the back-trace take Euler substeps."""
+    dx, dy, dt = spacing
+    uv = synth.vortex_sum(40, 52, 5, seed=9, drift=1.5)
+    compare(uv, 1e-2, "sl", dx=dx, dy=dy, dt=dt)
+    compare(uv, 1e-2, "mop", dx=dx, dy=dy, dt=dt, block=8)
+
+
 def test_mop_block8_stride3():
     uv = synth.vortex_sum(50, 61, 5, seed=4)
     compare(uv, 1e-2, "mop", block=8, stride=3)
