@@ -120,6 +120,16 @@ typedef struct {
                              * encoded again, up to 3 rounds (reading R14 of the verification
                              * policy the paper leaves open); the stream returned then verifies.
                              * The slices before the earliest forced vertex encode as before. */
+    uint64_t device_budget; /* 0 = no limit; else the device bytes the call may allocate (the
+                             * caller's input not counted).  A field whose working set (about
+                             * 90 B per vertex) exceeds it is compressed slab by slab: a window of
+                             * S + 2 slices (S chosen from the budget, about 70 B per vertex of a
+                             * slice) holds the slab, the reconstructed slice before it and the
+                             * original slice after it; the bound and residual codes of each
+                             * slab go to host memory and the Huffman streams are built from
+                             * them in chunks.  The stream is byte for byte the stream of the
+                             * in-memory call.  Not with cpt_debug outputs or repair
+                             * (CPT_ERR_UNSUPPORTED); CPT_ERR_OOM when one slice does not fit. */
 } cpt_params;
 
 /* Statistics of one compression.  ms_stage (CUDA-event time on the library's

@@ -32,7 +32,7 @@ class Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("eb", C.c_double), ("pred", C.c_int), ("block", C.c_int32),
                 ("stride", C.c_int32), ("verify", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("model", C.c_void_p), ("tune", C.c_int32), ("schedule", C.c_int32 * 6),
-                ("zstd_level", C.c_int32), ("repair", C.c_int32)]
+                ("zstd_level", C.c_int32), ("repair", C.c_int32), ("device_budget", C.c_uint64)]
 
 
 class BatchStats(C.Structure):
@@ -178,22 +178,26 @@ class Stream:
             self._ptr = None
 
 
-def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd=0, repair=False):
+def _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd=0, repair=False,
+            device_budget=0):
     sch = (C.c_int32 * 6)(*(tuple(schedule or ()) + (0,) * 6)[:6])
     return Params(EB_MODE[eb_mode], float(eb), PRED[pred], block, stride, 1 if verify else 0, stream,
-                  None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch, int(zstd), 1 if repair else 0)
+                  None if mdl is None else mdl.ctypes.data, 1 if tune else 0, sch, int(zstd), 1 if repair else 0,
+                  int(device_budget))
 
 
 def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verify=True, stream=None,
              dx=1.0, dy=1.0, dt=1.0, debug=False, check=True, copy=True, model=None, tune=False,
-             schedule=None, rates=False, zstd=0, repair=False):
+             schedule=None, rates=False, zstd=0, repair=False, device_budget=0):
     """Compresses float32 uv [T][H][W][2] (numpy array or torch tensor, host
     or device).  Returns (bytes, stats dict, debug dict or None); with
     copy=False the stream comes back as a Stream over the library's buffer.
     pred="learned" and "learned_mop" need `model`: uint16 [NET_PARAMS]
     bfloat16 bits.  zstd=L > 0 returns the stream wrapped in a ZSTD frame
     (level L, host side).  repair=True stores the vertices of faces a failed
-    verification reports losslessly and encodes again.  tune=True lets the
+    verification reports losslessly and encodes again.  device_budget=B > 0
+    compresses slab by slab when the field's working set exceeds B bytes of
+    device memory (same stream).  tune=True lets the
     library pick the encoder pipeline's
     schedule; schedule=(prep_share, sl_unit, slice_weight, slack, warps_per_sm)
     fixes it (zeros: defaults).
@@ -204,7 +208,8 @@ def compress(uv, eb, *, eb_mode="rel", pred="lorenzo", block=16, stride=2, verif
         stream = dev_stream
     dims = Dims(H, W, T, dx, dy, dt)
     mdl = None if model is None else _model_array(model)
-    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd, repair)
+    prm = _params(eb, eb_mode, pred, block, stride, verify, stream, mdl, tune, schedule, zstd, repair,
+                  device_budget)
     out = C.POINTER(C.c_uint8)()
     n = C.c_size_t(0)
     st = Stats()

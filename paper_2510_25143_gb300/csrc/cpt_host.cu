@@ -447,6 +447,21 @@ static const PipeTuning kDecodeSchedule = {0, 0, 0, 0, 0, 0};
 // ---------------------------------------------------------------------------
 // compression (Alg. 3)
 // ---------------------------------------------------------------------------
+// Argument checks shared by the in-memory and the slab-by-slab compressor.
+static cpt_status check_args(const cpt_dims& d, const cpt_params* prm) {
+    if (d.H < 2 || d.W < 2 || d.T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
+    if ((long long)d.H * d.W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
+    if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
+    if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_LEARNED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+    const bool net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
+    const bool modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
+    if (net && !prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
+    const int B = prm->block > 0 ? prm->block : 16;
+    if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
+    if (modes && (32 % B != 0 || B < 4)) return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
+    return CPT_OK;
+}
+
 // Failure injection for tests (per host thread): the next compression adds
 // delta to the u component of one reconstructed vertex before verification.
 struct VerifyFault {
@@ -532,17 +547,12 @@ struct FieldJob {
     cpt_status begin(int nsm) {
         if (!uv) return fail(CPT_ERR_ARG, "null argument");
         H = dims.H; W = dims.W; T = dims.T;
-        if (H < 2 || W < 2 || T < 1) return fail(CPT_ERR_ARG, "need H >= 2, W >= 2, T >= 1");
-        if ((long long)H * W > (1ll << 31) / 4) return fail(CPT_ERR_ARG, "slice too large");
-        if (!(prm->eb >= 0) || !std::isfinite(prm->eb)) return fail(CPT_ERR_ARG, "error bound must be finite and >= 0");
-        if (prm->pred < CPT_PRED_LORENZO || prm->pred > CPT_PRED_LEARNED_MOP) return fail(CPT_ERR_ARG, "unknown predictor");
+        const cpt_status ca = check_args(dims, prm);
+        if (ca != CPT_OK) return ca;
         has_net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
         has_modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
-        if (has_net && !prm->model) return fail(CPT_ERR_ARG, "the learned predictor needs a model");
         B = prm->block > 0 ? prm->block : 16;
         nstride = prm->stride > 0 ? prm->stride : 2;
-        if (B < 2 || B > 32) return fail(CPT_ERR_ARG, "block side must be in [2, 32]");
-        if (has_modes && (32 % B != 0 || B < 4)) return fail(CPT_ERR_UNSUPPORTED, "MoP block side must be 4, 8, 16 or 32");
         dx = dims.dx > 0 ? dims.dx : 1.0;
         dy = dims.dy > 0 ? dims.dy : 1.0;
         dt = dims.dt > 0 ? dims.dt : 1.0;
@@ -634,6 +644,7 @@ struct FieldJob {
         A.xi_out = d_xiout;
         A.counters = d_cnt64 + 1;
         A.H = H; A.W = W; A.T = T;
+        A.t_end = T;
         A.eps_int = eps_int;
         A.pred = (int)prm->pred;
         A.B = B; A.n = nstride; A.nby = nby; A.nbx = nbx;
@@ -1300,11 +1311,46 @@ static PipeTuning tuning_of(const cpt_params* prm) {
                       prm->schedule[5]};
 }
 
+static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
+                                    size_t* out_bytes, cpt_stats* stats);
+
 static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
                                 size_t* out_bytes, cpt_stats* stats, const cpt_debug* dbg) {
     if (!uv || !dims || !prm || !out || !out_bytes) return fail(CPT_ERR_ARG, "null argument");
     cpt_status rc = check_device();
     if (rc != CPT_OK) return rc;
+    if (prm->device_budget > 0) {
+        rc = check_args(*dims, prm);
+        if (rc != CPT_OK) return rc;
+        if (FieldJob::device_bytes(*dims, !is_device_pointer(uv)) > prm->device_budget) {
+            // the field's working set exceeds the budget: slab by slab
+            if (dbg || prm->repair) return fail(CPT_ERR_UNSUPPORTED, "debug outputs and repair need the in-memory call");
+            *out = nullptr;
+            *out_bytes = 0;
+            cudaEvent_t a0, a1;
+            CPT_CUDA(cudaEventCreate(&a0));
+            CPT_CUDA(cudaEventCreate(&a1));
+            cudaStream_t st = static_cast<cudaStream_t>(prm->cuda_stream);
+            CPT_CUDA(cudaEventRecord(a0, st));
+            rc = compress_streamed(uv, dims, prm, out, out_bytes, stats);
+            cudaEventRecord(a1, st);
+            cudaEventSynchronize(a1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a0, a1);
+            cudaEventDestroy(a0);
+            cudaEventDestroy(a1);
+            if (stats) stats->ms_total = ms;
+            if (rc != CPT_OK && rc != CPT_ERR_VERIFY) return rc;
+            const cpt_status rz = wrap_output(prm, out, out_bytes, stats, (size_t)dims->H * dims->W * dims->T * 8);
+            if (rz != CPT_OK) {
+                cpt_free(*out);
+                *out = nullptr;
+                *out_bytes = 0;
+                return rz;
+            }
+            return rc;
+        }
+    }
     cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
     cudaEvent_t ev0, ev1;
     CPT_CUDA(cudaEventCreate(&ev0));
@@ -1377,6 +1423,545 @@ static cpt_status compress_impl(const float* uv, const cpt_dims* dims, const cpt
         return rz;
     }
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Slab-by-slab compression (cpt_params.device_budget below a field's working
+// set).  Alg. 3 encodes slice t from slices t-1, t and t+1 only, so the field
+// is encoded in slabs of S slices [t0, t1) inside a window of slices
+// [t0 - 1, t1]: the reconstruction of slice t0 - 1 (carried from the previous
+// slab, with its crossed-face masks), the slab, and the original slice t1.
+// The encoder pipeline runs the slab's slices only (SliceArgs::t_end; the
+// prediction units of the window's first encoded slice are queued before the
+// launch).  Each slab's bound codes, residual symbols and verbatim values go
+// to host memory; the histograms add up on the device.  The Huffman streams
+// are then built from the host codes in chunks of tiles (tile bit counts,
+// one host scan, the words), and laid out exactly as in the in-memory call.
+// ---------------------------------------------------------------------------
+static constexpr size_t kStreamBytesPerVertexSlice = 72;  // window bytes per vertex of one window slice
+static constexpr size_t kStreamChunkSyms = (size_t)1 << 24;  // symbols per entropy chunk (a multiple of the tiles)
+
+struct StreamedField {
+    // inputs
+    const float* uv;
+    cpt_dims dims;
+    const cpt_params* prm;
+    cudaStream_t s;
+    int S;  // slices per slab
+    // derived
+    int H = 0, W = 0, T = 0, B = 16, nstride = 2;
+    double dx = 1, dy = 1, dt = 1;
+    size_t HW = 0, N = 0;
+    bool has_net = false, has_modes = false, want_sl = false, dev_in = false;
+    int k = 0, eps_int = 0;
+    double eps = 0;
+    float mn = 0, mx = 0, am = 0;
+    int nby = 0, nbx = 0, nstrips = 0;
+    cpt_stats st{};
+};
+
+// the range of u and v over the field, slab by slab through a device buffer
+static cpt_status streamed_range(StreamedField& F, DevArena& ar, float* d_win) {
+    const int nsm = sm_count();
+    const int rblocks = nsm * 4;
+    RangePartial* d_part;
+    CPT_CUDA(ar.alloc(&d_part, rblocks));
+    std::vector<RangePartial> part(rblocks);
+    F.mn = INFINITY;
+    F.mx = -INFINITY;
+    F.am = 0.f;
+    unsigned bad = 0;
+    const int slab = F.S + 2;
+    for (int t0 = 0; t0 < F.T; t0 += slab) {
+        const int n = std::min(slab, F.T - t0);
+        const size_t nv = 2 * F.HW * n;
+        const float* src = F.uv + 2 * F.HW * t0;
+        const float* d_src = src;
+        if (!F.dev_in || (reinterpret_cast<uintptr_t>(src) & 15u)) {  // 16-byte aligned device copy
+            CPT_CUDA(cudaMemcpyAsync(d_win, src, nv * sizeof(float), cudaMemcpyDefault, F.s));
+            d_src = d_win;
+        }
+        launch_range(d_src, nv, d_part, rblocks, F.s);
+        CPT_CUDA(cudaMemcpyAsync(part.data(), d_part, sizeof(RangePartial) * rblocks, cudaMemcpyDeviceToHost, F.s));
+        CPT_CUDA(cudaStreamSynchronize(F.s));
+        for (const RangePartial& p : part) {
+            F.mn = std::min(F.mn, p.mn);
+            F.mx = std::max(F.mx, p.mx);
+            F.am = std::max(F.am, p.amax);
+            bad |= p.bad;
+        }
+    }
+    if (bad) return fail(CPT_ERR_ARG, "input holds a non-finite value");
+    return CPT_OK;
+}
+
+// The Huffman words of one stream from its host symbols, in chunks: tile bit
+// counts, one host scan, then each chunk's words (its two edge words OR-ed
+// with the neighbouring chunks').  Fills sp.nwords and sp.chunk_off (pass
+// 1) or the words (pass 2, words_h: the stream's word region in the output,
+// zeroed; any alignment).
+template <typename Sym>
+static cpt_status streamed_huffman(StreamPlan& sp, const Sym* sym_h, const uint32_t* d_table, Sym* d_chunk,
+                                   unsigned long long* d_tiles, uint32_t* d_words, std::vector<unsigned long long>& to,
+                                   uint8_t* words_h, cudaStream_t s) {
+    const size_t nt = (sp.nsym + kTileSyms - 1) / kTileSyms;
+    const size_t per_chunk_tiles = kStreamChunkSyms / kTileSyms;
+    if (!words_h) {  // pass 1: tile bit counts and their exclusive scan
+        to.assign(nt + 1, 0ull);
+        for (size_t c0 = 0; c0 < sp.nsym; c0 += kStreamChunkSyms) {
+            const size_t n = std::min(kStreamChunkSyms, sp.nsym - c0);
+            const size_t ntc = (n + kTileSyms - 1) / kTileSyms;
+            CPT_CUDA(cudaMemcpyAsync(d_chunk, sym_h + c0, n * sizeof(Sym), cudaMemcpyHostToDevice, s));
+            if (sizeof(Sym) == 1)
+                launch_tile_bits_u8(reinterpret_cast<const uint8_t*>(d_chunk), n, d_table, d_tiles, s);
+            else
+                launch_tile_bits_u16(reinterpret_cast<const uint16_t*>(d_chunk), n, d_table, d_tiles, s);
+            CPT_CUDA(cudaMemcpyAsync(to.data() + c0 / kTileSyms, d_tiles, ntc * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+        }
+        unsigned long long acc = 0;
+        for (size_t x = 0; x <= nt; ++x) {
+            const unsigned long long b = x < nt ? to[x] : 0ull;
+            to[x] = acc;
+            acc += b;
+        }
+        sp.nt = nt;
+        sp.nwords = (to[nt] + 31) / 32;
+        const size_t per_sync = kChunkSyms / kTileSyms;
+        sp.chunk_off.clear();
+        for (size_t c = 0; c * kChunkSyms < sp.nsym; ++c) sp.chunk_off.push_back(to[c * per_sync]);
+        return CPT_OK;
+    }
+    std::vector<unsigned long long> rel(per_chunk_tiles);
+    std::vector<uint32_t> buf;
+    for (size_t c0 = 0; c0 < sp.nsym; c0 += kStreamChunkSyms) {
+        const size_t n = std::min(kStreamChunkSyms, sp.nsym - c0);
+        const size_t tf = c0 / kTileSyms, ntc = (n + kTileSyms - 1) / kTileSyms;
+        const size_t wbase = (size_t)(to[tf] >> 5), wend = (size_t)((to[tf + ntc] + 31) >> 5);
+        if (wend <= wbase) continue;  // no bits in this chunk
+        for (size_t x = 0; x < ntc; ++x) rel[x] = to[tf + x] - 32ull * wbase;
+        CPT_CUDA(cudaMemcpyAsync(d_chunk, sym_h + c0, n * sizeof(Sym), cudaMemcpyHostToDevice, s));
+        CPT_CUDA(cudaMemcpyAsync(d_tiles, rel.data(), ntc * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+        CPT_CUDA(cudaMemsetAsync(d_words, 0, (wend - wbase + 1) * sizeof(uint32_t), s));
+        if (sizeof(Sym) == 1)
+            launch_encode_u8(reinterpret_cast<const uint8_t*>(d_chunk), n, d_table, d_tiles, d_words, s);
+        else
+            launch_encode_u16(reinterpret_cast<const uint16_t*>(d_chunk), n, d_table, d_tiles, d_words, s);
+        buf.resize(wend - wbase);
+        CPT_CUDA(cudaMemcpyAsync(buf.data(), d_words, buf.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        for (size_t x = 0; x < buf.size(); ++x) {
+            uint32_t w;
+            std::memcpy(&w, words_h + 4 * (wbase + x), 4);
+            w |= buf[x];
+            std::memcpy(words_h + 4 * (wbase + x), &w, 4);
+        }
+    }
+    return CPT_OK;
+}
+
+// After the slabs: code books from the summed histograms, the two Huffman
+// streams from the host codes, and the stream laid out as in the in-memory
+// call (FieldJob::write_stream); then the statistics and the verdict.
+static cpt_status streamed_finish(StreamedField& F, const cpt_params* prm, DevArena& ar, const unsigned* d_hist,
+                                  const unsigned long long* d_cnt64, const VerifyOut* d_vo,
+                                  const std::vector<uint8_t>& qxi_h, const std::vector<uint16_t>& qd_h,
+                                  const std::vector<int32_t>& ld_h, const std::vector<uint8_t>& modes_h,
+                                  uint8_t** out, size_t* out_bytes, cpt_stats* stats) {
+    cudaStream_t s = F.s;
+    std::vector<unsigned> hist(33 + 2 * kRadius);
+    unsigned long long cnt[8];
+    VerifyOut vo;
+    CPT_CUDA(cudaMemcpyAsync(hist.data(), d_hist, sizeof(unsigned) * hist.size(), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaMemcpyAsync(cnt, d_cnt64, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaMemcpyAsync(&vo, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
+    CPT_CUDA(cudaStreamSynchronize(s));
+    StreamPlan sx, sd;
+    sx.nsym = F.N;
+    sx.alphabet = 33;
+    sd.nsym = qd_h.size();
+    sd.alphabet = 2 * kRadius;
+    std::vector<uint32_t> tab(33 + 2 * kRadius);
+    if (!build_codebook(sx, hist.data(), tab.data()) || !build_codebook(sd, hist.data() + 33, tab.data() + 33))
+        return fail(CPT_ERR_ARG, "alphabet too large for code length limit");
+    uint32_t *d_tab, *d_words;
+    uint16_t* d_chunk;
+    unsigned long long* d_tiles;
+    CPT_CUDA(ar.alloc(&d_tab, tab.size()));
+    CPT_CUDA(ar.alloc(&d_chunk, kStreamChunkSyms));
+    CPT_CUDA(ar.alloc(&d_tiles, kStreamChunkSyms / kTileSyms + 1));
+    CPT_CUDA(ar.alloc(&d_words, kStreamChunkSyms * kMaxCodeLen / 32 + 64));
+    CPT_CUDA(cudaMemcpyAsync(d_tab, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice, s));
+    std::vector<unsigned long long> tox, tod;
+    cpt_status rc = streamed_huffman<uint8_t>(sx, qxi_h.data(), d_tab, reinterpret_cast<uint8_t*>(d_chunk), d_tiles,
+                                              d_words, tox, nullptr, s);
+    if (rc == CPT_OK)
+        rc = streamed_huffman<uint16_t>(sd, qd_h.data(), d_tab + 33, d_chunk, d_tiles, d_words, tod, nullptr, s);
+    if (rc != CPT_OK) return rc;
+    // block modes as bits
+    const size_t nblk = modes_h.size(), mode_bytes = (nblk + 7) / 8;
+    std::vector<uint8_t> packed(mode_bytes, 0);
+    cpt_stats& st = F.st;
+    for (size_t x = 0; x < nblk; ++x)
+        if (modes_h[x]) {
+            packed[x >> 3] |= (uint8_t)(1u << (x & 7));
+            ++st.sl_blocks;
+        }
+    // layout: header | mode bits | model | stream Q_xi | stream Q_d | L_d
+    const size_t kHeaderBytes = 4 + 11 * 4 + 4 * 8 + 8 + 8;
+    const size_t model_bytes = F.has_net ? 4 + 4 * (size_t)((kNetParams + 1) / 2) : 0;
+    const size_t off_x = kHeaderBytes + mode_bytes + model_bytes;
+    const size_t off_xw = off_x + sx.header_bytes();
+    const size_t off_d = off_xw + 4 * sx.nwords;
+    const size_t off_dw = off_d + sd.header_bytes();
+    const size_t off_ld = off_dw + 4 * sd.nwords;
+    const size_t n_ld = ld_h.size();
+    const size_t total = off_ld + 4 * n_ld;
+    uint8_t* obuf = static_cast<uint8_t*>(pinned_pool().get(total));
+    const bool pinned = obuf != nullptr;
+    if (!obuf) obuf = static_cast<uint8_t*>(std::malloc(total));
+    if (!obuf) return fail(CPT_ERR_OOM, "host allocation failed");
+    auto release = [&]() {
+        if (!(pinned && pinned_pool().put(obuf))) std::free(obuf);
+    };
+    Writer w{obuf};
+    w.raw("CPT1", 4);
+    w.u32(kFormat);
+    w.u32((uint32_t)F.H);
+    w.u32((uint32_t)F.W);
+    w.u32((uint32_t)F.T);
+    w.u32((uint32_t)F.k);
+    w.u32((uint32_t)F.eps_int);
+    w.u32((uint32_t)prm->pred);
+    w.u32((uint32_t)F.B);
+    w.u32((uint32_t)F.nstride);
+    w.u32((uint32_t)kRadius);
+    w.u32(0);
+    w.f64(F.dx);
+    w.f64(F.dy);
+    w.f64(F.dt);
+    w.f64(F.eps);
+    w.u64(n_ld);
+    w.u64(mode_bytes);
+    if (mode_bytes) w.raw(packed.data(), mode_bytes);
+    if (model_bytes) {
+        w.u32((uint32_t)kNetParams);
+        for (int x = 0; x < kNetParams; x += 2)
+            w.u32((uint32_t)prm->model[x] | (x + 1 < kNetParams ? (uint32_t)prm->model[x + 1] << 16 : 0u));
+    }
+    write_stream_header(w, sx);
+    std::memset(obuf + off_xw, 0, 4 * sx.nwords);
+    w.n = off_d;
+    write_stream_header(w, sd);
+    std::memset(obuf + off_dw, 0, 4 * sd.nwords);
+    if (w.n != off_dw) {
+        release();
+        return fail(CPT_ERR_ARG, "internal: stream layout");
+    }
+    rc = streamed_huffman<uint8_t>(sx, qxi_h.data(), d_tab, reinterpret_cast<uint8_t*>(d_chunk), d_tiles, d_words,
+                                   tox, obuf + off_xw, s);
+    if (rc == CPT_OK)
+        rc = streamed_huffman<uint16_t>(sd, qd_h.data(), d_tab + 33, d_chunk, d_tiles, d_words, tod, obuf + off_dw, s);
+    if (rc != CPT_OK) {
+        release();
+        return rc;
+    }
+    if (n_ld) std::memcpy(obuf + off_ld, ld_h.data(), 4 * n_ld);
+    // statistics, as FieldJob::finish
+    {
+        const unsigned long long Hl = F.H, Wl = F.W, Tl = F.T;
+        const unsigned long long E = Hl * (Wl - 1) + Wl * (Hl - 1) + (Hl - 1) * (Wl - 1);
+        st.faces = 2 * (Hl - 1) * (Wl - 1) * Tl + (Tl - 1) * (2 * E + 4 * (Hl - 1) * (Wl - 1));
+    }
+    st.crossed_faces = cnt[0];
+    st.blocks = F.has_modes ? (uint64_t)F.T * F.nby * F.nbx : 0;
+    st.n_ld = n_ld;
+    st.n_qd = sd.nsym;
+    st.out_bytes = total;
+    st.raw_bytes = total;
+    st.ratio = (double)(F.N * 8) / (double)total;
+    st.verify_mismatch_slice = vo.mismatch_slice;
+    st.verify_mismatch_slab = vo.mismatch_slab;
+    double linf;
+    std::memcpy(&linf, &vo.linf_bits, 8);
+    st.linf = linf;
+    if (prm->verify) {
+        const double mse = vo.sq_err / (double)(2 * F.N);
+        const double range = (double)F.mx - (double)F.mn;
+        st.psnr = mse > 0 ? 20.0 * std::log10(range) - 10.0 * std::log10(mse) : INFINITY;
+    }
+    st.lossless_vertices = F.N - sd.nsym / 2;
+    st.unpredictable = n_ld - 2 * st.lossless_vertices;
+    if (stats) *stats = st;
+    *out = obuf;
+    *out_bytes = total;
+    const double bound = std::max(F.eps, std::ldexp(0.5, -F.k));
+    if (prm->verify && (vo.mismatch_slice || vo.mismatch_slab || !(linf <= bound)))
+        return fail(CPT_ERR_VERIFY, "reconstruction changed a face predicate or exceeded the bound");
+    return CPT_OK;
+}
+
+static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const cpt_params* prm, uint8_t** out,
+                                    size_t* out_bytes, cpt_stats* stats) {
+    cudaStream_t s = static_cast<cudaStream_t>(prm->cuda_stream);
+    StreamedField F;
+    F.uv = uv;
+    F.dims = *dims;
+    F.prm = prm;
+    F.s = s;
+    F.H = dims->H;
+    F.W = dims->W;
+    F.T = dims->T;
+    const int H = F.H, W = F.W, T = F.T;
+    F.HW = (size_t)H * W;
+    F.N = F.HW * T;
+    F.has_net = prm->pred == CPT_PRED_LEARNED || prm->pred == CPT_PRED_LEARNED_MOP;
+    F.has_modes = prm->pred == CPT_PRED_MOP || prm->pred == CPT_PRED_LEARNED_MOP;
+    F.B = prm->block > 0 ? prm->block : 16;
+    F.nstride = prm->stride > 0 ? prm->stride : 2;
+    F.dx = dims->dx > 0 ? dims->dx : 1.0;
+    F.dy = dims->dy > 0 ? dims->dy : 1.0;
+    F.dt = dims->dt > 0 ? dims->dt : 1.0;
+    F.dev_in = is_device_pointer(uv);
+    const int B = F.B;
+    // the slab: what fits the budget after the fixed buffers
+    const size_t fixed = (size_t)160 << 20;
+    const size_t per_slice = kStreamBytesPerVertexSlice * F.HW;
+    if (prm->device_budget <= fixed + 3 * per_slice) return fail(CPT_ERR_OOM, "device budget below one slab of one slice");
+    F.S = (int)std::min<size_t>((size_t)T, (prm->device_budget - fixed) / per_slice - 2);
+    const int S = F.S, Tw = S + 2;
+    DevArena ar(s);
+    float* d_uvw;
+    CPT_CUDA(ar.alloc(&d_uvw, 2 * F.HW * Tw));
+    cpt_status rc = streamed_range(F, ar, d_uvw);
+    if (rc != CPT_OK) return rc;
+    // scale and bound, as in the in-memory call
+    int& k = F.k;
+    k = 0;
+    if (F.am > 0.f) { int e; std::frexp((double)F.am, &e); k = 23 - e; }
+    F.eps = prm->mode == CPT_EB_REL ? prm->eb * ((double)F.mx - (double)F.mn) : prm->eb;
+    const double ef = std::floor(std::ldexp(F.eps, k) - 0.5);
+    F.eps_int = !(ef > 0) ? 0 : (ef > 8388608.0 ? 8388608 : (int)ef);
+    cpt_stats& st = F.st;
+    std::memset(&st, 0, sizeof(st));
+    st.scale_log2 = k;
+    st.eps_int = F.eps_int;
+    st.eps = F.eps;
+    F.nby = (H + B - 1) / B;
+    F.nbx = (W + B - 1) / B;
+    F.nstrips = (H + 31) / 32;
+    F.want_sl = prm->pred != CPT_PRED_LORENZO && T > 1 && F.eps_int > 0;
+    const int nsm = sm_count();
+    // call-wide device state
+    unsigned long long* d_lg;
+    CPT_CUDA(ar.alloc(&d_lg, kLog2Tab));
+    launch_log2_table(d_lg, kLog2Tab, s);
+    NetDev net{};
+    if (F.has_net) {
+        float* d_net;
+        CPT_CUDA(ar.alloc(&d_net, kNetDevFloats));
+        rc = upload_net(prm->model, d_net, &net, s);
+        if (rc != CPT_OK) return rc;
+    }
+    // the window
+    const size_t HW = F.HW, ND = diag_elems(H, W, Tw);
+    int32_t *d_q, *d_qhat, *d_ld;
+    uint16_t *d_mask, *d_qd, *d_mask_carry;
+    int2 *d_cls, *d_qdiag, *d_psl, *d_qhat_carry;
+    unsigned *d_clsm, *d_prep, *d_hist, *d_queue, *d_ticket;
+    uint8_t *d_qxi, *d_modes;
+    uint32_t* d_sym;
+    unsigned long long *d_cnt64, *d_off, *d_stmp;
+    int* d_status;
+    int4* d_order;
+    VerifyOut* d_vo;
+    const int Umin = F.has_modes ? (B == 32 ? 32 : 16) : 8;
+    const size_t nprep = (size_t)Tw * ((H + Umin - 1) / Umin) * ((W + Umin - 1) / Umin);
+    const size_t NS = HW * S;  // vertices of a slab
+    CPT_CUDA(ar.alloc(&d_q, 2 * HW * Tw));
+    CPT_CUDA(ar.alloc(&d_qhat, 2 * HW * Tw));
+    CPT_CUDA(ar.alloc(&d_mask, HW * Tw));
+    CPT_CUDA(ar.alloc(&d_mask_carry, HW));
+    CPT_CUDA(ar.alloc(&d_qhat_carry, HW));
+    CPT_CUDA(ar.alloc(&d_cls, ND));
+    CPT_CUDA(ar.alloc(&d_clsm, ND));
+    CPT_CUDA(ar.alloc(&d_qdiag, ND));
+    CPT_CUDA(ar.alloc(&d_psl, F.want_sl ? HW * Tw : 1));
+    CPT_CUDA(ar.alloc(&d_qxi, HW * Tw));
+    CPT_CUDA(ar.alloc(&d_sym, HW * Tw));
+    CPT_CUDA(ar.alloc(&d_modes, (size_t)Tw * F.nby * F.nbx));
+    CPT_CUDA(ar.alloc(&d_prep, nprep));
+    CPT_CUDA(ar.alloc(&d_cnt64, 8));
+    CPT_CUDA(ar.alloc(&d_off, compact_tiles(NS) + 1));
+    CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(compact_tiles(NS) + 1)));
+    CPT_CUDA(ar.alloc(&d_qd, 2 * NS));
+    CPT_CUDA(ar.alloc(&d_ld, 2 * NS));
+    CPT_CUDA(ar.alloc(&d_hist, 33 + 2 * kRadius));
+    CPT_CUDA(ar.alloc(&d_queue, nprep + 2));
+    CPT_CUDA(ar.alloc(&d_ticket, 1));
+    CPT_CUDA(ar.alloc(&d_status, 1));
+    CPT_CUDA(ar.alloc(&d_order, (size_t)Tw * F.nstrips));
+    CPT_CUDA(ar.alloc(&d_vo, 1));
+    CPT_CUDA(cudaMemsetAsync(d_cnt64, 0, 8 * sizeof(unsigned long long), s));
+    CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * (33 + 2 * kRadius), s));
+    CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
+    // host copies of the codes
+    std::vector<uint8_t> qxi_h(F.N), modes_h(F.has_modes ? (size_t)T * F.nby * F.nbx : 0);
+    std::vector<uint16_t> qd_h;
+    std::vector<int32_t> ld_h;
+    const PipeTuning tune = tuning_of(prm);
+    const long long timeout_ns = 2000000000ll;
+    const size_t ntw = HW * 2;  // values per window slice
+    for (int t0 = 0; t0 < T;) {
+        const int t1 = std::min(t0 + S, T);
+        const int w0 = t0 > 0 ? t0 - 1 : 0, we = std::min(t1 + 1, T);
+        const int Tv = we - w0, vb = t0 - w0, ve = t1 - w0;
+        // the window's input slices, 16-byte aligned on the device
+        const float* src = uv + ntw * w0;
+        const float* d_src = src;
+        if (!F.dev_in || (reinterpret_cast<uintptr_t>(src) & 15u)) {
+            CPT_CUDA(cudaMemcpyAsync(d_uvw, src, ntw * Tv * sizeof(float), cudaMemcpyDefault, s));
+            d_src = d_uvw;
+        }
+        launch_to_fixed(d_src, ntw * Tv, k, d_q, nsm * 8, s);
+        // masks: the carried slice t0 - 1, the slab's (their own slab faces
+        // reach slice t1), none for the context slice
+        if (vb == 1) CPT_CUDA(cudaMemcpyAsync(d_mask, d_mask_carry, HW * sizeof(uint16_t), cudaMemcpyDeviceToDevice, s));
+        if (ve < Tv) CPT_CUDA(cudaMemsetAsync(d_mask + HW * ve, 0, HW * sizeof(uint16_t), s));
+        launch_face_masks(d_q, H, W, Tv, d_mask, d_cnt64, s, vb, ve - vb);
+        // classification of the slab (and the strip-diagonal copy of q for the context slice)
+        CPT_CUDA(cudaMemsetAsync(d_cls, 0, ND * sizeof(int2), s));
+        CPT_CUDA(cudaMemsetAsync(d_clsm, 0, ND * sizeof(unsigned), s));
+        CPT_CUDA(cudaMemsetAsync(d_qdiag, 0, ND * sizeof(int2), s));
+        launch_classify(d_q, d_mask, H, W, Tv, F.eps_int, d_cls, d_clsm, d_qdiag, s, vb, std::min(ve + 1, Tv) - vb);
+        // the encoder pipeline over slices [vb, ve) of the window
+        SliceArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.q = reinterpret_cast<const int2*>(d_q);
+        A.qhat = reinterpret_cast<int2*>(d_qhat);
+        A.mask = d_mask;
+        A.cls = d_cls;
+        A.cls_m = d_clsm;
+        A.qd = d_qdiag;
+        A.psl = d_psl;
+        A.modes = d_modes;
+        A.qxi = d_qxi;
+        A.sym = d_sym;
+        A.counters = d_cnt64 + 1;
+        A.H = H; A.W = W; A.T = Tv;
+        A.t_end = ve;
+        A.eps_int = F.eps_int;
+        A.pred = (int)prm->pred;
+        A.B = B; A.n = F.nstride; A.nby = F.nby; A.nbx = F.nbx;
+        A.nchunks = (W + 31) / 32;
+        A.cfl_x = std::ldexp(F.dt / F.dx, -k);
+        A.cfl_y = std::ldexp(F.dt / F.dy, -k);
+        A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
+        A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
+        if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
+        A.R = 0;
+        if (F.want_sl && F.has_net) {
+            A.R = kNetReach;
+        } else if (F.want_sl) {
+            const double qmax = std::ceil((double)F.am * std::ldexp(1.0, k)) +
+                                (F.eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)F.eps_int))) : 0.0);
+            const double reach = std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0;
+            A.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
+        }
+        if (F.has_net) A.net = net;
+        A.log2tab = d_lg;
+        A.prep_done = d_prep;
+        int U = F.has_modes ? (B == 32 ? 32 : 16) : 8;
+        if (prm->pred == CPT_PRED_SL && tune.sl_unit == 16) U = 16;
+        A.U = U;
+        A.nur = (H + U - 1) / U;
+        A.nuc = (W + U - 1) / U;
+        const int u_first = std::max(vb, 1);  // units of slices >= 1 only
+        const unsigned per_slice_units = (unsigned)A.nur * (unsigned)A.nuc;
+        A.n_units = F.want_sl && ve > u_first ? (unsigned)(ve - u_first) * per_slice_units : 0u;
+        A.unit_base = 0;
+        A.queue_len = A.n_units;
+        A.qslot = d_queue + 2;
+        A.qtail = d_queue + 1;
+        A.status = d_status;
+        A.timeout_ns = timeout_ns;
+        // reconstruction words: the carried slice, then nothing present
+        if (vb == 1) CPT_CUDA(cudaMemcpyAsync(d_qhat, d_qhat_carry, HW * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+        CPT_CUDA(cudaMemsetAsync(d_qhat + 2 * HW * vb, 0, 2 * HW * (Tv - vb) * sizeof(int32_t), s));
+        CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
+        CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)Tw * F.nby * F.nbx, s));
+        CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * (nprep + 2), s));
+        CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
+        CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        std::vector<unsigned> pre;
+        if (vb == 1 && A.n_units > 0) {
+            // the slab's first slice follows a finished slice: its units are ready now
+            pre.resize(per_slice_units + 2);
+            pre[0] = 0;                // head
+            pre[1] = per_slice_units;  // tail
+            for (unsigned x = 0; x < per_slice_units; ++x) pre[2 + x] = x + 1u;  // unit id (slice 1) + 1
+            CPT_CUDA(cudaMemcpyAsync(d_queue, pre.data(), sizeof(unsigned) * pre.size(), cudaMemcpyHostToDevice, s));
+        }
+        std::vector<int4> order, all;
+        merged_order({OrderField{Tv, F.nstrips, A.R, A.n_units}}, tune, all);
+        for (const int4& it : all)
+            if (it.y >= vb && it.y < ve) order.push_back(it);
+        CPT_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int4) * order.size(), cudaMemcpyHostToDevice, s));
+        PipeArgs P;
+        std::memset(&P, 0, sizeof(P));
+        P.one = A;
+        P.fields = nullptr;
+        P.nfields = 1;
+        P.order = d_order;
+        P.total_items = (unsigned)order.size();
+        P.ticket = d_ticket;
+        P.qhead = d_queue;
+        P.queue_len = A.n_units;
+        P.status = d_status;
+        P.timeout_ns = timeout_ns;
+        P.skip_item = ~0u;
+        CPT_CUDA(launch_encode_pipeline(P, (int)prm->pred, nsm, tune, s));
+        int status = 0;
+        CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        if (status != 0) return fail((cpt_status)status, "wavefront wait timed out");
+        // the slab's codes: bound codes to the host and their histogram,
+        // residual symbols and verbatim values compacted, counted, to the host
+        const size_t Ns = HW * (ve - vb), o = HW * vb;
+        CPT_CUDA(cudaMemcpyAsync(qxi_h.data() + HW * t0, d_qxi + o, Ns, cudaMemcpyDeviceToHost, s));
+        launch_hist_u8(d_qxi + o, Ns, d_hist, s);
+        const size_t nt = compact_tiles(Ns);
+        CPT_CUDA(cudaMemsetAsync(d_off + nt, 0, sizeof(unsigned long long), s));
+        launch_tile_count(d_qxi + o, d_sym + o, Ns, d_off, s);
+        launch_exclusive_scan_u64(d_off, nt + 1, d_stmp, s);
+        unsigned long long tot = 0;
+        CPT_CUDA(cudaMemcpyAsync(&tot, d_off + nt, 8, cudaMemcpyDeviceToHost, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        const size_t nq = (size_t)(tot >> 32), nl = (size_t)(tot & 0xFFFFFFFFull);
+        launch_tile_scatter(d_qxi + o, d_sym + o, d_q + 2 * o, d_off, Ns, d_qd, d_ld, s);
+        launch_hist_u16(d_qd, nq, d_hist + 33, s);
+        const size_t q0 = qd_h.size(), l0 = ld_h.size();
+        qd_h.resize(q0 + nq);
+        ld_h.resize(l0 + nl);
+        if (nq) CPT_CUDA(cudaMemcpyAsync(qd_h.data() + q0, d_qd, nq * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+        if (nl) CPT_CUDA(cudaMemcpyAsync(ld_h.data() + l0, d_ld, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (F.has_modes) {
+            const size_t per = (size_t)F.nby * F.nbx;
+            CPT_CUDA(cudaMemcpyAsync(modes_h.data() + per * t0, d_modes + per * vb, per * (ve - vb),
+                                     cudaMemcpyDeviceToHost, s));
+        }
+        // verification of the slices whose slab faces are now reconstructed
+        const int vend = t1 == T ? ve : ve - 1;
+        if (prm->verify && vend > 0)
+            launch_verify(d_qhat, d_mask, d_src, H, W, Tv, k, d_vo, s, 0, vend);
+        // carry the slab's last slice
+        CPT_CUDA(cudaMemcpyAsync(d_qhat_carry, d_qhat + 2 * HW * (ve - 1), HW * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+        CPT_CUDA(cudaMemcpyAsync(d_mask_carry, d_mask + HW * (ve - 1), HW * sizeof(uint16_t), cudaMemcpyDeviceToDevice, s));
+        CPT_CUDA(cudaStreamSynchronize(s));
+        t0 = t1;
+    }
+    return streamed_finish(F, prm, ar, d_hist, d_cnt64, d_vo, qxi_h, qd_h, ld_h, modes_h, out, out_bytes, stats);
 }
 
 // Many fields, one set of parameters: fields are taken in order into groups
@@ -1768,6 +2353,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     A.decode = 1;
     A.counters = d_ctr + 1;
     A.H = H; A.W = W; A.T = T;
+    A.t_end = T;
     A.eps_int = eps_int;
     A.pred = pred;
     A.B = B; A.n = stride_hdr; A.nby = nby; A.nbx = nbx;

@@ -61,6 +61,7 @@ struct SliceArgs {
     const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
+    int t_end;              // slices >= t_end are not encoded (their units are not queued)
     int sl_fbx, sl_fby;     // CFL = 2^(1 - fb) with an exact fixed-point RK2 midpoint; -1 = general FP64 path
     long long timeout_ns;
     // Decoding: the same pipeline rebuilds qhat from a stream.  cls then holds
@@ -125,10 +126,11 @@ struct HuffDecode {
 // k_field.cu
 void launch_range(const float* uv, size_t n, RangePartial* part, int nblocks, cudaStream_t s);
 void launch_to_fixed(const float* uv, size_t n, int k, int32_t* q, int nblocks, cudaStream_t s);  // q = rint(x 2^k)
+// over slices [t_first, t_first + t_count) of a [T][H][W] field (default: all)
 void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, unsigned long long* ncrossed,
-                       cudaStream_t s);
+                       cudaStream_t s, int t_first = 0, int t_count = -1);
 void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T, int k,
-                   VerifyOut* out, cudaStream_t s);
+                   VerifyOut* out, cudaStream_t s, int t_first = 0, int t_count = -1);
 // repair of a failed verification: flags (zeroed before) of the vertices of
 // changed faces and of vertices past the bound (qhat untagged); the flagged
 // vertices' classification set to lossless (strip-diagonal cls)
@@ -139,7 +141,7 @@ void launch_force_lossless(const uint8_t* flags, int H, int W, int T, int2* cls,
 // k_encode.cu
 // out, out_m and qd in the strip-diagonal layout (see SliceArgs), zeroed before
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
-                     unsigned* out_m, int2* qd, cudaStream_t s);
+                     unsigned* out_m, int2* qd, cudaStream_t s, int t_first = 0, int t_count = -1);
 inline size_t diag_elems(int H, int W, int T) { return (size_t)T * ((H + 31) / 32) * (W + 31) * 32; }
 cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s);
 void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);

@@ -35,6 +35,7 @@
 // so the pipeline cannot deadlock; each wait is bounded in time and sets the
 // status word when it expires.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "cpt_dev.cuh"
@@ -92,9 +93,11 @@ __device__ __forceinline__ unsigned unc_pair(int f) {
 // ---------------------------------------------------------------------------
 constexpr int kClsRows = 32;
 
+// The 14 neighbour values; an absent neighbour reads as the vertex's own
+// value z (faces through it are never evaluated, and it passes the fast
+// path's sign tests whenever the vertex itself does).
 __device__ __forceinline__ void load_nb(const int2* __restrict__ q, size_t v, size_t sl, int W, unsigned valid,
-                                        int2 nb[14]) {
-    const int2 z = make_int2(0, 0);
+                                        int2 nb[14], int2 z) {
     nb[0] = (valid & (1u << 0)) ? __ldg(q + v - sl - W - 1) : z;
     nb[1] = (valid & (1u << 1)) ? __ldg(q + v - sl - W) : z;
     nb[2] = (valid & (1u << 2)) ? __ldg(q + v - sl - 1) : z;
@@ -121,15 +124,16 @@ __device__ __forceinline__ void store_cls(int2* __restrict__ out, unsigned* __re
     qd[dv] = __ldg(q + v);
 }
 
-__global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
+__global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
                                                        int H, int W, int T, int eps_int, int2* __restrict__ out,
-                                                       unsigned* __restrict__ out_m, int2* __restrict__ qd) {
+                                                       unsigned* __restrict__ out_m, int2* __restrict__ qd,
+                                                       int t_first) {
     __shared__ unsigned short s_slow[32 * kClsRows];  // (row in the block) * 32 + lane
     __shared__ int s_nslow;
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 32 + lane;
     const int ib = blockIdx.y * kClsRows;
-    const int t = blockIdx.z;
+    const int t = t_first + (int)blockIdx.z;
     const size_t sl = (size_t)H * W;
     if (threadIdx.x == 0) s_nslow = 0;
     __syncthreads();
@@ -138,41 +142,51 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
         bool slow = false;
         if (i < H && j < W) {
             const size_t v = ((size_t)t * H + i) * W + j;
+            // a crossed incident face: one of the eight owners' masks (the
+            // owners lie at offsets (0..-1, 0..-1, 0..-1) from the vertex)
             bool crossed = false;
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
-                const int ot = t + kOwners[o].dt, oi = i + kOwners[o].di, oj = j + kOwners[o].dj;
-                if (ot >= 0 && oi >= 0 && oj >= 0)
-                    crossed |= (__ldg(mask + ((size_t)ot * H + oi) * W + oj) & kOwners[o].types) != 0;
+                const bool ok = (kOwners[o].dt == 0 || t > 0) && (kOwners[o].di == 0 || i > 0) &&
+                                (kOwners[o].dj == 0 || j > 0);
+                const long long off = (long long)kOwners[o].dt * (long long)sl + (long long)kOwners[o].di * W +
+                                      kOwners[o].dj;
+                if (ok) crossed |= (__ldg(mask + (long long)v + off) & kOwners[o].types) != 0;
             }
             int xi = 0;
             unsigned um_m = 0;
             if (!crossed && eps_int > 0) {
                 xi = eps_int;
                 const unsigned valid = nb_valid(H, W, T, t, i, j);
-                int2 nb[14];
-                load_nb(q, v, sl, W, valid, nb);
                 const int2 qv = __ldg(q + v);
+                int2 nb[14];
+                load_nb(q, v, sl, W, valid, nb, qv);
                 const int E = 1 << (31 - __clz(eps_int));
                 // Fast path (exact): every existing neighbour keeps the vertex's
                 // strict sign of u (or of v), with margin E where its value may
                 // still change, and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on
                 // every face unless M = 0, and no uncertain face needs the full
                 // Alg. 2: it is class 1 when |M| <= D, else class 0.
-                // M = det(n_a - q, n_b - q).
+                // M = det(n_a - q, n_b - q).  The sign tests are minima and
+                // maxima over the uncertain neighbours (0..6) and the others.
                 bool fast = false;
 #pragma unroll
                 for (int c = 0; c < 2 && !fast; ++c) {
                     const int x0 = c ? qv.y : qv.x;
                     if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
-                    bool ok = true;
+                    int lo_u = INT_MAX, hi_u = INT_MIN, lo_c = INT_MAX, hi_c = INT_MIN;
 #pragma unroll
                     for (int k = 0; k < 14; ++k) {
-                        const int m = is_uncertain(k) ? E : 0, x = c ? nb[k].y : nb[k].x;
-                        const bool same = x0 > 0 ? x > m : x < -m;
-                        ok &= !((valid >> k) & 1u) || same;
+                        const int x = c ? nb[k].y : nb[k].x;
+                        if (is_uncertain(k)) {
+                            lo_u = min(lo_u, x);
+                            hi_u = max(hi_u, x);
+                        } else {
+                            lo_c = min(lo_c, x);
+                            hi_c = max(hi_c, x);
+                        }
                     }
-                    fast = ok;
+                    fast = x0 > 0 ? (lo_c > 0 && lo_u > E) : (hi_c < 0 && hi_u < -E);
                 }
                 if (fast) {
                     // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
@@ -229,12 +243,13 @@ __global__ void __launch_bounds__(256) classify_kernel(const int2* __restrict__ 
         const int i = ib + (int)(e >> 5), jj = blockIdx.x * 32 + (int)(e & 31u);
         const size_t v = ((size_t)t * H + i) * W + jj;
         const unsigned valid = nb_valid(H, W, T, t, i, jj);
-        int2 nb[14];
-        load_nb(q, v, sl, W, valid, nb);
         const int2 qv = __ldg(q + v);
+        int2 nb[14];
+        load_nb(q, v, sl, W, valid, nb, qv);
         const int E = 1 << (31 - __clz(eps_int));
         int xi = eps_int;
         unsigned um_full = 0, um_m = 0;
+        (void)E;
         CPT_CERT_FACES(CPT_FACE)
         if (xi > 0) {
             int bit = 0;
@@ -934,7 +949,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     const bool has_prev = t >= 1, has_above = s > 0;
     const bool need_sl = has_prev && a.n_units > 0;  // SL predictions present for this slice
     const bool mop = a.pred == 2 || a.pred == 4;  // psl carries the 3DL marker
-    const bool feeds = a.n_units > 0 && t + 1 < T;   // queues the prep units of slice t+1
+    const bool feeds = a.n_units > 0 && t + 1 < a.t_end;  // queues the prep units of slice t+1
     const bool has_next = t + 1 < T;
     const bool dec = a.decode != 0;  // decoding: reconstruct from the stream's symbols
     const bool stage_next = has_next && !dec, stage_below = below_ok && !dec;
@@ -1235,9 +1250,12 @@ void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s) {
 }
 
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
-                     unsigned* out_m, int2* qd, cudaStream_t s) {
-    dim3 grid((W + 31) / 32, (H + kClsRows - 1) / kClsRows, T);
-    classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m, qd);
+                     unsigned* out_m, int2* qd, cudaStream_t s, int t_first, int t_count) {
+    if (t_count < 0) t_count = T - t_first;
+    if (t_count <= 0) return;
+    dim3 grid((W + 31) / 32, (H + kClsRows - 1) / kClsRows, t_count);
+    classify_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const int2*>(q), mask, H, W, T, eps_int, out, out_m, qd,
+                                         t_first);
 }
 
 template <int UMAX, bool NET>

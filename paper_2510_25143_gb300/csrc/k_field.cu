@@ -354,11 +354,12 @@ struct FaceGrid {
     int nstrips, nchunks;
     long long items;
 };
-__host__ __device__ inline FaceGrid face_grid(int H, int W, int T) {
+// work items over t_count slices
+__host__ __device__ inline FaceGrid face_grid(int H, int W, int t_count) {
     FaceGrid g;
     g.nstrips = (W + kStrip - 1) / kStrip;
     g.nchunks = (H + kFaceRows - 1) / kFaceRows;
-    g.items = (long long)T * g.nchunks * g.nstrips;
+    g.items = (long long)t_count * g.nchunks * g.nstrips;
     return g;
 }
 
@@ -370,16 +371,17 @@ __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q
                                                    const uint16_t* __restrict__ mask_in,
                                                    const float2* __restrict__ uv, float g1, float g2,
                                                    unsigned long long* __restrict__ ncrossed,
-                                                   VerifyOut* __restrict__ vout) {
-    const FaceGrid g = face_grid(H, W, T);
+                                                   VerifyOut* __restrict__ vout, int t_first, int t_count) {
+    const FaceGrid g = face_grid(H, W, t_count);
     const long long per_t = (long long)g.nchunks * g.nstrips;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     __shared__ uint16_t s_queue[8][kQueueCap];
     FaceAcc acc{0ull, 0u, 0u, ErrMax{0.f, 0.f}, 0.f};
     for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < g.items;
          item += nwarps) {
-        const int t = (int)(item / per_t);
-        const long long r = item - (long long)t * per_t;
+        const int tr = (int)(item / per_t);
+        const long long r = item - (long long)tr * per_t;
+        const int t = t_first + tr;
         const int ib = (int)(r / g.nstrips) * kFaceRows;
         const int j0 = (int)(r % g.nstrips) * kStrip;
         face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
@@ -522,7 +524,7 @@ void launch_to_fixed(const float* uv, size_t n, int k, int32_t* q, int nblocks, 
 // One wave of resident blocks (8 warps each) walks the work items; one set
 // of atomics per block.
 template <bool kVerify, bool kVec>
-static unsigned face_blocks(int H, int W, int T) {
+static unsigned face_blocks(int H, int W, int t_count) {
     static int resident = 0;
     if (!resident) {
         int dev = 0, nsm = 0, per_sm = 0;
@@ -535,33 +537,37 @@ static unsigned face_blocks(int H, int W, int T) {
             per_sm = 1;
         resident = nsm * per_sm;
     }
-    const long long want = (face_grid(H, W, T).items + 7) / 8;
+    const long long want = (face_grid(H, W, t_count).items + 7) / 8;
     return (unsigned)std::max(1ll, std::min(want, (long long)resident));
 }
 
 void launch_face_masks(const int32_t* q, int H, int W, int T, uint16_t* mask, unsigned long long* ncrossed,
-                       cudaStream_t s) {
+                       cudaStream_t s, int t_first, int t_count) {
+    if (t_count < 0) t_count = T - t_first;
+    if (t_count <= 0) return;
     const int2* q2 = reinterpret_cast<const int2*>(q);
     if (W % 2 == 0)
-        face_kernel<false, true><<<face_blocks<false, true>(H, W, T), 256, 0, s>>>(q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f,
-                                                                      ncrossed, nullptr);
+        face_kernel<false, true><<<face_blocks<false, true>(H, W, t_count), 256, 0, s>>>(
+            q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f, ncrossed, nullptr, t_first, t_count);
     else
-        face_kernel<false, false><<<face_blocks<false, false>(H, W, T), 256, 0, s>>>(q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f,
-                                                                       ncrossed, nullptr);
+        face_kernel<false, false><<<face_blocks<false, false>(H, W, t_count), 256, 0, s>>>(
+            q2, H, W, T, mask, nullptr, nullptr, 0.f, 0.f, ncrossed, nullptr, t_first, t_count);
 }
 
 void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, int H, int W, int T, int k,
-                   VerifyOut* out, cudaStream_t s) {
+                   VerifyOut* out, cudaStream_t s, int t_first, int t_count) {
+    if (t_count < 0) t_count = T - t_first;
+    if (t_count <= 0) return;
     const int a = -k / 2, b = -k - a;
     const int2* q2 = reinterpret_cast<const int2*>(qhat);
     const float2* x2 = reinterpret_cast<const float2*>(uv);
     const float g1 = std::ldexp(1.0f, a), g2 = std::ldexp(1.0f, b);
     if (W % 2 == 0)
-        face_kernel<true, true><<<face_blocks<true, true>(H, W, T), 256, 0, s>>>(q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr,
-                                                                     out);
+        face_kernel<true, true><<<face_blocks<true, true>(H, W, t_count), 256, 0, s>>>(
+            q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr, out, t_first, t_count);
     else
-        face_kernel<true, false><<<face_blocks<true, false>(H, W, T), 256, 0, s>>>(q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr,
-                                                                      out);
+        face_kernel<true, false><<<face_blocks<true, false>(H, W, t_count), 256, 0, s>>>(
+            q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr, out, t_first, t_count);
 }
 
 }  // namespace cpt
