@@ -95,7 +95,8 @@ typedef enum {
  *              them, [4] worker warps per SM (0 = as many as shared memory
  *              and registers allow), [5] warp layout: 0 = whole CTAs per role
  *              (every warp slot the larger role's size), 1 = prediction and
- *              wave warps in every CTA, each slot of its own size.  The
+ *              wave warps in every CTA, each slot of its own size, w >= 2 =
+ *              as 0 with at most w wave warps working per CTA.  The
  *              schedule orders and places work only: the stream does not
  *              depend on it.                                                  */
 typedef struct {

@@ -417,108 +417,6 @@ __device__ __forceinline__ int sl_predict(const Slice& P, int H, int W, int i, i
     return mode;
 }
 
-// ---------------------------------------------------------------------------
-// The same predictor when CFL_x = 2^(1 - fbx) and CFL_y = 2^(1 - fby) are
-// powers of two (the spacings' ratios dt/dx, dt/dy are) with 0 <= fbx, fby
-// <= 26 and max(H, W) 2^fb + 2^31 < 2^53 (checked on the host).  Then the
-// RK2 midpoint is exact in fixed point: 0.5 du = g.x 2^-fbx, so
-// j - 0.5 du = (j 2^fbx - g.x) 2^-fbx, its clamp, floor and fraction are
-// integer operations, and every weight (1-fx)(1-fy), fx(1-fy), ... is an
-// integer below 2^52 times 2^-(fbx+fby): exact in FP64, so the FP64 steps that
-// compute them return these very values.  u_h CFL_x is exact too (a power-of-
-// two scaling of a value far from the subnormal range).  The rounded steps
-// (the bilinear sums, j - u_h CFL_x, the final weights and + 0.5) stay in FP64
-// in the same order: the result is bit for bit that of sl_predict, with 36
-// instead of 52 FP64 operations per RK2 prediction.  Substeps (d_inf > 2)
-// take sl_predict itself.
-// ---------------------------------------------------------------------------
-// m 2^e2 for 0 <= m < 2^53 (a normal result), exact, from the bit layout
-__device__ __forceinline__ double ll2d_scaled(unsigned long long m, int e2) {
-    if (m == 0) return 0.0;
-    const int e = 63 - __clzll((long long)m);
-    const unsigned long long mant = (m << (52 - e)) & 0xFFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(((unsigned long long)(e + e2 + 1023) << 52) | mant));
-}
-
-// x 2^c for a finite x, |x| far from the subnormal range (or zero: unchanged)
-__device__ __forceinline__ double scale_pow2(double x, int c) {
-    const long long b = __double_as_longlong(x);
-    if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return x;
-    return __longlong_as_double(b + ((long long)c << 52));
-}
-
-// bilinear stencil of a clamped (non-negative) position; 1 - fx is exact
-// whenever x >= 1 (the fraction is then a multiple of 2^-52), and taken from
-// the integer fraction
-__device__ __forceinline__ Bil bil_weights_x(double x, double y, int H, int W) {
-    Bil b;
-    double gxy[2], fxy[2];
-    int p0[2];
-    const double v[2] = {x, y};
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(v[c]) & 0x7FFFFFFFFFFFFFFFull;
-        const int e = (int)(bits >> 52) - 1023;
-        if (e < 0) {  // v < 1: the FP64 subtraction
-            p0[c] = 0;
-            fxy[c] = __longlong_as_double((long long)bits);
-            gxy[c] = __dsub_rn(1.0, fxy[c]);
-        } else {
-            const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-            const int sh = 52 - e;
-            p0[c] = (int)(m >> sh);
-            const unsigned long long f = m & ((1ull << sh) - 1ull);
-            fxy[c] = ll2d_scaled(f, -sh);
-            gxy[c] = ll2d_scaled((1ull << sh) - f, -sh);
-        }
-    }
-    b.x0 = p0[0];
-    b.y0 = p0[1];
-    b.x1 = b.x0 + 1 < W ? b.x0 + 1 : W - 1;
-    b.y1 = b.y0 + 1 < H ? b.y0 + 1 : H - 1;
-    b.w00 = __dmul_rn(gxy[0], gxy[1]);
-    b.w10 = __dmul_rn(fxy[0], gxy[1]);
-    b.w01 = __dmul_rn(gxy[0], fxy[1]);
-    b.w11 = __dmul_rn(fxy[0], fxy[1]);
-    return b;
-}
-
-template <class Slice>
-__device__ __forceinline__ int sl_predict_fix(const Slice& P, int H, int W, int i, int j, int fbx, int fby,
-                                              double cfl_x, double cfl_y, int& pu, int& pv) {
-    const int2 g = P.at(i, j);
-    // d_inf <= 2  <=>  |g.x| 2^(1-fbx) <= 2 and |g.y| 2^(1-fby) <= 2
-    if ((long long)abs(g.x) > (1ll << fbx) || (long long)abs(g.y) > (1ll << fby))
-        return sl_predict(P, H, W, i, j, cfl_x, cfl_y, pu, pv);
-    long long X = ((long long)j << fbx) - g.x, Y = ((long long)i << fby) - g.y;
-    const long long Xm = (long long)(W - 1) << fbx, Ym = (long long)(H - 1) << fby;
-    X = X < 0 ? 0 : (X > Xm ? Xm : X);
-    Y = Y < 0 ? 0 : (Y > Ym ? Ym : Y);
-    Bil b;
-    {
-        b.x0 = (int)(X >> fbx);
-        b.y0 = (int)(Y >> fby);
-        b.x1 = b.x0 + 1 < W ? b.x0 + 1 : W - 1;
-        b.y1 = b.y0 + 1 < H ? b.y0 + 1 : H - 1;
-        const unsigned long long fx = (unsigned long long)(X & ((1ll << fbx) - 1)), gx = (1ull << fbx) - fx;
-        const unsigned long long fy = (unsigned long long)(Y & ((1ll << fby) - 1)), gy = (1ull << fby) - fy;
-        const int e2 = -(fbx + fby);
-        b.w00 = ll2d_scaled(gx * gy, e2);
-        b.w10 = ll2d_scaled(fx * gy, e2);
-        b.w01 = ll2d_scaled(gx * fy, e2);
-        b.w11 = ll2d_scaled(fx * fy, e2);
-    }
-    const double uh = bil_sample(b, P, 0);
-    const double vh = bil_sample(b, P, 1);
-    const double xmax = i2d(W - 1), ymax = i2d(H - 1);
-    const double xs = clamp_pos(__dsub_rn(i2d(j), scale_pow2(uh, 1 - fbx)), xmax);
-    const double ys = clamp_pos(__dsub_rn(i2d(i), scale_pow2(vh, 1 - fby)), ymax);
-    const Bil bf = bil_weights_x(xs, ys, H, W);
-    pu = floor_int(__dadd_rn(bil_sample(bf, P, 0), 0.5));
-    pv = floor_int(__dadd_rn(bil_sample(bf, P, 1), 0.5));
-    return 0;
-}
-
 // Asynchronous global -> shared copies (zero-filled when !valid; the source is
 // then not read).  Only for data that no running kernel writes: they may be
 // served from L1.

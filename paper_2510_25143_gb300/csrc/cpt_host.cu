@@ -370,20 +370,6 @@ static bool is_device_pointer(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// fb with cfl = 2^(1 - fb), 0 <= fb <= 26 and max(H, W) 2^fb + 2^31 < 2^53,
-// else -1: the conditions under which the semi-Lagrangian RK2 midpoint is
-// exact in fixed point with fb fractional bits (sl_predict_fix)
-static int sl_fixed_bits(double cfl, int H, int W) {
-    if (!(cfl > 0) || !std::isfinite(cfl)) return -1;
-    int e = 0;
-    const double m = std::frexp(cfl, &e);  // cfl = m 2^e, m in [0.5, 1)
-    if (m != 0.5) return -1;               // not a power of two
-    const int fb = 2 - e;                  // cfl = 2^(e-1) = 2^(1 - fb)
-    if (fb < 0 || fb > 26) return -1;
-    if (std::ldexp((double)std::max(H, W), fb) + 2147483648.0 >= 9007199254740992.0) return -1;
-    return fb;
-}
-
 static int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -651,9 +637,6 @@ struct FieldJob {
         A.nchunks = nchunks;
         A.cfl_x = std::ldexp(dt / dx, -k);
         A.cfl_y = std::ldexp(dt / dy, -k);
-        A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
-        A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
-        if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
         // Reach of the semi-Lagrangian back-trace into slice t-1: no
         // reconstruction exceeds max|q| + E in magnitude, every displacement is
         // at most that times CFL, the bilinear stencil adds one cell, and one
@@ -1024,25 +1007,28 @@ static std::map<std::tuple<int, int, int, int>, PipeTuning> g_tune_cache;
 
 // Candidate schedules of the encoder pipeline for a predictor.
 static std::vector<PipeTuning> tuning_candidates(int pred) {
-    // {prep share %, pure-SL unit side, 3DL slice weight, slack, warps per SM (0 = as many as fit)}
     std::vector<PipeTuning> c;
+    // {prep share %, pure-SL unit side, 3DL slice weight, slack, warps per SM, layout / wave cap}
     if (pred == CPT_PRED_LORENZO) {
-        for (int w : {3, 0})
-            for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, w});
+        for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, 3, 0});
+        for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, 0, 8});
     } else if (pred == CPT_PRED_SL) {
         // large slices are bound by the throughput of the prediction units:
-        // shares up to 75 % of the warps pay there; small ones by the lag
-        c.push_back({45, 8, 0, 0, 3});
+        // shares up to 75 % of the warps pay there; small ones by the lag.
+        // At most 8 working wave warps per CTA keep the wave steps short.
+        c.push_back({45, 8, 0, 0, 3, 0});
         for (int u : {8, 16})
-            for (int share : {35, 55, 65, 75}) c.push_back({share, u, 0, 0, 0});
+            for (int share : {35, 55, 65, 75}) c.push_back({share, u, 0, 0, 0, 0});
+        for (int share : {55, 65}) c.push_back({share, 8, 0, 0, 0, 8});
     } else if (pred == CPT_PRED_LEARNED) {
-        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 0, 0});
+        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED_MOP) {
-        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 64, 0});
+        for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 64, 0, 0});
     } else {
-        c.push_back({45, 0, 0, 64, 3});
-        for (int share : {35, 55, 65, 70, 75, 80}) c.push_back({share, 0, 0, 64, 0});
-        c.push_back({75, 0, 0, 128, 0});
+        c.push_back({45, 0, 0, 64, 3, 0});
+        for (int share : {35, 55, 65, 70, 75, 80}) c.push_back({share, 0, 0, 64, 0, 0});
+        for (int share : {70, 75, 80}) c.push_back({share, 0, 0, 64, 0, 8});
+        c.push_back({75, 0, 0, 128, 0, 0});
     }
     return c;
 }
@@ -1857,9 +1843,6 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
         A.nchunks = (W + 31) / 32;
         A.cfl_x = std::ldexp(F.dt / F.dx, -k);
         A.cfl_y = std::ldexp(F.dt / F.dy, -k);
-        A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
-        A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
-        if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
         A.R = 0;
         if (F.want_sl && F.has_net) {
             A.R = kNetReach;
@@ -2360,9 +2343,6 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     A.nchunks = (W + 31) / 32;
     A.cfl_x = std::ldexp(dt / dx, -k);
     A.cfl_y = std::ldexp(dt / dy, -k);
-    A.sl_fbx = sl_fixed_bits(A.cfl_x, H, W);
-    A.sl_fby = sl_fixed_bits(A.cfl_y, H, W);
-    if (A.sl_fbx < 0 || A.sl_fby < 0) A.sl_fbx = A.sl_fby = -1;
     // Reach of the back-trace: |qhat| <= 2^23 + E for every stream (the
     // fixed-point scale keeps |q| <= 2^23, the quantiser moves a value by at
     // most E), so no displacement exceeds that times CFL.
@@ -2429,7 +2409,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
         const bool dev = is_device_pointer(uv_out) && !(reinterpret_cast<uintptr_t>(uv_out) & 7u);
         float* dst = uv_out;
         if (!dev) CPT_CUDA(ar.alloc(&dst, 2 * N));
-        launch_to_float(d_qhat, N, std::ldexp(1.0, -k), dst, s);
+        launch_to_float(d_qhat, N, k, dst, s);
         if (!dev) CPT_CUDA(cudaMemcpyAsync(uv_out, dst, N * 8, cudaMemcpyDefault, s));
     }
     CPT_CUDA(cudaStreamSynchronize(s));

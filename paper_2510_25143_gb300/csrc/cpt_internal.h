@@ -62,7 +62,6 @@ struct SliceArgs {
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
     double cfl_x, cfl_y;
     int t_end;              // slices >= t_end are not encoded (their units are not queued)
-    int sl_fbx, sl_fby;     // CFL = 2^(1 - fb) with an exact fixed-point RK2 midpoint; -1 = general FP64 path
     long long timeout_ns;
     // Decoding: the same pipeline rebuilds qhat from a stream.  cls then holds
     // (bound code, residual symbols u | v << 16) and qd the verbatim values,
@@ -91,6 +90,7 @@ struct PipeArgs {
     int mixed;                // 0: every warp has a slot of one size, whole CTAs per role;
                               // 1: prep and wave slots of their own sizes in every CTA
     unsigned slot_bytes;      // layout 0: bytes of a warp's slot
+    int wave_cap;             // layout 0: wave warps per CTA at most (0 = all; the others idle)
     unsigned skip_item;       // failure injection: the ticket of a wave that never runs (~0u = none)
 };
 
@@ -103,7 +103,8 @@ struct PipeTuning {
     int slack;         // extra slice weight of the ticket order with prep units (0 = default)
     int warps_per_sm;  // worker warps per SM (0 = as many as shared memory and registers allow)
     int mixed;         // 1: prep and wave warps in every CTA, each with a slot of its own size;
-                       // 0: whole CTAs per role, every slot the size of the larger one
+                       // 0: whole CTAs per role, every slot the size of the larger one;
+                       // w >= 2: as 0 with at most w wave warps working in a CTA
 };
 
 // Canonical Huffman decoding tables of one stream (device pointers).
@@ -181,7 +182,7 @@ void launch_gather_sym(const uint8_t* qxi, const unsigned long long* off, const 
 void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned long long* off, const int32_t* ld,
                        size_t n_ld, int H, int W, int T, int2* dcs, int2* draw, int* status, cudaStream_t s);
 void launch_untag(int2* qhat, size_t N, cudaStream_t s);  // reconstruction words -> values
-void launch_to_float(const int2* qhat, size_t N, double inv_scale, float* out, cudaStream_t s);
+void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s);  // q_hat 2^-k
 
 // k_traj.cu
 void launch_iota(unsigned* x, size_t n, cudaStream_t s);

@@ -5,6 +5,8 @@
 // bounds from the stream and no face work), and the conversion back to
 // float.  A malformed stream sets the status word to a corruption code;
 // nothing reads or writes out of bounds.
+#include <cmath>
+
 #include "cpt_dev.cuh"
 #include "cpt_internal.h"
 
@@ -138,29 +140,34 @@ __global__ void __launch_bounds__(256) gather_raw_kernel(const uint8_t* __restri
                                                          const int32_t* __restrict__ ld, size_t n_ld, int H, int W,
                                                          int T, int2* __restrict__ dcs, int2* __restrict__ raw,
                                                          int* __restrict__ status) {
-    const size_t N = (size_t)H * W * T, sl = (size_t)H * W;
     const size_t nstrips = (size_t)(H + 31) >> 5;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        const size_t t = v / sl, rem = v - t * sl;
-        const int i = (int)(rem / W), j = (int)(rem - (size_t)i * W);
-        const size_t dv = ((t * nstrips + (i >> 5)) * (size_t)(W + 31) + (j + (i & 31))) * 32 + (i & 31);
-        size_t o = (size_t)(off[v] & 0xFFFFFFFFull);
-        int2 r = make_int2(0, 0);
-        if (qxi[v] == 0) {
-            if (o + 2 > n_ld) { atomicCAS(status, 0, kStatusCorrupt); }
-            else { r.x = ld[o]; r.y = ld[o + 1]; }
-        } else {
-            const uint32_t s = sym[v];
-            const size_t need = ((s & 0xFFFFu) == 0) + ((s >> 16) == 0);
-            if (o + need > n_ld) {
-                atomicCAS(status, 0, kStatusCorrupt);
+    // one row of one slice per block iteration: no division per vertex
+    for (long long r = blockIdx.x; r < (long long)T * H; r += gridDim.x) {
+        const int t = (int)(r / H), i = (int)(r - (long long)t * H);
+        const size_t row = (size_t)r * W;
+        const size_t drow = (((size_t)t * nstrips + (i >> 5)) * (size_t)(W + 31) + (i & 31)) * 32 + (i & 31);
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            const size_t v = row + j;
+            const size_t dv = drow + (size_t)j * 32;
+            size_t o = (size_t)(off[v] & 0xFFFFFFFFull);
+            int2 rr = make_int2(0, 0);
+            const uint8_t c = qxi[v];
+            const uint32_t sy = c ? sym[v] : 0u;
+            if (c == 0) {
+                if (o + 2 > n_ld) { atomicCAS(status, 0, kStatusCorrupt); }
+                else { rr.x = ld[o]; rr.y = ld[o + 1]; }
             } else {
-                if ((s & 0xFFFFu) == 0) r.x = ld[o++];
-                if ((s >> 16) == 0) r.y = ld[o];
+                const size_t need = ((sy & 0xFFFFu) == 0) + ((sy >> 16) == 0);
+                if (o + need > n_ld) {
+                    atomicCAS(status, 0, kStatusCorrupt);
+                } else {
+                    if ((sy & 0xFFFFu) == 0) rr.x = ld[o++];
+                    if ((sy >> 16) == 0) rr.y = ld[o];
+                }
             }
+            raw[dv] = rr;
+            dcs[dv] = make_int2((int)c, (int)sy);
         }
-        raw[dv] = r;
-        dcs[dv] = make_int2((int)qxi[v], (int)sym[v]);
     }
 }
 
@@ -170,13 +177,31 @@ __global__ void __launch_bounds__(256) untag_kernel(int2* __restrict__ q, size_t
         q[v].y ^= kQhatTag;
 }
 
-// q_hat * 2^-k in float32 (exact: |q_hat| <= 2^24)
-__global__ void __launch_bounds__(256) to_float_kernel(const int2* __restrict__ qhat, size_t N, double inv_scale,
-                                                       float2* __restrict__ out) {
+// q_hat * 2^-k in float32: q_hat is exact in float (|q_hat| <= 2^24) and the
+// power of two is applied as two factors 2^a 2^b (a + b = -k) that never
+// leave the normal range on the way, so every product is exact
+__global__ void __launch_bounds__(256) to_float_kernel(const int4* __restrict__ qhat, size_t N2, float g1, float g2,
+                                                       float4* __restrict__ out) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N2; v += (size_t)gridDim.x * blockDim.x) {
+        const int4 q = __ldcs(qhat + v);
+        out[v] = make_float4(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
+                             __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2),
+                             __fmul_rn(__fmul_rn(__int2float_rn(q.z), g1), g2),
+                             __fmul_rn(__fmul_rn(__int2float_rn(q.w), g1), g2));
+    }
+}
+__global__ void __launch_bounds__(256) to_float_v_kernel(const int2* __restrict__ qhat, size_t N, float g1, float g2,
+                                                          float2* __restrict__ out) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
         const int2 q = qhat[v];
-        out[v] = make_float2((float)((double)q.x * inv_scale), (float)((double)q.y * inv_scale));
+        out[v] = make_float2(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
+                             __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2));
     }
+}
+__global__ void to_float_tail_kernel(const int2* __restrict__ qhat, float g1, float g2, float2* __restrict__ out) {
+    const int2 q = qhat[0];
+    out[0] = make_float2(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
+                         __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2));
 }
 
 // ---------------------------------------------------------------------------
@@ -202,8 +227,18 @@ void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned l
     gather_raw_kernel<<<1216, 256, 0, s>>>(qxi, sym, off, ld, n_ld, H, W, T, dcs, draw, status);
 }
 void launch_untag(int2* qhat, size_t N, cudaStream_t s) { untag_kernel<<<1216, 256, 0, s>>>(qhat, N); }
-void launch_to_float(const int2* qhat, size_t N, double inv_scale, float* out, cudaStream_t s) {
-    to_float_kernel<<<1216, 256, 0, s>>>(qhat, N, inv_scale, reinterpret_cast<float2*>(out));
+void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s) {
+    const int a = -k / 2, b = -k - a;
+    const float g1 = std::ldexp(1.0f, a), g2 = std::ldexp(1.0f, b);
+    // two vertices per thread (16-byte accesses when out is 16-byte aligned)
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+        if (N / 2)
+            to_float_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const int4*>(qhat), N / 2, g1, g2,
+                                                 reinterpret_cast<float4*>(out));
+        if (N & 1) to_float_tail_kernel<<<1, 1, 0, s>>>(qhat + N - 1, g1, g2, reinterpret_cast<float2*>(out) + N - 1);
+    } else {  // output only 8-byte aligned: one vertex per thread
+        to_float_v_kernel<<<1216, 256, 0, s>>>(qhat, N, g1, g2, reinterpret_cast<float2*>(out));
+    }
 }
 
 }  // namespace cpt

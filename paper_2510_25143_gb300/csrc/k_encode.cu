@@ -600,14 +600,6 @@ __device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, 
     __syncwarp();
 }
 
-// The semi-Lagrangian prediction of vertex (i, j): the fixed-point midpoint
-// variant when the CFL numbers allow it (same result, fewer FP64 operations).
-template <class Slice>
-__device__ __forceinline__ int sl_pred(const SliceArgs& a, const Slice& P, int i, int j, int& pu, int& pv) {
-    if (a.sl_fbx >= 0) return sl_predict_fix(P, a.H, a.W, i, j, a.sl_fbx, a.sl_fby, a.cfl_x, a.cfl_y, pu, pv);
-    return sl_predict(P, a.H, a.W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-}
-
 // One prep unit: the U x U vertices from (r0, c0) of slice t >= 1 (it enters
 // the ready queue once slice t-1 is reconstructed around it).  Leaves in psl
 // the SL prediction of every vertex that uses SL, and with MoP the marker
@@ -744,7 +736,8 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             const int li = fr + (k / nc) * st, lj = fc + (k % nc) * st;
             const int i = r0 + li, j = c0 + lj;
             int pu, pv;
-            const int md = staged ? sl_pred(a, Ps, i, j, pu, pv) : sl_pred(a, Pg, i, j, pu, pv);
+            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
             const int2 p = make_int2(pu, pv);
             if (mop) ps.psl[li][lj] = p;
             Psl[(size_t)i * W + j] = p;
@@ -779,7 +772,8 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             const unsigned v = ps.list[m];
             const int i = r0 + (int)(v >> 5), j = c0 + (int)(v & 31u);
             int pu, pv;
-            const int md = staged ? sl_pred(a, Ps, i, j, pu, pv) : sl_pred(a, Pg, i, j, pu, pv);
+            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
             Psl[(size_t)i * W + j] = make_int2(pu, pv);
             sub += md > 0;
             steps += md;
@@ -1208,6 +1202,10 @@ __global__ void __maxnreg__(168) encode_pipeline_kernel(const __grid_constant__ 
             return;
         }
     }
+    if (!mixed && p.wave_cap > 0) {  // layout 0: only the first wave_cap wave warps of a CTA work
+        const int first_wave = min(wpc, max(0, p.prep_warps - (int)blockIdx.x * wpc));
+        if (wid - first_wave >= p.wave_cap) return;
+    }
     WaveSlot& sm = *reinterpret_cast<WaveSlot*>(slot);
     int cur = -1;  // field whose arguments sit in the warp's slot
     for (;;) {
@@ -1270,7 +1268,7 @@ static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const
     // with SL, MoP or the learned predictor a share of the warps works the
     // prep queue; the most warps whose slots fit the shared memory
     const bool prep = UMAX > 0 && p.queue_len > 0;
-    const bool mixed = prep && tune.mixed != 0;
+    const bool mixed = prep && tune.mixed == 1;
     const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
     const size_t uslot = std::max(pslot, wslot);  // layout 0: one slot size
     int wmax = kMaxWarpsPerCta;
@@ -1299,6 +1297,7 @@ static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const
     b.mixed = mixed ? 1 : 0;
     b.prep_per_cta = np;
     b.slot_bytes = (unsigned)uslot;
+    b.wave_cap = !mixed && tune.mixed >= 2 ? tune.mixed : 0;
     b.prep_warps = 0;
     if (prep && !mixed) {
         const int warps = nsm * per_sm * wpc;

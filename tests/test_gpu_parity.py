@@ -75,9 +75,9 @@ def test_sl_nonunit_spacing_and_host_input():
 
 @pytest.mark.parametrize("spacing", [(0.5, 0.25, 1.0), (0.125, 0.125, 1.0), (1.0, 1.0, 2.0)])
 def test_sl_power_of_two_spacing(spacing):
-    """CFL numbers that are powers of two take the fixed-point midpoint of the
-    semi-Lagrangian back-trace (exact, so the same predictions); large ones
-    make the back-trace take Euler substeps."""
+    """Other spacings of the semi-Lagrangian back-trace: CFL numbers that
+    are powers of two other than 2^-k, and large ones that make the
+    back-trace take Euler substeps."""
     dx, dy, dt = spacing
     uv = synth.vortex_sum(40, 52, 5, seed=9, drift=1.5)
     compare(uv, 1e-2, "sl", dx=dx, dy=dy, dt=dt)
