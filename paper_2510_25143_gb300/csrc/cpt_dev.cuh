@@ -163,11 +163,11 @@ __device__ __forceinline__ int min_alg2(int cur, int u0, int v0, int u1, int v1,
 // bounded vertex (its value is final when it is processed), neighbours 0 and 1
 // hold their current values, an uncertain neighbour's original value standing
 // in for a reconstruction within +-E of it (E bounds every |qhat - q|).
-// Returns 0 when, for any such reconstructions, M != 0 and a same-sign clause
-// holds with bound >= xi (the face cannot lower a bound that starts at xi);
-// 1 when the same-sign clause is guaranteed but M = 0 cannot be excluded (only
-// M needs evaluating once the reconstructions are known: M = 0 makes Alg. 2
-// return 0); 2 otherwise (the full Alg. 2 is needed).
+// Returns 1 when, for any such reconstructions, a same-sign clause holds with
+// bound >= xi: the face can then only lower the bound through M = 0 (Alg. 2
+// returns 0), which the encoder checks with the actual reconstructions (a
+// face whose M cannot reach 0 passes that check); 2 otherwise (the full Alg. 2
+// is needed).
 __device__ __forceinline__ int unc_face_class(int2 a0, int2 a1, int2 c, bool p0, bool p1, int E, int xi) {
     const int m0 = p0 ? E : 0, m1 = p1 ? E : 0;
     const bool su = (c.x > 0 && a0.x > m0 && a1.x > m1) || (c.x < 0 && a0.x < -m0 && a1.x < -m1);
@@ -175,17 +175,7 @@ __device__ __forceinline__ int unc_face_class(int2 a0, int2 a1, int2 c, bool p0,
     int fl = -1;
     if (su) fl = abs(c.x) - 1;
     if (sv) fl = max(fl, abs(c.y) - 1);
-    if (fl < xi) return 2;
-    // With a0' = a0 + d0, a1' = a1 + d1 (|d|_inf <= E, zero for exact values):
-    // M' = M + det(d0, a1 - c) + det(d1, c - a0) + det(d0, d1).
-    long long M = (long long)(a1.x - a0.x) * (c.y - a0.y) - (long long)(a1.y - a0.y) * (c.x - a0.x);
-    M = M < 0 ? -M : M;
-    const long long e = E;
-    long long D = 0;
-    if (p0) D += e * ((long long)abs(a1.x - c.x) + abs(a1.y - c.y));
-    if (p1) D += e * ((long long)abs(c.x - a0.x) + abs(c.y - a0.y));
-    if (p0 && p1) D += 2 * e * e;
-    return M > D ? 0 : 1;
+    return fl < xi ? 2 : 1;
 }
 
 // M of Alg. 2 (twice the signed area of the triangle of values) is zero.

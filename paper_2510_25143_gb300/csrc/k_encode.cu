@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict
                 // Fast path (exact): every existing neighbour keeps the vertex's
                 // strict sign of u (or of v), with margin E where its value may
                 // still change, and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on
-                // every face unless M = 0, and no uncertain face needs the full
-                // Alg. 2: it is class 1 when |M| <= D, else class 0.
-                // M = det(n_a - q, n_b - q).  The sign tests are minima and
-                // maxima over the uncertain neighbours (0..6) and the others.
+                // every face unless M = 0 (M = det(n_a - q, n_b - q)), and no
+                // uncertain face needs the full Alg. 2.  The sign tests are
+                // minima and maxima over the uncertain neighbours (0..6) and
+                // the others.
                 bool fast = false;
 #pragma unroll
                 for (int c = 0; c < 2 && !fast; ++c) {
@@ -190,12 +190,11 @@ __global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict
                 }
                 if (fast) {
                     // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
-                    int dx[14], dy[14], l1[14];
+                    int dx[14], dy[14];
 #pragma unroll
                     for (int k = 0; k < 14; ++k) {
                         dx[k] = nb[k].x - qv.x;
                         dy[k] = nb[k].y - qv.y;
-                        l1[k] = abs(dx[k]) + abs(dy[k]);
                     }
                     bool mz = false;
 #define CPT_CERT_M(a, b) \
@@ -205,19 +204,14 @@ __global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict
                     if (mz) {
                         xi = 0;
                     } else {
-                        const int lg = 31 - __clz(E);
+                        // every existing uncertain face keeps the same-sign
+                        // clause; only its M = 0 check remains, done by the
+                        // wave with the actual reconstructions (a face whose M
+                        // cannot reach 0 passes that check anyway)
                         int bit = 0;
-#define CPT_UNC_FAST(a, b)                                                                                  \
-    if ((valid >> (a)) & (valid >> (b)) & 1u) {                                                             \
-        long long M = (long long)dx[a] * dy[b] - (long long)dy[a] * dx[b];                                  \
-        M = M < 0 ? -M : M;                                                                                 \
-        long long D = (long long)((is_uncertain(a) ? l1[b] : 0) + (is_uncertain(b) ? l1[a] : 0)) << lg;    \
-        if (is_uncertain(a) && is_uncertain(b)) D += 2ll << (2 * lg);                                       \
-        if (M <= D) um_m |= 1u << bit;                                                                      \
-    }                                                                                                       \
-    ++bit;
-                        CPT_UNC_FACES(CPT_UNC_FAST)
-#undef CPT_UNC_FAST
+#define CPT_UNC_VALID(a, b) um_m |= ((valid >> (a)) & (valid >> (b)) & 1u) << bit; ++bit;
+                        CPT_UNC_FACES(CPT_UNC_VALID)
+#undef CPT_UNC_VALID
                     }
                 } else {
                     slow = true;

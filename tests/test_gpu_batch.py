@@ -80,7 +80,8 @@ def test_autotune_keeps_bytes():
     ref, _, _ = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop")
     tuned, _, b = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop", tune=True)
     assert tuned == ref
-    assert b["schedule"][0] in (25, 35, 45, 55) and b["schedule"][3] in (64, 128)
+    # one of the MoP candidates: prediction-warp share 35..80 %, slack 64 or 128
+    assert 35 <= b["schedule"][0] <= 80 and b["schedule"][3] in (64, 128)
     again, _, b2 = cpt.compress_batch([_dev(uv) for uv in fields], 5e-3, pred="mop", tune=True)
     assert again == ref and b2["ms_tune"] == 0.0 and b2["schedule"] == b["schedule"]  # cached
 
