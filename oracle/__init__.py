@@ -145,8 +145,8 @@ def _declare(L):
     L.o_quantize.argtypes = [i64, i64, i64, P(i64)]
     L.o_lorenzo.restype = i64
     L.o_lorenzo.argtypes = [P(i32)] + [C.c_int] * 6
-    L.o_sl_predict.argtypes = [P(i32), C.c_int, C.c_int, C.c_int, C.c_int, dbl, dbl, P(i64), P(i64)]
-    L.o_cfl.restype = dbl
+    L.o_sl_predict.argtypes = [P(i32), C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, P(i64), P(i64)]
+    L.o_cfl.restype = C.c_float
     L.o_cfl.argtypes = [dbl, dbl, C.c_int]
     L.o_ilog2_q32.restype = u64
     L.o_ilog2_q32.argtypes = [C.c_uint32]
@@ -262,7 +262,8 @@ def lorenzo(Q, t, i, j, c):
 
 
 def sl_predict(P, i, j, cfl_x, cfl_y):
-    """P: reconstructed slice t-1, int32 [H][W][2]."""
+    """P: reconstructed slice t-1, int32 [H][W][2]; cfl_x, cfl_y are rounded
+    to binary32, the precision of the back-trace."""
     P = np.ascontiguousarray(P, np.int32)
     H, W, _ = P.shape
     pu, pv = C.c_int64(), C.c_int64()

@@ -342,28 +342,34 @@ i64 o_lorenzo(const int32_t* Q, int H, int W, int t, int i, int j, int c) {
            qat(Q, H, W, t - 1, i, j - 1, c) + qat(Q, H, W, t - 1, i - 1, j - 1, c);
 }
 
+/* The SL predictor runs in IEEE binary32 (reading R9): Sec. VI-A fixes no
+ * precision, the fields are single precision (Sec. V), and the prediction is
+ * an integer guess both sides reproduce.  Every float operation below is one
+ * correctly rounded IEEE operation (built with -ffp-contract=off; binary32
+ * arithmetic has no excess precision on x86-64 or AArch64). */
+
 /* Bilinear interpolation I_bil of one component of slice P (Eq. 6), at a
  * position already clamped to [0,W-1]x[0,H-1].  x is the column, y the row. */
-static double bilinear(const int32_t* P, int H, int W, int c, double x, double y) {
-    double xf = floor(x), yf = floor(y);
+static float bilinear(const int32_t* P, int H, int W, int c, float x, float y) {
+    float xf = floorf(x), yf = floorf(y);
     int x0 = (int)xf, y0 = (int)yf;
     int x1 = x0 + 1 < W ? x0 + 1 : W - 1;
     int y1 = y0 + 1 < H ? y0 + 1 : H - 1;
-    double fx = x - xf, fy = y - yf;
-    double gx = 1.0 - fx, gy = 1.0 - fy;
-    double f00 = (double)P[2 * ((i64)y0 * W + x0) + c];
-    double f10 = (double)P[2 * ((i64)y0 * W + x1) + c];
-    double f01 = (double)P[2 * ((i64)y1 * W + x0) + c];
-    double f11 = (double)P[2 * ((i64)y1 * W + x1) + c];
-    double w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
-    double p = w00 * f00 + w10 * f10;
+    float fx = x - xf, fy = y - yf;
+    float gx = 1.0f - fx, gy = 1.0f - fy;
+    float f00 = (float)P[2 * ((i64)y0 * W + x0) + c];
+    float f10 = (float)P[2 * ((i64)y0 * W + x1) + c];
+    float f01 = (float)P[2 * ((i64)y1 * W + x0) + c];
+    float f11 = (float)P[2 * ((i64)y1 * W + x1) + c];
+    float w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
+    float p = w00 * f00 + w10 * f10;
     p = p + w01 * f01;
     p = p + w11 * f11;
     return p;
 }
 
-static inline double clampd(double x, double hi) {
-    if (x < 0.0) return 0.0;
+static inline float clampf(float x, float hi) {
+    if (x < 0.0f) return 0.0f;
     if (x > hi) return hi;
     return x;
 }
@@ -372,44 +378,45 @@ static inline double clampd(double x, double hi) {
  * reconstructed slice t-1 ([H][W][2]); the departure point of grid point
  * (i,j) is traced back with the velocity of slice t-1 and both components are
  * sampled there.  Returns the mode used: 0 RK2, N>0 number of Euler substeps. */
-int o_sl_predict(const int32_t* P, int H, int W, int i, int j, double cfl_x, double cfl_y,
+int o_sl_predict(const int32_t* P, int H, int W, int i, int j, float cfl_x, float cfl_y,
                  i64* pu, i64* pv) {
     const int32_t* g = P + 2 * ((i64)i * W + j);
-    double du = (double)g[0] * cfl_x;
-    double dv = (double)g[1] * cfl_y;
-    double dinf = fabs(du) > fabs(dv) ? fabs(du) : fabs(dv);
-    double xs, ys;
+    float du = (float)g[0] * cfl_x;
+    float dv = (float)g[1] * cfl_y;
+    float dinf = fabsf(du) > fabsf(dv) ? fabsf(du) : fabsf(dv);
+    float xs, ys;
     int mode;
-    if (dinf <= 2.0) {
+    if (dinf <= 2.0f) {
         /* RK2 midpoint (Eqs. 7-8) */
-        double xh = clampd((double)j - 0.5 * du, (double)(W - 1));
-        double yh = clampd((double)i - 0.5 * dv, (double)(H - 1));
-        double uh = bilinear(P, H, W, 0, xh, yh);
-        double vh = bilinear(P, H, W, 1, xh, yh);
-        xs = clampd((double)j - uh * cfl_x, (double)(W - 1));
-        ys = clampd((double)i - vh * cfl_y, (double)(H - 1));
+        float xh = clampf((float)j - 0.5f * du, (float)(W - 1));
+        float yh = clampf((float)i - 0.5f * dv, (float)(H - 1));
+        float uh = bilinear(P, H, W, 0, xh, yh);
+        float vh = bilinear(P, H, W, 1, xh, yh);
+        xs = clampf((float)j - uh * cfl_x, (float)(W - 1));
+        ys = clampf((float)i - vh * cfl_y, (float)(H - 1));
         mode = 0;
     } else {
         /* adaptive Euler substepping (Eq. 9) */
-        double nd = ceil(dinf / 2.0);
-        int N = nd > 32.0 ? 32 : (int)nd;
-        double sx = cfl_x / (double)N, sy = cfl_y / (double)N;
-        xs = (double)j;
-        ys = (double)i;
+        float nd = ceilf(dinf / 2.0f);
+        int N = nd > 32.0f ? 32 : (int)nd;
+        float sx = cfl_x / (float)N, sy = cfl_y / (float)N;
+        xs = (float)j;
+        ys = (float)i;
         for (int s = 0; s < N; ++s) {
-            double us = bilinear(P, H, W, 0, xs, ys);
-            double vs = bilinear(P, H, W, 1, xs, ys);
-            xs = clampd(xs - us * sx, (double)(W - 1));
-            ys = clampd(ys - vs * sy, (double)(H - 1));
+            float us = bilinear(P, H, W, 0, xs, ys);
+            float vs = bilinear(P, H, W, 1, xs, ys);
+            xs = clampf(xs - us * sx, (float)(W - 1));
+            ys = clampf(ys - vs * sy, (float)(H - 1));
         }
         mode = N;
     }
-    *pu = (i64)floor(bilinear(P, H, W, 0, xs, ys) + 0.5);
-    *pv = (i64)floor(bilinear(P, H, W, 1, xs, ys) + 0.5);
+    *pu = (i64)floorf(bilinear(P, H, W, 0, xs, ys) + 0.5f);
+    *pv = (i64)floorf(bilinear(P, H, W, 1, xs, ys) + 0.5f);
     return mode;
 }
 
-double o_cfl(double d_t, double d_x, int k) { return ldexp(d_t / d_x, -k); }
+/* CFL number dt / (dx * S), S = 2^k, rounded once to binary32 */
+float o_cfl(double d_t, double d_x, int k) { return (float)ldexp(d_t / d_x, -k); }
 
 /* ------------------------------------------------------------------------ */
 /* MoP scoring (Sec. VI-B; reading R11).                                       */
@@ -806,7 +813,7 @@ void o_net_predict(const uint16_t* model, const int32_t* prev, int H, int W, int
 /* Score of one block (Sec. VI) with mode 0 = 3DL, 1 = SL, 2 = the learned
  * predictions npred of the slice (the learned mixture). */
 static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx, int B, int n,
-                           int mode, i64 xiq, double cfl_x, double cfl_y, const int32_t* npred,
+                           int mode, i64 xiq, float cfl_x, float cfl_y, const int32_t* npred,
                            int32_t* cand, uint32_t* hist) {
     int i0 = by * B, j0 = bx * B;
     int i1 = i0 + B < H ? i0 + B : H, j1 = j0 + B < W ? j0 + B : W;
@@ -854,8 +861,8 @@ static i64 mop_block_score(const int32_t* Q, int H, int W, int t, int by, int bx
     return o_score_q32(hist, nv, nf, B);
 }
 
-static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 xiq, double cfl_x,
-                      double cfl_y, const int32_t* npred /* NULL: SL */, uint8_t* modes /* nby*nbx */,
+static void mop_modes(const int32_t* Q, int H, int W, int t, int B, int n, i64 xiq, float cfl_x,
+                      float cfl_y, const int32_t* npred /* NULL: SL */, uint8_t* modes /* nby*nbx */,
                       o_stats* st) {
     int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * 2 * (B + 1) * (B + 1));
@@ -917,7 +924,7 @@ int o_compress2(const float* uv, int H, int W, int T, double d_x, double d_y, do
     o_face_masks(q, H, W, T, mask);
     for (i64 v = 0; v < N; ++v)
         for (int b = 0; b < 12; ++b) S.crossed_faces += (mask[v] >> b) & 1u;
-    double cfl_x = o_cfl(d_t, d_x, S.k), cfl_y = o_cfl(d_t, d_y, S.k);
+    float cfl_x = o_cfl(d_t, d_x, S.k), cfl_y = o_cfl(d_t, d_y, S.k);
     i64 xiq_eps = eps_int >= 1 ? (i64)1 << floor_log2_u64((u64)eps_int) : 0;
     if (t_end > T || t_end < 0) t_end = T;
     u64 nqd = 0, nld = 0;
@@ -1099,7 +1106,7 @@ int o_decompress(const uint8_t* in, size_t nbytes, int* dims /* H W T k */, int3
     off += used;
     if ((nbytes - off) / 4 < nld) { free(xs); free(Q); free(qd); return O_ERR_CORRUPT; }
     const uint8_t* ldp = in + off;
-    double cfl_x = o_cfl(d_t, d_x, k), cfl_y = o_cfl(d_t, d_y, k);
+    float cfl_x = o_cfl(d_t, d_x, k), cfl_y = o_cfl(d_t, d_y, k);
     u64 iq = 0, il = 0;
     int32_t* npred = has_net ? (int32_t*)malloc(sizeof(int32_t) * 2 * H * W) : NULL;
     if (has_net && !npred) rc = O_ERR_OOM;

@@ -240,102 +240,41 @@ __device__ __forceinline__ unsigned quantize(int q, int p, int xiq, int& qhat) {
 }
 
 // ---------------------------------------------------------------------------
-// Semi-Lagrangian predictor (Sec. VI-A, Eqs. 5-9) in FP64 with a fixed
-// evaluation order (no contraction): x = column moves by u*CFL_x, y = row by
-// v*CFL_y; RK2 midpoint when d_inf <= 2, otherwise N = min(ceil(d_inf/2), 32)
-// Euler substeps; every position is clamped to the domain before sampling;
-// the prediction is floor(p + 0.5).  P = reconstructed slice t-1 [H][W].
+// Semi-Lagrangian predictor (Sec. VI-A, Eqs. 5-9) in IEEE binary32 with a
+// fixed evaluation order (no contraction; every product and sum rounded to
+// nearest): x = column moves by u*CFL_x, y = row by v*CFL_y; RK2 midpoint when
+// d_inf <= 2, otherwise N = min(ceil(d_inf/2), 32) Euler substeps; every
+// position is clamped to the domain before sampling; the prediction is
+// floor(p + 0.5).  P = reconstructed slice t-1 [H][W].  The section fixes no
+// precision; the fields are single precision (Sec. V), and the prediction is
+// only an integer guess that encoder and decoder reproduce bit for bit, so
+// binary32 is used (GB300's FP64 rate is a small fraction of its FP32 rate).
 // ---------------------------------------------------------------------------
-//
-// FP64 arithmetic is scarce on this part (about 20 SM cycles per warp
-// instruction, shared by the SM), so the steps that are exact by definition
-// run on the integer pipes from the IEEE binary64 bit layout: integer to
-// double conversion, comparisons of finite values, and floor / fractional
-// part of a non-negative position.  They return the very bits the FP64
-// instructions would; only the rounded products and sums stay in FP64.
-// ---------------------------------------------------------------------------
-// (double)n, exact: sign, exponent from the bit length, mantissa shifted up.
-__device__ __forceinline__ double i2d(int n) {
-    const unsigned neg = n < 0 ? 1u : 0u;
-    const unsigned m = neg ? 0u - (unsigned)n : (unsigned)n;
-    const int e = 31 - __clz(m | 1u);
-    const unsigned long long mant = ((unsigned long long)m << (52 - e)) & 0xFFFFFFFFFFFFFull;
-    const unsigned long long bits =
-        ((unsigned long long)neg << 63) | ((unsigned long long)(e + 1023) << 52) | mant;
-    return m ? __longlong_as_double((long long)bits) : 0.0;
-}
-
-// Position clamp to [0, hi] for finite x and hi >= 0: a finite double below
-// zero has the sign bit set (and is not -0.0); non-negative doubles order as
-// their bit patterns do.
-__device__ __forceinline__ double clamp_pos(double x, double hi) {
-    const long long b = __double_as_longlong(x);
-    if (b < 0 && b != (long long)0x8000000000000000ull) return 0.0;
-    if (b > __double_as_longlong(hi)) return hi;
+__device__ __forceinline__ float clamp_pos(float x, float hi) {
+    if (x < 0.0f) return 0.0f;
+    if (x > hi) return hi;
     return x;
-}
-
-// |a| > |b| and a <= c for finite doubles, from their bit patterns
-__device__ __forceinline__ bool abs_greater(double a, double b) {
-    return (__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll) > (__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFll);
-}
-
-// floor(x) as an int and x - floor(x) (exact) for 0 <= x < 2^31.
-__device__ __forceinline__ int floor_frac(double x, double& frac) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-    const int e = (int)(b >> 52) - 1023;
-    if (e < 0) {  // x < 1 (including zero)
-        frac = __longlong_as_double((long long)b);
-        return 0;
-    }
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 52 - e;  // fraction bits
-    const int ip = (int)(m >> sh);
-    const unsigned long long f = m & ((1ull << sh) - 1ull);  // fraction * 2^sh
-    if (f == 0) {
-        frac = 0.0;
-        return ip;
-    }
-    // f * 2^-sh, normalised: the leading bit of f moves to bit 52
-    const int lz = __clzll((long long)f) - 11;  // f < 2^52: lz >= 1
-    const unsigned long long mf = (f << lz) & 0xFFFFFFFFFFFFFull;
-    const int ef = 1023 + 52 - lz - sh;  // the leading bit of f is bit 52 - lz: value < 1, normal
-    frac = __longlong_as_double((long long)(((unsigned long long)ef << 52) | mf));
-    return ip;
-}
-
-// floor(x) as an int for finite |x| < 2^31
-__device__ __forceinline__ int floor_int(double x) {
-    const long long sb = __double_as_longlong(x);
-    const unsigned long long b = (unsigned long long)sb & 0x7FFFFFFFFFFFFFFFull;
-    const bool neg = sb < 0;
-    const int e = (int)(b >> 52) - 1023;
-    if (e < 0) return (neg && b != 0) ? -1 : 0;
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 52 - e;
-    const int ip = (int)(m >> sh);
-    const bool fr = (m & ((1ull << sh) - 1ull)) != 0;
-    return neg ? (fr ? -ip - 1 : -ip) : ip;
 }
 
 struct Bil {
     int x0, x1, y0, y1;
-    double w00, w10, w01, w11;
+    float w00, w10, w01, w11;
 };
 
 // bilinear stencil of a clamped (non-negative) position
-__device__ __forceinline__ Bil bil_weights(double x, double y, int H, int W) {
+__device__ __forceinline__ Bil bil_weights(float x, float y, int H, int W) {
     Bil b;
-    double fx, fy;
-    b.x0 = floor_frac(x, fx);
-    b.y0 = floor_frac(y, fy);
+    const float xf = floorf(x), yf = floorf(y);
+    b.x0 = (int)xf;
+    b.y0 = (int)yf;
     b.x1 = b.x0 + 1 < W ? b.x0 + 1 : W - 1;
     b.y1 = b.y0 + 1 < H ? b.y0 + 1 : H - 1;
-    const double gx = __dsub_rn(1.0, fx), gy = __dsub_rn(1.0, fy);
-    b.w00 = __dmul_rn(gx, gy);
-    b.w10 = __dmul_rn(fx, gy);
-    b.w01 = __dmul_rn(gx, fy);
-    b.w11 = __dmul_rn(fx, fy);
+    const float fx = __fsub_rn(x, xf), fy = __fsub_rn(y, yf);
+    const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
+    b.w00 = __fmul_rn(gx, gy);
+    b.w10 = __fmul_rn(fx, gy);
+    b.w01 = __fmul_rn(gx, fy);
+    b.w11 = __fmul_rn(fx, fy);
     return b;
 }
 
@@ -353,57 +292,55 @@ struct SmemSlice {
     __device__ __forceinline__ int2 at(int i, int j) const { return S[(i - i_org) * pitch + (j - j_org)]; }
 };
 
+// both components at one stencil: the four corners are read once
 template <class Slice>
-__device__ __forceinline__ double bil_sample(const Bil& b, const Slice& P, int c) {
+__device__ __forceinline__ float2 bil_sample2(const Bil& b, const Slice& P) {
     const int2 a00 = P.at(b.y0, b.x0), a10 = P.at(b.y0, b.x1);
     const int2 a01 = P.at(b.y1, b.x0), a11 = P.at(b.y1, b.x1);
-    const double f00 = i2d(c ? a00.y : a00.x), f10 = i2d(c ? a10.y : a10.x);
-    const double f01 = i2d(c ? a01.y : a01.x), f11 = i2d(c ? a11.y : a11.x);
-    double p = __dadd_rn(__dmul_rn(b.w00, f00), __dmul_rn(b.w10, f10));
-    p = __dadd_rn(p, __dmul_rn(b.w01, f01));
-    p = __dadd_rn(p, __dmul_rn(b.w11, f11));
-    return p;
+    float pu = __fadd_rn(__fmul_rn(b.w00, __int2float_rn(a00.x)), __fmul_rn(b.w10, __int2float_rn(a10.x)));
+    pu = __fadd_rn(pu, __fmul_rn(b.w01, __int2float_rn(a01.x)));
+    pu = __fadd_rn(pu, __fmul_rn(b.w11, __int2float_rn(a11.x)));
+    float pv = __fadd_rn(__fmul_rn(b.w00, __int2float_rn(a00.y)), __fmul_rn(b.w10, __int2float_rn(a10.y)));
+    pv = __fadd_rn(pv, __fmul_rn(b.w01, __int2float_rn(a01.y)));
+    pv = __fadd_rn(pv, __fmul_rn(b.w11, __int2float_rn(a11.y)));
+    return make_float2(pu, pv);
 }
 
 // returns 0 for RK2, N for N substeps
 template <class Slice>
-__device__ __forceinline__ int sl_predict(const Slice& P, int H, int W, int i, int j, double cfl_x,
-                                          double cfl_y, int& pu, int& pv) {
+__device__ __forceinline__ int sl_predict(const Slice& P, int H, int W, int i, int j, float cfl_x, float cfl_y,
+                                          int& pu, int& pv) {
     const int2 g = P.at(i, j);
-    const double du = __dmul_rn(i2d(g.x), cfl_x);
-    const double dv = __dmul_rn(i2d(g.y), cfl_y);
-    const double dinf = abs_greater(du, dv) ? fabs(du) : fabs(dv);
-    const double jd = i2d(j), id = i2d(i);
-    double xs, ys;
+    const float du = __fmul_rn(__int2float_rn(g.x), cfl_x);
+    const float dv = __fmul_rn(__int2float_rn(g.y), cfl_y);
+    const float dinf = fabsf(du) > fabsf(dv) ? fabsf(du) : fabsf(dv);
+    const float jd = __int2float_rn(j), id = __int2float_rn(i);
+    const float xmax = __int2float_rn(W - 1), ymax = __int2float_rn(H - 1);
+    float xs, ys;
     int mode;
-    const double xmax = i2d(W - 1), ymax = i2d(H - 1);
-    if (__double_as_longlong(dinf) <= __double_as_longlong(2.0)) {  // dinf <= 2 (dinf >= 0)
-        const double xh = clamp_pos(__dsub_rn(jd, __dmul_rn(0.5, du)), xmax);
-        const double yh = clamp_pos(__dsub_rn(id, __dmul_rn(0.5, dv)), ymax);
-        const Bil b = bil_weights(xh, yh, H, W);
-        const double uh = bil_sample(b, P, 0);
-        const double vh = bil_sample(b, P, 1);
-        xs = clamp_pos(__dsub_rn(jd, __dmul_rn(uh, cfl_x)), xmax);
-        ys = clamp_pos(__dsub_rn(id, __dmul_rn(vh, cfl_y)), ymax);
+    if (dinf <= 2.0f) {
+        const float xh = clamp_pos(__fsub_rn(jd, __fmul_rn(0.5f, du)), xmax);
+        const float yh = clamp_pos(__fsub_rn(id, __fmul_rn(0.5f, dv)), ymax);
+        const float2 h = bil_sample2(bil_weights(xh, yh, H, W), P);
+        xs = clamp_pos(__fsub_rn(jd, __fmul_rn(h.x, cfl_x)), xmax);
+        ys = clamp_pos(__fsub_rn(id, __fmul_rn(h.y, cfl_y)), ymax);
         mode = 0;
     } else {
-        const double nd = ceil(__ddiv_rn(dinf, 2.0));
-        const int N = nd > 32.0 ? 32 : (int)nd;
-        const double sx = __ddiv_rn(cfl_x, i2d(N)), sy = __ddiv_rn(cfl_y, i2d(N));
+        const float nd = ceilf(__fmul_rn(dinf, 0.5f));  // dinf / 2, exact
+        const int N = nd > 32.0f ? 32 : (int)nd;
+        const float sx = __fdiv_rn(cfl_x, __int2float_rn(N)), sy = __fdiv_rn(cfl_y, __int2float_rn(N));
         xs = jd;
         ys = id;
         for (int st = 0; st < N; ++st) {
-            const Bil b = bil_weights(xs, ys, H, W);
-            const double us = bil_sample(b, P, 0);
-            const double vs = bil_sample(b, P, 1);
-            xs = clamp_pos(__dsub_rn(xs, __dmul_rn(us, sx)), xmax);
-            ys = clamp_pos(__dsub_rn(ys, __dmul_rn(vs, sy)), ymax);
+            const float2 s = bil_sample2(bil_weights(xs, ys, H, W), P);
+            xs = clamp_pos(__fsub_rn(xs, __fmul_rn(s.x, sx)), xmax);
+            ys = clamp_pos(__fsub_rn(ys, __fmul_rn(s.y, sy)), ymax);
         }
         mode = N;
     }
-    const Bil b = bil_weights(xs, ys, H, W);
-    pu = floor_int(__dadd_rn(bil_sample(b, P, 0), 0.5));
-    pv = floor_int(__dadd_rn(bil_sample(b, P, 1), 0.5));
+    const float2 p = bil_sample2(bil_weights(xs, ys, H, W), P);
+    pu = (int)floorf(__fadd_rn(p.x, 0.5f));
+    pv = (int)floorf(__fadd_rn(p.y, 0.5f));
     return mode;
 }
 

@@ -200,6 +200,23 @@ struct Writer {
     void raw(const void* src, size_t m) { std::memcpy(p + n, src, m); n += m; }
 };
 
+// CFL number of the SL predictor: dt / (dx * S) with S = 2^k, rounded once to
+// binary32 (the precision of the back-trace).
+static float sl_cfl(double dt, double dx, int k) { return (float)std::ldexp(dt / dx, -k); }
+
+// Reach of the SL back-trace into slice t-1 (rows and columns around a unit)
+// when no reconstruction exceeds qmax in magnitude.  The exact displacement
+// is at most qmax * CFL; the binary32 evaluation adds at most a few units in
+// the last place to the bilinear sums (relative < 2^-20 altogether) and to
+// the positions (< 2^-8 of a cell over 32 substeps); the bilinear stencil
+// adds one cell and one more cell covers those roundings.  A clamped position
+// never leaves the domain, so max(H, W) + 2 always suffices.
+static int sl_reach(double qmax, float cfl_x, float cfl_y, int H, int W) {
+    const double c = std::max((double)cfl_x, (double)cfl_y);
+    const double reach = std::ceil(qmax * c * (1.0 + std::ldexp(1.0, -20))) + 2.0;
+    return (int)std::min(reach, (double)std::max(H, W) + 2.0);
+}
+
 static constexpr uint32_t kMaxCodeLen = 24;
 static constexpr long long kOrderStrip = 32;         // wave ticket order: strip weight
 static constexpr long long kOrderSliceLorenzo = 2;   // slice weight without prep units
@@ -635,8 +652,8 @@ struct FieldJob {
         A.pred = (int)prm->pred;
         A.B = B; A.n = nstride; A.nby = nby; A.nbx = nbx;
         A.nchunks = nchunks;
-        A.cfl_x = std::ldexp(dt / dx, -k);
-        A.cfl_y = std::ldexp(dt / dy, -k);
+        A.cfl_x = sl_cfl(dt, dx, k);
+        A.cfl_y = sl_cfl(dt, dy, k);
         // Reach of the semi-Lagrangian back-trace into slice t-1: no
         // reconstruction exceeds max|q| + E in magnitude, every displacement is
         // at most that times CFL, the bilinear stencil adds one cell, and one
@@ -647,8 +664,7 @@ struct FieldJob {
         } else if (want_sl) {
             qmax = std::ceil((double)am * std::ldexp(1.0, k)) +
                    (eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)eps_int))) : 0.0);
-            const double reach = std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0;
-            A.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
+            A.R = sl_reach(qmax, A.cfl_x, A.cfl_y, H, W);
         }
         if (has_net) A.net = *net;
         A.log2tab = d_log2;
@@ -1013,22 +1029,23 @@ static std::vector<PipeTuning> tuning_candidates(int pred) {
         for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, 3, 0});
         for (int kl : {1, 2, 8}) c.push_back({0, 0, kl, 0, 0, 8});
     } else if (pred == CPT_PRED_SL) {
-        // large slices are bound by the throughput of the prediction units:
-        // shares up to 75 % of the warps pay there; small ones by the lag.
-        // At most 8 working wave warps per CTA keep the wave steps short.
+        // large slices balance the prediction units' throughput against the
+        // wave steps (about 45 % of the warps on prediction units); small
+        // ones are bound by the lag.  At most 8 working wave warps per CTA
+        // keep the wave steps short.
         c.push_back({45, 8, 0, 0, 3, 0});
         for (int u : {8, 16})
-            for (int share : {35, 55, 65, 75}) c.push_back({share, u, 0, 0, 0, 0});
-        for (int share : {55, 65}) c.push_back({share, 8, 0, 0, 0, 8});
+            for (int share : {25, 35, 45, 55, 65}) c.push_back({share, u, 0, 0, 0, 0});
+        for (int share : {35, 45, 55}) c.push_back({share, 8, 0, 0, 0, 8});
     } else if (pred == CPT_PRED_LEARNED) {
         for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED_MOP) {
         for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 64, 0, 0});
     } else {
         c.push_back({45, 0, 0, 64, 3, 0});
-        for (int share : {35, 55, 65, 70, 75, 80}) c.push_back({share, 0, 0, 64, 0, 0});
-        for (int share : {70, 75, 80}) c.push_back({share, 0, 0, 64, 0, 8});
-        c.push_back({75, 0, 0, 128, 0, 0});
+        for (int share : {25, 35, 45, 55, 65, 75}) c.push_back({share, 0, 0, 64, 0, 0});
+        for (int share : {35, 45, 55, 65}) c.push_back({share, 0, 0, 64, 0, 8});
+        c.push_back({45, 0, 0, 128, 0, 0});
     }
     return c;
 }
@@ -1841,16 +1858,15 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
         A.pred = (int)prm->pred;
         A.B = B; A.n = F.nstride; A.nby = F.nby; A.nbx = F.nbx;
         A.nchunks = (W + 31) / 32;
-        A.cfl_x = std::ldexp(F.dt / F.dx, -k);
-        A.cfl_y = std::ldexp(F.dt / F.dy, -k);
+        A.cfl_x = sl_cfl(F.dt, F.dx, k);
+        A.cfl_y = sl_cfl(F.dt, F.dy, k);
         A.R = 0;
         if (F.want_sl && F.has_net) {
             A.R = kNetReach;
         } else if (F.want_sl) {
             const double qmax = std::ceil((double)F.am * std::ldexp(1.0, k)) +
                                 (F.eps_int > 0 ? std::ldexp(1.0, (int)std::floor(std::log2((double)F.eps_int))) : 0.0);
-            const double reach = std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0;
-            A.R = (int)std::min(reach, (double)std::max(H, W) + 2.0);
+            A.R = sl_reach(qmax, A.cfl_x, A.cfl_y, H, W);
         }
         if (F.has_net) A.net = net;
         A.log2tab = d_lg;
@@ -2341,8 +2357,8 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     A.pred = pred;
     A.B = B; A.n = stride_hdr; A.nby = nby; A.nbx = nbx;
     A.nchunks = (W + 31) / 32;
-    A.cfl_x = std::ldexp(dt / dx, -k);
-    A.cfl_y = std::ldexp(dt / dy, -k);
+    A.cfl_x = sl_cfl(dt, dx, k);
+    A.cfl_y = sl_cfl(dt, dy, k);
     // Reach of the back-trace: |qhat| <= 2^23 + E for every stream (the
     // fixed-point scale keeps |q| <= 2^23, the quantiser moves a value by at
     // most E), so no displacement exceeds that times CFL.
@@ -2350,7 +2366,7 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
         A.R = kNetReach;
     } else if (want_sl) {
         const double qmax = 8388608.0 + (eps_int > 0 ? std::ldexp(1.0, 31 - __builtin_clz((unsigned)eps_int)) : 0.0);
-        A.R = (int)std::min(std::ceil(qmax * std::max(A.cfl_x, A.cfl_y)) + 2.0, (double)std::max(H, W) + 2.0);
+        A.R = sl_reach(qmax, A.cfl_x, A.cfl_y, H, W);
     }
     if (has_net) {
         float* d_net;

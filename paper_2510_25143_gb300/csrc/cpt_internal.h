@@ -60,7 +60,7 @@ struct SliceArgs {
     unsigned queue_len;     // prep units of the whole launch (every field)
     const unsigned long long* log2tab;  // [kLog2Tab] Q32 binary logarithms
     int R;                  // rows/columns of slice t-1 a prep tile may read beyond itself
-    double cfl_x, cfl_y;
+    float cfl_x, cfl_y;  // binary32 CFL numbers of the SL predictor
     int t_end;              // slices >= t_end are not encoded (their units are not queued)
     long long timeout_ns;
     // Decoding: the same pipeline rebuilds qhat from a stream.  cls then holds

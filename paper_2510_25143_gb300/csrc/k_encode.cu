@@ -45,8 +45,9 @@
 namespace cpt {
 
 constexpr int kPublishEvery = 8;   // steps between checks for prep units made ready
-constexpr int kPrepShareSL = 65;   // percent of the warps working prep units (SL)
-constexpr int kPrepShareMoP = 65;  // (MoP and the learned predictors)
+constexpr int kPrepShareSL = 45;   // percent of the warps working prep units (SL)
+constexpr int kPrepShareMoP = 45;  // (MoP)
+constexpr int kPrepShareNet = 65;  // (the learned predictors: the net's inference is the heavier side)
 constexpr int kNoSL = (int)0x80000000;  // psl marker: the block keeps 3DL (no prediction reaches it)
 
 __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, int j) {
@@ -1263,7 +1264,8 @@ static cudaError_t launch_pipeline_t(const PipeArgs& p, int pred, int nsm, const
     // prep queue; the most warps whose slots fit the shared memory
     const bool prep = UMAX > 0 && p.queue_len > 0;
     const bool mixed = prep && tune.mixed == 1;
-    const int share = tune.prep_share > 0 ? tune.prep_share : (pred == 1 ? kPrepShareSL : kPrepShareMoP);
+    const int share = tune.prep_share > 0 ? tune.prep_share
+                                          : (NET ? kPrepShareNet : (pred == 1 ? kPrepShareSL : kPrepShareMoP));
     const size_t uslot = std::max(pslot, wslot);  // layout 0: one slot size
     int wmax = kMaxWarpsPerCta;
     if (tune.warps_per_sm > 0) wmax = std::min(wmax, tune.warps_per_sm);

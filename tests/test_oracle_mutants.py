@@ -48,15 +48,15 @@ MUTANTS = [
     ("quantiser-bin-width", "Sec. V (linear quantisation)",
      "i64 w = 2 * xiq + 1;", "i64 w = 2 * xiq;"),
     ("sl-downstream-trace", "Eqs. 7-8",
-     "xs = clampd((double)j - uh * cfl_x, (double)(W - 1));",
-     "xs = clampd((double)j + uh * cfl_x, (double)(W - 1));"),
+     "xs = clampf((float)j - uh * cfl_x, (float)(W - 1));",
+     "xs = clampf((float)j + uh * cfl_x, (float)(W - 1));"),
     ("sl-u-v-swapped", "Eqs. 5-8",
-     "double du = (double)g[0] * cfl_x;", "double du = (double)g[1] * cfl_x;"),
+     "float du = (float)g[0] * cfl_x;", "float du = (float)g[1] * cfl_x;"),
     ("sl-substep-count", "Eq. 9",
-     "double nd = ceil(dinf / 2.0);", "double nd = ceil(dinf / 4.0);"),
+     "float nd = ceilf(dinf / 2.0f);", "float nd = ceilf(dinf / 4.0f);"),
     ("bilinear-weights-transposed", "Eq. 6",
-     "double w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;",
-     "double w00 = gx * gy, w10 = gx * fy, w01 = fx * gy, w11 = fx * fy;"),
+     "float w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;",
+     "float w00 = gx * gy, w10 = gx * fy, w01 = fx * gy, w11 = fx * fy;"),
     ("mop-switch-reversed", "Sec. VI-B",
      "uint8_t m = (1000 * rs < 997 * r3) ? 1 : 0;", "uint8_t m = (1000 * r3 < 997 * rs) ? 1 : 0;"),
     ("mop-penalty-weight", "Eq. 10",
@@ -73,8 +73,8 @@ MUTANTS = [
      "    i64 self = vid(H, W, t, i, j);\n    for (int type = 0; type < 12; ++type)\n        for (int k = 0; k < 3; ++k) {",
      "    i64 self = vid(H, W, t, i, j);\n    for (int type = 0; type < 12; ++type)\n        for (int k = 0; k < 2; ++k) {"),
     ("rk2-full-step-midpoint", "Eqs. 7-8 (midpoint)",
-     "double xh = clampd((double)j - 0.5 * du, (double)(W - 1));",
-     "double xh = clampd((double)j - 1.0 * du, (double)(W - 1));"),
+     "float xh = clampf((float)j - 0.5f * du, (float)(W - 1));",
+     "float xh = clampf((float)j - 1.0f * du, (float)(W - 1));"),
     ("trajectory-reverse-link-dropped", "Thm. 2 (faces joined through tets)",
      "if (nb[2 * c] < 0) nb[2 * c] = a; else nb[2 * c + 1] = a;", "(void)0;"),
     ("trajectory-walk-start", "Thm. 2 (paths from their ends)",
