@@ -310,8 +310,11 @@ def ours(args):
     nbytes = uv.nbytes
     d_uv = torch.from_numpy(uv).cuda()
     stream = torch.cuda.current_stream()
-    # the pipeline's schedule is autotuned on the first (warm-up) call
+    # the pipeline's schedule is autotuned on the first (warm-up) call,
+    # unless --schedule fixes it (profiling: every launch then has one shape)
     kw = dict(eb_mode="rel", pred=args.pred, verify=True, tune=True)
+    if args.schedule:
+        kw.update(tune=False, schedule=tuple(int(x) for x in args.schedule.split(",")))
 
     def step(src):
         # the stream stays in the library's host buffer (no Python copy)
@@ -656,6 +659,8 @@ def main():
     p.add_argument("--workload", default="turb1024", choices=["turb1024", "street512", "jets721", "vortex64"])
     p.add_argument("--slices", type=int, default=0, help="cut the workload to its first N slices (profiling)")
     p.add_argument("--pred", default="mop", choices=["lorenzo", "sl", "mop"])
+    p.add_argument("--schedule", default="", help="fixed pipeline schedule, six comma-separated integers "
+                   "(cpt_params.schedule) instead of the autotuned one")
     p.add_argument("--cpu-slices", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu", action="store_true")
