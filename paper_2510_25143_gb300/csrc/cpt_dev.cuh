@@ -183,6 +183,21 @@ __device__ __forceinline__ bool m_zero(int2 a0, int2 a1, int2 c) {
     return (long long)(a1.x - a0.x) * (c.y - a0.y) == (long long)(a1.y - a0.y) * (c.x - a0.x);
 }
 
+// Quotient and remainder of an unsigned x by a divisor d >= 1 known only at
+// run time, without a division per call: with m = floor((2^32 - 1) / d),
+// d m > 2^32 - 1 - d, so x m / 2^32 > x / d - 1 and the multiply-high estimate
+// is the quotient or one below it; one comparison corrects it.
+struct FastDiv {
+    unsigned d, m;
+    __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(0xFFFFFFFFu / dd) {}
+    __device__ __forceinline__ unsigned div(unsigned x) const {
+        unsigned q = __umulhi(x, m);
+        if (x - q * d >= d) ++q;
+        return q;
+    }
+    __device__ __forceinline__ unsigned mod(unsigned x) const { return x - div(x) * d; }
+};
+
 // ---------------------------------------------------------------------------
 // Quantisers.  The bound xi becomes xi_q = 2^floor(log2 xi) with code
 // floor(log2 xi)+1 (0 = lossless); the residual r = q - p becomes

@@ -479,44 +479,51 @@ __device__ long long warp_block_score(const uint16_t* smp, int nslots, int B, un
 template <class PS>
 __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int Rw) {
     constexpr int kPP = PS::kPitch;
-    const int lane = (int)(threadIdx.x & 31u), B = a.B, n = a.n, H = a.H, W = a.W;
-    const int nbu = a.U / B, nbt = nbu * nbu;  // blocks per unit side, per unit
-    const int bpp = 32 / B;                    // blocks per pass
+    const int lane = (int)(threadIdx.x & 31u), B = a.B, H = a.H, W = a.W;
+    const int lgB = __ffs(B) - 1, lgN = __ffs(a.U) - 1 - lgB;  // B and U are powers of two
+    const int nbu = 1 << lgN, nbt = nbu * nbu;                 // blocks per unit side, per unit
+    const int bpp = 32 >> lgB;                                 // blocks per pass
     const int code = xi_code(a.eps_int);
-    const int r = lane % B, bl = lane / B;
+    const int r = lane & (B - 1), bl = lane >> lgB;
     const int nslots = 2 * B * B;  // room per block; a block's sampled sites fill the first ones
+    const FastDiv n(a.n);
     const int2* pp = ps.pp + (Rw + 1) * kPP + (Rw + 1);  // (0,0) = vertex (r0, c0) of slice t-1
     // sampled sites of the block at (ib, jb): rows and columns from the
-    // first multiple of n, every n-th; slot of a site in row r, column jj
+    // first multiple of n, every n-th
     auto sampled = [&](int ib, int jb, int& fr, int& fc, int& nrs, int& ncs) {
         const int ih = min(B, H - ib), iw = min(B, W - jb);
-        fr = (n - ib % n) % n;
-        fc = (n - jb % n) % n;
-        nrs = ih > fr ? (ih - fr + n - 1) / n : 0;
-        ncs = iw > fc ? (iw - fc + n - 1) / n : 0;
+        fr = (int)n.mod(n.d - n.mod(ib));
+        fc = (int)n.mod(n.d - n.mod(jb));
+        nrs = ih > fr ? (int)n.div(ih - fr + n.d - 1) : 0;
+        ncs = iw > fc ? (int)n.div(iw - fc + n.d - 1) : 0;
     };
     for (int b0 = 0; b0 < nbt; b0 += bpp) {
         const int bi = b0 + bl;
-        const int ib = r0 + (bi / nbu) * B, jb = c0 + (bi % nbu) * B;
+        const int ib = r0 + ((bi >> lgN) << lgB), jb = c0 + ((bi & (nbu - 1)) << lgB);
         const int i = ib + r, li = i - r0;
         const bool live = bi < nbt && i < H && jb < W;
         int fr = 0, fc = 0, nrs = 0, ncs = 0;
         if (live) sampled(ib, jb, fr, fc, nrs, ncs);
-        auto slot = [&](int jj) { return bl * nslots + 2 * (((r - fr) / n) * ncs + (jj - fc) / n); };
+        // this lane's row is sampled when r = fr (mod n); its slots start at
+        // row_slot, and column jj = fc + n m takes slot row_slot + 2 m
+        const bool row_s = live && r >= fr && n.mod(r - fr) == 0;
+        const int row_slot = bl * nslots + (row_s ? 2 * (int)n.div(r - fr) * ncs : 0);
         __syncwarp();
-        if (live && (i % n) == 0) {
-            for (int jj = 0; jj < B; ++jj) {
-                const int j = jb + jj;
-                if (j < W && (j % n) == 0) {
-                    const int2 qv = ps.qc[li + 1][j - c0 + 1];
-                    const int2 p = ps.psl[li][j - c0];
-                    int d;
-                    uint16_t* dst = &ps.smp[1][slot(jj)];
-                    dst[0] = (uint16_t)quantize_code(qv.x, p.x, code, d);
-                    dst[1] = (uint16_t)quantize_code(qv.y, p.y, code, d);
-                }
+        if (row_s) {
+            int m = 0;
+            for (int jj = fc; jj < B && jb + jj < W; jj += n.d, ++m) {
+                const int lj = jb + jj - c0;
+                const int2 qv = ps.qc[li + 1][lj + 1];
+                const int2 p = ps.psl[li][lj];
+                int d;
+                uint16_t* dst = &ps.smp[1][row_slot + 2 * m];
+                dst[0] = (uint16_t)quantize_code(qv.x, p.x, code, d);
+                dst[1] = (uint16_t)quantize_code(qv.y, p.y, code, d);
             }
         }
+        // 3DL micro-encoding: anti-diagonal sweep, lane r at column k - r;
+        // jn = the next sampled column of this row, m its slot
+        int jn = fc, m = 0;
         int2 res = make_int2(0, 0), up = res, left = res;
         for (int k = 0; k < 2 * B - 1; ++k) {
             const int jj = k - r;
@@ -537,10 +544,12 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
                 int2 rec;
                 const unsigned su = quantize_code(qv.x, pu, code, rec.x);
                 const unsigned sv = quantize_code(qv.y, pv, code, rec.y);
-                if ((i % n) == 0 && (j % n) == 0) {
-                    uint16_t* dst = &ps.smp[0][slot(jj)];
+                if (row_s && jj == jn) {
+                    uint16_t* dst = &ps.smp[0][row_slot + 2 * m];
                     dst[0] = (uint16_t)su;
                     dst[1] = (uint16_t)sv;
+                    jn += n.d;
+                    ++m;
                 }
                 up = u;
                 res = rec;
@@ -554,7 +563,7 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
         const int nbp = min(bpp, nbt - b0);
         for (int b = 0; b < nbp; ++b) {
             const int bb = b0 + b;
-            const int ibb = r0 + (bb / nbu) * B, jbb = c0 + (bb % nbu) * B;
+            const int ibb = r0 + ((bb >> lgN) << lgB), jbb = c0 + ((bb & (nbu - 1)) << lgB);
             if (ibb >= H || jbb >= W) continue;
             int frb, fcb, nrb, ncb;
             sampled(ibb, jbb, frb, fcb, nrb, ncb);
@@ -562,10 +571,10 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
             const long long r3 = warp_block_score(&ps.smp[0][b * nslots], used, B, ps.hist, a.log2tab);
             const long long rs = warp_block_score(&ps.smp[1][b * nslots], used, B, ps.hist, a.log2tab);
             if (lane == 0) {
-                const unsigned char m = (1000 * rs < 997 * r3) ? 1 : 0;
-                a.modes[((size_t)t * a.nby + ibb / B) * a.nbx + jbb / B] = m;
-                ps.modes[bb] = m;
-                if (m) atomicAdd(a.counters + 2, 1ull);
+                const unsigned char md = (1000 * rs < 997 * r3) ? 1 : 0;
+                a.modes[((size_t)t * a.nby + (ibb >> lgB)) * a.nbx + (jbb >> lgB)] = md;
+                ps.modes[bb] = md;
+                if (md) atomicAdd(a.counters + 2, 1ull);
             }
         }
         __syncwarp();
@@ -582,9 +591,10 @@ __device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
 
 // Decoding: the modes of the unit's blocks from the stream's mode bits.
 __device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, unsigned char* modes) {
-    const int nbu = a.U / a.B;
+    const int lgB = __ffs(a.B) - 1, lgN = __ffs(a.U) - 1 - lgB;  // B and U are powers of two
+    const int nbu = 1 << lgN;
     for (int bb = (int)(threadIdx.x & 31u); bb < nbu * nbu; bb += 32) {
-        const int ib = r0 / a.B + bb / nbu, jb = c0 / a.B + bb % nbu;
+        const int ib = (r0 >> lgB) + (bb >> lgN), jb = (c0 >> lgB) + (bb & (nbu - 1));
         unsigned char m = 0;
         if (ib < a.nby && jb < a.nbx) {
             const size_t x = ((size_t)t * a.nby + ib) * a.nbx + jb;
@@ -604,6 +614,11 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
     const unsigned FULL = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31u), H = a.H, W = a.W, U = a.U;
     const int uh = min(U, H - r0), uw = min(U, W - c0);
+    // unit and block sides are powers of two: the unit's sites as k = li U + lj
+    const int lgU = __ffs(U) - 1;
+    const int lgB = __ffs(a.B) - 1, lgN = lgU - lgB;  // (MoP) block of site (li, lj): (li >> lgB) << lgN | lj >> lgB
+    auto block_of = [&](int li, int lj) { return ((li >> lgB) << lgN) + (lj >> lgB); };
+    const FastDiv ns((unsigned)a.n);  // (MoP) sampling stride
     auto& ps = sm.prep;
     constexpr int kPP = std::remove_reference<decltype(ps)>::type::kPitch;
     const size_t sl = (size_t)H * W;
@@ -643,8 +658,11 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
     asm volatile("cp.async.commit_group;" ::: "memory");
     cp_async_wait_all();
     __syncwarp();
-    for (int k = lane; k < span * span; k += 32) {
-        const int rr = k / span, cc = k - rr * span;
+    // (row rr, column cc) of word k = lane + 32 m, advanced without a division
+    int rr = 0, cc = lane;
+    while (cc >= span) { cc -= span; ++rr; }
+    for (int k = lane; k < span * span; k += 32, cc += 32) {
+        while (cc >= span) { cc -= span; ++rr; }
         const int i = r0 - 1 - Rw + rr, j = c0 - 1 - Rw + cc;
         if (i < 0 || i >= H || j < 0 || j >= W) continue;  // zero-filled
         int2& e = ps.pp[rr * kPP + cc];
@@ -681,10 +699,10 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
                 }
             if (a.pred == 4 && dec) {
                 unit_modes_from_bits(a, t, r0, c0, ps.modes);
-                const int nbu = U / a.B;
-                for (int k = lane; k < uh * uw; k += 32) {
-                    const int li = k / uw, lj = k % uw;
-                    if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+                for (int k = lane; k < U * U; k += 32) {
+                    const int li = k >> lgU, lj = k & (U - 1);
+                    if (li < uh && lj < uw && !ps.modes[block_of(li, lj)])
+                        Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
                 }
             } else if (a.pred == 4) {
                 // the learned mixture: block modes as MoP's with the net in SL's
@@ -701,43 +719,53 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
                     }
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                for (int k = lane; k < uh * uw; k += 32) {
-                    const int li = k / uw, lj = k % uw;
-                    if (((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0)
+                for (int k = lane; k < U * U; k += 32) {
+                    const int li = k >> lgU, lj = k & (U - 1);
+                    if (li < uh && lj < uw && ns.mod(r0 + li) == 0 && ns.mod(c0 + lj) == 0)
                         ps.psl[li][lj] = __ldcg(Psl + (size_t)(r0 + li) * W + c0 + lj);
                 }
                 cp_async_wait_all();
                 __syncwarp();
                 mop_unit(a, t, r0, c0, ps, Rw);
-                const int nbu = U / a.B;
-                for (int k = lane; k < uh * uw; k += 32) {
-                    const int li = k / uw, lj = k % uw;
-                    if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+                for (int k = lane; k < U * U; k += 32) {
+                    const int li = k >> lgU, lj = k & (U - 1);
+                    if (li < uh && lj < uw && !ps.modes[block_of(li, lj)])
+                        Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
                 }
             }
-            warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
+            warp_publish_add(a.prep_done + ((size_t)t * a.nur + (r0 >> lgU)) * a.nuc + (c0 >> lgU), 1u);
             return;
         }
     }
     unsigned sub = 0, steps = 0;
     // semi-Lagrangian predictions, lanes over a compact list of sites: every
     // vertex (pure SL) or the sampled sites (MoP encoding, for the decisions)
-    if (!(mop && dec)) {
-        const int st = mop ? a.n : 1;
-        const int fr = (st - r0 % st) % st, fc = (st - c0 % st) % st;
-        const int nr = uh > fr ? (uh - fr + st - 1) / st : 0;
-        const int nc = uw > fc ? (uw - fc + st - 1) / st : 0;
+    auto predict_site = [&](int li, int lj) {
+        const int i = r0 + li, j = c0 + lj;
+        int pu, pv;
+        const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
+                              : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
+        const int2 p = make_int2(pu, pv);
+        if (mop) ps.psl[li][lj] = p;
+        Psl[(size_t)i * W + j] = p;
+        sub += md > 0;
+        steps += md;
+    };
+    if (!mop) {
+        for (int k = lane; k < U * U; k += 32) {
+            const int li = k >> lgU, lj = k & (U - 1);
+            if (li < uh && lj < uw) predict_site(li, lj);
+        }
+    } else if (!dec) {
+        // sampled sites: rows fr, fr + n, ..., columns fc, fc + n, ...
+        const unsigned n = ns.d;
+        const int fr = (int)ns.mod(n - ns.mod(r0)), fc = (int)ns.mod(n - ns.mod(c0));
+        const int nr = uh > fr ? (int)ns.div(uh - fr + n - 1) : 0;
+        const int nc = uw > fc ? (int)ns.div(uw - fc + n - 1) : 0;
+        const FastDiv ncd((unsigned)max(nc, 1));
         for (int k = lane; k < nr * nc; k += 32) {
-            const int li = fr + (k / nc) * st, lj = fc + (k % nc) * st;
-            const int i = r0 + li, j = c0 + lj;
-            int pu, pv;
-            const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
-                                  : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-            const int2 p = make_int2(pu, pv);
-            if (mop) ps.psl[li][lj] = p;
-            Psl[(size_t)i * W + j] = p;
-            sub += md > 0;
-            steps += md;
+            const int q = (int)ncd.div(k);
+            predict_site(fr + q * (int)n, fc + (k - q * nc) * (int)n);
         }
     }
     __syncwarp();
@@ -746,23 +774,21 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
         else mop_unit(a, t, r0, c0, ps, Rw);
         // the other vertices of the blocks that chose SL (decoding: all of
         // them), gathered into a list
-        const int nbu = U / a.B;
         int cnt = 0;
-        for (int base = 0; base < uh * uw; base += 32) {
+        for (int base = 0; base < U * U; base += 32) {
             const int k = base + lane;
-            const int li = k / uw, lj = k % uw;
-            const bool sampled = !dec && ((r0 + li) % a.n) == 0 && ((c0 + lj) % a.n) == 0;
-            const bool need = k < uh * uw && !sampled && ps.modes[(li / a.B) * nbu + lj / a.B] != 0;
+            const int li = k >> lgU, lj = k & (U - 1);
+            const bool in = li < uh && lj < uw;
+            const bool mode_sl = in && ps.modes[block_of(li, lj)] != 0;
+            const bool sampled = !dec && ns.mod(r0 + li) == 0 && ns.mod(c0 + lj) == 0;
+            const bool need = mode_sl && !sampled;
             const unsigned bal = __ballot_sync(FULL, need);
             if (need) ps.list[cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(li * 32 + lj);
             cnt += __popc(bal);
+            // vertices of the blocks that kept 3DL: the marker instead of a prediction
+            if (in && !mode_sl) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
         }
         __syncwarp();
-        // vertices of the blocks that kept 3DL: the marker instead of a prediction
-        for (int k = lane; k < uh * uw; k += 32) {
-            const int li = k / uw, lj = k % uw;
-            if (!ps.modes[(li / a.B) * nbu + lj / a.B]) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
-        }
         for (int m = lane; m < cnt; m += 32) {
             const unsigned v = ps.list[m];
             const int i = r0 + (int)(v >> 5), j = c0 + (int)(v & 31u);
@@ -785,7 +811,7 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
     }
     const int nstrips = (H + 31) / 32;
     (void)nstrips;
-    warp_publish_add(a.prep_done + ((size_t)t * a.nur + r0 / U) * a.nuc + c0 / U, 1u);
+    warp_publish_add(a.prep_done + ((size_t)t * a.nur + (r0 >> lgU)) * a.nuc + (c0 >> lgU), 1u);
 }
 
 // Units of slice t (t >= 1) that became ready while wave(t-1, s) went from
@@ -1097,14 +1123,27 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
                 CPT_D(0) CPT_D(1) CPT_D(2) CPT_D(3) CPT_D(4) CPT_D(5) CPT_D(6)
                 CPT_D(7) CPT_D(8) CPT_D(9) CPT_D(10) CPT_D(11) CPT_D(12)
 #undef CPT_D
+                // The low 32 bits of the two products agree whenever M = 0:
+                // that filter runs on 32-bit multiplies, and the rare faces
+                // that pass it are confirmed with the exact 64-bit products.
                 unsigned hits = 0;
                 int bit = 0;
-#define CPT_PM(fa, fb)                                                       \
-    hits |= ((long long)dx##fa * dy##fb == (long long)dy##fa * dx##fb ? 1u : 0u) << bit; \
+#define CPT_PM(fa, fb)                                                                            \
+    hits |= ((unsigned)dx##fa * (unsigned)dy##fb == (unsigned)dy##fa * (unsigned)dx##fb ? 1u : 0u) << bit; \
     ++bit;
                 CPT_UNC_FACES(CPT_PM)
 #undef CPT_PM
-                if (hits & mm) xi = 0;
+                hits &= mm;
+                if (hits) {
+                    unsigned exact = 0;
+                    bit = 0;
+#define CPT_PM64(fa, fb)                                                                  \
+    exact |= ((long long)dx##fa * dy##fb == (long long)dy##fa * dx##fb ? 1u : 0u) << bit; \
+    ++bit;
+                    CPT_UNC_FACES(CPT_PM64)
+#undef CPT_PM64
+                    if (exact & hits) xi = 0;
+                }
                 if (xi > 0 && mf) {
                     int2* nb = sm.nbs[lane];
                     nb[0] = n0; nb[1] = n1; nb[2] = n2; nb[3] = n3;
