@@ -824,14 +824,15 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
 __device__ void enqueue_units(const SliceArgs& a, int t, int s, int k0, int k1) {
     const int U = a.U, R = a.R, W = a.W, H = a.H, lane = (int)(threadIdx.x & 31u);
     const int nstrips = (H + 31) / 32;
+    const int lgU = __ffs(U) - 1;  // unit sides are powers of two
     auto ready_cols = [&](int x) -> int {  // unit columns whose column need is <= x
         if (x >= W - 1) return a.nuc;
         const int v = x - U + 1 - R;
-        return v < 0 ? 0 : min(a.nuc, v / U + 1);
+        return v < 0 ? 0 : min(a.nuc, (v >> lgU) + 1);
     };
     auto first_row = [&](int sx) -> int {  // first unit row whose row need is in strip sx or below
         const int num = 32 * sx - U + 1 - R;
-        return num <= 0 ? 0 : min(a.nur, (num + U - 1) / U);
+        return num <= 0 ? 0 : min(a.nur, (num + U - 1) >> lgU);
     };
     const int ur0 = first_row(s), ur1 = s + 1 < nstrips ? first_row(s + 1) : a.nur;
     auto need_lane = [&](int ur) { return min(H - 1, ur * U + U - 1 + R) - 32 * s; };
@@ -996,12 +997,13 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     };
     // the SL predictions of unit (ur, uc) before the first load that reads
     // them: the unit's first row (lane lu) reaches column uc*U at step uc*U + lu
+    const int lgU = __ffs(a.U) - 1;  // unit sides are powers of two
     auto await_sl = [&](int kk) -> bool {
         if (!need_sl) return true;
         for (int lu = 0; lu < 32 && i0 + lu < H; lu += a.U) {
             const int c = kk - lu;
-            if (c < 0 || c % a.U != 0 || c >= W) continue;
-            const unsigned* f = a.prep_done + ((size_t)t * a.nur + (i0 + lu) / a.U) * a.nuc + c / a.U;
+            if (c < 0 || (c & (a.U - 1)) != 0 || c >= W) continue;
+            const unsigned* f = a.prep_done + ((size_t)t * a.nur + ((i0 + lu) >> lgU)) * a.nuc + (c >> lgU);
             if (!warp_wait_geq(a, f, 1u)) return false;
         }
         return true;
