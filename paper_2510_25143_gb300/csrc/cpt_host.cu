@@ -509,7 +509,7 @@ struct FieldJob {
     int32_t *d_q = nullptr, *d_qhat = nullptr;
     uint16_t* d_mask = nullptr;
     unsigned long long* d_cnt64 = nullptr;  // [0] crossed faces, [1..4] encoder counters
-    uint8_t *d_qxi = nullptr, *d_modes = nullptr;
+    uint8_t *d_qxi = nullptr, *d_modes = nullptr, *d_mbits = nullptr;
     uint32_t* d_sym = nullptr;
     int* d_xiout = nullptr;
     int2 *d_psl = nullptr, *d_cls = nullptr, *d_qdiag = nullptr;
@@ -776,6 +776,10 @@ struct FieldJob {
         sd.alphabet = 2 * kRadius;
         nblk = has_modes ? (size_t)T * nby * nbx : 0;
         mode_bytes = (nblk + 7) / 8;
+        if (nblk) {  // the stream's mode bits, packed on the device
+            CPT_CUDA(ar.alloc(&d_mbits, mode_bytes));
+            launch_pack_bits(d_modes, nblk, d_mbits, s);
+        }
         CPT_CUDA(ar.alloc(&d_hist, sx.alphabet + sd.alphabet));
         CPT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * (sx.alphabet + sd.alphabet), s));
         launch_hist_u8(d_qxi, N, d_hist, s);
@@ -784,7 +788,7 @@ struct FieldJob {
         sd.nt = (sd.nsym + kTileSyms - 1) / kTileSyms;
         // staging: histograms | block modes | tables | tile offsets
         st_hist = sizeof(unsigned) * (sx.alphabet + sd.alphabet);
-        st_modes = (nblk + 15) & ~(size_t)15;
+        st_modes = (mode_bytes + 15) & ~(size_t)15;
         st_tab = sizeof(uint32_t) * (sx.alphabet + sd.alphabet);
         st_toff = sizeof(unsigned long long) * (sx.nt + 1 + sd.nt + 1);
         return CPT_OK;
@@ -793,7 +797,7 @@ struct FieldJob {
         unsigned* hist_h = reinterpret_cast<unsigned*>(stage_h);
         uint8_t* modes_h = stage_h + st_hist;
         CPT_CUDA(cudaMemcpyAsync(hist_h, d_hist, st_hist, cudaMemcpyDeviceToHost, s));
-        if (nblk) CPT_CUDA(cudaMemcpyAsync(modes_h, d_modes, nblk, cudaMemcpyDeviceToHost, s));
+        if (nblk) CPT_CUDA(cudaMemcpyAsync(modes_h, d_mbits, mode_bytes, cudaMemcpyDeviceToHost, s));
         return CPT_OK;
     }
 
@@ -833,16 +837,10 @@ struct FieldJob {
     // ---- phase 5 (after the tile offsets arrived): layout, header, words,
     // verification, debug copies
     cpt_status write_stream() {
-        const uint8_t* modes_h = stage_h + st_hist;
+        const uint8_t* mbits_h = stage_h + st_hist;  // block modes as bits (packed on the device)
         const unsigned long long* toff_h =
             reinterpret_cast<const unsigned long long*>(stage_h + st_hist + st_modes + st_tab);
-        // block modes as bits
-        std::vector<uint8_t> packed(mode_bytes, 0);
-        for (size_t x = 0; x < nblk; ++x)
-            if (modes_h[x]) {
-                packed[x >> 3] |= (uint8_t)(1u << (x & 7));
-                ++st.sl_blocks;
-            }
+        for (size_t b = 0; b < mode_bytes; ++b) st.sl_blocks += (uint64_t)__builtin_popcount(mbits_h[b]);
         {
             const unsigned long long* to = toff_h;
             for (StreamPlan* sp : {&sx, &sd}) {
@@ -886,7 +884,7 @@ struct FieldJob {
         w.u64(n_ld);
         w.u64(mode_bytes);
         if (w.n != kHeaderBytes) return fail(CPT_ERR_ARG, "internal: header size");
-        if (mode_bytes) w.raw(packed.data(), mode_bytes);
+        if (mode_bytes) w.raw(mbits_h, mode_bytes);
         if (model_bytes) {  // the model: parameter count, then the bfloat16 parameters two per word
             w.u32((uint32_t)kNetParams);
             for (int x = 0; x < kNetParams; x += 2)

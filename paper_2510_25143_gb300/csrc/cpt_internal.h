@@ -157,6 +157,7 @@ void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long
 size_t compact_tiles(size_t N);
 void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* tile_cnt,
                        cudaStream_t s);
+void launch_pack_bits(const uint8_t* in, size_t n, uint8_t* out, cudaStream_t s);
 void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q,
                          const unsigned long long* tile_off, size_t N, uint16_t* qd_out, int32_t* ld_out,
                          cudaStream_t s);

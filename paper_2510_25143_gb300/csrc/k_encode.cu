@@ -197,11 +197,25 @@ __global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict
                         dx[k] = nb[k].x - qv.x;
                         dy[k] = nb[k].y - qv.y;
                     }
+                    // M = 0 on a certain face: filtered on the low 32 bits of
+                    // the two products, confirmed with the exact 64-bit ones
+                    unsigned cand = 0;
+                    int cbit = 0;
+#define CPT_CERT_LO(a, b)                                                                                  \
+    cand |= (((valid >> (a)) & (valid >> (b)) & 1u) &&                                                    \
+             (unsigned)dx[a] * (unsigned)dy[b] == (unsigned)dy[a] * (unsigned)dx[b] ? 1u : 0u) << cbit;   \
+    ++cbit;
+                    CPT_CERT_FACES(CPT_CERT_LO)
+#undef CPT_CERT_LO
                     bool mz = false;
+                    if (cand) {
+                        cbit = 0;
 #define CPT_CERT_M(a, b) \
-    mz |= ((valid >> (a)) & (valid >> (b)) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b];
-                    CPT_CERT_FACES(CPT_CERT_M)
+    mz |= ((cand >> cbit) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b]; \
+    ++cbit;
+                        CPT_CERT_FACES(CPT_CERT_M)
 #undef CPT_CERT_M
+                    }
                     if (mz) {
                         xi = 0;
                     } else {

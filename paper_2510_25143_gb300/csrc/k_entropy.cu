@@ -154,12 +154,21 @@ __global__ void __launch_bounds__(kCmpThreads) tile_count_kernel(const uint8_t* 
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
 }
 
+// The tile's outputs are contiguous in both arrays: they are gathered in
+// shared memory at their offsets within the tile, then copied out by the whole
+// block with consecutive addresses (a thread's own 16 vertices would scatter
+// narrow stores across the warp).
+constexpr size_t kScatterSmem = (size_t)kCmpTile * 2 * sizeof(uint16_t) + (size_t)kCmpTile * 2 * sizeof(int32_t);
+
 __global__ void __launch_bounds__(kCmpThreads) tile_scatter_kernel(const uint8_t* __restrict__ qxi,
                                                                    const uint32_t* __restrict__ sym,
                                                                    const int2* __restrict__ q,
                                                                    const unsigned long long* __restrict__ tile_off,
                                                                    size_t N, uint16_t* __restrict__ qd,
                                                                    int32_t* __restrict__ ld) {
+    extern __shared__ __align__(16) unsigned char sm_scatter[];
+    uint16_t* sq = reinterpret_cast<uint16_t*>(sm_scatter);                              // 2 per vertex at most
+    int32_t* sld = reinterpret_cast<int32_t*>(sm_scatter + (size_t)kCmpTile * 2 * sizeof(uint16_t));
     __shared__ unsigned long long wt[32], tot;
     const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
     unsigned char c[kCmpPer];
@@ -169,26 +178,32 @@ __global__ void __launch_bounds__(kCmpThreads) tile_scatter_kernel(const uint8_t
 #pragma unroll
     for (int k = 0; k < kCmpPer; ++k)
         if (base + k < N) n += vertex_count(c[k], sy[k]);
-    const unsigned long long o = block_exclusive_scan(n, wt, &tot) + tile_off[blockIdx.x];
-    size_t pq = (size_t)(o >> 32), pl = (size_t)(o & 0xFFFFFFFFull);
+    const unsigned long long o = block_exclusive_scan(n, wt, &tot);  // offsets within the tile
+    unsigned pq = (unsigned)(o >> 32), pl = (unsigned)(o & 0xFFFFFFFFull);
 #pragma unroll
     for (int k = 0; k < kCmpPer; ++k) {
         const size_t v = base + k;
         if (v >= N) break;
         if (c[k]) {
             const uint16_t su = (uint16_t)(sy[k] & 0xFFFFu), sv = (uint16_t)(sy[k] >> 16);
-            qd[pq] = su;
-            qd[pq + 1] = sv;
+            sq[pq] = su;
+            sq[pq + 1] = sv;
             pq += 2;
-            if (su == 0) ld[pl++] = __ldg(q + v).x;
-            if (sv == 0) ld[pl++] = __ldg(q + v).y;
+            if (su == 0) sld[pl++] = __ldg(q + v).x;
+            if (sv == 0) sld[pl++] = __ldg(q + v).y;
         } else {
             const int2 x = __ldg(q + v);
-            ld[pl] = x.x;
-            ld[pl + 1] = x.y;
+            sld[pl] = x.x;
+            sld[pl + 1] = x.y;
             pl += 2;
         }
     }
+    __syncthreads();
+    const unsigned long long g = tile_off[blockIdx.x];
+    const size_t gq = (size_t)(g >> 32), gl = (size_t)(g & 0xFFFFFFFFull);
+    const unsigned nq = (unsigned)(tot >> 32), nl = (unsigned)(tot & 0xFFFFFFFFull);
+    for (unsigned k = threadIdx.x; k < nq; k += kCmpThreads) qd[gq + k] = sq[k];
+    for (unsigned k = threadIdx.x; k < nl; k += kCmpThreads) ld[gl + k] = sld[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -282,6 +297,21 @@ void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsign
     count_pack_kernel<<<1216, 256, 0, s>>>(qxi, sym, N, cnt);
 }
 
+// Block modes (one byte each, nonzero = SL) as bits, least significant bit
+// first: byte b of the output holds modes 8b .. 8b + 7.
+__global__ void __launch_bounds__(256) pack_bits_kernel(const uint8_t* __restrict__ in, size_t n,
+                                                        uint8_t* __restrict__ out) {
+    const size_t nb = (n + 7) / 8;
+    for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < nb; b += (size_t)gridDim.x * blockDim.x) {
+        unsigned v = 0;
+        for (int k = 0; k < 8; ++k) {
+            const size_t x = 8 * b + k;
+            if (x < n && in[x]) v |= 1u << k;
+        }
+        out[b] = (uint8_t)v;
+    }
+}
+
 size_t compact_tiles(size_t N) { return (N + kCmpTile - 1) / kCmpTile; }
 
 void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* tile_cnt,
@@ -292,9 +322,19 @@ void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsign
 void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q,
                          const unsigned long long* tile_off, size_t N, uint16_t* qd_out, int32_t* ld_out,
                          cudaStream_t s) {
-    if (N)
-        tile_scatter_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(
-            qxi, sym, reinterpret_cast<const int2*>(q), tile_off, N, qd_out, ld_out);
+    if (!N) return;
+    // the gather buffer is above the default 48 KB of shared memory (set once;
+    // if that failed, so does the launch, and the caller reads the error)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        tile_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    (void)attr;
+    tile_scatter_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, kScatterSmem, s>>>(
+        qxi, sym, reinterpret_cast<const int2*>(q), tile_off, N, qd_out, ld_out);
+}
+
+void launch_pack_bits(const uint8_t* in, size_t n, uint8_t* out, cudaStream_t s) {
+    const size_t nb = (n + 7) / 8;
+    if (nb) pack_bits_kernel<<<(unsigned)std::min<size_t>((nb + 255) / 256, 4096), 256, 0, s>>>(in, n, out);
 }
 
 void launch_hist_u8(const uint8_t* x, size_t n, unsigned* hist, cudaStream_t s) {
