@@ -58,6 +58,7 @@ __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, 
 }
 
 __host__ __device__ constexpr bool is_uncertain(int n) { return n <= 6; }
+constexpr unsigned kAllNeighbours = 0x3FFFu;  // nb_valid of an interior vertex
 
 // The CPT_UNC_FACES pairs as bytes (first | second << 4), face f in byte f % 8
 // of word f / 8, for loops over a face mask.
@@ -143,95 +144,103 @@ __global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict
         bool slow = false;
         if (i < H && j < W) {
             const size_t v = ((size_t)t * H + i) * W + j;
-            // a crossed incident face: one of the eight owners' masks (the
-            // owners lie at offsets (0..-1, 0..-1, 0..-1) from the vertex)
-            bool crossed = false;
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const bool ok = (kOwners[o].dt == 0 || t > 0) && (kOwners[o].di == 0 || i > 0) &&
-                                (kOwners[o].dj == 0 || j > 0);
-                const long long off = (long long)kOwners[o].dt * (long long)sl + (long long)kOwners[o].di * W +
-                                      kOwners[o].dj;
-                if (ok) crossed |= (__ldg(mask + (long long)v + off) & kOwners[o].types) != 0;
-            }
             int xi = 0;
             unsigned um_m = 0;
-            if (!crossed && eps_int > 0) {
-                xi = eps_int;
-                const unsigned valid = nb_valid(H, W, T, t, i, j);
-                const int2 qv = __ldg(q + v);
-                int2 nb[14];
-                load_nb(q, v, sl, W, valid, nb, qv);
-                const int E = 1 << (31 - __clz(eps_int));
-                // Fast path (exact): every existing neighbour keeps the vertex's
-                // strict sign of u (or of v), with margin E where its value may
-                // still change, and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on
-                // every face unless M = 0 (M = det(n_a - q, n_b - q)), and no
-                // uncertain face needs the full Alg. 2.  The sign tests are
-                // minima and maxima over the uncertain neighbours (0..6) and
-                // the others.
-                bool fast = false;
+            // the vertex's work, with a copy for interior vertices (every
+            // neighbour present: the presence tests fold away)
+            auto classify_vertex = [&](const unsigned valid) {
+                // a crossed incident face: one of the eight owners' masks (the
+                // owners lie at offsets (0..-1, 0..-1, 0..-1) from the vertex)
+                bool crossed = false;
 #pragma unroll
-                for (int c = 0; c < 2 && !fast; ++c) {
-                    const int x0 = c ? qv.y : qv.x;
-                    if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
-                    int lo_u = INT_MAX, hi_u = INT_MIN, lo_c = INT_MAX, hi_c = INT_MIN;
+                for (int o = 0; o < 8; ++o) {
+                    // owner present: t > 0, i > 0, j > 0 are bits 3, 5, 6 of valid
+                    const bool ok = (kOwners[o].dt == 0 || ((valid >> 3) & 1u)) &&
+                                    (kOwners[o].di == 0 || ((valid >> 5) & 1u)) &&
+                                    (kOwners[o].dj == 0 || ((valid >> 6) & 1u));
+                    const long long off = (long long)kOwners[o].dt * (long long)sl + (long long)kOwners[o].di * W +
+                                          kOwners[o].dj;
+                    if (ok) crossed |= (__ldg(mask + (long long)v + off) & kOwners[o].types) != 0;
+                }
+                if (!crossed && eps_int > 0) {
+                    xi = eps_int;
+                    const int2 qv = __ldg(q + v);
+                    int2 nb[14];
+                    load_nb(q, v, sl, W, valid, nb, qv);
+                    const int E = 1 << (31 - __clz(eps_int));
+                    // Fast path (exact): every existing neighbour keeps the vertex's
+                    // strict sign of u (or of v), with margin E where its value may
+                    // still change, and |q| - 1 >= eps'.  Then Alg. 2 keeps eps' on
+                    // every face unless M = 0 (M = det(n_a - q, n_b - q)), and no
+                    // uncertain face needs the full Alg. 2.  The sign tests are
+                    // minima and maxima over the uncertain neighbours (0..6) and
+                    // the others.
+                    bool fast = false;
 #pragma unroll
-                    for (int k = 0; k < 14; ++k) {
-                        const int x = c ? nb[k].y : nb[k].x;
-                        if (is_uncertain(k)) {
-                            lo_u = min(lo_u, x);
-                            hi_u = max(hi_u, x);
-                        } else {
-                            lo_c = min(lo_c, x);
-                            hi_c = max(hi_c, x);
+                    for (int c = 0; c < 2 && !fast; ++c) {
+                        const int x0 = c ? qv.y : qv.x;
+                        if (x0 == 0 || abs(x0) - 1 < eps_int) continue;
+                        int lo_u = INT_MAX, hi_u = INT_MIN, lo_c = INT_MAX, hi_c = INT_MIN;
+#pragma unroll
+                        for (int k = 0; k < 14; ++k) {
+                            const int x = c ? nb[k].y : nb[k].x;
+                            if (is_uncertain(k)) {
+                                lo_u = min(lo_u, x);
+                                hi_u = max(hi_u, x);
+                            } else {
+                                lo_c = min(lo_c, x);
+                                hi_c = max(hi_c, x);
+                            }
                         }
+                        fast = x0 > 0 ? (lo_c > 0 && lo_u > E) : (hi_c < 0 && hi_u < -E);
                     }
-                    fast = x0 > 0 ? (lo_c > 0 && lo_u > E) : (hi_c < 0 && hi_u < -E);
-                }
-                if (fast) {
-                    // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
-                    int dx[14], dy[14];
+                    if (fast) {
+                        // |differences| < 2^26: 32-bit, products widened (one 32 x 32 -> 64 multiply each)
+                        int dx[14], dy[14];
 #pragma unroll
-                    for (int k = 0; k < 14; ++k) {
-                        dx[k] = nb[k].x - qv.x;
-                        dy[k] = nb[k].y - qv.y;
-                    }
-                    // M = 0 on a certain face: filtered on the low 32 bits of
-                    // the two products, confirmed with the exact 64-bit ones
-                    unsigned cand = 0;
-                    int cbit = 0;
+                        for (int k = 0; k < 14; ++k) {
+                            dx[k] = nb[k].x - qv.x;
+                            dy[k] = nb[k].y - qv.y;
+                        }
+                        // M = 0 on a certain face: filtered on the low 32 bits of
+                        // the two products, confirmed with the exact 64-bit ones
+                        unsigned cand = 0;
+                        int cbit = 0;
 #define CPT_CERT_LO(a, b)                                                                                  \
-    cand |= (((valid >> (a)) & (valid >> (b)) & 1u) &&                                                    \
-             (unsigned)dx[a] * (unsigned)dy[b] == (unsigned)dy[a] * (unsigned)dx[b] ? 1u : 0u) << cbit;   \
-    ++cbit;
-                    CPT_CERT_FACES(CPT_CERT_LO)
+        cand |= (((valid >> (a)) & (valid >> (b)) & 1u) &&                                                    \
+                 (unsigned)dx[a] * (unsigned)dy[b] == (unsigned)dy[a] * (unsigned)dx[b] ? 1u : 0u) << cbit;   \
+        ++cbit;
+                        CPT_CERT_FACES(CPT_CERT_LO)
 #undef CPT_CERT_LO
-                    bool mz = false;
-                    if (cand) {
-                        cbit = 0;
+                        bool mz = false;
+                        if (cand) {
+                            cbit = 0;
 #define CPT_CERT_M(a, b) \
-    mz |= ((cand >> cbit) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b]; \
-    ++cbit;
-                        CPT_CERT_FACES(CPT_CERT_M)
+        mz |= ((cand >> cbit) & 1u) && (long long)dx[a] * dy[b] == (long long)dy[a] * dx[b]; \
+        ++cbit;
+                            CPT_CERT_FACES(CPT_CERT_M)
 #undef CPT_CERT_M
-                    }
-                    if (mz) {
-                        xi = 0;
-                    } else {
-                        // every existing uncertain face keeps the same-sign
-                        // clause; only its M = 0 check remains, done by the
-                        // wave with the actual reconstructions (a face whose M
-                        // cannot reach 0 passes that check anyway)
-                        int bit = 0;
+                        }
+                        if (mz) {
+                            xi = 0;
+                        } else {
+                            // every existing uncertain face keeps the same-sign
+                            // clause; only its M = 0 check remains, done by the
+                            // wave with the actual reconstructions (a face whose M
+                            // cannot reach 0 passes that check anyway)
+                            int bit = 0;
 #define CPT_UNC_VALID(a, b) um_m |= ((valid >> (a)) & (valid >> (b)) & 1u) << bit; ++bit;
-                        CPT_UNC_FACES(CPT_UNC_VALID)
+                            CPT_UNC_FACES(CPT_UNC_VALID)
 #undef CPT_UNC_VALID
+                        }
+                    } else {
+                        slow = true;
                     }
-                } else {
-                    slow = true;
                 }
-            }
+            };
+            const unsigned valid_nb = nb_valid(H, W, T, t, i, j);
+            if (valid_nb == kAllNeighbours) classify_vertex(kAllNeighbours);
+            else classify_vertex(valid_nb);
             if (!slow) store_cls(out, out_m, qd, q, H, W, t, i, j, v, xi, 0u, um_m);
         }
         // queue the slow vertices of the warp (one shared atomic per warp)
