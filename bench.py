@@ -53,20 +53,22 @@ STAGE_BYTES = {
     "wavefront": (31.0, "field"),
     "verify": (18.0, "field"),          # read qhat 8 B, the mask 2 B and the input 8 B
 }
-KERNEL_NAMES = {"range_fixed": "range_kernel + to_fixed_kernel", "face_masks": "face_mask_kernel",
+KERNEL_NAMES = {"range_fixed": "range_kernel + to_fixed_kernel", "face_masks": "face_kernel<false, .> (face test)",
                 "incident_bounds": "classify_kernel", "wavefront": "encode_pipeline_kernel",
-                "verify": "verify_kernel", "mop_sl": "mop/SL prediction"}
+                "verify": "face_kernel<true, .> (verification)", "mop_sl": "mop/SL prediction"}
 
 # ncu summaries: DRAM bytes of one launch of a kernel, valid while its
 # sources hash as they did when captured.  (stage, predictor) -> file
 PROFILES = {
     ("wavefront", "mop"): "encode_pipeline_turb1024_mop.md",
-    ("face_masks", None): "face_mask_turb1024.md",
+    ("face_masks", None): "face_test_turb1024.md",
+    ("incident_bounds", None): "classify_turb1024.md",
     ("verify", None): "verify_turb1024.md",
 }
 KERNEL_SOURCES = {
     "wavefront": ["k_encode.cu", "cpt_dev.cuh", "cpt_internal.h"],
     "face_masks": ["k_field.cu", "cpt_dev.cuh", "cpt_internal.h"],
+    "incident_bounds": ["k_encode.cu", "cpt_dev.cuh", "cpt_internal.h"],
     "verify": ["k_field.cu", "cpt_dev.cuh", "cpt_internal.h"],
 }
 
