@@ -151,6 +151,17 @@ __device__ __forceinline__ RowVals load_row(const int2* __restrict__ q, size_t r
     return r;
 }
 
+// The tag of reconstruction words removed (verification input), applied when
+// a prefetched row is consumed rather than right after its load.
+template <bool kTag>
+__device__ __forceinline__ RowVals untag(RowVals r) {
+    if (kTag) {
+        r.v0.y ^= kQhatTag;
+        r.v1.y ^= kQhatTag;
+    }
+    return r;
+}
+
 struct RowWords {
     unsigned w0, w1;
 };
@@ -253,21 +264,25 @@ __device__ __forceinline__ void face_item_rows(const int2* __restrict__ q, int H
     const size_t sl = (size_t)H * W, base = (size_t)t * sl;
     const int ie = min(H, ib + kFaceRows);
     int nq = 0;
-    // rows i (A: slice t, P: slice t + 1) and i + 1 (D, Dp)
+    // rows i (A: slice t, P: slice t + 1) and i + 1 (D, Dp); rows i + 2 (N,
+    // Np) are loaded one row step ahead, without their tag removed yet
+    const int re = min(H, ib + kFaceRows + 1);  // rows the item reads: [ib, re)
     RowVals A = load_row<kVec, kVerify>(q, base + (size_t)ib * W, c0, W, true);
     RowVals P = load_row<kVec, kVerify>(q, base + sl + (size_t)ib * W, c0, W, nx);
     RowVals D = load_row<kVec, kVerify>(q, base + (size_t)(ib + 1) * W, c0, W, ib + 1 < H);
     RowVals Dp = load_row<kVec, kVerify>(q, base + sl + (size_t)(ib + 1) * W, c0, W, nx && ib + 1 < H);
+    RowVals N = load_row<kVec, false>(q, base + (size_t)(ib + 2) * W, c0, W, ib + 2 < re);
+    RowVals Np = load_row<kVec, false>(q, base + sl + (size_t)(ib + 2) * W, c0, W, ib + 2 < re && nx);
     RowWords wa = row_words(A, true, in0, in1), wp = row_words(P, nx, in0, in1);
     unsigned col0 = wa.w0 & wp.w0, col1 = wa.w1 & wp.w1;
     unsigned omN = 0;
     float4 oxN = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kVerify) orig_row<kVec>(mask_in, uv, base + (size_t)ib * W, c0, own0, own1, omN, oxN);
     for (int i = ib; i < ie; ++i) {
-        const bool dn = i + 1 < H, nn = i + 2 < min(H, ib + kFaceRows + 1);
-        // prefetch row i + 2
-        RowVals N = load_row<kVec, kVerify>(q, base + (size_t)(i + 2) * W, c0, W, nn);
-        RowVals Np = load_row<kVec, kVerify>(q, base + sl + (size_t)(i + 2) * W, c0, W, nn && nx);
+        const bool dn = i + 1 < H, n3 = i + 3 < re;
+        // prefetch row i + 3
+        const RowVals NN = load_row<kVec, false>(q, base + (size_t)(i + 3) * W, c0, W, n3);
+        const RowVals NNp = load_row<kVec, false>(q, base + sl + (size_t)(i + 3) * W, c0, W, n3 && nx);
         const size_t vrow = base + (size_t)i * W;
         // verification: the original masks and values of row i (loaded one
         // row ahead), and those of row i + 1 for the next iteration
@@ -319,8 +334,10 @@ __device__ __forceinline__ void face_item_rows(const int2* __restrict__ q, int H
         }
         A = D;
         P = Dp;
-        D = N;
-        Dp = Np;
+        D = untag<kVerify>(N);
+        Dp = untag<kVerify>(Np);
+        N = NN;
+        Np = NNp;
         wa = wd;
         wp = wdp;
         col0 = dcol0;
