@@ -59,6 +59,7 @@ __device__ __forceinline__ unsigned nb_valid(int H, int W, int T, int t, int i, 
 
 __host__ __device__ constexpr bool is_uncertain(int n) { return n <= 6; }
 constexpr unsigned kAllNeighbours = 0x3FFFu;  // nb_valid of an interior vertex
+constexpr unsigned kAllUncFaces = (1u << 24) - 1u;  // every uncertain face present
 
 // The CPT_UNC_FACES pairs as bytes (first | second << 4), face f in byte f % 8
 // of word f / 8, for loops over a face mask.
@@ -1151,14 +1152,27 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
                 // The low 32 bits of the two products agree whenever M = 0:
                 // that filter runs on 32-bit multiplies, and the rare faces
                 // that pass it are confirmed with the exact 64-bit products.
+                // When mm holds all 24 faces (interior vertices) the filter
+                // is first folded into one predicate, and the face mask is
+                // built only if some face passes it.
+                bool any = true;
+                if (mm == kAllUncFaces) {
+                    bool z = false;
+#define CPT_PZ(fa, fb) z = z | ((unsigned)dx##fa * (unsigned)dy##fb == (unsigned)dy##fa * (unsigned)dx##fb);
+                    CPT_UNC_FACES(CPT_PZ)
+#undef CPT_PZ
+                    any = z;
+                }
                 unsigned hits = 0;
                 int bit = 0;
+                if (any) {
 #define CPT_PM(fa, fb)                                                                            \
     hits |= ((unsigned)dx##fa * (unsigned)dy##fb == (unsigned)dy##fa * (unsigned)dx##fb ? 1u : 0u) << bit; \
     ++bit;
-                CPT_UNC_FACES(CPT_PM)
+                    CPT_UNC_FACES(CPT_PM)
 #undef CPT_PM
-                hits &= mm;
+                    hits &= mm;
+                }
                 if (hits) {
                     unsigned exact = 0;
                     bit = 0;
