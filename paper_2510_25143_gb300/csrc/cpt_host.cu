@@ -513,7 +513,7 @@ struct FieldJob {
     uint32_t* d_sym = nullptr;
     int* d_xiout = nullptr;
     int2 *d_psl = nullptr, *d_cls = nullptr, *d_qdiag = nullptr;
-    unsigned *d_clsm = nullptr, *d_prep = nullptr;
+    unsigned* d_clsm = nullptr;
     size_t nprep_alloc = 0;
     int nby = 0, nbx = 0, nstrips = 0;
     double qmax = 0;  // bound on |reconstruction| for the semi-Lagrangian reach
@@ -668,12 +668,10 @@ struct FieldJob {
         }
         if (has_net) A.net = *net;
         A.log2tab = d_log2;
-        // prep units (SL and MoP): U x U squares of slices 1..T-1; the
-        // progress flags are sized for the smallest unit a schedule may pick
+        // prep units (SL and MoP): U x U squares of slices 1..T-1; the ready
+        // queue is sized for the smallest unit a schedule may pick
         const int Umin = has_modes ? (B == 32 ? 32 : 16) : 8;
         nprep_alloc = (size_t)T * ((H + Umin - 1) / Umin) * ((W + Umin - 1) / Umin);
-        CPT_CUDA(ar.alloc(&d_prep, nprep_alloc));
-        A.prep_done = d_prep;
         cpt_status rc = set_units(tune);
         if (rc != CPT_OK) return rc;
 
@@ -739,7 +737,7 @@ struct FieldJob {
     // Resets what the encoder pipeline reads and writes back (before every launch).
     cpt_status reset_pipeline() {
         CPT_CUDA(cudaMemsetAsync(d_qhat, 0, NV * sizeof(int32_t), s));  // no reconstruction word present
-        CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep_alloc, s));
+        if (want_sl) CPT_CUDA(cudaMemsetAsync(d_psl, 0, N * sizeof(int2), s));  // no prediction word present
         CPT_CUDA(cudaMemsetAsync(d_cnt64 + 1, 0, 4 * sizeof(unsigned long long), s));
         return CPT_OK;
     }
@@ -1770,7 +1768,7 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
     int32_t *d_q, *d_qhat, *d_ld;
     uint16_t *d_mask, *d_qd, *d_mask_carry;
     int2 *d_cls, *d_qdiag, *d_psl, *d_qhat_carry;
-    unsigned *d_clsm, *d_prep, *d_hist, *d_queue, *d_ticket;
+    unsigned *d_clsm, *d_hist, *d_queue, *d_ticket;
     uint8_t *d_qxi, *d_modes;
     uint32_t* d_sym;
     unsigned long long *d_cnt64, *d_off, *d_stmp;
@@ -1792,7 +1790,6 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
     CPT_CUDA(ar.alloc(&d_qxi, HW * Tw));
     CPT_CUDA(ar.alloc(&d_sym, HW * Tw));
     CPT_CUDA(ar.alloc(&d_modes, (size_t)Tw * F.nby * F.nbx));
-    CPT_CUDA(ar.alloc(&d_prep, nprep));
     CPT_CUDA(ar.alloc(&d_cnt64, 8));
     CPT_CUDA(ar.alloc(&d_off, compact_tiles(NS) + 1));
     CPT_CUDA(ar.alloc(&d_stmp, scan_temp_elems(compact_tiles(NS) + 1)));
@@ -1868,7 +1865,6 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
         }
         if (F.has_net) A.net = net;
         A.log2tab = d_lg;
-        A.prep_done = d_prep;
         int U = F.has_modes ? (B == 32 ? 32 : 16) : 8;
         if (prm->pred == CPT_PRED_SL && tune.sl_unit == 16) U = 16;
         A.U = U;
@@ -1886,7 +1882,7 @@ static cpt_status compress_streamed(const float* uv, const cpt_dims* dims, const
         // reconstruction words: the carried slice, then nothing present
         if (vb == 1) CPT_CUDA(cudaMemcpyAsync(d_qhat, d_qhat_carry, HW * sizeof(int2), cudaMemcpyDeviceToDevice, s));
         CPT_CUDA(cudaMemsetAsync(d_qhat + 2 * HW * vb, 0, 2 * HW * (Tv - vb) * sizeof(int32_t), s));
-        CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
+        if (F.want_sl) CPT_CUDA(cudaMemsetAsync(d_psl, 0, HW * Tw * sizeof(int2), s));  // no prediction word present
         CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)Tw * F.nby * F.nbx, s));
         CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * (nprep + 2), s));
         CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
@@ -2378,16 +2374,13 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     const unsigned long long nu = want_sl ? (unsigned long long)(T - 1) * A.nur * A.nuc : 0ull;
     if (nu >= 0x7FFFFFFFull) return fail(CPT_ERR_UNSUPPORTED, "too many prediction units");
     A.n_units = (unsigned)nu;
-    unsigned *d_prep, *d_queue, *d_ticket;
-    const size_t nprep = (size_t)T * A.nur * A.nuc;
-    CPT_CUDA(ar.alloc(&d_prep, nprep));
+    unsigned *d_queue, *d_ticket;
     CPT_CUDA(ar.alloc(&d_queue, (size_t)A.n_units + 2));
     CPT_CUDA(ar.alloc(&d_ticket, 1));
-    CPT_CUDA(cudaMemsetAsync(d_prep, 0, sizeof(unsigned) * nprep, s));
+    if (pred != 0) CPT_CUDA(cudaMemsetAsync(d_psl, 0, N * sizeof(int2), s));  // no prediction word present
     CPT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(unsigned) * ((size_t)A.n_units + 2), s));
     CPT_CUDA(cudaMemsetAsync(d_ticket, 0, sizeof(unsigned), s));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
-    A.prep_done = d_prep;
     A.qslot = d_queue + 2;
     A.qtail = d_queue + 1;
     A.status = d_status;

@@ -41,7 +41,6 @@ struct SliceArgs {
     uint8_t* qxi;           // [T][H][W] bound codes
     uint32_t* sym;          // [T][H][W] residual symbols, u | v << 16
     int* xi_out;            // optional [T][H][W] integer bounds
-    unsigned* prep_done;    // [T][nur][nuc] 1 once the prep unit is done
     unsigned* qslot;        // [queue_len] ready queue of prep units of the launch (global unit id + 1, 0 = not yet filled)
     unsigned* qtail;        // next queue position to fill
     int* status;            // device status word of the launch (0 = ok)

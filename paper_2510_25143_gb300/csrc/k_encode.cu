@@ -605,14 +605,6 @@ __device__ void mop_unit(const SliceArgs& a, int t, int r0, int c0, PS& ps, int 
     }
 }
 
-// Release-ordered add: everything this warp wrote before is visible to a
-// reader that acquires the counter.
-__device__ __forceinline__ void warp_publish_add(unsigned* ctr, unsigned v) {
-    __threadfence();
-    __syncwarp();
-    if ((threadIdx.x & 31u) == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
-}
-
 // Decoding: the modes of the unit's blocks from the stream's mode bits.
 __device__ void unit_modes_from_bits(const SliceArgs& a, int t, int r0, int c0, unsigned char* modes) {
     const int lgB = __ffs(a.B) - 1, lgN = __ffs(a.U) - 1 - lgB;  // B and U are powers of two
@@ -718,16 +710,17 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             auto prev = [&](int i, int j) -> int2 { return Ps.at(i, j); };
             for (int tr = 0; tr < uh; tr += 8)
                 for (int tc = 0; tc < uw; tc += 8) {
-                    auto out = [&](int li, int lj, int2 p) { Psl[(size_t)(r0 + tr + li) * W + c0 + tc + lj] = p; };
+                    // the learned predictor alone: the final (tagged) word; the
+                    // mixture: a plain value, tagged once the block's mode is known
+                    auto out = [&](int li, int lj, int2 p) {
+                        int2* d = Psl + (size_t)(r0 + tr + li) * W + c0 + tc + lj;
+                        if (a.pred == 3) st_word(d, p);
+                        else *d = p;
+                    };
                     net_tile<8>(nd, ps.net, r0 + tr, c0 + tc, H, W, prev, out);
                 }
             if (a.pred == 4 && dec) {
                 unit_modes_from_bits(a, t, r0, c0, ps.modes);
-                for (int k = lane; k < U * U; k += 32) {
-                    const int li = k >> lgU, lj = k & (U - 1);
-                    if (li < uh && lj < uw && !ps.modes[block_of(li, lj)])
-                        Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
-                }
             } else if (a.pred == 4) {
                 // the learned mixture: block modes as MoP's with the net in SL's
                 // place; the scratch of the net gives way to q(t) and the samples
@@ -751,13 +744,19 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
                 cp_async_wait_all();
                 __syncwarp();
                 mop_unit(a, t, r0, c0, ps, Rw);
+            }
+            if (a.pred == 4) {
+                // the mixture's final words: the net's prediction in the blocks
+                // that chose it, the 3DL marker in the others
+                __threadfence();  // the plain values are read back through L2 by other lanes
+                __syncwarp();
                 for (int k = lane; k < U * U; k += 32) {
                     const int li = k >> lgU, lj = k & (U - 1);
-                    if (li < uh && lj < uw && !ps.modes[block_of(li, lj)])
-                        Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+                    if (li >= uh || lj >= uw) continue;
+                    int2* d = Psl + (size_t)(r0 + li) * W + c0 + lj;
+                    st_word(d, ps.modes[block_of(li, lj)] ? __ldcg(d) : make_int2(kNoSL, 0));
                 }
             }
-            warp_publish_add(a.prep_done + ((size_t)t * a.nur + (r0 >> lgU)) * a.nuc + (c0 >> lgU), 1u);
             return;
         }
     }
@@ -770,8 +769,9 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
         const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
                               : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
         const int2 p = make_int2(pu, pv);
+        // MoP keeps a sampled prediction until its block's mode is known
         if (mop) ps.psl[li][lj] = p;
-        Psl[(size_t)i * W + j] = p;
+        else st_word(Psl + (size_t)i * W + j, p);
         sub += md > 0;
         steps += md;
     };
@@ -809,8 +809,10 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             const unsigned bal = __ballot_sync(FULL, need);
             if (need) ps.list[cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(li * 32 + lj);
             cnt += __popc(bal);
-            // vertices of the blocks that kept 3DL: the marker instead of a prediction
-            if (in && !mode_sl) Psl[(size_t)(r0 + li) * W + c0 + lj] = make_int2(kNoSL, kNoSL);
+            // the sampled predictions of the blocks that chose SL, and the
+            // marker instead of a prediction in the blocks that kept 3DL
+            if (mode_sl && sampled) st_word(Psl + (size_t)(r0 + li) * W + c0 + lj, ps.psl[li][lj]);
+            if (in && !mode_sl) st_word(Psl + (size_t)(r0 + li) * W + c0 + lj, make_int2(kNoSL, 0));
         }
         __syncwarp();
         for (int m = lane; m < cnt; m += 32) {
@@ -819,7 +821,7 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
             int pu, pv;
             const int md = staged ? sl_predict(Ps, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv)
                                   : sl_predict(Pg, H, W, i, j, a.cfl_x, a.cfl_y, pu, pv);
-            Psl[(size_t)i * W + j] = make_int2(pu, pv);
+            st_word(Psl + (size_t)i * W + j, make_int2(pu, pv));
             sub += md > 0;
             steps += md;
         }
@@ -833,9 +835,6 @@ __device__ void prep_unit(const SliceArgs& a, int t, int r0, int c0, Sm& sm, con
         atomicAdd(a.counters + 0, (unsigned long long)sub);
         atomicAdd(a.counters + 1, (unsigned long long)steps);
     }
-    const int nstrips = (H + 31) / 32;
-    (void)nstrips;
-    warp_publish_add(a.prep_done + ((size_t)t * a.nur + (r0 >> lgU)) * a.nuc + (c0 >> lgU), 1u);
 }
 
 // Units of slice t (t >= 1) that became ready while wave(t-1, s) went from
@@ -1004,7 +1003,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     // loads for a step, issued two steps ahead (two alternating register sets)
     struct Pf {
         unsigned long long wp, wa, wu;  // slice t-1 at (i, j); lane 0: slice t-1 and t at (i-1, j)
-        int2 pn;                        // SL prediction at (i, j)
+        unsigned long long wn;          // SL prediction word at (i, j) (tagged like a reconstruction)
     };
     auto issue = [&](int kk, Pf& f) {
         const int jj = kk - lane;
@@ -1017,22 +1016,9 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
             if (has_prev) f.wa = ld_word(Pm + (size_t)(i0 - 1) * W + jj);
             f.wu = ld_word(Pc + (size_t)(i0 - 1) * W + jj);
         }
-        if (need_sl && rowok && col) f.pn = __ldcg(Psl + (size_t)i * W + jj);
+        f.wn = 0;
+        if (need_sl && rowok && col) f.wn = ld_word(Psl + (size_t)i * W + jj);
     };
-    // the SL predictions of unit (ur, uc) before the first load that reads
-    // them: the unit's first row (lane lu) reaches column uc*U at step uc*U + lu
-    const int lgU = __ffs(a.U) - 1;  // unit sides are powers of two
-    auto await_sl = [&](int kk) -> bool {
-        if (!need_sl) return true;
-        for (int lu = 0; lu < 32 && i0 + lu < H; lu += a.U) {
-            const int c = kk - lu;
-            if (c < 0 || (c & (a.U - 1)) != 0 || c >= W) continue;
-            const unsigned* f = a.prep_done + ((size_t)t * a.nur + ((i0 + lu) >> lgU)) * a.nuc + (c >> lgU);
-            if (!warp_wait_geq(a, f, 1u)) return false;
-        }
-        return true;
-    };
-
     WaveRing& ring = sm.ring;
     __syncwarp();
     stage_chunk(ring, 0, cls, cm, Dq, Dn, Db, Dnb, stage_next, stage_below, !dec, W);
@@ -1040,17 +1026,7 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     stage_chunk(ring, 1, cls, cm, Dq, Dn, Db, Dnb, stage_next, stage_below, !dec, W);
     asm volatile("cp.async.commit_group;" ::: "memory");
     Pf fa, fb;
-    fa.pn = fb.pn = z;
-    // on a failed wait the item gives up after its copies into the ring land
-    if (!await_sl(0)) {
-        cp_async_wait_all();
-        return false;
-    }
     issue(0, fa);
-    if (!await_sl(1)) {
-        cp_async_wait_all();
-        return false;
-    }
     issue(1, fb);
 
     int2 h0 = z, h1 = z, h2 = z;  // slice t-1 at (i, j), (i, j-1), (i, j-2)
@@ -1067,10 +1043,13 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
             return false;
         if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), lane == 0 && has_above && col, f.wu))
             return false;
+        // the SL prediction, once its unit has written it
+        if (!poll_word(a, Psl + (size_t)(rowok ? i : 0) * W + (col ? j : 0), need_sl && rowok && col, f.wn))
+            return false;
         const int2 pk = (has_prev && rowok && col) ? word_value(f.wp) : z;
         const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(f.wa) : z;
         const int2 uk = (lane == 0 && has_above && col) ? word_value(f.wu) : z;
-        const int2 pslk = f.pn;
+        const int2 pslk = (need_sl && rowok && col) ? word_value(f.wn) : z;
         // chunk g of the staged inputs starts: stage g + 2 over the slot of
         // g - 1 (no longer read), then wait for g and g + 1
         if (k % kChunk == 0) {
@@ -1080,7 +1059,6 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
         }
-        if (!await_sl(k + 2)) return false;
         issue(k + 2, f);
         // neighbours 0..3
         h2 = h1;
