@@ -96,6 +96,7 @@ struct StageTimer {
     }
     void begin(int stage) {
         if (!on) return;
+        end();  // a stage still open ends here
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
         cudaEventRecord(e, s);
@@ -297,6 +298,11 @@ struct Staging {
     }
 };
 static thread_local Staging t_staging;
+
+// A CUDA event owned by a host thread (created on first use).
+struct EventHolder {
+    cudaEvent_t ev = nullptr;
+};
 
 // One Huffman stream: host-side code book and the device buffers of its
 // tile offsets and words.
@@ -832,8 +838,38 @@ struct FieldJob {
         return CPT_OK;
     }
 
+    // ---- stage 6: verification (Eq. 4 on every face, pointwise bound),
+    // launched once the histograms are on their way to the host, so that it
+    // runs while the host builds the code books; its result is read after the
+    // call's last synchronisation
+    cpt_status verify_launch() {
+        std::memset(vo_h, 0, sizeof(VerifyOut));
+        if (prm->verify && vfault.vertex >= 0 && (size_t)vfault.vertex < N) {
+            // failure injection (tests): one corrupted reconstruction word
+            int2 w;
+            int2* p = reinterpret_cast<int2*>(d_qhat) + vfault.vertex;
+            CPT_CUDA(cudaMemcpyAsync(&w, p, sizeof(int2), cudaMemcpyDeviceToHost, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+            w.x += vfault.delta;
+            CPT_CUDA(cudaMemcpyAsync(p, &w, sizeof(int2), cudaMemcpyHostToDevice, s));
+            CPT_CUDA(cudaStreamSynchronize(s));
+        }
+        if (prm->verify) {
+            const int open = tm.open_stage;  // the entropy stage, timed apart from the verification
+            tm.begin(6);
+            CPT_CUDA(ar.alloc(&d_vo, 1));
+            CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
+            launch_verify(d_qhat, d_mask, d_uv, H, W, T, k, d_vo, s);
+            st.launches[6]++;
+            CPT_CUDA(cudaMemcpyAsync(vo_h, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
+            tm.end();
+            if (open >= 0) tm.begin(open);
+        }
+        return CPT_OK;
+    }
+
     // ---- phase 5 (after the tile offsets arrived): layout, header, words,
-    // verification, debug copies
+    // debug copies
     cpt_status write_stream() {
         const uint8_t* mbits_h = stage_h + st_hist;  // block modes as bits (packed on the device)
         const unsigned long long* toff_h =
@@ -905,27 +941,6 @@ struct FieldJob {
         st.launches[5] += 9;
         tm.end();
 
-        // ---- stage 6: verification (Eq. 4 on every face, pointwise bound)
-        std::memset(vo_h, 0, sizeof(VerifyOut));
-        if (prm->verify && vfault.vertex >= 0 && (size_t)vfault.vertex < N) {
-            // failure injection (tests): one corrupted reconstruction word
-            int2 w;
-            int2* p = reinterpret_cast<int2*>(d_qhat) + vfault.vertex;
-            CPT_CUDA(cudaMemcpyAsync(&w, p, sizeof(int2), cudaMemcpyDeviceToHost, s));
-            CPT_CUDA(cudaStreamSynchronize(s));
-            w.x += vfault.delta;
-            CPT_CUDA(cudaMemcpyAsync(p, &w, sizeof(int2), cudaMemcpyHostToDevice, s));
-            CPT_CUDA(cudaStreamSynchronize(s));
-        }
-        if (prm->verify) {
-            tm.begin(6);
-            CPT_CUDA(ar.alloc(&d_vo, 1));
-            CPT_CUDA(cudaMemsetAsync(d_vo, 0, sizeof(VerifyOut), s));
-            launch_verify(d_qhat, d_mask, d_uv, H, W, T, k, d_vo, s);
-            st.launches[6]++;
-            CPT_CUDA(cudaMemcpyAsync(vo_h, d_vo, sizeof(VerifyOut), cudaMemcpyDeviceToHost, s));
-            tm.end();
-        }
         // ---- debug copies and rate diagnostics
         if (dbg && dbg->zero_runs) {
             unsigned long long* d_bins;
@@ -1229,6 +1244,11 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
     }
     CPT_CUDA(cudaStreamSynchronize(s));
     mark(3);
+    static thread_local EventHolder t_hist_ev;  // the histograms' arrival on the host
+    if (!t_hist_ev.ev && cudaEventCreateWithFlags(&t_hist_ev.ev, cudaEventDisableTiming) != cudaSuccess) {
+        t_hist_ev.ev = nullptr;
+        return fail(CPT_ERR_CUDA, "event creation failed");
+    }
     size_t stage_total = 0;
     for (int f = 0; f < n; ++f) {
         cpt_status rc = jobs[f]->scatter_hist();
@@ -1243,7 +1263,12 @@ static cpt_status run_jobs(FieldJob* const* jobs, int n, const cpt_params* prm, 
         cpt_status rc = jobs[f]->copy_hist();
         if (rc != CPT_OK) return rc;
     }
-    CPT_CUDA(cudaStreamSynchronize(s));
+    CPT_CUDA(cudaEventRecord(t_hist_ev.ev, s));
+    for (int f = 0; f < n; ++f) {
+        cpt_status rc = jobs[f]->verify_launch();
+        if (rc != CPT_OK) return rc;
+    }
+    CPT_CUDA(cudaEventSynchronize(t_hist_ev.ev));
     mark(4);
     {   // the fields' code books on host threads (package-merge is the host's share of the method)
         const int nth = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));

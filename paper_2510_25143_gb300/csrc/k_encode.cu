@@ -489,7 +489,8 @@ __device__ long long warp_block_score(const uint16_t* smp, int nslots, int B, un
     if (nv > 0) h0 = ((long long)nv * (long long)__ldg(lg + nv) - (long long)acc) / (long long)nv;
     long long pen = 0;
     if (nv + nf > 0) pen = (long long)(((unsigned long long)(16u * nf) << 32) / (unsigned long long)(nv + nf));
-    long long meta = (long long)((1ull << 32) / (unsigned long long)(2 * B * B));
+    const int lgB = __ffs(B) - 1;  // B is a power of two: 2^32 / (2 B^2) exactly
+    long long meta = (long long)((1ull << 32) >> (2 * lgB + 1));
     __syncwarp();
     return h0 + pen + meta;
 }
