@@ -2306,8 +2306,8 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     uint16_t* d_qd;
     uint32_t* d_sym;
     int32_t* d_ld;
-    int2 *d_dcs, *d_draw, *d_qhat, *d_psl;
-    unsigned long long *d_cnt, *d_tmp;
+    int2 *d_dcs, *d_draw, *d_qhat, *d_psl, *d_rraw;
+    unsigned long long *d_qoff, *d_loff, *d_tmp;
     CPT_CUDA(ar.alloc(&d_status, 1));
     CPT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
     CPT_CUDA(ar.alloc(&d_qxi, N));
@@ -2315,40 +2315,45 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(ar.alloc(&d_sym, N));
     CPT_CUDA(ar.alloc(&d_ld, n_ld));
     const size_t ND = diag_elems(H, W, T);  // strip-diagonal inputs of the pipeline, zero padding
-    CPT_CUDA(ar.alloc(&d_dcs, ND));
+    CPT_CUDA(ar.alloc(&d_dcs, ND));  // every element written by the transposing copy (padding zero)
     CPT_CUDA(ar.alloc(&d_draw, ND));
-    CPT_CUDA(cudaMemsetAsync(d_dcs, 0, ND * sizeof(int2), s));
-    CPT_CUDA(cudaMemsetAsync(d_draw, 0, ND * sizeof(int2), s));
     CPT_CUDA(ar.alloc(&d_qhat, N));
     CPT_CUDA(ar.alloc(&d_psl, pred != 0 ? N : 1));
-    CPT_CUDA(ar.alloc(&d_cnt, N));
-    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(N)));
+    CPT_CUDA(ar.alloc(&d_rraw, N));
+    const size_t nt = compact_tiles(N);
+    CPT_CUDA(ar.alloc(&d_qoff, nt + 1));
+    CPT_CUDA(ar.alloc(&d_loff, nt + 1));
+    CPT_CUDA(ar.alloc(&d_tmp, scan_temp_elems(nt + 1)));
     CPT_CUDA(ar.alloc(&d_modes, std::max<size_t>(mode_bytes, 1)));
     if (mode_bytes) CPT_CUDA(cudaMemcpyAsync(d_modes, modes, mode_bytes, cudaMemcpyHostToDevice, s));
     if (n_ld) CPT_CUDA(cudaMemcpyAsync(d_ld, ldp, 4 * n_ld, cudaMemcpyHostToDevice, s));
     cpt_status rc = decode_huff_stream<uint8_t>(hx, d_qxi, d_status, ar, s);
     if (rc != CPT_OK) return rc;
-    launch_qd_count(d_qxi, N, d_cnt, d_status, s);
-    unsigned long long last_cnt = 0, last_off = 0;
-    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    launch_exclusive_scan_u64(d_cnt, N, d_tmp, s);
-    CPT_CUDA(cudaMemcpyAsync(&last_off, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
+    // residual symbols per tile of the bound codes; their total must be the
+    // length of the Q_d stream
+    unsigned long long total = 0;
     int status = 0;
+    CPT_CUDA(cudaMemsetAsync(d_qoff + nt, 0, sizeof(unsigned long long), s));
+    launch_dec_tile_qd(d_qxi, N, d_qoff, d_status, s);
+    launch_exclusive_scan_u64(d_qoff, nt + 1, d_tmp, s);
+    CPT_CUDA(cudaMemcpyAsync(&total, d_qoff + nt, 8, cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaStreamSynchronize(s));
-    if (status != 0 || last_off + last_cnt != hd.nsym) return fail(CPT_ERR_CORRUPT, "bound codes do not match the residuals");
+    if (status != 0 || total != hd.nsym) return fail(CPT_ERR_CORRUPT, "bound codes do not match the residuals");
     rc = decode_huff_stream<uint16_t>(hd, d_qd, d_status, ar, s);
     if (rc != CPT_OK) return rc;
-    launch_gather_sym(d_qxi, d_cnt, d_qd, hd.nsym, N, d_sym, d_status, s);
-    launch_count_pack(d_qxi, d_sym, N, d_cnt, s);
-    CPT_CUDA(cudaMemcpyAsync(&last_cnt, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    launch_exclusive_scan_u64(d_cnt, N, d_tmp, s);
-    CPT_CUDA(cudaMemcpyAsync(&last_off, d_cnt + N - 1, 8, cudaMemcpyDeviceToHost, s));
-    launch_gather_raw(d_qxi, d_sym, d_cnt, d_ld, n_ld, H, W, T, d_dcs, d_draw, d_status, s);
+    // each vertex's symbols, the verbatim values per tile, then the values;
+    // (bound code, symbols) go to d_qhat and the values to d_rraw in raster
+    // order, from where the transposing copy lays both out strip-diagonally
+    CPT_CUDA(cudaMemsetAsync(d_loff + nt, 0, sizeof(unsigned long long), s));
+    launch_dec_tile_sym(d_qxi, N, d_qd, hd.nsym, d_qoff, d_sym, d_loff, d_status, s);
+    launch_exclusive_scan_u64(d_loff, nt + 1, d_tmp, s);
+    launch_dec_tile_raw(d_qxi, d_sym, N, d_ld, n_ld, d_loff, d_qhat, d_rraw, d_status, s);
+    launch_diag_transpose(d_qhat, d_rraw, H, W, T, d_dcs, d_draw, s);
+    CPT_CUDA(cudaMemcpyAsync(&total, d_loff + nt, 8, cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaStreamSynchronize(s));
-    if (status != 0 || ((last_off + last_cnt) & 0xFFFFFFFFull) != n_ld)
-        return fail(CPT_ERR_CORRUPT, "verbatim values do not match the codes");
+    if (status != 0 || total != n_ld) return fail(CPT_ERR_CORRUPT, "verbatim values do not match the codes");
     // reconstruction: the encoder's pipeline in decoding mode.  Waves rebuild
     // qhat from the symbols in raster order, prediction units give the SL or
     // learned predictions, MoP block modes come from the stream.

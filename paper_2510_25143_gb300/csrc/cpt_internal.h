@@ -149,7 +149,6 @@ constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols
 
 // k_entropy.cu
 size_t scan_temp_elems(size_t n);
-void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s);
 void launch_exclusive_scan_u64(unsigned long long* data, size_t n, unsigned long long* tmp, cudaStream_t s);
 // compaction in tiles: counts per tile, then (after an exclusive scan of the
 // tile counts, with one extra element for the total) the scatter
@@ -157,6 +156,15 @@ size_t compact_tiles(size_t N);
 void launch_tile_count(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* tile_cnt,
                        cudaStream_t s);
 void launch_pack_bits(const uint8_t* in, size_t n, uint8_t* out, cudaStream_t s);
+// decoder: tiled expansion of Q_d and L_d, then the strip-diagonal layout
+void launch_dec_tile_qd(const uint8_t* qxi, size_t N, unsigned long long* tile_cnt, int* status, cudaStream_t s);
+void launch_dec_tile_sym(const uint8_t* qxi, size_t N, const uint16_t* qd, size_t n_qd,
+                         const unsigned long long* qd_off, uint32_t* sym, unsigned long long* tile_ld, int* status,
+                         cudaStream_t s);
+void launch_dec_tile_raw(const uint8_t* qxi, const uint32_t* sym, size_t N, const int32_t* ld, size_t n_ld,
+                         const unsigned long long* ld_off, int2* dcs, int2* raw, int* status, cudaStream_t s);
+void launch_diag_transpose(const int2* a_in, const int2* b_in, int H, int W, int T, int2* a_out, int2* b_out,
+                           cudaStream_t s);
 void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t* q,
                          const unsigned long long* tile_off, size_t N, uint16_t* qd_out, int32_t* ld_out,
                          cudaStream_t s);
@@ -174,13 +182,6 @@ void launch_encode_u16(const uint16_t* x, size_t n, const uint32_t* table, const
 // k_decode.cu
 void launch_huff_decode_u8(const HuffDecode& h, uint8_t* out, int* status, cudaStream_t s);
 void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cudaStream_t s);
-void launch_qd_count(const uint8_t* qxi, size_t N, unsigned long long* cnt, int* status, cudaStream_t s);
-void launch_gather_sym(const uint8_t* qxi, const unsigned long long* off, const uint16_t* qd, size_t n_qd, size_t N,
-                       uint32_t* sym, int* status, cudaStream_t s);
-// the decoder's inputs of the pipeline, strip-diagonal (zeroed before): dcs =
-// (bound code, residual symbols), draw = verbatim values from L_d
-void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned long long* off, const int32_t* ld,
-                       size_t n_ld, int H, int W, int T, int2* dcs, int2* draw, int* status, cudaStream_t s);
 void launch_untag(int2* qhat, size_t N, cudaStream_t s);  // reconstruction words -> values
 void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s);  // q_hat 2^-k
 

@@ -1,9 +1,10 @@
 // Decoder kernels: canonical Huffman decoding from the stream's sync points,
-// expansion of the bound codes, residual symbols and verbatim values to the
-// vertices (in the strip-diagonal layout of the encoder's pipeline, which
-// then runs in decoding mode: the inverse of the raster loop of Alg. 3, with
-// bounds from the stream and no face work), and the conversion back to
-// float.  A malformed stream sets the status word to a corruption code;
+// the untagging of the reconstruction words and the conversion back to
+// float.  (The expansion of the bound codes, residual symbols and verbatim
+// values to the vertices, in the strip-diagonal layout of the encoder's
+// pipeline, sits beside the encoder's compaction; the pipeline then runs in
+// decoding mode: the inverse of the raster loop of Alg. 3, with bounds from
+// the stream and no face work.)  A malformed stream sets the status word to a corruption code;
 // nothing reads or writes out of bounds.
 #include <cmath>
 
@@ -103,74 +104,6 @@ __global__ void __launch_bounds__(64) huff_decode_kernel(HuffDecode h, Out* __re
     if (c + 1 < nchunks && p != h.chunk_off[c + 1]) atomicCAS(status, 0, kStatusCorrupt);
 }
 
-// ---------------------------------------------------------------------------
-// expansion to the vertices
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) qd_count_kernel(const uint8_t* __restrict__ qxi, size_t N,
-                                                       unsigned long long* __restrict__ cnt, int* __restrict__ status) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        const uint8_t c = qxi[v];
-        if (c > 24) atomicCAS(status, 0, kStatusCorrupt);
-        cnt[v] = c ? 2ull : 0ull;
-    }
-}
-
-__global__ void __launch_bounds__(256) gather_sym_kernel(const uint8_t* __restrict__ qxi,
-                                                         const unsigned long long* __restrict__ off,
-                                                         const uint16_t* __restrict__ qd, size_t n_qd, size_t N,
-                                                         uint32_t* __restrict__ sym, int* __restrict__ status) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        uint32_t s = 0;
-        if (qxi[v]) {
-            const size_t o = (size_t)off[v];
-            if (o + 2 > n_qd) {
-                atomicCAS(status, 0, kStatusCorrupt);
-            } else {
-                s = (uint32_t)qd[o] | ((uint32_t)qd[o + 1] << 16);
-            }
-        }
-        sym[v] = s;
-    }
-}
-
-// Verbatim values of each vertex from L_d, written with (bound code, residual
-// symbols) in the strip-diagonal layout the reconstruction pipeline stages.
-__global__ void __launch_bounds__(256) gather_raw_kernel(const uint8_t* __restrict__ qxi, const uint32_t* __restrict__ sym,
-                                                         const unsigned long long* __restrict__ off,
-                                                         const int32_t* __restrict__ ld, size_t n_ld, int H, int W,
-                                                         int T, int2* __restrict__ dcs, int2* __restrict__ raw,
-                                                         int* __restrict__ status) {
-    const size_t nstrips = (size_t)(H + 31) >> 5;
-    // one row of one slice per block iteration: no division per vertex
-    for (long long r = blockIdx.x; r < (long long)T * H; r += gridDim.x) {
-        const int t = (int)(r / H), i = (int)(r - (long long)t * H);
-        const size_t row = (size_t)r * W;
-        const size_t drow = (((size_t)t * nstrips + (i >> 5)) * (size_t)(W + 31) + (i & 31)) * 32 + (i & 31);
-        for (int j = threadIdx.x; j < W; j += blockDim.x) {
-            const size_t v = row + j;
-            const size_t dv = drow + (size_t)j * 32;
-            size_t o = (size_t)(off[v] & 0xFFFFFFFFull);
-            int2 rr = make_int2(0, 0);
-            const uint8_t c = qxi[v];
-            const uint32_t sy = c ? sym[v] : 0u;
-            if (c == 0) {
-                if (o + 2 > n_ld) { atomicCAS(status, 0, kStatusCorrupt); }
-                else { rr.x = ld[o]; rr.y = ld[o + 1]; }
-            } else {
-                const size_t need = ((sy & 0xFFFFu) == 0) + ((sy >> 16) == 0);
-                if (o + need > n_ld) {
-                    atomicCAS(status, 0, kStatusCorrupt);
-                } else {
-                    if ((sy & 0xFFFFu) == 0) rr.x = ld[o++];
-                    if ((sy >> 16) == 0) rr.y = ld[o];
-                }
-            }
-            raw[dv] = rr;
-            dcs[dv] = make_int2((int)c, (int)sy);
-        }
-    }
-}
-
 // The pipeline's reconstruction words (x, y ^ kQhatTag) back to values.
 __global__ void __launch_bounds__(256) untag_kernel(int2* __restrict__ q, size_t N) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x)
@@ -214,17 +147,6 @@ void launch_huff_decode_u8(const HuffDecode& h, uint8_t* out, int* status, cudaS
 void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cudaStream_t s) {
     const unsigned long long nchunks = (h.nsym + kChunkSyms - 1) / kChunkSyms;
     if (nchunks) huff_decode_kernel<uint16_t><<<(unsigned)((nchunks + 63) / 64), 64, 0, s>>>(h, out, status);
-}
-void launch_qd_count(const uint8_t* qxi, size_t N, unsigned long long* cnt, int* status, cudaStream_t s) {
-    qd_count_kernel<<<1216, 256, 0, s>>>(qxi, N, cnt, status);
-}
-void launch_gather_sym(const uint8_t* qxi, const unsigned long long* off, const uint16_t* qd, size_t n_qd, size_t N,
-                       uint32_t* sym, int* status, cudaStream_t s) {
-    gather_sym_kernel<<<1216, 256, 0, s>>>(qxi, off, qd, n_qd, N, sym, status);
-}
-void launch_gather_raw(const uint8_t* qxi, const uint32_t* sym, const unsigned long long* off, const int32_t* ld,
-                       size_t n_ld, int H, int W, int T, int2* dcs, int2* draw, int* status, cudaStream_t s) {
-    gather_raw_kernel<<<1216, 256, 0, s>>>(qxi, sym, off, ld, n_ld, H, W, T, dcs, draw, status);
 }
 void launch_untag(int2* qhat, size_t N, cudaStream_t s) { untag_kernel<<<1216, 256, 0, s>>>(qhat, N); }
 void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s) {

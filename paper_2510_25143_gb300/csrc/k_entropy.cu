@@ -286,15 +286,176 @@ __global__ void __launch_bounds__(512) hist_u16_kernel(const uint16_t* __restric
 
 // per-vertex counts (the decoder's layout of the verbatim values needs each
 // vertex's offset)
-__global__ void __launch_bounds__(256) count_pack_kernel(const uint8_t* __restrict__ qxi,
-                                                         const uint32_t* __restrict__ sym, size_t N,
-                                                         unsigned long long* __restrict__ cnt) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x)
-        cnt[v] = vertex_count(qxi[v], qxi[v] ? sym[v] : 0u);
+
+
+// ---------------------------------------------------------------------------
+// Decoder: expansion of Q_xi, Q_d and L_d to the vertices, the inverse of the
+// tiled compaction above.  Tiles of kCmpTile vertices in raster order: a
+// count per tile (residual symbols from the bound codes), a scan of the tile
+// counts, a pass that gathers each vertex's two residual symbols (block scan
+// of the counts inside the tile) and counts the verbatim values they call
+// for, a scan of those tile counts, and a pass that gathers the verbatim
+// values.  The results are laid out in raster order and then moved to the
+// pipeline's strip-diagonal layout by a transposing copy.  A stream whose
+// counts do not match is reported through the status word; nothing reads or
+// writes out of bounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load16_codes(const uint8_t* __restrict__ qxi, size_t N, size_t base,
+                                             unsigned char c[kCmpPer]) {
+    if (base + kCmpPer <= N) {
+        const uint4 cv = __ldg(reinterpret_cast<const uint4*>(qxi + base));
+        const unsigned cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int k = 0; k < kCmpPer; ++k) c[k] = (unsigned char)(cw[k >> 2] >> (8 * (k & 3)));
+    } else {
+#pragma unroll
+        for (int k = 0; k < kCmpPer; ++k) c[k] = base + k < N ? qxi[base + k] : (unsigned char)0;
+    }
 }
 
-void launch_count_pack(const uint8_t* qxi, const uint32_t* sym, size_t N, unsigned long long* cnt, cudaStream_t s) {
-    count_pack_kernel<<<1216, 256, 0, s>>>(qxi, sym, N, cnt);
+// residual symbols per tile (2 per vertex with a nonzero bound code)
+__global__ void __launch_bounds__(kCmpThreads) dec_tile_qd_kernel(const uint8_t* __restrict__ qxi, size_t N,
+                                                                  unsigned long long* __restrict__ tile_cnt,
+                                                                  int* __restrict__ status) {
+    __shared__ unsigned long long wt[32], tot;
+    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    unsigned char c[kCmpPer];
+    load16_codes(qxi, N, base, c);
+    unsigned long long n = 0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k) {
+        n += c[k] ? 2u : 0u;
+        bad |= c[k] > 24;
+    }
+    if (bad) atomicCAS(status, 0, kStatusCorrupt);
+    block_exclusive_scan(n, wt, &tot);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+// sym[v] = both residual symbols of v (0 without a bound); tile_ld[b] = the
+// verbatim values the tile's symbols call for
+__global__ void __launch_bounds__(kCmpThreads) dec_tile_sym_kernel(const uint8_t* __restrict__ qxi, size_t N,
+                                                                   const uint16_t* __restrict__ qd, size_t n_qd,
+                                                                   const unsigned long long* __restrict__ qd_off,
+                                                                   uint32_t* __restrict__ sym,
+                                                                   unsigned long long* __restrict__ tile_ld,
+                                                                   int* __restrict__ status) {
+    __shared__ unsigned long long wt[32], tot;
+    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    unsigned char c[kCmpPer];
+    load16_codes(qxi, N, base, c);
+    unsigned long long n = 0;
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k) n += c[k] ? 2u : 0u;
+    size_t o = (size_t)(block_exclusive_scan(n, wt, &tot) + qd_off[blockIdx.x]);
+    __syncthreads();  // wt is scanned again below
+    unsigned long long nl = 0;
+    uint32_t sy[kCmpPer];
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k) {
+        uint32_t x = 0;
+        if (c[k]) {
+            if (o + 2 > n_qd) {
+                atomicCAS(status, 0, kStatusCorrupt);
+            } else {
+                x = (uint32_t)qd[o] | ((uint32_t)qd[o + 1] << 16);
+            }
+            o += 2;
+        }
+        sy[k] = x;
+        nl += vertex_count(c[k], x) & 0xFFFFFFFFull;
+    }
+    if (base + kCmpPer <= N) {
+#pragma unroll
+        for (int k = 0; k < kCmpPer; k += 4)
+            *reinterpret_cast<uint4*>(sym + base + k) = make_uint4(sy[k], sy[k + 1], sy[k + 2], sy[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kCmpPer; ++k)
+            if (base + k < N) sym[base + k] = sy[k];
+    }
+    // tiles past N count nothing (their codes read as 0, so nl counts 2 per
+    // missing vertex: exclude them)
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k)
+        if (base + k >= N) nl -= 2;
+    block_exclusive_scan(nl, wt, &tot);
+    if (threadIdx.x == 0) tile_ld[blockIdx.x] = tot;
+}
+
+// the vertices' (bound code, symbols) and verbatim values in raster order
+__global__ void __launch_bounds__(kCmpThreads) dec_tile_raw_kernel(const uint8_t* __restrict__ qxi,
+                                                                   const uint32_t* __restrict__ sym, size_t N,
+                                                                   const int32_t* __restrict__ ld, size_t n_ld,
+                                                                   const unsigned long long* __restrict__ ld_off,
+                                                                   int2* __restrict__ dcs, int2* __restrict__ raw,
+                                                                   int* __restrict__ status) {
+    __shared__ unsigned long long wt[32], tot;
+    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    unsigned char c[kCmpPer];
+    uint32_t sy[kCmpPer];
+    load16(qxi, sym, N, base, c, sy);
+    unsigned long long n = 0;
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k)
+        if (base + k < N) n += vertex_count(c[k], sy[k]) & 0xFFFFFFFFull;
+    size_t o = (size_t)(block_exclusive_scan(n, wt, &tot) + ld_off[blockIdx.x]);
+#pragma unroll
+    for (int k = 0; k < kCmpPer; ++k) {
+        const size_t v = base + k;
+        if (v >= N) break;
+        int2 rr = make_int2(0, 0);
+        const bool need_u = c[k] == 0 || (sy[k] & 0xFFFFu) == 0, need_v = c[k] == 0 || (sy[k] >> 16) == 0;
+        if (o + need_u + need_v > n_ld) {
+            atomicCAS(status, 0, kStatusCorrupt);
+        } else {
+            if (need_u) rr.x = ld[o++];
+            if (need_v) rr.y = ld[o++];
+        }
+        raw[v] = rr;
+        dcs[v] = make_int2((int)c[k], (int)sy[k]);
+    }
+}
+
+// Raster [T][H][W] -> strip-diagonal [T][strip][W + 31][32] (step k of a
+// strip, lane l = row 32s + l at column k - l), zero where no vertex sits.
+// A block moves 32 steps of one strip: it reads the 32 row segments those
+// steps touch (row l: columns k0 - l .. k0 + 31 - l) and writes 32 whole
+// 256-byte step lines of each array.
+constexpr int kDiagSteps = 32;
+__global__ void __launch_bounds__(256) diag_transpose_kernel(const int2* __restrict__ a_in,
+                                                             const int2* __restrict__ b_in, int H, int W, int T,
+                                                             int2* __restrict__ a_out, int2* __restrict__ b_out) {
+    __shared__ int2 sa[32][kDiagSteps + 1], sb[32][kDiagSteps + 1];  // [lane][step in the block]
+    const int nstrips = (H + 31) >> 5, nsteps = W + 31;
+    const int nkb = (nsteps + kDiagSteps - 1) / kDiagSteps;
+    const long long nb = (long long)T * nstrips * nkb;
+    const int lane = (int)(threadIdx.x & 31u), w = (int)(threadIdx.x >> 5);
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int kb = (int)(b % nkb);
+        const long long ts = b / nkb;
+        const int s = (int)(ts % nstrips), t = (int)(ts / nstrips);
+        const int k0 = kb * kDiagSteps;
+        // row l of the strip, columns k0 - l + m (m = lane): coalesced reads
+        for (int l = w; l < 32; l += 8) {
+            const int i = 32 * s + l, j = k0 - l + lane;
+            const bool ok = i < H && j >= 0 && j < W;
+            const size_t v = ((size_t)t * H + (ok ? i : 0)) * W + (ok ? j : 0);
+            sa[l][lane] = ok ? __ldg(a_in + v) : make_int2(0, 0);
+            sb[l][lane] = ok ? __ldg(b_in + v) : make_int2(0, 0);
+        }
+        __syncthreads();
+        // step k0 + m: lane l's element is (row l, column k0 + m - l) = s?[l][m]
+        for (int m = w; m < kDiagSteps; m += 8) {
+            const int k = k0 + m;
+            if (k >= nsteps) break;
+            const size_t d = (((size_t)t * nstrips + s) * (size_t)nsteps + k) * 32 + lane;
+            a_out[d] = sa[lane][m];
+            b_out[d] = sb[lane][m];
+        }
+        __syncthreads();
+    }
 }
 
 // Block modes (one byte each, nonzero = SL) as bits, least significant bit
@@ -330,6 +491,29 @@ void launch_tile_scatter(const uint8_t* qxi, const uint32_t* sym, const int32_t*
     (void)attr;
     tile_scatter_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, kScatterSmem, s>>>(
         qxi, sym, reinterpret_cast<const int2*>(q), tile_off, N, qd_out, ld_out);
+}
+
+void launch_dec_tile_qd(const uint8_t* qxi, size_t N, unsigned long long* tile_cnt, int* status, cudaStream_t s) {
+    if (N) dec_tile_qd_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(qxi, N, tile_cnt, status);
+}
+void launch_dec_tile_sym(const uint8_t* qxi, size_t N, const uint16_t* qd, size_t n_qd,
+                         const unsigned long long* qd_off, uint32_t* sym, unsigned long long* tile_ld, int* status,
+                         cudaStream_t s) {
+    if (N)
+        dec_tile_sym_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(qxi, N, qd, n_qd, qd_off, sym, tile_ld,
+                                                                              status);
+}
+void launch_dec_tile_raw(const uint8_t* qxi, const uint32_t* sym, size_t N, const int32_t* ld, size_t n_ld,
+                         const unsigned long long* ld_off, int2* dcs, int2* raw, int* status, cudaStream_t s) {
+    if (N)
+        dec_tile_raw_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(qxi, sym, N, ld, n_ld, ld_off, dcs, raw,
+                                                                              status);
+}
+void launch_diag_transpose(const int2* a_in, const int2* b_in, int H, int W, int T, int2* a_out, int2* b_out,
+                           cudaStream_t s) {
+    const long long nb = (long long)T * ((H + 31) / 32) * ((W + 31 + kDiagSteps - 1) / kDiagSteps);
+    if (nb) diag_transpose_kernel<<<(unsigned)std::min<long long>(nb, 152 * 16), 256, 0, s>>>(a_in, b_in, H, W, T,
+                                                                                              a_out, b_out);
 }
 
 void launch_pack_bits(const uint8_t* in, size_t n, uint8_t* out, cudaStream_t s) {
