@@ -1047,7 +1047,8 @@ static std::vector<PipeTuning> tuning_candidates(int pred) {
         c.push_back({45, 8, 0, 0, 3, 0});
         for (int u : {8, 16})
             for (int share : {25, 35, 45, 55, 65}) c.push_back({share, u, 0, 0, 0, 0});
-        for (int share : {35, 45, 55}) c.push_back({share, 8, 0, 0, 0, 8});
+        for (int share : {35, 45, 55})
+            for (int cap : {4, 8}) c.push_back({share, 8, 0, 0, 0, cap});
     } else if (pred == CPT_PRED_LEARNED) {
         for (int share : {65, 75, 85}) c.push_back({share, 0, 0, 0, 0, 0});
     } else if (pred == CPT_PRED_LEARNED_MOP) {
@@ -1055,7 +1056,8 @@ static std::vector<PipeTuning> tuning_candidates(int pred) {
     } else {
         c.push_back({45, 0, 0, 64, 3, 0});
         for (int share : {25, 35, 45, 55, 65, 75}) c.push_back({share, 0, 0, 64, 0, 0});
-        for (int share : {35, 45, 55, 65}) c.push_back({share, 0, 0, 64, 0, 8});
+        for (int share : {35, 45, 55, 65})
+            for (int cap : {4, 6, 8}) c.push_back({share, 0, 0, 64, 0, cap});
         c.push_back({45, 0, 0, 128, 0, 0});
     }
     return c;

@@ -1036,17 +1036,18 @@ __device__ bool wave_item(const SliceArgs& a, int t, int s, Sm& sm) {
     auto step = [&](int k, Pf& f) -> bool {
         const int j = k - lane;
         const bool col = j >= 0 && j < W;
-        // this step's words (issued two steps ago)
-        if (!poll_word(a, Pm + (size_t)(rowok ? i : 0) * W + (col ? j : 0), has_prev && rowok && col, f.wp))
-            return false;
-        if (!poll_word(a, Pm + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0),
-                       lane == 0 && has_above && has_prev && col, f.wa))
-            return false;
-        if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), lane == 0 && has_above && col, f.wu))
-            return false;
-        // the SL prediction, once its unit has written it
-        if (!poll_word(a, Psl + (size_t)(rowok ? i : 0) * W + (col ? j : 0), need_sl && rowok && col, f.wn))
-            return false;
+        // this step's words (issued two steps ago) and the SL prediction,
+        // once its unit has written it: one vote when all are present
+        const bool np = has_prev && rowok && col, na = lane == 0 && has_above && has_prev && col;
+        const bool nu = lane == 0 && has_above && col, nn = need_sl && rowok && col;
+        const bool present = (!np || word_ready(f.wp)) && (!na || word_ready(f.wa)) && (!nu || word_ready(f.wu)) &&
+                             (!nn || word_ready(f.wn));
+        if (!__all_sync(FULL, present)) {
+            if (!poll_word(a, Pm + (size_t)(rowok ? i : 0) * W + (col ? j : 0), np, f.wp)) return false;
+            if (!poll_word(a, Pm + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), na, f.wa)) return false;
+            if (!poll_word(a, Pc + (size_t)(i0 > 0 ? i0 - 1 : 0) * W + (col ? j : 0), nu, f.wu)) return false;
+            if (!poll_word(a, Psl + (size_t)(rowok ? i : 0) * W + (col ? j : 0), nn, f.wn)) return false;
+        }
         const int2 pk = (has_prev && rowok && col) ? word_value(f.wp) : z;
         const int2 ak = (lane == 0 && has_above && has_prev && col) ? word_value(f.wa) : z;
         const int2 uk = (lane == 0 && has_above && col) ? word_value(f.wu) : z;
