@@ -2442,13 +2442,17 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(cudaStreamSynchronize(s));  // (the host order table outlives its copy)
     if (status == (int)CPT_ERR_TIMEOUT) return fail(CPT_ERR_TIMEOUT, "decoder wavefront wait timed out");
     if (status != 0) return fail(CPT_ERR_CORRUPT, "corrupt stream");
-    launch_untag(d_qhat, N, s);
-    if (qhat_out) CPT_CUDA(cudaMemcpyAsync(qhat_out, d_qhat, N * 8, cudaMemcpyDeviceToHost, s));
+    // the reconstruction words lose their tag in place only when the integers
+    // are asked for; the float conversion removes it on the fly
+    if (qhat_out) {
+        launch_untag(d_qhat, N, s);
+        CPT_CUDA(cudaMemcpyAsync(qhat_out, d_qhat, N * 8, cudaMemcpyDeviceToHost, s));
+    }
     if (uv_out) {
         const bool dev = is_device_pointer(uv_out) && !(reinterpret_cast<uintptr_t>(uv_out) & 7u);
         float* dst = uv_out;
         if (!dev) CPT_CUDA(ar.alloc(&dst, 2 * N));
-        launch_to_float(d_qhat, N, k, dst, s);
+        launch_to_float(d_qhat, N, k, dst, s, !qhat_out);
         if (!dev) CPT_CUDA(cudaMemcpyAsync(uv_out, dst, N * 8, cudaMemcpyDefault, s));
     }
     CPT_CUDA(cudaStreamSynchronize(s));

@@ -183,7 +183,8 @@ void launch_encode_u16(const uint16_t* x, size_t n, const uint32_t* table, const
 void launch_huff_decode_u8(const HuffDecode& h, uint8_t* out, int* status, cudaStream_t s);
 void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cudaStream_t s);
 void launch_untag(int2* qhat, size_t N, cudaStream_t s);  // reconstruction words -> values
-void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s);  // q_hat 2^-k
+// q_hat 2^-k; tagged: the words still carry the reconstruction tag
+void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s, bool tagged = false);
 
 // k_traj.cu
 void launch_iota(unsigned* x, size_t n, cudaStream_t s);

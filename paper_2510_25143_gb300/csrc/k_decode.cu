@@ -112,11 +112,14 @@ __global__ void __launch_bounds__(256) untag_kernel(int2* __restrict__ q, size_t
 
 // q_hat * 2^-k in float32: q_hat is exact in float (|q_hat| <= 2^24) and the
 // power of two is applied as two factors 2^a 2^b (a + b = -k) that never
-// leave the normal range on the way, so every product is exact
+// leave the normal range on the way, so every product is exact.  tag: the
+// y halves still carry the reconstruction words' tag (removed here).
 __global__ void __launch_bounds__(256) to_float_kernel(const int4* __restrict__ qhat, size_t N2, float g1, float g2,
-                                                       float4* __restrict__ out) {
+                                                       int tag, float4* __restrict__ out) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N2; v += (size_t)gridDim.x * blockDim.x) {
-        const int4 q = __ldcs(qhat + v);
+        int4 q = __ldcs(qhat + v);
+        q.y ^= tag;
+        q.w ^= tag;
         out[v] = make_float4(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
                              __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2),
                              __fmul_rn(__fmul_rn(__int2float_rn(q.z), g1), g2),
@@ -124,15 +127,18 @@ __global__ void __launch_bounds__(256) to_float_kernel(const int4* __restrict__ 
     }
 }
 __global__ void __launch_bounds__(256) to_float_v_kernel(const int2* __restrict__ qhat, size_t N, float g1, float g2,
-                                                          float2* __restrict__ out) {
+                                                          int tag, float2* __restrict__ out) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
-        const int2 q = qhat[v];
+        int2 q = qhat[v];
+        q.y ^= tag;
         out[v] = make_float2(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
                              __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2));
     }
 }
-__global__ void to_float_tail_kernel(const int2* __restrict__ qhat, float g1, float g2, float2* __restrict__ out) {
-    const int2 q = qhat[0];
+__global__ void to_float_tail_kernel(const int2* __restrict__ qhat, float g1, float g2, int tag,
+                                     float2* __restrict__ out) {
+    int2 q = qhat[0];
+    q.y ^= tag;
     out[0] = make_float2(__fmul_rn(__fmul_rn(__int2float_rn(q.x), g1), g2),
                          __fmul_rn(__fmul_rn(__int2float_rn(q.y), g1), g2));
 }
@@ -149,17 +155,19 @@ void launch_huff_decode_u16(const HuffDecode& h, uint16_t* out, int* status, cud
     if (nchunks) huff_decode_kernel<uint16_t><<<(unsigned)((nchunks + 63) / 64), 64, 0, s>>>(h, out, status);
 }
 void launch_untag(int2* qhat, size_t N, cudaStream_t s) { untag_kernel<<<1216, 256, 0, s>>>(qhat, N); }
-void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s) {
+void launch_to_float(const int2* qhat, size_t N, int k, float* out, cudaStream_t s, bool tagged) {
+    const int tag = tagged ? kQhatTag : 0;
     const int a = -k / 2, b = -k - a;
     const float g1 = std::ldexp(1.0f, a), g2 = std::ldexp(1.0f, b);
     // two vertices per thread (16-byte accesses when out is 16-byte aligned)
     if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
         if (N / 2)
-            to_float_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const int4*>(qhat), N / 2, g1, g2,
+            to_float_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const int4*>(qhat), N / 2, g1, g2, tag,
                                                  reinterpret_cast<float4*>(out));
-        if (N & 1) to_float_tail_kernel<<<1, 1, 0, s>>>(qhat + N - 1, g1, g2, reinterpret_cast<float2*>(out) + N - 1);
+        if (N & 1)
+            to_float_tail_kernel<<<1, 1, 0, s>>>(qhat + N - 1, g1, g2, tag, reinterpret_cast<float2*>(out) + N - 1);
     } else {  // output only 8-byte aligned: one vertex per thread
-        to_float_v_kernel<<<1216, 256, 0, s>>>(qhat, N, g1, g2, reinterpret_cast<float2*>(out));
+        to_float_v_kernel<<<1216, 256, 0, s>>>(qhat, N, g1, g2, tag, reinterpret_cast<float2*>(out));
     }
 }
 

@@ -384,15 +384,22 @@ __global__ void __launch_bounds__(kCmpThreads) dec_tile_sym_kernel(const uint8_t
     if (threadIdx.x == 0) tile_ld[blockIdx.x] = tot;
 }
 
-// the vertices' (bound code, symbols) and verbatim values in raster order
+// the vertices' (bound code, symbols) and verbatim values in raster order,
+// gathered in shared memory and written out with consecutive addresses (a
+// thread's own 16 vertices would scatter the stores across the warp)
+constexpr size_t kRawSmem = (size_t)kCmpTile * 2 * sizeof(int2);
 __global__ void __launch_bounds__(kCmpThreads) dec_tile_raw_kernel(const uint8_t* __restrict__ qxi,
                                                                    const uint32_t* __restrict__ sym, size_t N,
                                                                    const int32_t* __restrict__ ld, size_t n_ld,
                                                                    const unsigned long long* __restrict__ ld_off,
                                                                    int2* __restrict__ dcs, int2* __restrict__ raw,
                                                                    int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    int2* sdcs = reinterpret_cast<int2*>(sm_raw);  // [kCmpTile]
+    int2* sraw = sdcs + kCmpTile;
     __shared__ unsigned long long wt[32], tot;
-    const size_t base = (size_t)blockIdx.x * kCmpTile + (size_t)threadIdx.x * kCmpPer;
+    const size_t tile0 = (size_t)blockIdx.x * kCmpTile;
+    const size_t base = tile0 + (size_t)threadIdx.x * kCmpPer;
     unsigned char c[kCmpPer];
     uint32_t sy[kCmpPer];
     load16(qxi, sym, N, base, c, sy);
@@ -413,8 +420,14 @@ __global__ void __launch_bounds__(kCmpThreads) dec_tile_raw_kernel(const uint8_t
             if (need_u) rr.x = ld[o++];
             if (need_v) rr.y = ld[o++];
         }
-        raw[v] = rr;
-        dcs[v] = make_int2((int)c[k], (int)sy[k]);
+        sraw[v - tile0] = rr;
+        sdcs[v - tile0] = make_int2((int)c[k], (int)sy[k]);
+    }
+    __syncthreads();
+    const size_t nt = min((size_t)kCmpTile, N - tile0);
+    for (size_t x = threadIdx.x; x < nt; x += kCmpThreads) {
+        dcs[tile0 + x] = sdcs[x];
+        raw[tile0 + x] = sraw[x];
     }
 }
 
@@ -505,9 +518,14 @@ void launch_dec_tile_sym(const uint8_t* qxi, size_t N, const uint16_t* qd, size_
 }
 void launch_dec_tile_raw(const uint8_t* qxi, const uint32_t* sym, size_t N, const int32_t* ld, size_t n_ld,
                          const unsigned long long* ld_off, int2* dcs, int2* raw, int* status, cudaStream_t s) {
-    if (N)
-        dec_tile_raw_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, 0, s>>>(qxi, sym, N, ld, n_ld, ld_off, dcs, raw,
-                                                                              status);
+    if (!N) return;
+    // the gather buffers are above the default 48 KB of shared memory (set
+    // once; if that failed, so does the launch, and the caller reads the error)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(dec_tile_raw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRawSmem);
+    (void)attr;
+    dec_tile_raw_kernel<<<(unsigned)compact_tiles(N), kCmpThreads, kRawSmem, s>>>(qxi, sym, N, ld, n_ld, ld_off, dcs,
+                                                                                raw, status);
 }
 void launch_diag_transpose(const int2* a_in, const int2* b_in, int H, int W, int T, int2* a_out, int2* b_out,
                            cudaStream_t s) {
