@@ -212,6 +212,16 @@ def test_decompress_rejects_malformed_streams():
     with pytest.raises(cpt.CptError) as e:
         cpt.decompress(bytes(b))
     assert e.value.status == cpt.ERR_CORRUPT
+    # a verbatim-value count (header offset 80) that disagrees with the codes,
+    # with the section resized to match, is caught after the tiled expansion
+    n_ld = int.from_bytes(blob[80:88], "little")
+    for delta in (-2, 2):
+        b = bytearray(blob)
+        b[80:88] = (n_ld + delta).to_bytes(8, "little")
+        b = b[:len(blob) - 8] if delta < 0 else b + bytes(8)
+        with pytest.raises(cpt.CptError) as e:
+            cpt.decompress(bytes(b))
+        assert e.value.status == cpt.ERR_CORRUPT
 
 
 def test_oracle_stream_decodes_on_gpu():
