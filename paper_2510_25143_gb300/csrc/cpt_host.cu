@@ -304,6 +304,23 @@ struct EventHolder {
     cudaEvent_t ev = nullptr;
 };
 
+// The decoder's second stream and its fork/join events, one set per host
+// thread (created on first use, kept for the thread's lifetime).
+struct DecodeSide {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool ready() {
+        if (!s2 && cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) s2 = nullptr;
+        if (!ev_fork && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) ev_fork = nullptr;
+        if (!ev_join && cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) ev_join = nullptr;
+        if (!s2 || !ev_fork || !ev_join) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+};
+
 // One Huffman stream: host-side code book and the device buffers of its
 // tile offsets and words.
 struct StreamPlan {
@@ -2192,44 +2209,54 @@ static bool parse_huff(Reader& r, uint32_t alphabet, HuffHost& h) {
     return true;
 }
 
-template <typename Sym>
-static cpt_status decode_huff_stream(const HuffHost& hh, Sym* d_out, int* d_status, DevArena& ar, cudaStream_t s) {
+// One Huffman stream's device buffers (from the arena, on the call's stream).
+struct HuffBufs {
+    uint32_t *words = nullptr, *tab = nullptr;
+    unsigned long long *off = nullptr, *lut3 = nullptr;
+    size_t ntab = 0;
+};
+static cpt_status huff_alloc(const HuffHost& hh, DevArena& ar, HuffBufs& b) {
     if (hh.nsym == 0) return CPT_OK;
-    uint32_t *d_words, *d_tab;
-    unsigned long long* d_off;
-    CPT_CUDA(ar.alloc(&d_words, hh.nwords + 2));
-    CPT_CUDA(cudaMemsetAsync(d_words, 0, 4 * (hh.nwords + 2), s));
-    if (hh.nwords) CPT_CUDA(cudaMemcpyAsync(d_words, hh.words, 4 * hh.nwords, cudaMemcpyHostToDevice, s));
-    CPT_CUDA(ar.alloc(&d_off, hh.chunk_off.size()));
-    CPT_CUDA(cudaMemcpyAsync(d_off, hh.chunk_off.data(), 8 * hh.chunk_off.size(), cudaMemcpyHostToDevice, s));
-    unsigned long long* d_lut3;
-    CPT_CUDA(ar.alloc(&d_lut3, 4096));
-    CPT_CUDA(cudaMemcpyAsync(d_lut3, hh.lut3.data(), 8 * 4096, cudaMemcpyHostToDevice, s));
-    const size_t ntab = 4096 + 3 * 25 + hh.sorted.size();
+    b.ntab = 4096 + 3 * 25 + hh.sorted.size();
+    CPT_CUDA(ar.alloc(&b.words, hh.nwords + 2));
+    CPT_CUDA(ar.alloc(&b.off, hh.chunk_off.size()));
+    CPT_CUDA(ar.alloc(&b.lut3, 4096));
+    CPT_CUDA(ar.alloc(&b.tab, b.ntab));
+    return CPT_OK;
+}
+
+// Uploads one Huffman stream into its buffers and decodes it on stream s
+// (the copies come from pageable host memory, staged by the driver before
+// each call returns, so `tab` may go after the launch).
+template <typename Sym>
+static cpt_status decode_huff_stream(const HuffHost& hh, const HuffBufs& b, Sym* d_out, int* d_status,
+                                     cudaStream_t s) {
+    if (hh.nsym == 0) return CPT_OK;
+    CPT_CUDA(cudaMemsetAsync(b.words, 0, 4 * (hh.nwords + 2), s));
+    if (hh.nwords) CPT_CUDA(cudaMemcpyAsync(b.words, hh.words, 4 * hh.nwords, cudaMemcpyHostToDevice, s));
+    CPT_CUDA(cudaMemcpyAsync(b.off, hh.chunk_off.data(), 8 * hh.chunk_off.size(), cudaMemcpyHostToDevice, s));
+    CPT_CUDA(cudaMemcpyAsync(b.lut3, hh.lut3.data(), 8 * 4096, cudaMemcpyHostToDevice, s));
     std::vector<uint32_t> tab;
-    tab.reserve(ntab);
+    tab.reserve(b.ntab);
     tab.insert(tab.end(), hh.lut.begin(), hh.lut.end());
     tab.insert(tab.end(), hh.first.begin(), hh.first.end());
     tab.insert(tab.end(), hh.count.begin(), hh.count.end());
     tab.insert(tab.end(), hh.base.begin(), hh.base.end());
     tab.insert(tab.end(), hh.sorted.begin(), hh.sorted.end());
-    CPT_CUDA(ar.alloc(&d_tab, ntab));
-    CPT_CUDA(cudaMemcpyAsync(d_tab, tab.data(), 4 * ntab, cudaMemcpyHostToDevice, s));
+    CPT_CUDA(cudaMemcpyAsync(b.tab, tab.data(), 4 * b.ntab, cudaMemcpyHostToDevice, s));
     HuffDecode h;
-    h.words = d_words;
+    h.words = b.words;
     h.nwords = hh.nwords;
     h.nsym = hh.nsym;
-    h.chunk_off = d_off;
-    h.lut = d_tab;
-    h.first = d_tab + 4096;
-    h.count = d_tab + 4096 + 25;
-    h.base = d_tab + 4096 + 50;
-    h.sorted = d_tab + 4096 + 75;
-    h.lut3 = d_lut3;
+    h.chunk_off = b.off;
+    h.lut = b.tab;
+    h.first = b.tab + 4096;
+    h.count = b.tab + 4096 + 25;
+    h.base = b.tab + 4096 + 50;
+    h.sorted = b.tab + 4096 + 75;
+    h.lut3 = b.lut3;
     if constexpr (sizeof(Sym) == 1) launch_huff_decode_u8(h, reinterpret_cast<uint8_t*>(d_out), d_status, s);
     else launch_huff_decode_u16(h, reinterpret_cast<uint16_t*>(d_out), d_status, s);
-    // the host copies of words/tables must outlive the asynchronous copies
-    CPT_CUDA(cudaStreamSynchronize(s));
     return CPT_OK;
 }
 
@@ -2329,8 +2356,24 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(ar.alloc(&d_modes, std::max<size_t>(mode_bytes, 1)));
     if (mode_bytes) CPT_CUDA(cudaMemcpyAsync(d_modes, modes, mode_bytes, cudaMemcpyHostToDevice, s));
     if (n_ld) CPT_CUDA(cudaMemcpyAsync(d_ld, ldp, 4 * n_ld, cudaMemcpyHostToDevice, s));
-    cpt_status rc = decode_huff_stream<uint8_t>(hx, d_qxi, d_status, ar, s);
+    // the two Huffman streams decode at once: Q_xi on the call's stream, Q_d
+    // on a second one, joined before the residual symbols are used
+    static thread_local DecodeSide t_side;
+    if (!t_side.ready()) return fail(CPT_ERR_CUDA, "stream or event creation failed");
+    HuffBufs bx, bd;
+    cpt_status rc = huff_alloc(hx, ar, bx);
     if (rc != CPT_OK) return rc;
+    rc = huff_alloc(hd, ar, bd);
+    if (rc != CPT_OK) return rc;
+    CPT_CUDA(cudaEventRecord(t_side.ev_fork, s));  // every buffer above exists for the second stream
+    CPT_CUDA(cudaStreamWaitEvent(t_side.s2, t_side.ev_fork, 0));
+    rc = decode_huff_stream<uint8_t>(hx, bx, d_qxi, d_status, s);
+    if (rc == CPT_OK) rc = decode_huff_stream<uint16_t>(hd, bd, d_qd, d_status, t_side.s2);
+    CPT_CUDA(cudaEventRecord(t_side.ev_join, t_side.s2));
+    if (rc != CPT_OK) {
+        cudaStreamWaitEvent(s, t_side.ev_join, 0);  // nothing of the call outlives s
+        return rc;
+    }
     // residual symbols per tile of the bound codes; their total must be the
     // length of the Q_d stream
     unsigned long long total = 0;
@@ -2338,12 +2381,11 @@ static cpt_status decompress_impl(const uint8_t* in, size_t in_bytes, float* uv_
     CPT_CUDA(cudaMemsetAsync(d_qoff + nt, 0, sizeof(unsigned long long), s));
     launch_dec_tile_qd(d_qxi, N, d_qoff, d_status, s);
     launch_exclusive_scan_u64(d_qoff, nt + 1, d_tmp, s);
+    CPT_CUDA(cudaStreamWaitEvent(s, t_side.ev_join, 0));  // the Q_d symbols (and nothing of the call outlives s)
     CPT_CUDA(cudaMemcpyAsync(&total, d_qoff + nt, 8, cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CPT_CUDA(cudaStreamSynchronize(s));
     if (status != 0 || total != hd.nsym) return fail(CPT_ERR_CORRUPT, "bound codes do not match the residuals");
-    rc = decode_huff_stream<uint16_t>(hd, d_qd, d_status, ar, s);
-    if (rc != CPT_OK) return rc;
     // each vertex's symbols, the verbatim values per tile, then the values;
     // (bound code, symbols) go to d_qhat and the values to d_rraw in raster
     // order, from where the transposing copy lays both out strip-diagonally

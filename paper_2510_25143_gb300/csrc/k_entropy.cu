@@ -284,9 +284,6 @@ __global__ void __launch_bounds__(512) hist_u16_kernel(const uint16_t* __restric
         if (h[k]) atomicAdd(&hist[lo + k], h[k]);
 }
 
-// per-vertex counts (the decoder's layout of the verbatim values needs each
-// vertex's offset)
-
 
 // ---------------------------------------------------------------------------
 // Decoder: expansion of Q_xi, Q_d and L_d to the vertices, the inverse of the
