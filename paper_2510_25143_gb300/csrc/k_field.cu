@@ -128,13 +128,13 @@ struct RowVals {
     int2 v0, v1;
 };
 
-template <bool kVec, bool kTag>
+template <bool kVec, bool kTag, bool kIn = false>
 __device__ __forceinline__ RowVals load_row(const int2* __restrict__ q, size_t row_base, int c0, int W, bool ok) {
     RowVals r;
     r.v0 = r.v1 = make_int2(0, 0);
     if (ok) {
         if (kVec) {
-            if (c0 < W) {
+            if (kIn || c0 < W) {
                 const int4 x = __ldg(reinterpret_cast<const int4*>(q + row_base + c0));
                 r.v0 = make_int2(x.x, x.y);
                 r.v1 = make_int2(x.z, x.w);
@@ -241,48 +241,94 @@ __device__ __forceinline__ void orig_row(const uint16_t* __restrict__ mask_in, c
 }
 
 // The warp's deferred vertices: the 2 x 2 x 2 cube shares no strict sign.
-// Entries (row - ib) << 6 | (column - j0); every owned vertex of an item fits.
-constexpr int kQueueCap = kFaceRows * kStrip;
+// Entries (row - ib) << 6 | (column - j0).  Interior items queue them in
+// kQueueCap entries, worked off before a row (at most kStrip entries) could
+// overflow it; the others in the warp's ring storage, which holds every
+// owned vertex of an item.
+constexpr int kQueueCap = 512;
+
+// The exact test of the queued vertices, one per lane, their corners read
+// again (from L2).  Returns (crossed faces, 0) for the masks and (slice,
+// slab mismatches) for the verification.
+template <bool kVerify>
+__device__ __forceinline__ uint2 face_exact(const int2* __restrict__ q, int H, int W, int T, int t, int ib, int j0,
+                                         uint16_t* __restrict__ mask_out, const uint16_t* __restrict__ mask_in,
+                                         const uint16_t* __restrict__ queue, int nq) {
+    const int lane = threadIdx.x & 31;
+    const size_t base = (size_t)t * H * W;
+    uint2 r = make_uint2(0u, 0u);
+    __syncwarp();
+    for (int k = lane; k < nq; k += 32) {
+        const unsigned e = queue[k];
+        const int i = ib + (int)(e >> 6), j = j0 + (int)(e & 63u);
+        int2 c[8];
+        unsigned w[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) c[n] = corner<kVerify>(q, H, W, T, t + (n >> 2), i + ((n >> 1) & 1), j + (n & 1), w[n]);
+        const unsigned m = exact_mask(c, w, owned_valid(H, W, T, t, i, j));
+        const size_t v = base + (size_t)i * W + j;
+        if (kVerify) {
+            const unsigned x = m ^ (unsigned)mask_in[v];
+            r.x += __popc(x & 3u);
+            r.y += __popc(x & 0xffcu);
+        } else {
+            mask_out[v] = (uint16_t)m;
+            r.x += __popc(m);
+        }
+    }
+    __syncwarp();
+    return r;
+}
+
+__device__ __forceinline__ void add_exact(FaceAcc& acc, uint2 r, bool verify) {
+    if (verify) {
+        acc.ms += r.x;
+        acc.mb += r.y;
+    } else {
+        acc.crossed += r.x;
+    }
+}
 
 // One work item: rows [ib, ib + kFaceRows) of slice t, columns [j0, j0 + 62).
 // The rows are streamed with the sign filter only; vertices that pass it
-// are queued and get the exact test afterwards, one per lane, their corners
-// read again (from L2).
-template <bool kVerify, bool kVec>
-__device__ __forceinline__ void face_item_rows(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
+// are queued for face_exact.  It returns the updated accumulators.  kInner:
+// rows ib .. ib + kFaceRows, the lanes' columns and slice t + 1 all lie in
+// the field, so every validity test folds away.
+template <bool kVerify, bool kVec, bool kInner = false>
+__device__ __forceinline__ FaceAcc face_item_rows(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
                                                int j0, uint16_t* __restrict__ mask_out,
                                                const uint16_t* __restrict__ mask_in,
-                                               const float2* __restrict__ uv, float g1, float g2, FaceAcc& acc,
+                                               const float2* __restrict__ uv, float g1, float g2, FaceAcc acc,
                                                uint16_t* __restrict__ queue) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int c0 = j0 + 2 * lane, c1 = c0 + 1;
-    const bool in0 = c0 < W, in1 = c1 < W;             // columns inside the field
+    const bool in0 = kInner || c0 < W, in1 = kInner || c1 < W;  // columns inside the field
     const bool own0 = in0 && lane < 31, own1 = in1 && lane < 31;
-    const bool nx = t + 1 < T;
+    const bool nx = kInner || t + 1 < T;
     const size_t sl = (size_t)H * W, base = (size_t)t * sl;
-    const int ie = min(H, ib + kFaceRows);
+    const int ie = kInner ? ib + kFaceRows : min(H, ib + kFaceRows);
     int nq = 0;
     // rows i (A: slice t, P: slice t + 1) and i + 1 (D, Dp); rows i + 2 (N,
     // Np) are loaded one row step ahead, without their tag removed yet
-    const int re = min(H, ib + kFaceRows + 1);  // rows the item reads: [ib, re)
-    RowVals A = load_row<kVec, kVerify>(q, base + (size_t)ib * W, c0, W, true);
-    RowVals P = load_row<kVec, kVerify>(q, base + sl + (size_t)ib * W, c0, W, nx);
-    RowVals D = load_row<kVec, kVerify>(q, base + (size_t)(ib + 1) * W, c0, W, ib + 1 < H);
-    RowVals Dp = load_row<kVec, kVerify>(q, base + sl + (size_t)(ib + 1) * W, c0, W, nx && ib + 1 < H);
-    RowVals N = load_row<kVec, false>(q, base + (size_t)(ib + 2) * W, c0, W, ib + 2 < re);
-    RowVals Np = load_row<kVec, false>(q, base + sl + (size_t)(ib + 2) * W, c0, W, ib + 2 < re && nx);
+    const int re = kInner ? ib + kFaceRows + 1 : min(H, ib + kFaceRows + 1);  // rows the item reads: [ib, re)
+    RowVals A = load_row<kVec, kVerify, kInner>(q, base + (size_t)ib * W, c0, W, true);
+    RowVals P = load_row<kVec, kVerify, kInner>(q, base + sl + (size_t)ib * W, c0, W, nx);
+    RowVals D = load_row<kVec, kVerify, kInner>(q, base + (size_t)(ib + 1) * W, c0, W, kInner || ib + 1 < H);
+    RowVals Dp = load_row<kVec, kVerify, kInner>(q, base + sl + (size_t)(ib + 1) * W, c0, W, nx && (kInner || ib + 1 < H));
+    RowVals N = load_row<kVec, false, kInner>(q, base + (size_t)(ib + 2) * W, c0, W, ib + 2 < re);
+    RowVals Np = load_row<kVec, false, kInner>(q, base + sl + (size_t)(ib + 2) * W, c0, W, ib + 2 < re && nx);
     RowWords wa = row_words(A, true, in0, in1), wp = row_words(P, nx, in0, in1);
     unsigned col0 = wa.w0 & wp.w0, col1 = wa.w1 & wp.w1;
     unsigned omN = 0;
     float4 oxN = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kVerify) orig_row<kVec>(mask_in, uv, base + (size_t)ib * W, c0, own0, own1, omN, oxN);
     for (int i = ib; i < ie; ++i) {
-        const bool dn = i + 1 < H, n3 = i + 3 < re;
+        const bool dn = kInner || i + 1 < H, n3 = i + 3 < re;
         // prefetch row i + 3
-        const RowVals NN = load_row<kVec, false>(q, base + (size_t)(i + 3) * W, c0, W, n3);
-        const RowVals NNp = load_row<kVec, false>(q, base + sl + (size_t)(i + 3) * W, c0, W, n3 && nx);
+        const RowVals NN = load_row<kVec, false, kInner>(q, base + (size_t)(i + 3) * W, c0, W, n3);
+        const RowVals NNp = load_row<kVec, false, kInner>(q, base + sl + (size_t)(i + 3) * W, c0, W, n3 && nx);
         const size_t vrow = base + (size_t)i * W;
         // verification: the original masks and values of row i (loaded one
         // row ahead), and those of row i + 1 for the next iteration
@@ -343,28 +389,176 @@ __device__ __forceinline__ void face_item_rows(const int2* __restrict__ q, int H
         col0 = dcol0;
         col1 = dcol1;
     }
-    if (nq == 0) return;
-    __syncwarp();
-    // the exact test of the queued vertices, one per lane
-    for (int k = lane; k < nq; k += 32) {
-        const unsigned e = queue[k];
-        const int i = ib + (int)(e >> 6), j = j0 + (int)(e & 63u);
-        int2 c[8];
-        unsigned w[8];
+    if (nq) add_exact(acc, face_exact<kVerify>(q, H, W, T, t, ib, j0, mask_out, mask_in, queue, nq), kVerify);
+    return acc;
+}
+
+// The same out of line, beside the interior path (its registers are then its
+// own).
+template <bool kVerify, bool kVec>
+__device__ __noinline__ FaceAcc face_item_rows_call(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
+                                                    int j0, uint16_t* __restrict__ mask_out,
+                                                    const uint16_t* __restrict__ mask_in,
+                                                    const float2* __restrict__ uv, float g1, float g2, FaceAcc acc,
+                                                    uint16_t* __restrict__ queue) {
+    return face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, queue);
+}
+
+// The vertices of rows [i_from, ib + kFaceRows) of an interior item whose
+// cube shares no strict sign, tested one by one (corners from L2): the
+// interior path's fallback once its queue is full (rough fields).
+template <bool kVerify>
+__device__ __noinline__ uint2 face_rescan(const int2* __restrict__ q, int H, int W, int T, int t, int ib, int j0,
+                                          int i_from, uint16_t* __restrict__ mask_out,
+                                          const uint16_t* __restrict__ mask_in) {
+    const int lane = threadIdx.x & 31;
+    const size_t base = (size_t)t * H * W;
+    uint2 r = make_uint2(0u, 0u);
+    if (lane < 31) {
+        for (int i = i_from; i < ib + kFaceRows; ++i) {
+            for (int d = 0; d < 2; ++d) {
+                const int j = j0 + 2 * lane + d;
+                int2 c[8];
+                unsigned w[8];
 #pragma unroll
-        for (int n = 0; n < 8; ++n) c[n] = corner<kVerify>(q, H, W, T, t + (n >> 2), i + ((n >> 1) & 1), j + (n & 1), w[n]);
-        const unsigned m = exact_mask(c, w, owned_valid(H, W, T, t, i, j));
-        const size_t v = base + (size_t)i * W + j;
-        if (kVerify) {
-            const unsigned x = m ^ (unsigned)mask_in[v];
-            acc.ms += __popc(x & 3u);
-            acc.mb += __popc(x & 0xffcu);
-        } else {
-            mask_out[v] = (uint16_t)m;
-            acc.crossed += __popc(m);
+                for (int n = 0; n < 8; ++n)
+                    c[n] = corner<kVerify>(q, H, W, T, t + (n >> 2), i + ((n >> 1) & 1), j + (n & 1), w[n]);
+                const unsigned all = w[0] & w[1] & w[2] & w[3] & w[4] & w[5] & w[6] & w[7];
+                if (all & kSignBits) continue;  // handled by the row loop
+                const unsigned m = exact_mask(c, w, owned_valid(H, W, T, t, i, j));
+                const size_t v = base + (size_t)i * W + j;
+                if (kVerify) {
+                    const unsigned x = m ^ (unsigned)mask_in[v];
+                    r.x += __popc(x & 3u);
+                    r.y += __popc(x & 0xffcu);
+                } else {
+                    mask_out[v] = (uint16_t)m;
+                    r.x += __popc(m);
+                }
+            }
         }
     }
-    __syncwarp();
+    return r;
+}
+
+// Interior items (W even; rows ib .. ib + kFaceRows, columns j0 .. j0 + 63
+// and slice t + 1 inside the field): every corner exists, so the sign words
+// need no validity selects.  The rows of slices t and t + 1 stream through
+// a per-warp ring of kRing shared-memory stages filled by 16-byte async
+// copies, kRing rows ahead of the one in use; a lane reads back only what
+// its own copies wrote.
+constexpr int kRing = 4;
+struct FaceRing {
+    int4 r[kRing][2][32];  // [stage][slice t, t + 1][lane]
+};
+
+template <bool kVerify>
+__device__ __forceinline__ void face_item_inner(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
+                                                int j0, uint16_t* __restrict__ mask_out,
+                                                const uint16_t* __restrict__ mask_in,
+                                                const float2* __restrict__ uv, float g1, float g2, FaceAcc& acc,
+                                                uint16_t* __restrict__ queue, FaceRing& ring) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const bool own = lane < 31;
+    const int c0 = j0 + 2 * lane;
+    const size_t sl = (size_t)H * W, base = (size_t)t * sl;
+    const int2* src = q + base + (size_t)ib * W + c0;  // (t, ib, c0)
+#pragma unroll
+    for (int s = 0; s < kRing; ++s) {
+        cp_async16(&ring.r[s][0][lane], src + (size_t)s * W, true);
+        cp_async16(&ring.r[s][1][lane], src + sl + (size_t)s * W, true);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const int2* nxt = src + (size_t)kRing * W;  // the next row to fetch
+    int stage = 0, nq = 0, i_over = ib + kFaceRows;  // i_over: first row not queued
+    unsigned cw0 = 0, cw1 = 0;  // column words (slices t and t + 1) of the row above
+    int4 above = make_int4(0, 0, 0, 0);  // its slice-t values (verification)
+    unsigned omN = 0;
+    float4 oxN = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kVerify) orig_row<true>(mask_in, uv, base + (size_t)ib * W, c0, own, own, omN, oxN);
+    for (int r = 0; r <= kFaceRows; ++r) {
+        // row ib + r of both slices has landed once at most kRing - 1 newer
+        // copy groups are pending
+        asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");
+        int4 a = ring.r[stage][0][lane], p = ring.r[stage][1][lane];
+        if (kVerify) {
+            a.y ^= kQhatTag;
+            a.w ^= kQhatTag;
+            p.y ^= kQhatTag;
+            p.w ^= kQhatTag;
+        }
+        const unsigned w0 = sign_word(a.x, a.y) & sign_word(p.x, p.y);
+        const unsigned w1 = sign_word(a.z, a.w) & sign_word(p.z, p.w);
+        // the stage is refilled only after its values are in registers
+        asm volatile("" ::"r"(w0), "r"(w1), "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w));
+        if (r + kRing <= kFaceRows) {
+            cp_async16(&ring.r[stage][0][lane], nxt, true);
+            cp_async16(&ring.r[stage][1][lane], nxt + sl, true);
+            nxt += W;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        stage = stage + 1 == kRing ? 0 : stage + 1;
+        if (r > 0) {
+            // vertex row i = ib + r - 1: its cube is the row above and this one
+            const int i = ib + r - 1;
+            const size_t vrow = base + (size_t)i * W;
+            const unsigned om = omN;
+            const float4 ox = oxN;
+            if (kVerify && r < kFaceRows) orig_row<true>(mask_in, uv, vrow + W, c0, own, own, omN, oxN);
+            const unsigned vp0 = cw0 & w0, vp1 = cw1 & w1;
+            const unsigned right = __shfl_down_sync(FULL, vp0, 1);
+            const bool need0 = own && ((vp0 & vp1 & kSignBits) == 0u);
+            const bool need1 = own && ((vp1 & right & kSignBits) == 0u);
+            if (__any_sync(FULL, need0 || need1) && i_over > i) {
+                const unsigned b0 = __ballot_sync(FULL, need0), b1 = __ballot_sync(FULL, need1);
+                const int add = __popc(b0) + __popc(b1);
+                if (nq + add > kQueueCap) {
+                    i_over = i;  // this row and the rest: face_rescan
+                } else {
+                    int pos = nq + __popc(b0 & lt) + __popc(b1 & lt);
+                    const uint16_t e = (uint16_t)(((i - ib) << 6) | (2 * lane));
+                    if (need0) queue[pos++] = e;
+                    if (need1) queue[pos] = (uint16_t)(e + 1);
+                    nq += add;
+                }
+            }
+            if (kVerify) {
+                // a queued vertex is counted after its exact test
+                const unsigned x = om & ~((need0 ? 0x0000ffffu : 0u) | (need1 ? 0xffff0000u : 0u));
+                acc.ms += __popc(x & 0x00030003u);
+                acc.mb += __popc(x & 0x0ffc0ffcu);
+                if (own) {
+                    // x_hat = qhat * 2^-k, exact in FP32 (|qhat| < 2^24)
+                    const float ax = __fmul_rn(__fmul_rn(__int2float_rn(above.x), g1), g2);
+                    const float ay = __fmul_rn(__fmul_rn(__int2float_rn(above.y), g1), g2);
+                    const float bx = __fmul_rn(__fmul_rn(__int2float_rn(above.z), g1), g2);
+                    const float by = __fmul_rn(__fmul_rn(__int2float_rn(above.w), g1), g2);
+                    const ErrMax e0 = err_pair(ax, ox.x), e1 = err_pair(ay, ox.y);
+                    const ErrMax e2 = err_pair(bx, ox.z), e3 = err_pair(by, ox.w);
+                    acc.em = err_max(acc.em, err_max(err_max(e0, e1), err_max(e2, e3)));
+                    acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
+                    acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e2.s, e2.s), __fmul_rn(e3.s, e3.s)));
+                }
+            } else if (own) {
+                // a vertex that passes no test has every owned face uncrossed;
+                // a queued one is written by its exact test
+                if (!(need0 | need1))
+                    *reinterpret_cast<unsigned*>(mask_out + vrow + c0) = 0u;
+                else if (!need0)
+                    mask_out[vrow + c0] = 0;
+                else if (!need1)
+                    mask_out[vrow + c0 + 1] = 0;
+            }
+        }
+        cw0 = w0;
+        cw1 = w1;
+        above = a;
+    }
+    if (nq) add_exact(acc, face_exact<kVerify>(q, H, W, T, t, ib, j0, mask_out, mask_in, queue, nq), kVerify);
+    if (i_over < ib + kFaceRows)
+        add_exact(acc, face_rescan<kVerify>(q, H, W, T, t, ib, j0, i_over, mask_out, mask_in), kVerify);
 }
 
 struct FaceGrid {
@@ -393,6 +587,8 @@ __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q
     const long long per_t = (long long)g.nchunks * g.nstrips;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     __shared__ uint16_t s_queue[8][kQueueCap];
+    __shared__ FaceRing s_ring[8];
+    static_assert(sizeof(FaceRing) >= kFaceRows * kStrip * sizeof(uint16_t), "queue of a general item");
     FaceAcc acc{0ull, 0u, 0u, ErrMax{0.f, 0.f}, 0.f};
     for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < g.items;
          item += nwarps) {
@@ -401,8 +597,17 @@ __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q
         const int t = t_first + tr;
         const int ib = (int)(r / g.nstrips) * kFaceRows;
         const int j0 = (int)(r % g.nstrips) * kStrip;
-        face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
-                                      s_queue[threadIdx.x >> 5]);
+        uint16_t* const wq = reinterpret_cast<uint16_t*>(&s_ring[threadIdx.x >> 5]);
+        const bool inner = ib + kFaceRows < H && j0 + 64 <= W && t + 1 < T;
+        if (!kVerify && kVec && inner)
+            acc = face_item_rows<kVerify, kVec, true>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, wq);
+        else if (!kVerify || !kVec)
+            acc = face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, wq);
+        else if (inner)
+            face_item_inner<kVerify>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
+                                     s_queue[threadIdx.x >> 5], s_ring[threadIdx.x >> 5]);
+        else
+            acc = face_item_rows_call<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, wq);
     }
     // warp, then block reduction; one set of atomics per block
     __shared__ unsigned long long s_c[8];
