@@ -127,7 +127,7 @@ __device__ __forceinline__ void store_cls(int2* __restrict__ out, unsigned* __re
     qd[dv] = __ldg(q + v);
 }
 
-__global__ void __launch_bounds__(256, 3) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
+__global__ void __launch_bounds__(256, 4) classify_kernel(const int2* __restrict__ q, const uint16_t* __restrict__ mask,
                                                        int H, int W, int T, int eps_int, int2* __restrict__ out,
                                                        unsigned* __restrict__ out_m, int2* __restrict__ qd,
                                                        int t_first) {

@@ -136,3 +136,34 @@ def test_repair_after_a_failed_verification(case):
     assert s2["status"] == cpt.ERR_VERIFY
     b3, s3, _ = cpt.compress(d, eb, pred="mop", repair=True)
     assert s3["repair_rounds"] == 0 and b3 == r0["bytes"]
+
+
+def test_verification_counts_on_a_rough_field():
+    """On a field where most vertices take the exact face test (integers in
+    -2..2), the per-warp queue of the interior items fills and the rest of
+    such an item is tested vertex by vertex.  A corrupted reconstruction is
+    counted exactly there: slice and slab mismatches equal the popcounts of
+    the oracle's mask difference."""
+    import numpy as np
+    rng = np.random.default_rng(31)
+    uv = rng.integers(-2, 3, (3, 70, 130, 2)).astype(np.float32)
+    d = _dev(uv)
+    r0 = oracle.compress(uv, 0.4, eb_mode="abs", pred="lorenzo")
+    T, H, W, _ = uv.shape
+    for (t, i, j) in ((1, 55, 70), (0, 60, 100), (1, 20, 10)):
+        v = (t * H + i) * W + j
+        qv = int(r0["qhat"].reshape(-1, 2)[v, 0])
+        delta = -2 * qv if qv != 0 else 3
+        qh = r0["qhat"].copy()
+        qh.reshape(-1, 2)[v, 0] += delta
+        diff = (oracle.face_masks(qh) ^ r0["mask"]).astype(np.uint32)
+        bits = np.unpackbits(diff.view(np.uint8).reshape(-1, 4), axis=1, bitorder="little")
+        want_slice = int(bits[:, 0:2].sum())
+        want_slab = int(bits[:, 2:12].sum())
+        assert want_slice + want_slab > 0
+        cpt.inject_verify_fault(v, delta)
+        _, s, _ = cpt.compress(d, 0.4, eb_mode="abs", pred="lorenzo", check=False)
+        assert s["status"] == cpt.ERR_VERIFY
+        assert s["verify_mismatch_slice"] == want_slice and s["verify_mismatch_slab"] == want_slab
+    _, s, _ = cpt.compress(d, 0.4, eb_mode="abs", pred="lorenzo")
+    assert s["verify_mismatch_slice"] == 0 and s["verify_mismatch_slab"] == 0

@@ -97,6 +97,17 @@ def test_small_integer_fields_degenerate_sos(seed):
     compare(uv, 0.4, "mop", eb_mode="abs", block=4)
 
 
+@pytest.mark.parametrize("pred", ["lorenzo", "mop"])
+def test_rough_field_interior_items(pred):
+    """Integers in -2..2 on a field with interior work items: most vertices
+    need the exact face test, so the interior items' queues fill and the
+    rest of each item is tested vertex by vertex; masks, codes and bytes
+    stay identical to the oracle's."""
+    rng = np.random.default_rng(30)
+    uv = rng.integers(-2, 3, (3, 70, 130, 2)).astype(np.float32)
+    compare(uv, 0.4, pred, eb_mode="abs", block=8)
+
+
 @pytest.mark.parametrize("shift,noise", [(1.0, 0.0), (1.0, 2e-4), (0.0, 2e-4)])
 def test_mop_carried_and_static_patterns(shift, noise):
     """Fields on which the MoP choice is fixed by the predictors' exactness
