@@ -197,6 +197,17 @@ __device__ __forceinline__ ErrMax err_max(ErrMax a, ErrMax b) {
     return (b.s > a.s || (b.s == a.s && b.e > a.e)) ? b : a;
 }
 
+// One reconstructed component against the original: the largest exact
+// difference and the sum of squared differences (a statistic, fused).
+// Rounding is monotonic, so a rounded difference below the largest one's
+// comes from a smaller exact difference: the TwoSum runs only for the
+// others.
+__device__ __forceinline__ void err_acc(FaceAcc& acc, float xh, float x) {
+    const float s = __fsub_rn(xh, x);
+    if (fabsf(s) >= acc.em.s) acc.em = err_max(acc.em, err_pair(xh, x));
+    acc.sq = __fmaf_rn(s, s, acc.sq);
+}
+
 // A corner value for the exact test (zero and an all-signs word outside the
 // field; faces through such corners are not valid).
 template <bool kTag>
@@ -358,16 +369,14 @@ __device__ __forceinline__ FaceAcc face_item_rows(const int2* __restrict__ q, in
             if (own0) {
                 const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.v0.x), g1), g2);
                 const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.v0.y), g1), g2);
-                const ErrMax e0 = err_pair(a, ox.x), e1 = err_pair(b, ox.y);
-                acc.em = err_max(acc.em, err_max(e0, e1));
-                acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
+                err_acc(acc, a, ox.x);
+                err_acc(acc, b, ox.y);
             }
             if (own1) {
                 const float a = __fmul_rn(__fmul_rn(__int2float_rn(A.v1.x), g1), g2);
                 const float b = __fmul_rn(__fmul_rn(__int2float_rn(A.v1.y), g1), g2);
-                const ErrMax e0 = err_pair(a, ox.z), e1 = err_pair(b, ox.w);
-                acc.em = err_max(acc.em, err_max(e0, e1));
-                acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
+                err_acc(acc, a, ox.z);
+                err_acc(acc, b, ox.w);
             }
         } else {
             // every owned face of a vertex that passes no test is uncrossed
@@ -535,11 +544,10 @@ __device__ __forceinline__ void face_item_inner(const int2* __restrict__ q, int 
                     const float ay = __fmul_rn(__fmul_rn(__int2float_rn(above.y), g1), g2);
                     const float bx = __fmul_rn(__fmul_rn(__int2float_rn(above.z), g1), g2);
                     const float by = __fmul_rn(__fmul_rn(__int2float_rn(above.w), g1), g2);
-                    const ErrMax e0 = err_pair(ax, ox.x), e1 = err_pair(ay, ox.y);
-                    const ErrMax e2 = err_pair(bx, ox.z), e3 = err_pair(by, ox.w);
-                    acc.em = err_max(acc.em, err_max(err_max(e0, e1), err_max(e2, e3)));
-                    acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e0.s, e0.s), __fmul_rn(e1.s, e1.s)));
-                    acc.sq = __fadd_rn(acc.sq, __fadd_rn(__fmul_rn(e2.s, e2.s), __fmul_rn(e3.s, e3.s)));
+                    err_acc(acc, ax, ox.x);
+                    err_acc(acc, ay, ox.y);
+                    err_acc(acc, bx, ox.z);
+                    err_acc(acc, by, ox.w);
                 }
             } else if (own) {
                 // a vertex that passes no test has every owned face uncrossed;

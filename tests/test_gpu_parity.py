@@ -35,6 +35,10 @@ def compare(uv, eb, pred="lorenzo", eb_mode="rel", block=16, stride=2, dx=1.0, d
     assert blob == r["bytes"]
     assert st["verify_mismatch_slice"] == 0 and st["verify_mismatch_slab"] == 0
     assert st["linf"] <= st["eps"] or st["eps_int"] == 0
+    # the verification's L-inf error: the largest exact |x_hat - x|, rounded
+    # once to double (a double difference of two floats is that rounding)
+    err = np.abs(np.ldexp(r["qhat"].astype(np.float64), -r["stats"]["k"]) - np.asarray(uv, np.float64))
+    assert st["linf"] == (err.max() if err.size else 0.0)
     assert st["crossed_faces"] == r["stats"]["crossed_faces"]
     assert st["n_ld"] == r["stats"]["n_ld"] and st["n_qd"] == r["stats"]["n_qd"]
     return blob, st, g, r
