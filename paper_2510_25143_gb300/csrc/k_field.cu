@@ -456,12 +456,19 @@ __device__ __noinline__ uint2 face_rescan(const int2* __restrict__ q, int H, int
 // a per-warp ring of kRing shared-memory stages filled by 16-byte async
 // copies, kRing rows ahead of the one in use; a lane reads back only what
 // its own copies wrote.
+template <bool kOne>
+__device__ __forceinline__ float x_hat(int q, float g1, float g2) {
+    return kOne ? __fmul_rn(__int2float_rn(q), g1) : __fmul_rn(__fmul_rn(__int2float_rn(q), g1), g2);
+}
+
 constexpr int kRing = 4;
 struct FaceRing {
     int4 r[kRing][2][32];  // [stage][slice t, t + 1][lane]
 };
 
-template <bool kVerify>
+// kOne: 2^-k is a normal float (in g1, g2 = 1), so one multiply forms
+// x_hat = qhat * 2^-k with the same single rounding as the two-step product.
+template <bool kVerify, bool kOne = false>
 __device__ __forceinline__ void face_item_inner(const int2* __restrict__ q, int H, int W, int T, int t, int ib,
                                                 int j0, uint16_t* __restrict__ mask_out,
                                                 const uint16_t* __restrict__ mask_in,
@@ -540,10 +547,8 @@ __device__ __forceinline__ void face_item_inner(const int2* __restrict__ q, int 
                 acc.mb += __popc(x & 0x0ffc0ffcu);
                 if (own) {
                     // x_hat = qhat * 2^-k, exact in FP32 (|qhat| < 2^24)
-                    const float ax = __fmul_rn(__fmul_rn(__int2float_rn(above.x), g1), g2);
-                    const float ay = __fmul_rn(__fmul_rn(__int2float_rn(above.y), g1), g2);
-                    const float bx = __fmul_rn(__fmul_rn(__int2float_rn(above.z), g1), g2);
-                    const float by = __fmul_rn(__fmul_rn(__int2float_rn(above.w), g1), g2);
+                    const float ax = x_hat<kOne>(above.x, g1, g2), ay = x_hat<kOne>(above.y, g1, g2);
+                    const float bx = x_hat<kOne>(above.z, g1, g2), by = x_hat<kOne>(above.w, g1, g2);
                     err_acc(acc, ax, ox.x);
                     err_acc(acc, ay, ox.y);
                     err_acc(acc, bx, ox.z);
@@ -584,7 +589,7 @@ __host__ __device__ inline FaceGrid face_grid(int H, int W, int t_count) {
 
 // Work items run in slice order (then row chunk, then strip) over a grid of
 // warps, so that slice t + 1, read again as slice t, is still in L2.
-template <bool kVerify, bool kVec>
+template <bool kVerify, bool kVec, bool kOne = false>
 __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q, int H, int W, int T,
                                                    uint16_t* __restrict__ mask_out,
                                                    const uint16_t* __restrict__ mask_in,
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(256, 4) face_kernel(const int2* __restrict__ q
         else if (!kVerify || !kVec)
             acc = face_item_rows<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, wq);
         else if (inner)
-            face_item_inner<kVerify>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
+            face_item_inner<kVerify, kOne>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc,
                                      s_queue[threadIdx.x >> 5], s_ring[threadIdx.x >> 5]);
         else
             acc = face_item_rows_call<kVerify, kVec>(q, H, W, T, t, ib, j0, mask_out, mask_in, uv, g1, g2, acc, wq);
@@ -792,7 +797,10 @@ void launch_verify(const int32_t* qhat, const uint16_t* mask, const float* uv, i
     const int2* q2 = reinterpret_cast<const int2*>(qhat);
     const float2* x2 = reinterpret_cast<const float2*>(uv);
     const float g1 = std::ldexp(1.0f, a), g2 = std::ldexp(1.0f, b);
-    if (W % 2 == 0)
+    if (W % 2 == 0 && k >= -127 && k <= 126)  // 2^-k a normal float: one multiply
+        face_kernel<true, true, true><<<face_blocks<true, true>(H, W, t_count), 256, 0, s>>>(
+            q2, H, W, T, nullptr, mask, x2, std::ldexp(1.0f, -k), 1.0f, nullptr, out, t_first, t_count);
+    else if (W % 2 == 0)
         face_kernel<true, true><<<face_blocks<true, true>(H, W, t_count), 256, 0, s>>>(
             q2, H, W, T, nullptr, mask, x2, g1, g2, nullptr, out, t_first, t_count);
     else
