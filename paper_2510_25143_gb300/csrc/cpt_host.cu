@@ -649,9 +649,8 @@ struct FieldJob {
         CPT_CUDA(ar.alloc(&d_cls, ND));
         CPT_CUDA(ar.alloc(&d_clsm, ND));
         CPT_CUDA(ar.alloc(&d_qdiag, ND));
-        CPT_CUDA(cudaMemsetAsync(d_cls, 0, ND * sizeof(int2), s));
-        CPT_CUDA(cudaMemsetAsync(d_clsm, 0, ND * sizeof(unsigned), s));
-        CPT_CUDA(cudaMemsetAsync(d_qdiag, 0, ND * sizeof(int2), s));
+        // classification writes every vertex's entry; only the padding is zeroed
+        launch_diag_pad(d_cls, d_clsm, d_qdiag, H, W, T, s);
         CPT_CUDA(ar.alloc(&d_psl, want_sl ? N : 1));
         if (dbg && dbg->xi) CPT_CUDA(ar.alloc(&d_xiout, N));
         CPT_CUDA(cudaMemsetAsync(d_modes, 0, (size_t)T * nby * nbx, s));

@@ -143,6 +143,9 @@ void launch_force_lossless(const uint8_t* flags, int H, int W, int T, int2* cls,
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, int2* qd, cudaStream_t s, int t_first = 0, int t_count = -1);
 inline size_t diag_elems(int H, int W, int T) { return (size_t)T * ((H + 31) / 32) * (W + 31) * 32; }
+// zeroes the entries of launch_classify's three strip-diagonal outputs that
+// hold no vertex (slices [0, T)); launch_classify over [0, T) writes the rest
+void launch_diag_pad(int2* cls, unsigned* cls_m, int2* qd, int H, int W, int T, cudaStream_t s);
 cudaError_t launch_encode_pipeline(const PipeArgs& p, int pred, int nsm, const PipeTuning& tune, cudaStream_t s);
 void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s);
 constexpr int kLog2Tab = 4097;  // counts of at most 2 * 32 * 32 sampled symbols

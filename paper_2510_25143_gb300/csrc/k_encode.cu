@@ -1300,6 +1300,50 @@ void launch_log2_table(unsigned long long* tab, int n, cudaStream_t s) {
     log2_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(tab, n);
 }
 
+// The padding of classify_kernel's strip-diagonal outputs: entries (strip,
+// step s, lane l) with no vertex, i.e. s < l or s - l >= W (the first and last
+// 31 steps of a strip), and every step of the lanes past H in a last, partial
+// strip.  classify_kernel writes every other entry of slices [0, T), so this
+// replaces zeroing the whole arrays.  One thread per entry of those steps.
+__global__ void __launch_bounds__(256) diag_pad_kernel(int2* __restrict__ cls, unsigned* __restrict__ cls_m,
+                                                       int2* __restrict__ qd, int H, int W, int T) {
+    const int nstrips = (H + 31) >> 5;
+    const int S = W + 31;  // steps per strip
+    const int rows_last = H - ((nstrips - 1) << 5);
+    const long long n_edge = (long long)T * nstrips * 62 * 32;
+    const long long n_mid = rows_last < 32 && W > 31 ? (long long)T * (W - 31) * 32 : 0;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n_edge + n_mid;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int lane = (int)(x & 31);
+        int t, strip, st;
+        if (x < n_edge) {
+            const long long line = x >> 5;  // (t, strip, edge step)
+            const int e = (int)(line % 62);
+            const long long ts = line / 62;
+            strip = (int)(ts % nstrips);
+            t = (int)(ts / nstrips);
+            st = e < 31 ? e : W + (e - 31);
+        } else {  // the middle steps of the partial strip
+            const long long line = (x - n_edge) >> 5;
+            st = 31 + (int)(line % (W - 31));
+            t = (int)(line / (W - 31));
+            strip = nstrips - 1;
+        }
+        const int i = (strip << 5) + lane, j = st - lane;
+        if (i < H && j >= 0 && j < W) continue;  // a vertex's entry
+        const size_t dv = (((size_t)t * nstrips + strip) * (size_t)S + st) * 32 + lane;
+        cls[dv] = make_int2(0, 0);
+        cls_m[dv] = 0u;
+        qd[dv] = make_int2(0, 0);
+    }
+}
+
+void launch_diag_pad(int2* cls, unsigned* cls_m, int2* qd, int H, int W, int T, cudaStream_t s) {
+    const long long n = (long long)T * ((H + 31) / 32) * 62 * 32 + (long long)T * (W > 31 ? W - 31 : 0) * 32;
+    const long long blocks = std::min<long long>((n + 255) / 256, 152 * 16);
+    diag_pad_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(cls, cls_m, qd, H, W, T);
+}
+
 void launch_classify(const int32_t* q, const uint16_t* mask, int H, int W, int T, int eps_int, int2* out,
                      unsigned* out_m, int2* qd, cudaStream_t s, int t_first, int t_count) {
     if (t_count < 0) t_count = T - t_first;
