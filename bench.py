@@ -61,6 +61,7 @@ KERNEL_NAMES = {"range_fixed": "range_kernel + to_fixed_kernel", "face_masks": "
 # sources hash as they did when captured.  (stage, predictor) -> file
 PROFILES = {
     ("wavefront", "mop"): "encode_pipeline_turb1024_mop.md",
+    ("wavefront", "learned"): "encode_pipeline_turb1024_learned.md",
     ("face_masks", None): "face_test_turb1024.md",
     ("incident_bounds", None): "classify_turb1024.md",
     ("verify", None): "verify_turb1024.md",
@@ -193,14 +194,27 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def bench_model(pred, n_params):
+    """The learned predictors' net for --pred learned / learned_mop: seeded
+    random bfloat16 parameters, N(0, 0.03) rounded to nearest even (the
+    inference cost does not depend on the values; for profiling).  None for
+    the plain predictors."""
+    import numpy as np
+    if not pred.startswith("learned"):
+        return None
+    u = np.random.default_rng(7).normal(0.0, 0.03, n_params).astype(np.float32).view(np.uint32)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
 def cpu_oracle_run(uv_sample, eb_abs, pred, min_seconds):
     """Times the oracle as it stands on uv_sample (absolute bound eb_abs, the
     workload's bound), repeating for >= min_seconds on one host thread."""
     import oracle
     oracle.lib()
+    model = bench_model(pred, oracle.net_params())
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.compress(uv_sample, eb_abs, eb_mode="abs", pred=pred, debug=False)
+        oracle.compress(uv_sample, eb_abs, eb_mode="abs", pred=pred, debug=False, model=model)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
@@ -253,12 +267,13 @@ def reference_arm(args):
     T_full = uv.shape[0]
     del uv
     oracle.lib()
+    model = bench_model(args.pred, oracle.net_params())
     for _ in range(args.warmup):
-        oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False)
+        oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False, model=model)
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False)
+        last = oracle.compress(sample, eps, eb_mode="abs", pred=args.pred, debug=False, model=model)
     el = time.perf_counter() - t0
     ms = el / args.steps * 1e3
     value = sample.nbytes / 1e6 / (ms / 1e3)
@@ -314,7 +329,7 @@ def ours(args):
     stream = torch.cuda.current_stream()
     # the pipeline's schedule is autotuned on the first (warm-up) call,
     # unless --schedule fixes it (profiling: every launch then has one shape)
-    kw = dict(eb_mode="rel", pred=args.pred, verify=True, tune=True)
+    kw = dict(eb_mode="rel", pred=args.pred, verify=True, tune=True, model=bench_model(args.pred, cpt.NET_PARAMS))
     if args.schedule:
         kw.update(tune=False, schedule=tuple(int(x) for x in args.schedule.split(",")))
 
@@ -664,7 +679,8 @@ def main():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="turb1024", choices=["turb1024", "street512", "jets721", "vortex64"])
     p.add_argument("--slices", type=int, default=0, help="cut the workload to its first N slices (profiling)")
-    p.add_argument("--pred", default="mop", choices=["lorenzo", "sl", "mop"])
+    p.add_argument("--pred", default="mop", choices=["lorenzo", "sl", "mop", "learned", "learned_mop"],
+                   help="predictor; the learned ones run a seeded random net (profiling)")
     p.add_argument("--schedule", default="", help="fixed pipeline schedule, six comma-separated integers "
                    "(cpt_params.schedule) instead of the autotuned one")
     p.add_argument("--cpu-slices", type=int, default=2)
