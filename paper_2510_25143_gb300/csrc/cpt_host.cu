@@ -2882,7 +2882,7 @@ cpt_status cpt_pipeline_order(int32_t nfields, const int32_t* fields, const int3
     *n_items = total;
     if (!items) return CPT_OK;
     const cpt::PipeTuning tune = schedule ? cpt::PipeTuning{schedule[0], schedule[1], schedule[2], schedule[3],
-                                                            schedule[4]}
+                                                            schedule[4], schedule[5]}
                                           : cpt::PipeTuning{};
     std::vector<int4> order;
     cpt::merged_order(fs, tune, order);
