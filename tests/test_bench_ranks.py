@@ -55,3 +55,25 @@ def test_reference_arm_only_rank0_prints():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("pred", ["mop", "learned"])
+def test_reference_arm_line(pred):
+    """Rank 0's reference arm (the oracle on the host) prints one JSON line
+    with the keys the benchmark contract names; --pred learned runs the
+    oracle with the bench's seeded net."""
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "vortex64", "--pred", pred, "--steps", "1", "--warmup", "0", "--cpu-slices", "2"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "MB/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["config"]["workload"] == "vortex64" and d["config"]["pred"] == pred
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["ratio"] > 1.0
