@@ -153,8 +153,12 @@ typedef struct {
     uint64_t n_ld, n_qd;
     uint64_t verify_mismatch_slice;  /* FC_t: slice faces whose predicate changed */
     uint64_t verify_mismatch_slab;   /* FC_s: slab faces whose predicate changed */
-    double linf;              /* max |x_hat - x| */
-    double psnr;
+    double linf;              /* max |x_hat - x| over both components: the exact largest
+                                 difference of the float32 values, rounded once to double
+                                 (0 without params->verify) */
+    double psnr;              /* 20 log10(value range) - 10 log10(mean squared difference); the
+                                 squares are summed in float32 per thread (a statistic, not
+                                 bit-reproducible) */
     double ratio;             /* input bytes / output bytes */
     uint64_t out_bytes;
     uint64_t raw_bytes;       /* bytes of the stream before the optional ZSTD frame */
